@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the boosted-frame PIC step on GB300.
+
+One step = the whole hot path of the method: gather + Boris push + Esirkepov
+deposit of the electrons (one fused kernel), deposit of the drifting ions,
+laser antenna, binomial current filter, Yee update and injection of the
+plasma entering the box.  Default workload: the 3D gamma_boost = 13 stage
+(256 x 256 x 1024 cells, 2x2x2 electrons per cell, ~535M electrons plus as
+many drifting ions), FP32.  The metric is electron particle-steps per second
+of whole steps, with all state resident in HBM; `e2e` is the same metric
+through the C ABI with the initial state restored from pinned host memory and
+the on-axis field line read back to the host after every step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torchrun) every rank runs an independent replica of
+the workload on its own GPU: the stage does not shard across GPUs here, the
+replicas exchange nothing, and rank 0 prints one JSON line.  `--impl
+reference` times the FP64 CPU oracle on a bounded slab of the same stage.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (gather+push+deposit+Yee), %HBM roofline, adjoint/forward time"
+UNIT = "particle-steps/s"
+# algorithmic bytes per electron particle-step of the fused gather/push/deposit
+# kernel in 3D: particle state read 32 B + written 28 B, plus fields read
+# (24 B/cell) and current written (12 B/cell) amortised over ppc = 8
+BYTES_PER_PARTICLE_STEP_3D = 60.0 + 36.0 / 8.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--slots-per-cell", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "", 1).isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        pw = [float(r[3]) for r in self.rows if r[3].replace(".", "", 1).isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows), "power_w_max": max(pw) if pw else None}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_from_profiles(kernel_key: str):
+    """DRAM bytes per launch of the kernel from the committed ncu summary, if
+    that summary is for the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel_key)
+    if not e:
+        return None
+    from paper_1011_0917_gb300 import build
+    import hashlib
+    h = hashlib.sha256(open(os.path.join(build.CSRC, "pic_particles.cu"), "rb").read()).hexdigest()[:16]
+    if e.get("source_sha") != h:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# --------------------------------------------------------------------- ours
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_1011_0917_gb300 as P
+    from paper_1011_0917_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    st = W.stage(args.workload)
+    g = st.grid
+    stream = torch.cuda.Stream()
+    sim = P.Simulation(dim=g["dim"], nx=g["nx"], ny=g["ny"], nz=g["nz"], dx=g["dx"], dy=g["dy"], dz=g["dz"],
+                       cfl=g["cfl"], gamma_boost=g["gamma_boost"], shape_order=g["shape_order"],
+                       filter_passes=g["filter_passes"], bc_z=g["bc_z"], precision=P.PIC_FP32, seed=g["seed"],
+                       slots_per_cell=args.slots_per_cell, stream=stream)
+    p = st.plasma
+    sim.load_plasma(p["ne"], p["z_start"], p["z_end"], p["ramp"], p["ppc"], p["jitter"], (), p["ions"])
+    l = st.laser
+    sim.launch_laser(l["a0"], l["waist"], l["fwhm"], l["z_antenna"], -1.0, l["pol"])
+    ctx = sim.ctx
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # warm-up (untimed)
+    P.pic_step(ctx, args.warmup)
+    d0 = sim.diagnostics()
+    P.pic_profile(ctx, True)
+    P.pic_profile_read(ctx)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    P.pic_step_async(ctx, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clock_info = clocks.stop()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    phase_ms, phase_calls, kernels = P.pic_profile_read(ctx)
+    P.pic_profile(ctx, False)
+    d1 = sim.diagnostics()
+    n_e = 0.5 * (d0.n_particles[0] + d1.n_particles[0])
+    n_i = 0.5 * (d0.n_particles[1] + d1.n_particles[1])
+    psteps = n_e * args.steps
+
+    # whole-job aggregation: max time, summed work
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        w_ = torch.tensor([psteps], device="cuda", dtype=torch.float64)
+        dist.all_reduce(w_, op=dist.ReduceOp.SUM)
+        psteps = float(w_.item())
+    value = psteps / (ms * 1e-3)
+
+    # roofline of the dominant kernel (the fused electron gather/push/deposit)
+    push_ms = phase_ms[1] / max(phase_calls[1], 1)
+    algo_bytes = BYTES_PER_PARTICLE_STEP_3D * n_e if g["dim"] == 3 else (52.0 + 36.0 / 4) * n_e
+    achieved = algo_bytes / (push_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    phases = ["zero_j", "push", "ions", "antenna", "filter", "yee", "inject", "time"]
+    share = {phases[i]: round(phase_ms[i] / max(sum(phase_ms), 1e-30), 4) for i in range(7)}
+
+    # end to end through the C ABI: restore the initial state from pinned host
+    # memory, then each step read the on-axis E_z line back to the host
+    e2e = None
+    if not args.no_e2e:
+        nbytes = P.pic_state_bytes(ctx)
+        host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        P.pic_get_state(ctx, host.data_ptr(), nbytes, False)
+        line = torch.empty(g["nz"] + 1, dtype=torch.float32, pin_memory=True)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        P.pic_set_state(ctx, host.data_ptr(), nbytes, False)
+        for _ in range(args.steps):
+            P.pic_step_async(ctx, 1)
+            P.pic_get_axis(ctx, 2, line.data_ptr(), line.numel() * 4, False)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        el = t1 - t0
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": (n_e * args.steps * world) / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(nbytes // args.steps), "d2h_bytes_per_step": int(line.numel() * 4),
+               "note": "initial state restored from pinned host memory once per job of --steps steps; "
+                       "on-axis Ez line read back after every step"}
+        del host
+
+    result = None
+    if rank == 0:
+        cpu = None if args.no_cpu_baseline else cpu_baseline(args.workload, steps=4)
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded lattice plasma + Gaussian laser antenna)",
+            "config": {"workload": workload_name(args.workload), "n_electrons": n_e, "n_drift_ions": n_i,
+                       "grid": [g["nx"], g["ny"], g["nz"]], "gamma_boost": g["gamma_boost"],
+                       "filter_passes": g["filter_passes"], "shape_order": g["shape_order"],
+                       "slots_per_cell": args.slots_per_cell,
+                       "l2": "inputs larger than L2 (particle store >> 129 MB)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": traffic_from_profiles("push_kernel<float,3,1>"),
+                         "kernel": "push_kernel<float,3,1> (gather+Boris+Esirkepov+re-bucket)",
+                         "bytes_per_unit": BYTES_PER_PARTICLE_STEP_3D, "unit_of_work": "electron particle-step",
+                         "ms_per_launch": push_ms},
+            "phase_share": share,
+            "e2e": e2e,
+            "gpu_launches": int(kernels),
+            "clocks": clock_info,
+            "cpu_baseline": cpu,
+            "adjoint_forward_ratio": None,
+        }
+    sim.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return result
+
+
+def workload_name(w: str) -> str:
+    names = {
+        "c2": "3D boosted frame gamma=13, 256x256x1024 cells, 2x2x2 electrons/cell (+drifting ions), CIC, "
+              "2 binomial passes, FP32",
+        "c1": "2D3V boosted frame gamma=13, 256x8192 cells, 2x2 electrons/cell, CIC, 2 passes, FP32",
+        "c0": "2D3V lab frame, 64x512 cells, 2x2 electrons/cell, CIC, 1 pass, FP32",
+    }
+    return names.get(w, w)
+
+
+# ------------------------------------------------------------------ oracle
+
+
+def oracle_slab(workload: str):
+    """A bounded slab of the workload for the FP64 CPU oracle: same cell
+    sizes, boost, shape, filter, density and lattice, fewer cells."""
+    import oracle.oracle as O
+    from paper_1011_0917_gb300 import workloads as W
+    st = W.stage(workload)
+    g = dict(st.grid)
+    if g["dim"] == 3:
+        g.update(nx=32, ny=32, nz=64)
+    else:
+        g.update(nx=min(g["nx"], 64), nz=min(g["nz"], 256))
+    o = O.Oracle(O.GridParams(dim=g["dim"], nx=g["nx"], ny=g["ny"], nz=g["nz"], dx=g["dx"], dy=g["dy"], dz=g["dz"],
+                              cfl=g["cfl"], gamma_boost=g["gamma_boost"], shape=g["shape_order"],
+                              npass=g["filter_passes"], bc_z=g["bc_z"], seed=g["seed"]))
+    p = st.plasma
+    o.load_plasma(O.PlasmaParams(ne=p["ne"], z_start=p["z_start"], z_end=p["z_end"], ramp=p["ramp"], ppc=p["ppc"],
+                                 jitter=p["jitter"], ions=p["ions"]))
+    l = st.laser
+    o.set_laser(O.LaserParams(a0=l["a0"], waist=l["waist"], fwhm=l["fwhm"], z_antenna=l["z_antenna"], pol=l["pol"]))
+    return o, g
+
+
+def cpu_baseline(workload: str, steps: int = 2):
+    o, g = oracle_slab(workload)
+    n = o.num(0)
+    t0 = time.perf_counter()
+    o.step(steps)
+    el = time.perf_counter() - t0
+    return {"value": n * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{g['nx']}x{g['ny']}x{g['nz']} slab of the same stage, {n} electrons (+{o.num(1)} ions), "
+                      f"{steps} steps, {el:.1f} s, single-threaded FP64 C"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    o, g = oracle_slab(args.workload)
+    o.step(args.warmup)
+    n = o.num(0)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    el = time.perf_counter() - t0
+    value = n * args.steps / el
+    sample = (f"{g['nx']}x{g['ny']}x{g['nz']} slab of the same stage per step, {n} electrons "
+              f"(+{o.num(1)} ions), single-threaded FP64 C oracle")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded lattice plasma + Gaussian laser antenna)",
+            "config": {"workload": workload_name(args.workload), "parallelism": "host cores, rank 0 only"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

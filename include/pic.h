@@ -1,0 +1,277 @@
+/*
+ * pic.h -- C ABI of the GB300 (sm_103a) boosted-frame electromagnetic
+ * particle-in-cell library.
+ *
+ * The library advances a laser-plasma stage in a frame Lorentz-boosted along
+ * the laser axis z (Vay et al., arXiv:1011.0917, introduction and section
+ * "Effect of the hyperbolic rotation in Minkowski space": the boost contracts
+ * the plasma and dilates the laser so that far fewer steps are needed).  One
+ * step is: field gather and relativistic Boris push of the electrons,
+ * Esirkepov charge-conserving current deposition (electrons and, in a boosted
+ * frame, the ions drifting at -beta), the laser antenna current, binomial
+ * filtering of the current (section "Mitigation of a numerical instability":
+ * filtering of short wavelengths), the Yee update of B and E, and injection
+ * of the plasma that enters the box.
+ *
+ * Units everywhere in this interface: lengths in the laser wavelength lambda0,
+ * times in lambda0/c, momenta u = gamma v / c, fields in m c omega0 / e (a laser
+ * of normalised amplitude a0 has peak E = a0), densities in the critical
+ * density n_c.  Lab-frame inputs are transformed to the simulation frame by
+ * the library in FP64.
+ *
+ * Memory: the CALLER owns all device memory.  pic_query_sizes() reports the
+ * byte size of each buffer; the caller allocates them on the device (256-byte
+ * aligned) and passes them to pic_bind_buffers().  The library owns only its
+ * small host context.  All device work is enqueued on the stream given in
+ * pic_grid_params; calls that return data synchronise that stream.
+ *
+ * Errors: every call returns a pic_status; no exception or longjmp crosses the
+ * ABI.  pic_last_error() gives a human-readable detail of the last failure of
+ * a context.  A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pic_status {
+    PIC_OK = 0,
+    PIC_ERR_ARG = 1,      /* invalid argument or size                          */
+    PIC_ERR_STATE = 2,    /* call out of order (e.g. step before bind)         */
+    PIC_ERR_CUDA = 3,     /* a CUDA call failed; detail in pic_last_error      */
+    PIC_ERR_CAPACITY = 4, /* a tile bucket overflowed; particles were dropped  */
+    PIC_ERR_CFL = 5,      /* a particle moved a cell or more in one step       */
+    PIC_ERR_NAN = 6,      /* a non-finite momentum or position was produced    */
+    PIC_ERR_TIMEOUT = 7   /* reserved for bounded device waits                 */
+} pic_status;
+
+enum { PIC_BC_PERIODIC = 0, PIC_BC_MUR = 1 };       /* z boundary (x, y periodic) */
+enum { PIC_FP32 = 0, PIC_FP64 = 1 };                /* arithmetic of the path     */
+enum { PIC_ELECTRONS = 0, PIC_IONS = 1 };           /* species index              */
+enum { PIC_POL_X = 0, PIC_POL_Y = 1 };              /* laser polarisation         */
+
+/* field components, bit i of a component mask selects component i */
+enum {
+    PIC_EX = 0, PIC_EY = 1, PIC_EZ = 2, PIC_BX = 3, PIC_BY = 4, PIC_BZ = 5,
+    PIC_JX = 6, PIC_JY = 7, PIC_JZ = 8, PIC_NCOMP = 9
+};
+
+/* Phases of one step, in the order pic_step runs them (a mask of these bits
+   selects a subset for pic_step_phases; PIC_PH_ALL is one full step):
+     ZERO_J   J = 0
+     PUSH     electrons: gather E^n, B^n at x^n, Boris u^{n-1/2} -> u^{n+1/2},
+              x^{n+1} = x^n + dt u/gamma, Esirkepov J^{n+1/2}, boundaries,
+              re-bucketing by tile
+     IONS     ions (boosted frame): constant drift, deposit, boundaries
+     ANTENNA  laser current sheet at t^{n+1/2}
+     FILTER   filter_passes binomial passes along each axis on Jx, Jy, Jz
+     YEE      B -= dt/2 curl E; E += dt (curl B - 2 pi J) (+ Mur); B -= dt/2 curl E
+     INJECT   plasma crossing z = Lz during (t, t+dt] appended at x^{n+1}
+     TIME     t += dt (FP64 host accumulator)                                  */
+#define PIC_PH_ZERO_J 1u
+#define PIC_PH_PUSH 2u
+#define PIC_PH_IONS 4u
+#define PIC_PH_ANTENNA 8u
+#define PIC_PH_FILTER 16u
+#define PIC_PH_YEE 32u
+#define PIC_PH_INJECT 64u
+#define PIC_PH_TIME 128u
+#define PIC_PH_ALL 255u
+
+typedef struct pic_ctx pic_ctx;
+
+/* Grid and numerics.  Lab-frame cell sizes: the simulation-frame ones are
+   hx = dx, hy = dy, hz = dz * gamma * (1 + beta) (same cells per Doppler-
+   stretched laser wavelength), dt = cfl / sqrt(sum 1/h_d^2). */
+typedef struct pic_grid_params {
+    int dim;                /* 2: (x, z) with y ignorable (2D3V); 3: (x, y, z)  */
+    int nx, ny, nz;         /* cells; ny must be 1 when dim == 2                */
+    double dx, dy, dz;      /* lab-frame cell sizes, lambda0 (dy unused in 2D) */
+    double cfl;             /* time step as a fraction of the Courant limit, <1 */
+    double gamma_boost;     /* Lorentz factor of the frame, >= 1                */
+    int shape_order;        /* 1: linear (CIC), 2: quadratic spline             */
+    int filter_passes;      /* binomial passes per axis, >= 0                   */
+    int bc_z;               /* PIC_BC_MUR or PIC_BC_PERIODIC                    */
+    int precision;          /* PIC_FP32 (production) or PIC_FP64 (debug)        */
+    uint64_t seed;          /* SplitMix64 seed of the plasma jitter             */
+    double slots_per_cell;  /* particle slots per cell and species, > 0         */
+    int tile[3];            /* tile shape in cells, powers of two; 0: default   */
+    int track_ids;          /* 1: carry an int64 lattice id with each particle */
+    void *stream;           /* cudaStream_t for all device work (NULL: legacy)  */
+} pic_grid_params;
+
+/* Sizes of the caller-owned device buffers and derived quantities. */
+typedef struct pic_sizes {
+    size_t field_bytes;        /* 9 components x (nz+1) x ny x nx elements         */
+    size_t species_bytes[2];   /* particle store per species (two bucket sides)    */
+    size_t scratch_bytes;      /* tile counters, filter buffer, error word, ...    */
+    int64_t slots[2];          /* particle slots per side and species              */
+    int64_t ntiles;            /* number of tiles                                  */
+    int tile_capacity;         /* slots per tile                                   */
+    int tile[3];               /* tile shape in cells                              */
+    int elem_bytes;            /* 4 (FP32) or 8 (FP64)                             */
+    double dt, hx, hy, hz;     /* simulation-frame step and cell sizes, lambda0    */
+    double beta;               /* boost velocity / c                               */
+} pic_sizes;
+
+typedef struct pic_buffers {
+    void *fields;              /* field_bytes                                      */
+    void *species[2];          /* species_bytes[s]; species[1] may be NULL if 0    */
+    void *scratch;             /* scratch_bytes                                    */
+} pic_buffers;
+
+/* Plasma at rest in the lab frame, loaded on a lattice of ppc points per cell
+   and axis with a uniform jitter; in a boosted frame it drifts at -beta and
+   is contracted by gamma, and the part beyond z = Lz enters the box later. */
+typedef struct pic_plasma_params {
+    double ne_over_nc;         /* lab-frame electron density / n_c                 */
+    double z_start, z_end;     /* lab-frame extent, lambda0                        */
+    double ramp_len;           /* linear up-ramp length from z_start, lambda0      */
+    int ppc[3];                /* lattice points per cell and axis (ppc[1] 2D: 1)  */
+    double jitter;             /* uniform jitter half width, cells, in [0, 0.5)    */
+    int n_profile;             /* number of cosine-profile coefficients, <= 16     */
+    const double *profile;     /* c_m: n = n0 (1 + sum_m c_m cos(m pi zeta))      */
+    int ions;                  /* 1: ions immobile in the lab frame                */
+} pic_plasma_params;
+
+/* Linearly polarised Gaussian laser, lab-frame parameters.  The antenna is a
+   current sheet at rest in the simulation frame on the node plane nearest to
+   z_antenna (at least 2 nodes from either z end). */
+typedef struct pic_laser_params {
+    double a0;                 /* peak normalised amplitude                        */
+    double waist;              /* 1/e field radius, lambda0                        */
+    double fwhm;               /* intensity FWHM duration, lambda0/c               */
+    double z_antenna;          /* antenna plane, simulation frame, lambda0         */
+    double t_peak;             /* envelope peak (lab time at antenna); <0: 3 tau   */
+    int polarization;          /* PIC_POL_X or PIC_POL_Y                           */
+    double x_center, y_center; /* transverse centre, lambda0; NaN: box centre      */
+} pic_laser_params;
+
+typedef struct pic_diag {
+    double t;                  /* simulation-frame time                            */
+    int64_t step;              /* steps taken                                      */
+    int64_t n_particles[2];    /* live particles per species                       */
+    double field_energy;       /* (1/2) sum (E^2 + B^2) V, Kahan-compensated FP64   */
+    double kinetic_energy;     /* sum w (gamma - 1) of the electrons, FP64 Kahan   */
+    double charge;             /* sum q w of both species, FP64 Kahan              */
+} pic_diag;
+
+/* ---------------------------------------------------------------- set-up */
+
+/* Validates the parameters and creates a context.  PIC_ERR_CFL if cfl >= 1,
+   PIC_ERR_ARG for any other invalid field.  *out is NULL on failure. */
+pic_status pic_init_grid(const pic_grid_params *p, pic_ctx **out);
+
+/* Buffer sizes and derived quantities of a context. */
+pic_status pic_query_sizes(const pic_ctx *ctx, pic_sizes *out);
+
+/* Binds the caller-owned device buffers and clears them (fields, particle
+   counts, error word) on the stream.  Pointers must be 256-byte aligned and
+   at least the queried sizes.  May be called once per context. */
+pic_status pic_bind_buffers(pic_ctx *ctx, const pic_buffers *b);
+
+/* Generates the plasma on the device: every lattice point whose simulation-
+   frame position at the current time lies in the box becomes an electron
+   (and, boosted with ions, a drifting ion at the same place); the rest of a
+   boosted plasma is injected as it crosses z = Lz.  Lab-frame immobile ions
+   are a neutralising background and carry no current.  The lattice id of a
+   point with indices (ix, iy, iz) is (iz * NY + iy) * NX + ix, NX = nx*ppc[0],
+   NY = ny*ppc[1] (1 in 2D).  PIC_ERR_CAPACITY if a tile overflowed. */
+pic_status pic_load_plasma(pic_ctx *ctx, const pic_plasma_params *p);
+
+/* Appends n particles given as host FP64 arrays (simulation frame):
+   state[a*n + i] for a = 0..6 = x, y, z, ux, uy, uz, w.  Ions take the
+   species' drift momentum and ignore ux, uy, uz.  ids (may be NULL) are kept
+   when track_ids is set.  Positions outside the box are rejected
+   (PIC_ERR_ARG); PIC_ERR_CAPACITY if a tile overflowed. */
+pic_status pic_load_particles(pic_ctx *ctx, int species, int64_t n, const double *state,
+                              const int64_t *ids);
+
+/* Sets the laser; the antenna current is added in every later step. */
+pic_status pic_launch_laser(pic_ctx *ctx, const pic_laser_params *p);
+
+/* ------------------------------------------------------------------ step */
+
+/* Advances nsteps full steps, synchronises the stream and checks the device
+   error word (PIC_ERR_CAPACITY / PIC_ERR_CFL / PIC_ERR_NAN). */
+pic_status pic_step(pic_ctx *ctx, int nsteps);
+
+/* Same as pic_step without the synchronisation and the error check. */
+pic_status pic_step_async(pic_ctx *ctx, int nsteps);
+
+/* One step restricted to the phases in mask (PIC_PH_* bits), synchronised
+   and checked like pic_step.  Used to test each phase on its own. */
+pic_status pic_step_phases(pic_ctx *ctx, unsigned mask);
+
+/* --------------------------------------------------------------- output */
+
+/* Copies the components selected by mask, in component order, each as
+   (nz+1) x ny x nx elements of elem_bytes in [k][j][i] order (the native
+   layout; the plane k = nz of Ez, Bx, By, Jz is unused and zero).  dst may be
+   host (dst_is_device = 0) or device memory; dst_bytes must hold them all. */
+pic_status pic_get_fields(pic_ctx *ctx, unsigned mask, void *dst, size_t dst_bytes,
+                          int dst_is_device);
+
+/* Overwrites the selected components from src, same layout as pic_get_fields. */
+pic_status pic_set_fields(pic_ctx *ctx, unsigned mask, const void *src, size_t src_bytes,
+                          int src_is_device);
+
+/* Component c on the line i = nx/2, j = ny/2, k = 0..nz (nz+1 elements of
+   elem_bytes): the on-axis field history diagnostic of the paper's Fig. 2. */
+pic_status pic_get_axis(pic_ctx *ctx, int component, void *dst, size_t dst_bytes,
+                        int dst_is_device);
+
+/* Live particles of a species as host FP64 arrays in the pic_load_particles
+   layout (order unspecified); *n_out receives the count.  With dst == NULL
+   only *n_out is set.  ids (may be NULL) receives the lattice ids when
+   track_ids is set. */
+pic_status pic_get_particles(pic_ctx *ctx, int species, double *dst, size_t dst_bytes,
+                             int64_t *n_out, int64_t *ids);
+
+/* Nodal charge density (nz+1) x ny x nx of the particles (electrons and
+   drifting ions, shape of the grid's order), elem_bytes each, into host or
+   device memory.  Lab-frame immobile ions are not included. */
+pic_status pic_get_rho(pic_ctx *ctx, void *dst, size_t dst_bytes, int dst_is_device);
+
+/* Time, counts and FP64 Kahan-compensated sums (synchronises the stream). */
+pic_status pic_get_diagnostics(pic_ctx *ctx, pic_diag *out);
+
+/* ------------------------------------------------------------ checkpoint */
+
+/* Size of a compact snapshot (fields, live particles, time, laser) now. */
+pic_status pic_state_bytes(pic_ctx *ctx, size_t *bytes);
+
+/* Writes the snapshot to host or device memory. */
+pic_status pic_get_state(pic_ctx *ctx, void *dst, size_t dst_bytes, int dst_is_device);
+
+/* Restores a snapshot taken from a context with the same grid parameters.
+   PIC_ERR_ARG if it does not match; PIC_ERR_CAPACITY on bucket overflow. */
+pic_status pic_set_state(pic_ctx *ctx, const void *src, size_t src_bytes, int src_is_device);
+
+/* -------------------------------------------------------------- profiling */
+
+/* While enabled, every phase of later steps is bracketed by CUDA events on the
+   context's stream and the kernels the library launches are counted. */
+pic_status pic_profile(pic_ctx *ctx, int enable);
+
+/* Accumulated device time since the last read: ms[i] milliseconds and calls[i]
+   runs of phase bit i (i = 0..7, PIC_PH_ZERO_J .. PIC_PH_TIME), *kernels the
+   number of kernel launches.  Synchronises the stream and resets the sums.
+   Any output pointer may be NULL. */
+pic_status pic_profile_read(pic_ctx *ctx, double ms[8], int64_t calls[8], int64_t *kernels);
+
+/* ------------------------------------------------------------------ misc */
+
+const char *pic_last_error(const pic_ctx *ctx);
+const char *pic_status_string(pic_status s);
+void pic_destroy(pic_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIC_H */

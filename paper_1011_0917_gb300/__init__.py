@@ -1,0 +1,364 @@
+"""GB300 (sm_103a) boosted-frame electromagnetic PIC library -- Python binding.
+
+Thin ctypes binding of the C ABI in ``include/pic.h``: the functions below
+carry the same names and marshal arguments only; every step of the PIC loop
+runs in the CUDA kernels of ``libpic.so``.  PyTorch provides the device memory
+(the caller-owned buffers the library asks for) and the CUDA stream.
+
+There is no CPU fallback: importing the binding when ``libpic.so`` cannot be
+built or loaded raises, and a context cannot be created without a CUDA device.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+from . import build as _build
+
+__all__ = [
+    "PIC_OK", "PicError", "GridParams", "PlasmaParams", "LaserParams", "Sizes", "Buffers", "Diag",
+    "pic_init_grid", "pic_query_sizes", "pic_bind_buffers", "pic_load_plasma", "pic_load_particles",
+    "pic_launch_laser", "pic_step", "pic_step_async", "pic_step_phases", "pic_get_fields", "pic_set_fields",
+    "pic_get_axis", "pic_get_particles", "pic_get_rho", "pic_get_diagnostics", "pic_state_bytes",
+    "pic_get_state", "pic_set_state", "pic_last_error", "pic_status_string", "pic_destroy", "pic_profile",
+    "pic_profile_read", "Simulation",
+    "library_path",
+]
+
+PIC_OK, PIC_ERR_ARG, PIC_ERR_STATE, PIC_ERR_CUDA = 0, 1, 2, 3
+PIC_ERR_CAPACITY, PIC_ERR_CFL, PIC_ERR_NAN, PIC_ERR_TIMEOUT = 4, 5, 6, 7
+PIC_BC_PERIODIC, PIC_BC_MUR = 0, 1
+PIC_FP32, PIC_FP64 = 0, 1
+PIC_ELECTRONS, PIC_IONS = 0, 1
+PIC_POL_X, PIC_POL_Y = 0, 1
+COMPONENTS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx", "Jy", "Jz")
+PH_ZERO_J, PH_PUSH, PH_IONS, PH_ANTENNA = 1, 2, 4, 8
+PH_FILTER, PH_YEE, PH_INJECT, PH_TIME = 16, 32, 64, 128
+PH_ALL = 255
+
+
+class PicError(RuntimeError):
+    def __init__(self, status: int, detail: str):
+        super().__init__(f"pic status {status}: {detail}")
+        self.status = status
+
+
+class GridParams(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double), ("cfl", C.c_double),
+                ("gamma_boost", C.c_double), ("shape_order", C.c_int), ("filter_passes", C.c_int),
+                ("bc_z", C.c_int), ("precision", C.c_int), ("seed", C.c_uint64),
+                ("slots_per_cell", C.c_double), ("tile", C.c_int * 3), ("track_ids", C.c_int),
+                ("stream", C.c_void_p)]
+
+
+class Sizes(C.Structure):
+    _fields_ = [("field_bytes", C.c_size_t), ("species_bytes", C.c_size_t * 2), ("scratch_bytes", C.c_size_t),
+                ("slots", C.c_int64 * 2), ("ntiles", C.c_int64), ("tile_capacity", C.c_int),
+                ("tile", C.c_int * 3), ("elem_bytes", C.c_int), ("dt", C.c_double), ("hx", C.c_double),
+                ("hy", C.c_double), ("hz", C.c_double), ("beta", C.c_double)]
+
+
+class Buffers(C.Structure):
+    _fields_ = [("fields", C.c_void_p), ("species", C.c_void_p * 2), ("scratch", C.c_void_p)]
+
+
+class PlasmaParams(C.Structure):
+    _fields_ = [("ne_over_nc", C.c_double), ("z_start", C.c_double), ("z_end", C.c_double),
+                ("ramp_len", C.c_double), ("ppc", C.c_int * 3), ("jitter", C.c_double),
+                ("n_profile", C.c_int), ("profile", C.POINTER(C.c_double)), ("ions", C.c_int)]
+
+
+class LaserParams(C.Structure):
+    _fields_ = [("a0", C.c_double), ("waist", C.c_double), ("fwhm", C.c_double), ("z_antenna", C.c_double),
+                ("t_peak", C.c_double), ("polarization", C.c_int), ("x_center", C.c_double),
+                ("y_center", C.c_double)]
+
+
+class Diag(C.Structure):
+    _fields_ = [("t", C.c_double), ("step", C.c_int64), ("n_particles", C.c_int64 * 2),
+                ("field_energy", C.c_double), ("kinetic_energy", C.c_double), ("charge", C.c_double)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    lib = C.CDLL(path)
+    P, S, I, U = C.c_void_p, C.c_int, C.c_int, C.c_uint
+    sig = {
+        "pic_init_grid": (S, [C.POINTER(GridParams), C.POINTER(C.c_void_p)]),
+        "pic_query_sizes": (S, [P, C.POINTER(Sizes)]),
+        "pic_bind_buffers": (S, [P, C.POINTER(Buffers)]),
+        "pic_load_plasma": (S, [P, C.POINTER(PlasmaParams)]),
+        "pic_load_particles": (S, [P, I, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+        "pic_launch_laser": (S, [P, C.POINTER(LaserParams)]),
+        "pic_step": (S, [P, I]),
+        "pic_step_async": (S, [P, I]),
+        "pic_step_phases": (S, [P, U]),
+        "pic_get_fields": (S, [P, U, P, C.c_size_t, I]),
+        "pic_set_fields": (S, [P, U, P, C.c_size_t, I]),
+        "pic_get_axis": (S, [P, I, P, C.c_size_t, I]),
+        "pic_get_particles": (S, [P, I, C.POINTER(C.c_double), C.c_size_t, C.POINTER(C.c_int64),
+                                  C.POINTER(C.c_int64)]),
+        "pic_get_rho": (S, [P, P, C.c_size_t, I]),
+        "pic_get_diagnostics": (S, [P, C.POINTER(Diag)]),
+        "pic_state_bytes": (S, [P, C.POINTER(C.c_size_t)]),
+        "pic_get_state": (S, [P, P, C.c_size_t, I]),
+        "pic_set_state": (S, [P, P, C.c_size_t, I]),
+        "pic_last_error": (C.c_char_p, [P]),
+        "pic_status_string": (C.c_char_p, [S]),
+        "pic_destroy": (None, [P]),
+        "pic_profile": (S, [P, I]),
+        "pic_profile_read": (S, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def lib():
+    return _load()
+
+
+def _check(ctx, status: int):
+    if status != PIC_OK:
+        detail = _load().pic_last_error(ctx).decode() if ctx else _load().pic_status_string(status).decode()
+        raise PicError(status, detail or _load().pic_status_string(status).decode())
+
+
+# ------------------------------------------------------ C-ABI, same names
+
+
+def pic_init_grid(params: GridParams):
+    ctx = C.c_void_p()
+    st = _load().pic_init_grid(C.byref(params), C.byref(ctx))
+    _check(None, st)
+    return ctx
+
+
+def pic_query_sizes(ctx) -> Sizes:
+    s = Sizes()
+    _check(ctx, _load().pic_query_sizes(ctx, C.byref(s)))
+    return s
+
+
+def pic_bind_buffers(ctx, bufs: Buffers):
+    _check(ctx, _load().pic_bind_buffers(ctx, C.byref(bufs)))
+
+
+def pic_load_plasma(ctx, p: PlasmaParams):
+    _check(ctx, _load().pic_load_plasma(ctx, C.byref(p)))
+
+
+def pic_load_particles(ctx, species: int, state, ids=None):
+    """state: float64 array (7, n) = x, y, z, ux, uy, uz, w (host memory)."""
+    import numpy as np
+    st = np.ascontiguousarray(np.asarray(state, dtype=np.float64))
+    n = st.shape[1] if st.ndim == 2 else 0
+    idp = None
+    if ids is not None:
+        ids = np.ascontiguousarray(np.asarray(ids, dtype=np.int64))
+        idp = ids.ctypes.data_as(C.POINTER(C.c_int64))
+    _check(ctx, _load().pic_load_particles(ctx, species, n, st.ctypes.data_as(C.POINTER(C.c_double)), idp))
+
+
+def pic_launch_laser(ctx, p: LaserParams):
+    _check(ctx, _load().pic_launch_laser(ctx, C.byref(p)))
+
+
+def pic_step(ctx, nsteps: int = 1):
+    _check(ctx, _load().pic_step(ctx, int(nsteps)))
+
+
+def pic_step_async(ctx, nsteps: int = 1):
+    _check(ctx, _load().pic_step_async(ctx, int(nsteps)))
+
+
+def pic_step_phases(ctx, mask: int):
+    _check(ctx, _load().pic_step_phases(ctx, int(mask)))
+
+
+def pic_get_fields(ctx, mask: int, dst_ptr: int, dst_bytes: int, dst_is_device: bool):
+    _check(ctx, _load().pic_get_fields(ctx, mask, C.c_void_p(dst_ptr), dst_bytes, int(dst_is_device)))
+
+
+def pic_set_fields(ctx, mask: int, src_ptr: int, src_bytes: int, src_is_device: bool):
+    _check(ctx, _load().pic_set_fields(ctx, mask, C.c_void_p(src_ptr), src_bytes, int(src_is_device)))
+
+
+def pic_get_axis(ctx, comp: int, dst_ptr: int, dst_bytes: int, dst_is_device: bool):
+    _check(ctx, _load().pic_get_axis(ctx, comp, C.c_void_p(dst_ptr), dst_bytes, int(dst_is_device)))
+
+
+def pic_get_particles(ctx, species: int, with_ids: bool = False):
+    """Returns (state (7, n) float64, ids or None)."""
+    import numpy as np
+    n = C.c_int64(0)
+    _check(ctx, _load().pic_get_particles(ctx, species, None, 0, C.byref(n), None))
+    out = np.zeros((7, n.value), dtype=np.float64)
+    ids = np.zeros(n.value, dtype=np.int64) if with_ids else None
+    if n.value:
+        _check(ctx, _load().pic_get_particles(ctx, species, out.ctypes.data_as(C.POINTER(C.c_double)), out.nbytes,
+                                              C.byref(n), ids.ctypes.data_as(C.POINTER(C.c_int64))
+                                              if ids is not None else None))
+    return out, ids
+
+
+def pic_get_rho(ctx, dst_ptr: int, dst_bytes: int, dst_is_device: bool):
+    _check(ctx, _load().pic_get_rho(ctx, C.c_void_p(dst_ptr), dst_bytes, int(dst_is_device)))
+
+
+def pic_get_diagnostics(ctx) -> Diag:
+    d = Diag()
+    _check(ctx, _load().pic_get_diagnostics(ctx, C.byref(d)))
+    return d
+
+
+def pic_state_bytes(ctx) -> int:
+    n = C.c_size_t(0)
+    _check(ctx, _load().pic_state_bytes(ctx, C.byref(n)))
+    return n.value
+
+
+def pic_get_state(ctx, dst_ptr: int, dst_bytes: int, dst_is_device: bool):
+    _check(ctx, _load().pic_get_state(ctx, C.c_void_p(dst_ptr), dst_bytes, int(dst_is_device)))
+
+
+def pic_set_state(ctx, src_ptr: int, src_bytes: int, src_is_device: bool):
+    _check(ctx, _load().pic_set_state(ctx, C.c_void_p(src_ptr), src_bytes, int(src_is_device)))
+
+
+def pic_last_error(ctx) -> str:
+    return _load().pic_last_error(ctx).decode()
+
+
+def pic_status_string(status: int) -> str:
+    return _load().pic_status_string(status).decode()
+
+
+def pic_destroy(ctx):
+    _load().pic_destroy(ctx)
+
+
+def pic_profile(ctx, enable: bool):
+    _check(ctx, _load().pic_profile(ctx, int(enable)))
+
+
+def pic_profile_read(ctx):
+    """Returns (ms[8], calls[8], kernels) accumulated since the last read."""
+    ms = (C.c_double * 8)()
+    calls = (C.c_int64 * 8)()
+    k = C.c_int64(0)
+    _check(ctx, _load().pic_profile_read(ctx, ms, calls, C.byref(k)))
+    return list(ms), list(calls), k.value
+
+
+# --------------------------------------------------- torch-owned buffers
+
+
+class Simulation:
+    """Owns one context and the torch device buffers it is bound to."""
+
+    def __init__(self, *, dim=2, nx=64, ny=1, nz=512, dx=0.5, dy=1.0, dz=1.0 / 16, cfl=0.99,
+                 gamma_boost=1.0, shape_order=1, filter_passes=1, bc_z=PIC_BC_MUR, precision=PIC_FP32,
+                 seed=10110917, slots_per_cell=8.0, tile=(0, 0, 0), track_ids=False, device="cuda",
+                 stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the PIC library needs a CUDA device; there is no CPU path")
+        self.torch = torch
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.params = GridParams(dim, nx, ny, nz, dx, dy, dz, cfl, gamma_boost, shape_order, filter_passes, bc_z,
+                                 precision, seed, slots_per_cell, (C.c_int * 3)(*tile), int(track_ids),
+                                 C.c_void_p(self.stream.cuda_stream))
+        self.ctx = pic_init_grid(self.params)
+        self.sizes = pic_query_sizes(self.ctx)
+        s = self.sizes
+
+        def alloc(n):
+            return torch.empty(max(int(n), 256), dtype=torch.uint8, device=self.device)
+
+        self.fields_buf = alloc(s.field_bytes)
+        self.species_buf = [alloc(s.species_bytes[0]), alloc(s.species_bytes[1]) if s.species_bytes[1] else None]
+        self.scratch_buf = alloc(s.scratch_bytes)
+        b = Buffers(self.fields_buf.data_ptr(),
+                    (C.c_void_p * 2)(self.species_buf[0].data_ptr(),
+                                     self.species_buf[1].data_ptr() if self.species_buf[1] is not None else None),
+                    self.scratch_buf.data_ptr())
+        pic_bind_buffers(self.ctx, b)
+        self.dtype = torch.float64 if s.elem_bytes == 8 else torch.float32
+        self.shape3 = (nz + 1, ny if dim == 3 else 1, nx)
+
+    # derived
+    @property
+    def dt(self):
+        return self.sizes.dt
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            pic_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_plasma(self, ne, z_start, z_end, ramp=0.0, ppc=(2, 1, 2), jitter=0.1, profile=(), ions=1):
+        prof = (C.c_double * max(1, len(profile)))(*profile) if len(profile) else None
+        self._prof = prof
+        p = PlasmaParams(ne, z_start, z_end, ramp, (C.c_int * 3)(*ppc), jitter, len(profile),
+                         C.cast(prof, C.POINTER(C.c_double)) if prof is not None else None, ions)
+        pic_load_plasma(self.ctx, p)
+
+    def launch_laser(self, a0, waist, fwhm, z_antenna=0.0, t_peak=-1.0, polarization=PIC_POL_Y,
+                     x_center=math.nan, y_center=math.nan):
+        pic_launch_laser(self.ctx, LaserParams(a0, waist, fwhm, z_antenna, t_peak, polarization, x_center, y_center))
+
+    def step(self, n=1):
+        pic_step(self.ctx, n)
+
+    def step_phases(self, mask):
+        pic_step_phases(self.ctx, mask)
+
+    def fields(self, mask=0x1FF):
+        """dict component -> torch tensor (nz+1, ny, nx) on the device."""
+        comps = [c for q, c in enumerate(COMPONENTS) if mask >> q & 1]
+        out = self.torch.empty((len(comps),) + self.shape3, dtype=self.dtype, device=self.device)
+        pic_get_fields(self.ctx, mask, out.data_ptr(), out.numel() * out.element_size(), True)
+        return {c: out[q] for q, c in enumerate(comps)}
+
+    def set_fields(self, values: dict):
+        for c, v in values.items():
+            q = COMPONENTS.index(c)
+            t = self.torch.as_tensor(v, dtype=self.dtype, device=self.device).contiguous().reshape(self.shape3)
+            pic_set_fields(self.ctx, 1 << q, t.data_ptr(), t.numel() * t.element_size(), True)
+
+    def rho(self):
+        out = self.torch.empty(self.shape3, dtype=self.dtype, device=self.device)
+        pic_get_rho(self.ctx, out.data_ptr(), out.numel() * out.element_size(), True)
+        return out
+
+    def particles(self, species=PIC_ELECTRONS, with_ids=False):
+        return pic_get_particles(self.ctx, species, with_ids)
+
+    def load_particles(self, species, state, ids=None):
+        pic_load_particles(self.ctx, species, state, ids)
+
+    def diagnostics(self) -> Diag:
+        return pic_get_diagnostics(self.ctx)

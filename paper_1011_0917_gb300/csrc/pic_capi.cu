@@ -1,0 +1,1085 @@
+// pic_capi.cu -- host side of the C ABI declared in include/pic.h.
+//
+// Holds the small host context (parameters, derived simulation-frame
+// quantities, the FP64 time accumulator, pointers into the caller's buffers)
+// and enqueues the kernels of pic_particles.cu, pic_fields.cu and
+// pic_inject.cu on the caller's stream.
+#include "pic.h"
+#include "pic_internal.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace pic;
+
+namespace {
+
+constexpr double kPi = 3.141592653589793;
+constexpr double kTwoPi = 6.283185307179586;
+constexpr int kPartialBlocks = 1024;
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t n) { return (n + kAlign - 1) / kAlign * kAlign; }
+
+int ceil_log2(int64_t n)
+{
+    int b = 0;
+    while ((int64_t(1) << b) < n) ++b;
+    return b;
+}
+
+struct SideLayout {  // byte offsets of the attribute arrays within one side
+    size_t off[9];   // ox oy oz w ux uy uz cell id (SIZE_MAX: absent)
+    size_t bytes;
+};
+
+struct StateHeader {
+    char magic[8];
+    int32_t dim, nx, ny, nz, precision, track_ids, has_ions, laser_on;
+    int64_t n[2];
+    double t;
+    int64_t step;
+    pic_laser_params laser;
+    int32_t cur[2];
+    char pad[512 - 8 - 8 * 4 - 16 - 8 - 8 - sizeof(pic_laser_params) - 8];
+};
+static_assert(sizeof(StateHeader) == 512, "state header must be 512 bytes");
+
+}  // namespace
+
+struct pic_ctx {
+    pic_grid_params p{};
+    Geom g{};
+    cudaStream_t stream = nullptr;
+    double gam = 1, beta = 0, hx = 1, hy = 1, hz = 1, dt = 0, Lx = 0, Ly = 0, Lz = 0, vol = 1;
+    int es = 4;  // element bytes
+    bool ions_species = false;
+
+    size_t field_bytes = 0, species_bytes[2] = {0, 0}, scratch_bytes = 0;
+    int64_t slots = 0;
+    SideLayout side[2]{};
+    size_t off_cnt = 0, off_tmp = 0, off_offsets = 0, off_partials = 0, off_err = 0;
+
+    bool bound = false;
+    unsigned char *fields = nullptr;
+    unsigned char *species[2] = {nullptr, nullptr};
+    unsigned char *scratch = nullptr;
+    int cur[2] = {0, 0};
+
+    bool plasma_loaded = false;
+    pic_plasma_params plasma{};
+    double prof[16] = {0};
+
+    bool laser_on = false;
+    pic_laser_params laser{};
+    int ka = 2;
+
+    double t = 0;
+    int64_t step = 0;
+    std::string err;
+
+    // profiling: event pairs recorded around phases, summed on read
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, size_t>> ev_used;  // (phase bit index, first event of the pair)
+    int64_t kernels = 0;
+
+    ~pic_ctx()
+    {
+        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    }
+};
+
+// ------------------------------------------------------------------ helpers
+
+static pic_status fail(pic_ctx *c, pic_status s, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+#define CUDA_TRY(ctx, call)                                                                      \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail((ctx), PIC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+static int *counts(pic_ctx *c, int sp, int sidx)
+{
+    return reinterpret_cast<int *>(c->scratch + c->off_cnt) + ((size_t)(2 * sp + sidx)) * (size_t)c->g.ntiles;
+}
+
+static void *field_ptr(pic_ctx *c, int comp) { return c->fields + (size_t)comp * c->g.ncomp * c->es; }
+
+template <typename real>
+static Species<real> species_view(pic_ctx *c, int sp, int sidx)
+{
+    Species<real> s{};
+    unsigned char *base = c->species[sp] + (size_t)sidx * c->side[sp].bytes;
+    auto at = [&](int a) -> void * {
+        return c->side[sp].off[a] == SIZE_MAX ? nullptr : (void *)(base + c->side[sp].off[a]);
+    };
+    s.ox = (real *)at(0);
+    s.oy = (real *)at(1);
+    s.oz = (real *)at(2);
+    s.w = (real *)at(3);
+    s.ux = (real *)at(4);
+    s.uy = (real *)at(5);
+    s.uz = (real *)at(6);
+    s.cell = (int32_t *)at(7);
+    s.id = (int64_t *)at(8);
+    return s;
+}
+
+static void side_raw(pic_ctx *c, int sp, int sidx, void *out[9])
+{
+    unsigned char *base = c->species[sp] + (size_t)sidx * c->side[sp].bytes;
+    for (int a = 0; a < 9; ++a) out[a] = c->side[sp].off[a] == SIZE_MAX ? nullptr : (void *)(base + c->side[sp].off[a]);
+}
+
+static cudaMemcpyKind kind_out(int dst_is_device) { return dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+static cudaMemcpyKind kind_in(int src_is_device) { return src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+
+static size_t attr_size(const pic_ctx *c, int a) { return a == 7 ? 4 : (a == 8 ? 8 : (size_t)c->es); }
+
+static pic_status check_device_error(pic_ctx *c)
+{
+    unsigned h = 0;
+    unsigned *d = reinterpret_cast<unsigned *>(c->scratch + c->off_err);
+    CUDA_TRY(c, cudaMemcpyAsync(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (h == 0) return PIC_OK;
+    CUDA_TRY(c, cudaMemsetAsync(d, 0, sizeof(unsigned), c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (h & ERR_NAN) return fail(c, PIC_ERR_NAN, "a non-finite particle momentum or position was produced");
+    if (h & ERR_CFL) return fail(c, PIC_ERR_CFL, "a particle moved one cell or more in one step");
+    if (h & ERR_CAPACITY) return fail(c, PIC_ERR_CAPACITY, "a tile bucket overflowed (raise slots_per_cell)");
+    return fail(c, PIC_ERR_STATE, "a particle was found outside its tile bucket");
+}
+
+// ------------------------------------------------------------------- set-up
+
+extern "C" pic_status pic_init_grid(const pic_grid_params *p, pic_ctx **out)
+{
+    if (!out) return PIC_ERR_ARG;
+    *out = nullptr;
+    if (!p) return PIC_ERR_ARG;
+    if (p->dim != 2 && p->dim != 3) return PIC_ERR_ARG;
+    if (p->nx < 1 || p->nz < 4 || (p->dim == 3 && p->ny < 1) || (p->dim == 2 && p->ny != 1)) return PIC_ERR_ARG;
+    if (!(p->dx > 0) || !(p->dz > 0) || (p->dim == 3 && !(p->dy > 0))) return PIC_ERR_ARG;
+    if (!(p->cfl > 0)) return PIC_ERR_ARG;
+    if (!(p->cfl < 1)) return PIC_ERR_CFL;
+    if (!(p->gamma_boost >= 1) || !std::isfinite(p->gamma_boost)) return PIC_ERR_ARG;
+    if (p->shape_order != 1 && p->shape_order != 2) return PIC_ERR_ARG;
+    if (p->filter_passes < 0 || p->filter_passes > 64) return PIC_ERR_ARG;
+    if (p->bc_z != PIC_BC_MUR && p->bc_z != PIC_BC_PERIODIC) return PIC_ERR_ARG;
+    if (p->precision != PIC_FP32 && p->precision != PIC_FP64) return PIC_ERR_ARG;
+    if (!(p->slots_per_cell > 0) || p->slots_per_cell > 4096) return PIC_ERR_ARG;
+    for (int d = 0; d < 3; ++d)
+        if (p->tile[d] < 0 || (p->tile[d] & (p->tile[d] - 1))) return PIC_ERR_ARG;
+
+    pic_ctx *c = new (std::nothrow) pic_ctx();
+    if (!c) return PIC_ERR_ARG;
+    c->p = *p;
+    c->stream = static_cast<cudaStream_t>(p->stream);
+    c->es = p->precision == PIC_FP64 ? 8 : 4;
+
+    // simulation-frame quantities (FP64): beta, contracted-grid cell sizes, dt
+    c->gam = p->gamma_boost;
+    c->beta = std::sqrt(1.0 - 1.0 / (c->gam * c->gam));
+    c->hx = p->dx;
+    c->hy = p->dim == 3 ? p->dy : 1.0;
+    c->hz = p->dz * (c->gam * (1.0 + c->beta));
+    if (p->dim == 3)
+        c->dt = p->cfl / std::sqrt(1.0 / (c->hx * c->hx) + 1.0 / (c->hy * c->hy) + 1.0 / (c->hz * c->hz));
+    else
+        c->dt = p->cfl / std::sqrt(1.0 / (c->hx * c->hx) + 1.0 / (c->hz * c->hz));
+    c->Lx = p->nx * c->hx;
+    c->Ly = (p->dim == 3 ? p->ny : 1) * c->hy;
+    c->Lz = p->nz * c->hz;
+    c->vol = p->dim == 3 ? c->hx * c->hy * c->hz : c->hx * c->hz;
+    c->ions_species = c->gam > 1.0;
+
+    Geom &g = c->g;
+    g.dim = p->dim;
+    g.nx = p->nx;
+    g.ny = p->dim == 3 ? p->ny : 1;
+    g.nz = p->nz;
+    g.bc_z = p->bc_z == PIC_BC_PERIODIC ? 0 : 1;
+    g.shape = p->shape_order;
+    g.bx = ceil_log2(g.nx) > 0 ? ceil_log2(g.nx) : 1;
+    g.by = p->dim == 3 ? ceil_log2(g.ny) : 0;
+    const int bz = ceil_log2(g.nz);
+    if (g.bx + g.by + bz > 31) {
+        delete c;
+        return PIC_ERR_ARG;
+    }
+    const int def2[3] = {16, 1, 16}, def3[3] = {8, 8, 8};
+    const int ncell[3] = {g.nx, g.ny, g.nz};
+    int64_t cells_per_tile = 1;
+    for (int d = 0; d < 3; ++d) {
+        int t = p->tile[d] ? p->tile[d] : (p->dim == 3 ? def3[d] : def2[d]);
+        if (p->dim == 2 && d == 1) t = 1;
+        const int cap_t = 1 << ceil_log2(ncell[d]);
+        if (t > cap_t) t = cap_t;
+        g.lt[d] = ceil_log2(t);
+        g.nt[d] = (ncell[d] + t - 1) / t;
+        cells_per_tile *= t;
+    }
+    if ((1 << g.lt[0]) > 64 || (1 << g.lt[1]) > 64 || (1 << g.lt[2]) > 64) {
+        delete c;
+        return PIC_ERR_ARG;
+    }
+    g.ntiles = (int64_t)g.nt[0] * g.nt[1] * g.nt[2];
+    int64_t cap = (int64_t)std::ceil(p->slots_per_cell * (double)cells_per_tile);
+    cap = (cap + 31) / 32 * 32;
+    if (cap < 32) cap = 32;
+    if (cap > (1 << 24)) {
+        delete c;
+        return PIC_ERR_ARG;
+    }
+    g.cap = (int)cap;
+    g.plane = (int64_t)g.nx * g.ny;
+    g.ncomp = (int64_t)(g.nz + 1) * g.plane;
+    c->slots = g.ntiles * (int64_t)g.cap;
+
+    // buffer layout
+    c->field_bytes = (size_t)PIC_NCOMP * (size_t)g.ncomp * c->es;
+    for (int sp = 0; sp < 2; ++sp) {
+        SideLayout &L = c->side[sp];
+        size_t o = 0;
+        for (int a = 0; a < 9; ++a) {
+            bool present = true;
+            if (a == 1 && p->dim != 3) present = false;
+            if (sp == 1 && a >= 4 && a <= 6) present = false;
+            if (a == 8 && !p->track_ids) present = false;
+            if (!present) {
+                L.off[a] = SIZE_MAX;
+                continue;
+            }
+            L.off[a] = o;
+            o += align_up((size_t)c->slots * attr_size(c, a));
+        }
+        L.bytes = o;
+        c->species_bytes[sp] = (sp == 1 && !c->ions_species) ? 0 : 2 * o;
+    }
+    size_t o = 0;
+    c->off_cnt = o;
+    o += align_up(sizeof(int) * 4 * (size_t)g.ntiles);
+    c->off_tmp = o;
+    o += align_up((size_t)3 * g.ncomp * c->es);
+    c->off_offsets = o;
+    o += align_up(sizeof(int64_t) * (size_t)g.ntiles);
+    c->off_partials = o;
+    o += align_up(sizeof(double) * 2 * kPartialBlocks);
+    c->off_err = o;
+    o += kAlign;
+    c->scratch_bytes = o;
+    c->plasma.ions = 0;
+    *out = c;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_query_sizes(const pic_ctx *c, pic_sizes *s)
+{
+    if (!c || !s) return PIC_ERR_ARG;
+    std::memset(s, 0, sizeof(*s));
+    s->field_bytes = c->field_bytes;
+    s->species_bytes[0] = c->species_bytes[0];
+    s->species_bytes[1] = c->species_bytes[1];
+    s->scratch_bytes = c->scratch_bytes;
+    s->slots[0] = c->slots;
+    s->slots[1] = c->ions_species ? c->slots : 0;
+    s->ntiles = c->g.ntiles;
+    s->tile_capacity = c->g.cap;
+    for (int d = 0; d < 3; ++d) s->tile[d] = 1 << c->g.lt[d];
+    s->elem_bytes = c->es;
+    s->dt = c->dt;
+    s->hx = c->hx;
+    s->hy = c->hy;
+    s->hz = c->hz;
+    s->beta = c->beta;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_bind_buffers(pic_ctx *c, const pic_buffers *b)
+{
+    if (!c || !b) return PIC_ERR_ARG;
+    if (c->bound) return fail(c, PIC_ERR_STATE, "buffers are already bound");
+    auto aligned = [](const void *q) { return ((uintptr_t)q % kAlign) == 0; };
+    if (!b->fields || !b->species[0] || !b->scratch) return fail(c, PIC_ERR_ARG, "null buffer");
+    if (c->species_bytes[1] && !b->species[1]) return fail(c, PIC_ERR_ARG, "null ion buffer");
+    if (!aligned(b->fields) || !aligned(b->species[0]) || !aligned(b->scratch) ||
+        (c->species_bytes[1] && !aligned(b->species[1])))
+        return fail(c, PIC_ERR_ARG, "buffers must be 256-byte aligned");
+    c->fields = (unsigned char *)b->fields;
+    c->species[0] = (unsigned char *)b->species[0];
+    c->species[1] = (unsigned char *)b->species[1];
+    c->scratch = (unsigned char *)b->scratch;
+    CUDA_TRY(c, cudaMemsetAsync(c->fields, 0, c->field_bytes, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->scratch, 0, c->scratch_bytes, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->bound = true;
+    return PIC_OK;
+}
+
+// --------------------------------------------------------------- plasma
+
+static void fill_inject_common(pic_ctx *c, InjectArgs &a)
+{
+    const pic_plasma_params &p = c->plasma;
+    a.g = c->g;
+    a.hx = c->hx;
+    a.hy = c->hy;
+    a.hz = c->hz;
+    a.Lx = c->Lx;
+    a.Ly = c->Ly;
+    a.Lz = c->Lz;
+    a.gam = c->gam;
+    a.beta = c->beta;
+    a.ppx = p.ppc[0];
+    a.ppy = c->g.dim == 3 ? p.ppc[1] : 1;
+    a.ppz = p.ppc[2];
+    a.NX = (int64_t)c->g.nx * a.ppx;
+    a.NY = c->g.dim == 3 ? (int64_t)c->g.ny * a.ppy : 1;
+    a.z_start = p.z_start;
+    a.z_end = p.z_end;
+    a.ramp = p.ramp_len;
+    a.ne = p.ne_over_nc;
+    a.jitter = p.jitter;
+    a.hz_lab = c->gam * c->hz;
+    a.dzl = a.hz_lab / (double)a.ppz;
+    a.wfac = c->gam * c->vol / (double)(a.ppx * a.ppy * a.ppz);
+    a.uz0 = -(c->gam * c->beta);
+    a.nprof = p.n_profile;
+    for (int m = 0; m < 16; ++m) a.prof[m] = m < p.n_profile ? c->prof[m] : 0.0;
+    a.seed = c->p.seed;
+    a.drift_ions = (p.ions && c->ions_species) ? 1 : 0;
+    a.precision = c->p.precision;
+    side_raw(c, 0, c->cur[0], a.sp_e);
+    a.cnt_e = counts(c, 0, c->cur[0]);
+    if (a.drift_ions) {
+        side_raw(c, 1, c->cur[1], a.sp_i);
+        a.cnt_i = counts(c, 1, c->cur[1]);
+    } else {
+        for (int q = 0; q < 9; ++q) a.sp_i[q] = nullptr;
+        a.cnt_i = nullptr;
+    }
+    a.err = reinterpret_cast<unsigned *>(c->scratch + c->off_err);
+}
+
+// lattice planes whose lab z may fall in [zlo, zhi) after jitter
+static void lattice_band(const InjectArgs &a, double zlo, double zhi, int64_t &m_lo, int64_t &m_hi)
+{
+    const int64_t MZ = (int64_t)std::ceil((a.z_end - a.z_start) / a.dzl);
+    const double jm = a.jitter * a.hz_lab + a.dzl;
+    double lo = std::floor((zlo - a.z_start - jm) / a.dzl - 0.5) - 1.0;
+    double hi = std::ceil((zhi - a.z_start + jm) / a.dzl - 0.5) + 2.0;
+    if (lo < 0) lo = 0;
+    if (hi > (double)MZ) hi = (double)MZ;
+    m_lo = (int64_t)lo;
+    m_hi = (int64_t)hi;
+    if (m_hi < m_lo) m_hi = m_lo;
+}
+
+extern "C" pic_status pic_load_plasma(pic_ctx *c, const pic_plasma_params *p)
+{
+    if (!c || !p) return PIC_ERR_ARG;
+    if (!c->bound) return fail(c, PIC_ERR_STATE, "bind buffers first");
+    const bool dim3 = c->g.dim == 3;
+    if (!(p->ne_over_nc >= 0) || !(p->z_end > p->z_start) || !(p->ramp_len >= 0) || p->ppc[0] < 1 ||
+        p->ppc[2] < 1 || (dim3 && p->ppc[1] < 1) || !(p->jitter >= 0 && p->jitter < 0.5) || p->n_profile < 0 ||
+        p->n_profile > 16 || (p->n_profile > 0 && !p->profile))
+        return fail(c, PIC_ERR_ARG, "invalid plasma parameters");
+    c->plasma = *p;
+    for (int m = 0; m < 16; ++m) c->prof[m] = m < p->n_profile ? p->profile[m] : 0.0;
+    c->plasma.profile = c->prof;
+    c->plasma_loaded = true;
+    InjectArgs a{};
+    fill_inject_common(c, a);
+    a.mode = 0;
+    a.t = c->t;
+    a.t1 = c->t;
+    // every lattice plane whose simulation-frame position lies in [0, Lz)
+    lattice_band(a, c->gam * (c->beta * c->t), c->gam * (c->Lz + c->beta * c->t), a.m_lo, a.m_hi);
+    launch_inject(a, c->stream);
+    CUDA_TRY(c, cudaGetLastError());
+    return check_device_error(c);
+}
+
+// host FP64 position -> cell + offset in the working precision (same rules as
+// the device loader: offsets in [0,1), an offset that rounds to 1 moves on)
+template <typename real>
+static bool host_to_cell(double x, double h, int n, bool periodic, int &cell, real &off)
+{
+    const double xi = x / h;
+    const double f = std::floor(xi);
+    if (!(f >= 0) || f > (double)n) return false;
+    cell = (int)f;
+    double o = xi - f;
+    if (cell >= n) {
+        if (periodic) cell -= n;
+        else { cell = n - 1; o = (double)below_one<real>(); }
+    }
+    off = (real)o;
+    if (off >= real(1)) {
+        if (cell + 1 < n) { cell += 1; off = 0; }
+        else if (periodic) { cell = 0; off = 0; }
+        else off = below_one<real>();
+    }
+    return true;
+}
+
+// bucket slots [0, n) of the inactive (staging) side into the active side
+template <typename real>
+static pic_status bucket_staged(pic_ctx *c, int sp, int64_t n)
+{
+    const int stage = c->cur[sp] ^ 1;
+    BucketArgs<real> b{};
+    b.g = c->g;
+    b.src = species_view<real>(c, sp, stage);
+    b.dst = species_view<real>(c, sp, c->cur[sp]);
+    b.n = n;
+    b.cnt_dst = counts(c, sp, c->cur[sp]);
+    b.err = reinterpret_cast<unsigned *>(c->scratch + c->off_err);
+    launch_bucket<real>(b, c->stream);
+    CUDA_TRY(c, cudaGetLastError());
+    return check_device_error(c);
+}
+
+// copy flat columns (host or device) into the staging side, then bucket them
+template <typename real>
+static pic_status upload_flat(pic_ctx *c, int sp, int64_t n, const void *const cols[9], int src_is_device)
+{
+    void *dst[9];
+    side_raw(c, sp, c->cur[sp] ^ 1, dst);
+    for (int a = 0; a < 9; ++a) {
+        if (!dst[a]) continue;
+        const size_t bytes = (size_t)n * attr_size(c, a);
+        if (bytes == 0) continue;
+        CUDA_TRY(c, cudaMemcpyAsync(dst[a], cols[a], bytes, kind_in(src_is_device), c->stream));
+    }
+    return bucket_staged<real>(c, sp, n);
+}
+
+template <typename real>
+static pic_status load_particles_t(pic_ctx *c, int sp, int64_t n, const double *state, const int64_t *ids)
+{
+    const bool dim3 = c->g.dim == 3;
+    std::vector<std::vector<unsigned char>> cols(9);
+    for (int a = 0; a < 9; ++a)
+        if (c->side[sp].off[a] != SIZE_MAX) cols[a].resize((size_t)n * attr_size(c, a));
+    auto R = [&](int a) { return reinterpret_cast<real *>(cols[a].data()); };
+    for (int64_t i = 0; i < n; ++i) {
+        double x = state[0 * n + i], y = state[1 * n + i], z = state[2 * n + i];
+        int ci = 0, cj = 0, ck = 0;
+        real ox, oy = 0, oz;
+        if (!(x >= 0 && x < c->Lx) || !(z >= 0 && z < c->Lz) || (dim3 && !(y >= 0 && y < c->Ly)))
+            return fail(c, PIC_ERR_ARG, "particle outside the box");
+        if (!host_to_cell<real>(x, c->hx, c->g.nx, true, ci, ox) ||
+            !host_to_cell<real>(z, c->hz, c->g.nz, c->g.bc_z == 0, ck, oz) ||
+            (dim3 && !host_to_cell<real>(y, c->hy, c->g.ny, true, cj, oy)))
+            return fail(c, PIC_ERR_ARG, "particle outside the box");
+        R(0)[i] = ox;
+        if (dim3) R(1)[i] = oy;
+        R(2)[i] = oz;
+        R(3)[i] = (real)state[6 * n + i];
+        if (sp == 0) {
+            R(4)[i] = (real)state[3 * n + i];
+            R(5)[i] = (real)state[4 * n + i];
+            R(6)[i] = (real)state[5 * n + i];
+        }
+        reinterpret_cast<int32_t *>(cols[7].data())[i] = pack_cell(c->g, ci, cj, ck);
+        if (c->p.track_ids) reinterpret_cast<int64_t *>(cols[8].data())[i] = ids ? ids[i] : i;
+    }
+    const void *ptrs[9];
+    for (int a = 0; a < 9; ++a) ptrs[a] = cols[a].empty() ? nullptr : cols[a].data();
+    return upload_flat<real>(c, sp, n, ptrs, 0);
+}
+
+extern "C" pic_status pic_load_particles(pic_ctx *c, int sp, int64_t n, const double *state, const int64_t *ids)
+{
+    if (!c || (sp != 0 && sp != 1) || n < 0 || (n > 0 && !state)) return PIC_ERR_ARG;
+    if (!c->bound) return fail(c, PIC_ERR_STATE, "bind buffers first");
+    if (sp == 1 && !c->ions_species) return fail(c, PIC_ERR_ARG, "drifting ions exist only in a boosted frame");
+    if (n > c->slots) return fail(c, PIC_ERR_CAPACITY, "more particles than slots");
+    if (n == 0) return PIC_OK;
+    return c->es == 4 ? load_particles_t<float>(c, sp, n, state, ids) : load_particles_t<double>(c, sp, n, state, ids);
+}
+
+extern "C" pic_status pic_launch_laser(pic_ctx *c, const pic_laser_params *p)
+{
+    if (!c || !p) return PIC_ERR_ARG;
+    if (!(p->a0 >= 0) || !(p->waist > 0) || !(p->fwhm > 0) || !std::isfinite(p->z_antenna) ||
+        (p->polarization != PIC_POL_X && p->polarization != PIC_POL_Y))
+        return fail(c, PIC_ERR_ARG, "invalid laser parameters");
+    c->laser = *p;
+    int ka = (int)std::floor(p->z_antenna / c->hz + 0.5);
+    if (ka < 2) ka = 2;
+    if (ka > c->g.nz - 2) ka = c->g.nz - 2;
+    c->ka = ka;
+    if (std::isnan(c->laser.x_center)) c->laser.x_center = 0.5 * c->Lx;
+    if (std::isnan(c->laser.y_center)) c->laser.y_center = 0.5 * c->Ly;
+    c->laser_on = true;
+    return PIC_OK;
+}
+
+// ---------------------------------------------------------------------- step
+
+template <typename real>
+static PushArgs<real> push_args(pic_ctx *c, int sp)
+{
+    PushArgs<real> a{};
+    a.g = c->g;
+    real *F[9];
+    for (int q = 0; q < 9; ++q) F[q] = (real *)field_ptr(c, q);
+    for (int q = 0; q < 3; ++q) {
+        a.E[q] = F[q];
+        a.B[q] = F[3 + q];
+        a.J[q] = F[6 + q];
+    }
+    a.in = species_view<real>(c, sp, c->cur[sp]);
+    a.out = species_view<real>(c, sp, c->cur[sp] ^ 1);
+    a.cnt_in = counts(c, sp, c->cur[sp]);
+    a.cnt_out = counts(c, sp, c->cur[sp] ^ 1);
+    a.dtdh[0] = (real)(c->dt / c->hx);
+    a.dtdh[1] = (real)(c->dt / c->hy);
+    a.dtdh[2] = (real)(c->dt / c->hz);
+    const double q = sp == 0 ? -1.0 : 1.0;
+    a.eps = (real)(kPi * -1.0 * c->dt);
+    a.jfac[0] = (real)(-q * c->hx / (c->dt * c->vol));
+    a.jfac[1] = (real)(-q * c->hy / (c->dt * c->vol));
+    a.jfac[2] = (real)(-q * c->hz / (c->dt * c->vol));
+    a.jyfac = (real)(q / c->vol);
+    a.ion_u[0] = 0;
+    a.ion_u[1] = 0;
+    a.ion_u[2] = (real)(-(c->gam * c->beta));
+    a.err = reinterpret_cast<unsigned *>(c->scratch + c->off_err);
+    return a;
+}
+
+// records an event pair around one phase when profiling is on
+struct PhaseTimer {
+    pic_ctx *c;
+    int bit;
+    size_t first = SIZE_MAX;
+    PhaseTimer(pic_ctx *ctx, int b) : c(ctx), bit(b)
+    {
+        if (!c->profiling) return;
+        first = c->ev_used.empty() ? 0 : c->ev_used.back().second + 2;
+        while (c->ev_pool.size() < first + 2) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                first = SIZE_MAX;
+                return;
+            }
+            c->ev_pool.push_back(e);
+        }
+        cudaEventRecord(c->ev_pool[first], c->stream);
+    }
+    ~PhaseTimer()
+    {
+        if (first == SIZE_MAX) return;
+        cudaEventRecord(c->ev_pool[first + 1], c->stream);
+        c->ev_used.push_back({bit, first});
+    }
+};
+
+template <typename real>
+static void run_phases_t(pic_ctx *c, unsigned mask)
+{
+    real *F[9];
+    for (int q = 0; q < 9; ++q) F[q] = (real *)field_ptr(c, q);
+    if (mask & PIC_PH_ZERO_J) {
+        PhaseTimer pt(c, 0);
+        cudaMemsetAsync(F[6], 0, (size_t)3 * c->g.ncomp * sizeof(real), c->stream);
+    }
+    if (mask & PIC_PH_PUSH) {
+        PhaseTimer pt(c, 1);
+        launch_push<real>(push_args<real>(c, 0), c->stream);
+        c->cur[0] ^= 1;
+        c->kernels += 1;
+    }
+    if ((mask & PIC_PH_IONS) && c->ions_species) {
+        PhaseTimer pt(c, 2);
+        launch_ions<real>(push_args<real>(c, 1), c->stream);
+        c->cur[1] ^= 1;
+        c->kernels += 1;
+    }
+    if ((mask & PIC_PH_ANTENNA) && c->laser_on) {
+        PhaseTimer pt(c, 3);
+        // the lab laser seen by an antenna at rest in the boosted frame:
+        // amplitude and time argument scaled by D = gamma (1 - beta)
+        const pic_laser_params &l = c->laser;
+        const double D = 1.0 / (c->gam * (1.0 + c->beta));
+        const double tau = l.fwhm / std::sqrt(2.0 * std::log(2.0));
+        const double spk = l.t_peak >= 0.0 ? l.t_peak : 3.0 * tau;
+        const double th = c->t + 0.5 * c->dt;
+        const double sr = D * th - spk;
+        const double env = std::exp(-(sr / tau) * (sr / tau));
+        const double amp = l.a0 * D * env * std::sin(kTwoPi * sr);
+        const double j0 = -amp / (kPi * c->hz);
+        const int comp = l.polarization == PIC_POL_X ? 0 : 1;
+        launch_antenna<real>(c->g, F[6 + comp], l.polarization, c->ka, j0, c->hx, c->hy, l.x_center, l.y_center,
+                             l.waist, c->stream);
+        c->kernels += 1;
+    }
+    if ((mask & PIC_PH_FILTER) && c->p.filter_passes > 0) {
+        PhaseTimer pt(c, 4);
+        real *J[3] = {F[6], F[7], F[8]};
+        launch_filter<real>(c->g, J, (real *)(c->scratch + c->off_tmp), c->p.filter_passes, c->stream);
+        c->kernels += (int64_t)(c->g.dim == 3 ? 3 : 2) * c->p.filter_passes;
+    }
+    if (mask & PIC_PH_YEE) {
+        PhaseTimer pt(c, 5);
+        launch_yee<real>(c->g, F, c->dt, c->hx, c->hy, c->hz, c->stream);
+        c->kernels += 3;
+    }
+    if ((mask & PIC_PH_INJECT) && c->plasma_loaded && c->gam > 1.0) {
+        PhaseTimer pt(c, 6);
+        InjectArgs a{};
+        fill_inject_common(c, a);
+        a.mode = 1;
+        a.t = c->t;
+        a.t1 = c->t + c->dt;
+        lattice_band(a, c->gam * (c->Lz + c->beta * a.t), c->gam * (c->Lz + c->beta * a.t1), a.m_lo, a.m_hi);
+        launch_inject(a, c->stream);
+        if (a.m_hi > a.m_lo) c->kernels += 1;
+    }
+    if (mask & PIC_PH_TIME) {
+        c->t += c->dt;
+        c->step += 1;
+    }
+}
+
+static pic_status run_steps(pic_ctx *c, int nsteps, unsigned mask, bool check)
+{
+    if (!c) return PIC_ERR_ARG;
+    if (!c->bound) return fail(c, PIC_ERR_STATE, "bind buffers first");
+    if (nsteps < 0) return fail(c, PIC_ERR_ARG, "negative step count");
+    for (int n = 0; n < nsteps; ++n) {
+        if (c->es == 4) run_phases_t<float>(c, mask);
+        else run_phases_t<double>(c, mask);
+    }
+    CUDA_TRY(c, cudaGetLastError());
+    if (!check) return PIC_OK;
+    return check_device_error(c);
+}
+
+extern "C" pic_status pic_step(pic_ctx *c, int nsteps) { return run_steps(c, nsteps, PIC_PH_ALL, true); }
+extern "C" pic_status pic_step_async(pic_ctx *c, int nsteps) { return run_steps(c, nsteps, PIC_PH_ALL, false); }
+extern "C" pic_status pic_step_phases(pic_ctx *c, unsigned mask)
+{
+    if (mask & ~PIC_PH_ALL) return fail(c, PIC_ERR_ARG, "unknown phase bits");
+    return run_steps(c, 1, mask, true);
+}
+
+// -------------------------------------------------------------------- output
+
+
+static int popcount9(unsigned m)
+{
+    int n = 0;
+    for (int q = 0; q < PIC_NCOMP; ++q) n += (m >> q) & 1u;
+    return n;
+}
+
+extern "C" pic_status pic_get_fields(pic_ctx *c, unsigned mask, void *dst, size_t dst_bytes, int dst_is_device)
+{
+    if (!c || !dst || (mask & ~0x1FFu) || mask == 0) return PIC_ERR_ARG;
+    if (!c->bound) return fail(c, PIC_ERR_STATE, "bind buffers first");
+    const size_t per = (size_t)c->g.ncomp * c->es;
+    if (dst_bytes < per * popcount9(mask)) return fail(c, PIC_ERR_ARG, "destination too small");
+    size_t o = 0;
+    for (int q = 0; q < PIC_NCOMP; ++q) {
+        if (!(mask >> q & 1u)) continue;
+        CUDA_TRY(c, cudaMemcpyAsync((unsigned char *)dst + o, field_ptr(c, q), per, kind_out(dst_is_device), c->stream));
+        o += per;
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_set_fields(pic_ctx *c, unsigned mask, const void *src, size_t src_bytes, int src_is_device)
+{
+    if (!c || !src || (mask & ~0x1FFu) || mask == 0) return PIC_ERR_ARG;
+    if (!c->bound) return fail(c, PIC_ERR_STATE, "bind buffers first");
+    const size_t per = (size_t)c->g.ncomp * c->es;
+    if (src_bytes < per * popcount9(mask)) return fail(c, PIC_ERR_ARG, "source too small");
+    size_t o = 0;
+    for (int q = 0; q < PIC_NCOMP; ++q) {
+        if (!(mask >> q & 1u)) continue;
+        CUDA_TRY(c, cudaMemcpyAsync(field_ptr(c, q), (const unsigned char *)src + o, per, kind_in(src_is_device), c->stream));
+        o += per;
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_get_axis(pic_ctx *c, int comp, void *dst, size_t dst_bytes, int dst_is_device)
+{
+    if (!c || !dst || comp < 0 || comp >= PIC_NCOMP) return PIC_ERR_ARG;
+    if (!c->bound) return fail(c, PIC_ERR_STATE, "bind buffers first");
+    const size_t n = (size_t)c->g.nz + 1;
+    if (dst_bytes < n * c->es) return fail(c, PIC_ERR_ARG, "destination too small");
+    const size_t off = ((size_t)(c->g.ny / 2) * c->g.nx + c->g.nx / 2) * c->es;
+    CUDA_TRY(c, cudaMemcpy2DAsync(dst, c->es, (unsigned char *)field_ptr(c, comp) + off, (size_t)c->g.plane * c->es,
+                                  c->es, n, kind_out(dst_is_device), c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+// live count per tile (clamped to the capacity) and exclusive offsets
+static pic_status tile_offsets(pic_ctx *c, int sp, std::vector<int64_t> &off, int64_t &total)
+{
+    std::vector<int> cnt((size_t)c->g.ntiles);
+    CUDA_TRY(c, cudaMemcpyAsync(cnt.data(), counts(c, sp, c->cur[sp]), sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    off.resize(cnt.size());
+    total = 0;
+    for (size_t t = 0; t < cnt.size(); ++t) {
+        off[t] = total;
+        total += cnt[t] < c->g.cap ? cnt[t] : c->g.cap;
+    }
+    return PIC_OK;
+}
+
+// compact the live particles of a species into slots [0, n) of its inactive side
+template <typename real>
+static pic_status compact_t(pic_ctx *c, int sp, int64_t &n)
+{
+    std::vector<int64_t> off;
+    pic_status s = tile_offsets(c, sp, off, n);
+    if (s != PIC_OK) return s;
+    int64_t *d_off = reinterpret_cast<int64_t *>(c->scratch + c->off_offsets);
+    CUDA_TRY(c, cudaMemcpyAsync(d_off, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice, c->stream));
+    CompactArgs<real> a{};
+    a.g = c->g;
+    a.src = species_view<real>(c, sp, c->cur[sp]);
+    a.dst = species_view<real>(c, sp, c->cur[sp] ^ 1);
+    a.cnt = counts(c, sp, c->cur[sp]);
+    a.offset = d_off;
+    launch_compact<real>(a, c->stream);
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+template <typename real>
+static pic_status get_particles_t(pic_ctx *c, int sp, double *dst, size_t dst_bytes, int64_t *n_out, int64_t *ids)
+{
+    int64_t n = 0;
+    pic_status s = compact_t<real>(c, sp, n);
+    if (s != PIC_OK) return s;
+    if (n_out) *n_out = n;
+    if (!dst) return PIC_OK;
+    if (dst_bytes < (size_t)n * 7 * sizeof(double)) return fail(c, PIC_ERR_ARG, "destination too small");
+    void *col[9];
+    side_raw(c, sp, c->cur[sp] ^ 1, col);
+    std::vector<std::vector<unsigned char>> h(9);
+    for (int a = 0; a < 9; ++a) {
+        if (!col[a]) continue;
+        h[a].resize((size_t)n * attr_size(c, a));
+        if (n) CUDA_TRY(c, cudaMemcpyAsync(h[a].data(), col[a], h[a].size(), cudaMemcpyDeviceToHost, c->stream));
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    auto R = [&](int a) { return reinterpret_cast<const real *>(h[a].data()); };
+    const int32_t *cell = reinterpret_cast<const int32_t *>(h[7].data());
+    for (int64_t p = 0; p < n; ++p) {
+        int i, j, k;
+        unpack_cell(c->g, cell[p], i, j, k);
+        dst[0 * n + p] = ((double)i + (double)R(0)[p]) * c->hx;
+        dst[1 * n + p] = c->g.dim == 3 ? ((double)j + (double)R(1)[p]) * c->hy : 0.0;
+        dst[2 * n + p] = ((double)k + (double)R(2)[p]) * c->hz;
+        if (sp == 0) {
+            dst[3 * n + p] = (double)R(4)[p];
+            dst[4 * n + p] = (double)R(5)[p];
+            dst[5 * n + p] = (double)R(6)[p];
+        } else {
+            dst[3 * n + p] = 0.0;
+            dst[4 * n + p] = 0.0;
+            dst[5 * n + p] = (double)(real)(-(c->gam * c->beta));
+        }
+        dst[6 * n + p] = (double)R(3)[p];
+        if (ids) ids[p] = c->p.track_ids ? reinterpret_cast<const int64_t *>(h[8].data())[p] : -1;
+    }
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_get_particles(pic_ctx *c, int sp, double *dst, size_t dst_bytes, int64_t *n_out, int64_t *ids)
+{
+    if (!c || (sp != 0 && sp != 1)) return PIC_ERR_ARG;
+    if (!c->bound) return fail(c, PIC_ERR_STATE, "bind buffers first");
+    if (sp == 1 && !c->ions_species) {
+        if (n_out) *n_out = 0;
+        return PIC_OK;
+    }
+    return c->es == 4 ? get_particles_t<float>(c, sp, dst, dst_bytes, n_out, ids)
+                      : get_particles_t<double>(c, sp, dst, dst_bytes, n_out, ids);
+}
+
+template <typename real>
+static pic_status get_rho_t(pic_ctx *c, void *dst, size_t dst_bytes, int dst_is_device)
+{
+    const size_t bytes = (size_t)c->g.ncomp * sizeof(real);
+    if (dst_bytes < bytes) return fail(c, PIC_ERR_ARG, "destination too small");
+    real *rho = (real *)(c->scratch + c->off_tmp);
+    CUDA_TRY(c, cudaMemsetAsync(rho, 0, bytes, c->stream));
+    launch_rho<real>(c->g, species_view<real>(c, 0, c->cur[0]), counts(c, 0, c->cur[0]), (real)(-1.0 / c->vol), rho,
+                     c->stream);
+    if (c->ions_species)
+        launch_rho<real>(c->g, species_view<real>(c, 1, c->cur[1]), counts(c, 1, c->cur[1]), (real)(1.0 / c->vol), rho,
+                         c->stream);
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaMemcpyAsync(dst, rho, bytes, kind_out(dst_is_device), c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_get_rho(pic_ctx *c, void *dst, size_t dst_bytes, int dst_is_device)
+{
+    if (!c || !dst) return PIC_ERR_ARG;
+    if (!c->bound) return fail(c, PIC_ERR_STATE, "bind buffers first");
+    return c->es == 4 ? get_rho_t<float>(c, dst, dst_bytes, dst_is_device) : get_rho_t<double>(c, dst, dst_bytes, dst_is_device);
+}
+
+static double kahan_sum(const double *v, size_t n, size_t stride)
+{
+    double s = 0, comp = 0;
+    for (size_t i = 0; i < n; ++i) {
+        const double y = v[i * stride] - comp;
+        const double t = s + y;
+        comp = (t - s) - y;
+        s = t;
+    }
+    return s;
+}
+
+template <typename real>
+static pic_status diagnostics_t(pic_ctx *c, pic_diag *out)
+{
+    double *part = reinterpret_cast<double *>(c->scratch + c->off_partials);
+    std::vector<double> h(2 * kPartialBlocks);
+    real *F[9];
+    for (int q = 0; q < 9; ++q) F[q] = (real *)field_ptr(c, q);
+    launch_field_sums<real>(c->g, F, part, kPartialBlocks, c->stream);
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaMemcpyAsync(h.data(), part, sizeof(double) * kPartialBlocks, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    out->field_energy = 0.5 * c->vol * kahan_sum(h.data(), kPartialBlocks, 1);
+    out->kinetic_energy = 0;
+    out->charge = 0;
+    const real ion_u[3] = {0, 0, (real)(-(c->gam * c->beta))};
+    for (int sp = 0; sp < (c->ions_species ? 2 : 1); ++sp) {
+        launch_particle_sums<real>(c->g, species_view<real>(c, sp, c->cur[sp]), counts(c, sp, c->cur[sp]),
+                                   sp == 0 ? -1.0 : 1.0, ion_u, part, kPartialBlocks, c->stream);
+        CUDA_TRY(c, cudaGetLastError());
+        CUDA_TRY(c, cudaMemcpyAsync(h.data(), part, sizeof(double) * 2 * kPartialBlocks, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        if (sp == 0) out->kinetic_energy = kahan_sum(h.data(), kPartialBlocks, 2);
+        out->charge += kahan_sum(h.data() + 1, kPartialBlocks, 2);
+    }
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_get_diagnostics(pic_ctx *c, pic_diag *out)
+{
+    if (!c || !out) return PIC_ERR_ARG;
+    if (!c->bound) return fail(c, PIC_ERR_STATE, "bind buffers first");
+    std::memset(out, 0, sizeof(*out));
+    out->t = c->t;
+    out->step = c->step;
+    for (int sp = 0; sp < 2; ++sp) {
+        if (sp == 1 && !c->ions_species) break;
+        std::vector<int64_t> off;
+        int64_t n = 0;
+        pic_status s = tile_offsets(c, sp, off, n);
+        if (s != PIC_OK) return s;
+        out->n_particles[sp] = n;
+    }
+    return c->es == 4 ? diagnostics_t<float>(c, out) : diagnostics_t<double>(c, out);
+}
+
+// ---------------------------------------------------------------- checkpoint
+
+static size_t species_state_bytes(const pic_ctx *c, int sp, int64_t n)
+{
+    size_t b = 0;
+    for (int a = 0; a < 9; ++a)
+        if (c->side[sp].off[a] != SIZE_MAX) b += (size_t)n * attr_size(c, a);
+    return b;
+}
+
+extern "C" pic_status pic_state_bytes(pic_ctx *c, size_t *bytes)
+{
+    if (!c || !bytes) return PIC_ERR_ARG;
+    if (!c->bound) return fail(c, PIC_ERR_STATE, "bind buffers first");
+    size_t b = sizeof(StateHeader) + c->field_bytes;
+    for (int sp = 0; sp < (c->ions_species ? 2 : 1); ++sp) {
+        std::vector<int64_t> off;
+        int64_t n = 0;
+        pic_status s = tile_offsets(c, sp, off, n);
+        if (s != PIC_OK) return s;
+        b += species_state_bytes(c, sp, n);
+    }
+    *bytes = b;
+    return PIC_OK;
+}
+
+template <typename real>
+static pic_status get_state_t(pic_ctx *c, unsigned char *dst, size_t dst_bytes, int dst_is_device)
+{
+    StateHeader h{};
+    std::memcpy(h.magic, "PICSTAT1", 8);
+    h.dim = c->g.dim;
+    h.nx = c->g.nx;
+    h.ny = c->g.ny;
+    h.nz = c->g.nz;
+    h.precision = c->p.precision;
+    h.track_ids = c->p.track_ids;
+    h.has_ions = c->ions_species;
+    h.laser_on = c->laser_on;
+    h.t = c->t;
+    h.step = c->step;
+    h.laser = c->laser;
+    int64_t n[2] = {0, 0};
+    for (int sp = 0; sp < (c->ions_species ? 2 : 1); ++sp) {
+        pic_status s = compact_t<real>(c, sp, n[sp]);
+        if (s != PIC_OK) return s;
+    }
+    h.n[0] = n[0];
+    h.n[1] = n[1];
+    size_t need = sizeof(StateHeader) + c->field_bytes + species_state_bytes(c, 0, n[0]) +
+                  (c->ions_species ? species_state_bytes(c, 1, n[1]) : 0);
+    if (dst_bytes < need) return fail(c, PIC_ERR_ARG, "destination too small");
+    CUDA_TRY(c, cudaMemcpyAsync(dst, &h, sizeof(h), dst_is_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, c->stream));
+    size_t o = sizeof(StateHeader);
+    CUDA_TRY(c, cudaMemcpyAsync(dst + o, c->fields, c->field_bytes, kind_out(dst_is_device), c->stream));
+    o += c->field_bytes;
+    for (int sp = 0; sp < (c->ions_species ? 2 : 1); ++sp) {
+        void *col[9];
+        side_raw(c, sp, c->cur[sp] ^ 1, col);
+        for (int a = 0; a < 9; ++a) {
+            if (!col[a]) continue;
+            const size_t b = (size_t)n[sp] * attr_size(c, a);
+            if (b) CUDA_TRY(c, cudaMemcpyAsync(dst + o, col[a], b, kind_out(dst_is_device), c->stream));
+            o += b;
+        }
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_get_state(pic_ctx *c, void *dst, size_t dst_bytes, int dst_is_device)
+{
+    if (!c || !dst) return PIC_ERR_ARG;
+    if (!c->bound) return fail(c, PIC_ERR_STATE, "bind buffers first");
+    return c->es == 4 ? get_state_t<float>(c, (unsigned char *)dst, dst_bytes, dst_is_device)
+                      : get_state_t<double>(c, (unsigned char *)dst, dst_bytes, dst_is_device);
+}
+
+template <typename real>
+static pic_status set_state_t(pic_ctx *c, const unsigned char *src, size_t src_bytes, int src_is_device)
+{
+    StateHeader h{};
+    if (src_bytes < sizeof(h)) return fail(c, PIC_ERR_ARG, "snapshot too small");
+    CUDA_TRY(c, cudaMemcpyAsync(&h, src, sizeof(h), src_is_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (std::memcmp(h.magic, "PICSTAT1", 8) != 0 || h.dim != c->g.dim || h.nx != c->g.nx || h.ny != c->g.ny ||
+        h.nz != c->g.nz || h.precision != c->p.precision || h.track_ids != c->p.track_ids ||
+        h.has_ions != (int)c->ions_species || h.n[0] < 0 || h.n[1] < 0 || h.n[0] > c->slots || h.n[1] > c->slots)
+        return fail(c, PIC_ERR_ARG, "snapshot does not match this grid");
+    const size_t need = sizeof(StateHeader) + c->field_bytes + species_state_bytes(c, 0, h.n[0]) +
+                        (c->ions_species ? species_state_bytes(c, 1, h.n[1]) : 0);
+    if (src_bytes < need) return fail(c, PIC_ERR_ARG, "snapshot truncated");
+    size_t o = sizeof(StateHeader);
+    CUDA_TRY(c, cudaMemcpyAsync(c->fields, src + o, c->field_bytes, kind_in(src_is_device), c->stream));
+    o += c->field_bytes;
+    for (int sp = 0; sp < (c->ions_species ? 2 : 1); ++sp) {
+        CUDA_TRY(c, cudaMemsetAsync(counts(c, sp, 0), 0, sizeof(int) * 2 * (size_t)c->g.ntiles, c->stream));
+        const void *cols[9] = {nullptr};
+        for (int a = 0; a < 9; ++a) {
+            if (c->side[sp].off[a] == SIZE_MAX) continue;
+            cols[a] = src + o;
+            o += (size_t)h.n[sp] * attr_size(c, a);
+        }
+        if (h.n[sp] == 0) continue;
+        pic_status s = upload_flat<real>(c, sp, h.n[sp], cols, src_is_device);
+        if (s != PIC_OK) return s;
+    }
+    c->t = h.t;
+    c->step = h.step;
+    c->laser_on = h.laser_on != 0;
+    c->laser = h.laser;
+    if (c->laser_on) {
+        int ka = (int)std::floor(c->laser.z_antenna / c->hz + 0.5);
+        c->ka = ka < 2 ? 2 : (ka > c->g.nz - 2 ? c->g.nz - 2 : ka);
+    }
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_set_state(pic_ctx *c, const void *src, size_t src_bytes, int src_is_device)
+{
+    if (!c || !src) return PIC_ERR_ARG;
+    if (!c->bound) return fail(c, PIC_ERR_STATE, "bind buffers first");
+    return c->es == 4 ? set_state_t<float>(c, (const unsigned char *)src, src_bytes, src_is_device)
+                      : set_state_t<double>(c, (const unsigned char *)src, src_bytes, src_is_device);
+}
+
+// ----------------------------------------------------------------- profiling
+
+extern "C" pic_status pic_profile(pic_ctx *c, int enable)
+{
+    if (!c) return PIC_ERR_ARG;
+    c->profiling = enable != 0;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_profile_read(pic_ctx *c, double ms[8], int64_t calls[8], int64_t *kernels)
+{
+    if (!c) return PIC_ERR_ARG;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    double acc[8] = {0};
+    int64_t cnt[8] = {0};
+    for (const auto &u : c->ev_used) {
+        float e = 0;
+        CUDA_TRY(c, cudaEventElapsedTime(&e, c->ev_pool[u.second], c->ev_pool[u.second + 1]));
+        acc[u.first] += e;
+        cnt[u.first] += 1;
+    }
+    c->ev_used.clear();
+    for (int q = 0; q < 8; ++q) {
+        if (ms) ms[q] = acc[q];
+        if (calls) calls[q] = cnt[q];
+    }
+    if (kernels) *kernels = c->kernels;
+    c->kernels = 0;
+    return PIC_OK;
+}
+
+// ---------------------------------------------------------------------- misc
+
+extern "C" const char *pic_last_error(const pic_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+extern "C" const char *pic_status_string(pic_status s)
+{
+    switch (s) {
+    case PIC_OK: return "ok";
+    case PIC_ERR_ARG: return "invalid argument";
+    case PIC_ERR_STATE: return "call out of order";
+    case PIC_ERR_CUDA: return "CUDA error";
+    case PIC_ERR_CAPACITY: return "tile bucket overflow";
+    case PIC_ERR_CFL: return "Courant condition violated";
+    case PIC_ERR_NAN: return "non-finite value";
+    case PIC_ERR_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+extern "C" void pic_destroy(pic_ctx *c) { delete c; }

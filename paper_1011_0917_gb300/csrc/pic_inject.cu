@@ -1,0 +1,164 @@
+// pic_inject.cu -- plasma loading and boosted-frame injection (FP64).
+//
+// A plasma at rest in the lab sits on a lattice of ppc points per cell and
+// axis with a seeded uniform jitter; in a frame boosted by gamma it is seen at
+// z' = z_lab / gamma - beta t' (the Lorentz transform, the paper's "hyperbolic
+// rotation"), with density gamma n and drift u_z = -gamma beta.  One thread
+// handles one lattice point: it recomputes the point's lab position from its
+// index (SplitMix64 jitter, counter 3 * id + axis), and either places it if it
+// lies in the box at time t (load) or appends it if it crosses z = Lz during
+// (t, t1] (injection), at its position at t1.  No list of pending plasma is
+// kept.
+//
+// This file is compiled without floating-point contraction so that every
+// double operation rounds once, in the order written: the decision "in the
+// box" / "crosses now" is then the same as in any other IEEE implementation
+// of the same expressions.
+#include "pic_internal.cuh"
+
+namespace pic {
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t counter)
+{
+    uint64_t z = seed + (counter + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double uniform01(uint64_t seed, uint64_t counter)
+{
+    return (double)(splitmix64(seed, counter) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// lab-frame density: linear up-ramp, then the cosine-series profile
+__device__ double lab_density(const InjectArgs &a, double z)
+{
+    if (z < a.z_start || z >= a.z_end) return 0.0;
+    double r = 1.0;
+    if (a.ramp > 0.0 && z < a.z_start + a.ramp) r = (z - a.z_start) / a.ramp;
+    double f = 1.0;
+    if (a.nprof > 0) {
+        const double zeta = (z - a.z_start) / (a.z_end - a.z_start);
+        for (int m = 1; m <= a.nprof; ++m) f += a.prof[m - 1] * cos((double)m * 3.141592653589793 * zeta);
+    }
+    return a.ne * r * f;
+}
+
+// position (one axis) -> cell and offset in [0,1) of the working precision
+template <typename real>
+__device__ __forceinline__ void to_cell(double x, double h, int n, bool periodic, int &c, real &off)
+{
+    const double xi = x / h;
+    double f = floor(xi);
+    c = (int)f;
+    double o = xi - f;
+    if (c >= n) {  // x just below the box end rounded up
+        if (periodic) { c -= n; } else { c = n - 1; o = (double)below_one<real>(); }
+    }
+    off = (real)o;
+    if (off >= real(1)) {
+        if (c + 1 < n) { c += 1; off = 0; }
+        else if (periodic) { c = 0; off = 0; }
+        else off = below_one<real>();
+    }
+}
+
+template <typename real>
+__device__ __forceinline__ void store(void *const sp[9], int64_t d, real ox, real oy, real oz, real w, real uz,
+                                      int32_t cell, int64_t id, bool electron, bool dim3)
+{
+    static_cast<real *>(sp[0])[d] = ox;
+    if (dim3) static_cast<real *>(sp[1])[d] = oy;
+    static_cast<real *>(sp[2])[d] = oz;
+    static_cast<real *>(sp[3])[d] = w;
+    if (electron) {
+        static_cast<real *>(sp[4])[d] = real(0);
+        static_cast<real *>(sp[5])[d] = real(0);
+        static_cast<real *>(sp[6])[d] = uz;
+    }
+    static_cast<int32_t *>(sp[7])[d] = cell;
+    if (sp[8]) static_cast<int64_t *>(sp[8])[d] = id;
+}
+
+template <typename real>
+__global__ void inject_kernel(InjectArgs a)
+{
+    const bool dim3 = a.g.dim == 3;
+    const int64_t total = (a.m_hi - a.m_lo) * a.NY * a.NX;
+    const int64_t nround = (total + 31) / 32 * 32;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nround; q += stride) {
+        int64_t dest = -1;
+        int ci = 0, cj = 0, ck = 0;
+        real ox = 0, oy = 0, oz = 0, wr = 0;
+        int64_t L = 0;
+        if (q < total) {
+            const int64_t ix = q % a.NX;
+            const int64_t r = q / a.NX;
+            const int64_t iy = r % a.NY;
+            const int64_t m = a.m_lo + r / a.NY;
+            L = (m * a.NY + iy) * a.NX + ix;
+            const uint64_t c0 = 3ull * (uint64_t)L;
+            double x = ((double)ix + 0.5) * (a.hx / (double)a.ppx) +
+                       (a.jitter * a.hx) * (2.0 * uniform01(a.seed, c0) - 1.0);
+            if (x < 0.0) x += a.Lx;
+            if (x >= a.Lx) x -= a.Lx;
+            double y = 0.0;
+            if (dim3) {
+                y = ((double)iy + 0.5) * (a.hy / (double)a.ppy) +
+                    (a.jitter * a.hy) * (2.0 * uniform01(a.seed, c0 + 1ull) - 1.0);
+                if (y < 0.0) y += a.Ly;
+                if (y >= a.Ly) y -= a.Ly;
+            }
+            const double zlab = a.z_start + ((double)m + 0.5) * a.dzl +
+                                (a.jitter * a.hz_lab) * (2.0 * uniform01(a.seed, c0 + 2ull) - 1.0);
+            const double n = lab_density(a, zlab);
+            if (n > 0.0) {
+                bool take;
+                double zb;
+                if (a.mode == 0) {
+                    zb = zlab / a.gam - a.beta * a.t;
+                    take = zb >= 0.0 && zb < a.Lz;
+                } else {
+                    const double zb0 = zlab / a.gam - a.beta * a.t;
+                    zb = zlab / a.gam - a.beta * a.t1;
+                    take = zb0 >= a.Lz && zb < a.Lz;
+                }
+                if (take) {
+                    to_cell<real>(x, a.hx, a.g.nx, true, ci, ox);
+                    if (dim3) to_cell<real>(y, a.hy, a.g.ny, true, cj, oy);
+                    to_cell<real>(zb, a.hz, a.g.nz, a.g.bc_z == 0, ck, oz);
+                    wr = (real)(n * a.wfac);
+                    dest = tile_of(a.g, ci, cj, ck);
+                }
+            }
+        }
+        const int re = reserve_slot(a.cnt_e, dest);
+        int ri = 0;
+        if (a.drift_ions) ri = reserve_slot(a.cnt_i, dest);
+        if (dest < 0) continue;
+        // every reserved slot below the capacity is written, so a bucket never
+        // holds a stale entry; an overflow drops the particle and is reported
+        const int32_t cell = pack_cell(a.g, ci, cj, ck);
+        const real uz = (real)a.uz0;
+        if (re < a.g.cap) store<real>(a.sp_e, dest * (int64_t)a.g.cap + re, ox, oy, oz, wr, uz, cell, L, true, dim3);
+        else atomicOr(a.err, ERR_CAPACITY);
+        if (a.drift_ions) {
+            if (ri < a.g.cap) store<real>(a.sp_i, dest * (int64_t)a.g.cap + ri, ox, oy, oz, wr, uz, cell, L, false, dim3);
+            else atomicOr(a.err, ERR_CAPACITY);
+        }
+    }
+}
+
+void launch_inject(const InjectArgs &a, cudaStream_t s)
+{
+    const int64_t total = (a.m_hi - a.m_lo) * a.NY * a.NX;
+    if (total <= 0) return;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 152LL * 64) blocks = 152LL * 64;
+    if (a.precision == 0) inject_kernel<float><<<(unsigned)blocks, 256, 0, s>>>(a);
+    else inject_kernel<double><<<(unsigned)blocks, 256, 0, s>>>(a);
+}
+
+}  // namespace pic

@@ -1,0 +1,241 @@
+// pic_internal.cuh -- device-side data layout and helpers of the PIC library.
+//
+// Layout in HBM (all caller-owned):
+//   fields:  9 components (Ex Ey Ez Bx By Bz Jx Jy Jz), each (nz+1) x ny x nx
+//            elements in [k][j][i] order.  Yee staggering of component c at
+//            array index (i, j, k): Ex (i+1/2, j, k), Ey (i, j+1/2, k),
+//            Ez (i, j, k+1/2), Bx (i, j+1/2, k+1/2), By (i+1/2, j, k+1/2),
+//            Bz (i+1/2, j+1/2, k); J like E.
+//   species: per species two "sides" (double buffer).  A side is a structure
+//            of arrays with `slots` entries per attribute; tile t owns slots
+//            [t*cap, t*cap + count[t]).  A particle is an int32 packed cell
+//            index plus its offsets in [0,1) inside that cell (real), its
+//            weight and (electrons) u = gamma v.
+//   scratch: per-side tile counters, the filter ping-pong buffer, per-tile
+//            offsets for compaction, reduction partials and the error word.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pic {
+
+enum : unsigned { ERR_CAPACITY = 1u, ERR_CFL = 2u, ERR_NAN = 4u, ERR_TILE = 8u };
+
+struct Geom {
+    int dim;            // 2 or 3
+    int nx, ny, nz;     // cells (ny = 1 in 2D)
+    int bc_z;           // 0 periodic, 1 Mur
+    int shape;          // 1 or 2
+    int bx, by;         // bits of i and j in a packed cell index
+    int lt[3];          // log2 of the tile shape
+    int nt[3];          // tiles per axis
+    int cap;            // slots per tile
+    int64_t plane;      // nx * ny
+    int64_t ncomp;      // (nz + 1) * plane, elements per field component
+    int64_t ntiles;
+};
+
+template <typename real>
+struct Species {
+    real *ox, *oy, *oz, *w;     // oy is null in 2D
+    real *ux, *uy, *uz;         // null for ions (constant drift)
+    int32_t *cell;
+    int64_t *id;                // null unless ids are tracked
+};
+
+__host__ __device__ inline int32_t pack_cell(const Geom &g, int i, int j, int k)
+{
+    return (int32_t)((uint32_t)i | ((uint32_t)j << g.bx) | ((uint32_t)k << (g.bx + g.by)));
+}
+
+__host__ __device__ inline void unpack_cell(const Geom &g, int32_t c, int &i, int &j, int &k)
+{
+    uint32_t u = (uint32_t)c;
+    i = (int)(u & ((1u << g.bx) - 1u));
+    j = g.by ? (int)((u >> g.bx) & ((1u << g.by) - 1u)) : 0;
+    k = (int)(u >> (g.bx + g.by));
+}
+
+__host__ __device__ inline int64_t tile_of(const Geom &g, int i, int j, int k)
+{
+    return ((int64_t)(k >> g.lt[2]) * g.nt[1] + (j >> g.lt[1])) * g.nt[0] + (i >> g.lt[0]);
+}
+
+__host__ __device__ inline int64_t fidx(const Geom &g, int i, int j, int k)
+{
+    return ((int64_t)k * g.ny + j) * g.nx + i;
+}
+
+// z index range of a component: half-integer-z components (Ez, Bx, By, Jz)
+// live on k = 0..nz-1, the others on 0..nz; periodic z wraps over nz.
+__host__ __device__ inline int zmax_of(const Geom &g, bool half_z)
+{
+    if (g.bc_z == 0) return g.nz - 1;
+    return half_z ? g.nz - 1 : g.nz;
+}
+
+__host__ __device__ inline int wrapi(int i, int n)
+{
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+// ------------------------------------------------------------- buckets
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// Reserve one slot per lane in the bucket of `dest` (dest < 0: no slot),
+// one atomic per distinct destination in the warp.  All 32 lanes must call.
+__device__ __forceinline__ int reserve_slot(int *cnt, int64_t dest)
+{
+    const unsigned lane = lane_id();
+    const unsigned peers = __match_any_sync(0xffffffffu, (unsigned long long)dest);
+    const int leader = __ffs(peers) - 1;
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    int base = 0;
+    if (dest >= 0 && (int)lane == leader) base = atomicAdd(&cnt[dest], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    return base + rank;
+}
+
+// ---------------------------------------------------------------- shapes
+
+// 1D B-spline weights of order S at a position p measured from node 0 of a
+// window; returns the first node of the support and fills S+1 weights.
+template <int S, typename real>
+__device__ __forceinline__ int spline_weights(real p, real w[S + 1])
+{
+    if (S == 1) {
+        real f = floor(p);
+        real d = p - f;
+        w[0] = real(1) - d;
+        w[1] = d;
+        return (int)f;
+    } else {
+        real c = floor(p + real(0.5));
+        real d = p - c;
+        real a = real(0.5) - d, b = real(0.5) + d;
+        w[0] = real(0.5) * a * a;
+        w[1] = real(0.75) - d * d;
+        w[2] = real(0.5) * b * b;
+        return (int)c - 1;
+    }
+}
+
+// ----------------------------------------------------------------- Boris
+
+// relativistic Boris rotation for du/dt = 2 pi (q/m)(E + u x B / gamma);
+// eps = pi (q/m) dt is half the impulse factor
+template <typename real>
+__device__ __forceinline__ void boris(real &ux, real &uy, real &uz, real ex, real ey, real ez,
+                                      real bx, real by, real bz, real eps)
+{
+    real umx = ux + eps * ex, umy = uy + eps * ey, umz = uz + eps * ez;
+    real gm = sqrt(real(1) + umx * umx + umy * umy + umz * umz);
+    real f = eps / gm;
+    real tx = f * bx, ty = f * by, tz = f * bz;
+    real t2 = tx * tx + ty * ty + tz * tz;
+    real s = real(2) / (real(1) + t2);
+    real sx = s * tx, sy = s * ty, sz = s * tz;
+    real upx = umx + (umy * tz - umz * ty);
+    real upy = umy + (umz * tx - umx * tz);
+    real upz = umz + (umx * ty - umy * tx);
+    ux = umx + (upy * sz - upz * sy) + eps * ex;
+    uy = umy + (upz * sx - upx * sz) + eps * ey;
+    uz = umz + (upx * sy - upy * sx) + eps * ez;
+}
+
+// inverse Lorentz factor of u; shared by electrons and drifting ions so that a
+// field-free electron and its ion partner move bit-identically
+template <typename real>
+__device__ __forceinline__ real inv_gamma(real ux, real uy, real uz)
+{
+    return real(1) / sqrt(real(1) + ux * ux + uy * uy + uz * uz);
+}
+
+// largest value below one, for offsets that round up to 1
+template <typename real> __host__ __device__ inline real below_one();
+template <> __host__ __device__ inline float below_one<float>() { return 0.99999994f; }
+template <> __host__ __device__ inline double below_one<double>() { return 0.99999999999999989; }
+
+// ---------------------------------------------------- kernel argument packs
+
+template <typename real>
+struct PushArgs {
+    Geom g;
+    const real *E[3];
+    const real *B[3];
+    real *J[3];
+    Species<real> in, out;
+    int *cnt_in, *cnt_out;
+    real dtdh[3];       // dt / h_d
+    real eps;           // pi (q/m) dt
+    real jfac[3];       // -q h_d / (dt V): multiplied by w and the running sum
+    real jyfac;         // q / V (2D out-of-plane current, times w vy)
+    real ion_u[3];      // drift momentum of the ion species
+    unsigned *err;
+};
+
+template <typename real>
+struct BucketArgs {      // re-bucket a flat list into tiles
+    Geom g;
+    Species<real> src, dst;
+    int64_t n;
+    int *cnt_dst;
+    unsigned *err;
+};
+
+template <typename real>
+struct CompactArgs {     // copy tiles into a flat list
+    Geom g;
+    Species<real> src, dst;
+    const int *cnt;
+    const int64_t *offset;
+};
+
+struct InjectArgs {      // lattice load / boosted injection, FP64
+    Geom g;
+    double hx, hy, hz, Lx, Ly, Lz, gam, beta;
+    int ppx, ppy, ppz;
+    int64_t NX, NY, m_lo, m_hi;
+    double z_start, z_end, ramp, ne, jitter, dzl, hz_lab, wfac, uz0;
+    int nprof;
+    double prof[16];
+    uint64_t seed;
+    int mode;           // 0: in the box at t; 1: crossing z = Lz during (t, t1]
+    double t, t1;
+    int drift_ions;
+    int precision;      // 0 float, 1 double
+    void *sp_e[9];      // ox oy oz w ux uy uz cell id of the electron side
+    void *sp_i[9];      // same for the ion side (ux..uz unused)
+    int *cnt_e, *cnt_i;
+    unsigned *err;
+};
+
+// host launchers (defined in the .cu files)
+template <typename real> void launch_push(const PushArgs<real> &a, cudaStream_t s);
+template <typename real> void launch_ions(const PushArgs<real> &a, cudaStream_t s);
+template <typename real> void launch_bucket(const BucketArgs<real> &a, cudaStream_t s);
+template <typename real> void launch_compact(const CompactArgs<real> &a, cudaStream_t s);
+template <typename real>
+void launch_rho(const Geom &g, const Species<real> &sp, const int *cnt, real qfac, real *rho,
+                cudaStream_t s);
+template <typename real>
+void launch_particle_sums(const Geom &g, const Species<real> &sp, const int *cnt, double q,
+                          const real ion_u[3], double *partials, int nblocks, cudaStream_t s);
+void launch_inject(const InjectArgs &a, cudaStream_t s);
+
+template <typename real>
+void launch_yee(const Geom &g, real *const F[9], double dt, double hx, double hy, double hz,
+                cudaStream_t s);
+template <typename real>
+void launch_filter(const Geom &g, real *const J[3], real *tmp, int npass, cudaStream_t s);
+template <typename real>
+void launch_antenna(const Geom &g, real *J, int pol, int ka, double j0, double hx, double hy,
+                    double xc, double yc, double waist, cudaStream_t s);
+template <typename real>
+void launch_field_sums(const Geom &g, real *const F[9], double *partials, int nblocks,
+                       cudaStream_t s);
+
+}  // namespace pic

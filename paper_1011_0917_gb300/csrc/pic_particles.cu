@@ -1,0 +1,679 @@
+// pic_particles.cu -- particle kernels: fused gather / Boris push / Esirkepov
+// deposit / re-bucketing per tile, the drifting-ion deposit, bucketing of flat
+// lists, compaction, charge density and particle sums.
+//
+// One CTA owns one tile of cells.  It stages E and B of the tile plus guard
+// nodes in shared memory, pushes every particle of the tile, accumulates the
+// current of all of them in a shared-memory J tile (tile plus the guard nodes
+// a one-cell move can reach) and adds that tile to J in HBM once.  Each pushed
+// particle is written straight into the bucket of the tile it now lies in, on
+// the other side of the double buffer, so the store stays tile-sorted without
+// a separate sort pass.
+#include "pic_internal.cuh"
+
+namespace pic {
+
+// ---------------------------------------------------------------- helpers
+
+// Esirkepov window along one axis: old offset x0 in [0,1), new position x1 =
+// x0 + d (|d| < 1), both relative to the old cell.  Returns the first node of a
+// window of S+2 nodes that holds both supports, with S0 and DS = S1 - S0 on it.
+template <int S, typename real>
+__device__ __forceinline__ int esirk_axis(real x0, real x1, real S0[S + 2], real DS[S + 2])
+{
+    real w0[S + 1], w1[S + 1];
+    const int b0 = spline_weights<S>(x0, w0);
+    const int b1 = spline_weights<S>(x1, w1);
+    const int anchor = b0 < b1 ? b0 : b1;
+    const bool s0 = b0 != anchor;  // support shifted one node up in the window
+    const bool s1 = b1 != anchor;
+#pragma unroll
+    for (int q = 0; q < S + 2; ++q) {
+        real v0 = s0 ? (q >= 1 ? w0[q - 1 < S ? q - 1 : S] : real(0)) : (q <= S ? w0[q <= S ? q : S] : real(0));
+        real v1 = s1 ? (q >= 1 ? w1[q - 1 < S ? q - 1 : S] : real(0)) : (q <= S ? w1[q <= S ? q : S] : real(0));
+        S0[q] = v0;
+        DS[q] = v1 - v0;
+    }
+    return anchor;
+}
+
+template <typename real>
+__device__ __forceinline__ void sh_add(real *p, real v)
+{
+    atomicAdd(p, v);
+}
+
+// ---------------------------------------------------------------- gather
+
+// interpolate one component from the shared field tile: node (a, b, c) of the
+// support of each axis starts at base + cell-local index (+ guard FL)
+template <int DIM, int S, typename real>
+__device__ __forceinline__ real gather_comp(const real *F, int FX, int FY, int ix, int iy, int iz,
+                                            const real *wx, const real *wy, const real *wz)
+{
+    real sum = 0;
+    if (DIM == 3) {
+#pragma unroll
+        for (int c = 0; c <= S; ++c) {
+#pragma unroll
+            for (int b = 0; b <= S; ++b) {
+                const real *row = F + ((int64_t)(iz + c) * FY + (iy + b)) * FX + ix;
+                real r = 0;
+#pragma unroll
+                for (int a = 0; a <= S; ++a) r += wx[a] * row[a];
+                sum += wz[c] * wy[b] * r;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c <= S; ++c) {
+            const real *row = F + (int64_t)(iz + c) * FX + ix;
+            real r = 0;
+#pragma unroll
+            for (int a = 0; a <= S; ++a) r += wx[a] * row[a];
+            sum += wz[c] * r;
+        }
+    }
+    return sum;
+}
+
+// ------------------------------------------------------------ push kernel
+
+template <typename real, int DIM, int S>
+__global__ void __launch_bounds__(256) push_kernel(PushArgs<real> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Geom &g = a.g;
+    constexpr int FL = 1, FH = S;        // field guards below / above the tile
+    constexpr int JL = S, JH = S + 1;    // current guards below / above the tile
+    const int TX = 1 << g.lt[0], TY = DIM == 3 ? 1 << g.lt[1] : 1, TZ = 1 << g.lt[2];
+    const int FX = TX + FL + FH, FY = DIM == 3 ? TY + FL + FH : 1, FZ = TZ + FL + FH;
+    const int QX = TX + JL + JH, QY = DIM == 3 ? TY + JL + JH : 1, QZ = TZ + JL + JH;
+    const int FN = FX * FY * FZ, QN = QX * QY * QZ;
+    real *sF = reinterpret_cast<real *>(smem_raw);
+    real *sJ = sF + 6 * FN;
+
+    for (int64_t t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+        const int n = min(a.cnt_in[t], g.cap);
+        if (n == 0) continue;  // uniform over the CTA
+        const int tix = (int)(t % g.nt[0]);
+        const int tiy = (int)((t / g.nt[0]) % g.nt[1]);
+        const int tiz = (int)(t / ((int64_t)g.nt[0] * g.nt[1]));
+        const int lox = tix << g.lt[0], loy = tiy << g.lt[1], loz = tiz << g.lt[2];
+
+        __syncthreads();  // previous tile finished with shared memory
+        for (int q = threadIdx.x; q < 6 * FN; q += blockDim.x) {
+            const int c = q / FN, r = q - c * FN;
+            const int lz = r / (FX * FY), ly = (r / FX) % FY, lx = r % FX;
+            const int gi = wrapi(lox - FL + lx, g.nx);
+            const int gj = DIM == 3 ? wrapi(loy - FL + ly, g.ny) : 0;
+            int gk = loz - FL + lz;
+            const bool halfz = (c == 2 || c == 3 || c == 4);
+            real v = 0;
+            if (g.bc_z == 0) {
+                gk = wrapi(gk, g.nz);
+                v = c < 3 ? a.E[c][fidx(g, gi, gj, gk)] : a.B[c - 3][fidx(g, gi, gj, gk)];
+            } else if (gk >= 0 && gk <= zmax_of(g, halfz)) {
+                v = c < 3 ? a.E[c][fidx(g, gi, gj, gk)] : a.B[c - 3][fidx(g, gi, gj, gk)];
+            }
+            sF[q] = v;
+        }
+        for (int q = threadIdx.x; q < 3 * QN; q += blockDim.x) sJ[q] = 0;
+        __syncthreads();
+
+        const int64_t slot0 = t * (int64_t)g.cap;
+        for (int base = 0; base < n; base += blockDim.x) {
+            const int p = base + threadIdx.x;
+            bool valid = p < n;
+            int64_t dest = -1;
+            real ox = 0, oy = 0, oz = 0, w = 0, ux = 0, uy = 0, uz = 0;
+            int ni = 0, nj = 0, nk = 0;
+            int64_t pid = 0;
+            if (valid) {
+                const int64_t s = slot0 + p;
+                int ci, cj, ck;
+                unpack_cell(g, a.in.cell[s], ci, cj, ck);
+                const int li = ci - lox, lj = cj - loy, lk = ck - loz;
+                if (li < 0 || li >= TX || lj < 0 || lj >= TY || lk < 0 || lk >= TZ) {
+                    atomicOr(a.err, ERR_TILE);
+                    valid = false;
+                } else {
+                    ox = a.in.ox[s];
+                    oy = DIM == 3 ? a.in.oy[s] : real(0);
+                    oz = a.in.oz[s];
+                    w = a.in.w[s];
+                    ux = a.in.ux[s];
+                    uy = a.in.uy[s];
+                    uz = a.in.uz[s];
+                    if (a.in.id) pid = a.in.id[s];
+
+                    // gather: unstaggered (u) and half-shifted (h) weights per axis
+                    real wxu[S + 1], wxh[S + 1], wyu[S + 1], wyh[S + 1], wzu[S + 1], wzh[S + 1];
+                    const int bxu = spline_weights<S>(ox, wxu) + li + FL;
+                    const int bxh = spline_weights<S>(ox - real(0.5), wxh) + li + FL;
+                    const int bzu = spline_weights<S>(oz, wzu) + lk + FL;
+                    const int bzh = spline_weights<S>(oz - real(0.5), wzh) + lk + FL;
+                    int byu = 0, byh = 0;
+                    if (DIM == 3) {
+                        byu = spline_weights<S>(oy, wyu) + lj + FL;
+                        byh = spline_weights<S>(oy - real(0.5), wyh) + lj + FL;
+                    } else {
+#pragma unroll
+                        for (int q = 0; q <= S; ++q) wyu[q] = wyh[q] = real(q == 0);
+                    }
+                    real ex, ey, ez, bx, by, bz;
+                    ex = gather_comp<DIM, S>(sF + 0 * FN, FX, FY, bxh, byu, bzu, wxh, wyu, wzu);
+                    ey = gather_comp<DIM, S>(sF + 1 * FN, FX, FY, bxu, byh, bzu, wxu, wyh, wzu);
+                    ez = gather_comp<DIM, S>(sF + 2 * FN, FX, FY, bxu, byu, bzh, wxu, wyu, wzh);
+                    bx = gather_comp<DIM, S>(sF + 3 * FN, FX, FY, bxu, byh, bzh, wxu, wyh, wzh);
+                    by = gather_comp<DIM, S>(sF + 4 * FN, FX, FY, bxh, byu, bzh, wxh, wyu, wzh);
+                    bz = gather_comp<DIM, S>(sF + 5 * FN, FX, FY, bxh, byh, bzu, wxh, wyh, wzu);
+
+                    boris(ux, uy, uz, ex, ey, ez, bx, by, bz, a.eps);
+                    const real ig = inv_gamma(ux, uy, uz);
+                    const real vy = uy * ig;
+                    const real dx = ux * ig * a.dtdh[0];
+                    const real dy = DIM == 3 ? uy * ig * a.dtdh[1] : real(0);
+                    const real dz = uz * ig * a.dtdh[2];
+                    if (!(fabs(dx) < real(1) && fabs(dy) < real(1) && fabs(dz) < real(1))) {
+                        atomicOr(a.err, (dx == dx && dy == dy && dz == dz) ? ERR_CFL : ERR_NAN);
+                        valid = false;
+                    } else {
+                        const real x1 = ox + dx, y1 = oy + dy, z1 = oz + dz;
+                        // Esirkepov deposit into the shared J tile
+                        real S0x[S + 2], DSx[S + 2], S0y[S + 2], DSy[S + 2], S0z[S + 2], DSz[S + 2];
+                        const int ax = esirk_axis<S>(ox, x1, S0x, DSx) + li + JL;
+                        const int az = esirk_axis<S>(oz, z1, S0z, DSz) + lk + JL;
+                        const real fx = a.jfac[0] * w, fz = a.jfac[2] * w;
+                        real *Jx = sJ, *Jy = sJ + QN, *Jz = sJ + 2 * QN;
+                        constexpr real third = real(1) / real(3);
+                        if (DIM == 3) {
+                            const int ay = esirk_axis<S>(oy, y1, S0y, DSy) + lj + JL;
+                            const real fy = a.jfac[1] * w;
+#pragma unroll
+                            for (int c = 0; c < S + 2; ++c) {
+#pragma unroll
+                                for (int b = 0; b < S + 2; ++b) {
+                                    const real tyz = S0y[b] * (S0z[c] + real(0.5) * DSz[c]) +
+                                                     DSy[b] * (real(0.5) * S0z[c] + third * DSz[c]);
+                                    real acc = 0;
+                                    real *row = Jx + ((az + c) * QY + (ay + b)) * QX + ax;
+#pragma unroll
+                                    for (int q = 0; q < S + 1; ++q) {
+                                        acc += DSx[q] * tyz;
+                                        sh_add(row + q, fx * acc);
+                                    }
+                                }
+                            }
+#pragma unroll
+                            for (int c = 0; c < S + 2; ++c) {
+#pragma unroll
+                                for (int q = 0; q < S + 2; ++q) {
+                                    const real tzx = S0z[c] * (S0x[q] + real(0.5) * DSx[q]) +
+                                                     DSz[c] * (real(0.5) * S0x[q] + third * DSx[q]);
+                                    real acc = 0;
+#pragma unroll
+                                    for (int b = 0; b < S + 1; ++b) {
+                                        acc += DSy[b] * tzx;
+                                        sh_add(Jy + ((az + c) * QY + (ay + b)) * QX + ax + q, fy * acc);
+                                    }
+                                }
+                            }
+#pragma unroll
+                            for (int b = 0; b < S + 2; ++b) {
+#pragma unroll
+                                for (int q = 0; q < S + 2; ++q) {
+                                    const real txy = S0x[q] * (S0y[b] + real(0.5) * DSy[b]) +
+                                                     DSx[q] * (real(0.5) * S0y[b] + third * DSy[b]);
+                                    real acc = 0;
+#pragma unroll
+                                    for (int c = 0; c < S + 1; ++c) {
+                                        acc += DSz[c] * txy;
+                                        sh_add(Jz + ((az + c) * QY + (ay + b)) * QX + ax + q, fz * acc);
+                                    }
+                                }
+                            }
+                        } else {
+                            const real fyv = a.jyfac * w * vy;
+#pragma unroll
+                            for (int c = 0; c < S + 2; ++c) {
+                                const real tz = S0z[c] + real(0.5) * DSz[c];
+                                real acc = 0;
+                                real *row = Jx + (az + c) * QX + ax;
+#pragma unroll
+                                for (int q = 0; q < S + 1; ++q) {
+                                    acc += DSx[q] * tz;
+                                    sh_add(row + q, fx * acc);
+                                }
+                            }
+#pragma unroll
+                            for (int q = 0; q < S + 2; ++q) {
+                                const real tx = S0x[q] + real(0.5) * DSx[q];
+                                real acc = 0;
+#pragma unroll
+                                for (int c = 0; c < S + 1; ++c) {
+                                    acc += DSz[c] * tx;
+                                    sh_add(Jz + (az + c) * QX + ax + q, fz * acc);
+                                }
+                            }
+#pragma unroll
+                            for (int c = 0; c < S + 2; ++c) {
+#pragma unroll
+                                for (int q = 0; q < S + 2; ++q) {
+                                    const real wgt = S0x[q] * (S0z[c] + real(0.5) * DSz[c]) +
+                                                     DSx[q] * (real(0.5) * S0z[c] + third * DSz[c]);
+                                    sh_add(Jy + (az + c) * QX + ax + q, fyv * wgt);
+                                }
+                            }
+                        }
+                        // new cell and offsets; an offset that rounds to 1 moves on
+                        int sx = (int)floor(x1), sy = DIM == 3 ? (int)floor(y1) : 0, sz = (int)floor(z1);
+                        ox = x1 - real(sx);
+                        if (ox >= real(1)) { sx += 1; ox = 0; }
+                        if (DIM == 3) {
+                            oy = y1 - real(sy);
+                            if (oy >= real(1)) { sy += 1; oy = 0; }
+                        }
+                        oz = z1 - real(sz);
+                        if (oz >= real(1)) { sz += 1; oz = 0; }
+                        ni = ci + sx;
+                        if (ni < 0) ni += g.nx; else if (ni >= g.nx) ni -= g.nx;
+                        nj = cj + sy;
+                        if (DIM == 3) { if (nj < 0) nj += g.ny; else if (nj >= g.ny) nj -= g.ny; }
+                        nk = ck + sz;
+                        bool alive = true;
+                        if (g.bc_z == 0) {
+                            if (nk < 0) nk += g.nz; else if (nk >= g.nz) nk -= g.nz;
+                        } else if (nk < 0 || nk >= g.nz) {
+                            alive = false;
+                        }
+                        if (alive) dest = tile_of(g, ni, nj, nk);
+                    }
+                }
+            }
+            const int r = reserve_slot(a.cnt_out, dest);
+            if (dest >= 0) {
+                if (r >= g.cap) {
+                    atomicOr(a.err, ERR_CAPACITY);
+                } else {
+                    const int64_t d = dest * (int64_t)g.cap + r;
+                    a.out.ox[d] = ox;
+                    if (DIM == 3) a.out.oy[d] = oy;
+                    a.out.oz[d] = oz;
+                    a.out.w[d] = w;
+                    a.out.ux[d] = ux;
+                    a.out.uy[d] = uy;
+                    a.out.uz[d] = uz;
+                    a.out.cell[d] = pack_cell(g, ni, nj, nk);
+                    if (a.out.id) a.out.id[d] = pid;
+                }
+            }
+        }
+        __syncthreads();
+        // flush the J tile: one global add per non-zero node
+        for (int q = threadIdx.x; q < 3 * QN; q += blockDim.x) {
+            const real v = sJ[q];
+            if (v == real(0)) continue;
+            const int c = q / QN, r = q - c * QN;
+            const int lz = r / (QX * QY), ly = (r / QX) % QY, lx = r % QX;
+            const int gi = wrapi(lox - JL + lx, g.nx);
+            const int gj = DIM == 3 ? wrapi(loy - JL + ly, g.ny) : 0;
+            int gk = loz - JL + lz;
+            if (g.bc_z == 0) gk = wrapi(gk, g.nz);
+            else if (gk < 0 || gk > zmax_of(g, c == 2)) continue;
+            atomicAdd(a.J[c] + fidx(g, gi, gj, gk), v);
+        }
+        if (threadIdx.x == 0) a.cnt_in[t] = 0;
+    }
+}
+
+// ----------------------------------------------------- drifting-ion kernel
+
+// Ions immobile in the lab move at the species' constant u in the boosted
+// frame; their transverse shapes do not change, so only Jz is deposited:
+// Wz = DSz (S0x S0y), identical to the general formula with DSx = DSy = 0.
+template <typename real, int DIM, int S>
+__global__ void __launch_bounds__(256) ion_kernel(PushArgs<real> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Geom &g = a.g;
+    constexpr int JL = S, JH = S + 1;
+    const int TX = 1 << g.lt[0], TY = DIM == 3 ? 1 << g.lt[1] : 1, TZ = 1 << g.lt[2];
+    const int QX = TX + JL + JH, QY = DIM == 3 ? TY + JL + JH : 1, QZ = TZ + JL + JH;
+    const int QN = QX * QY * QZ;
+    real *sJ = reinterpret_cast<real *>(smem_raw);
+    const real ig = inv_gamma(a.ion_u[0], a.ion_u[1], a.ion_u[2]);
+    const real dx = a.ion_u[0] * ig * a.dtdh[0];
+    const real dy = DIM == 3 ? a.ion_u[1] * ig * a.dtdh[1] : real(0);
+    const real dz = a.ion_u[2] * ig * a.dtdh[2];
+
+    for (int64_t t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+        const int n = min(a.cnt_in[t], g.cap);
+        if (n == 0) continue;
+        const int tix = (int)(t % g.nt[0]);
+        const int tiy = (int)((t / g.nt[0]) % g.nt[1]);
+        const int tiz = (int)(t / ((int64_t)g.nt[0] * g.nt[1]));
+        const int lox = tix << g.lt[0], loy = tiy << g.lt[1], loz = tiz << g.lt[2];
+        __syncthreads();
+        for (int q = threadIdx.x; q < QN; q += blockDim.x) sJ[q] = 0;
+        __syncthreads();
+        const int64_t slot0 = t * (int64_t)g.cap;
+        for (int base = 0; base < n; base += blockDim.x) {
+            const int p = base + threadIdx.x;
+            int64_t dest = -1;
+            real ox = 0, oy = 0, oz = 0, w = 0;
+            int ni = 0, nj = 0, nk = 0;
+            int64_t pid = 0;
+            if (p < n) {
+                const int64_t s = slot0 + p;
+                int ci, cj, ck;
+                unpack_cell(g, a.in.cell[s], ci, cj, ck);
+                const int li = ci - lox, lj = cj - loy, lk = ck - loz;
+                if (li < 0 || li >= TX || lj < 0 || lj >= TY || lk < 0 || lk >= TZ) {
+                    atomicOr(a.err, ERR_TILE);
+                } else {
+                    ox = a.in.ox[s];
+                    oy = DIM == 3 ? a.in.oy[s] : real(0);
+                    oz = a.in.oz[s];
+                    w = a.in.w[s];
+                    if (a.in.id) pid = a.in.id[s];
+                    const real x1 = ox + dx, y1 = oy + dy, z1 = oz + dz;
+                    real S0z[S + 2], DSz[S + 2], wx[S + 1], wy[S + 1];
+                    const int az = esirk_axis<S>(oz, z1, S0z, DSz) + lk + JL;
+                    const int bx = spline_weights<S>(ox, wx) + li + JL;
+                    int by = 0;
+                    if (DIM == 3) by = spline_weights<S>(oy, wy) + lj + JL;
+                    const real fz = a.jfac[2] * w;
+#pragma unroll
+                    for (int b = 0; b < (DIM == 3 ? S + 1 : 1); ++b) {
+#pragma unroll
+                        for (int q = 0; q < S + 1; ++q) {
+                            const real sxy = DIM == 3 ? wx[q] * wy[b] : wx[q];
+                            real acc = 0;
+#pragma unroll
+                            for (int c = 0; c < S + 1; ++c) {
+                                acc += DSz[c] * sxy;
+                                atomicAdd(sJ + ((az + c) * QY + (by + b)) * QX + bx + q, fz * acc);
+                            }
+                        }
+                    }
+                    int sx = (int)floor(x1), sy = DIM == 3 ? (int)floor(y1) : 0, sz = (int)floor(z1);
+                    ox = x1 - real(sx);
+                    if (ox >= real(1)) { sx += 1; ox = 0; }
+                    if (DIM == 3) {
+                        oy = y1 - real(sy);
+                        if (oy >= real(1)) { sy += 1; oy = 0; }
+                    }
+                    oz = z1 - real(sz);
+                    if (oz >= real(1)) { sz += 1; oz = 0; }
+                    ni = ci + sx;
+                    if (ni < 0) ni += g.nx; else if (ni >= g.nx) ni -= g.nx;
+                    nj = cj + sy;
+                    if (DIM == 3) { if (nj < 0) nj += g.ny; else if (nj >= g.ny) nj -= g.ny; }
+                    nk = ck + sz;
+                    bool alive = true;
+                    if (g.bc_z == 0) {
+                        if (nk < 0) nk += g.nz; else if (nk >= g.nz) nk -= g.nz;
+                    } else if (nk < 0 || nk >= g.nz) {
+                        alive = false;
+                    }
+                    if (alive) dest = tile_of(g, ni, nj, nk);
+                }
+            }
+            const int r = reserve_slot(a.cnt_out, dest);
+            if (dest >= 0) {
+                if (r >= g.cap) {
+                    atomicOr(a.err, ERR_CAPACITY);
+                } else {
+                    const int64_t d = dest * (int64_t)g.cap + r;
+                    a.out.ox[d] = ox;
+                    if (DIM == 3) a.out.oy[d] = oy;
+                    a.out.oz[d] = oz;
+                    a.out.w[d] = w;
+                    a.out.cell[d] = pack_cell(g, ni, nj, nk);
+                    if (a.out.id) a.out.id[d] = pid;
+                }
+            }
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < QN; q += blockDim.x) {
+            const real v = sJ[q];
+            if (v == real(0)) continue;
+            const int lz = q / (QX * QY), ly = (q / QX) % QY, lx = q % QX;
+            const int gi = wrapi(lox - JL + lx, g.nx);
+            const int gj = DIM == 3 ? wrapi(loy - JL + ly, g.ny) : 0;
+            int gk = loz - JL + lz;
+            if (g.bc_z == 0) gk = wrapi(gk, g.nz);
+            else if (gk < 0 || gk > zmax_of(g, true)) continue;
+            atomicAdd(a.J[2] + fidx(g, gi, gj, gk), v);
+        }
+        if (threadIdx.x == 0) a.cnt_in[t] = 0;
+    }
+}
+
+template <typename real, int DIM, int S>
+static size_t push_smem(const Geom &g, bool ions)
+{
+    const int TX = 1 << g.lt[0], TY = DIM == 3 ? 1 << g.lt[1] : 1, TZ = 1 << g.lt[2];
+    const int FN = (TX + 1 + S) * (DIM == 3 ? TY + 1 + S : 1) * (TZ + 1 + S);
+    const int QN = (TX + 2 * S + 1) * (DIM == 3 ? TY + 2 * S + 1 : 1) * (TZ + 2 * S + 1);
+    return ions ? sizeof(real) * (size_t)QN : sizeof(real) * (size_t)(6 * FN + 3 * QN);
+}
+
+template <typename real, int DIM, int S>
+static void launch_push_t(const PushArgs<real> &a, bool ions, cudaStream_t s)
+{
+    const size_t smem = push_smem<real, DIM, S>(a.g, ions);
+    auto k = ions ? ion_kernel<real, DIM, S> : push_kernel<real, DIM, S>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int64_t grid = a.g.ntiles < 2147483647LL ? a.g.ntiles : 2147483647LL;
+    k<<<(unsigned)grid, 256, smem, s>>>(a);
+}
+
+template <typename real>
+static void dispatch_push(const PushArgs<real> &a, bool ions, cudaStream_t s)
+{
+    if (a.g.dim == 3) {
+        if (a.g.shape == 1) launch_push_t<real, 3, 1>(a, ions, s);
+        else launch_push_t<real, 3, 2>(a, ions, s);
+    } else {
+        if (a.g.shape == 1) launch_push_t<real, 2, 1>(a, ions, s);
+        else launch_push_t<real, 2, 2>(a, ions, s);
+    }
+}
+
+template <typename real> void launch_push(const PushArgs<real> &a, cudaStream_t s) { dispatch_push(a, false, s); }
+template <typename real> void launch_ions(const PushArgs<real> &a, cudaStream_t s) { dispatch_push(a, true, s); }
+
+// ------------------------------------------------------ bucket / compact
+
+template <typename real>
+__global__ void bucket_kernel(BucketArgs<real> a)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t nround = (a.n + 31) / 32 * 32;  // whole warps iterate together
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nround; p += stride) {
+        int64_t dest = -1;
+        int ci = 0, cj = 0, ck = 0;
+        if (p < a.n) {
+            unpack_cell(a.g, a.src.cell[p], ci, cj, ck);
+            dest = tile_of(a.g, ci, cj, ck);
+        }
+        const int r = reserve_slot(a.cnt_dst, dest);
+        if (dest < 0) continue;
+        if (r >= a.g.cap) {
+            atomicOr(a.err, ERR_CAPACITY);
+            continue;
+        }
+        const int64_t d = dest * (int64_t)a.g.cap + r;
+        a.dst.ox[d] = a.src.ox[p];
+        if (a.dst.oy) a.dst.oy[d] = a.src.oy[p];
+        a.dst.oz[d] = a.src.oz[p];
+        a.dst.w[d] = a.src.w[p];
+        if (a.dst.ux) {
+            a.dst.ux[d] = a.src.ux[p];
+            a.dst.uy[d] = a.src.uy[p];
+            a.dst.uz[d] = a.src.uz[p];
+        }
+        a.dst.cell[d] = a.src.cell[p];
+        if (a.dst.id) a.dst.id[d] = a.src.id ? a.src.id[p] : 0;
+    }
+}
+
+template <typename real>
+void launch_bucket(const BucketArgs<real> &a, cudaStream_t s)
+{
+    if (a.n <= 0) return;
+    int64_t blocks = (a.n + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    bucket_kernel<real><<<(unsigned)blocks, 256, 0, s>>>(a);
+}
+
+template <typename real>
+__global__ void compact_kernel(CompactArgs<real> a)
+{
+    for (int64_t t = blockIdx.x; t < a.g.ntiles; t += gridDim.x) {
+        const int n = min(a.cnt[t], a.g.cap);
+        const int64_t o = a.offset[t], s0 = t * (int64_t)a.g.cap;
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+            const int64_t s = s0 + p, d = o + p;
+            a.dst.ox[d] = a.src.ox[s];
+            if (a.src.oy) a.dst.oy[d] = a.src.oy[s];
+            a.dst.oz[d] = a.src.oz[s];
+            a.dst.w[d] = a.src.w[s];
+            if (a.src.ux) {
+                a.dst.ux[d] = a.src.ux[s];
+                a.dst.uy[d] = a.src.uy[s];
+                a.dst.uz[d] = a.src.uz[s];
+            }
+            a.dst.cell[d] = a.src.cell[s];
+            if (a.src.id) a.dst.id[d] = a.src.id[s];
+        }
+    }
+}
+
+template <typename real>
+void launch_compact(const CompactArgs<real> &a, cudaStream_t s)
+{
+    const int64_t grid = a.g.ntiles < 1048576 ? a.g.ntiles : 1048576;
+    if (grid > 0) compact_kernel<real><<<(unsigned)grid, 256, 0, s>>>(a);
+}
+
+// ------------------------------------------------------- charge density
+
+template <typename real, int DIM, int S>
+__global__ void rho_kernel(Geom g, Species<real> sp, const int *cnt, real qfac, real *rho)
+{
+    for (int64_t t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+        const int n = min(cnt[t], g.cap);
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+            const int64_t s = t * (int64_t)g.cap + p;
+            int ci, cj, ck;
+            unpack_cell(g, sp.cell[s], ci, cj, ck);
+            real wx[S + 1], wy[S + 1], wz[S + 1];
+            const int bx = spline_weights<S>(sp.ox[s], wx) + ci;
+            const int bz = spline_weights<S>(sp.oz[s], wz) + ck;
+            int by = 0;
+            if (DIM == 3) by = spline_weights<S>(sp.oy[s], wy) + cj;
+            const real q = qfac * sp.w[s];
+            for (int c = 0; c <= S; ++c) {
+                int k = bz + c;
+                if (g.bc_z == 0) k = wrapi(k, g.nz);
+                else if (k < 0 || k > g.nz) continue;
+                for (int b = 0; b < (DIM == 3 ? S + 1 : 1); ++b) {
+                    const int j = DIM == 3 ? wrapi(by + b, g.ny) : 0;
+                    for (int a = 0; a <= S; ++a) {
+                        const int i = wrapi(bx + a, g.nx);
+                        const real wt = DIM == 3 ? wx[a] * wy[b] * wz[c] : wx[a] * wz[c];
+                        atomicAdd(rho + fidx(g, i, j, k), q * wt);
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <typename real>
+void launch_rho(const Geom &g, const Species<real> &sp, const int *cnt, real qfac, real *rho,
+                cudaStream_t s)
+{
+    const int64_t grid = g.ntiles < 1048576 ? g.ntiles : 1048576;
+    if (grid <= 0) return;
+    if (g.dim == 3) {
+        if (g.shape == 1) rho_kernel<real, 3, 1><<<(unsigned)grid, 128, 0, s>>>(g, sp, cnt, qfac, rho);
+        else rho_kernel<real, 3, 2><<<(unsigned)grid, 128, 0, s>>>(g, sp, cnt, qfac, rho);
+    } else {
+        if (g.shape == 1) rho_kernel<real, 2, 1><<<(unsigned)grid, 128, 0, s>>>(g, sp, cnt, qfac, rho);
+        else rho_kernel<real, 2, 2><<<(unsigned)grid, 128, 0, s>>>(g, sp, cnt, qfac, rho);
+    }
+}
+
+// -------------------------------------------------------- particle sums
+
+// Kahan-compensated FP64 partial sums per block: [0] sum w (gamma-1),
+// [1] sum q w.  The host adds the block partials, also with compensation.
+template <typename real>
+__global__ void particle_sums_kernel(Geom g, Species<real> sp, const int *cnt, double q,
+                                     double iux, double iuy, double iuz, double *partials)
+{
+    double s0 = 0, c0 = 0, s1 = 0, c1 = 0;
+    for (int64_t t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+        const int n = min(cnt[t], g.cap);
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+            const int64_t s = t * (int64_t)g.cap + p;
+            const double w = (double)sp.w[s];
+            double ux = iux, uy = iuy, uz = iuz;
+            if (sp.ux) {
+                ux = (double)sp.ux[s];
+                uy = (double)sp.uy[s];
+                uz = (double)sp.uz[s];
+            }
+            const double u2 = ux * ux + uy * uy + uz * uz;
+            const double ke = w * (u2 / (sqrt(1.0 + u2) + 1.0));  // gamma - 1 without cancellation
+            double y = ke - c0, tt = s0 + y;
+            c0 = (tt - s0) - y;
+            s0 = tt;
+            y = q * w - c1;
+            tt = s1 + y;
+            c1 = (tt - s1) - y;
+            s1 = tt;
+        }
+    }
+    __shared__ double red[2][256];
+    red[0][threadIdx.x] = s0 - c0;
+    red[1][threadIdx.x] = s1 - c1;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + off];
+            red[1][threadIdx.x] += red[1][threadIdx.x + off];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = red[0][0];
+        partials[2 * blockIdx.x + 1] = red[1][0];
+    }
+}
+
+template <typename real>
+void launch_particle_sums(const Geom &g, const Species<real> &sp, const int *cnt, double q,
+                          const real ion_u[3], double *partials, int nblocks, cudaStream_t s)
+{
+    particle_sums_kernel<real><<<nblocks, 256, 0, s>>>(g, sp, cnt, q, (double)ion_u[0], (double)ion_u[1],
+                                                       (double)ion_u[2], partials);
+}
+
+#define PIC_INSTANTIATE(real)                                                                       \
+    template void launch_push<real>(const PushArgs<real> &, cudaStream_t);                          \
+    template void launch_ions<real>(const PushArgs<real> &, cudaStream_t);                          \
+    template void launch_bucket<real>(const BucketArgs<real> &, cudaStream_t);                      \
+    template void launch_compact<real>(const CompactArgs<real> &, cudaStream_t);                    \
+    template void launch_rho<real>(const Geom &, const Species<real> &, const int *, real, real *,  \
+                                   cudaStream_t);                                                   \
+    template void launch_particle_sums<real>(const Geom &, const Species<real> &, const int *,      \
+                                             double, const real *, double *, int, cudaStream_t);
+PIC_INSTANTIATE(float)
+PIC_INSTANTIATE(double)
+
+}  // namespace pic

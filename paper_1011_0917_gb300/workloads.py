@@ -1,0 +1,113 @@
+"""Seeded synthetic workloads: parameter sets of the stages and random inputs.
+
+This module holds configuration and random-number generation only -- none of
+the PIC method's arithmetic -- and is the one module that both the CUDA path
+(through the binding) and the FP64 oracle are fed from.  Lengths in lambda0,
+times in lambda0/c, densities in n_c, lab-frame quantities unless noted.
+
+Stages (the paper's 100 MeV stage at gamma_boost 13 and the 10 GeV-class stage
+at gamma_boost 130 stand behind these; no dataset is involved):
+  c0  lab frame, 2D3V, 64 x 512, dx = 1/2, dz = 1/16, CIC, 1 filter pass,
+      n = 0.01 over z in [4, 32) with a 2 lambda0 ramp, 2 x 2 per cell with
+      0.1-cell jitter, immobile ions, laser a0 = 1, w0 = 8, FWHM 5.
+  c1  gamma_boost = 13, 2D3V, 256 x 8192, dx = 1, dz = 1/32 (lab), CIC,
+      2 passes, n = 0.001 over 2000 lambda0 (lab), 2 x 2 per cell, laser
+      a0 = 1, w0 = 20, FWHM 10.  The plasma starts 18000 lambda0 (lab) ahead
+      of the antenna so the boosted pulse is emitted in vacuum.
+  c2  the c1 stage in 3D: 256 x 256 x 1024, 2 x 2 x 2 per cell with the
+      plasma filling the box from 4 cells on (~535M electrons) and streaming
+      in through z = Lz for the whole run; the throughput workload.
+  c3  gamma_boost = 130, 2D3V, 512 x 16384, quadratic shape, 4 passes,
+      n = 5.7e-5, 5 lambda0 ramp, laser a0 = 1.5, w0 = 50, FWHM 30; c3_small
+      is the same stage on a 4x coarser grid (128 x 4096).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+SEED0 = 10110917
+
+
+@dataclasses.dataclass
+class Stage:
+    name: str
+    grid: dict
+    plasma: dict
+    laser: dict
+    steps: int
+
+    def seed(self) -> int:
+        return self.grid.get("seed", SEED0)
+
+
+def _grid(**kw):
+    g = dict(dim=2, nx=64, ny=1, nz=512, dx=0.5, dy=1.0, dz=1.0 / 16, cfl=0.99, gamma_boost=1.0,
+             shape_order=1, filter_passes=1, bc_z=1, seed=SEED0)
+    g.update(kw)
+    return g
+
+
+def stage(name: str) -> Stage:
+    if name == "c0":
+        return Stage(name, _grid(seed=SEED0 + 0),
+                     dict(ne=0.01, z_start=4.0, z_end=32.0, ramp=2.0, ppc=(2, 1, 2), jitter=0.1, ions=1),
+                     dict(a0=1.0, waist=8.0, fwhm=5.0, z_antenna=0.0, pol=1), steps=512)
+    if name == "c1":
+        return Stage(name, _grid(nx=256, nz=8192, dx=1.0, dz=1.0 / 32, gamma_boost=13.0, filter_passes=2,
+                                 seed=SEED0 + 1),
+                     dict(ne=0.001, z_start=18000.0, z_end=20000.0, ramp=2.0, ppc=(2, 1, 2), jitter=0.1, ions=1),
+                     dict(a0=1.0, waist=20.0, fwhm=10.0, z_antenna=0.0, pol=1), steps=1800)
+    if name == "c2":
+        gam = 13.0
+        beta = math.sqrt(1.0 - 1.0 / gam ** 2)
+        hz = (1.0 / 32) * gam * (1.0 + beta)
+        return Stage(name, _grid(dim=3, nx=256, ny=256, nz=1024, dx=1.0, dy=1.0, dz=1.0 / 32, gamma_boost=gam,
+                                 filter_passes=2, seed=SEED0 + 2),
+                     dict(ne=0.001, z_start=gam * 4 * hz, z_end=gam * 4 * hz + 50000.0, ramp=2.0, ppc=(2, 2, 2),
+                          jitter=0.1, ions=1),
+                     dict(a0=1.0, waist=20.0, fwhm=10.0, z_antenna=0.0, pol=1), steps=1000)
+    if name in ("c3", "c3_small"):
+        small = name == "c3_small"
+        return Stage(name, _grid(nx=128 if small else 512, nz=4096 if small else 16384, dx=4.0 if small else 1.0,
+                                 dz=(4.0 if small else 1.0) / 32, gamma_boost=130.0, shape_order=2,
+                                 filter_passes=4, seed=SEED0 + 3),
+                     dict(ne=5.7e-5, z_start=6.0e5, z_end=1.6e6, ramp=5.0, ppc=(2, 1, 2), jitter=0.1, ions=1),
+                     dict(a0=1.5, waist=50.0, fwhm=30.0, z_antenna=0.0, pol=1), steps=2000)
+    raise KeyError(name)
+
+
+def scaled(st: Stage, **grid_overrides) -> Stage:
+    """Copy of a stage with some grid fields replaced (smaller parity cases)."""
+    g = dict(st.grid)
+    g.update(grid_overrides)
+    return Stage(st.name + "*", g, dict(st.plasma), dict(st.laser), st.steps)
+
+
+# -------------------------------------------------------- random inputs
+
+
+def random_fields(shape3, seed: int, scale: float = 0.05) -> dict:
+    """Smooth-ish random E, B, J arrays (k, j, i) for single-phase tests."""
+    rng = np.random.default_rng(seed)
+    out = {}
+    for c in ("Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx", "Jy", "Jz"):
+        out[c] = rng.normal(scale=scale, size=shape3)
+    return out
+
+
+def random_particles(n: int, box: tuple, seed: int, u_scale: float = 0.5, w_range=(0.5, 1.5),
+                     dim: int = 2, margin_z: float = 0.0) -> np.ndarray:
+    """(7, n) float64: x, y, z uniform in the box (z kept `margin_z` from the
+    ends), u normal, w uniform."""
+    rng = np.random.default_rng(seed)
+    Lx, Ly, Lz = box
+    s = np.zeros((7, n))
+    s[0] = rng.uniform(0, Lx, n)
+    s[1] = rng.uniform(0, Ly, n) if dim == 3 else 0.0
+    s[2] = rng.uniform(margin_z, Lz - margin_z, n)
+    s[3:6] = rng.normal(scale=u_scale, size=(3, n))
+    s[6] = rng.uniform(*w_range, n)
+    return s

@@ -1,0 +1,94 @@
+"""Helpers that run the CUDA library and the FP64 oracle side by side on the
+same seeded inputs (test infrastructure)."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+COMPONENTS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx", "Jy", "Jz")
+HALF_Z = {"Ez", "Bx", "By", "Jz"}
+
+
+def oracle_grid(O, g: dict):
+    return O.GridParams(dim=g["dim"], nx=g["nx"], ny=g.get("ny", 1), nz=g["nz"], dx=g["dx"], dy=g.get("dy", 1.0),
+                        dz=g["dz"], cfl=g.get("cfl", 0.99), gamma_boost=g.get("gamma_boost", 1.0),
+                        shape=g.get("shape_order", 1), npass=g.get("filter_passes", 1), bc_z=g.get("bc_z", 1),
+                        seed=g.get("seed", 1))
+
+
+def make_pair(O, g: dict, precision: int, track_ids: bool = True, slots_per_cell: float = 16.0, tile=(0, 0, 0)):
+    import paper_1011_0917_gb300 as P
+    sim = P.Simulation(dim=g["dim"], nx=g["nx"], ny=g.get("ny", 1), nz=g["nz"], dx=g["dx"], dy=g.get("dy", 1.0),
+                       dz=g["dz"], cfl=g.get("cfl", 0.99), gamma_boost=g.get("gamma_boost", 1.0),
+                       shape_order=g.get("shape_order", 1), filter_passes=g.get("filter_passes", 1),
+                       bc_z=g.get("bc_z", 1), precision=precision, seed=g.get("seed", 1),
+                       slots_per_cell=slots_per_cell, track_ids=track_ids, tile=tile)
+    o = O.Oracle(oracle_grid(O, g))
+    assert sim.dt == o.dt
+    return sim, o
+
+
+def zmax(c: str, nz: int, bc_z: int) -> int:
+    if bc_z == 0:
+        return nz - 1
+    return nz - 1 if c in HALF_Z else nz
+
+
+def set_fields_both(sim, o, fields: dict, bc_z: int):
+    nz = o.grid.nz
+    clean = {}
+    for c, v in fields.items():
+        v = np.array(v, dtype=np.float64)
+        v[zmax(c, nz, bc_z) + 1:] = 0.0
+        clean[c] = v
+        o.field(c)[...] = v
+    sim.set_fields(clean)
+
+
+def gpu_fields(sim) -> dict:
+    return {c: t.double().cpu().numpy() for c, t in sim.fields().items()}
+
+
+def field_errors(sim, o, comps=COMPONENTS, bc_z: int = 1) -> dict:
+    """relative L2 error of each component over its valid planes"""
+    g = gpu_fields(sim)
+    nz = o.grid.nz
+    out = {}
+    for c in comps:
+        km = zmax(c, nz, bc_z) + 1
+        a, b = g[c][:km], o.field(c)[:km]
+        nb = np.linalg.norm(b)
+        out[c] = np.linalg.norm(a - b) / nb if nb > 0 else np.linalg.norm(a)
+    return out
+
+
+def field_maxrel(sim, o, comps=COMPONENTS, bc_z: int = 1) -> dict:
+    """max |a - b| / max |b| of each component over its valid planes"""
+    g = gpu_fields(sim)
+    nz = o.grid.nz
+    out = {}
+    for c in comps:
+        km = zmax(c, nz, bc_z) + 1
+        a, b = g[c][:km], o.field(c)[:km]
+        m = np.abs(b).max()
+        out[c] = np.abs(a - b).max() / m if m > 0 else np.abs(a).max()
+    return out
+
+
+def gpu_particles(sim, sp: int = 0):
+    st, ids = sim.particles(sp, with_ids=True)
+    order = np.argsort(ids, kind="stable")
+    return st[:, order], ids[order]
+
+
+def oracle_particles(o, sp: int = 0):
+    p = o.particles(sp)
+    st = np.stack([p["x"], p["y"], p["z"], p["ux"], p["uy"], p["uz"], p["w"]])
+    order = np.argsort(p["id"], kind="stable")
+    return st[:, order], p["id"][order]
+
+
+def periodic_delta(a, b, L):
+    d = a - b
+    return d - L * np.round(d / L)

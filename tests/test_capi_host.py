@@ -1,0 +1,105 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds for
+sm_103a, loads, exports every function include/pic.h declares, validates its
+arguments, and derives the simulation-frame quantities exactly as the oracle
+does (bit for bit)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1011_0917_gb300 as P
+    P.lib()
+    return P
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "pic.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pic_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("pic_init_grid", "pic_load_plasma", "pic_launch_laser", "pic_step", "pic_get_fields",
+                     "pic_get_particles"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(P):
+    lib = C.CDLL(P.library_path())
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_library_targets_sm_103a(P):
+    # the build line passes exactly one -gencode for compute_103a / sm_103a
+    from paper_1011_0917_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def grid(P, **kw):
+    d = dict(dim=2, nx=64, ny=1, nz=512, dx=0.5, dy=1.0, dz=1 / 16, cfl=0.99, gamma_boost=1.0, shape_order=1,
+             filter_passes=1, bc_z=1, precision=0, seed=1, slots_per_cell=8.0, tile=(0, 0, 0), track_ids=0)
+    d.update(kw)
+    return P.GridParams(d["dim"], d["nx"], d["ny"], d["nz"], d["dx"], d["dy"], d["dz"], d["cfl"], d["gamma_boost"],
+                        d["shape_order"], d["filter_passes"], d["bc_z"], d["precision"], d["seed"],
+                        d["slots_per_cell"], (C.c_int * 3)(*d["tile"]), d["track_ids"], None)
+
+
+@pytest.mark.parametrize("bad,status", [
+    (dict(cfl=1.0), 5), (dict(cfl=1.2), 5), (dict(cfl=0.0), 1), (dict(dim=4), 1), (dict(nx=0), 1),
+    (dict(ny=2), 1), (dict(shape_order=3), 1), (dict(gamma_boost=0.5), 1), (dict(tile=(3, 0, 0)), 1),
+    (dict(precision=7), 1), (dict(slots_per_cell=0.0), 1), (dict(filter_passes=-1), 1), (dict(nz=2), 1),
+    (dict(dim=3, ny=4, dy=-1.0), 1),
+])
+def test_init_grid_rejects_invalid_parameters(P, bad, status):
+    with pytest.raises(P.PicError) as e:
+        P.pic_init_grid(grid(P, **bad))
+    assert e.value.status == status
+
+
+@pytest.mark.parametrize("kw", [
+    dict(), dict(gamma_boost=13.0, dx=1.0, dz=1 / 32, nx=256, nz=8192),
+    dict(dim=3, nx=32, ny=16, nz=64, dx=1.0, dy=1.0, dz=1 / 32, gamma_boost=13.0),
+    dict(gamma_boost=130.0, dx=1.0, dz=1 / 32, nx=512, nz=16384, shape_order=2, filter_passes=4),
+])
+def test_derived_quantities_match_oracle(P, oracle_mod, kw):
+    g = grid(P, **kw)
+    ctx = P.pic_init_grid(g)
+    try:
+        s = P.pic_query_sizes(ctx)
+        o = oracle_mod.Oracle(oracle_mod.GridParams(dim=g.dim, nx=g.nx, ny=g.ny, nz=g.nz, dx=g.dx, dy=g.dy, dz=g.dz,
+                                                    cfl=g.cfl, gamma_boost=g.gamma_boost, shape=g.shape_order,
+                                                    npass=g.filter_passes))
+        assert (s.dt, s.hx, s.hz, s.beta) == (o.dt, o.hx, o.hz, o.beta)
+        if g.dim == 3:
+            assert s.hy == o.hy
+        # buffers: 9 field components, two bucket sides per species
+        es = s.elem_bytes
+        assert s.field_bytes == 9 * (g.nz + 1) * (g.ny if g.dim == 3 else 1) * g.nx * es
+        assert s.slots[0] == s.ntiles * s.tile_capacity and s.tile_capacity % 32 == 0
+        assert (s.species_bytes[1] > 0) == (g.gamma_boost > 1.0)
+    finally:
+        P.pic_destroy(ctx)
+
+
+def test_calls_before_bind_are_rejected(P):
+    ctx = P.pic_init_grid(grid(P))
+    try:
+        with pytest.raises(P.PicError) as e:
+            P.pic_step(ctx, 1)
+        assert e.value.status == 2
+        assert "bind" in P.pic_last_error(ctx)
+    finally:
+        P.pic_destroy(ctx)
+
+
+def test_status_strings(P):
+    for s in range(8):
+        assert P.pic_status_string(s)
