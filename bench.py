@@ -277,6 +277,8 @@ def workload_name(w: str) -> str:
               "2 binomial passes, FP32",
         "c1": "2D3V boosted frame gamma=13, 256x8192 cells, 2x2 electrons/cell, CIC, 2 passes, FP32",
         "c0": "2D3V lab frame, 64x512 cells, 2x2 electrons/cell, CIC, 1 pass, FP32",
+        "c2_small": "3D boosted frame gamma=13, 128x128x256 cells (profiling slab of the 256x256x1024 stage), "
+                    "2x2x2 electrons/cell (+drifting ions), CIC, 2 binomial passes, FP32",
     }
     return names.get(w, w)
 

@@ -227,21 +227,22 @@ void launch_filter(const Geom &g, real *const J[3], real *tmp, int npass, cudaSt
 // ---------------------------------------------------------------- antenna
 
 // Current sheet on plane ka: J_pol += j0 exp(-r^2 / w0^2) at each node of the
-// polarisation component (its own staggered transverse position).
+// polarisation component (its own staggered transverse position).  One plane
+// per step: the profile is evaluated in FP64 and rounded once.
 template <typename real>
-__global__ void antenna_kernel(Geom g, real *J, int pol, int ka, real j0, real hx, real hy, real xc,
-                               real yc, real inv_w2)
+__global__ void antenna_kernel(Geom g, real *J, int pol, int ka, double j0, double hx, double hy, double xc,
+                               double yc, double inv_w2)
 {
     const int64_t n = g.plane;
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(o % g.nx), j = (int)(o / g.nx);
-        const real x = ((real)i + (pol == 0 ? real(0.5) : real(0))) * hx - xc;
-        real r2 = x * x;
+        const double x = ((double)i + (pol == 0 ? 0.5 : 0.0)) * hx - xc;
+        double r2 = x * x;
         if (g.dim == 3) {
-            const real y = ((real)j + (pol == 1 ? real(0.5) : real(0))) * hy - yc;
+            const double y = ((double)j + (pol == 1 ? 0.5 : 0.0)) * hy - yc;
             r2 += y * y;
         }
-        J[(int64_t)ka * g.plane + o] += j0 * exp(-r2 * inv_w2);
+        J[(int64_t)ka * g.plane + o] += (real)(j0 * exp(-r2 * inv_w2));
     }
 }
 
@@ -249,8 +250,8 @@ template <typename real>
 void launch_antenna(const Geom &g, real *J, int pol, int ka, double j0, double hx, double hy, double xc,
                     double yc, double waist, cudaStream_t s)
 {
-    antenna_kernel<real><<<grid_for(g.plane, 256), 256, 0, s>>>(g, J, pol, ka, (real)j0, (real)hx, (real)hy,
-                                                               (real)xc, (real)yc, (real)(1.0 / (waist * waist)));
+    antenna_kernel<real><<<grid_for(g.plane, 256), 256, 0, s>>>(g, J, pol, ka, j0, hx, hy, xc, yc,
+                                                               1.0 / (waist * waist));
 }
 
 // ------------------------------------------------------------ field sums

@@ -16,7 +16,8 @@ at gamma_boost 130 stand behind these; no dataset is involved):
       of the antenna so the boosted pulse is emitted in vacuum.
   c2  the c1 stage in 3D: 256 x 256 x 1024, 2 x 2 x 2 per cell with the
       plasma filling the box from 4 cells on (~535M electrons) and streaming
-      in through z = Lz for the whole run; the throughput workload.
+      in through z = Lz for the whole run; the throughput workload.  c2_small
+      is the same stage on a 128 x 128 x 256 box, for kernel profiles.
   c3  gamma_boost = 130, 2D3V, 512 x 16384, quadratic shape, 4 passes,
       n = 5.7e-5, 5 lambda0 ramp, laser a0 = 1.5, w0 = 50, FWHM 30; c3_small
       is the same stage on a 4x coarser grid (128 x 4096).
@@ -69,6 +70,12 @@ def stage(name: str) -> Stage:
                      dict(ne=0.001, z_start=gam * 4 * hz, z_end=gam * 4 * hz + 50000.0, ramp=2.0, ppc=(2, 2, 2),
                           jitter=0.1, ions=1),
                      dict(a0=1.0, waist=20.0, fwhm=10.0, z_antenna=0.0, pol=1), steps=1000)
+    if name == "c2_small":
+        # the c2 stage on a 128 x 128 x 256 box (~33M electrons, a few GB on
+        # the device): the case the kernel profiles are captured on
+        st = stage("c2")
+        g = dict(st.grid, nx=128, ny=128, nz=256)
+        return Stage(name, g, dict(st.plasma), dict(st.laser), steps=100)
     if name in ("c3", "c3_small"):
         small = name == "c3_small"
         return Stage(name, _grid(nx=128 if small else 512, nz=4096 if small else 16384, dx=4.0 if small else 1.0,

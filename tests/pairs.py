@@ -92,3 +92,29 @@ def oracle_particles(o, sp: int = 0):
 def periodic_delta(a, b, L):
     d = a - b
     return d - L * np.round(d / L)
+
+
+def vector_errors(sim, o, bc_z: int = 1, floor: float = 0.1) -> dict:
+    """Relative L2 of the E field and of the B field as vectors (all three
+    components together), plus the relative L2 of every component that carries
+    at least `floor` of its vector field's norm.  A component the physics
+    leaves at zero (e.g. Ez where no wake has formed yet) holds round-off only
+    on both sides; its own relative error says nothing about the method."""
+    g = gpu_fields(sim)
+    nz = o.grid.nz
+    out = {}
+    for name, comps in (("E", ("Ex", "Ey", "Ez")), ("B", ("Bx", "By", "Bz"))):
+        num = den = 0.0
+        norms = {}
+        for c in comps:
+            km = zmax(c, nz, bc_z) + 1
+            a, b = g[c][:km], o.field(c)[:km]
+            num += float(np.sum((a - b) ** 2))
+            den += float(np.sum(b ** 2))
+            norms[c] = (float(np.linalg.norm(a - b)), float(np.linalg.norm(b)))
+        out[name] = math.sqrt(num / den) if den > 0 else math.sqrt(num)
+        vn = math.sqrt(den)
+        for c, (dn, bn) in norms.items():
+            if vn > 0 and bn >= floor * vn:
+                out[c] = dn / bn
+    return out
