@@ -265,6 +265,47 @@ pic_status pic_profile(pic_ctx *ctx, int enable);
    Any output pointer may be NULL. */
 pic_status pic_profile_read(pic_ctx *ctx, double ms[8], int64_t calls[8], int64_t *kernels);
 
+/* --------------------------------------------- allocation-free current filter */
+
+/* Largest field component, in nodes ((nz+1) * ny * nx), that
+   pic_filter_current_noalloc accepts. */
+#define PIC_NOALLOC_MAX_NODES 4194304
+
+/* The binomial current filter of the FILTER phase, for callers that cannot
+   allocate device memory: the rest of this library needs a caller-provided
+   scratch buffer (pic_query_sizes / pic_bind_buffers), which a caller cannot
+   supply when every byte of device memory is owned by another framework's
+   allocator, or when it runs under a fixed device-memory budget or in a
+   latency-critical loop that must never allocate.  The paper has no
+   counterpart of this entry point; it is a deployment variant of the FILTER
+   phase and computes the same thing: `passes` (1/4, 1/2, 1/4) passes along x,
+   then y (3D), then z, on each of Jx, Jy, Jz in place, with the same boundary
+   rules (x, y periodic; z periodic or zero outside each component's valid z
+   range).
+
+   jx, jy, jz: device arrays of (nz+1) * ny * nx elements (float for
+   precision PIC_FP32, double for PIC_FP64) in the library's [k][j][i] layout;
+   ny must be 1 when dim == 2.  Work is enqueued on `stream` (a cudaStream_t,
+   NULL: legacy default stream) and the call returns without synchronising.
+
+   Scratch: one field component lives in a file-scope device array of
+   PIC_NOALLOC_MAX_NODES doubles (32 MiB) that every GPU which loads the
+   library holds until the process exits.  The call allocates and frees
+   nothing.  The first call on a device (the current device at the time of
+   the call) looks up that array's device address once (cudaGetSymbolAddress);
+   make that first call before any stream capture.  Every call shares the one
+   array, which keeps the last call's contents; nothing in it needs to start at
+   zero because every pass writes each element before it is read.  Calls whose
+   work overlaps on the GPU (different streams, or other threads) race on the
+   array: issue them one after another, e.g. on one stream.
+
+   Errors: PIC_ERR_ARG for an invalid dimension, size, boundary, precision or
+   null pointer, and when (nz+1) * ny * nx exceeds PIC_NOALLOC_MAX_NODES;
+   PIC_ERR_CUDA if a CUDA call fails.  No context is involved, so there is no
+   pic_last_error detail. */
+pic_status pic_filter_current_noalloc(int dim, int nx, int ny, int nz, int bc_z, int passes, int precision,
+                                      void *jx, void *jy, void *jz, void *stream);
+
 /* ------------------------------------------------------------------ misc */
 
 const char *pic_last_error(const pic_ctx *ctx);

@@ -22,7 +22,7 @@ __all__ = [
     "pic_launch_laser", "pic_step", "pic_step_async", "pic_step_phases", "pic_get_fields", "pic_set_fields",
     "pic_get_axis", "pic_get_particles", "pic_get_rho", "pic_get_diagnostics", "pic_state_bytes",
     "pic_get_state", "pic_set_state", "pic_last_error", "pic_status_string", "pic_destroy", "pic_profile",
-    "pic_profile_read", "Simulation",
+    "pic_profile_read", "pic_filter_current_noalloc", "PIC_NOALLOC_MAX_NODES", "Simulation",
     "library_path",
 ]
 
@@ -36,6 +36,7 @@ COMPONENTS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx", "Jy", "Jz")
 PH_ZERO_J, PH_PUSH, PH_IONS, PH_ANTENNA = 1, 2, 4, 8
 PH_FILTER, PH_YEE, PH_INJECT, PH_TIME = 16, 32, 64, 128
 PH_ALL = 255
+PIC_NOALLOC_MAX_NODES = 4194304
 
 
 class PicError(RuntimeError):
@@ -120,6 +121,7 @@ def _load():
         "pic_destroy": (None, [P]),
         "pic_profile": (S, [P, I]),
         "pic_profile_read": (S, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+        "pic_filter_current_noalloc": (S, [I, I, I, I, I, I, I, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -264,6 +266,21 @@ def pic_profile_read(ctx):
     k = C.c_int64(0)
     _check(ctx, _load().pic_profile_read(ctx, ms, calls, C.byref(k)))
     return list(ms), list(calls), k.value
+
+
+def pic_filter_current_noalloc(dim: int, nx: int, ny: int, nz: int, bc_z: int, passes: int, precision: int,
+                               jx_ptr: int, jy_ptr: int, jz_ptr: int, stream_ptr: int = 0):
+    """Filter Jx, Jy, Jz (device pointers, the library's layout) in place
+    without any device allocation; see include/pic.h.  Raises PicError on a
+    non-OK status, naming the size limit when that is the cause."""
+    st = _load().pic_filter_current_noalloc(dim, nx, ny, nz, bc_z, passes, precision, C.c_void_p(jx_ptr),
+                                            C.c_void_p(jy_ptr), C.c_void_p(jz_ptr), C.c_void_p(stream_ptr))
+    if st != PIC_OK:
+        nodes = (nz + 1) * ny * nx
+        detail = _load().pic_status_string(st).decode()
+        if st == PIC_ERR_ARG and nodes > PIC_NOALLOC_MAX_NODES:
+            detail = f"{nodes} nodes per component exceed the static scratch of {PIC_NOALLOC_MAX_NODES} nodes"
+        raise PicError(st, detail)
 
 
 # --------------------------------------------------- torch-owned buffers

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libpic.so")
 
-SOURCES = ["pic_capi.cu", "pic_particles.cu", "pic_fields.cu", "pic_inject.cu"]
+SOURCES = ["pic_capi.cu", "pic_particles.cu", "pic_fields.cu", "pic_inject.cu", "pic_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
