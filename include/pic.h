@@ -100,7 +100,8 @@ typedef struct pic_grid_params {
     int precision;          /* PIC_FP32 (production) or PIC_FP64 (debug)        */
     uint64_t seed;          /* SplitMix64 seed of the plasma jitter             */
     double slots_per_cell;  /* particle slots per cell and species, > 0         */
-    int tile[3];            /* tile shape in cells, powers of two; 0: default   */
+    int tile[3];            /* tile shape in cells: 0 or the compiled shape,     */
+                            /* 8x8x8 in 3D, 16x1x16 in 2D (others: PIC_ERR_ARG) */
     int track_ids;          /* 1: carry an int64 lattice id with each particle */
     void *stream;           /* cudaStream_t for all device work (NULL: legacy)  */
 } pic_grid_params;

@@ -219,21 +219,19 @@ extern "C" pic_status pic_init_grid(const pic_grid_params *p, pic_ctx **out)
         delete c;
         return PIC_ERR_ARG;
     }
+    // the particle kernels are compiled for one tile shape per dimension
     const int def2[3] = {16, 1, 16}, def3[3] = {8, 8, 8};
     const int ncell[3] = {g.nx, g.ny, g.nz};
     int64_t cells_per_tile = 1;
     for (int d = 0; d < 3; ++d) {
-        int t = p->tile[d] ? p->tile[d] : (p->dim == 3 ? def3[d] : def2[d]);
-        if (p->dim == 2 && d == 1) t = 1;
-        const int cap_t = 1 << ceil_log2(ncell[d]);
-        if (t > cap_t) t = cap_t;
+        const int t = p->dim == 3 ? def3[d] : def2[d];
+        if (p->tile[d] != 0 && p->tile[d] != t && !(p->dim == 2 && d == 1)) {
+            delete c;
+            return PIC_ERR_ARG;
+        }
         g.lt[d] = ceil_log2(t);
         g.nt[d] = (ncell[d] + t - 1) / t;
         cells_per_tile *= t;
-    }
-    if ((1 << g.lt[0]) > 64 || (1 << g.lt[1]) > 64 || (1 << g.lt[2]) > 64) {
-        delete c;
-        return PIC_ERR_ARG;
     }
     g.ntiles = (int64_t)g.nt[0] * g.nt[1] * g.nt[2];
     int64_t cap = (int64_t)std::ceil(p->slots_per_cell * (double)cells_per_tile);
@@ -633,7 +631,7 @@ static void run_phases_t(pic_ctx *c, unsigned mask)
         PhaseTimer pt(c, 4);
         real *J[3] = {F[6], F[7], F[8]};
         launch_filter<real>(c->g, J, (real *)(c->scratch + c->off_tmp), c->p.filter_passes, c->stream);
-        c->kernels += (int64_t)(c->g.dim == 3 ? 3 : 2) * c->p.filter_passes;
+        c->kernels += c->p.filter_passes <= 4 ? 1 : (int64_t)(c->g.dim == 3 ? 3 : 2) * c->p.filter_passes;
     }
     if (mask & PIC_PH_YEE) {
         PhaseTimer pt(c, 5);

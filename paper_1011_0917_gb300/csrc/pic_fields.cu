@@ -199,10 +199,107 @@ __global__ void filter_kernel(Geom g, const real *in0, const real *in1, const re
     }
 }
 
+// All passes of all axes in one kernel: a CTA stages a block of one component
+// plus a halo of H = npass nodes per side in shared memory, applies the passes
+// there (x, then y, then z, each from one buffer into the other, the same
+// arithmetic in the same order as filter_kernel) and writes the block centre
+// to `out`.  With absorbing z, nodes outside the component's valid z range are
+// zero before every z pass, as the per-pass kernel treats them.
+template <typename real, int DIM, int BX, int BY, int BZ, int H>
+__global__ void __launch_bounds__(256) filter_fused_kernel(Geom g, const real *in0, const real *in1, const real *in2,
+                                                           real *out0, real *out1, real *out2)
+{
+    constexpr int AX = BX + 2 * H, AY = DIM == 3 ? BY + 2 * H : 1, AZ = BZ + 2 * H;
+    constexpr int AN = AX * AY * AZ;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    real *A = reinterpret_cast<real *>(smem_raw);
+    real *Bf = A + AN;
+    const int c = blockIdx.z;
+    const real *in = c == 0 ? in0 : (c == 1 ? in1 : in2);
+    real *out = c == 0 ? out0 : (c == 1 ? out1 : out2);
+    const int zmax = zmax_of(g, c == 2);
+    const int nbx = (g.nx + BX - 1) / BX;
+    const int bxi = blockIdx.x % nbx, byi = blockIdx.x / nbx;
+    const int ox = bxi * BX - H, oy = DIM == 3 ? byi * BY - H : 0, oz = blockIdx.y * BZ - H;
+    for (int q = threadIdx.x; q < AN; q += blockDim.x) {
+        const int lx = q % AX, ly = (q / AX) % AY, lz = q / (AX * AY);
+        const int gi = wrapi(ox + lx, g.nx);
+        const int gj = DIM == 3 ? wrapi(oy + ly, g.ny) : 0;
+        int gk = oz + lz;
+        real v = 0;
+        if (g.bc_z == 0) v = in[fidx(g, gi, gj, wrapi(gk, g.nz))];
+        else if (gk >= 0 && gk <= zmax) v = in[fidx(g, gi, gj, gk)];
+        A[q] = v;
+    }
+    __syncthreads();
+    const int npass = H;
+    for (int axis = 0; axis < 3; ++axis) {
+        if (axis == 1 && DIM != 3) continue;
+        const int stride = axis == 0 ? 1 : (axis == 1 ? AX : AX * AY);
+        const int ext = axis == 0 ? AX : (axis == 1 ? AY : AZ);
+        for (int p = 0; p < npass; ++p) {
+            for (int q = threadIdx.x; q < AN; q += blockDim.x) {
+                const int l = axis == 0 ? q % AX : (axis == 1 ? (q / AX) % AY : q / (AX * AY));
+                real v;
+                if (l == 0 || l == ext - 1) v = A[q];  // halo edge: never reaches the centre
+                else v = real(0.25) * A[q - stride] + real(0.5) * A[q] + real(0.25) * A[q + stride];
+                if (axis == 2 && g.bc_z != 0) {
+                    const int gk = oz + q / (AX * AY);
+                    if (gk < 0 || gk > zmax) v = 0;
+                }
+                Bf[q] = v;
+            }
+            __syncthreads();
+            real *t = A;
+            A = Bf;
+            Bf = t;
+        }
+    }
+    for (int q = threadIdx.x; q < BX * (DIM == 3 ? BY : 1) * BZ; q += blockDim.x) {
+        const int lx = q % BX, ly = DIM == 3 ? (q / BX) % BY : 0, lz = q / (BX * (DIM == 3 ? BY : 1));
+        const int gi = bxi * BX + lx, gj = DIM == 3 ? byi * BY + ly : 0, gk = blockIdx.y * BZ + lz;
+        if (gi >= g.nx || gj >= g.ny || gk > g.nz) continue;
+        out[fidx(g, gi, gj, gk)] = gk > zmax ? real(0) : A[((lz + H) * AY + (ly + (DIM == 3 ? H : 0))) * AX + lx + H];
+    }
+}
+
+template <typename real, int DIM, int BX, int BY, int BZ, int H>
+static void launch_fused(const Geom &g, real *const J[3], real *tmp, cudaStream_t s)
+{
+    constexpr int AN = (BX + 2 * H) * (DIM == 3 ? BY + 2 * H : 1) * (BZ + 2 * H);
+    const size_t smem = 2 * sizeof(real) * AN;
+    auto k = filter_fused_kernel<real, DIM, BX, BY, BZ, H>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const unsigned nbx = (g.nx + BX - 1) / BX, nby = DIM == 3 ? (g.ny + BY - 1) / BY : 1;
+    dim3 grid(nbx * nby, (g.nz + 1 + BZ - 1) / BZ, 3);
+    k<<<grid, 256, smem, s>>>(g, J[0], J[1], J[2], tmp, tmp + g.ncomp, tmp + 2 * g.ncomp);
+    cudaMemcpyAsync(J[0], tmp, 3 * sizeof(real) * g.ncomp, cudaMemcpyDeviceToDevice, s);
+}
+
 template <typename real>
 void launch_filter(const Geom &g, real *const J[3], real *tmp, int npass, cudaStream_t s)
 {
     if (npass <= 0) return;
+    // the three components are contiguous in the field buffer; the fused
+    // kernel covers 1..4 passes, more fall back to one launch per pass
+    const bool contiguous = J[1] == J[0] + g.ncomp && J[2] == J[1] + g.ncomp;
+    if (contiguous && npass <= 4) {
+        if (g.dim == 3) {
+            switch (npass) {
+            case 1: launch_fused<real, 3, 32, 8, 8, 1>(g, J, tmp, s); return;
+            case 2: launch_fused<real, 3, 32, 8, 8, 2>(g, J, tmp, s); return;
+            case 3: launch_fused<real, 3, 32, 8, 8, 3>(g, J, tmp, s); return;
+            default: launch_fused<real, 3, 32, 8, 8, 4>(g, J, tmp, s); return;
+            }
+        } else {
+            switch (npass) {
+            case 1: launch_fused<real, 2, 64, 1, 32, 1>(g, J, tmp, s); return;
+            case 2: launch_fused<real, 2, 64, 1, 32, 2>(g, J, tmp, s); return;
+            case 3: launch_fused<real, 2, 64, 1, 32, 3>(g, J, tmp, s); return;
+            default: launch_fused<real, 2, 64, 1, 32, 4>(g, J, tmp, s); return;
+            }
+        }
+    }
     real *src[3] = {J[0], J[1], J[2]};
     real *dst[3] = {tmp, tmp + g.ncomp, tmp + 2 * g.ncomp};
     const unsigned grid = grid_for(3 * g.ncomp, 256);

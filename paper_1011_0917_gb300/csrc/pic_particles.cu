@@ -37,10 +37,106 @@ __device__ __forceinline__ int esirk_axis(real x0, real x1, real S0[S + 2], real
     return anchor;
 }
 
+// shared-memory accumulation of one Esirkepov contribution; exact zeros
+// (nodes of the window outside both supports) are not added
 template <typename real>
 __device__ __forceinline__ void sh_add(real *p, real v)
 {
-    atomicAdd(p, v);
+    if (v != real(0)) atomicAdd(p, v);
+}
+
+// periodic index for i in [-n, 2n)
+__device__ __forceinline__ int wrap1(int i, int n)
+{
+    return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+
+// Stage `ncomp` field components of the box [lo - L, lo - L + F) (per axis)
+// into shared memory, one warp per row of FX nodes along x (coalesced loads,
+// one index decomposition per row).  Nodes outside the valid z range of a
+// component (absorbing z) are zero; x and y wrap.
+template <typename real>
+struct Ptr6 {
+    const real *p0, *p1, *p2, *p3, *p4, *p5;
+    __device__ __forceinline__ const real *operator[](int c) const
+    {
+        return c == 0 ? p0 : c == 1 ? p1 : c == 2 ? p2 : c == 3 ? p3 : c == 4 ? p4 : p5;
+    }
+};
+
+template <typename real>
+struct Ptr3 {
+    real *p0, *p1, *p2;
+    __device__ __forceinline__ real *operator[](int c) const { return c == 0 ? p0 : c == 1 ? p1 : p2; }
+};
+
+template <typename real, int DIM>
+__device__ __forceinline__ void stage_rows(const Geom &g, const Ptr6<real> src, unsigned half_z, int ncomp,
+                                           real *dst, int FX, int FY, int FZ, int lox, int loy, int loz, int L)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int per_c = FY * FZ;
+    const bool tiny = g.nx < FX || (DIM == 3 && g.ny < FY);
+    for (int row = warp; row < ncomp * per_c; row += nwarps) {
+        const int c = row / per_c, rr = row - c * per_c;
+        const int lz = rr / FY, ly = rr - lz * FY;
+        int gk = loz - L + lz;
+        bool ok = true;
+        if (g.bc_z == 0) gk = wrapi(gk, g.nz);
+        else ok = gk >= 0 && gk <= zmax_of(g, (half_z >> c) & 1u);
+        const int gj = DIM == 3 ? (tiny ? wrapi(loy - L + ly, g.ny) : wrap1(loy - L + ly, g.ny)) : 0;
+        const real *row_src = src[c] + ((int64_t)(ok ? gk : 0) * g.ny + gj) * g.nx;
+        real *row_dst = dst + (int64_t)c * FX * per_c + (lz * FY + ly) * FX;
+        for (int lx = lane; lx < FX; lx += 32) {
+            const int gi = tiny ? wrapi(lox - L + lx, g.nx) : wrap1(lox - L + lx, g.nx);
+            row_dst[lx] = ok ? row_src[gi] : real(0);
+        }
+    }
+}
+
+// Add `ncomp` shared-memory tiles (box [lo - L, lo - L + Q) per axis) to the
+// global arrays: one warp per row, non-zero nodes only, periodic x and y,
+// nodes outside a component's valid z range dropped (absorbing z).
+template <typename real, int DIM>
+__device__ __forceinline__ void flush_rows(const Geom &g, const Ptr3<real> dstJ, unsigned half_z, int ncomp,
+                                           const real *src, int QX, int QY, int QZ, int lox, int loy, int loz, int L)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int per_c = QY * QZ;
+    const bool tiny = g.nx < QX || (DIM == 3 && g.ny < QY);
+    for (int row = warp; row < ncomp * per_c; row += nwarps) {
+        const int c = row / per_c, rr = row - c * per_c;
+        const int lz = rr / QY, ly = rr - lz * QY;
+        int gk = loz - L + lz;
+        if (g.bc_z == 0) gk = wrapi(gk, g.nz);
+        else if (gk < 0 || gk > zmax_of(g, (half_z >> c) & 1u)) continue;
+        const int gj = DIM == 3 ? (tiny ? wrapi(loy - L + ly, g.ny) : wrap1(loy - L + ly, g.ny)) : 0;
+        real *row_dst = dstJ[c] + ((int64_t)gk * g.ny + gj) * g.nx;
+        const real *row_src = src + (int64_t)c * QX * per_c + (lz * QY + ly) * QX;
+        for (int lx = lane; lx < QX; lx += 32) {
+            const real v = row_src[lx];
+            if (v != real(0)) {
+                const int gi = tiny ? wrapi(lox - L + lx, g.nx) : wrap1(lox - L + lx, g.nx);
+                atomicAdd(row_dst + gi, v);
+            }
+        }
+    }
+}
+
+// Slot in the bucket of `dest` for every lane (dest < 0: none).  Fast path:
+// when every valid lane of the warp stays in tile `own`, one atomic.
+__device__ __forceinline__ int reserve_slot_own(int *cnt, int64_t dest, int64_t own)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned valid = __ballot_sync(0xffffffffu, dest >= 0);
+    const unsigned stay = __ballot_sync(0xffffffffu, dest == own);
+    if (stay == valid) {
+        int base = 0;
+        if (lane == 0 && valid) base = atomicAdd(&cnt[own], __popc(valid));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        return base + __popc(valid & ((1u << lane) - 1u));
+    }
+    return reserve_slot(cnt, dest);
 }
 
 // ---------------------------------------------------------------- gather
@@ -79,17 +175,18 @@ __device__ __forceinline__ real gather_comp(const real *F, int FX, int FY, int i
 
 // ------------------------------------------------------------ push kernel
 
-template <typename real, int DIM, int S>
+template <typename real, int DIM, int S, int TX, int TY, int TZ>
 __global__ void __launch_bounds__(256) push_kernel(PushArgs<real> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Geom &g = a.g;
+    // tile shape and shared-tile extents are compile-time constants, so every
+    // stencil offset below folds into an immediate
     constexpr int FL = 1, FH = S;        // field guards below / above the tile
     constexpr int JL = S, JH = S + 1;    // current guards below / above the tile
-    const int TX = 1 << g.lt[0], TY = DIM == 3 ? 1 << g.lt[1] : 1, TZ = 1 << g.lt[2];
-    const int FX = TX + FL + FH, FY = DIM == 3 ? TY + FL + FH : 1, FZ = TZ + FL + FH;
-    const int QX = TX + JL + JH, QY = DIM == 3 ? TY + JL + JH : 1, QZ = TZ + JL + JH;
-    const int FN = FX * FY * FZ, QN = QX * QY * QZ;
+    constexpr int FX = TX + FL + FH, FY = DIM == 3 ? TY + FL + FH : 1, FZ = TZ + FL + FH;
+    constexpr int QX = TX + JL + JH, QY = DIM == 3 ? TY + JL + JH : 1, QZ = TZ + JL + JH;
+    constexpr int FN = FX * FY * FZ, QN = QX * QY * QZ;
     real *sF = reinterpret_cast<real *>(smem_raw);
     real *sJ = sF + 6 * FN;
 
@@ -102,22 +199,9 @@ __global__ void __launch_bounds__(256) push_kernel(PushArgs<real> a)
         const int lox = tix << g.lt[0], loy = tiy << g.lt[1], loz = tiz << g.lt[2];
 
         __syncthreads();  // previous tile finished with shared memory
-        for (int q = threadIdx.x; q < 6 * FN; q += blockDim.x) {
-            const int c = q / FN, r = q - c * FN;
-            const int lz = r / (FX * FY), ly = (r / FX) % FY, lx = r % FX;
-            const int gi = wrapi(lox - FL + lx, g.nx);
-            const int gj = DIM == 3 ? wrapi(loy - FL + ly, g.ny) : 0;
-            int gk = loz - FL + lz;
-            const bool halfz = (c == 2 || c == 3 || c == 4);
-            real v = 0;
-            if (g.bc_z == 0) {
-                gk = wrapi(gk, g.nz);
-                v = c < 3 ? a.E[c][fidx(g, gi, gj, gk)] : a.B[c - 3][fidx(g, gi, gj, gk)];
-            } else if (gk >= 0 && gk <= zmax_of(g, halfz)) {
-                v = c < 3 ? a.E[c][fidx(g, gi, gj, gk)] : a.B[c - 3][fidx(g, gi, gj, gk)];
-            }
-            sF[q] = v;
-        }
+        // Ez, Bx, By live on half-integer z (bits 2, 3, 4)
+        stage_rows<real, DIM>(g, Ptr6<real>{a.E[0], a.E[1], a.E[2], a.B[0], a.B[1], a.B[2]}, 0x1Cu, 6, sF, FX, FY,
+                              FZ, lox, loy, loz, FL);
         for (int q = threadIdx.x; q < 3 * QN; q += blockDim.x) sJ[q] = 0;
         __syncthreads();
 
@@ -291,7 +375,7 @@ __global__ void __launch_bounds__(256) push_kernel(PushArgs<real> a)
                     }
                 }
             }
-            const int r = reserve_slot(a.cnt_out, dest);
+            const int r = reserve_slot_own(a.cnt_out, dest, t);
             if (dest >= 0) {
                 if (r >= g.cap) {
                     atomicOr(a.err, ERR_CAPACITY);
@@ -311,18 +395,7 @@ __global__ void __launch_bounds__(256) push_kernel(PushArgs<real> a)
         }
         __syncthreads();
         // flush the J tile: one global add per non-zero node
-        for (int q = threadIdx.x; q < 3 * QN; q += blockDim.x) {
-            const real v = sJ[q];
-            if (v == real(0)) continue;
-            const int c = q / QN, r = q - c * QN;
-            const int lz = r / (QX * QY), ly = (r / QX) % QY, lx = r % QX;
-            const int gi = wrapi(lox - JL + lx, g.nx);
-            const int gj = DIM == 3 ? wrapi(loy - JL + ly, g.ny) : 0;
-            int gk = loz - JL + lz;
-            if (g.bc_z == 0) gk = wrapi(gk, g.nz);
-            else if (gk < 0 || gk > zmax_of(g, c == 2)) continue;
-            atomicAdd(a.J[c] + fidx(g, gi, gj, gk), v);
-        }
+        flush_rows<real, DIM>(g, Ptr3<real>{a.J[0], a.J[1], a.J[2]}, 0x4u, 3, sJ, QX, QY, QZ, lox, loy, loz, JL);
         if (threadIdx.x == 0) a.cnt_in[t] = 0;
     }
 }
@@ -332,15 +405,14 @@ __global__ void __launch_bounds__(256) push_kernel(PushArgs<real> a)
 // Ions immobile in the lab move at the species' constant u in the boosted
 // frame; their transverse shapes do not change, so only Jz is deposited:
 // Wz = DSz (S0x S0y), identical to the general formula with DSx = DSy = 0.
-template <typename real, int DIM, int S>
+template <typename real, int DIM, int S, int TX, int TY, int TZ>
 __global__ void __launch_bounds__(256) ion_kernel(PushArgs<real> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Geom &g = a.g;
     constexpr int JL = S, JH = S + 1;
-    const int TX = 1 << g.lt[0], TY = DIM == 3 ? 1 << g.lt[1] : 1, TZ = 1 << g.lt[2];
-    const int QX = TX + JL + JH, QY = DIM == 3 ? TY + JL + JH : 1, QZ = TZ + JL + JH;
-    const int QN = QX * QY * QZ;
+    constexpr int QX = TX + JL + JH, QY = DIM == 3 ? TY + JL + JH : 1, QZ = TZ + JL + JH;
+    constexpr int QN = QX * QY * QZ;
     real *sJ = reinterpret_cast<real *>(smem_raw);
     const real ig = inv_gamma(a.ion_u[0], a.ion_u[1], a.ion_u[2]);
     const real dx = a.ion_u[0] * ig * a.dtdh[0];
@@ -393,7 +465,7 @@ __global__ void __launch_bounds__(256) ion_kernel(PushArgs<real> a)
 #pragma unroll
                             for (int c = 0; c < S + 1; ++c) {
                                 acc += DSz[c] * sxy;
-                                atomicAdd(sJ + ((az + c) * QY + (by + b)) * QX + bx + q, fz * acc);
+                                sh_add(sJ + ((az + c) * QY + (by + b)) * QX + bx + q, fz * acc);
                             }
                         }
                     }
@@ -420,7 +492,7 @@ __global__ void __launch_bounds__(256) ion_kernel(PushArgs<real> a)
                     if (alive) dest = tile_of(g, ni, nj, nk);
                 }
             }
-            const int r = reserve_slot(a.cnt_out, dest);
+            const int r = reserve_slot_own(a.cnt_out, dest, t);
             if (dest >= 0) {
                 if (r >= g.cap) {
                     atomicOr(a.err, ERR_CAPACITY);
@@ -436,35 +508,28 @@ __global__ void __launch_bounds__(256) ion_kernel(PushArgs<real> a)
             }
         }
         __syncthreads();
-        for (int q = threadIdx.x; q < QN; q += blockDim.x) {
-            const real v = sJ[q];
-            if (v == real(0)) continue;
-            const int lz = q / (QX * QY), ly = (q / QX) % QY, lx = q % QX;
-            const int gi = wrapi(lox - JL + lx, g.nx);
-            const int gj = DIM == 3 ? wrapi(loy - JL + ly, g.ny) : 0;
-            int gk = loz - JL + lz;
-            if (g.bc_z == 0) gk = wrapi(gk, g.nz);
-            else if (gk < 0 || gk > zmax_of(g, true)) continue;
-            atomicAdd(a.J[2] + fidx(g, gi, gj, gk), v);
-        }
+        flush_rows<real, DIM>(g, Ptr3<real>{a.J[2], a.J[2], a.J[2]}, 0x1u, 1, sJ, QX, QY, QZ, lox, loy, loz, JL);
         if (threadIdx.x == 0) a.cnt_in[t] = 0;
     }
 }
 
-template <typename real, int DIM, int S>
-static size_t push_smem(const Geom &g, bool ions)
+// the tile shapes the kernels are compiled for (pic_init_grid accepts these)
+constexpr int kTile3[3] = {8, 8, 8};
+constexpr int kTile2[3] = {16, 1, 16};
+
+template <typename real, int DIM, int S, int TX, int TY, int TZ>
+static size_t push_smem(bool ions)
 {
-    const int TX = 1 << g.lt[0], TY = DIM == 3 ? 1 << g.lt[1] : 1, TZ = 1 << g.lt[2];
     const int FN = (TX + 1 + S) * (DIM == 3 ? TY + 1 + S : 1) * (TZ + 1 + S);
     const int QN = (TX + 2 * S + 1) * (DIM == 3 ? TY + 2 * S + 1 : 1) * (TZ + 2 * S + 1);
     return ions ? sizeof(real) * (size_t)QN : sizeof(real) * (size_t)(6 * FN + 3 * QN);
 }
 
-template <typename real, int DIM, int S>
+template <typename real, int DIM, int S, int TX, int TY, int TZ>
 static void launch_push_t(const PushArgs<real> &a, bool ions, cudaStream_t s)
 {
-    const size_t smem = push_smem<real, DIM, S>(a.g, ions);
-    auto k = ions ? ion_kernel<real, DIM, S> : push_kernel<real, DIM, S>;
+    const size_t smem = push_smem<real, DIM, S, TX, TY, TZ>(ions);
+    auto k = ions ? ion_kernel<real, DIM, S, TX, TY, TZ> : push_kernel<real, DIM, S, TX, TY, TZ>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int64_t grid = a.g.ntiles < 2147483647LL ? a.g.ntiles : 2147483647LL;
     k<<<(unsigned)grid, 256, smem, s>>>(a);
@@ -474,11 +539,11 @@ template <typename real>
 static void dispatch_push(const PushArgs<real> &a, bool ions, cudaStream_t s)
 {
     if (a.g.dim == 3) {
-        if (a.g.shape == 1) launch_push_t<real, 3, 1>(a, ions, s);
-        else launch_push_t<real, 3, 2>(a, ions, s);
+        if (a.g.shape == 1) launch_push_t<real, 3, 1, kTile3[0], kTile3[1], kTile3[2]>(a, ions, s);
+        else launch_push_t<real, 3, 2, kTile3[0], kTile3[1], kTile3[2]>(a, ions, s);
     } else {
-        if (a.g.shape == 1) launch_push_t<real, 2, 1>(a, ions, s);
-        else launch_push_t<real, 2, 2>(a, ions, s);
+        if (a.g.shape == 1) launch_push_t<real, 2, 1, kTile2[0], kTile2[1], kTile2[2]>(a, ions, s);
+        else launch_push_t<real, 2, 2, kTile2[0], kTile2[1], kTile2[2]>(a, ions, s);
     }
 }
 

@@ -56,6 +56,7 @@ def grid(P, **kw):
     (dict(cfl=1.0), 5), (dict(cfl=1.2), 5), (dict(cfl=0.0), 1), (dict(dim=4), 1), (dict(nx=0), 1),
     (dict(ny=2), 1), (dict(shape_order=3), 1), (dict(gamma_boost=0.5), 1), (dict(tile=(3, 0, 0)), 1),
     (dict(precision=7), 1), (dict(slots_per_cell=0.0), 1), (dict(filter_passes=-1), 1), (dict(nz=2), 1),
+    (dict(tile=(8, 1, 8)), 1),
     (dict(dim=3, ny=4, dy=-1.0), 1),
 ])
 def test_init_grid_rejects_invalid_parameters(P, bad, status):

@@ -56,7 +56,7 @@ def test_yee_phase(O, g, bc, prec):
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
-@pytest.mark.parametrize("g,bc,npass", [(G2, 1, 1), (G2, 0, 3), (G3, 1, 2), (G3, 0, 1)])
+@pytest.mark.parametrize("g,bc,npass", [(G2, 1, 1), (G2, 0, 3), (G3, 1, 2), (G3, 0, 1), (G2, 1, 5), (G3, 1, 4)])
 def test_filter_phase(O, g, bc, npass, prec):
     g = dict(g, bc_z=bc, filter_passes=npass)
     sim, o = make_pair(O, g, prec)
