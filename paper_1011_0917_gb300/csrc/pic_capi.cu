@@ -109,9 +109,12 @@ static pic_status fail(pic_ctx *c, pic_status s, const std::string &msg)
             return fail((ctx), PIC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-static int *counts(pic_ctx *c, int sp, int sidx)
+// run lengths per tile of one side of one species: which 0 = bottom run (the
+// tile's own CTA), 1 = top run (appended by others)
+static int *counts(pic_ctx *c, int sp, int sidx, int which)
 {
-    return reinterpret_cast<int *>(c->scratch + c->off_cnt) + ((size_t)(2 * sp + sidx)) * (size_t)c->g.ntiles;
+    return reinterpret_cast<int *>(c->scratch + c->off_cnt) +
+           ((size_t)((2 * sp + sidx) * 2 + which)) * (size_t)c->g.ntiles;
 }
 
 static void *field_ptr(pic_ctx *c, int comp) { return c->fields + (size_t)comp * c->g.ncomp * c->es; }
@@ -268,7 +271,7 @@ extern "C" pic_status pic_init_grid(const pic_grid_params *p, pic_ctx **out)
     }
     size_t o = 0;
     c->off_cnt = o;
-    o += align_up(sizeof(int) * 4 * (size_t)g.ntiles);
+    o += align_up(sizeof(int) * 8 * (size_t)g.ntiles);
     c->off_tmp = o;
     o += align_up((size_t)3 * g.ncomp * c->es);
     c->off_offsets = o;
@@ -360,13 +363,13 @@ static void fill_inject_common(pic_ctx *c, InjectArgs &a)
     a.drift_ions = (p.ions && c->ions_species) ? 1 : 0;
     a.precision = c->p.precision;
     side_raw(c, 0, c->cur[0], a.sp_e);
-    a.cnt_e = counts(c, 0, c->cur[0]);
+    a.hi_e = counts(c, 0, c->cur[0], 1);
     if (a.drift_ions) {
         side_raw(c, 1, c->cur[1], a.sp_i);
-        a.cnt_i = counts(c, 1, c->cur[1]);
+        a.hi_i = counts(c, 1, c->cur[1], 1);
     } else {
         for (int q = 0; q < 9; ++q) a.sp_i[q] = nullptr;
-        a.cnt_i = nullptr;
+        a.hi_i = nullptr;
     }
     a.err = reinterpret_cast<unsigned *>(c->scratch + c->off_err);
 }
@@ -443,7 +446,7 @@ static pic_status bucket_staged(pic_ctx *c, int sp, int64_t n)
     b.src = species_view<real>(c, sp, stage);
     b.dst = species_view<real>(c, sp, c->cur[sp]);
     b.n = n;
-    b.cnt_dst = counts(c, sp, c->cur[sp]);
+    b.dst_hi = counts(c, sp, c->cur[sp], 1);
     b.err = reinterpret_cast<unsigned *>(c->scratch + c->off_err);
     launch_bucket<real>(b, c->stream);
     CUDA_TRY(c, cudaGetLastError());
@@ -543,8 +546,10 @@ static PushArgs<real> push_args(pic_ctx *c, int sp)
     }
     a.in = species_view<real>(c, sp, c->cur[sp]);
     a.out = species_view<real>(c, sp, c->cur[sp] ^ 1);
-    a.cnt_in = counts(c, sp, c->cur[sp]);
-    a.cnt_out = counts(c, sp, c->cur[sp] ^ 1);
+    a.in_lo = counts(c, sp, c->cur[sp], 0);
+    a.in_hi = counts(c, sp, c->cur[sp], 1);
+    a.out_lo = counts(c, sp, c->cur[sp] ^ 1, 0);
+    a.out_hi = counts(c, sp, c->cur[sp] ^ 1, 1);
     a.dtdh[0] = (real)(c->dt / c->hx);
     a.dtdh[1] = (real)(c->dt / c->hy);
     a.dtdh[2] = (real)(c->dt / c->hz);
@@ -732,19 +737,31 @@ extern "C" pic_status pic_get_axis(pic_ctx *c, int comp, void *dst, size_t dst_b
     return PIC_OK;
 }
 
-// live count per tile (clamped to the capacity) and exclusive offsets
+// live count per tile (both runs, clamped to the capacity) and exclusive
+// offsets; PIC_ERR_CAPACITY if the runs of a tile overlap (the bucket overflowed)
 static pic_status tile_offsets(pic_ctx *c, int sp, std::vector<int64_t> &off, int64_t &total)
 {
-    std::vector<int> cnt((size_t)c->g.ntiles);
-    CUDA_TRY(c, cudaMemcpyAsync(cnt.data(), counts(c, sp, c->cur[sp]), sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost,
+    const size_t nt = (size_t)c->g.ntiles;
+    std::vector<int> lo(nt), hi(nt);
+    CUDA_TRY(c, cudaMemcpyAsync(lo.data(), counts(c, sp, c->cur[sp], 0), sizeof(int) * nt, cudaMemcpyDeviceToHost,
+                                c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(hi.data(), counts(c, sp, c->cur[sp], 1), sizeof(int) * nt, cudaMemcpyDeviceToHost,
                                 c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    off.resize(cnt.size());
+    off.resize(nt);
     total = 0;
-    for (size_t t = 0; t < cnt.size(); ++t) {
+    bool overflow = false;
+    for (size_t t = 0; t < nt; ++t) {
         off[t] = total;
-        total += cnt[t] < c->g.cap ? cnt[t] : c->g.cap;
+        const int l = lo[t] < c->g.cap ? lo[t] : c->g.cap;
+        int h = hi[t];
+        if (h > c->g.cap - l) {
+            overflow = true;
+            h = c->g.cap - l;
+        }
+        total += l + h;
     }
+    if (overflow) return fail(c, PIC_ERR_CAPACITY, "a tile bucket overflowed (raise slots_per_cell)");
     return PIC_OK;
 }
 
@@ -761,7 +778,8 @@ static pic_status compact_t(pic_ctx *c, int sp, int64_t &n)
     a.g = c->g;
     a.src = species_view<real>(c, sp, c->cur[sp]);
     a.dst = species_view<real>(c, sp, c->cur[sp] ^ 1);
-    a.cnt = counts(c, sp, c->cur[sp]);
+    a.lo = counts(c, sp, c->cur[sp], 0);
+    a.hi = counts(c, sp, c->cur[sp], 1);
     a.offset = d_off;
     launch_compact<real>(a, c->stream);
     CUDA_TRY(c, cudaGetLastError());
@@ -829,11 +847,11 @@ static pic_status get_rho_t(pic_ctx *c, void *dst, size_t dst_bytes, int dst_is_
     if (dst_bytes < bytes) return fail(c, PIC_ERR_ARG, "destination too small");
     real *rho = (real *)(c->scratch + c->off_tmp);
     CUDA_TRY(c, cudaMemsetAsync(rho, 0, bytes, c->stream));
-    launch_rho<real>(c->g, species_view<real>(c, 0, c->cur[0]), counts(c, 0, c->cur[0]), (real)(-1.0 / c->vol), rho,
-                     c->stream);
+    launch_rho<real>(c->g, species_view<real>(c, 0, c->cur[0]), counts(c, 0, c->cur[0], 0), counts(c, 0, c->cur[0], 1),
+                     (real)(-1.0 / c->vol), rho, c->stream);
     if (c->ions_species)
-        launch_rho<real>(c->g, species_view<real>(c, 1, c->cur[1]), counts(c, 1, c->cur[1]), (real)(1.0 / c->vol), rho,
-                         c->stream);
+        launch_rho<real>(c->g, species_view<real>(c, 1, c->cur[1]), counts(c, 1, c->cur[1], 0),
+                         counts(c, 1, c->cur[1], 1), (real)(1.0 / c->vol), rho, c->stream);
     CUDA_TRY(c, cudaGetLastError());
     CUDA_TRY(c, cudaMemcpyAsync(dst, rho, bytes, kind_out(dst_is_device), c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -875,8 +893,9 @@ static pic_status diagnostics_t(pic_ctx *c, pic_diag *out)
     out->charge = 0;
     const real ion_u[3] = {0, 0, (real)(-(c->gam * c->beta))};
     for (int sp = 0; sp < (c->ions_species ? 2 : 1); ++sp) {
-        launch_particle_sums<real>(c->g, species_view<real>(c, sp, c->cur[sp]), counts(c, sp, c->cur[sp]),
-                                   sp == 0 ? -1.0 : 1.0, ion_u, part, kPartialBlocks, c->stream);
+        launch_particle_sums<real>(c->g, species_view<real>(c, sp, c->cur[sp]), counts(c, sp, c->cur[sp], 0),
+                                   counts(c, sp, c->cur[sp], 1), sp == 0 ? -1.0 : 1.0, ion_u, part, kPartialBlocks,
+                                   c->stream);
         CUDA_TRY(c, cudaGetLastError());
         CUDA_TRY(c, cudaMemcpyAsync(h.data(), part, sizeof(double) * 2 * kPartialBlocks, cudaMemcpyDeviceToHost, c->stream));
         CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -1000,7 +1019,7 @@ static pic_status set_state_t(pic_ctx *c, const unsigned char *src, size_t src_b
     CUDA_TRY(c, cudaMemcpyAsync(c->fields, src + o, c->field_bytes, kind_in(src_is_device), c->stream));
     o += c->field_bytes;
     for (int sp = 0; sp < (c->ions_species ? 2 : 1); ++sp) {
-        CUDA_TRY(c, cudaMemsetAsync(counts(c, sp, 0), 0, sizeof(int) * 2 * (size_t)c->g.ntiles, c->stream));
+        CUDA_TRY(c, cudaMemsetAsync(counts(c, sp, 0, 0), 0, sizeof(int) * 4 * (size_t)c->g.ntiles, c->stream));
         const void *cols[9] = {nullptr};
         for (int a = 0; a < 9; ++a) {
             if (c->side[sp].off[a] == SIZE_MAX) continue;

@@ -134,18 +134,22 @@ __global__ void inject_kernel(InjectArgs a)
                 }
             }
         }
-        const int re = reserve_slot(a.cnt_e, dest);
+        // appended to the top run of the destination bucket
+        const int re = reserve_slot(a.hi_e, dest);
         int ri = 0;
-        if (a.drift_ions) ri = reserve_slot(a.cnt_i, dest);
+        if (a.drift_ions) ri = reserve_slot(a.hi_i, dest);
         if (dest < 0) continue;
         // every reserved slot below the capacity is written, so a bucket never
         // holds a stale entry; an overflow drops the particle and is reported
         const int32_t cell = pack_cell(a.g, ci, cj, ck);
         const real uz = (real)a.uz0;
-        if (re < a.g.cap) store<real>(a.sp_e, dest * (int64_t)a.g.cap + re, ox, oy, oz, wr, uz, cell, L, true, dim3);
+        if (re < a.g.cap)
+            store<real>(a.sp_e, dest * (int64_t)a.g.cap + (a.g.cap - 1 - re), ox, oy, oz, wr, uz, cell, L, true, dim3);
         else atomicOr(a.err, ERR_CAPACITY);
         if (a.drift_ions) {
-            if (ri < a.g.cap) store<real>(a.sp_i, dest * (int64_t)a.g.cap + ri, ox, oy, oz, wr, uz, cell, L, false, dim3);
+            if (ri < a.g.cap)
+                store<real>(a.sp_i, dest * (int64_t)a.g.cap + (a.g.cap - 1 - ri), ox, oy, oz, wr, uz, cell, L, false,
+                            dim3);
             else atomicOr(a.err, ERR_CAPACITY);
         }
     }

@@ -8,9 +8,14 @@
 //            Bz (i+1/2, j+1/2, k); J like E.
 //   species: per species two "sides" (double buffer).  A side is a structure
 //            of arrays with `slots` entries per attribute; tile t owns slots
-//            [t*cap, t*cap + count[t]).  A particle is an int32 packed cell
-//            index plus its offsets in [0,1) inside that cell (real), its
-//            weight and (electrons) u = gamma v.
+//            [t*cap, (t+1)*cap) and keeps its particles in two runs: a bottom
+//            run [0, lo) that the tile's own CTA writes (particles that stayed
+//            in the tile, counted in shared memory) and a top run
+//            [cap - hi, cap) that others append to with global atomics
+//            (particles that arrived from a neighbour, were loaded or were
+//            injected).  A particle is an int32 packed cell index plus its
+//            offsets in [0,1) inside that cell (real), its weight and
+//            (electrons) u = gamma v.
 //   scratch: per-side tile counters, the filter ping-pong buffer, per-tile
 //            offsets for compaction, reduction partials and the error word.
 #pragma once
@@ -99,6 +104,26 @@ __device__ __forceinline__ int reserve_slot(int *cnt, int64_t dest)
     return base + rank;
 }
 
+// slot of the p-th live particle of tile t (bottom run first, then top run)
+__device__ __forceinline__ int64_t bucket_slot(int64_t t, int cap, int n_lo, int n_hi, int p)
+{
+    return t * (int64_t)cap + (p < n_lo ? p : cap - n_hi + (p - n_lo));
+}
+
+// run lengths of tile t; runs that overlap mean the bucket overflowed: that is
+// reported and the runs are clamped so that no slot is read twice
+__device__ __forceinline__ void bucket_counts(const int *lo, const int *hi, int64_t t, int cap, int &n_lo,
+                                              int &n_hi, unsigned *err)
+{
+    n_lo = lo[t];
+    n_hi = hi[t];
+    if (n_lo > cap) n_lo = cap;
+    if (n_hi > cap - n_lo) {
+        if (err) atomicOr(err, ERR_CAPACITY);
+        n_hi = cap - n_lo;
+    }
+}
+
 // ---------------------------------------------------------------- shapes
 
 // 1D B-spline weights of order S at a position p measured from node 0 of a
@@ -168,7 +193,7 @@ struct PushArgs {
     const real *B[3];
     real *J[3];
     Species<real> in, out;
-    int *cnt_in, *cnt_out;
+    int *in_lo, *in_hi, *out_lo, *out_hi;   // run lengths per tile (see the layout note)
     real dtdh[3];       // dt / h_d
     real eps;           // pi (q/m) dt
     real jfac[3];       // -q h_d / (dt V): multiplied by w and the running sum
@@ -182,7 +207,7 @@ struct BucketArgs {      // re-bucket a flat list into tiles
     Geom g;
     Species<real> src, dst;
     int64_t n;
-    int *cnt_dst;
+    int *dst_hi;         // top-run lengths of the destination side
     unsigned *err;
 };
 
@@ -190,7 +215,7 @@ template <typename real>
 struct CompactArgs {     // copy tiles into a flat list
     Geom g;
     Species<real> src, dst;
-    const int *cnt;
+    const int *lo, *hi;
     const int64_t *offset;
 };
 
@@ -209,7 +234,7 @@ struct InjectArgs {      // lattice load / boosted injection, FP64
     int precision;      // 0 float, 1 double
     void *sp_e[9];      // ox oy oz w ux uy uz cell id of the electron side
     void *sp_i[9];      // same for the ion side (ux..uz unused)
-    int *cnt_e, *cnt_i;
+    int *hi_e, *hi_i;    // top-run lengths of the electron / ion sides
     unsigned *err;
 };
 
@@ -219,10 +244,10 @@ template <typename real> void launch_ions(const PushArgs<real> &a, cudaStream_t 
 template <typename real> void launch_bucket(const BucketArgs<real> &a, cudaStream_t s);
 template <typename real> void launch_compact(const CompactArgs<real> &a, cudaStream_t s);
 template <typename real>
-void launch_rho(const Geom &g, const Species<real> &sp, const int *cnt, real qfac, real *rho,
+void launch_rho(const Geom &g, const Species<real> &sp, const int *lo, const int *hi, real qfac, real *rho,
                 cudaStream_t s);
 template <typename real>
-void launch_particle_sums(const Geom &g, const Species<real> &sp, const int *cnt, double q,
+void launch_particle_sums(const Geom &g, const Species<real> &sp, const int *lo, const int *hi, double q,
                           const real ion_u[3], double *partials, int nblocks, cudaStream_t s);
 void launch_inject(const InjectArgs &a, cudaStream_t s);
 

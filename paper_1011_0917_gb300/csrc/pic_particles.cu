@@ -51,10 +51,6 @@ __device__ __forceinline__ int wrap1(int i, int n)
     return i < 0 ? i + n : (i >= n ? i - n : i);
 }
 
-// Stage `ncomp` field components of the box [lo - L, lo - L + F) (per axis)
-// into shared memory, one warp per row of FX nodes along x (coalesced loads,
-// one index decomposition per row).  Nodes outside the valid z range of a
-// component (absorbing z) are zero; x and y wrap.
 template <typename real>
 struct Ptr6 {
     const real *p0, *p1, *p2, *p3, *p4, *p5;
@@ -70,73 +66,75 @@ struct Ptr3 {
     __device__ __forceinline__ real *operator[](int c) const { return c == 0 ? p0 : c == 1 ? p1 : p2; }
 };
 
-template <typename real, int DIM>
-__device__ __forceinline__ void stage_rows(const Geom &g, const Ptr6<real> src, unsigned half_z, int ncomp,
-                                           real *dst, int FX, int FY, int FZ, int lox, int loy, int loz, int L)
+// Stage NC field components of the box [lo - L, lo - L + F) (per axis) into
+// shared memory.  Element-wise over all threads with compile-time extents, so
+// the index decomposition is a few multiply-shifts; consecutive threads read
+// consecutive x.  Nodes outside the valid z range of a component (absorbing z)
+// are zero; x and y wrap.
+template <typename real, int DIM, int NC, int FX, int FY, int FZ, int L>
+__device__ __forceinline__ void stage_tile(const Geom &g, const Ptr6<real> src, unsigned half_z, real *dst, int lox,
+                                           int loy, int loz)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int per_c = FY * FZ;
+    constexpr int FN = FX * FY * FZ;
     const bool tiny = g.nx < FX || (DIM == 3 && g.ny < FY);
-    for (int row = warp; row < ncomp * per_c; row += nwarps) {
-        const int c = row / per_c, rr = row - c * per_c;
-        const int lz = rr / FY, ly = rr - lz * FY;
+    for (int q = threadIdx.x; q < NC * FN; q += blockDim.x) {
+        const int c = q / FN, r = q - c * FN;
+        const int lz = r / (FX * FY), r2 = r - lz * (FX * FY);
+        const int ly = r2 / FX, lx = r2 - ly * FX;
         int gk = loz - L + lz;
         bool ok = true;
         if (g.bc_z == 0) gk = wrapi(gk, g.nz);
         else ok = gk >= 0 && gk <= zmax_of(g, (half_z >> c) & 1u);
+        const int gi = tiny ? wrapi(lox - L + lx, g.nx) : wrap1(lox - L + lx, g.nx);
         const int gj = DIM == 3 ? (tiny ? wrapi(loy - L + ly, g.ny) : wrap1(loy - L + ly, g.ny)) : 0;
-        const real *row_src = src[c] + ((int64_t)(ok ? gk : 0) * g.ny + gj) * g.nx;
-        real *row_dst = dst + (int64_t)c * FX * per_c + (lz * FY + ly) * FX;
-        for (int lx = lane; lx < FX; lx += 32) {
-            const int gi = tiny ? wrapi(lox - L + lx, g.nx) : wrap1(lox - L + lx, g.nx);
-            row_dst[lx] = ok ? row_src[gi] : real(0);
-        }
+        dst[q] = ok ? src[c][fidx(g, gi, gj, gk)] : real(0);
     }
 }
 
-// Add `ncomp` shared-memory tiles (box [lo - L, lo - L + Q) per axis) to the
-// global arrays: one warp per row, non-zero nodes only, periodic x and y,
+// Add NC shared-memory tiles (box [lo - L, lo - L + Q) per axis) to the global
+// arrays, element-wise over all threads: non-zero nodes only, periodic x and y,
 // nodes outside a component's valid z range dropped (absorbing z).
-template <typename real, int DIM>
-__device__ __forceinline__ void flush_rows(const Geom &g, const Ptr3<real> dstJ, unsigned half_z, int ncomp,
-                                           const real *src, int QX, int QY, int QZ, int lox, int loy, int loz, int L)
+template <typename real, int DIM, int NC, int QX, int QY, int QZ, int L>
+__device__ __forceinline__ void flush_tile(const Geom &g, const Ptr3<real> dstJ, unsigned half_z, const real *src,
+                                           int lox, int loy, int loz)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int per_c = QY * QZ;
+    constexpr int QN = QX * QY * QZ;
     const bool tiny = g.nx < QX || (DIM == 3 && g.ny < QY);
-    for (int row = warp; row < ncomp * per_c; row += nwarps) {
-        const int c = row / per_c, rr = row - c * per_c;
-        const int lz = rr / QY, ly = rr - lz * QY;
+    for (int q = threadIdx.x; q < NC * QN; q += blockDim.x) {
+        const real v = src[q];
+        if (v == real(0)) continue;
+        const int c = q / QN, r = q - c * QN;
+        const int lz = r / (QX * QY), r2 = r - lz * (QX * QY);
+        const int ly = r2 / QX, lx = r2 - ly * QX;
         int gk = loz - L + lz;
         if (g.bc_z == 0) gk = wrapi(gk, g.nz);
         else if (gk < 0 || gk > zmax_of(g, (half_z >> c) & 1u)) continue;
+        const int gi = tiny ? wrapi(lox - L + lx, g.nx) : wrap1(lox - L + lx, g.nx);
         const int gj = DIM == 3 ? (tiny ? wrapi(loy - L + ly, g.ny) : wrap1(loy - L + ly, g.ny)) : 0;
-        real *row_dst = dstJ[c] + ((int64_t)gk * g.ny + gj) * g.nx;
-        const real *row_src = src + (int64_t)c * QX * per_c + (lz * QY + ly) * QX;
-        for (int lx = lane; lx < QX; lx += 32) {
-            const real v = row_src[lx];
-            if (v != real(0)) {
-                const int gi = tiny ? wrapi(lox - L + lx, g.nx) : wrap1(lox - L + lx, g.nx);
-                atomicAdd(row_dst + gi, v);
-            }
-        }
+        atomicAdd(dstJ[c] + fidx(g, gi, gj, gk), v);
     }
 }
 
-// Slot in the bucket of `dest` for every lane (dest < 0: none).  Fast path:
-// when every valid lane of the warp stays in tile `own`, one atomic.
-__device__ __forceinline__ int reserve_slot_own(int *cnt, int64_t dest, int64_t own)
+// Output slot of every lane's particle (dest < 0: none).  Particles that stay
+// in tile `own` take the next slots of its bottom run from a shared-memory
+// counter (one shared atomic per warp); the others take slots of their
+// destination's top run through global atomics (one per destination tile in
+// the warp).  Returns the slot index inside the destination bucket, or -1 when
+// the bucket is full.
+__device__ __forceinline__ int output_slot(int *s_stay, int *out_hi, int64_t dest, int64_t own, int cap)
 {
     const unsigned lane = threadIdx.x & 31u;
-    const unsigned valid = __ballot_sync(0xffffffffu, dest >= 0);
     const unsigned stay = __ballot_sync(0xffffffffu, dest == own);
-    if (stay == valid) {
-        int base = 0;
-        if (lane == 0 && valid) base = atomicAdd(&cnt[own], __popc(valid));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        return base + __popc(valid & ((1u << lane) - 1u));
+    int base = 0;
+    if (lane == 0 && stay) base = atomicAdd(s_stay, __popc(stay));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const bool leave = dest >= 0 && dest != own;
+    const int r = __any_sync(0xffffffffu, leave) ? reserve_slot(out_hi, leave ? dest : -1) : 0;
+    if (dest == own) {
+        const int slot = base + __popc(stay & ((1u << lane) - 1u));
+        return slot < cap ? slot : -1;
     }
-    return reserve_slot(cnt, dest);
+    return (leave && r < cap) ? cap - 1 - r : -1;
 }
 
 // ---------------------------------------------------------------- gather
@@ -173,10 +171,140 @@ __device__ __forceinline__ real gather_comp(const real *F, int FX, int FY, int i
     return sum;
 }
 
+// --------------------------------------------------------- Esirkepov
+
+// Esirkepov window along one axis as esirk_axis, plus whether the particle's
+// support moved to another first node (the window then needs S+2 nodes).
+template <int S, typename real>
+__device__ __forceinline__ int esirk_axis_c(real x0, real x1, real S0[S + 2], real DS[S + 2], bool &crossed)
+{
+    real w0[S + 1], w1[S + 1];
+    const int b0 = spline_weights<S>(x0, w0);
+    const int b1 = spline_weights<S>(x1, w1);
+    const int anchor = b0 < b1 ? b0 : b1;
+    const bool s0 = b0 != anchor, s1 = b1 != anchor;
+    crossed = b0 != b1;
+#pragma unroll
+    for (int q = 0; q < S + 2; ++q) {
+        const real v0 = s0 ? (q >= 1 ? w0[q - 1 < S ? q - 1 : S] : real(0)) : (q <= S ? w0[q <= S ? q : S] : real(0));
+        const real v1 = s1 ? (q >= 1 ? w1[q - 1 < S ? q - 1 : S] : real(0)) : (q <= S ? w1[q <= S ? q : S] : real(0));
+        S0[q] = v0;
+        DS[q] = v1 - v0;
+    }
+    return anchor;
+}
+
+// Current of one particle into the shared J tile.  Along an axis the window
+// has W nodes: S+1 when no lane of the warp moved its support to another first
+// node along that axis (the last node is then outside both supports), else
+// S+2.  The running sum along an axis is taken over DS first:
+//   Jx(a,b,c) = fx * (sum_{a'<=a} DSx[a']) * T_yz(b,c),
+//   T_yz = S0y (S0z + DSz/2) + DSy (S0z/2 + DSz/3)        (and cyclically),
+// which is Esirkepov's decomposition rearranged; the last running sum of a
+// window is zero and is not added.  In 2D3V the out-of-plane current is the
+// path average of the shape times q w vy / V.
+template <typename real, int DIM, int S, int QX, int QY, int QN, int WX, int WY, int WZ>
+__device__ __forceinline__ void deposit_w(real *sJ, const real *S0x, const real *DSx, const real *S0y,
+                                          const real *DSy, const real *S0z, const real *DSz, int ax, int ay, int az,
+                                          real fx, real fy, real fz, real fyv)
+{
+    constexpr real half = real(0.5), third = real(1) / real(3);
+    real *Jx = sJ, *Jy = sJ + QN, *Jz = sJ + 2 * QN;
+    real Px[WX], Pz[WZ];
+    real acc = 0;
+#pragma unroll
+    for (int q = 0; q < WX; ++q) { acc += DSx[q]; Px[q] = fx * acc; }
+    acc = 0;
+#pragma unroll
+    for (int c = 0; c < WZ; ++c) { acc += DSz[c]; Pz[c] = fz * acc; }
+    if (DIM == 3) {
+        real Py[WY];
+        acc = 0;
+#pragma unroll
+        for (int b = 0; b < WY; ++b) { acc += DSy[b]; Py[b] = fy * acc; }
+#pragma unroll
+        for (int c = 0; c < WZ; ++c) {
+            const real za = S0z[c] + half * DSz[c], zb = half * S0z[c] + third * DSz[c];
+#pragma unroll
+            for (int b = 0; b < WY; ++b) {
+                const real tyz = S0y[b] * za + DSy[b] * zb;
+                real *row = Jx + ((az + c) * QY + (ay + b)) * QX + ax;
+#pragma unroll
+                for (int q = 0; q < WX - 1; ++q) sh_add(row + q, Px[q] * tyz);
+            }
+#pragma unroll
+            for (int q = 0; q < WX; ++q) {
+                const real tzx = S0z[c] * (S0x[q] + half * DSx[q]) + DSz[c] * (half * S0x[q] + third * DSx[q]);
+                real *col = Jy + ((az + c) * QY + ay) * QX + ax + q;
+#pragma unroll
+                for (int b = 0; b < WY - 1; ++b) sh_add(col + b * QX, Py[b] * tzx);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < WY; ++b) {
+            const real ya = S0y[b] + half * DSy[b], yb = half * S0y[b] + third * DSy[b];
+#pragma unroll
+            for (int q = 0; q < WX; ++q) {
+                const real txy = S0x[q] * ya + DSx[q] * yb;
+                real *col = Jz + (az * QY + (ay + b)) * QX + ax + q;
+#pragma unroll
+                for (int c = 0; c < WZ - 1; ++c) sh_add(col + c * QX * QY, Pz[c] * txy);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < WZ; ++c) {
+            const real za = S0z[c] + half * DSz[c], zb = half * S0z[c] + third * DSz[c];
+            real *row = Jx + (az + c) * QX + ax;
+#pragma unroll
+            for (int q = 0; q < WX - 1; ++q) sh_add(row + q, Px[q] * za);
+#pragma unroll
+            for (int q = 0; q < WX; ++q) sh_add(Jy + (az + c) * QX + ax + q, fyv * (S0x[q] * za + DSx[q] * zb));
+        }
+#pragma unroll
+        for (int q = 0; q < WX; ++q) {
+            const real xa = S0x[q] + half * DSx[q];
+#pragma unroll
+            for (int c = 0; c < WZ - 1; ++c) sh_add(Jz + (az + c) * QX + ax + q, Pz[c] * xa);
+        }
+    }
+}
+
+// picks the window lengths for the warp: bit 2 x, bit 1 y, bit 0 z crossed
+template <typename real, int DIM, int S, int QX, int QY, int QN>
+__device__ __forceinline__ void deposit_sel(unsigned sel, real *sJ, const real *S0x, const real *DSx, const real *S0y,
+                                            const real *DSy, const real *S0z, const real *DSz, int ax, int ay, int az,
+                                            real fx, real fy, real fz, real fyv)
+{
+    constexpr int A = S + 1, B = S + 2;
+#define PIC_DEP(wx, wy, wz) \
+    deposit_w<real, DIM, S, QX, QY, QN, wx, wy, wz>(sJ, S0x, DSx, S0y, DSy, S0z, DSz, ax, ay, az, fx, fy, fz, fyv)
+    if (DIM == 3) {
+        switch (sel) {
+        case 0: PIC_DEP(A, A, A); break;
+        case 1: PIC_DEP(A, A, B); break;
+        case 2: PIC_DEP(A, B, A); break;
+        case 3: PIC_DEP(A, B, B); break;
+        case 4: PIC_DEP(B, A, A); break;
+        case 5: PIC_DEP(B, A, B); break;
+        case 6: PIC_DEP(B, B, A); break;
+        default: PIC_DEP(B, B, B); break;
+        }
+    } else {
+        switch (sel & 5u) {
+        case 0: PIC_DEP(A, 1, A); break;
+        case 1: PIC_DEP(A, 1, B); break;
+        case 4: PIC_DEP(B, 1, A); break;
+        default: PIC_DEP(B, 1, B); break;
+        }
+    }
+#undef PIC_DEP
+}
+
 // ------------------------------------------------------------ push kernel
 
 template <typename real, int DIM, int S, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(256) push_kernel(PushArgs<real> a)
+__global__ void __launch_bounds__(256, 4) push_kernel(PushArgs<real> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Geom &g = a.g;
@@ -189,9 +317,12 @@ __global__ void __launch_bounds__(256) push_kernel(PushArgs<real> a)
     constexpr int FN = FX * FY * FZ, QN = QX * QY * QZ;
     real *sF = reinterpret_cast<real *>(smem_raw);
     real *sJ = sF + 6 * FN;
+    __shared__ int s_stay;
 
     for (int64_t t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
-        const int n = min(a.cnt_in[t], g.cap);
+        int n_lo, n_hi;
+        bucket_counts(a.in_lo, a.in_hi, t, g.cap, n_lo, n_hi, a.err);
+        const int n = n_lo + n_hi;
         if (n == 0) continue;  // uniform over the CTA
         const int tix = (int)(t % g.nt[0]);
         const int tiy = (int)((t / g.nt[0]) % g.nt[1]);
@@ -199,185 +330,121 @@ __global__ void __launch_bounds__(256) push_kernel(PushArgs<real> a)
         const int lox = tix << g.lt[0], loy = tiy << g.lt[1], loz = tiz << g.lt[2];
 
         __syncthreads();  // previous tile finished with shared memory
+        if (threadIdx.x == 0) s_stay = 0;
         // Ez, Bx, By live on half-integer z (bits 2, 3, 4)
-        stage_rows<real, DIM>(g, Ptr6<real>{a.E[0], a.E[1], a.E[2], a.B[0], a.B[1], a.B[2]}, 0x1Cu, 6, sF, FX, FY,
-                              FZ, lox, loy, loz, FL);
+        stage_tile<real, DIM, 6, FX, FY, FZ, FL>(g, Ptr6<real>{a.E[0], a.E[1], a.E[2], a.B[0], a.B[1], a.B[2]},
+                                                 0x1Cu, sF, lox, loy, loz);
         for (int q = threadIdx.x; q < 3 * QN; q += blockDim.x) sJ[q] = 0;
         __syncthreads();
 
-        const int64_t slot0 = t * (int64_t)g.cap;
         for (int base = 0; base < n; base += blockDim.x) {
             const int p = base + threadIdx.x;
             bool valid = p < n;
-            int64_t dest = -1;
             real ox = 0, oy = 0, oz = 0, w = 0, ux = 0, uy = 0, uz = 0;
-            int ni = 0, nj = 0, nk = 0;
+            int ci = 0, cj = 0, ck = 0, li = 0, lj = 0, lk = 0;
             int64_t pid = 0;
+            // ---- load
             if (valid) {
-                const int64_t s = slot0 + p;
-                int ci, cj, ck;
+                const int64_t s = bucket_slot(t, g.cap, n_lo, n_hi, p);
                 unpack_cell(g, a.in.cell[s], ci, cj, ck);
-                const int li = ci - lox, lj = cj - loy, lk = ck - loz;
+                li = ci - lox;
+                lj = cj - loy;
+                lk = ck - loz;
                 if (li < 0 || li >= TX || lj < 0 || lj >= TY || lk < 0 || lk >= TZ) {
                     atomicOr(a.err, ERR_TILE);
                     valid = false;
                 } else {
                     ox = a.in.ox[s];
-                    oy = DIM == 3 ? a.in.oy[s] : real(0);
+                    if (DIM == 3) oy = a.in.oy[s];
                     oz = a.in.oz[s];
                     w = a.in.w[s];
                     ux = a.in.ux[s];
                     uy = a.in.uy[s];
                     uz = a.in.uz[s];
                     if (a.in.id) pid = a.in.id[s];
-
-                    // gather: unstaggered (u) and half-shifted (h) weights per axis
-                    real wxu[S + 1], wxh[S + 1], wyu[S + 1], wyh[S + 1], wzu[S + 1], wzh[S + 1];
-                    const int bxu = spline_weights<S>(ox, wxu) + li + FL;
-                    const int bxh = spline_weights<S>(ox - real(0.5), wxh) + li + FL;
-                    const int bzu = spline_weights<S>(oz, wzu) + lk + FL;
-                    const int bzh = spline_weights<S>(oz - real(0.5), wzh) + lk + FL;
-                    int byu = 0, byh = 0;
-                    if (DIM == 3) {
-                        byu = spline_weights<S>(oy, wyu) + lj + FL;
-                        byh = spline_weights<S>(oy - real(0.5), wyh) + lj + FL;
-                    } else {
-#pragma unroll
-                        for (int q = 0; q <= S; ++q) wyu[q] = wyh[q] = real(q == 0);
-                    }
-                    real ex, ey, ez, bx, by, bz;
-                    ex = gather_comp<DIM, S>(sF + 0 * FN, FX, FY, bxh, byu, bzu, wxh, wyu, wzu);
-                    ey = gather_comp<DIM, S>(sF + 1 * FN, FX, FY, bxu, byh, bzu, wxu, wyh, wzu);
-                    ez = gather_comp<DIM, S>(sF + 2 * FN, FX, FY, bxu, byu, bzh, wxu, wyu, wzh);
-                    bx = gather_comp<DIM, S>(sF + 3 * FN, FX, FY, bxu, byh, bzh, wxu, wyh, wzh);
-                    by = gather_comp<DIM, S>(sF + 4 * FN, FX, FY, bxh, byu, bzh, wxh, wyu, wzh);
-                    bz = gather_comp<DIM, S>(sF + 5 * FN, FX, FY, bxh, byh, bzu, wxh, wyh, wzu);
-
-                    boris(ux, uy, uz, ex, ey, ez, bx, by, bz, a.eps);
-                    const real ig = inv_gamma(ux, uy, uz);
-                    const real vy = uy * ig;
-                    const real dx = ux * ig * a.dtdh[0];
-                    const real dy = DIM == 3 ? uy * ig * a.dtdh[1] : real(0);
-                    const real dz = uz * ig * a.dtdh[2];
-                    if (!(fabs(dx) < real(1) && fabs(dy) < real(1) && fabs(dz) < real(1))) {
-                        atomicOr(a.err, (dx == dx && dy == dy && dz == dz) ? ERR_CFL : ERR_NAN);
-                        valid = false;
-                    } else {
-                        const real x1 = ox + dx, y1 = oy + dy, z1 = oz + dz;
-                        // Esirkepov deposit into the shared J tile
-                        real S0x[S + 2], DSx[S + 2], S0y[S + 2], DSy[S + 2], S0z[S + 2], DSz[S + 2];
-                        const int ax = esirk_axis<S>(ox, x1, S0x, DSx) + li + JL;
-                        const int az = esirk_axis<S>(oz, z1, S0z, DSz) + lk + JL;
-                        const real fx = a.jfac[0] * w, fz = a.jfac[2] * w;
-                        real *Jx = sJ, *Jy = sJ + QN, *Jz = sJ + 2 * QN;
-                        constexpr real third = real(1) / real(3);
-                        if (DIM == 3) {
-                            const int ay = esirk_axis<S>(oy, y1, S0y, DSy) + lj + JL;
-                            const real fy = a.jfac[1] * w;
-#pragma unroll
-                            for (int c = 0; c < S + 2; ++c) {
-#pragma unroll
-                                for (int b = 0; b < S + 2; ++b) {
-                                    const real tyz = S0y[b] * (S0z[c] + real(0.5) * DSz[c]) +
-                                                     DSy[b] * (real(0.5) * S0z[c] + third * DSz[c]);
-                                    real acc = 0;
-                                    real *row = Jx + ((az + c) * QY + (ay + b)) * QX + ax;
-#pragma unroll
-                                    for (int q = 0; q < S + 1; ++q) {
-                                        acc += DSx[q] * tyz;
-                                        sh_add(row + q, fx * acc);
-                                    }
-                                }
-                            }
-#pragma unroll
-                            for (int c = 0; c < S + 2; ++c) {
-#pragma unroll
-                                for (int q = 0; q < S + 2; ++q) {
-                                    const real tzx = S0z[c] * (S0x[q] + real(0.5) * DSx[q]) +
-                                                     DSz[c] * (real(0.5) * S0x[q] + third * DSx[q]);
-                                    real acc = 0;
-#pragma unroll
-                                    for (int b = 0; b < S + 1; ++b) {
-                                        acc += DSy[b] * tzx;
-                                        sh_add(Jy + ((az + c) * QY + (ay + b)) * QX + ax + q, fy * acc);
-                                    }
-                                }
-                            }
-#pragma unroll
-                            for (int b = 0; b < S + 2; ++b) {
-#pragma unroll
-                                for (int q = 0; q < S + 2; ++q) {
-                                    const real txy = S0x[q] * (S0y[b] + real(0.5) * DSy[b]) +
-                                                     DSx[q] * (real(0.5) * S0y[b] + third * DSy[b]);
-                                    real acc = 0;
-#pragma unroll
-                                    for (int c = 0; c < S + 1; ++c) {
-                                        acc += DSz[c] * txy;
-                                        sh_add(Jz + ((az + c) * QY + (ay + b)) * QX + ax + q, fz * acc);
-                                    }
-                                }
-                            }
-                        } else {
-                            const real fyv = a.jyfac * w * vy;
-#pragma unroll
-                            for (int c = 0; c < S + 2; ++c) {
-                                const real tz = S0z[c] + real(0.5) * DSz[c];
-                                real acc = 0;
-                                real *row = Jx + (az + c) * QX + ax;
-#pragma unroll
-                                for (int q = 0; q < S + 1; ++q) {
-                                    acc += DSx[q] * tz;
-                                    sh_add(row + q, fx * acc);
-                                }
-                            }
-#pragma unroll
-                            for (int q = 0; q < S + 2; ++q) {
-                                const real tx = S0x[q] + real(0.5) * DSx[q];
-                                real acc = 0;
-#pragma unroll
-                                for (int c = 0; c < S + 1; ++c) {
-                                    acc += DSz[c] * tx;
-                                    sh_add(Jz + (az + c) * QX + ax + q, fz * acc);
-                                }
-                            }
-#pragma unroll
-                            for (int c = 0; c < S + 2; ++c) {
-#pragma unroll
-                                for (int q = 0; q < S + 2; ++q) {
-                                    const real wgt = S0x[q] * (S0z[c] + real(0.5) * DSz[c]) +
-                                                     DSx[q] * (real(0.5) * S0z[c] + third * DSz[c]);
-                                    sh_add(Jy + (az + c) * QX + ax + q, fyv * wgt);
-                                }
-                            }
-                        }
-                        // new cell and offsets; an offset that rounds to 1 moves on
-                        int sx = (int)floor(x1), sy = DIM == 3 ? (int)floor(y1) : 0, sz = (int)floor(z1);
-                        ox = x1 - real(sx);
-                        if (ox >= real(1)) { sx += 1; ox = 0; }
-                        if (DIM == 3) {
-                            oy = y1 - real(sy);
-                            if (oy >= real(1)) { sy += 1; oy = 0; }
-                        }
-                        oz = z1 - real(sz);
-                        if (oz >= real(1)) { sz += 1; oz = 0; }
-                        ni = ci + sx;
-                        if (ni < 0) ni += g.nx; else if (ni >= g.nx) ni -= g.nx;
-                        nj = cj + sy;
-                        if (DIM == 3) { if (nj < 0) nj += g.ny; else if (nj >= g.ny) nj -= g.ny; }
-                        nk = ck + sz;
-                        bool alive = true;
-                        if (g.bc_z == 0) {
-                            if (nk < 0) nk += g.nz; else if (nk >= g.nz) nk -= g.nz;
-                        } else if (nk < 0 || nk >= g.nz) {
-                            alive = false;
-                        }
-                        if (alive) dest = tile_of(g, ni, nj, nk);
-                    }
                 }
             }
-            const int r = reserve_slot_own(a.cnt_out, dest, t);
+            // ---- gather E^n, B^n at x^n, Boris, move
+            real x1 = 0, y1 = 0, z1 = 0, vy = 0;
+            if (valid) {
+                real wxu[S + 1], wxh[S + 1], wyu[S + 1], wyh[S + 1], wzu[S + 1], wzh[S + 1];
+                const int bxu = spline_weights<S>(ox, wxu) + li + FL;
+                const int bxh = spline_weights<S>(ox - real(0.5), wxh) + li + FL;
+                const int bzu = spline_weights<S>(oz, wzu) + lk + FL;
+                const int bzh = spline_weights<S>(oz - real(0.5), wzh) + lk + FL;
+                int byu = 0, byh = 0;
+                if (DIM == 3) {
+                    byu = spline_weights<S>(oy, wyu) + lj + FL;
+                    byh = spline_weights<S>(oy - real(0.5), wyh) + lj + FL;
+                } else {
+#pragma unroll
+                    for (int q = 0; q <= S; ++q) wyu[q] = wyh[q] = real(q == 0);
+                }
+                const real ex = gather_comp<DIM, S>(sF + 0 * FN, FX, FY, bxh, byu, bzu, wxh, wyu, wzu);
+                const real ey = gather_comp<DIM, S>(sF + 1 * FN, FX, FY, bxu, byh, bzu, wxu, wyh, wzu);
+                const real ez = gather_comp<DIM, S>(sF + 2 * FN, FX, FY, bxu, byu, bzh, wxu, wyu, wzh);
+                const real bx = gather_comp<DIM, S>(sF + 3 * FN, FX, FY, bxu, byh, bzh, wxu, wyh, wzh);
+                const real by = gather_comp<DIM, S>(sF + 4 * FN, FX, FY, bxh, byu, bzh, wxh, wyu, wzh);
+                const real bz = gather_comp<DIM, S>(sF + 5 * FN, FX, FY, bxh, byh, bzu, wxh, wyh, wzu);
+                boris(ux, uy, uz, ex, ey, ez, bx, by, bz, a.eps);
+                const real ig = inv_gamma(ux, uy, uz);
+                vy = uy * ig;
+                const real dx = ux * ig * a.dtdh[0];
+                const real dy = DIM == 3 ? uy * ig * a.dtdh[1] : real(0);
+                const real dz = uz * ig * a.dtdh[2];
+                if (!(fabs(dx) < real(1) && fabs(dy) < real(1) && fabs(dz) < real(1))) {
+                    atomicOr(a.err, (dx == dx && dy == dy && dz == dz) ? ERR_CFL : ERR_NAN);
+                    valid = false;
+                } else {
+                    x1 = ox + dx;
+                    y1 = oy + dy;
+                    z1 = oz + dz;
+                }
+            }
+            // ---- Esirkepov windows; the warp agrees on their lengths
+            real S0x[S + 2], DSx[S + 2], S0y[S + 2], DSy[S + 2], S0z[S + 2], DSz[S + 2];
+            int ax = 0, ay = 0, az = 0;
+            bool cx = false, cy = false, cz = false;
+            if (valid) {
+                ax = esirk_axis_c<S>(ox, x1, S0x, DSx, cx) + li + JL;
+                az = esirk_axis_c<S>(oz, z1, S0z, DSz, cz) + lk + JL;
+                if (DIM == 3) ay = esirk_axis_c<S>(oy, y1, S0y, DSy, cy) + lj + JL;
+            }
+            const unsigned sel = (__any_sync(0xffffffffu, cx) ? 4u : 0u) | (__any_sync(0xffffffffu, cy) ? 2u : 0u) |
+                                 (__any_sync(0xffffffffu, cz) ? 1u : 0u);
+            int64_t dest = -1;
+            int ni = 0, nj = 0, nk = 0;
+            if (valid) {
+                deposit_sel<real, DIM, S, QX, QY, QN>(sel, sJ, S0x, DSx, S0y, DSy, S0z, DSz, ax, ay, az,
+                                                      a.jfac[0] * w, a.jfac[1] * w, a.jfac[2] * w,
+                                                      a.jyfac * w * vy);
+                // new cell and offsets; an offset that rounds to 1 moves on
+                int sx = (int)floor(x1), sy = DIM == 3 ? (int)floor(y1) : 0, sz = (int)floor(z1);
+                ox = x1 - real(sx);
+                if (ox >= real(1)) { sx += 1; ox = 0; }
+                if (DIM == 3) {
+                    oy = y1 - real(sy);
+                    if (oy >= real(1)) { sy += 1; oy = 0; }
+                }
+                oz = z1 - real(sz);
+                if (oz >= real(1)) { sz += 1; oz = 0; }
+                ni = ci + sx;
+                if (ni < 0) ni += g.nx; else if (ni >= g.nx) ni -= g.nx;
+                nj = cj + sy;
+                if (DIM == 3) { if (nj < 0) nj += g.ny; else if (nj >= g.ny) nj -= g.ny; }
+                nk = ck + sz;
+                bool alive = true;
+                if (g.bc_z == 0) {
+                    if (nk < 0) nk += g.nz; else if (nk >= g.nz) nk -= g.nz;
+                } else if (nk < 0 || nk >= g.nz) {
+                    alive = false;
+                }
+                if (alive) dest = tile_of(g, ni, nj, nk);
+            }
+            // ---- write into the bucket of the destination tile
+            const int r = output_slot(&s_stay, a.out_hi, dest, t, g.cap);
             if (dest >= 0) {
-                if (r >= g.cap) {
+                if (r < 0) {
                     atomicOr(a.err, ERR_CAPACITY);
                 } else {
                     const int64_t d = dest * (int64_t)g.cap + r;
@@ -395,8 +462,12 @@ __global__ void __launch_bounds__(256) push_kernel(PushArgs<real> a)
         }
         __syncthreads();
         // flush the J tile: one global add per non-zero node
-        flush_rows<real, DIM>(g, Ptr3<real>{a.J[0], a.J[1], a.J[2]}, 0x4u, 3, sJ, QX, QY, QZ, lox, loy, loz, JL);
-        if (threadIdx.x == 0) a.cnt_in[t] = 0;
+        flush_tile<real, DIM, 3, QX, QY, QZ, JL>(g, Ptr3<real>{a.J[0], a.J[1], a.J[2]}, 0x4u, sJ, lox, loy, loz);
+        if (threadIdx.x == 0) {
+            a.out_lo[t] = min(s_stay, g.cap);
+            a.in_lo[t] = 0;
+            a.in_hi[t] = 0;
+        }
     }
 }
 
@@ -418,18 +489,21 @@ __global__ void __launch_bounds__(256) ion_kernel(PushArgs<real> a)
     const real dx = a.ion_u[0] * ig * a.dtdh[0];
     const real dy = DIM == 3 ? a.ion_u[1] * ig * a.dtdh[1] : real(0);
     const real dz = a.ion_u[2] * ig * a.dtdh[2];
+    __shared__ int s_stay;
 
     for (int64_t t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
-        const int n = min(a.cnt_in[t], g.cap);
+        int n_lo, n_hi;
+        bucket_counts(a.in_lo, a.in_hi, t, g.cap, n_lo, n_hi, a.err);
+        const int n = n_lo + n_hi;
         if (n == 0) continue;
         const int tix = (int)(t % g.nt[0]);
         const int tiy = (int)((t / g.nt[0]) % g.nt[1]);
         const int tiz = (int)(t / ((int64_t)g.nt[0] * g.nt[1]));
         const int lox = tix << g.lt[0], loy = tiy << g.lt[1], loz = tiz << g.lt[2];
         __syncthreads();
+        if (threadIdx.x == 0) s_stay = 0;
         for (int q = threadIdx.x; q < QN; q += blockDim.x) sJ[q] = 0;
         __syncthreads();
-        const int64_t slot0 = t * (int64_t)g.cap;
         for (int base = 0; base < n; base += blockDim.x) {
             const int p = base + threadIdx.x;
             int64_t dest = -1;
@@ -437,7 +511,7 @@ __global__ void __launch_bounds__(256) ion_kernel(PushArgs<real> a)
             int ni = 0, nj = 0, nk = 0;
             int64_t pid = 0;
             if (p < n) {
-                const int64_t s = slot0 + p;
+                const int64_t s = bucket_slot(t, g.cap, n_lo, n_hi, p);
                 int ci, cj, ck;
                 unpack_cell(g, a.in.cell[s], ci, cj, ck);
                 const int li = ci - lox, lj = cj - loy, lk = ck - loz;
@@ -492,9 +566,9 @@ __global__ void __launch_bounds__(256) ion_kernel(PushArgs<real> a)
                     if (alive) dest = tile_of(g, ni, nj, nk);
                 }
             }
-            const int r = reserve_slot_own(a.cnt_out, dest, t);
+            const int r = output_slot(&s_stay, a.out_hi, dest, t, g.cap);
             if (dest >= 0) {
-                if (r >= g.cap) {
+                if (r < 0) {
                     atomicOr(a.err, ERR_CAPACITY);
                 } else {
                     const int64_t d = dest * (int64_t)g.cap + r;
@@ -508,8 +582,12 @@ __global__ void __launch_bounds__(256) ion_kernel(PushArgs<real> a)
             }
         }
         __syncthreads();
-        flush_rows<real, DIM>(g, Ptr3<real>{a.J[2], a.J[2], a.J[2]}, 0x1u, 1, sJ, QX, QY, QZ, lox, loy, loz, JL);
-        if (threadIdx.x == 0) a.cnt_in[t] = 0;
+        flush_tile<real, DIM, 1, QX, QY, QZ, JL>(g, Ptr3<real>{a.J[2], a.J[2], a.J[2]}, 0x1u, sJ, lox, loy, loz);
+        if (threadIdx.x == 0) {
+            a.out_lo[t] = min(s_stay, g.cap);
+            a.in_lo[t] = 0;
+            a.in_hi[t] = 0;
+        }
     }
 }
 
@@ -564,13 +642,13 @@ __global__ void bucket_kernel(BucketArgs<real> a)
             unpack_cell(a.g, a.src.cell[p], ci, cj, ck);
             dest = tile_of(a.g, ci, cj, ck);
         }
-        const int r = reserve_slot(a.cnt_dst, dest);
+        const int r = reserve_slot(a.dst_hi, dest);
         if (dest < 0) continue;
         if (r >= a.g.cap) {
             atomicOr(a.err, ERR_CAPACITY);
             continue;
         }
-        const int64_t d = dest * (int64_t)a.g.cap + r;
+        const int64_t d = dest * (int64_t)a.g.cap + (a.g.cap - 1 - r);
         a.dst.ox[d] = a.src.ox[p];
         if (a.dst.oy) a.dst.oy[d] = a.src.oy[p];
         a.dst.oz[d] = a.src.oz[p];
@@ -598,10 +676,12 @@ template <typename real>
 __global__ void compact_kernel(CompactArgs<real> a)
 {
     for (int64_t t = blockIdx.x; t < a.g.ntiles; t += gridDim.x) {
-        const int n = min(a.cnt[t], a.g.cap);
-        const int64_t o = a.offset[t], s0 = t * (int64_t)a.g.cap;
+        int n_lo, n_hi;
+        bucket_counts(a.lo, a.hi, t, a.g.cap, n_lo, n_hi, nullptr);
+        const int n = n_lo + n_hi;
+        const int64_t o = a.offset[t];
         for (int p = threadIdx.x; p < n; p += blockDim.x) {
-            const int64_t s = s0 + p, d = o + p;
+            const int64_t s = bucket_slot(t, a.g.cap, n_lo, n_hi, p), d = o + p;
             a.dst.ox[d] = a.src.ox[s];
             if (a.src.oy) a.dst.oy[d] = a.src.oy[s];
             a.dst.oz[d] = a.src.oz[s];
@@ -627,12 +707,14 @@ void launch_compact(const CompactArgs<real> &a, cudaStream_t s)
 // ------------------------------------------------------- charge density
 
 template <typename real, int DIM, int S>
-__global__ void rho_kernel(Geom g, Species<real> sp, const int *cnt, real qfac, real *rho)
+__global__ void rho_kernel(Geom g, Species<real> sp, const int *lo, const int *hi, real qfac, real *rho)
 {
     for (int64_t t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
-        const int n = min(cnt[t], g.cap);
+        int n_lo, n_hi;
+        bucket_counts(lo, hi, t, g.cap, n_lo, n_hi, nullptr);
+        const int n = n_lo + n_hi;
         for (int p = threadIdx.x; p < n; p += blockDim.x) {
-            const int64_t s = t * (int64_t)g.cap + p;
+            const int64_t s = bucket_slot(t, g.cap, n_lo, n_hi, p);
             int ci, cj, ck;
             unpack_cell(g, sp.cell[s], ci, cj, ck);
             real wx[S + 1], wy[S + 1], wz[S + 1];
@@ -659,17 +741,17 @@ __global__ void rho_kernel(Geom g, Species<real> sp, const int *cnt, real qfac, 
 }
 
 template <typename real>
-void launch_rho(const Geom &g, const Species<real> &sp, const int *cnt, real qfac, real *rho,
+void launch_rho(const Geom &g, const Species<real> &sp, const int *lo, const int *hi, real qfac, real *rho,
                 cudaStream_t s)
 {
     const int64_t grid = g.ntiles < 1048576 ? g.ntiles : 1048576;
     if (grid <= 0) return;
     if (g.dim == 3) {
-        if (g.shape == 1) rho_kernel<real, 3, 1><<<(unsigned)grid, 128, 0, s>>>(g, sp, cnt, qfac, rho);
-        else rho_kernel<real, 3, 2><<<(unsigned)grid, 128, 0, s>>>(g, sp, cnt, qfac, rho);
+        if (g.shape == 1) rho_kernel<real, 3, 1><<<(unsigned)grid, 128, 0, s>>>(g, sp, lo, hi, qfac, rho);
+        else rho_kernel<real, 3, 2><<<(unsigned)grid, 128, 0, s>>>(g, sp, lo, hi, qfac, rho);
     } else {
-        if (g.shape == 1) rho_kernel<real, 2, 1><<<(unsigned)grid, 128, 0, s>>>(g, sp, cnt, qfac, rho);
-        else rho_kernel<real, 2, 2><<<(unsigned)grid, 128, 0, s>>>(g, sp, cnt, qfac, rho);
+        if (g.shape == 1) rho_kernel<real, 2, 1><<<(unsigned)grid, 128, 0, s>>>(g, sp, lo, hi, qfac, rho);
+        else rho_kernel<real, 2, 2><<<(unsigned)grid, 128, 0, s>>>(g, sp, lo, hi, qfac, rho);
     }
 }
 
@@ -678,14 +760,16 @@ void launch_rho(const Geom &g, const Species<real> &sp, const int *cnt, real qfa
 // Kahan-compensated FP64 partial sums per block: [0] sum w (gamma-1),
 // [1] sum q w.  The host adds the block partials, also with compensation.
 template <typename real>
-__global__ void particle_sums_kernel(Geom g, Species<real> sp, const int *cnt, double q,
+__global__ void particle_sums_kernel(Geom g, Species<real> sp, const int *lo, const int *hi, double q,
                                      double iux, double iuy, double iuz, double *partials)
 {
     double s0 = 0, c0 = 0, s1 = 0, c1 = 0;
     for (int64_t t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
-        const int n = min(cnt[t], g.cap);
+        int n_lo, n_hi;
+        bucket_counts(lo, hi, t, g.cap, n_lo, n_hi, nullptr);
+        const int n = n_lo + n_hi;
         for (int p = threadIdx.x; p < n; p += blockDim.x) {
-            const int64_t s = t * (int64_t)g.cap + p;
+            const int64_t s = bucket_slot(t, g.cap, n_lo, n_hi, p);
             const double w = (double)sp.w[s];
             double ux = iux, uy = iuy, uz = iuz;
             if (sp.ux) {
@@ -722,10 +806,10 @@ __global__ void particle_sums_kernel(Geom g, Species<real> sp, const int *cnt, d
 }
 
 template <typename real>
-void launch_particle_sums(const Geom &g, const Species<real> &sp, const int *cnt, double q,
+void launch_particle_sums(const Geom &g, const Species<real> &sp, const int *lo, const int *hi, double q,
                           const real ion_u[3], double *partials, int nblocks, cudaStream_t s)
 {
-    particle_sums_kernel<real><<<nblocks, 256, 0, s>>>(g, sp, cnt, q, (double)ion_u[0], (double)ion_u[1],
+    particle_sums_kernel<real><<<nblocks, 256, 0, s>>>(g, sp, lo, hi, q, (double)ion_u[0], (double)ion_u[1],
                                                        (double)ion_u[2], partials);
 }
 
@@ -734,10 +818,11 @@ void launch_particle_sums(const Geom &g, const Species<real> &sp, const int *cnt
     template void launch_ions<real>(const PushArgs<real> &, cudaStream_t);                          \
     template void launch_bucket<real>(const BucketArgs<real> &, cudaStream_t);                      \
     template void launch_compact<real>(const CompactArgs<real> &, cudaStream_t);                    \
-    template void launch_rho<real>(const Geom &, const Species<real> &, const int *, real, real *,  \
-                                   cudaStream_t);                                                   \
+    template void launch_rho<real>(const Geom &, const Species<real> &, const int *, const int *, real, \
+                                   real *, cudaStream_t);                                            \
     template void launch_particle_sums<real>(const Geom &, const Species<real> &, const int *,      \
-                                             double, const real *, double *, int, cudaStream_t);
+                                             const int *, double, const real *, double *, int,      \
+                                             cudaStream_t);
 PIC_INSTANTIATE(float)
 PIC_INSTANTIATE(double)
 
