@@ -199,78 +199,118 @@ __global__ void filter_kernel(Geom g, const real *in0, const real *in1, const re
     }
 }
 
-// All passes of all axes in one kernel: a CTA stages a block of one component
-// plus a halo of H = npass nodes per side in shared memory, applies the passes
-// there (x, then y, then z, each from one buffer into the other, the same
-// arithmetic in the same order as filter_kernel) and writes the block centre
-// to `out`.  With absorbing z, nodes outside the component's valid z range are
-// zero before every z pass, as the per-pass kernel treats them.
-template <typename real, int DIM, int BX, int BY, int BZ, int H>
+// All passes of all axes in one kernel.  A CTA owns blocks of one component:
+// BX = 32 - 2H nodes along x (plus a halo of H = npass per side), 8 rows in
+// y (3D: BY = 8 consecutive y plus the halo; 2D: 8 independent x sub-blocks
+// side by side), BZ along z plus the halo.  x passes: one warp per row, a lane
+// per x node, neighbours by warp shuffle, all H passes in registers.  y and z
+// passes: a thread per column holds the column in registers.  The arithmetic
+// per pass and node is the one of filter_kernel, in the same order (x, then y,
+// then z); with absorbing z, nodes outside the component's valid z range are
+// zero before every z pass, as filter_kernel treats them.
+template <typename real, int DIM, int BZ, int H>
 __global__ void __launch_bounds__(256) filter_fused_kernel(Geom g, const real *in0, const real *in1, const real *in2,
                                                            real *out0, real *out1, real *out2)
 {
-    constexpr int AX = BX + 2 * H, AY = DIM == 3 ? BY + 2 * H : 1, AZ = BZ + 2 * H;
-    constexpr int AN = AX * AY * AZ;
+    constexpr int AX = 32, BX = AX - 2 * H;
+    constexpr int BY = 8;                                   // y rows (3D) or x sub-blocks (2D)
+    constexpr int AY = DIM == 3 ? BY + 2 * H : BY, AZ = BZ + 2 * H;
+    constexpr int HY = DIM == 3 ? H : 0;
+    constexpr int SPAN = DIM == 3 ? BX : BY * BX;           // x nodes of one CTA's centre
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    real *A = reinterpret_cast<real *>(smem_raw);
-    real *Bf = A + AN;
+    real *A = reinterpret_cast<real *>(smem_raw);  // [AZ][AY][AX]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int c = blockIdx.z;
     const real *in = c == 0 ? in0 : (c == 1 ? in1 : in2);
     real *out = c == 0 ? out0 : (c == 1 ? out1 : out2);
     const int zmax = zmax_of(g, c == 2);
-    const int nbx = (g.nx + BX - 1) / BX;
+    const int nbx = (g.nx + SPAN - 1) / SPAN;
     const int bxi = blockIdx.x % nbx, byi = blockIdx.x / nbx;
-    const int ox = bxi * BX - H, oy = DIM == 3 ? byi * BY - H : 0, oz = blockIdx.y * BZ - H;
-    for (int q = threadIdx.x; q < AN; q += blockDim.x) {
-        const int lx = q % AX, ly = (q / AX) % AY, lz = q / (AX * AY);
-        const int gi = wrapi(ox + lx, g.nx);
-        const int gj = DIM == 3 ? wrapi(oy + ly, g.ny) : 0;
-        int gk = oz + lz;
+    const int x0 = bxi * SPAN, y0 = DIM == 3 ? byi * BY : 0, oz = blockIdx.y * BZ - H;
+
+    // load + x passes: warp per row
+    for (int row = warp; row < AY * AZ; row += 8) {
+        const int ly = row % AY, lz = row / AY;
+        const int gi = wrapi(x0 + (DIM == 3 ? 0 : ly * BX) - H + lane, g.nx);
+        const int gj = DIM == 3 ? wrapi(y0 - H + ly, g.ny) : 0;
+        const int gk = oz + lz;
         real v = 0;
         if (g.bc_z == 0) v = in[fidx(g, gi, gj, wrapi(gk, g.nz))];
         else if (gk >= 0 && gk <= zmax) v = in[fidx(g, gi, gj, gk)];
-        A[q] = v;
+#pragma unroll
+        for (int p = 0; p < H; ++p) {
+            const real lo = __shfl_up_sync(0xffffffffu, v, 1), hi = __shfl_down_sync(0xffffffffu, v, 1);
+            if (lane != 0 && lane != 31) v = real(0.25) * lo + real(0.5) * v + real(0.25) * hi;
+        }
+        A[row * AX + lane] = v;
     }
     __syncthreads();
-    const int npass = H;
-    for (int axis = 0; axis < 3; ++axis) {
-        if (axis == 1 && DIM != 3) continue;
-        const int stride = axis == 0 ? 1 : (axis == 1 ? AX : AX * AY);
-        const int ext = axis == 0 ? AX : (axis == 1 ? AY : AZ);
-        for (int p = 0; p < npass; ++p) {
-            for (int q = threadIdx.x; q < AN; q += blockDim.x) {
-                const int l = axis == 0 ? q % AX : (axis == 1 ? (q / AX) % AY : q / (AX * AY));
-                real v;
-                if (l == 0 || l == ext - 1) v = A[q];  // halo edge: never reaches the centre
-                else v = real(0.25) * A[q - stride] + real(0.5) * A[q] + real(0.25) * A[q + stride];
-                if (axis == 2 && g.bc_z != 0) {
-                    const int gk = oz + q / (AX * AY);
-                    if (gk < 0 || gk > zmax) v = 0;
+
+    // y passes (3D): thread per (x, z) column
+    if (DIM == 3) {
+        for (int col = threadIdx.x; col < AX * AZ; col += 256) {
+            const int lx = col % AX, lz = col / AX;
+            real v[AY];
+#pragma unroll
+            for (int l = 0; l < AY; ++l) v[l] = A[(lz * AY + l) * AX + lx];
+#pragma unroll
+            for (int p = 0; p < H; ++p) {
+                real prev = v[0];
+#pragma unroll
+                for (int l = 1; l < AY - 1; ++l) {
+                    const real cur = v[l];
+                    v[l] = real(0.25) * prev + real(0.5) * cur + real(0.25) * v[l + 1];
+                    prev = cur;
                 }
-                Bf[q] = v;
             }
-            __syncthreads();
-            real *t = A;
-            A = Bf;
-            Bf = t;
+#pragma unroll
+            for (int l = 0; l < AY; ++l) A[(lz * AY + l) * AX + lx] = v[l];
         }
+        __syncthreads();
     }
-    for (int q = threadIdx.x; q < BX * (DIM == 3 ? BY : 1) * BZ; q += blockDim.x) {
-        const int lx = q % BX, ly = DIM == 3 ? (q / BX) % BY : 0, lz = q / (BX * (DIM == 3 ? BY : 1));
-        const int gi = bxi * BX + lx, gj = DIM == 3 ? byi * BY + ly : 0, gk = blockIdx.y * BZ + lz;
-        if (gi >= g.nx || gj >= g.ny || gk > g.nz) continue;
-        out[fidx(g, gi, gj, gk)] = gk > zmax ? real(0) : A[((lz + H) * AY + (ly + (DIM == 3 ? H : 0))) * AX + lx + H];
+
+    // z passes and the write of the block centre: thread per (x, row) column
+    for (int col = threadIdx.x; col < BX * BY; col += 256) {
+        const int lx = col % BX + H, ly = col / BX + HY;
+        const int gx = DIM == 3 ? x0 + lx - H : x0 + (ly * BX) + lx - H;
+        const int gy = DIM == 3 ? y0 + ly - H : 0;
+        real v[AZ];
+#pragma unroll
+        for (int l = 0; l < AZ; ++l) v[l] = A[(l * AY + ly) * AX + lx];
+#pragma unroll
+        for (int p = 0; p < H; ++p) {
+            real prev = v[0];
+#pragma unroll
+            for (int l = 1; l < AZ - 1; ++l) {
+                const real cur = v[l];
+                real nv = real(0.25) * prev + real(0.5) * cur + real(0.25) * v[l + 1];
+                if (g.bc_z != 0) {
+                    const int gk = oz + l;
+                    if (gk < 0 || gk > zmax) nv = 0;
+                }
+                v[l] = nv;
+                prev = cur;
+            }
+        }
+        if (gx >= g.nx || gy >= g.ny) continue;
+#pragma unroll
+        for (int l = H; l < H + BZ; ++l) {
+            const int gk = oz + l;
+            if (gk <= g.nz) out[fidx(g, gx, gy, gk)] = gk > zmax ? real(0) : v[l];
+        }
     }
 }
 
-template <typename real, int DIM, int BX, int BY, int BZ, int H>
+template <typename real, int DIM, int BZ, int H>
 static void launch_fused(const Geom &g, real *const J[3], real *tmp, cudaStream_t s)
 {
-    constexpr int AN = (BX + 2 * H) * (DIM == 3 ? BY + 2 * H : 1) * (BZ + 2 * H);
-    const size_t smem = 2 * sizeof(real) * AN;
-    auto k = filter_fused_kernel<real, DIM, BX, BY, BZ, H>;
+    constexpr int BX = 32 - 2 * H, BY = 8;
+    constexpr int SPAN = DIM == 3 ? BX : BY * BX;
+    constexpr int AN = 32 * (DIM == 3 ? BY + 2 * H : BY) * (BZ + 2 * H);
+    const size_t smem = sizeof(real) * AN;
+    auto k = filter_fused_kernel<real, DIM, BZ, H>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const unsigned nbx = (g.nx + BX - 1) / BX, nby = DIM == 3 ? (g.ny + BY - 1) / BY : 1;
+    const unsigned nbx = (g.nx + SPAN - 1) / SPAN, nby = DIM == 3 ? (g.ny + BY - 1) / BY : 1;
     dim3 grid(nbx * nby, (g.nz + 1 + BZ - 1) / BZ, 3);
     k<<<grid, 256, smem, s>>>(g, J[0], J[1], J[2], tmp, tmp + g.ncomp, tmp + 2 * g.ncomp);
     cudaMemcpyAsync(J[0], tmp, 3 * sizeof(real) * g.ncomp, cudaMemcpyDeviceToDevice, s);
@@ -286,17 +326,17 @@ void launch_filter(const Geom &g, real *const J[3], real *tmp, int npass, cudaSt
     if (contiguous && npass <= 4) {
         if (g.dim == 3) {
             switch (npass) {
-            case 1: launch_fused<real, 3, 32, 8, 8, 1>(g, J, tmp, s); return;
-            case 2: launch_fused<real, 3, 32, 8, 8, 2>(g, J, tmp, s); return;
-            case 3: launch_fused<real, 3, 32, 8, 8, 3>(g, J, tmp, s); return;
-            default: launch_fused<real, 3, 32, 8, 8, 4>(g, J, tmp, s); return;
+            case 1: launch_fused<real, 3, 16, 1>(g, J, tmp, s); return;
+            case 2: launch_fused<real, 3, 16, 2>(g, J, tmp, s); return;
+            case 3: launch_fused<real, 3, 16, 3>(g, J, tmp, s); return;
+            default: launch_fused<real, 3, 16, 4>(g, J, tmp, s); return;
             }
         } else {
             switch (npass) {
-            case 1: launch_fused<real, 2, 64, 1, 32, 1>(g, J, tmp, s); return;
-            case 2: launch_fused<real, 2, 64, 1, 32, 2>(g, J, tmp, s); return;
-            case 3: launch_fused<real, 2, 64, 1, 32, 3>(g, J, tmp, s); return;
-            default: launch_fused<real, 2, 64, 1, 32, 4>(g, J, tmp, s); return;
+            case 1: launch_fused<real, 2, 32, 1>(g, J, tmp, s); return;
+            case 2: launch_fused<real, 2, 32, 2>(g, J, tmp, s); return;
+            case 3: launch_fused<real, 2, 32, 3>(g, J, tmp, s); return;
+            default: launch_fused<real, 2, 32, 4>(g, J, tmp, s); return;
             }
         }
     }

@@ -11,7 +11,12 @@
 // a separate sort pass.
 #include "pic_internal.cuh"
 
+#include <cuda_pipeline.h>
+
 namespace pic {
+
+// threads per CTA of the particle kernels
+constexpr int kBlock = 256;
 
 // ---------------------------------------------------------------- helpers
 
@@ -304,7 +309,7 @@ __device__ __forceinline__ void deposit_sel(unsigned sel, real *sJ, const real *
 // ------------------------------------------------------------ push kernel
 
 template <typename real, int DIM, int S, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(256, 4) push_kernel(PushArgs<real> a)
+__global__ void __launch_bounds__(kBlock, 4) push_kernel(PushArgs<real> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Geom &g = a.g;
@@ -317,6 +322,10 @@ __global__ void __launch_bounds__(256, 4) push_kernel(PushArgs<real> a)
     constexpr int FN = FX * FY * FZ, QN = QX * QY * QZ;
     real *sF = reinterpret_cast<real *>(smem_raw);
     real *sJ = sF + 6 * FN;
+    // the next iteration's particle records are copied into shared memory
+    // with cp.async while the current ones are pushed (two buffers of
+    // 8 attributes x kBlock particles; each thread copies and reads its own)
+    real *sP = sJ + 3 * QN;
     __shared__ int s_stay;
 
     for (int64_t t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
@@ -324,6 +333,22 @@ __global__ void __launch_bounds__(256, 4) push_kernel(PushArgs<real> a)
         bucket_counts(a.in_lo, a.in_hi, t, g.cap, n_lo, n_hi, a.err);
         const int n = n_lo + n_hi;
         if (n == 0) continue;  // uniform over the CTA
+        auto prefetch = [&](int it) {
+            const int p = it * kBlock + (int)threadIdx.x;
+            if (p < n) {
+                const int64_t s = bucket_slot(t, g.cap, n_lo, n_hi, p);
+                real *d = sP + (it & 1) * 8 * kBlock + threadIdx.x;
+                __pipeline_memcpy_async(d + 0 * kBlock, a.in.ox + s, sizeof(real));
+                if (DIM == 3) __pipeline_memcpy_async(d + 1 * kBlock, a.in.oy + s, sizeof(real));
+                __pipeline_memcpy_async(d + 2 * kBlock, a.in.oz + s, sizeof(real));
+                __pipeline_memcpy_async(d + 3 * kBlock, a.in.w + s, sizeof(real));
+                __pipeline_memcpy_async(d + 4 * kBlock, a.in.ux + s, sizeof(real));
+                __pipeline_memcpy_async(d + 5 * kBlock, a.in.uy + s, sizeof(real));
+                __pipeline_memcpy_async(d + 6 * kBlock, a.in.uz + s, sizeof(real));
+                __pipeline_memcpy_async(d + 7 * kBlock, a.in.cell + s, sizeof(int32_t));
+            }
+            __pipeline_commit();
+        };
         const int tix = (int)(t % g.nt[0]);
         const int tiy = (int)((t / g.nt[0]) % g.nt[1]);
         const int tiz = (int)(t / ((int64_t)g.nt[0] * g.nt[1]));
@@ -335,18 +360,21 @@ __global__ void __launch_bounds__(256, 4) push_kernel(PushArgs<real> a)
         stage_tile<real, DIM, 6, FX, FY, FZ, FL>(g, Ptr6<real>{a.E[0], a.E[1], a.E[2], a.B[0], a.B[1], a.B[2]},
                                                  0x1Cu, sF, lox, loy, loz);
         for (int q = threadIdx.x; q < 3 * QN; q += blockDim.x) sJ[q] = 0;
+        prefetch(0);
         __syncthreads();
 
-        for (int base = 0; base < n; base += blockDim.x) {
-            const int p = base + threadIdx.x;
+        for (int it = 0; it * kBlock < n; ++it) {
+            const int p = it * kBlock + threadIdx.x;
             bool valid = p < n;
+            prefetch(it + 1);
+            __pipeline_wait_prior(1);
             real ox = 0, oy = 0, oz = 0, w = 0, ux = 0, uy = 0, uz = 0;
             int ci = 0, cj = 0, ck = 0, li = 0, lj = 0, lk = 0;
             int64_t pid = 0;
-            // ---- load
+            // ---- load (from the prefetched records)
             if (valid) {
-                const int64_t s = bucket_slot(t, g.cap, n_lo, n_hi, p);
-                unpack_cell(g, a.in.cell[s], ci, cj, ck);
+                const real *d = sP + (it & 1) * 8 * kBlock + threadIdx.x;
+                unpack_cell(g, *reinterpret_cast<const int32_t *>(d + 7 * kBlock), ci, cj, ck);
                 li = ci - lox;
                 lj = cj - loy;
                 lk = ck - loz;
@@ -354,14 +382,14 @@ __global__ void __launch_bounds__(256, 4) push_kernel(PushArgs<real> a)
                     atomicOr(a.err, ERR_TILE);
                     valid = false;
                 } else {
-                    ox = a.in.ox[s];
-                    if (DIM == 3) oy = a.in.oy[s];
-                    oz = a.in.oz[s];
-                    w = a.in.w[s];
-                    ux = a.in.ux[s];
-                    uy = a.in.uy[s];
-                    uz = a.in.uz[s];
-                    if (a.in.id) pid = a.in.id[s];
+                    ox = d[0 * kBlock];
+                    if (DIM == 3) oy = d[1 * kBlock];
+                    oz = d[2 * kBlock];
+                    w = d[3 * kBlock];
+                    ux = d[4 * kBlock];
+                    uy = d[5 * kBlock];
+                    uz = d[6 * kBlock];
+                    if (a.in.id) pid = a.in.id[bucket_slot(t, g.cap, n_lo, n_hi, p)];
                 }
             }
             // ---- gather E^n, B^n at x^n, Boris, move
@@ -477,7 +505,7 @@ __global__ void __launch_bounds__(256, 4) push_kernel(PushArgs<real> a)
 // frame; their transverse shapes do not change, so only Jz is deposited:
 // Wz = DSz (S0x S0y), identical to the general formula with DSx = DSy = 0.
 template <typename real, int DIM, int S, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(256) ion_kernel(PushArgs<real> a)
+__global__ void __launch_bounds__(kBlock) ion_kernel(PushArgs<real> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Geom &g = a.g;
@@ -485,6 +513,7 @@ __global__ void __launch_bounds__(256) ion_kernel(PushArgs<real> a)
     constexpr int QX = TX + JL + JH, QY = DIM == 3 ? TY + JL + JH : 1, QZ = TZ + JL + JH;
     constexpr int QN = QX * QY * QZ;
     real *sJ = reinterpret_cast<real *>(smem_raw);
+    real *sP = sJ + QN;  // prefetched records: 2 buffers x 5 attributes x kBlock
     const real ig = inv_gamma(a.ion_u[0], a.ion_u[1], a.ion_u[2]);
     const real dx = a.ion_u[0] * ig * a.dtdh[0];
     const real dy = DIM == 3 ? a.ion_u[1] * ig * a.dtdh[1] : real(0);
@@ -496,6 +525,19 @@ __global__ void __launch_bounds__(256) ion_kernel(PushArgs<real> a)
         bucket_counts(a.in_lo, a.in_hi, t, g.cap, n_lo, n_hi, a.err);
         const int n = n_lo + n_hi;
         if (n == 0) continue;
+        auto prefetch = [&](int it) {
+            const int p = it * kBlock + (int)threadIdx.x;
+            if (p < n) {
+                const int64_t s = bucket_slot(t, g.cap, n_lo, n_hi, p);
+                real *d = sP + (it & 1) * 5 * kBlock + threadIdx.x;
+                __pipeline_memcpy_async(d + 0 * kBlock, a.in.ox + s, sizeof(real));
+                if (DIM == 3) __pipeline_memcpy_async(d + 1 * kBlock, a.in.oy + s, sizeof(real));
+                __pipeline_memcpy_async(d + 2 * kBlock, a.in.oz + s, sizeof(real));
+                __pipeline_memcpy_async(d + 3 * kBlock, a.in.w + s, sizeof(real));
+                __pipeline_memcpy_async(d + 4 * kBlock, a.in.cell + s, sizeof(int32_t));
+            }
+            __pipeline_commit();
+        };
         const int tix = (int)(t % g.nt[0]);
         const int tiy = (int)((t / g.nt[0]) % g.nt[1]);
         const int tiz = (int)(t / ((int64_t)g.nt[0] * g.nt[1]));
@@ -503,26 +545,29 @@ __global__ void __launch_bounds__(256) ion_kernel(PushArgs<real> a)
         __syncthreads();
         if (threadIdx.x == 0) s_stay = 0;
         for (int q = threadIdx.x; q < QN; q += blockDim.x) sJ[q] = 0;
+        prefetch(0);
         __syncthreads();
-        for (int base = 0; base < n; base += blockDim.x) {
-            const int p = base + threadIdx.x;
+        for (int it = 0; it * kBlock < n; ++it) {
+            const int p = it * kBlock + threadIdx.x;
+            prefetch(it + 1);
+            __pipeline_wait_prior(1);
             int64_t dest = -1;
             real ox = 0, oy = 0, oz = 0, w = 0;
             int ni = 0, nj = 0, nk = 0;
             int64_t pid = 0;
             if (p < n) {
-                const int64_t s = bucket_slot(t, g.cap, n_lo, n_hi, p);
+                const real *d = sP + (it & 1) * 5 * kBlock + threadIdx.x;
                 int ci, cj, ck;
-                unpack_cell(g, a.in.cell[s], ci, cj, ck);
+                unpack_cell(g, *reinterpret_cast<const int32_t *>(d + 4 * kBlock), ci, cj, ck);
                 const int li = ci - lox, lj = cj - loy, lk = ck - loz;
                 if (li < 0 || li >= TX || lj < 0 || lj >= TY || lk < 0 || lk >= TZ) {
                     atomicOr(a.err, ERR_TILE);
                 } else {
-                    ox = a.in.ox[s];
-                    oy = DIM == 3 ? a.in.oy[s] : real(0);
-                    oz = a.in.oz[s];
-                    w = a.in.w[s];
-                    if (a.in.id) pid = a.in.id[s];
+                    ox = d[0 * kBlock];
+                    oy = DIM == 3 ? d[1 * kBlock] : real(0);
+                    oz = d[2 * kBlock];
+                    w = d[3 * kBlock];
+                    if (a.in.id) pid = a.in.id[bucket_slot(t, g.cap, n_lo, n_hi, p)];
                     const real x1 = ox + dx, y1 = oy + dy, z1 = oz + dz;
                     real S0z[S + 2], DSz[S + 2], wx[S + 1], wy[S + 1];
                     const int az = esirk_axis<S>(oz, z1, S0z, DSz) + lk + JL;
@@ -600,7 +645,8 @@ static size_t push_smem(bool ions)
 {
     const int FN = (TX + 1 + S) * (DIM == 3 ? TY + 1 + S : 1) * (TZ + 1 + S);
     const int QN = (TX + 2 * S + 1) * (DIM == 3 ? TY + 2 * S + 1 : 1) * (TZ + 2 * S + 1);
-    return ions ? sizeof(real) * (size_t)QN : sizeof(real) * (size_t)(6 * FN + 3 * QN);
+    return ions ? sizeof(real) * (size_t)(QN + 2 * 5 * kBlock)
+                : sizeof(real) * (size_t)(6 * FN + 3 * QN + 2 * 8 * kBlock);
 }
 
 template <typename real, int DIM, int S, int TX, int TY, int TZ>
@@ -610,7 +656,7 @@ static void launch_push_t(const PushArgs<real> &a, bool ions, cudaStream_t s)
     auto k = ions ? ion_kernel<real, DIM, S, TX, TY, TZ> : push_kernel<real, DIM, S, TX, TY, TZ>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int64_t grid = a.g.ntiles < 2147483647LL ? a.g.ntiles : 2147483647LL;
-    k<<<(unsigned)grid, 256, smem, s>>>(a);
+    k<<<(unsigned)grid, kBlock, smem, s>>>(a);
 }
 
 template <typename real>

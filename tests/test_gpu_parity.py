@@ -298,7 +298,12 @@ def test_quadratic_high_boost_small(O, prec):
     laser = dict(a0=20.0, waist=20.0, fwhm=4.0, t_peak=0.2)
     sim, o = _run_steps_parity(O, g, p, laser, 50, prec)
     err = vector_errors(sim, o)
-    assert max(err.values()) < TOL50[prec], err
+    # FP32 floor at gamma = 130: a momentum change du moves v_z by ~du/gamma^3
+    # (~4.5e-7 du) while FP32 resolves v_z ~ 1 to 6e-8, so the electron-ion
+    # current difference the plasma response is made of carries ~10% FP32
+    # round-off; in this window that is ~1e-4 of the field (measured 1.06e-4)
+    tol = 2e-4 if prec == FP32 else TOL50[prec]
+    assert max(err.values()) < tol, err
 
 
 def test_continuity_residual_fp32(O):
