@@ -15,8 +15,11 @@
 
 namespace pic {
 
-// threads per CTA of the particle kernels
+// threads per CTA of the particle kernels; resident CTAs per SM the push
+// kernel is compiled for (FP32: 4, i.e. 64 registers a thread; the FP64 debug
+// path keeps more registers)
 constexpr int kBlock = 256;
+template <typename real> struct MinBlocks { static constexpr int value = sizeof(real) == 4 ? 4 : 2; };
 
 // ---------------------------------------------------------------- helpers
 
@@ -275,6 +278,32 @@ __device__ __forceinline__ void deposit_w(real *sJ, const real *S0x, const real 
     }
 }
 
+// The current of particles that did not move across z (3D): Wx = Wy = 0
+// exactly, so Jx = Jy = 0 and Jz(q,b,c) = fz (sum_{c'<=c} DSz[c']) S0x[q] S0y[b]
+// -- the general formula's values with DSx = DSy = 0.  Windows along x and y
+// have S+1 nodes (their supports did not move).
+template <typename real, int S, int QX, int QY, int QN, int WZ>
+__device__ __forceinline__ void deposit_z(real *sJ, const real *S0x, const real *S0y, const real *S0z,
+                                          const real *DSz, int ax, int ay, int az, real fz)
+{
+    real *Jz = sJ + 2 * QN;
+    real Pz[WZ];
+    real acc = 0;
+#pragma unroll
+    for (int c = 0; c < WZ; ++c) { acc += DSz[c]; Pz[c] = fz * acc; }
+    (void)S0z;
+#pragma unroll
+    for (int b = 0; b < S + 1; ++b) {
+#pragma unroll
+        for (int q = 0; q < S + 1; ++q) {
+            const real txy = S0x[q] * S0y[b];
+            real *col = Jz + (az * QY + (ay + b)) * QX + ax + q;
+#pragma unroll
+            for (int c = 0; c < WZ - 1; ++c) sh_add(col + c * QX * QY, Pz[c] * txy);
+        }
+    }
+}
+
 // picks the window lengths for the warp: bit 2 x, bit 1 y, bit 0 z crossed
 template <typename real, int DIM, int S, int QX, int QY, int QN>
 __device__ __forceinline__ void deposit_sel(unsigned sel, real *sJ, const real *S0x, const real *DSx, const real *S0y,
@@ -309,7 +338,7 @@ __device__ __forceinline__ void deposit_sel(unsigned sel, real *sJ, const real *
 // ------------------------------------------------------------ push kernel
 
 template <typename real, int DIM, int S, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(kBlock, 4) push_kernel(PushArgs<real> a)
+__global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(PushArgs<real> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Geom &g = a.g;
@@ -440,12 +469,21 @@ __global__ void __launch_bounds__(kBlock, 4) push_kernel(PushArgs<real> a)
             }
             const unsigned sel = (__any_sync(0xffffffffu, cx) ? 4u : 0u) | (__any_sync(0xffffffffu, cy) ? 2u : 0u) |
                                  (__any_sync(0xffffffffu, cz) ? 1u : 0u);
+            // 3D: no lane moved in x or y (e.g. plasma the laser has not reached)
+            const bool z_only = DIM == 3 && __all_sync(0xffffffffu, !valid || (x1 == ox && y1 == oy));
             int64_t dest = -1;
             int ni = 0, nj = 0, nk = 0;
             if (valid) {
-                deposit_sel<real, DIM, S, QX, QY, QN>(sel, sJ, S0x, DSx, S0y, DSy, S0z, DSz, ax, ay, az,
-                                                      a.jfac[0] * w, a.jfac[1] * w, a.jfac[2] * w,
-                                                      a.jyfac * w * vy);
+                if (z_only) {
+                    if (sel & 1u)
+                        deposit_z<real, S, QX, QY, QN, S + 2>(sJ, S0x, S0y, S0z, DSz, ax, ay, az, a.jfac[2] * w);
+                    else
+                        deposit_z<real, S, QX, QY, QN, S + 1>(sJ, S0x, S0y, S0z, DSz, ax, ay, az, a.jfac[2] * w);
+                } else {
+                    deposit_sel<real, DIM, S, QX, QY, QN>(sel, sJ, S0x, DSx, S0y, DSy, S0z, DSz, ax, ay, az,
+                                                          a.jfac[0] * w, a.jfac[1] * w, a.jfac[2] * w,
+                                                          a.jyfac * w * vy);
+                }
                 // new cell and offsets; an offset that rounds to 1 moves on
                 int sx = (int)floor(x1), sy = DIM == 3 ? (int)floor(y1) : 0, sz = (int)floor(z1);
                 ox = x1 - real(sx);
@@ -569,23 +607,27 @@ __global__ void __launch_bounds__(kBlock) ion_kernel(PushArgs<real> a)
                     w = d[3 * kBlock];
                     if (a.in.id) pid = a.in.id[bucket_slot(t, g.cap, n_lo, n_hi, p)];
                     const real x1 = ox + dx, y1 = oy + dy, z1 = oz + dz;
+                    // Wz = DSz S0x S0y (the general formula with DSx = DSy = 0), in
+                    // the arithmetic order of the electrons' z-only deposit
                     real S0z[S + 2], DSz[S + 2], wx[S + 1], wy[S + 1];
-                    const int az = esirk_axis<S>(oz, z1, S0z, DSz) + lk + JL;
+                    bool crossed;
+                    const int az = esirk_axis_c<S>(oz, z1, S0z, DSz, crossed) + lk + JL;
                     const int bx = spline_weights<S>(ox, wx) + li + JL;
                     int by = 0;
                     if (DIM == 3) by = spline_weights<S>(oy, wy) + lj + JL;
                     const real fz = a.jfac[2] * w;
+                    real Pz[S + 2];
+                    real acc = 0;
+#pragma unroll
+                    for (int c = 0; c < S + 2; ++c) { acc += DSz[c]; Pz[c] = fz * acc; }
 #pragma unroll
                     for (int b = 0; b < (DIM == 3 ? S + 1 : 1); ++b) {
 #pragma unroll
                         for (int q = 0; q < S + 1; ++q) {
                             const real sxy = DIM == 3 ? wx[q] * wy[b] : wx[q];
-                            real acc = 0;
 #pragma unroll
-                            for (int c = 0; c < S + 1; ++c) {
-                                acc += DSz[c] * sxy;
-                                sh_add(sJ + ((az + c) * QY + (by + b)) * QX + bx + q, fz * acc);
-                            }
+                            for (int c = 0; c < S + 1; ++c)
+                                sh_add(sJ + ((az + c) * QY + (by + b)) * QX + bx + q, Pz[c] * sxy);
                         }
                     }
                     int sx = (int)floor(x1), sy = DIM == 3 ? (int)floor(y1) : 0, sz = (int)floor(z1);

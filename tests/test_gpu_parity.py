@@ -192,11 +192,16 @@ def test_injection_matches_oracle(O, prec):
     _plasma_both(sim, o, O, p)
     assert o.pending() > 0
     mask_gpu = 2 | 4 | 64 | 128
-    for _ in range(40):
+    nsteps = 40
+    for _ in range(nsteps):
         sim.step_phases(1 | mask_gpu)
         o.step_phases(O.PH_ZERO_J | O.PH_PUSH | O.PH_IONS | O.PH_INJECT | O.PH_TIME)
-    _compare_particles(sim, o, 0, prec)
-    _compare_particles(sim, o, 1, prec)
+    # a field-free drift repeats the same rounded displacement v dt / hz every
+    # step: in FP32, v = u/gamma carries up to ~1 ulp (1.2e-7 relative), so the
+    # position error grows like steps x (cells per step) x 1.2e-7
+    tol = 1e-12 if prec == FP64 else 2e-6 + nsteps * 0.61 * 1.2e-7 * 1.5
+    _compare_particles(sim, o, 0, prec, pos_tol=tol)
+    _compare_particles(sim, o, 1, prec, pos_tol=tol)
 
 
 def _run_steps_parity(O, g, p, laser, nsteps, prec, slots=16.0):
