@@ -187,6 +187,9 @@ def run_ours(args, rank, world, local):
     d1 = sim.diagnostics()
     n_e = 0.5 * (d0.n_particles[0] + d1.n_particles[0])
     n_i = 0.5 * (d0.n_particles[1] + d1.n_particles[1])
+    # electrons still paired with their ion (plasma no field has reached yet:
+    # the pair's current is exactly zero and is not deposited)
+    paired = [d0.n_paired / max(d0.n_particles[0], 1), d1.n_paired / max(d1.n_particles[0], 1)]
     psteps = n_e * args.steps
 
     # whole-job aggregation: max time, summed work
@@ -249,6 +252,7 @@ def run_ours(args, rank, world, local):
                        "grid": [g["nx"], g["ny"], g["nz"]], "gamma_boost": g["gamma_boost"],
                        "filter_passes": g["filter_passes"], "shape_order": g["shape_order"],
                        "slots_per_cell": args.slots_per_cell,
+                       "paired_fraction_start_end": [round(paired[0], 4), round(paired[1], 4)],
                        "l2": "inputs larger than L2 (particle store >> 129 MB)",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -156,7 +156,9 @@ typedef struct pic_laser_params {
 typedef struct pic_diag {
     double t;                  /* simulation-frame time                            */
     int64_t step;              /* steps taken                                      */
-    int64_t n_particles[2];    /* live particles per species                       */
+    int64_t n_particles[2];    /* live particles per species (ions: stored ions    */
+                               /* plus the ions of paired electrons)               */
+    int64_t n_paired;          /* electrons still paired with their ion            */
     double field_energy;       /* (1/2) sum (E^2 + B^2) V, Kahan-compensated FP64   */
     double kinetic_energy;     /* sum w (gamma - 1) of the electrons, FP64 Kahan   */
     double charge;             /* sum q w of both species, FP64 Kahan              */
@@ -182,7 +184,13 @@ pic_status pic_bind_buffers(pic_ctx *ctx, const pic_buffers *b);
    boosted plasma is injected as it crosses z = Lz.  Lab-frame immobile ions
    are a neutralising background and carry no current.  The lattice id of a
    point with indices (ix, iy, iz) is (iz * NY + iy) * NX + ix, NX = nx*ppc[0],
-   NY = ny*ppc[1] (1 in 2D).  PIC_ERR_CAPACITY if a tile overflowed. */
+   NY = ny*ppc[1] (1 in 2D).  PIC_ERR_CAPACITY if a tile overflowed.
+   Storage of drifting ions: an electron and its ion start at the same place
+   with the same momentum and move identically until a non-zero field reaches
+   the electron, so their currents cancel exactly; such a pair is kept as the
+   electron record alone ("paired"), and the ion gets its own record, at the
+   electron's position, in the step the electron first gathers a non-zero
+   field.  pic_get_particles and pic_get_diagnostics report both members. */
 pic_status pic_load_plasma(pic_ctx *ctx, const pic_plasma_params *p);
 
 /* Appends n particles given as host FP64 arrays (simulation frame):

@@ -78,7 +78,7 @@ class LaserParams(C.Structure):
 
 
 class Diag(C.Structure):
-    _fields_ = [("t", C.c_double), ("step", C.c_int64), ("n_particles", C.c_int64 * 2),
+    _fields_ = [("t", C.c_double), ("step", C.c_int64), ("n_particles", C.c_int64 * 2), ("n_paired", C.c_int64),
                 ("field_energy", C.c_double), ("kinetic_energy", C.c_double), ("charge", C.c_double)]
 
 

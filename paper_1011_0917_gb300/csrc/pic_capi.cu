@@ -277,7 +277,7 @@ extern "C" pic_status pic_init_grid(const pic_grid_params *p, pic_ctx **out)
     c->off_offsets = o;
     o += align_up(sizeof(int64_t) * (size_t)g.ntiles);
     c->off_partials = o;
-    o += align_up(sizeof(double) * 2 * kPartialBlocks);
+    o += align_up(sizeof(double) * 3 * kPartialBlocks);
     c->off_err = o;
     o += kAlign;
     c->scratch_bytes = o;
@@ -562,6 +562,10 @@ static PushArgs<real> push_args(pic_ctx *c, int sp)
     a.ion_u[0] = 0;
     a.ion_u[1] = 0;
     a.ion_u[2] = (real)(-(c->gam * c->beta));
+    if (c->ions_species) {
+        a.ion_in = species_view<real>(c, 1, c->cur[1]);
+        a.ion_in_hi = counts(c, 1, c->cur[1], 1);
+    }
     a.err = reinterpret_cast<unsigned *>(c->scratch + c->off_err);
     return a;
 }
@@ -787,43 +791,73 @@ static pic_status compact_t(pic_ctx *c, int sp, int64_t &n)
     return PIC_OK;
 }
 
+// compacted records of a species, downloaded: attribute columns as bytes
 template <typename real>
-static pic_status get_particles_t(pic_ctx *c, int sp, double *dst, size_t dst_bytes, int64_t *n_out, int64_t *ids)
+static pic_status download_species(pic_ctx *c, int sp, int64_t &n, std::vector<std::vector<unsigned char>> &h)
 {
-    int64_t n = 0;
     pic_status s = compact_t<real>(c, sp, n);
     if (s != PIC_OK) return s;
-    if (n_out) *n_out = n;
-    if (!dst) return PIC_OK;
-    if (dst_bytes < (size_t)n * 7 * sizeof(double)) return fail(c, PIC_ERR_ARG, "destination too small");
     void *col[9];
     side_raw(c, sp, c->cur[sp] ^ 1, col);
-    std::vector<std::vector<unsigned char>> h(9);
+    h.assign(9, {});
     for (int a = 0; a < 9; ++a) {
         if (!col[a]) continue;
         h[a].resize((size_t)n * attr_size(c, a));
         if (n) CUDA_TRY(c, cudaMemcpyAsync(h[a].data(), col[a], h[a].size(), cudaMemcpyDeviceToHost, c->stream));
     }
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    auto R = [&](int a) { return reinterpret_cast<const real *>(h[a].data()); };
-    const int32_t *cell = reinterpret_cast<const int32_t *>(h[7].data());
-    for (int64_t p = 0; p < n; ++p) {
+    return PIC_OK;
+}
+
+// Live particles as FP64 rows.  Species 1 (drifting ions) is the stored ion
+// records plus, for every paired electron, its ion at the electron's position.
+template <typename real>
+static pic_status get_particles_t(pic_ctx *c, int sp, double *dst, size_t dst_bytes, int64_t *n_out, int64_t *ids)
+{
+    int64_t ne = 0, ni = 0;
+    std::vector<std::vector<unsigned char>> he, hi;
+    pic_status s = download_species<real>(c, 0, ne, he);
+    if (s != PIC_OK) return s;
+    if (sp == 1) {
+        s = download_species<real>(c, 1, ni, hi);
+        if (s != PIC_OK) return s;
+    }
+    const int32_t *ecell = reinterpret_cast<const int32_t *>(he[7].data());
+    int64_t npaired = 0;
+    if (sp == 1)
+        for (int64_t p = 0; p < ne; ++p) npaired += ((uint32_t)ecell[p] & kPaired) ? 1 : 0;
+    const int64_t n = sp == 0 ? ne : ni + npaired;
+    if (n_out) *n_out = n;
+    if (!dst) return PIC_OK;
+    if (dst_bytes < (size_t)n * 7 * sizeof(double)) return fail(c, PIC_ERR_ARG, "destination too small");
+    const double uz_ion = (double)(real)(-(c->gam * c->beta));
+    int64_t row = 0;
+    auto emit = [&](const std::vector<std::vector<unsigned char>> &h, int64_t p, bool electron) {
+        auto R = [&](int a) { return reinterpret_cast<const real *>(h[a].data()); };
         int i, j, k;
-        unpack_cell(c->g, cell[p], i, j, k);
-        dst[0 * n + p] = ((double)i + (double)R(0)[p]) * c->hx;
-        dst[1 * n + p] = c->g.dim == 3 ? ((double)j + (double)R(1)[p]) * c->hy : 0.0;
-        dst[2 * n + p] = ((double)k + (double)R(2)[p]) * c->hz;
-        if (sp == 0) {
-            dst[3 * n + p] = (double)R(4)[p];
-            dst[4 * n + p] = (double)R(5)[p];
-            dst[5 * n + p] = (double)R(6)[p];
+        unpack_cell(c->g, reinterpret_cast<const int32_t *>(h[7].data())[p], i, j, k);
+        dst[0 * n + row] = ((double)i + (double)R(0)[p]) * c->hx;
+        dst[1 * n + row] = c->g.dim == 3 ? ((double)j + (double)R(1)[p]) * c->hy : 0.0;
+        dst[2 * n + row] = ((double)k + (double)R(2)[p]) * c->hz;
+        if (electron) {
+            dst[3 * n + row] = (double)R(4)[p];
+            dst[4 * n + row] = (double)R(5)[p];
+            dst[5 * n + row] = (double)R(6)[p];
         } else {
-            dst[3 * n + p] = 0.0;
-            dst[4 * n + p] = 0.0;
-            dst[5 * n + p] = (double)(real)(-(c->gam * c->beta));
+            dst[3 * n + row] = 0.0;
+            dst[4 * n + row] = 0.0;
+            dst[5 * n + row] = uz_ion;
         }
-        dst[6 * n + p] = (double)R(3)[p];
-        if (ids) ids[p] = c->p.track_ids ? reinterpret_cast<const int64_t *>(h[8].data())[p] : -1;
+        dst[6 * n + row] = (double)R(3)[p];
+        if (ids) ids[row] = c->p.track_ids ? reinterpret_cast<const int64_t *>(h[8].data())[p] : -1;
+        ++row;
+    };
+    if (sp == 0) {
+        for (int64_t p = 0; p < ne; ++p) emit(he, p, true);
+    } else {
+        for (int64_t p = 0; p < ni; ++p) emit(hi, p, false);
+        for (int64_t p = 0; p < ne; ++p)
+            if ((uint32_t)ecell[p] & kPaired) emit(he, p, false);
     }
     return PIC_OK;
 }
@@ -881,7 +915,7 @@ template <typename real>
 static pic_status diagnostics_t(pic_ctx *c, pic_diag *out)
 {
     double *part = reinterpret_cast<double *>(c->scratch + c->off_partials);
-    std::vector<double> h(2 * kPartialBlocks);
+    std::vector<double> h(3 * kPartialBlocks);
     real *F[9];
     for (int q = 0; q < 9; ++q) F[q] = (real *)field_ptr(c, q);
     launch_field_sums<real>(c->g, F, part, kPartialBlocks, c->stream);
@@ -897,10 +931,15 @@ static pic_status diagnostics_t(pic_ctx *c, pic_diag *out)
                                    counts(c, sp, c->cur[sp], 1), sp == 0 ? -1.0 : 1.0, ion_u, part, kPartialBlocks,
                                    c->stream);
         CUDA_TRY(c, cudaGetLastError());
-        CUDA_TRY(c, cudaMemcpyAsync(h.data(), part, sizeof(double) * 2 * kPartialBlocks, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(h.data(), part, sizeof(double) * 3 * kPartialBlocks, cudaMemcpyDeviceToHost, c->stream));
         CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-        if (sp == 0) out->kinetic_energy = kahan_sum(h.data(), kPartialBlocks, 2);
-        out->charge += kahan_sum(h.data() + 1, kPartialBlocks, 2);
+        if (sp == 0) {
+            out->kinetic_energy = kahan_sum(h.data(), kPartialBlocks, 3);
+            double np = 0;
+            for (int b = 0; b < kPartialBlocks; ++b) np += h[3 * b + 2];
+            out->n_paired = (int64_t)np;
+        }
+        out->charge += kahan_sum(h.data() + 1, kPartialBlocks, 3);
     }
     return PIC_OK;
 }
@@ -920,7 +959,9 @@ extern "C" pic_status pic_get_diagnostics(pic_ctx *c, pic_diag *out)
         if (s != PIC_OK) return s;
         out->n_particles[sp] = n;
     }
-    return c->es == 4 ? diagnostics_t<float>(c, out) : diagnostics_t<double>(c, out);
+    pic_status s = c->es == 4 ? diagnostics_t<float>(c, out) : diagnostics_t<double>(c, out);
+    if (s == PIC_OK) out->n_particles[1] += out->n_paired;
+    return s;
 }
 
 // ---------------------------------------------------------------- checkpoint

@@ -27,6 +27,13 @@ namespace pic {
 
 enum : unsigned { ERR_CAPACITY = 1u, ERR_CFL = 2u, ERR_NAN = 4u, ERR_TILE = 8u };
 
+// Bit 31 of an electron's cell word: the electron is paired with a drifting ion
+// at its own position that has moved exactly like it since both were placed
+// (the plasma no field has touched).  Such a pair carries no current and is
+// stored as the electron record alone; its ion gets a record of its own (at the
+// electron's position) the first time the electron gathers a non-zero field.
+constexpr uint32_t kPaired = 0x80000000u;
+
 struct Geom {
     int dim;            // 2 or 3
     int nx, ny, nz;     // cells (ny = 1 in 2D)
@@ -56,7 +63,7 @@ __host__ __device__ inline int32_t pack_cell(const Geom &g, int i, int j, int k)
 
 __host__ __device__ inline void unpack_cell(const Geom &g, int32_t c, int &i, int &j, int &k)
 {
-    uint32_t u = (uint32_t)c;
+    uint32_t u = (uint32_t)c & ~kPaired;
     i = (int)(u & ((1u << g.bx) - 1u));
     j = g.by ? (int)((u >> g.bx) & ((1u << g.by) - 1u)) : 0;
     k = (int)(u >> (g.bx + g.by));
@@ -213,6 +220,8 @@ struct PushArgs {
     real jfac[3];       // -q h_d / (dt V): multiplied by w and the running sum
     real jyfac;         // q / V (2D out-of-plane current, times w vy)
     real ion_u[3];      // drift momentum of the ion species
+    Species<real> ion_in;  // ion side the IONS phase reads next (released ions go there)
+    int *ion_in_hi;        // its top-run lengths
     unsigned *err;
 };
 
@@ -244,7 +253,7 @@ struct InjectArgs {      // lattice load / boosted injection, FP64
     uint64_t seed;
     int mode;           // 0: in the box at t; 1: crossing z = Lz during (t, t1]
     double t, t1;
-    int drift_ions;
+    int drift_ions;     // ions drift with the plasma: electrons are placed paired
     int precision;      // 0 float, 1 double
     void *sp_e[9];      // ox oy oz w ux uy uz cell id of the electron side
     void *sp_i[9];      // same for the ion side (ux..uz unused)

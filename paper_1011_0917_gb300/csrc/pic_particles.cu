@@ -400,10 +400,13 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
             real ox = 0, oy = 0, oz = 0, w = 0, ux = 0, uy = 0, uz = 0;
             int ci = 0, cj = 0, ck = 0, li = 0, lj = 0, lk = 0;
             int64_t pid = 0;
+            bool paired = false;
             // ---- load (from the prefetched records)
             if (valid) {
                 const real *d = sP + (it & 1) * 8 * kBlock + threadIdx.x;
-                unpack_cell(g, *reinterpret_cast<const int32_t *>(d + 7 * kBlock), ci, cj, ck);
+                const int32_t word = *reinterpret_cast<const int32_t *>(d + 7 * kBlock);
+                paired = ((uint32_t)word & kPaired) != 0u;
+                unpack_cell(g, word, ci, cj, ck);
                 li = ci - lox;
                 lj = cj - loy;
                 lk = ck - loz;
@@ -423,6 +426,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
             }
             // ---- gather E^n, B^n at x^n, Boris, move
             real x1 = 0, y1 = 0, z1 = 0, vy = 0;
+            bool release = false;
             if (valid) {
                 real wxu[S + 1], wxh[S + 1], wyu[S + 1], wyh[S + 1], wzu[S + 1], wzh[S + 1];
                 const int bxu = spline_weights<S>(ox, wxu) + li + FL;
@@ -443,6 +447,11 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
                 const real bx = gather_comp<DIM, S>(sF + 3 * FN, FX, FY, bxu, byh, bzh, wxu, wyh, wzh);
                 const real by = gather_comp<DIM, S>(sF + 4 * FN, FX, FY, bxh, byu, bzh, wxh, wyu, wzh);
                 const real bz = gather_comp<DIM, S>(sF + 5 * FN, FX, FY, bxh, byh, bzu, wxh, wyh, wzu);
+                // a paired electron that gathers a non-zero field leaves its ion
+                // behind: the pair's current is no longer zero
+                if (paired && (ex != real(0) || ey != real(0) || ez != real(0) || bx != real(0) ||
+                               by != real(0) || bz != real(0)))
+                    release = true;
                 boris(ux, uy, uz, ex, ey, ez, bx, by, bz, a.eps);
                 const real ig = inv_gamma(ux, uy, uz);
                 vy = uy * ig;
@@ -458,11 +467,30 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
                     z1 = oz + dz;
                 }
             }
+            // ---- released ion: a record at the pair's position x^n, in the ion
+            // side the IONS phase of this step reads (it moves and deposits it)
+            if (__any_sync(0xffffffffu, release)) {
+                const int r = reserve_slot(a.ion_in_hi, release ? t : -1);
+                if (release) {
+                    if (r >= g.cap) {
+                        atomicOr(a.err, ERR_CAPACITY);
+                    } else {
+                        const int64_t d = t * (int64_t)g.cap + (g.cap - 1 - r);
+                        a.ion_in.ox[d] = ox;
+                        if (DIM == 3) a.ion_in.oy[d] = oy;
+                        a.ion_in.oz[d] = oz;
+                        a.ion_in.w[d] = w;
+                        a.ion_in.cell[d] = pack_cell(g, ci, cj, ck);
+                        if (a.ion_in.id) a.ion_in.id[d] = pid;
+                    }
+                }
+            }
+            const bool keep_pair = valid && paired && !release;  // exactly zero net current
             // ---- Esirkepov windows; the warp agrees on their lengths
             real S0x[S + 2], DSx[S + 2], S0y[S + 2], DSy[S + 2], S0z[S + 2], DSz[S + 2];
             int ax = 0, ay = 0, az = 0;
             bool cx = false, cy = false, cz = false;
-            if (valid) {
+            if (valid && !keep_pair) {
                 ax = esirk_axis_c<S>(ox, x1, S0x, DSx, cx) + li + JL;
                 az = esirk_axis_c<S>(oz, z1, S0z, DSz, cz) + lk + JL;
                 if (DIM == 3) ay = esirk_axis_c<S>(oy, y1, S0y, DSy, cy) + lj + JL;
@@ -470,10 +498,13 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
             const unsigned sel = (__any_sync(0xffffffffu, cx) ? 4u : 0u) | (__any_sync(0xffffffffu, cy) ? 2u : 0u) |
                                  (__any_sync(0xffffffffu, cz) ? 1u : 0u);
             // 3D: no lane moved in x or y (e.g. plasma the laser has not reached)
-            const bool z_only = DIM == 3 && __all_sync(0xffffffffu, !valid || (x1 == ox && y1 == oy));
+            const bool z_only =
+                DIM == 3 && __all_sync(0xffffffffu, !valid || keep_pair || (x1 == ox && y1 == oy));
             int64_t dest = -1;
             int ni = 0, nj = 0, nk = 0;
-            if (valid) {
+            if (valid && keep_pair) {
+                // moved exactly like its ion: no deposit
+            } else if (valid) {
                 if (z_only) {
                     if (sel & 1u)
                         deposit_z<real, S, QX, QY, QN, S + 2>(sJ, S0x, S0y, S0z, DSz, ax, ay, az, a.jfac[2] * w);
@@ -484,6 +515,8 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
                                                           a.jfac[0] * w, a.jfac[1] * w, a.jfac[2] * w,
                                                           a.jyfac * w * vy);
                 }
+            }
+            if (valid) {
                 // new cell and offsets; an offset that rounds to 1 moves on
                 int sx = (int)floor(x1), sy = DIM == 3 ? (int)floor(y1) : 0, sz = (int)floor(z1);
                 ox = x1 - real(sx);
@@ -521,7 +554,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
                     a.out.ux[d] = ux;
                     a.out.uy[d] = uy;
                     a.out.uz[d] = uz;
-                    a.out.cell[d] = pack_cell(g, ni, nj, nk);
+                    a.out.cell[d] = (int32_t)((uint32_t)pack_cell(g, ni, nj, nk) | (keep_pair ? kPaired : 0u));
                     if (a.out.id) a.out.id[d] = pid;
                 }
             }
@@ -803,6 +836,7 @@ __global__ void rho_kernel(Geom g, Species<real> sp, const int *lo, const int *h
         const int n = n_lo + n_hi;
         for (int p = threadIdx.x; p < n; p += blockDim.x) {
             const int64_t s = bucket_slot(t, g.cap, n_lo, n_hi, p);
+            if ((uint32_t)sp.cell[s] & kPaired) continue;  // with its ion: no net charge
             int ci, cj, ck;
             unpack_cell(g, sp.cell[s], ci, cj, ck);
             real wx[S + 1], wy[S + 1], wz[S + 1];
@@ -846,12 +880,14 @@ void launch_rho(const Geom &g, const Species<real> &sp, const int *lo, const int
 // -------------------------------------------------------- particle sums
 
 // Kahan-compensated FP64 partial sums per block: [0] sum w (gamma-1),
-// [1] sum q w.  The host adds the block partials, also with compensation.
+// [1] sum q w (a paired electron and its ion carry no net charge), [2] the
+// number of paired electrons.  The host adds the block partials, also with
+// compensation.
 template <typename real>
 __global__ void particle_sums_kernel(Geom g, Species<real> sp, const int *lo, const int *hi, double q,
                                      double iux, double iuy, double iuz, double *partials)
 {
-    double s0 = 0, c0 = 0, s1 = 0, c1 = 0;
+    double s0 = 0, c0 = 0, s1 = 0, c1 = 0, npair = 0;
     for (int64_t t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
         int n_lo, n_hi;
         bucket_counts(lo, hi, t, g.cap, n_lo, n_hi, nullptr);
@@ -867,29 +903,34 @@ __global__ void particle_sums_kernel(Geom g, Species<real> sp, const int *lo, co
             }
             const double u2 = ux * ux + uy * uy + uz * uz;
             const double ke = w * (u2 / (sqrt(1.0 + u2) + 1.0));  // gamma - 1 without cancellation
+            const bool pair = ((uint32_t)sp.cell[s] & kPaired) != 0u;
+            npair += pair ? 1.0 : 0.0;
             double y = ke - c0, tt = s0 + y;
             c0 = (tt - s0) - y;
             s0 = tt;
-            y = q * w - c1;
+            y = (pair ? 0.0 : q * w) - c1;
             tt = s1 + y;
             c1 = (tt - s1) - y;
             s1 = tt;
         }
     }
-    __shared__ double red[2][256];
+    __shared__ double red[3][256];
     red[0][threadIdx.x] = s0 - c0;
     red[1][threadIdx.x] = s1 - c1;
+    red[2][threadIdx.x] = npair;
     __syncthreads();
     for (int off = blockDim.x / 2; off > 0; off >>= 1) {
         if ((int)threadIdx.x < off) {
             red[0][threadIdx.x] += red[0][threadIdx.x + off];
             red[1][threadIdx.x] += red[1][threadIdx.x + off];
+            red[2][threadIdx.x] += red[2][threadIdx.x + off];
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = red[0][0];
-        partials[2 * blockIdx.x + 1] = red[1][0];
+        partials[3 * blockIdx.x] = red[0][0];
+        partials[3 * blockIdx.x + 1] = red[1][0];
+        partials[3 * blockIdx.x + 2] = red[2][0];
     }
 }
 
