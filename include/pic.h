@@ -103,6 +103,8 @@ typedef struct pic_grid_params {
     int tile[3];            /* tile shape in cells: 0 or the compiled shape,     */
                             /* 8x8x8 in 3D, 16x1x16 in 2D (others: PIC_ERR_ARG) */
     int track_ids;          /* 1: carry an int64 lattice id with each particle */
+    int explicit_ions;      /* 1: store every drifting ion as its own record    */
+                            /* (0: electron-ion pairs, see pic_load_plasma)     */
     void *stream;           /* cudaStream_t for all device work (NULL: legacy)  */
 } pic_grid_params;
 

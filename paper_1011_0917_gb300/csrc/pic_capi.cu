@@ -361,6 +361,7 @@ static void fill_inject_common(pic_ctx *c, InjectArgs &a)
     for (int m = 0; m < 16; ++m) a.prof[m] = m < p.n_profile ? c->prof[m] : 0.0;
     a.seed = c->p.seed;
     a.drift_ions = (p.ions && c->ions_species) ? 1 : 0;
+    a.paired = (a.drift_ions && !c->p.explicit_ions) ? 1 : 0;
     a.precision = c->p.precision;
     side_raw(c, 0, c->cur[0], a.sp_e);
     a.hi_e = counts(c, 0, c->cur[0], 1);

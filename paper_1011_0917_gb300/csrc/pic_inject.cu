@@ -136,18 +136,25 @@ __global__ void inject_kernel(InjectArgs a)
         }
         // appended to the top run of the destination bucket
         const int re = reserve_slot(a.hi_e, dest);
-        const int ri = 0;
+        int ri = 0;
+        if (a.drift_ions && !a.paired) ri = reserve_slot(a.hi_i, dest);
         if (dest < 0) continue;
         // every reserved slot below the capacity is written, so a bucket never
         // holds a stale entry; an overflow drops the particle and is reported.
         // With drifting ions the electron is placed paired with its ion (one
         // record for both until a field reaches them).
-        const int32_t cell = (int32_t)((uint32_t)pack_cell(a.g, ci, cj, ck) | (a.drift_ions ? kPaired : 0u));
+        const int32_t cell = pack_cell(a.g, ci, cj, ck);
+        const int32_t ecell = (int32_t)((uint32_t)cell | (a.paired ? kPaired : 0u));
         const real uz = (real)a.uz0;
         if (re < a.g.cap)
-            store<real>(a.sp_e, dest * (int64_t)a.g.cap + (a.g.cap - 1 - re), ox, oy, oz, wr, uz, cell, L, true, dim3);
+            store<real>(a.sp_e, dest * (int64_t)a.g.cap + (a.g.cap - 1 - re), ox, oy, oz, wr, uz, ecell, L, true, dim3);
         else atomicOr(a.err, ERR_CAPACITY);
-        (void)ri;
+        if (a.drift_ions && !a.paired) {
+            if (ri < a.g.cap)
+                store<real>(a.sp_i, dest * (int64_t)a.g.cap + (a.g.cap - 1 - ri), ox, oy, oz, wr, uz, cell, L, false,
+                            dim3);
+            else atomicOr(a.err, ERR_CAPACITY);
+        }
     }
 }
 

@@ -253,7 +253,8 @@ struct InjectArgs {      // lattice load / boosted injection, FP64
     uint64_t seed;
     int mode;           // 0: in the box at t; 1: crossing z = Lz during (t, t1]
     double t, t1;
-    int drift_ions;     // ions drift with the plasma: electrons are placed paired
+    int drift_ions;     // ions drift with the plasma
+    int paired;         // electrons are placed paired with their ion (no ion record)
     int precision;      // 0 float, 1 double
     void *sp_e[9];      // ox oy oz w ux uy uz cell id of the electron side
     void *sp_i[9];      // same for the ion side (ux..uz unused)

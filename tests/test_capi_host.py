@@ -49,7 +49,7 @@ def grid(P, **kw):
     d.update(kw)
     return P.GridParams(d["dim"], d["nx"], d["ny"], d["nz"], d["dx"], d["dy"], d["dz"], d["cfl"], d["gamma_boost"],
                         d["shape_order"], d["filter_passes"], d["bc_z"], d["precision"], d["seed"],
-                        d["slots_per_cell"], (C.c_int * 3)(*d["tile"]), d["track_ids"], None)
+                        d["slots_per_cell"], (C.c_int * 3)(*d["tile"]), d["track_ids"], 0, None)
 
 
 @pytest.mark.parametrize("bad,status", [

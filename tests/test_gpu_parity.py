@@ -160,8 +160,9 @@ def _plasma_both(sim, o, O, p):
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
-@pytest.mark.parametrize("case", ["c0", "boost2d", "boost3d", "profile"])
-def test_plasma_load_matches_lattice(O, case, prec):
+@pytest.mark.parametrize("case,explicit", [("c0", False), ("boost2d", False), ("boost3d", False),
+                                           ("boost3d", True), ("profile", False)])
+def test_plasma_load_matches_lattice(O, case, explicit, prec):
     if case == "c0":
         st = W.stage("c0")
         g, p = st.grid, st.plasma
@@ -175,18 +176,21 @@ def test_plasma_load_matches_lattice(O, case, prec):
         g = dict(dim=2, nx=16, nz=200, dx=1.0, dz=1 / 16, gamma_boost=5.0, seed=9)
         p = dict(ne=0.002, z_start=50.0, z_end=400.0, ramp=3.0, ppc=(2, 1, 3), jitter=0.2, ions=1,
                  profile=(0.1, -0.05, 0.02, 0.0, 0.01, -0.02, 0.03, -0.01))
-    sim, o = make_pair(O, g, prec)
+    sim, o = make_pair(O, g, prec, explicit_ions=explicit)
     n = _plasma_both(sim, o, O, p)
     assert n > 100
+    if explicit or g.get("gamma_boost", 1.0) == 1.0:
+        assert sim.diagnostics().n_paired == 0
     _compare_particles(sim, o, 0, prec)
     if g.get("gamma_boost", 1.0) > 1.0:
         _compare_particles(sim, o, 1, prec)
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
-def test_injection_matches_oracle(O, prec):
+@pytest.mark.parametrize("explicit", [False, True])
+def test_injection_matches_oracle(O, explicit, prec):
     g = dict(dim=2, nx=12, nz=120, dx=1.0, dz=1 / 16, gamma_boost=5.0, filter_passes=1, seed=13)
-    sim, o = make_pair(O, g, prec)
+    sim, o = make_pair(O, g, prec, explicit_ions=explicit)
     zs = 5.0 * (o.Lz - 2.0)
     p = dict(ne=0.002, z_start=zs, z_end=zs + 5.0 * 40.0, ramp=1.0, ppc=(2, 1, 2), jitter=0.1, ions=1)
     _plasma_both(sim, o, O, p)
@@ -204,8 +208,8 @@ def test_injection_matches_oracle(O, prec):
     _compare_particles(sim, o, 1, prec, pos_tol=tol)
 
 
-def _run_steps_parity(O, g, p, laser, nsteps, prec, slots=16.0):
-    sim, o = make_pair(O, g, prec, slots_per_cell=slots)
+def _run_steps_parity(O, g, p, laser, nsteps, prec, slots=16.0, explicit=False):
+    sim, o = make_pair(O, g, prec, slots_per_cell=slots, explicit_ions=explicit)
     if p is not None:
         _plasma_both(sim, o, O, p)
     if laser is not None:
@@ -263,7 +267,8 @@ def test_c0_window_laser_in_plasma(O, prec):
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
-def test_boosted_2d_50_steps_with_injection(O, prec):
+@pytest.mark.parametrize("explicit", [False, True])
+def test_boosted_2d_50_steps_with_injection(O, explicit, prec):
     # gamma = 13, plasma 10 cells from the antenna streaming in through z = Lz;
     # the laser meets the plasma within the window
     g = dict(dim=2, nx=32, nz=256, dx=1.0, dz=1 / 32, gamma_boost=13.0, filter_passes=2, seed=17)
@@ -271,21 +276,26 @@ def test_boosted_2d_50_steps_with_injection(O, prec):
     hz = (1 / 32) * 13 * (1 + beta)
     p = dict(ne=0.004, z_start=13 * 10 * hz, z_end=13 * 600 * hz, ramp=2.0, ppc=(2, 1, 2), jitter=0.1, ions=1)
     laser = dict(a0=4.0, waist=8.0, fwhm=2.0, t_peak=0.5)
-    sim, o = _run_steps_parity(O, g, p, laser, 50, prec)
+    sim, o = _run_steps_parity(O, g, p, laser, 50, prec, explicit=explicit)
     err = vector_errors(sim, o)
     assert max(err.values()) < TOL50[prec], err
     d = sim.diagnostics()
     assert d.n_particles[0] == o.num(0) and d.n_particles[1] == o.num(1)
+    if explicit:
+        assert d.n_paired == 0
+    else:
+        assert 0 < d.n_paired < d.n_particles[0]  # some pairs were released by the laser
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
-def test_3d_boosted_30_steps(O, prec):
+@pytest.mark.parametrize("explicit", [False, True])
+def test_3d_boosted_30_steps(O, explicit, prec):
     g = dict(dim=3, nx=16, ny=16, nz=48, dx=1.0, dy=1.0, dz=1 / 32, gamma_boost=13.0, filter_passes=2, seed=19)
     beta = math.sqrt(1 - 1 / 169.0)
     hz = (1 / 32) * 13 * (1 + beta)
     p = dict(ne=0.004, z_start=13 * 6 * hz, z_end=13 * 200 * hz, ramp=2.0, ppc=(2, 2, 2), jitter=0.1, ions=1)
     laser = dict(a0=4.0, waist=4.0, fwhm=2.0, t_peak=0.5)
-    sim, o = _run_steps_parity(O, g, p, laser, 30, prec)
+    sim, o = _run_steps_parity(O, g, p, laser, 30, prec, explicit=explicit)
     err = vector_errors(sim, o)
     assert max(err.values()) < TOL50[prec], err
 
