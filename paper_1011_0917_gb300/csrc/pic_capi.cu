@@ -45,7 +45,8 @@ struct StateHeader {
     int64_t step;
     pic_laser_params laser;
     int32_t cur[2];
-    char pad[512 - 8 - 8 * 4 - 16 - 8 - 8 - sizeof(pic_laser_params) - 8];
+    double wmax;  // bound of the particle weights (fixed-point current scales)
+    char pad[512 - 8 - 8 * 4 - 16 - 8 - 8 - sizeof(pic_laser_params) - 8 - 8];
 };
 static_assert(sizeof(StateHeader) == 512, "state header must be 512 bytes");
 
@@ -69,6 +70,10 @@ struct pic_ctx {
     unsigned char *species[2] = {nullptr, nullptr};
     unsigned char *scratch = nullptr;
     int cur[2] = {0, 0};
+
+    // largest |weight| any particle loaded so far carries (weights never
+    // change), the bound of the fixed-point current scales
+    double wmax = 0;
 
     bool plasma_loaded = false;
     pic_plasma_params plasma{};
@@ -404,6 +409,13 @@ extern "C" pic_status pic_load_plasma(pic_ctx *c, const pic_plasma_params *p)
     c->plasma_loaded = true;
     InjectArgs a{};
     fill_inject_common(c, a);
+    {
+        // the lab density is at most ne (1 + sum |c_m|); the margin covers the
+        // rounding of the weight to the working precision
+        double f = 1.0;
+        for (int m = 0; m < p->n_profile; ++m) f += std::fabs(p->profile[m]);
+        c->wmax = std::max(c->wmax, std::fabs(p->ne_over_nc) * f * a.wfac * (1.0 + 1e-6));
+    }
     a.mode = 0;
     a.t = c->t;
     a.t1 = c->t;
@@ -477,12 +489,14 @@ static pic_status load_particles_t(pic_ctx *c, int sp, int64_t n, const double *
     for (int a = 0; a < 9; ++a)
         if (c->side[sp].off[a] != SIZE_MAX) cols[a].resize((size_t)n * attr_size(c, a));
     auto R = [&](int a) { return reinterpret_cast<real *>(cols[a].data()); };
+    double wmax = 0;
     for (int64_t i = 0; i < n; ++i) {
         double x = state[0 * n + i], y = state[1 * n + i], z = state[2 * n + i];
         int ci = 0, cj = 0, ck = 0;
         real ox, oy = 0, oz;
         if (!(x >= 0 && x < c->Lx) || !(z >= 0 && z < c->Lz) || (dim3 && !(y >= 0 && y < c->Ly)))
             return fail(c, PIC_ERR_ARG, "particle outside the box");
+        if (!std::isfinite(state[6 * n + i])) return fail(c, PIC_ERR_ARG, "non-finite particle weight");
         if (!host_to_cell<real>(x, c->hx, c->g.nx, true, ci, ox) ||
             !host_to_cell<real>(z, c->hz, c->g.nz, c->g.bc_z == 0, ck, oz) ||
             (dim3 && !host_to_cell<real>(y, c->hy, c->g.ny, true, cj, oy)))
@@ -491,6 +505,7 @@ static pic_status load_particles_t(pic_ctx *c, int sp, int64_t n, const double *
         if (dim3) R(1)[i] = oy;
         R(2)[i] = oz;
         R(3)[i] = (real)state[6 * n + i];
+        wmax = std::max(wmax, std::fabs(state[6 * n + i]) * (1.0 + 1e-6));
         if (sp == 0) {
             R(4)[i] = (real)state[3 * n + i];
             R(5)[i] = (real)state[4 * n + i];
@@ -501,6 +516,7 @@ static pic_status load_particles_t(pic_ctx *c, int sp, int64_t n, const double *
     }
     const void *ptrs[9];
     for (int a = 0; a < 9; ++a) ptrs[a] = cols[a].empty() ? nullptr : cols[a].data();
+    c->wmax = std::max(c->wmax, wmax);
     return upload_flat<real>(c, sp, n, ptrs, 0);
 }
 
@@ -533,6 +549,42 @@ extern "C" pic_status pic_launch_laser(pic_ctx *c, const pic_laser_params *p)
 
 // ---------------------------------------------------------------------- step
 
+// Scales of the FP32 fixed-point current accumulation (see sh_acc).  Every
+// contribution of one particle to one node of a component is at most
+// C_c = |f_c| w_max in magnitude (f_c the component's current factor before
+// the weight: the running sums of the shape differences lie in [-1, 1], the
+// path-averaged shape products in [0, 1], |v_y| < 1), and a node of a tile
+// receives at most one contribution per particle of the tile, at most cap of
+// them.  The scale lim / C_c with lim = min(2^30 / cap, 2^21) keeps every
+// rounded contribution below 2^21 and every node's "hi" sum below
+// 2^30 + cap / 2; the "lo" words take K = min(22, 30 - ceil(log2 cap)) bits
+// of the remainders, so their sums stay below cap 2^(K-1) <= 2^29.  The
+// scales are the same for electrons and ions, so the contributions of an
+// electron and an ion on the same path cancel exactly.
+template <typename real>
+static void fixed_point_scales(const pic_ctx *c, real scale[3], real quant[3], real lo[2])
+{
+    if (sizeof(real) != 4) {
+        for (int q = 0; q < 3; ++q) scale[q] = quant[q] = real(1);
+        lo[0] = lo[1] = real(1);
+        return;
+    }
+    const int cap = c->g.cap;
+    int lg = 0;
+    while ((1LL << lg) < (long long)cap) ++lg;  // ceil(log2 cap)
+    const int k = std::min(22, 30 - lg);
+    const double lim = std::min(std::ldexp(1.0, 30) / cap, std::ldexp(1.0, 21));
+    const double f[3] = {c->hx / (c->dt * c->vol), c->g.dim == 3 ? c->hy / (c->dt * c->vol) : 1.0 / c->vol,
+                         c->hz / (c->dt * c->vol)};
+    for (int q = 0; q < 3; ++q) {
+        const double cb = f[q] * c->wmax;
+        scale[q] = cb > 0 ? (real)(lim / cb) : real(0);
+        quant[q] = cb > 0 ? (real)(cb / lim) : real(0);
+    }
+    lo[0] = (real)std::ldexp(1.0, k);
+    lo[1] = (real)std::ldexp(1.0, -k);
+}
+
 template <typename real>
 static PushArgs<real> push_args(pic_ctx *c, int sp)
 {
@@ -563,6 +615,7 @@ static PushArgs<real> push_args(pic_ctx *c, int sp)
     a.ion_u[0] = 0;
     a.ion_u[1] = 0;
     a.ion_u[2] = (real)(-(c->gam * c->beta));
+    fixed_point_scales(c, a.fx_scale, a.fx_quant, a.fx_lo);
     if (c->ions_species) {
         a.ion_in = species_view<real>(c, 1, c->cur[1]);
         a.ion_in_hi = counts(c, 1, c->cur[1], 1);
@@ -995,7 +1048,7 @@ template <typename real>
 static pic_status get_state_t(pic_ctx *c, unsigned char *dst, size_t dst_bytes, int dst_is_device)
 {
     StateHeader h{};
-    std::memcpy(h.magic, "PICSTAT1", 8);
+    std::memcpy(h.magic, "PICSTAT2", 8);
     h.dim = c->g.dim;
     h.nx = c->g.nx;
     h.ny = c->g.ny;
@@ -1007,6 +1060,7 @@ static pic_status get_state_t(pic_ctx *c, unsigned char *dst, size_t dst_bytes, 
     h.t = c->t;
     h.step = c->step;
     h.laser = c->laser;
+    h.wmax = c->wmax;
     int64_t n[2] = {0, 0};
     for (int sp = 0; sp < (c->ions_species ? 2 : 1); ++sp) {
         pic_status s = compact_t<real>(c, sp, n[sp]);
@@ -1050,9 +1104,10 @@ static pic_status set_state_t(pic_ctx *c, const unsigned char *src, size_t src_b
     if (src_bytes < sizeof(h)) return fail(c, PIC_ERR_ARG, "snapshot too small");
     CUDA_TRY(c, cudaMemcpyAsync(&h, src, sizeof(h), src_is_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    if (std::memcmp(h.magic, "PICSTAT1", 8) != 0 || h.dim != c->g.dim || h.nx != c->g.nx || h.ny != c->g.ny ||
+    if (std::memcmp(h.magic, "PICSTAT2", 8) != 0 || h.dim != c->g.dim || h.nx != c->g.nx || h.ny != c->g.ny ||
         h.nz != c->g.nz || h.precision != c->p.precision || h.track_ids != c->p.track_ids ||
-        h.has_ions != (int)c->ions_species || h.n[0] < 0 || h.n[1] < 0 || h.n[0] > c->slots || h.n[1] > c->slots)
+        h.has_ions != (int)c->ions_species || h.n[0] < 0 || h.n[1] < 0 || h.n[0] > c->slots || h.n[1] > c->slots ||
+        !(h.wmax >= 0) || !std::isfinite(h.wmax))
         return fail(c, PIC_ERR_ARG, "snapshot does not match this grid");
     const size_t need = sizeof(StateHeader) + c->field_bytes + species_state_bytes(c, 0, h.n[0]) +
                         (c->ions_species ? species_state_bytes(c, 1, h.n[1]) : 0);
@@ -1072,6 +1127,7 @@ static pic_status set_state_t(pic_ctx *c, const unsigned char *src, size_t src_b
         pic_status s = upload_flat<real>(c, sp, h.n[sp], cols, src_is_device);
         if (s != PIC_OK) return s;
     }
+    c->wmax = h.wmax;
     c->t = h.t;
     c->step = h.step;
     c->laser_on = h.laser_on != 0;

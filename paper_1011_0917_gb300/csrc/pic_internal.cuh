@@ -220,6 +220,11 @@ struct PushArgs {
     real jfac[3];       // -q h_d / (dt V): multiplied by w and the running sum
     real jyfac;         // q / V (2D out-of-plane current, times w vy)
     real ion_u[3];      // drift momentum of the ion species
+    // fixed-point current accumulation (FP32; FP64 uses 1): the per-particle
+    // factors of Jx, Jy (2D: the out-of-plane factor), Jz are multiplied by
+    // fx_scale[c]; a shared-tile node's integer sum times fx_quant[c] =
+    // 1 / fx_scale[c] is its current; fx_lo = {2^K, 2^-K} scales the "lo" words
+    real fx_scale[3], fx_quant[3], fx_lo[2];
     Species<real> ion_in;  // ion side the IONS phase reads next (released ions go there)
     int *ion_in_hi;        // its top-run lengths
     unsigned *err;

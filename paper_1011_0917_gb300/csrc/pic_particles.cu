@@ -16,10 +16,11 @@
 namespace pic {
 
 // threads per CTA of the particle kernels; resident CTAs per SM the push
-// kernel is compiled for (FP32: 4, i.e. 64 registers a thread; the FP64 debug
-// path keeps more registers)
+// kernel is compiled for (FP32: 3, which its shared memory allows on a 3D
+// tile, i.e. up to 80 registers a thread; the FP64 debug path keeps more
+// registers)
 constexpr int kBlock = 256;
-template <typename real> struct MinBlocks { static constexpr int value = sizeof(real) == 4 ? 4 : 2; };
+template <typename real> struct MinBlocks { static constexpr int value = sizeof(real) == 4 ? 3 : 2; };
 
 // ---------------------------------------------------------------- helpers
 
@@ -45,12 +46,43 @@ __device__ __forceinline__ int esirk_axis(real x0, real x1, real S0[S + 2], real
     return anchor;
 }
 
-// shared-memory accumulation of one Esirkepov contribution; exact zeros
-// (nodes of the window outside both supports) are not added
-template <typename real>
-__device__ __forceinline__ void sh_add(real *p, real v)
+// Shared-memory current accumulators.  FP32 currents are accumulated exactly,
+// in 64-bit fixed point split over two 32-bit integer words per node: a
+// contribution p = a*b, already multiplied by the launch's fixed-point scale
+// (PushArgs::fx_scale, |p| < 2^21), is split into its nearest integer h and
+// the remainder r = p - h (exact, |r| <= 1/2), and h and round(r 2^K) go to
+// the "hi" and "lo" words with native integer atomics.  Integer addition is
+// exact and associative, so a tile's sums do not depend on the order in which
+// its particles are processed, and they carry the contributions to 2^-K.
+// The "lo" word of a node sits LOFF words after its "hi" word.  FP64
+// accumulates in double.  Exact zeros (nodes of a window outside both
+// supports) are not added.
+template <typename real> struct Acc { using type = double; };
+template <> struct Acc<float> { using type = int; };
+
+// adding 1.5 * 2^23 to x (|x| <= 2^22) leaves round(x) in the low mantissa
+// bits, which are read back as an integer
+constexpr float kRoundMagic = 12582912.0f;
+constexpr int kRoundMagicBits = 0x4B400000;
+
+template <int LOFF>
+__device__ __forceinline__ void sh_acc(int *p, float a, float b, float lo_scale)
 {
-    if (v != real(0)) atomicAdd(p, v);
+    const float v = a * b;
+    if (v == 0.f) return;
+    const float t = v + kRoundMagic;
+    const int h = __float_as_int(t) - kRoundMagicBits;
+    const float r = v - (t - kRoundMagic);
+    const int l = __float_as_int(fmaf(r, lo_scale, kRoundMagic)) - kRoundMagicBits;
+    if (h != 0) atomicAdd(p, h);
+    if (l != 0) atomicAdd(p + LOFF, l);
+}
+
+template <int LOFF>
+__device__ __forceinline__ void sh_acc(double *p, double a, double b, double)
+{
+    const double v = a * b;
+    if (v != 0.0) atomicAdd(p, v);
 }
 
 // periodic index for i in [-n, 2n)
@@ -101,16 +133,26 @@ __device__ __forceinline__ void stage_tile(const Geom &g, const Ptr6<real> src, 
 
 // Add NC shared-memory tiles (box [lo - L, lo - L + Q) per axis) to the global
 // arrays, element-wise over all threads: non-zero nodes only, periodic x and y,
-// nodes outside a component's valid z range dropped (absorbing z).
+// nodes outside a component's valid z range dropped (absorbing z).  FP32
+// tiles hold fixed-point "hi" and "lo" words (see sh_acc): the node's value is
+// (hi + lo lo_inv) times the component's quantum q_c.
 template <typename real, int DIM, int NC, int QX, int QY, int QZ, int L>
-__device__ __forceinline__ void flush_tile(const Geom &g, const Ptr3<real> dstJ, unsigned half_z, const real *src,
-                                           int lox, int loy, int loz)
+__device__ __forceinline__ void flush_tile(const Geom &g, const Ptr3<real> dstJ, unsigned half_z,
+                                           const typename Acc<real>::type *src, real q0, real q1, real q2,
+                                           real lo_inv, int lox, int loy, int loz)
 {
     constexpr int QN = QX * QY * QZ;
     const bool tiny = g.nx < QX || (DIM == 3 && g.ny < QY);
     for (int q = threadIdx.x; q < NC * QN; q += blockDim.x) {
-        const real v = src[q];
-        if (v == real(0)) continue;
+        real v;
+        if constexpr (sizeof(real) == 4) {
+            const int h = src[q], l = src[NC * QN + q];  // the node's "hi" and "lo" words
+            if ((h | l) == 0) continue;
+            v = fmaf((float)l, lo_inv, (float)h);
+        } else {
+            v = src[q];
+            if (v == real(0)) continue;
+        }
         const int c = q / QN, r = q - c * QN;
         const int lz = r / (QX * QY), r2 = r - lz * (QX * QY);
         const int ly = r2 / QX, lx = r2 - ly * QX;
@@ -119,7 +161,7 @@ __device__ __forceinline__ void flush_tile(const Geom &g, const Ptr3<real> dstJ,
         else if (gk < 0 || gk > zmax_of(g, (half_z >> c) & 1u)) continue;
         const int gi = tiny ? wrapi(lox - L + lx, g.nx) : wrap1(lox - L + lx, g.nx);
         const int gj = DIM == 3 ? (tiny ? wrapi(loy - L + ly, g.ny) : wrap1(loy - L + ly, g.ny)) : 0;
-        atomicAdd(dstJ[c] + fidx(g, gi, gj, gk), v);
+        atomicAdd(dstJ[c] + fidx(g, gi, gj, gk), v * (c == 0 ? q0 : c == 1 ? q1 : q2));
     }
 }
 
@@ -212,12 +254,13 @@ __device__ __forceinline__ int esirk_axis_c(real x0, real x1, real S0[S + 2], re
 // window is zero and is not added.  In 2D3V the out-of-plane current is the
 // path average of the shape times q w vy / V.
 template <typename real, int DIM, int S, int QX, int QY, int QN, int WX, int WY, int WZ>
-__device__ __forceinline__ void deposit_w(real *sJ, const real *S0x, const real *DSx, const real *S0y,
+__device__ __forceinline__ void deposit_w(typename Acc<real>::type *sJ, const real *S0x, const real *DSx, const real *S0y,
                                           const real *DSy, const real *S0z, const real *DSz, int ax, int ay, int az,
-                                          real fx, real fy, real fz, real fyv)
+                                          real fx, real fy, real fz, real fyv, real los)
 {
+    constexpr int LOFF = 3 * QN;  // "lo" words follow the three components' "hi" words
     constexpr real half = real(0.5), third = real(1) / real(3);
-    real *Jx = sJ, *Jy = sJ + QN, *Jz = sJ + 2 * QN;
+    auto *Jx = sJ, *Jy = sJ + QN, *Jz = sJ + 2 * QN;
     real Px[WX], Pz[WZ];
     real acc = 0;
 #pragma unroll
@@ -236,16 +279,16 @@ __device__ __forceinline__ void deposit_w(real *sJ, const real *S0x, const real 
 #pragma unroll
             for (int b = 0; b < WY; ++b) {
                 const real tyz = S0y[b] * za + DSy[b] * zb;
-                real *row = Jx + ((az + c) * QY + (ay + b)) * QX + ax;
+                auto *row = Jx + ((az + c) * QY + (ay + b)) * QX + ax;
 #pragma unroll
-                for (int q = 0; q < WX - 1; ++q) sh_add(row + q, Px[q] * tyz);
+                for (int q = 0; q < WX - 1; ++q) sh_acc<LOFF>(row + q, Px[q], tyz, los);
             }
 #pragma unroll
             for (int q = 0; q < WX; ++q) {
                 const real tzx = S0z[c] * (S0x[q] + half * DSx[q]) + DSz[c] * (half * S0x[q] + third * DSx[q]);
-                real *col = Jy + ((az + c) * QY + ay) * QX + ax + q;
+                auto *col = Jy + ((az + c) * QY + ay) * QX + ax + q;
 #pragma unroll
-                for (int b = 0; b < WY - 1; ++b) sh_add(col + b * QX, Py[b] * tzx);
+                for (int b = 0; b < WY - 1; ++b) sh_acc<LOFF>(col + b * QX, Py[b], tzx, los);
             }
         }
 #pragma unroll
@@ -254,26 +297,26 @@ __device__ __forceinline__ void deposit_w(real *sJ, const real *S0x, const real 
 #pragma unroll
             for (int q = 0; q < WX; ++q) {
                 const real txy = S0x[q] * ya + DSx[q] * yb;
-                real *col = Jz + (az * QY + (ay + b)) * QX + ax + q;
+                auto *col = Jz + (az * QY + (ay + b)) * QX + ax + q;
 #pragma unroll
-                for (int c = 0; c < WZ - 1; ++c) sh_add(col + c * QX * QY, Pz[c] * txy);
+                for (int c = 0; c < WZ - 1; ++c) sh_acc<LOFF>(col + c * QX * QY, Pz[c], txy, los);
             }
         }
     } else {
 #pragma unroll
         for (int c = 0; c < WZ; ++c) {
             const real za = S0z[c] + half * DSz[c], zb = half * S0z[c] + third * DSz[c];
-            real *row = Jx + (az + c) * QX + ax;
+            auto *row = Jx + (az + c) * QX + ax;
 #pragma unroll
-            for (int q = 0; q < WX - 1; ++q) sh_add(row + q, Px[q] * za);
+            for (int q = 0; q < WX - 1; ++q) sh_acc<LOFF>(row + q, Px[q], za, los);
 #pragma unroll
-            for (int q = 0; q < WX; ++q) sh_add(Jy + (az + c) * QX + ax + q, fyv * (S0x[q] * za + DSx[q] * zb));
+            for (int q = 0; q < WX; ++q) sh_acc<LOFF>(Jy + (az + c) * QX + ax + q, fyv, S0x[q] * za + DSx[q] * zb, los);
         }
 #pragma unroll
         for (int q = 0; q < WX; ++q) {
             const real xa = S0x[q] + half * DSx[q];
 #pragma unroll
-            for (int c = 0; c < WZ - 1; ++c) sh_add(Jz + (az + c) * QX + ax + q, Pz[c] * xa);
+            for (int c = 0; c < WZ - 1; ++c) sh_acc<LOFF>(Jz + (az + c) * QX + ax + q, Pz[c], xa, los);
         }
     }
 }
@@ -283,10 +326,11 @@ __device__ __forceinline__ void deposit_w(real *sJ, const real *S0x, const real 
 // -- the general formula's values with DSx = DSy = 0.  Windows along x and y
 // have S+1 nodes (their supports did not move).
 template <typename real, int S, int QX, int QY, int QN, int WZ>
-__device__ __forceinline__ void deposit_z(real *sJ, const real *S0x, const real *S0y, const real *S0z,
-                                          const real *DSz, int ax, int ay, int az, real fz)
+__device__ __forceinline__ void deposit_z(typename Acc<real>::type *sJ, const real *S0x, const real *S0y, const real *S0z,
+                                          const real *DSz, int ax, int ay, int az, real fz, real los)
 {
-    real *Jz = sJ + 2 * QN;
+    constexpr int LOFF = 3 * QN;
+    auto *Jz = sJ + 2 * QN;
     real Pz[WZ];
     real acc = 0;
 #pragma unroll
@@ -297,22 +341,22 @@ __device__ __forceinline__ void deposit_z(real *sJ, const real *S0x, const real 
 #pragma unroll
         for (int q = 0; q < S + 1; ++q) {
             const real txy = S0x[q] * S0y[b];
-            real *col = Jz + (az * QY + (ay + b)) * QX + ax + q;
+            auto *col = Jz + (az * QY + (ay + b)) * QX + ax + q;
 #pragma unroll
-            for (int c = 0; c < WZ - 1; ++c) sh_add(col + c * QX * QY, Pz[c] * txy);
+            for (int c = 0; c < WZ - 1; ++c) sh_acc<LOFF>(col + c * QX * QY, Pz[c], txy, los);
         }
     }
 }
 
 // picks the window lengths for the warp: bit 2 x, bit 1 y, bit 0 z crossed
 template <typename real, int DIM, int S, int QX, int QY, int QN>
-__device__ __forceinline__ void deposit_sel(unsigned sel, real *sJ, const real *S0x, const real *DSx, const real *S0y,
+__device__ __forceinline__ void deposit_sel(unsigned sel, typename Acc<real>::type *sJ, const real *S0x, const real *DSx, const real *S0y,
                                             const real *DSy, const real *S0z, const real *DSz, int ax, int ay, int az,
-                                            real fx, real fy, real fz, real fyv)
+                                            real fx, real fy, real fz, real fyv, real los)
 {
     constexpr int A = S + 1, B = S + 2;
 #define PIC_DEP(wx, wy, wz) \
-    deposit_w<real, DIM, S, QX, QY, QN, wx, wy, wz>(sJ, S0x, DSx, S0y, DSy, S0z, DSz, ax, ay, az, fx, fy, fz, fyv)
+    deposit_w<real, DIM, S, QX, QY, QN, wx, wy, wz>(sJ, S0x, DSx, S0y, DSy, S0z, DSz, ax, ay, az, fx, fy, fz, fyv, los)
     if (DIM == 3) {
         switch (sel) {
         case 0: PIC_DEP(A, A, A); break;
@@ -349,12 +393,13 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
     constexpr int FX = TX + FL + FH, FY = DIM == 3 ? TY + FL + FH : 1, FZ = TZ + FL + FH;
     constexpr int QX = TX + JL + JH, QY = DIM == 3 ? TY + JL + JH : 1, QZ = TZ + JL + JH;
     constexpr int FN = FX * FY * FZ, QN = QX * QY * QZ;
+    using acc_t = typename Acc<real>::type;
     real *sF = reinterpret_cast<real *>(smem_raw);
-    real *sJ = sF + 6 * FN;
+    acc_t *sJ = reinterpret_cast<acc_t *>(sF + 6 * FN);
     // the next iteration's particle records are copied into shared memory
     // with cp.async while the current ones are pushed (two buffers of
     // 8 attributes x kBlock particles; each thread copies and reads its own)
-    real *sP = sJ + 3 * QN;
+    real *sP = reinterpret_cast<real *>(sJ + (sizeof(real) == 4 ? 6 : 3) * QN);
     __shared__ int s_stay;
 
     for (int64_t t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
@@ -388,7 +433,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
         // Ez, Bx, By live on half-integer z (bits 2, 3, 4)
         stage_tile<real, DIM, 6, FX, FY, FZ, FL>(g, Ptr6<real>{a.E[0], a.E[1], a.E[2], a.B[0], a.B[1], a.B[2]},
                                                  0x1Cu, sF, lox, loy, loz);
-        for (int q = threadIdx.x; q < 3 * QN; q += blockDim.x) sJ[q] = 0;
+        for (int q = threadIdx.x; q < (sizeof(real) == 4 ? 6 : 3) * QN; q += blockDim.x) sJ[q] = 0;
         prefetch(0);
         __syncthreads();
 
@@ -505,15 +550,17 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
             if (valid && keep_pair) {
                 // moved exactly like its ion: no deposit
             } else if (valid) {
+                const real fz = a.jfac[2] * w * a.fx_scale[2];
                 if (z_only) {
                     if (sel & 1u)
-                        deposit_z<real, S, QX, QY, QN, S + 2>(sJ, S0x, S0y, S0z, DSz, ax, ay, az, a.jfac[2] * w);
+                        deposit_z<real, S, QX, QY, QN, S + 2>(sJ, S0x, S0y, S0z, DSz, ax, ay, az, fz, a.fx_lo[0]);
                     else
-                        deposit_z<real, S, QX, QY, QN, S + 1>(sJ, S0x, S0y, S0z, DSz, ax, ay, az, a.jfac[2] * w);
+                        deposit_z<real, S, QX, QY, QN, S + 1>(sJ, S0x, S0y, S0z, DSz, ax, ay, az, fz, a.fx_lo[0]);
                 } else {
                     deposit_sel<real, DIM, S, QX, QY, QN>(sel, sJ, S0x, DSx, S0y, DSy, S0z, DSz, ax, ay, az,
-                                                          a.jfac[0] * w, a.jfac[1] * w, a.jfac[2] * w,
-                                                          a.jyfac * w * vy);
+                                                          a.jfac[0] * w * a.fx_scale[0],
+                                                          a.jfac[1] * w * a.fx_scale[1], fz,
+                                                          a.jyfac * w * vy * a.fx_scale[1], a.fx_lo[0]);
                 }
             }
             if (valid) {
@@ -561,7 +608,8 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
         }
         __syncthreads();
         // flush the J tile: one global add per non-zero node
-        flush_tile<real, DIM, 3, QX, QY, QZ, JL>(g, Ptr3<real>{a.J[0], a.J[1], a.J[2]}, 0x4u, sJ, lox, loy, loz);
+        flush_tile<real, DIM, 3, QX, QY, QZ, JL>(g, Ptr3<real>{a.J[0], a.J[1], a.J[2]}, 0x4u, sJ, a.fx_quant[0],
+                                                 a.fx_quant[1], a.fx_quant[2], a.fx_lo[1], lox, loy, loz);
         if (threadIdx.x == 0) {
             a.out_lo[t] = min(s_stay, g.cap);
             a.in_lo[t] = 0;
@@ -583,8 +631,11 @@ __global__ void __launch_bounds__(kBlock) ion_kernel(PushArgs<real> a)
     constexpr int JL = S, JH = S + 1;
     constexpr int QX = TX + JL + JH, QY = DIM == 3 ? TY + JL + JH : 1, QZ = TZ + JL + JH;
     constexpr int QN = QX * QY * QZ;
-    real *sJ = reinterpret_cast<real *>(smem_raw);
-    real *sP = sJ + QN;  // prefetched records: 2 buffers x 5 attributes x kBlock
+    using acc_t = typename Acc<real>::type;
+    acc_t *sJ = reinterpret_cast<acc_t *>(smem_raw);
+    // prefetched records after the J tile ("hi" and, in FP32, "lo" words):
+    // 2 buffers x 5 attributes x kBlock
+    real *sP = reinterpret_cast<real *>(sJ + (sizeof(real) == 4 ? 2 : 1) * QN);
     const real ig = inv_gamma(a.ion_u[0], a.ion_u[1], a.ion_u[2]);
     const real dx = a.ion_u[0] * ig * a.dtdh[0];
     const real dy = DIM == 3 ? a.ion_u[1] * ig * a.dtdh[1] : real(0);
@@ -615,7 +666,7 @@ __global__ void __launch_bounds__(kBlock) ion_kernel(PushArgs<real> a)
         const int lox = tix << g.lt[0], loy = tiy << g.lt[1], loz = tiz << g.lt[2];
         __syncthreads();
         if (threadIdx.x == 0) s_stay = 0;
-        for (int q = threadIdx.x; q < QN; q += blockDim.x) sJ[q] = 0;
+        for (int q = threadIdx.x; q < (sizeof(real) == 4 ? 2 : 1) * QN; q += blockDim.x) sJ[q] = 0;
         prefetch(0);
         __syncthreads();
         for (int it = 0; it * kBlock < n; ++it) {
@@ -648,7 +699,7 @@ __global__ void __launch_bounds__(kBlock) ion_kernel(PushArgs<real> a)
                     const int bx = spline_weights<S>(ox, wx) + li + JL;
                     int by = 0;
                     if (DIM == 3) by = spline_weights<S>(oy, wy) + lj + JL;
-                    const real fz = a.jfac[2] * w;
+                    const real fz = a.jfac[2] * w * a.fx_scale[2];
                     real Pz[S + 2];
                     real acc = 0;
 #pragma unroll
@@ -660,7 +711,7 @@ __global__ void __launch_bounds__(kBlock) ion_kernel(PushArgs<real> a)
                             const real sxy = DIM == 3 ? wx[q] * wy[b] : wx[q];
 #pragma unroll
                             for (int c = 0; c < S + 1; ++c)
-                                sh_add(sJ + ((az + c) * QY + (by + b)) * QX + bx + q, Pz[c] * sxy);
+                                sh_acc<QN>(sJ + ((az + c) * QY + (by + b)) * QX + bx + q, Pz[c], sxy, a.fx_lo[0]);
                         }
                     }
                     int sx = (int)floor(x1), sy = DIM == 3 ? (int)floor(y1) : 0, sz = (int)floor(z1);
@@ -702,7 +753,8 @@ __global__ void __launch_bounds__(kBlock) ion_kernel(PushArgs<real> a)
             }
         }
         __syncthreads();
-        flush_tile<real, DIM, 1, QX, QY, QZ, JL>(g, Ptr3<real>{a.J[2], a.J[2], a.J[2]}, 0x1u, sJ, lox, loy, loz);
+        flush_tile<real, DIM, 1, QX, QY, QZ, JL>(g, Ptr3<real>{a.J[2], a.J[2], a.J[2]}, 0x1u, sJ, a.fx_quant[2],
+                                                 a.fx_quant[2], a.fx_quant[2], a.fx_lo[1], lox, loy, loz);
         if (threadIdx.x == 0) {
             a.out_lo[t] = min(s_stay, g.cap);
             a.in_lo[t] = 0;
@@ -720,8 +772,10 @@ static size_t push_smem(bool ions)
 {
     const int FN = (TX + 1 + S) * (DIM == 3 ? TY + 1 + S : 1) * (TZ + 1 + S);
     const int QN = (TX + 2 * S + 1) * (DIM == 3 ? TY + 2 * S + 1 : 1) * (TZ + 2 * S + 1);
-    return ions ? sizeof(real) * (size_t)(QN + 2 * 5 * kBlock)
-                : sizeof(real) * (size_t)(6 * FN + 3 * QN + 2 * 8 * kBlock);
+    // FP32 currents take two words per node ("hi" and "lo"), FP64 one
+    const int JW = sizeof(real) == 4 ? 2 : 1;
+    return ions ? sizeof(real) * (size_t)(JW * QN + 2 * 5 * kBlock)
+                : sizeof(real) * (size_t)(6 * FN + JW * 3 * QN + 2 * 8 * kBlock);
 }
 
 template <typename real, int DIM, int S, int TX, int TY, int TZ>
