@@ -64,6 +64,11 @@ struct pic_ctx {
     int64_t slots = 0;
     SideLayout side[2]{};
     size_t off_cnt = 0, off_tmp = 0, off_offsets = 0, off_partials = 0, off_err = 0;
+    // E and B live in two buffers that the Yee kernel alternates between (it
+    // reads one and writes the other): the field buffer (fset 0) and a copy of
+    // its first six components in scratch (fset 1)
+    size_t off_eb = 0;
+    int fset = 0;
 
     bool bound = false;
     unsigned char *fields = nullptr;
@@ -122,7 +127,18 @@ static int *counts(pic_ctx *c, int sp, int sidx, int which)
            ((size_t)((2 * sp + sidx) * 2 + which)) * (size_t)c->g.ntiles;
 }
 
-static void *field_ptr(pic_ctx *c, int comp) { return c->fields + (size_t)comp * c->g.ncomp * c->es; }
+// component comp (0..8: Ex Ey Ez Bx By Bz Jx Jy Jz) of the current fields;
+// eb_other: E, B component comp (0..5) of the buffer the next Yee update writes
+static void *field_ptr(pic_ctx *c, int comp)
+{
+    if (comp < 6 && c->fset) return c->scratch + c->off_eb + (size_t)comp * c->g.ncomp * c->es;
+    return c->fields + (size_t)comp * c->g.ncomp * c->es;
+}
+static void *eb_other(pic_ctx *c, int comp)
+{
+    if (!c->fset) return c->scratch + c->off_eb + (size_t)comp * c->g.ncomp * c->es;
+    return c->fields + (size_t)comp * c->g.ncomp * c->es;
+}
 
 template <typename real>
 static Species<real> species_view(pic_ctx *c, int sp, int sidx)
@@ -285,6 +301,8 @@ extern "C" pic_status pic_init_grid(const pic_grid_params *p, pic_ctx **out)
     o += align_up(sizeof(double) * 3 * kPartialBlocks);
     c->off_err = o;
     o += kAlign;
+    c->off_eb = o;
+    o += align_up((size_t)6 * g.ncomp * c->es);
     c->scratch_bytes = o;
     c->plasma.ions = 0;
     *out = c;
@@ -330,6 +348,7 @@ extern "C" pic_status pic_bind_buffers(pic_ctx *c, const pic_buffers *b)
     CUDA_TRY(c, cudaMemsetAsync(c->fields, 0, c->field_bytes, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->scratch, 0, c->scratch_bytes, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->fset = 0;
     c->bound = true;
     return PIC_OK;
 }
@@ -656,19 +675,32 @@ static void run_phases_t(pic_ctx *c, unsigned mask)
 {
     real *F[9];
     for (int q = 0; q < 9; ++q) F[q] = (real *)field_ptr(c, q);
+    // When one call zeroes, deposits and filters the current, the raw current
+    // is accumulated in the scratch buffer and the filter writes its result
+    // straight into J (no copy back); otherwise every phase works on J.
+    real *tmp = (real *)(c->scratch + c->off_tmp);
+    const bool raw_in_tmp = (mask & PIC_PH_ZERO_J) && (mask & PIC_PH_FILTER) && c->p.filter_passes >= 1 &&
+                            c->p.filter_passes <= 4;
+    real *R[3] = {F[6], F[7], F[8]};
+    if (raw_in_tmp)
+        for (int q = 0; q < 3; ++q) R[q] = tmp + (size_t)q * c->g.ncomp;
     if (mask & PIC_PH_ZERO_J) {
         PhaseTimer pt(c, 0);
-        cudaMemsetAsync(F[6], 0, (size_t)3 * c->g.ncomp * sizeof(real), c->stream);
+        cudaMemsetAsync(R[0], 0, (size_t)3 * c->g.ncomp * sizeof(real), c->stream);
     }
     if (mask & PIC_PH_PUSH) {
         PhaseTimer pt(c, 1);
-        launch_push<real>(push_args<real>(c, 0), c->stream);
+        PushArgs<real> a = push_args<real>(c, 0);
+        for (int q = 0; q < 3; ++q) a.J[q] = R[q];
+        launch_push<real>(a, c->stream);
         c->cur[0] ^= 1;
         c->kernels += 1;
     }
     if ((mask & PIC_PH_IONS) && c->ions_species) {
         PhaseTimer pt(c, 2);
-        launch_ions<real>(push_args<real>(c, 1), c->stream);
+        PushArgs<real> a = push_args<real>(c, 1);
+        for (int q = 0; q < 3; ++q) a.J[q] = R[q];
+        launch_ions<real>(a, c->stream);
         c->cur[1] ^= 1;
         c->kernels += 1;
     }
@@ -686,20 +718,28 @@ static void run_phases_t(pic_ctx *c, unsigned mask)
         const double amp = l.a0 * D * env * std::sin(kTwoPi * sr);
         const double j0 = -amp / (kPi * c->hz);
         const int comp = l.polarization == PIC_POL_X ? 0 : 1;
-        launch_antenna<real>(c->g, F[6 + comp], l.polarization, c->ka, j0, c->hx, c->hy, l.x_center, l.y_center,
+        launch_antenna<real>(c->g, R[comp], l.polarization, c->ka, j0, c->hx, c->hy, l.x_center, l.y_center,
                              l.waist, c->stream);
         c->kernels += 1;
     }
     if ((mask & PIC_PH_FILTER) && c->p.filter_passes > 0) {
         PhaseTimer pt(c, 4);
         real *J[3] = {F[6], F[7], F[8]};
-        launch_filter<real>(c->g, J, (real *)(c->scratch + c->off_tmp), c->p.filter_passes, c->stream);
+        if (!raw_in_tmp) {
+            launch_filter<real>(c->g, J, tmp, c->p.filter_passes, c->stream);
+        } else if (!launch_filter_from<real>(c->g, tmp, J, c->p.filter_passes, c->stream)) {
+            cudaMemcpyAsync(J[0], tmp, (size_t)3 * c->g.ncomp * sizeof(real), cudaMemcpyDeviceToDevice, c->stream);
+            launch_filter<real>(c->g, J, tmp, c->p.filter_passes, c->stream);
+        }
         c->kernels += c->p.filter_passes <= 4 ? 1 : (int64_t)(c->g.dim == 3 ? 3 : 2) * c->p.filter_passes;
     }
     if (mask & PIC_PH_YEE) {
         PhaseTimer pt(c, 5);
-        launch_yee<real>(c->g, F, c->dt, c->hx, c->hy, c->hz, c->stream);
-        c->kernels += 3;
+        real *F1[6];
+        for (int q = 0; q < 6; ++q) F1[q] = (real *)eb_other(c, q);
+        launch_yee<real>(c->g, F, F1, c->dt, c->hx, c->hy, c->hz, c->stream);
+        c->fset ^= 1;
+        c->kernels += 1;
     }
     if ((mask & PIC_PH_INJECT) && c->plasma_loaded && c->gam > 1.0) {
         PhaseTimer pt(c, 6);
@@ -1073,8 +1113,11 @@ static pic_status get_state_t(pic_ctx *c, unsigned char *dst, size_t dst_bytes, 
     if (dst_bytes < need) return fail(c, PIC_ERR_ARG, "destination too small");
     CUDA_TRY(c, cudaMemcpyAsync(dst, &h, sizeof(h), dst_is_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, c->stream));
     size_t o = sizeof(StateHeader);
-    CUDA_TRY(c, cudaMemcpyAsync(dst + o, c->fields, c->field_bytes, kind_out(dst_is_device), c->stream));
-    o += c->field_bytes;
+    for (int q = 0; q < PIC_NCOMP; ++q) {
+        const size_t per = (size_t)c->g.ncomp * c->es;
+        CUDA_TRY(c, cudaMemcpyAsync(dst + o, field_ptr(c, q), per, kind_out(dst_is_device), c->stream));
+        o += per;
+    }
     for (int sp = 0; sp < (c->ions_species ? 2 : 1); ++sp) {
         void *col[9];
         side_raw(c, sp, c->cur[sp] ^ 1, col);
@@ -1113,6 +1156,7 @@ static pic_status set_state_t(pic_ctx *c, const unsigned char *src, size_t src_b
                         (c->ions_species ? species_state_bytes(c, 1, h.n[1]) : 0);
     if (src_bytes < need) return fail(c, PIC_ERR_ARG, "snapshot truncated");
     size_t o = sizeof(StateHeader);
+    c->fset = 0;
     CUDA_TRY(c, cudaMemcpyAsync(c->fields, src + o, c->field_bytes, kind_in(src_is_device), c->stream));
     o += c->field_bytes;
     for (int sp = 0; sp < (c->ions_species ? 2 : 1); ++sp) {

@@ -3,125 +3,257 @@
 //
 // Yee (1966) on the staggered lattice of pic_internal.cuh, B split in two half
 // steps so that E and B both live at integer times:
-//   B -= (dt/2) curl E;   E += dt (curl B - 2 pi J);   B -= (dt/2) curl E.
-// With absorbing z the tangential E (Ex, Ey) on the end planes k = 0 and
-// k = nz follows Mur's first-order condition (Mur 1981)
-//   E0^{n+1} = E1^n + (dt - dz)/(dt + dz) (E1^{n+1} - E0^n)
-// and the thread that updates plane 1 (nz-1) also updates plane 0 (nz), so no
-// thread reads a value another thread of the same launch writes.
+//   B -= (dt/2) curl E;   E += dt (curl B - 2 pi J);   B -= (dt/2) curl E,
+// all three in one kernel that reads E^n, B^n from one field buffer and writes
+// E^{n+1}, B^{n+1} to another (yee_kernel).  With absorbing z the tangential E
+// (Ex, Ey) on the end planes k = 0 and k = nz follows Mur's first-order
+// condition (Mur 1981).
 #include "pic_internal.cuh"
+
+#include <cuda_pipeline.h>
 
 namespace pic {
 
 template <typename real>
 struct YeeArgs {
     Geom g;
-    real *E[3], *B[3];
+    const real *E[3], *B[3];  // E^n, B^n
+    real *E1[3], *B1[3];      // E^{n+1}, B^{n+1} (another buffer)
     const real *J[3];
-    real h;             // time step of this update (dt/2 for B, dt for E)
-    real ihx, ihy, ihz; // 1 / h_d
-    real twopi;         // 2 pi
-    real mur;           // (dt - hz) / (dt + hz)
+    real hb, he;              // dt/2 (B half steps), dt (E step)
+    real ihx, ihy, ihz;       // 1 / h_d
+    real twopi;               // 2 pi
+    real mur;                 // (dt - hz) / (dt + hz)
+    int cz, nchunks;          // z planes per chunk, chunks
 };
 
-template <typename real, int DIM>
-__global__ void yee_b_kernel(YeeArgs<real> a)
-{
-    const Geom &g = a.g;
-    const int64_t n = a.g.ncomp;
-    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(o % g.nx);
-        const int j = (int)((o / g.nx) % g.ny);
-        const int k = (int)(o / g.plane);
-        const int ip = i + 1 == g.nx ? 0 : i + 1;
-        const int jp = j + 1 == g.ny ? 0 : j + 1;
-        const real *Ex = a.E[0], *Ey = a.E[1], *Ez = a.E[2];
-        const bool per = g.bc_z == 0;
-        if (k < g.nz) {
-            const int kp = (per && k + 1 == g.nz) ? 0 : k + 1;
-            const int64_t okp = fidx(g, i, j, kp);
-            real dEz_dy = 0, dEx_dy = 0;
-            if (DIM == 3) dEz_dy = (Ez[fidx(g, i, jp, k)] - Ez[o]) * a.ihy;
-            const real dEy_dz = (Ey[okp] - Ey[o]) * a.ihz;
-            a.B[0][o] -= a.h * (dEz_dy - dEy_dz);
-            const real dEx_dz = (Ex[okp] - Ex[o]) * a.ihz;
-            const real dEz_dx = (Ez[fidx(g, ip, j, k)] - Ez[o]) * a.ihx;
-            a.B[1][o] -= a.h * (dEx_dz - dEz_dx);
-            (void)dEx_dy;
-        }
-        if (k < g.nz || !per) {
-            const real dEy_dx = (Ey[fidx(g, ip, j, k)] - Ey[o]) * a.ihx;
-            real dEx_dy = 0;
-            if (DIM == 3) dEx_dy = (Ex[fidx(g, i, jp, k)] - Ex[o]) * a.ihy;
-            a.B[2][o] -= a.h * (dEy_dx - dEx_dy);
-        }
-    }
-}
+// column shape of a CTA: 32 x 8 (x, y) in 3D, 256 x 1 in 2D
+template <int DIM> struct YeeTile { static constexpr int TX = 32, TY = 8, HY = 1; };
+template <> struct YeeTile<2> { static constexpr int TX = 256, TY = 1, HY = 0; };
 
+// One Yee step in one pass over the grid.  A CTA owns a column of TX x TY
+// nodes in (x, y) and a chunk of z planes; it marches up the chunk keeping a
+// few planes of E^n, B^n, J, of the half-step B (Bh) and of E^{n+1} (E') in
+// shared memory.  At plane k of the march:
+//   Bh(k)   = B^n(k) - (dt/2) curl E^n      (E^n at k and k+1)
+//   E'(k)   = E^n(k) + dt (curl Bh - 2 pi J) (Bh at k and k-1)
+//   B'(k-1) = Bh(k-1) - (dt/2) curl E'      (E' at k-1 and k)
+// while the planes the next step of the march reads (E^n(k+2), B^n(k+1),
+// J(k+1)) are copied into shared memory with cp.async.  Each curl takes the
+// next (x, y) neighbour on one side, so Bh is updated on the column widened
+// by one node on both sides, E' widened by one node above, and neighbouring
+// columns recompute the widened nodes; E' and B' of the column's own nodes
+// are written to the other field buffer, so no CTA reads a value another one
+// writes.  The chunk starts one plane early (the Bh plane below its first E'
+// plane) and ends one plane late (the E' plane above its last B' plane).
+// With absorbing z the tangential E (Ex, Ey) of the end planes follows Mur's
+// first-order condition
+//   E0^{n+1} = E1^n + (dt - dz)/(dt + dz) (E1^{n+1} - E0^n)
+// (Mur 1981), evaluated once E' of the neighbouring plane is known.  The
+// arithmetic per node is that of the split-B leapfrog written out term by
+// term.  Planes a component does not have (Ez, Bx, By at k = nz; every
+// component at k = nz with periodic z) are neither read nor written.
 template <typename real, int DIM>
-__device__ __forceinline__ void ampere_exy(const YeeArgs<real> &a, int i, int j, int k, int km, real &ex, real &ey)
+__global__ void __launch_bounds__(256) yee_kernel(YeeArgs<real> a)
 {
+    constexpr int TX = YeeTile<DIM>::TX, TY = YeeTile<DIM>::TY, HY = YeeTile<DIM>::HY;
+    constexpr int NT = 256;  // threads; every thread owns at most two nodes of each shared plane
+    // shared planes: E^n on x0-1 .. x0+TX+1, y0-HY .. y0+TY-1+2HY; B^n and Bh
+    // on x0-1 .. x0+TX, y0-HY .. y0+TY-1+HY; J and E' on x0 .. x0+TX,
+    // y0 .. y0+TY-1+HY
+    constexpr int NX0 = TX + 3, NY0 = TY + 3 * HY, P0 = NX0 * NY0;
+    constexpr int NX1 = TX + 2, NY1 = TY + 2 * HY, P1 = NX1 * NY1;
+    constexpr int NX2 = TX + 1, NY2 = TY + HY, P2 = NX2 * NY2;
+    static_assert(P0 <= 2 * NT && TX * TY == NT, "plane regions must fit two nodes per thread");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    real *sE = reinterpret_cast<real *>(smem_raw);  // E^n: [4 planes][3 components][P0]
+    real *sN = sE + 12 * P0;                         // B^n: [2][3][P1]
+    real *sJ = sN + 6 * P1;                          // J:   [2][3][P2]
+    real *sB = sJ + 6 * P2;                          // Bh:  [2][3][P1]
+    real *sF = sB + 6 * P1;                          // E':  [3][3][P2]
     const Geom &g = a.g;
-    const int im = i == 0 ? g.nx - 1 : i - 1;
-    const int jm = j == 0 ? g.ny - 1 : j - 1;
-    const int64_t o = fidx(g, i, j, k), okm = fidx(g, i, j, km);
-    const real *Bx = a.B[0], *By = a.B[1], *Bz = a.B[2];
-    real dBz_dy = 0;
-    if (DIM == 3) dBz_dy = (Bz[o] - Bz[fidx(g, i, jm, k)]) * a.ihy;
-    const real dBy_dz = (By[o] - By[okm]) * a.ihz;
-    ex = a.E[0][o] + a.h * ((dBz_dy - dBy_dz) - a.twopi * a.J[0][o]);
-    const real dBx_dz = (Bx[o] - Bx[okm]) * a.ihz;
-    const real dBz_dx = (Bz[o] - Bz[fidx(g, im, j, k)]) * a.ihx;
-    ey = a.E[1][o] + a.h * ((dBx_dz - dBz_dx) - a.twopi * a.J[1][o]);
-}
-
-template <typename real, int DIM>
-__global__ void yee_e_kernel(YeeArgs<real> a)
-{
-    const Geom &g = a.g;
-    const int64_t n = a.g.ncomp;
     const bool per = g.bc_z == 0;
-    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(o % g.nx);
-        const int j = (int)((o / g.nx) % g.ny);
-        const int k = (int)(o / g.plane);
-        const int im = i == 0 ? g.nx - 1 : i - 1;
-        const int jm = j == 0 ? g.ny - 1 : j - 1;
-        if (k < g.nz) {
-            const real *Bx = a.B[0], *By = a.B[1];
-            const real dBy_dx = (By[o] - By[fidx(g, im, j, k)]) * a.ihx;
-            real dBx_dy = 0;
-            if (DIM == 3) dBx_dy = (Bx[o] - Bx[fidx(g, i, jm, k)]) * a.ihy;
-            a.E[2][o] += a.h * ((dBy_dx - dBx_dy) - a.twopi * a.J[2][o]);
+    const int nbx = (g.nx + TX - 1) / TX;
+    const int x0 = (int)(blockIdx.x % nbx) * TX, y0 = (int)(blockIdx.x / nbx) * TY;
+    const int nzo = per ? g.nz : g.nz + 1;  // planes written
+    const int z0 = (int)blockIdx.y * a.cz;
+    const int z1 = (int)blockIdx.y == a.nchunks - 1 ? nzo : z0 + a.cz;
+    const int kb = z0 - 1;
+    const int tid = (int)threadIdx.x;
+    auto r2 = [&](int k) { return (k - kb) & 1; };
+    auto r3 = [&](int k) { return (k - kb) % 3; };
+    auto r4 = [&](int k) { return (k - kb) & 3; };
+    // plane k of a component in memory (-1: the component has no plane k)
+    auto mem_plane = [&](int k, bool half) {
+        return per ? wrapi(k, g.nz) : (k >= 0 && k <= zmax_of(g, half) ? k : -1);
+    };
+    // periodic x, y (columns of grids narrower than a CTA wrap more than once)
+    auto gxw = [&](int x) { return x >= 0 && x < g.nx ? x : wrapi(x, g.nx); };
+    auto gyw = [&](int y) { return DIM == 3 ? (y >= 0 && y < g.ny ? y : wrapi(y, g.ny)) : 0; };
+    // this thread's nodes r = tid, tid + NT of a region (nx_ wide, np nodes,
+    // origin (xo, yo)): their offsets within a plane in memory (-1: none)
+    auto offs = [&](int nx_, int np, int xo, int yo, int o[2]) {
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int r = tid + m * NT;
+            const int ly = r / nx_, lx = r - ly * nx_;
+            o[m] = r < np ? gyw(yo + ly) * g.nx + gxw(xo + lx) : -1;
         }
-        if (per) {
-            if (k < g.nz) {
-                real ex, ey;
-                ampere_exy<real, DIM>(a, i, j, k, k == 0 ? g.nz - 1 : k - 1, ex, ey);
-                a.E[0][o] = ex;
-                a.E[1][o] = ey;
+    };
+    int oE[2], oB[2], oJ[2];
+    offs(NX0, P0, x0 - 1, y0 - HY, oE);
+    offs(NX1, P1, x0 - 1, y0 - HY, oB);
+    offs(NX2, P2, x0, y0, oJ);
+    // copy plane k of three components into shared memory (this thread's
+    // nodes); planes a component does not have are zero
+    auto fetch = [&](const real *const src[3], real *dst, int k, int np, const int o[2], bool e_half) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int kk = mem_plane(k, e_half ? c == 2 : c != 2);
+            const real *base = src[c] + (int64_t)kk * g.plane;
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                if (o[m] < 0) continue;
+                real *d = dst + c * np + tid + m * NT;
+                if (kk >= 0) __pipeline_memcpy_async(d, base + o[m], sizeof(real));
+                else *d = real(0);
             }
-        } else if (k >= 1 && k <= g.nz - 1) {
-            real ex, ey;
-            ampere_exy<real, DIM>(a, i, j, k, k - 1, ex, ey);
-            if (k == 1) {  // this thread also owns plane 0
-                const int64_t o0 = fidx(g, i, j, 0);
-                const real ex1 = a.E[0][o], ey1 = a.E[1][o];
-                const real ex0 = a.E[0][o0], ey0 = a.E[1][o0];
-                a.E[0][o0] = ex1 + a.mur * (ex - ex0);
-                a.E[1][o0] = ey1 + a.mur * (ey - ey0);
-            }
-            if (k == g.nz - 1) {  // and plane nz
-                const int64_t on = fidx(g, i, j, g.nz);
-                const real exm = a.E[0][o], eym = a.E[1][o];
-                const real exn = a.E[0][on], eyn = a.E[1][on];
-                a.E[0][on] = exm + a.mur * (ex - exn);
-                a.E[1][on] = eym + a.mur * (ey - eyn);
-            }
-            a.E[0][o] = ex;
-            a.E[1][o] = ey;
         }
+    };
+    auto fetch_all = [&](int ke, int kbj) {
+        fetch(a.E, sE + r4(ke) * 3 * P0, ke, P0, oE, true);
+        fetch(a.B, sN + r2(kbj) * 3 * P1, kbj, P1, oB, false);
+        fetch(a.J, sJ + r2(kbj) * 3 * P2, kbj, P2, oJ, true);
+    };
+
+    // Bh(k) on its widened column
+    auto half_b = [&](int k) {
+        const real *e0 = sE + r4(k) * 3 * P0, *e1 = sE + r4(k + 1) * 3 * P0, *bn = sN + r2(k) * 3 * P1;
+        real *dst = sB + r2(k) * 3 * P1;
+        const bool vxy = mem_plane(k, true) >= 0, vz = mem_plane(k, false) >= 0;
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int r = tid + m * NT;
+            if (r >= P1) continue;
+            const int ly = r / NX1, lx = r - ly * NX1;
+            const int o = ly * NX0 + lx;  // the same node in the E^n plane
+            real dEz_dy = 0, dEx_dy = 0;
+            if (DIM == 3) {
+                dEz_dy = (e0[2 * P0 + o + NX0] - e0[2 * P0 + o]) * a.ihy;
+                dEx_dy = (e0[o + NX0] - e0[o]) * a.ihy;
+            }
+            const real dEy_dz = (e1[P0 + o] - e0[P0 + o]) * a.ihz;
+            const real dEx_dz = (e1[o] - e0[o]) * a.ihz;
+            const real dEz_dx = (e0[2 * P0 + o + 1] - e0[2 * P0 + o]) * a.ihx;
+            const real dEy_dx = (e0[P0 + o + 1] - e0[P0 + o]) * a.ihx;
+            dst[r] = vxy ? bn[r] - a.hb * (dEz_dy - dEy_dz) : real(0);
+            dst[P1 + r] = vxy ? bn[P1 + r] - a.hb * (dEx_dz - dEz_dx) : real(0);
+            dst[2 * P1 + r] = vz ? bn[2 * P1 + r] - a.hb * (dEy_dx - dEx_dy) : real(0);
+        }
+    };
+    // E'(k) on its widened column (Ampere; Ex, Ey of the Mur planes are set
+    // apart by the boundary condition)
+    auto full_e = [&](int k) {
+        const real *e0 = sE + r4(k) * 3 * P0, *jj = sJ + r2(k) * 3 * P2;
+        const real *b0 = sB + r2(k) * 3 * P1, *bm = sB + r2(k - 1) * 3 * P1;
+        real *dst = sF + r3(k) * 3 * P2;
+        const bool vz = mem_plane(k, true) >= 0;
+        const bool vxy = per || (k >= 1 && k <= g.nz - 1);
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int r = tid + m * NT;
+            if (r >= P2) continue;
+            const int ly = r / NX2, lx = r - ly * NX2;
+            const int ob = (ly + HY) * NX1 + lx + 1;  // the node in the Bh plane
+            const int oe = (ly + HY) * NX0 + lx + 1;  // and in the E^n plane
+            real dBz_dy = 0, dBx_dy = 0;
+            if (DIM == 3) {
+                dBz_dy = (b0[2 * P1 + ob] - b0[2 * P1 + ob - NX1]) * a.ihy;
+                dBx_dy = (b0[ob] - b0[ob - NX1]) * a.ihy;
+            }
+            if (vxy) {
+                const real dBy_dz = (b0[P1 + ob] - bm[P1 + ob]) * a.ihz;
+                dst[r] = e0[oe] + a.he * ((dBz_dy - dBy_dz) - a.twopi * jj[r]);
+                const real dBx_dz = (b0[ob] - bm[ob]) * a.ihz;
+                const real dBz_dx = (b0[2 * P1 + ob] - b0[2 * P1 + ob - 1]) * a.ihx;
+                dst[P2 + r] = e0[P0 + oe] + a.he * ((dBx_dz - dBz_dx) - a.twopi * jj[P2 + r]);
+            }
+            const real dBy_dx = (b0[P1 + ob] - b0[P1 + ob - 1]) * a.ihx;
+            dst[2 * P2 + r] = vz ? e0[2 * P0 + oe] + a.he * ((dBy_dx - dBx_dy) - a.twopi * jj[2 * P2 + r]) : real(0);
+        }
+    };
+    // Mur: Ex, Ey of plane kt from plane kn (its neighbour inside the box)
+    auto mur = [&](int kt, int kn) {
+        const real *et = sE + r4(kt) * 3 * P0, *en = sE + r4(kn) * 3 * P0;
+        const real *fn = sF + r3(kn) * 3 * P2;
+        real *ft = sF + r3(kt) * 3 * P2;
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int r = tid + m * NT;
+            if (r >= P2) continue;
+            const int ly = r / NX2, lx = r - ly * NX2;
+            const int oe = (ly + HY) * NX0 + lx + 1;
+            ft[r] = en[oe] + a.mur * (fn[r] - et[oe]);
+            ft[P2 + r] = en[P0 + oe] + a.mur * (fn[P2 + r] - et[P0 + oe]);
+        }
+    };
+    // B'(k) and E'(k) of the column's own node of this thread to memory
+    const int lxo = tid % TX, lyo = tid / TX;
+    const bool own = x0 + lxo < g.nx && (DIM == 2 || y0 + lyo < g.ny);
+    const int64_t oxy = own ? (int64_t)(y0 + lyo) * g.nx + (x0 + lxo) : 0;
+    auto write_out = [&](int k) {
+        if (!own) return;
+        const real *b0 = sB + r2(k) * 3 * P1;
+        const real *f0 = sF + r3(k) * 3 * P2, *f1 = sF + r3(k + 1) * 3 * P2;
+        const int64_t o = (int64_t)k * g.plane + oxy;
+        const int of = lyo * NX2 + lxo;               // the node in the E' plane
+        const int ob = (lyo + HY) * NX1 + lxo + 1;    // and in the Bh plane
+        const bool vxy = k <= zmax_of(g, false), vz = k <= zmax_of(g, true);
+        if (vxy) {
+            a.E1[0][o] = f0[of];
+            a.E1[1][o] = f0[P2 + of];
+        }
+        if (vz) {
+            a.E1[2][o] = f0[2 * P2 + of];
+            real dEz_dy = 0;
+            if (DIM == 3) dEz_dy = (f0[2 * P2 + of + NX2] - f0[2 * P2 + of]) * a.ihy;
+            const real dEy_dz = (f1[P2 + of] - f0[P2 + of]) * a.ihz;
+            a.B1[0][o] = b0[ob] - a.hb * (dEz_dy - dEy_dz);
+            const real dEx_dz = (f1[of] - f0[of]) * a.ihz;
+            const real dEz_dx = (f0[2 * P2 + of + 1] - f0[2 * P2 + of]) * a.ihx;
+            a.B1[1][o] = b0[P1 + ob] - a.hb * (dEx_dz - dEz_dx);
+        }
+        if (vxy) {
+            const real dEy_dx = (f0[P2 + of + 1] - f0[P2 + of]) * a.ihx;
+            real dEx_dy = 0;
+            if (DIM == 3) dEx_dy = (f0[of + NX2] - f0[of]) * a.ihy;
+            a.B1[2][o] = b0[2 * P1 + ob] - a.hb * (dEy_dx - dEx_dy);
+        }
+    };
+
+    fetch(a.E, sE + r4(kb) * 3 * P0, kb, P0, oE, true);
+    fetch_all(kb + 1, kb);
+    __pipeline_commit();
+    for (int k = kb; k <= z1; ++k) {
+        // the planes the next step reads, while this one is computed
+        fetch_all(k + 2, k + 1);
+        __pipeline_commit();
+        __pipeline_wait_prior(1);
+        __syncthreads();
+        half_b(k);
+        __syncthreads();
+        if (k >= z0) {
+            full_e(k);
+            __syncthreads();
+            if (!per && (k == 1 || k == g.nz - 1)) {
+                if (k == 1) mur(0, 1);
+                if (k == g.nz - 1) mur(g.nz, g.nz - 1);
+                __syncthreads();
+            }
+        }
+        if (k >= z0 + 1) write_out(k - 1);
     }
+    __pipeline_wait_prior(0);
 }
 
 static unsigned grid_for(int64_t n, int block)
@@ -132,7 +264,8 @@ static unsigned grid_for(int64_t n, int block)
 }
 
 template <typename real>
-void launch_yee(const Geom &g, real *const F[9], double dt, double hx, double hy, double hz, cudaStream_t s)
+void launch_yee(const Geom &g, real *const F[9], real *const F1[6], double dt, double hx, double hy, double hz,
+                cudaStream_t s)
 {
     YeeArgs<real> a;
     a.g = g;
@@ -140,22 +273,39 @@ void launch_yee(const Geom &g, real *const F[9], double dt, double hx, double hy
         a.E[c] = F[c];
         a.B[c] = F[3 + c];
         a.J[c] = F[6 + c];
+        a.E1[c] = F1[c];
+        a.B1[c] = F1[3 + c];
     }
+    a.hb = (real)(0.5 * dt);
+    a.he = (real)dt;
     a.ihx = (real)(1.0 / hx);
     a.ihy = (real)(1.0 / hy);
     a.ihz = (real)(1.0 / hz);
     a.twopi = (real)6.283185307179586;
     a.mur = (real)((dt - hz) / (dt + hz));
-    const unsigned grid = grid_for(g.ncomp, 256);
-    a.h = (real)(0.5 * dt);
-    if (g.dim == 3) yee_b_kernel<real, 3><<<grid, 256, 0, s>>>(a);
-    else yee_b_kernel<real, 2><<<grid, 256, 0, s>>>(a);
-    a.h = (real)dt;
-    if (g.dim == 3) yee_e_kernel<real, 3><<<grid, 256, 0, s>>>(a);
-    else yee_e_kernel<real, 2><<<grid, 256, 0, s>>>(a);
-    a.h = (real)(0.5 * dt);
-    if (g.dim == 3) yee_b_kernel<real, 3><<<grid, 256, 0, s>>>(a);
-    else yee_b_kernel<real, 2><<<grid, 256, 0, s>>>(a);
+    const int nzo = g.bc_z == 0 ? g.nz : g.nz + 1;
+    // chunks of 32 planes (the last one takes the remainder, at least 2)
+    a.cz = nzo >= 64 ? 32 : (nzo >= 8 ? 4 : nzo);
+    a.nchunks = nzo / a.cz;
+    if (a.nchunks < 1) a.nchunks = 1;
+    const bool is3 = g.dim == 3;
+    const int TX = is3 ? YeeTile<3>::TX : YeeTile<2>::TX, TY = is3 ? YeeTile<3>::TY : YeeTile<2>::TY;
+    const int HY = is3 ? 1 : 0;
+    // E^n 4 planes, B^n and Bh 2 each, J 2, E' 3 (three components each)
+    const size_t smem = sizeof(real) * 3 *
+                        (4 * (size_t)(TX + 3) * (TY + 3 * HY) + 4 * (size_t)(TX + 2) * (TY + 2 * HY) +
+                         5 * (size_t)(TX + 1) * (TY + HY));
+    const unsigned nb = (unsigned)(((g.nx + TX - 1) / TX) * (is3 ? (g.ny + TY - 1) / TY : 1));
+    dim3 grid(nb, (unsigned)a.nchunks);
+    if (is3) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(yee_kernel<real, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        yee_kernel<real, 3><<<grid, 256, smem, s>>>(a);
+    } else {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(yee_kernel<real, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        yee_kernel<real, 2><<<grid, 256, smem, s>>>(a);
+    }
 }
 
 // ---------------------------------------------------------------- filter
@@ -302,7 +452,7 @@ __global__ void __launch_bounds__(256) filter_fused_kernel(Geom g, const real *i
 }
 
 template <typename real, int DIM, int BZ, int H>
-static void launch_fused(const Geom &g, real *const J[3], real *tmp, cudaStream_t s)
+static void launch_fused(const Geom &g, const real *in, real *out, cudaStream_t s)
 {
     constexpr int BX = 32 - 2 * H, BY = 8;
     constexpr int SPAN = DIM == 3 ? BX : BY * BX;
@@ -312,8 +462,36 @@ static void launch_fused(const Geom &g, real *const J[3], real *tmp, cudaStream_
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const unsigned nbx = (g.nx + SPAN - 1) / SPAN, nby = DIM == 3 ? (g.ny + BY - 1) / BY : 1;
     dim3 grid(nbx * nby, (g.nz + 1 + BZ - 1) / BZ, 3);
-    k<<<grid, 256, smem, s>>>(g, J[0], J[1], J[2], tmp, tmp + g.ncomp, tmp + 2 * g.ncomp);
-    cudaMemcpyAsync(J[0], tmp, 3 * sizeof(real) * g.ncomp, cudaMemcpyDeviceToDevice, s);
+    k<<<grid, 256, smem, s>>>(g, in, in + g.ncomp, in + 2 * g.ncomp, out, out + g.ncomp, out + 2 * g.ncomp);
+}
+
+template <typename real>
+static bool fused_passes(const Geom &g, const real *in, real *out, int npass, cudaStream_t s)
+{
+    if (npass < 1 || npass > 4) return false;
+    if (g.dim == 3) {
+        switch (npass) {
+        case 1: launch_fused<real, 3, 16, 1>(g, in, out, s); break;
+        case 2: launch_fused<real, 3, 16, 2>(g, in, out, s); break;
+        case 3: launch_fused<real, 3, 16, 3>(g, in, out, s); break;
+        default: launch_fused<real, 3, 16, 4>(g, in, out, s); break;
+        }
+    } else {
+        switch (npass) {
+        case 1: launch_fused<real, 2, 32, 1>(g, in, out, s); break;
+        case 2: launch_fused<real, 2, 32, 2>(g, in, out, s); break;
+        case 3: launch_fused<real, 2, 32, 3>(g, in, out, s); break;
+        default: launch_fused<real, 2, 32, 4>(g, in, out, s); break;
+        }
+    }
+    return true;
+}
+
+template <typename real>
+bool launch_filter_from(const Geom &g, const real *src, real *const J[3], int npass, cudaStream_t s)
+{
+    const bool contiguous = J[1] == J[0] + g.ncomp && J[2] == J[1] + g.ncomp;
+    return contiguous && fused_passes<real>(g, src, J[0], npass, s);
 }
 
 template <typename real>
@@ -323,22 +501,9 @@ void launch_filter(const Geom &g, real *const J[3], real *tmp, int npass, cudaSt
     // the three components are contiguous in the field buffer; the fused
     // kernel covers 1..4 passes, more fall back to one launch per pass
     const bool contiguous = J[1] == J[0] + g.ncomp && J[2] == J[1] + g.ncomp;
-    if (contiguous && npass <= 4) {
-        if (g.dim == 3) {
-            switch (npass) {
-            case 1: launch_fused<real, 3, 16, 1>(g, J, tmp, s); return;
-            case 2: launch_fused<real, 3, 16, 2>(g, J, tmp, s); return;
-            case 3: launch_fused<real, 3, 16, 3>(g, J, tmp, s); return;
-            default: launch_fused<real, 3, 16, 4>(g, J, tmp, s); return;
-            }
-        } else {
-            switch (npass) {
-            case 1: launch_fused<real, 2, 32, 1>(g, J, tmp, s); return;
-            case 2: launch_fused<real, 2, 32, 2>(g, J, tmp, s); return;
-            case 3: launch_fused<real, 2, 32, 3>(g, J, tmp, s); return;
-            default: launch_fused<real, 2, 32, 4>(g, J, tmp, s); return;
-            }
-        }
+    if (contiguous && fused_passes<real>(g, J[0], tmp, npass, s)) {
+        cudaMemcpyAsync(J[0], tmp, 3 * sizeof(real) * g.ncomp, cudaMemcpyDeviceToDevice, s);
+        return;
     }
     real *src[3] = {J[0], J[1], J[2]};
     real *dst[3] = {tmp, tmp + g.ncomp, tmp + 2 * g.ncomp};
@@ -431,9 +596,10 @@ void launch_field_sums(const Geom &g, real *const F[9], double *partials, int nb
 }
 
 #define PIC_FIELDS_INSTANTIATE(real)                                                                    \
-    template void launch_yee<real>(const Geom &, real *const[9], double, double, double, double,       \
-                                   cudaStream_t);                                                       \
+    template void launch_yee<real>(const Geom &, real *const[9], real *const[6], double, double, double, \
+                                   double, cudaStream_t);                                               \
     template void launch_filter<real>(const Geom &, real *const[3], real *, int, cudaStream_t);         \
+    template bool launch_filter_from<real>(const Geom &, const real *, real *const[3], int, cudaStream_t); \
     template void launch_antenna<real>(const Geom &, real *, int, int, double, double, double, double,  \
                                        double, double, cudaStream_t);                                   \
     template void launch_field_sums<real>(const Geom &, real *const[9], double *, int, cudaStream_t);

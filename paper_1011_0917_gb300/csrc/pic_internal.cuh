@@ -281,10 +281,14 @@ void launch_particle_sums(const Geom &g, const Species<real> &sp, const int *lo,
 void launch_inject(const InjectArgs &a, cudaStream_t s);
 
 template <typename real>
-void launch_yee(const Geom &g, real *const F[9], double dt, double hx, double hy, double hz,
+void launch_yee(const Geom &g, real *const F[9], real *const F1[6], double dt, double hx, double hy, double hz,
                 cudaStream_t s);
 template <typename real>
 void launch_filter(const Geom &g, real *const J[3], real *tmp, int npass, cudaStream_t s);
+// all passes from src (3 contiguous components, left unchanged) into J;
+// false (nothing launched) where only the per-pass path applies (npass > 4)
+template <typename real>
+bool launch_filter_from(const Geom &g, const real *src, real *const J[3], int npass, cudaStream_t s);
 template <typename real>
 void launch_antenna(const Geom &g, real *J, int pol, int ka, double j0, double hx, double hy,
                     double xc, double yc, double waist, cudaStream_t s);

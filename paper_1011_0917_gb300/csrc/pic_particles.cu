@@ -55,7 +55,7 @@ __device__ __forceinline__ int esirk_axis(real x0, real x1, real S0[S + 2], real
 // exact and associative, so a tile's sums do not depend on the order in which
 // its particles are processed, and they carry the contributions to 2^-K.
 // The "lo" word of a node sits LOFF words after its "hi" word.  FP64
-// accumulates in double.  Exact zeros (nodes of a window outside both
+// accumulates in double.  Zero words (e.g. nodes of a window outside both
 // supports) are not added.
 template <typename real> struct Acc { using type = double; };
 template <> struct Acc<float> { using type = int; };
@@ -69,7 +69,6 @@ template <int LOFF>
 __device__ __forceinline__ void sh_acc(int *p, float a, float b, float lo_scale)
 {
     const float v = a * b;
-    if (v == 0.f) return;
     const float t = v + kRoundMagic;
     const int h = __float_as_int(t) - kRoundMagicBits;
     const float r = v - (t - kRoundMagic);
@@ -620,9 +619,14 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
 
 // ----------------------------------------------------- drifting-ion kernel
 
-// Ions immobile in the lab move at the species' constant u in the boosted
-// frame; their transverse shapes do not change, so only Jz is deposited:
-// Wz = DSz (S0x S0y), identical to the general formula with DSx = DSy = 0.
+// Ions immobile in the lab move at the species' constant u = (0, 0, -gamma
+// beta) in the boosted frame: every ion of a step moves by the same
+// dz = u_z dt / (gamma h_z), in (-1, 0) cells, and its transverse position
+// never changes.  So only Jz is deposited, Wz = DSz (S0x S0y) (the general
+// formula with DSx = DSy = 0, in the arithmetic order of the electrons'
+// z-only deposit), and an ion either stays in its tile or moves to the one
+// tile below it (the top tile when z wraps, none when it leaves the box):
+// one counter per warp reserves the slots of the leavers.
 template <typename real, int DIM, int S, int TX, int TY, int TZ>
 __global__ void __launch_bounds__(kBlock) ion_kernel(PushArgs<real> a)
 {
@@ -637,9 +641,8 @@ __global__ void __launch_bounds__(kBlock) ion_kernel(PushArgs<real> a)
     // 2 buffers x 5 attributes x kBlock
     real *sP = reinterpret_cast<real *>(sJ + (sizeof(real) == 4 ? 2 : 1) * QN);
     const real ig = inv_gamma(a.ion_u[0], a.ion_u[1], a.ion_u[2]);
-    const real dx = a.ion_u[0] * ig * a.dtdh[0];
-    const real dy = DIM == 3 ? a.ion_u[1] * ig * a.dtdh[1] : real(0);
     const real dz = a.ion_u[2] * ig * a.dtdh[2];
+    const unsigned lane = threadIdx.x & 31u;
     __shared__ int s_stay;
 
     for (int64_t t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
@@ -660,10 +663,14 @@ __global__ void __launch_bounds__(kBlock) ion_kernel(PushArgs<real> a)
             }
             __pipeline_commit();
         };
+        const int64_t ntxy = (int64_t)g.nt[0] * g.nt[1];
         const int tix = (int)(t % g.nt[0]);
         const int tiy = (int)((t / g.nt[0]) % g.nt[1]);
-        const int tiz = (int)(t / ((int64_t)g.nt[0] * g.nt[1]));
+        const int tiz = (int)(t / ntxy);
         const int lox = tix << g.lt[0], loy = tiy << g.lt[1], loz = tiz << g.lt[2];
+        // the tile an ion leaving this one through its lower z face enters
+        // (-1: it leaves the box)
+        const int64_t below = tiz > 0 ? t - ntxy : (g.bc_z == 0 ? t + (int64_t)(g.nt[2] - 1) * ntxy : -1);
         __syncthreads();
         if (threadIdx.x == 0) s_stay = 0;
         for (int q = threadIdx.x; q < (sizeof(real) == 4 ? 2 : 1) * QN; q += blockDim.x) sJ[q] = 0;
@@ -673,9 +680,9 @@ __global__ void __launch_bounds__(kBlock) ion_kernel(PushArgs<real> a)
             const int p = it * kBlock + threadIdx.x;
             prefetch(it + 1);
             __pipeline_wait_prior(1);
-            int64_t dest = -1;
+            bool stay = false, leave = false;
             real ox = 0, oy = 0, oz = 0, w = 0;
-            int ni = 0, nj = 0, nk = 0;
+            int32_t cell = 0;
             int64_t pid = 0;
             if (p < n) {
                 const real *d = sP + (it & 1) * 5 * kBlock + threadIdx.x;
@@ -690,9 +697,7 @@ __global__ void __launch_bounds__(kBlock) ion_kernel(PushArgs<real> a)
                     oz = d[2 * kBlock];
                     w = d[3 * kBlock];
                     if (a.in.id) pid = a.in.id[bucket_slot(t, g.cap, n_lo, n_hi, p)];
-                    const real x1 = ox + dx, y1 = oy + dy, z1 = oz + dz;
-                    // Wz = DSz S0x S0y (the general formula with DSx = DSy = 0), in
-                    // the arithmetic order of the electrons' z-only deposit
+                    const real z1 = oz + dz;
                     real S0z[S + 2], DSz[S + 2], wx[S + 1], wy[S + 1];
                     bool crossed;
                     const int az = esirk_axis_c<S>(oz, z1, S0z, DSz, crossed) + lk + JL;
@@ -714,42 +719,56 @@ __global__ void __launch_bounds__(kBlock) ion_kernel(PushArgs<real> a)
                                 sh_acc<QN>(sJ + ((az + c) * QY + (by + b)) * QX + bx + q, Pz[c], sxy, a.fx_lo[0]);
                         }
                     }
-                    int sx = (int)floor(x1), sy = DIM == 3 ? (int)floor(y1) : 0, sz = (int)floor(z1);
-                    ox = x1 - real(sx);
-                    if (ox >= real(1)) { sx += 1; ox = 0; }
-                    if (DIM == 3) {
-                        oy = y1 - real(sy);
-                        if (oy >= real(1)) { sy += 1; oy = 0; }
+                    // z1 in (-1, 1): the same cell or the one below; an offset
+                    // that rounds to 1 stays in the cell with offset 0
+                    int sz = 0;
+                    oz = z1;
+                    if (z1 < real(0)) {
+                        oz = z1 + real(1);
+                        sz = -1;
+                        if (oz >= real(1)) { oz = 0; sz = 0; }
                     }
-                    oz = z1 - real(sz);
-                    if (oz >= real(1)) { sz += 1; oz = 0; }
-                    ni = ci + sx;
-                    if (ni < 0) ni += g.nx; else if (ni >= g.nx) ni -= g.nx;
-                    nj = cj + sy;
-                    if (DIM == 3) { if (nj < 0) nj += g.ny; else if (nj >= g.ny) nj -= g.ny; }
-                    nk = ck + sz;
+                    int nk = ck + sz;
                     bool alive = true;
-                    if (g.bc_z == 0) {
-                        if (nk < 0) nk += g.nz; else if (nk >= g.nz) nk -= g.nz;
-                    } else if (nk < 0 || nk >= g.nz) {
-                        alive = false;
+                    if (nk < 0) {
+                        if (g.bc_z == 0) nk += g.nz;
+                        else alive = false;
                     }
-                    if (alive) dest = tile_of(g, ni, nj, nk);
+                    if (alive) {
+                        cell = pack_cell(g, ci, cj, nk);
+                        stay = lk + sz >= 0;
+                        leave = !stay;
+                    }
                 }
             }
-            const int r = output_slot(&s_stay, a.out_hi, dest, t, g.cap);
-            if (dest >= 0) {
-                if (r < 0) {
-                    atomicOr(a.err, ERR_CAPACITY);
-                } else {
-                    const int64_t d = dest * (int64_t)g.cap + r;
-                    a.out.ox[d] = ox;
-                    if (DIM == 3) a.out.oy[d] = oy;
-                    a.out.oz[d] = oz;
-                    a.out.w[d] = w;
-                    a.out.cell[d] = pack_cell(g, ni, nj, nk);
-                    if (a.out.id) a.out.id[d] = pid;
-                }
+            // slots: stayers from the shared counter, leavers from the counter
+            // of the tile below (one atomic each per warp)
+            const unsigned ms = __ballot_sync(0xffffffffu, stay), ml = __ballot_sync(0xffffffffu, leave);
+            int bs = 0, bl = 0;
+            if (lane == 0) {
+                if (ms) bs = atomicAdd(&s_stay, __popc(ms));
+                if (ml) bl = atomicAdd(&a.out_hi[below], __popc(ml));
+            }
+            bs = __shfl_sync(0xffffffffu, bs, 0);
+            bl = __shfl_sync(0xffffffffu, bl, 0);
+            const unsigned below_me = (1u << lane) - 1u;
+            int64_t d = -1;
+            if (stay) {
+                const int r = bs + __popc(ms & below_me);
+                if (r < g.cap) d = t * (int64_t)g.cap + r;
+                else atomicOr(a.err, ERR_CAPACITY);
+            } else if (leave) {
+                const int r = bl + __popc(ml & below_me);
+                if (r < g.cap) d = below * (int64_t)g.cap + (g.cap - 1 - r);
+                else atomicOr(a.err, ERR_CAPACITY);
+            }
+            if (d >= 0) {
+                a.out.ox[d] = ox;
+                if (DIM == 3) a.out.oy[d] = oy;
+                a.out.oz[d] = oz;
+                a.out.w[d] = w;
+                a.out.cell[d] = cell;
+                if (a.out.id) a.out.id[d] = pid;
             }
         }
         __syncthreads();
