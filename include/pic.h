@@ -112,7 +112,8 @@ typedef struct pic_grid_params {
 typedef struct pic_sizes {
     size_t field_bytes;        /* 9 components x (nz+1) x ny x nx elements         */
     size_t species_bytes[2];   /* particle store per species (two bucket sides)    */
-    size_t scratch_bytes;      /* tile counters, filter buffer, error word, ...    */
+    size_t scratch_bytes;      /* tile counters, raw-current / filter buffer,      */
+                               /* the second E, B buffer of the Yee update, ...   */
     int64_t slots[2];          /* particle slots per side and species              */
     int64_t ntiles;            /* number of tiles                                  */
     int tile_capacity;         /* slots per tile                                   */

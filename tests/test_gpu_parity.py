@@ -321,6 +321,29 @@ def test_quadratic_high_boost_small(O, prec):
     assert max(err.values()) < tol, err
 
 
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_c3_stage_a0_1_5(O, prec):
+    # the gamma = 130 stage at its own drive (a0 = 1.5) on the 4x coarser grid:
+    # the FP64 build meets the 1e-10 bar; in FP32 the laser fields (Ey, Bx, Bz)
+    # agree to 1e-5 while the plasma's longitudinal response is below the FP32
+    # resolution of v_z at this boost (du moves v_z by ~du / gamma^3), so the E
+    # vector is held to the measured floor (1.1e-3 / 1.3e-3 with / without
+    # electron-ion pairs) with a 2x margin
+    g = dict(dim=2, nx=32, nz=200, dx=4.0, dz=4 / 32, gamma_boost=130.0, shape_order=2, filter_passes=4, seed=23)
+    beta = math.sqrt(1 - 1 / 130.0 ** 2)
+    hz = (4 / 32) * 130 * (1 + beta)
+    p = dict(ne=5.7e-5, z_start=130 * 3 * hz, z_end=130 * 400 * hz, ramp=5.0, ppc=(2, 1, 2), jitter=0.1, ions=1)
+    laser = dict(a0=1.5, waist=20.0, fwhm=4.0, t_peak=0.2)
+    sim, o = _run_steps_parity(O, g, p, laser, 50, prec)
+    err = vector_errors(sim, o)
+    if prec == FP64:
+        assert max(err.values()) < TOL50[prec], err
+    else:
+        laser_f = field_errors(sim, o, ("Ey", "Bx", "Bz"))
+        assert max(laser_f.values()) < 1e-5, laser_f
+        assert err["E"] < 3e-3 and err["B"] < 1e-3, err
+
+
 def test_continuity_residual_fp32(O):
     # div E - 2 pi F(rho) stays constant; F = the same binomial passes on rho
     from test_oracle_physics import _div_e, _filtered
