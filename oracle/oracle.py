@@ -51,6 +51,11 @@ class _Plasma(C.Structure):
                 ("nprof", C.c_int), ("prof", C.POINTER(C.c_double)), ("ions", C.c_int)]
 
 
+class _Btd(C.Structure):
+    _fields_ = [("nsnap", C.c_int), ("t0", C.c_double), ("dt", C.c_double), ("z0", C.c_double),
+                ("dz", C.c_double), ("nz", C.c_int), ("plane", C.c_int)]
+
+
 class _Laser(C.Structure):
     _fields_ = [("a0", C.c_double), ("waist", C.c_double), ("fwhm", C.c_double),
                 ("z_antenna", C.c_double), ("t_peak", C.c_double), ("pol", C.c_int),
@@ -84,6 +89,19 @@ class PlasmaParams:
     jitter: float = 0.1
     profile: tuple = ()
     ions: int = 1
+
+
+@dataclasses.dataclass
+class BtdParams:
+    """Lab-frame snapshots: T_j = t0 + j dt (j < nsnap), Z_k = z0 + k dz (k < nz);
+    plane 0 the axis line, 1 the (x, z) plane through the box centre."""
+    nsnap: int = 4
+    t0: float = 0.0
+    dt: float = 10.0
+    z0: float = 0.0
+    dz: float = 1.0 / 32
+    nz: int = 256
+    plane: int = 0
 
 
 @dataclasses.dataclass
@@ -147,6 +165,12 @@ def _load():
         lib.opic_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
         lib.opic_uniform.restype = C.c_double
         lib.opic_uniform.argtypes = [C.c_uint64, C.c_uint64]
+        lib.opic_btd_setup.restype = C.c_int
+        lib.opic_btd_setup.argtypes = [P, C.POINTER(_Btd)]
+        lib.opic_btd_data.restype = D
+        lib.opic_btd_data.argtypes = [P, C.c_int]
+        lib.opic_btd_filled.restype = C.POINTER(C.c_ubyte)
+        lib.opic_btd_filled.argtypes = [P, C.c_int]
         _lib = lib
     return _lib
 
@@ -288,6 +312,26 @@ class Oracle:
     def zero_fields(self):
         for c in COMPONENTS:
             self.field(c)[...] = 0.0
+
+    # ------------------------------------------------ back-transformed data
+    def btd_setup(self, b: "BtdParams | None"):
+        if b is None:
+            self.lib.opic_btd_setup(self.h, None)
+            self.btd = None
+            return
+        s = _Btd(b.nsnap, b.t0, b.dt, b.z0, b.dz, b.nz, b.plane)
+        if self.lib.opic_btd_setup(self.h, C.byref(s)) != 0:
+            raise ValueError(f"oracle rejected snapshot parameters {b}")
+        self.btd = b
+
+    def btd_snapshot(self, j: int):
+        """(fields {Ex..Bz: (nz, nxs)}, filled (nz,) bool) of lab snapshot j."""
+        b = self.btd
+        nxs = self.grid.nx if b.plane else 1
+        d = np.ctypeslib.as_array(self.lib.opic_btd_data(self.h, j), shape=(6 * b.nz * nxs,))
+        f = np.ctypeslib.as_array(self.lib.opic_btd_filled(self.h, j), shape=(b.nz,))
+        d = d.reshape(6, b.nz, nxs).copy()
+        return {c: d[q] for q, c in enumerate(COMPONENTS[:6])}, f.astype(bool).copy()
 
 
 def boris(u, e, b, q_over_m, dt):

@@ -62,6 +62,13 @@ struct opic {
     int ka;
     double t;
     int64_t step;
+    /* back-transformed snapshots */
+    int btd_on;
+    opic_btd btd;
+    int btd_nxs;
+    double *btd_data;        /* [nsnap][6][nz][nxs] */
+    unsigned char *btd_fill; /* [nsnap][nz] */
+    double *btd_prev[6];     /* E, B at the start of the step */
 };
 
 /* ------------------------------------------------------------------ utils */
@@ -157,6 +164,10 @@ void opic_destroy(opic *s)
         free(s->sp[sp].id);
     }
     free(s->pend);
+    free(s->btd_data);
+    free(s->btd_fill);
+    for (int c = 0; c < 6; ++c)
+        free(s->btd_prev[c]);
     free(s);
 }
 
@@ -907,6 +918,112 @@ static void yee_e(opic *s)
     }
 }
 
+/* --------------------------------------------- back-transformed snapshots */
+
+int opic_btd_setup(opic *s, const opic_btd *b)
+{
+    free(s->btd_data);
+    free(s->btd_fill);
+    s->btd_data = NULL;
+    s->btd_fill = NULL;
+    s->btd_on = 0;
+    if (!b)
+        return 0;
+    if (s->gam <= 1.0 || b->nsnap < 1 || b->nsnap > 64 || b->nz < 1 || !(b->dz > 0.0) ||
+        (b->plane != 0 && b->plane != 1))
+        return -1;
+    s->btd = *b;
+    s->btd_nxs = b->plane ? s->g.nx : 1;
+    s->btd_data = (double *)calloc((size_t)b->nsnap * 6 * b->nz * s->btd_nxs, sizeof(double));
+    s->btd_fill = (unsigned char *)calloc((size_t)b->nsnap * b->nz, 1);
+    for (int c = 0; c < 6; ++c)
+        if (!s->btd_prev[c])
+            s->btd_prev[c] = (double *)calloc((size_t)s->nn, sizeof(double));
+    s->btd_on = 1;
+    return 0;
+}
+
+double *opic_btd_data(opic *s, int j)
+{
+    if (!s->btd_on || j < 0 || j >= s->btd.nsnap)
+        return NULL;
+    return s->btd_data + (size_t)j * 6 * s->btd.nz * s->btd_nxs;
+}
+
+unsigned char *opic_btd_filled(opic *s, int j)
+{
+    if (!s->btd_on || j < 0 || j >= s->btd.nsnap)
+        return NULL;
+    return s->btd_fill + (size_t)j * s->btd.nz;
+}
+
+/* component c of field array f at transverse node (i, j) and simulation-frame
+   height zp, linear in z between the component's own planes; returns 0 where
+   zp is not between two of them */
+static int btd_zinterp(const opic *s, const double *f, int c, int64_t i, int64_t j, double zp, double *out)
+{
+    const double sz = STAG[c][2];
+    const double u = zp / s->hz - sz;
+    const double k0 = floor(u);
+    const double fz = u - k0;
+    if (k0 < 0.0 || k0 + 1.0 > (double)zmax_of(s, sz))
+        return 0;
+    const int64_t k = (int64_t)k0;
+    *out = (1.0 - fz) * f[fidx(s, i, j, k)] + fz * f[fidx(s, i, j, k + 1)];
+    return 1;
+}
+
+/* Fill every lab point whose event lies in the boosted step [t0, t0 + dt):
+   the event (T, Z) of the lab frame is (t', z') = (gamma (T - beta Z),
+   gamma (Z - beta T)) in the simulation frame, which moves at +beta along z.
+   The simulation-frame fields at the event are linear in t' between the start
+   and the end of the step and linear in z' between planes, and go to the lab
+   frame by the inverse field transformation
+     Ex = gamma (Ex' + beta By'),  Ey = gamma (Ey' - beta Bx'),  Ez = Ez',
+     Bx = gamma (Bx' - beta Ey'),  By = gamma (By' + beta Ex'),  Bz = Bz'. */
+static void btd_fill(opic *s, double t0)
+{
+    const opic_btd *b = &s->btd;
+    const double gam = s->gam, beta = s->beta;
+    const int64_t jc = s->ny / 2;
+    const int nxs = s->btd_nxs;
+    for (int js = 0; js < b->nsnap; ++js) {
+        const double T = b->t0 + js * b->dt;
+        for (int k = 0; k < b->nz; ++k) {
+            const double Z = b->z0 + k * b->dz;
+            const double tp = gam * (T - beta * Z);
+            if (!(tp >= t0 && tp < t0 + s->dt))
+                continue;
+            const double zp = gam * (Z - beta * T);
+            const double th = (tp - t0) / s->dt;
+            int ok = 1;
+            double v[6][2];
+            for (int is = 0; is < nxs && ok; ++is) {
+                const int64_t i = nxs == 1 ? s->g.nx / 2 : is;
+                for (int c = 0; c < 6 && ok; ++c) {
+                    double a0, a1;
+                    ok = btd_zinterp(s, s->btd_prev[c], c, i, jc, zp, &a0) &&
+                         btd_zinterp(s, s->f[c], c, i, jc, zp, &a1);
+                    v[c][0] = a0;
+                    v[c][1] = a1;
+                }
+                if (!ok)
+                    break;
+                double e[6];
+                for (int c = 0; c < 6; ++c)
+                    e[c] = (1.0 - th) * v[c][0] + th * v[c][1];
+                double *d = s->btd_data + (size_t)js * 6 * b->nz * nxs;
+                const double lab[6] = {gam * (e[0] + beta * e[4]), gam * (e[1] - beta * e[3]), e[2],
+                                       gam * (e[3] - beta * e[1]), gam * (e[4] + beta * e[0]), e[5]};
+                for (int c = 0; c < 6; ++c)
+                    d[((size_t)c * b->nz + k) * nxs + is] = lab[c];
+            }
+            if (ok)
+                s->btd_fill[(size_t)js * b->nz + k] = 1;
+        }
+    }
+}
+
 /* ------------------------------------------------------------------- step */
 
 void opic_step_phases(opic *s, unsigned mask)
@@ -923,9 +1040,14 @@ void opic_step_phases(opic *s, unsigned mask)
     if ((mask & OPIC_PH_FILTER) && s->g.npass > 0)
         opic_filter(s);
     if (mask & OPIC_PH_YEE) {
+        if (s->btd_on)
+            for (int c = 0; c < 6; ++c)
+                memcpy(s->btd_prev[c], s->f[c], (size_t)s->nn * sizeof(double));
         yee_b(s, 0.5 * s->dt);
         yee_e(s);
         yee_b(s, 0.5 * s->dt);
+        if (s->btd_on)
+            btd_fill(s, s->t);
     }
     if ((mask & OPIC_PH_INJECT) && s->npend > 0)
         inject(s);

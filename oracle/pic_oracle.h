@@ -79,6 +79,23 @@ typedef struct opic_laser {
     double xc, yc;           /* transverse centre; NaN: box centre           */
 } opic_laser;
 
+/* Lab-frame snapshots of a boosted-frame run (the paper's boosted data
+   "plotted in laboratory coordinates after Lorentz transformation", section
+   "Effect of the hyperbolic rotation in Minkowski space", Fig. 2).  Snapshot j
+   holds the lab-frame fields at lab time T_j = t0 + j dt on the lab points
+   Z_k = z0 + k dz, k < nz; each is filled during the boosted step whose time
+   interval [t'^n, t'^{n+1}) contains the event's boosted time.  Parity
+   status: pinned (uniform fields transform exactly; lab-frame and boosted-frame
+   runs of one pulse agree). */
+typedef struct opic_btd {
+    int nsnap;               /* number of lab snapshots, 1..64                */
+    double t0, dt;           /* lab times T_j = t0 + j dt, lambda0/c          */
+    double z0, dz;           /* lab positions Z_k = z0 + k dz, lambda0        */
+    int nz;                  /* lab points per snapshot                       */
+    int plane;               /* 0: the axis line (i = nx/2, j = ny/2);        */
+                             /* 1: the (x, z) plane j = ny/2 (all i)          */
+} opic_btd;
+
 opic *opic_create(const opic_grid *g);
 void opic_destroy(opic *s);
 
@@ -108,6 +125,13 @@ double *opic_rho_background(opic *s);
 
 void opic_step(opic *s, int nsteps);
 void opic_step_phases(opic *s, unsigned mask);
+
+/* back-transformed snapshots: setup (0, or -1 on bad arguments or gamma = 1;
+   NULL switches them off), then per snapshot j the fields [6][nz][nxs]
+   (Ex Ey Ez Bx By Bz, nxs = 1 or nx) and nz fill flags */
+int opic_btd_setup(opic *s, const opic_btd *b);
+double *opic_btd_data(opic *s, int j);
+unsigned char *opic_btd_filled(opic *s, int j);
 
 /* building blocks exposed for the oracle's own pins */
 void opic_gather(const opic *s, int64_t n, const double *x, const double *y,
