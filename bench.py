@@ -58,6 +58,8 @@ def parse():
                     help="store every drifting ion as its own record (no electron-ion pairs)")
     ap.add_argument("--no-explicit-check", action="store_true",
                     help="skip the second, shorter timing of the same stage with explicit ion records")
+    ap.add_argument("--btd", type=int, default=16,
+                    help="lab-frame (x, z)-plane snapshots timed after the main measurement (0: none)")
     return ap.parse_args()
 
 
@@ -240,6 +242,35 @@ def run_ours(args, rank, world, local):
                "note": "initial state restored from pinned host memory once per job of --steps steps; "
                        "on-axis Ez line read back after every step"}
         del host
+
+    # lab-frame snapshots: the same steps with n (x, z)-plane snapshots whose
+    # events the run is passing now, filled by the YEE phase
+    btd = None
+    if args.btd > 0 and g["gamma_boost"] > 1.0:
+        k = max(1, min(args.steps, 8))
+        P.pic_profile(ctx, True)
+        P.pic_profile_read(ctx)
+        P.pic_step(ctx, k)
+        base_ms, base_calls, _ = P.pic_profile_read(ctx)
+        sz = sim.sizes
+        gam, beta = g["gamma_boost"], sz.beta
+        lz = g["nz"] * sz.hz
+        tnow = sim.diagnostics().t
+        t_first = gam * (tnow + 0.5 * beta * lz)
+        z0 = beta * t_first - 1.0
+        nz_lab = int((lz / gam + 2.0 + args.btd * sz.dt) / g["dz"])
+        sim.btd_setup(args.btd, t_first, gam * sz.dt, z0, g["dz"], nz_lab, 1)
+        P.pic_step(ctx, k)
+        btd_ms, btd_calls, _ = P.pic_profile_read(ctx)
+        P.pic_profile(ctx, False)
+        filled = sum(int(sim.btd_snapshot(j)[1].sum()) for j in range(args.btd))
+        yee = btd_ms[5] / max(btd_calls[5], 1)
+        yee0 = base_ms[5] / max(base_calls[5], 1)
+        btd = {"snapshots": args.btd, "plane": "(x, z) at y = Ly/2", "lab_points_per_snapshot": nz_lab,
+               "columns": g["nx"], "steps": k, "lab_planes_filled": filled,
+               "yee_phase_ms_with": yee, "yee_phase_ms_without": yee0, "added_ms_per_step": yee - yee0,
+               "buffer_bytes": int(sim._btd.numel())}
+        P.pic_btd_setup(ctx, None, 0, 0)
     sim.close()
     del sim
     torch.cuda.empty_cache()
@@ -300,6 +331,7 @@ def run_ours(args, rank, world, local):
             "cpu_baseline": cpu,
             "adjoint_forward_ratio": None,
             "explicit_ion_records": explicit,
+            "lab_frame_snapshots": btd,
         }
     if world > 1:
         import torch.distributed as dist

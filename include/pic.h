@@ -253,6 +253,48 @@ pic_status pic_get_rho(pic_ctx *ctx, void *dst, size_t dst_bytes, int dst_is_dev
 /* Time, counts and FP64 Kahan-compensated sums (synchronises the stream). */
 pic_status pic_get_diagnostics(pic_ctx *ctx, pic_diag *out);
 
+/* ------------------------------------------------- lab-frame snapshots */
+
+/* Lab-frame ("back-transformed") snapshots of a boosted run: the boosted data
+   seen in laboratory coordinates after Lorentz transformation (section
+   "Effect of the hyperbolic rotation in Minkowski space", Fig. 2).  Snapshot j
+   holds the lab fields at lab time T_j = t0 + j dt on the lab points
+   Z_k = z0 + k dz (k < nz): on the axis line (plane 0: the nodes i = nx/2,
+   j = ny/2 of each component) or on the (x, z) plane j = ny/2 (plane 1, all
+   nx columns).  A point is filled during the step whose interval
+   [t'^n, t'^{n+1}) holds its simulation-frame time t' = gamma (T - beta Z),
+   from the fields linear in t' between (E^n, B^n) and (E^{n+1}, B^{n+1}) and
+   linear in z' = gamma (Z - beta T) between the planes of each component,
+   transformed by
+     Ex = gamma (Ex' + beta By'), Ey = gamma (Ey' - beta Bx'), Ez = Ez',
+     Bx = gamma (Bx' - beta Ey'), By = gamma (By' + beta Ex'), Bz = Bz'.
+   A point whose z' does not lie between two planes of every component stays
+   unfilled (flag 0, fields 0).  Event times and weights are FP64; the fields
+   are in the working precision. */
+typedef struct pic_btd_params {
+    int n_snapshots;           /* 1..64                                            */
+    double t0, dt;             /* lab times of the snapshots, lambda0/c            */
+    double z0, dz;             /* lab positions, lambda0 (dz > 0)                  */
+    int nz;                    /* lab points per snapshot, >= 1                    */
+    int plane;                 /* 0: axis line, 1: (x, z) plane                    */
+} pic_btd_params;
+
+/* Bytes of the caller-owned device buffer of the snapshots: n_snapshots
+   blocks of [6 components: Ex Ey Ez Bx By Bz][nz][nxs] elements (elem_bytes
+   each, nxs = 1 for plane 0, nx for plane 1), then n_snapshots x nz int32
+   fill flags starting at a 256-byte boundary. */
+pic_status pic_btd_bytes(const pic_ctx *ctx, const pic_btd_params *p, size_t *bytes);
+
+/* Zeroes buf (device memory of at least pic_btd_bytes, owned by the caller,
+   which keeps it alive while snapshots are taken) and fills the snapshots
+   from the next step's YEE phase on.  p == NULL stops.  PIC_ERR_ARG for an
+   unboosted grid (gamma_boost = 1) or invalid parameters. */
+pic_status pic_btd_setup(pic_ctx *ctx, const pic_btd_params *p, void *buf, size_t bytes);
+
+/* Copies snapshot j to host or device memory: its [6][nz][nxs] elements,
+   then its nz int32 flags (1: filled). */
+pic_status pic_btd_get(pic_ctx *ctx, int j, void *dst, size_t dst_bytes, int dst_is_device);
+
 /* ------------------------------------------------------------ checkpoint */
 
 /* Size of a compact snapshot (fields, live particles, time, laser) now. */

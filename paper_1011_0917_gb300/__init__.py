@@ -22,8 +22,8 @@ __all__ = [
     "pic_launch_laser", "pic_step", "pic_step_async", "pic_step_phases", "pic_get_fields", "pic_set_fields",
     "pic_get_axis", "pic_get_particles", "pic_get_rho", "pic_get_diagnostics", "pic_state_bytes",
     "pic_get_state", "pic_set_state", "pic_last_error", "pic_status_string", "pic_destroy", "pic_profile",
-    "pic_profile_read", "pic_filter_current_noalloc", "PIC_NOALLOC_MAX_NODES", "Simulation",
-    "library_path",
+    "pic_profile_read", "pic_filter_current_noalloc", "PIC_NOALLOC_MAX_NODES", "BtdParams", "pic_btd_bytes",
+    "pic_btd_setup", "pic_btd_get", "Simulation", "library_path",
 ]
 
 PIC_OK, PIC_ERR_ARG, PIC_ERR_STATE, PIC_ERR_CUDA = 0, 1, 2, 3
@@ -89,6 +89,12 @@ def library_path() -> str:
     return _build.LIB
 
 
+class BtdParams(C.Structure):
+    """pic_btd_params: lab snapshots T_j = t0 + j dt, Z_k = z0 + k dz."""
+    _fields_ = [("n_snapshots", C.c_int), ("t0", C.c_double), ("dt", C.c_double), ("z0", C.c_double),
+                ("dz", C.c_double), ("nz", C.c_int), ("plane", C.c_int)]
+
+
 def _load():
     global _lib
     if _lib is not None:
@@ -122,6 +128,9 @@ def _load():
         "pic_profile": (S, [P, I]),
         "pic_profile_read": (S, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "pic_filter_current_noalloc": (S, [I, I, I, I, I, I, I, P, P, P, P]),
+        "pic_btd_bytes": (S, [P, C.POINTER(BtdParams), C.POINTER(C.c_size_t)]),
+        "pic_btd_setup": (S, [P, C.POINTER(BtdParams), P, C.c_size_t]),
+        "pic_btd_get": (S, [P, I, P, C.c_size_t, I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -283,6 +292,21 @@ def pic_filter_current_noalloc(dim: int, nx: int, ny: int, nz: int, bc_z: int, p
         raise PicError(st, detail)
 
 
+def pic_btd_bytes(ctx, p: BtdParams) -> int:
+    n = C.c_size_t(0)
+    _check(ctx, _load().pic_btd_bytes(ctx, C.byref(p), C.byref(n)))
+    return n.value
+
+
+def pic_btd_setup(ctx, p, buf_ptr: int, nbytes: int):
+    """Start (p a BtdParams) or stop (p None) the lab-frame snapshots."""
+    _check(ctx, _load().pic_btd_setup(ctx, C.byref(p) if p is not None else None, C.c_void_p(buf_ptr), nbytes))
+
+
+def pic_btd_get(ctx, j: int, dst_ptr: int, dst_bytes: int, dst_is_device: bool):
+    _check(ctx, _load().pic_btd_get(ctx, j, C.c_void_p(dst_ptr), dst_bytes, int(dst_is_device)))
+
+
 # --------------------------------------------------- torch-owned buffers
 
 
@@ -379,3 +403,25 @@ class Simulation:
 
     def diagnostics(self) -> Diag:
         return pic_get_diagnostics(self.ctx)
+
+    def btd_setup(self, n_snapshots, t0, dt, z0, dz, nz, plane=0):
+        """Lab-frame snapshots into a torch device buffer owned by this object."""
+        p = BtdParams(n_snapshots, t0, dt, z0, dz, nz, plane)
+        nbytes = pic_btd_bytes(self.ctx, p)
+        self._btd = self.torch.empty(nbytes, dtype=self.torch.uint8, device=self.device)
+        self._btd_p = p
+        pic_btd_setup(self.ctx, p, self._btd.data_ptr(), nbytes)
+
+    def btd_snapshot(self, j):
+        """({Ex..Bz: (nz, nxs) float64 arrays}, filled (nz,) bool) of lab snapshot j."""
+        import numpy as np
+        p = self._btd_p
+        nxs = self.params.nx if p.plane else 1
+        es = self.sizes.elem_bytes
+        nd = 6 * p.nz * nxs * es
+        host = np.zeros(nd + 4 * p.nz, dtype=np.uint8)
+        pic_btd_get(self.ctx, j, host.ctypes.data, host.nbytes, False)
+        vals = host[:nd].view(np.float32 if es == 4 else np.float64).astype(np.float64).reshape(6, p.nz, nxs)
+        filled = host[nd:].view(np.int32) != 0
+        names = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
+        return {c: vals[q] for q, c in enumerate(names)}, filled

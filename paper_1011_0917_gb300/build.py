@@ -1,8 +1,8 @@
 """Build the CUDA library libpic.so in-tree for sm_103a (GB300) with nvcc.
 
-Each translation unit is compiled in parallel; pic_inject.cu is compiled
-without FMA contraction (its FP64 lattice arithmetic must round operation by
-operation).  Host code is compiled with -ffp-contract=off so that derived FP64
+Each translation unit is compiled in parallel; pic_inject.cu and pic_btd.cu
+are compiled without FMA contraction (their FP64 lattice and event arithmetic
+must round operation by operation).  Host code is compiled with -ffp-contract=off so that derived FP64
 quantities are the same on x86-64 and aarch64 hosts.
 """
 from __future__ import annotations
@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libpic.so")
 
-SOURCES = ["pic_capi.cu", "pic_particles.cu", "pic_fields.cu", "pic_inject.cu", "pic_noalloc.cu"]
+SOURCES = ["pic_capi.cu", "pic_particles.cu", "pic_fields.cu", "pic_inject.cu", "pic_btd.cu", "pic_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -34,7 +34,7 @@ def nvcc() -> str:
 def _flags(src: str) -> list[str]:
     f = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", INCLUDE,
          "-I", CSRC] + ARCH
-    if src == "pic_inject.cu":
+    if src in ("pic_inject.cu", "pic_btd.cu"):
         f.append("-fmad=false")
     if os.environ.get("PIC_PTXAS_VERBOSE"):
         f += ["-Xptxas", "-v"]

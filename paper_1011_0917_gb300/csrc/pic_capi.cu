@@ -80,6 +80,12 @@ struct pic_ctx {
     // change), the bound of the fixed-point current scales
     double wmax = 0;
 
+    // lab-frame snapshots (caller's device buffer)
+    bool btd_on = false;
+    pic_btd_params btd{};
+    unsigned char *btd_buf = nullptr;
+    size_t btd_flags_off = 0;
+
     bool plasma_loaded = false;
     pic_plasma_params plasma{};
     double prof[16] = {0};
@@ -670,6 +676,54 @@ struct PhaseTimer {
     }
 };
 
+static int btd_nxs(const pic_ctx *c, const pic_btd_params *p) { return p->plane ? c->g.nx : 1; }
+
+// Lab snapshot points whose event falls in this step (E0, B0: the fields at
+// its start, E1, B1 at its end): per snapshot a range of lab points that holds
+// them all (the kernel decides each point exactly).  Returns the launches.
+template <typename real>
+static int fill_btd(pic_ctx *c, real *const F0[9], real *const F1[6])
+{
+    const pic_btd_params &p = c->btd;
+    BtdArgs<real> a{};
+    a.g = c->g;
+    for (int q = 0; q < 3; ++q) {
+        a.E0[q] = F0[q];
+        a.B0[q] = F0[3 + q];
+        a.E1[q] = F1[q];
+        a.B1[q] = F1[3 + q];
+    }
+    a.data = reinterpret_cast<real *>(c->btd_buf);
+    a.flags = reinterpret_cast<int *>(c->btd_buf + c->btd_flags_off);
+    a.gam = c->gam;
+    a.beta = c->beta;
+    a.hz = c->hz;
+    a.t0 = c->t;
+    a.dt = c->dt;
+    a.T0 = p.t0;
+    a.dT = p.dt;
+    a.Z0 = p.z0;
+    a.dZ = p.dz;
+    a.nsnap = p.n_snapshots;
+    a.nz = p.nz;
+    a.nxs = btd_nxs(c, &p);
+    bool any = false;
+    for (int j = 0; j < p.n_snapshots; ++j) {
+        // t0 <= gamma (T - beta Z) < t0 + dt  <=>  Z in ((T - (t0+dt)/gamma)/beta, (T - t0/gamma)/beta]
+        const double T = p.t0 + j * p.dt;
+        const double zlo = (T - (c->t + c->dt) / c->gam) / c->beta, zhi = (T - c->t / c->gam) / c->beta;
+        double klo = std::floor((zlo - p.z0) / p.dz) - 1.0, khi = std::ceil((zhi - p.z0) / p.dz) + 1.0;
+        if (klo < 0.0) klo = 0.0;
+        if (khi > (double)(p.nz - 1)) khi = (double)(p.nz - 1);
+        a.klo[j] = (int)klo;
+        a.kn[j] = khi >= klo ? (int)(khi - klo) + 1 : 0;
+        any = any || a.kn[j] > 0;
+    }
+    if (!any) return 0;
+    launch_btd<real>(a, c->stream);
+    return 1;
+}
+
 template <typename real>
 static void run_phases_t(pic_ctx *c, unsigned mask)
 {
@@ -740,6 +794,7 @@ static void run_phases_t(pic_ctx *c, unsigned mask)
         launch_yee<real>(c->g, F, F1, c->dt, c->hx, c->hy, c->hz, c->stream);
         c->fset ^= 1;
         c->kernels += 1;
+        if (c->btd_on) c->kernels += fill_btd<real>(c, F, F1);
     }
     if ((mask & PIC_PH_INJECT) && c->plasma_loaded && c->gam > 1.0) {
         PhaseTimer pt(c, 6);
@@ -778,6 +833,66 @@ extern "C" pic_status pic_step_phases(pic_ctx *c, unsigned mask)
 {
     if (mask & ~PIC_PH_ALL) return fail(c, PIC_ERR_ARG, "unknown phase bits");
     return run_steps(c, 1, mask, true);
+}
+
+// ---------------------------------------------------------- lab snapshots
+
+static bool btd_valid(const pic_ctx *c, const pic_btd_params *p)
+{
+    return c->gam > 1.0 && p->n_snapshots >= 1 && p->n_snapshots <= 64 && p->nz >= 1 && p->dz > 0.0 &&
+           std::isfinite(p->t0) && std::isfinite(p->dt) && std::isfinite(p->z0) && std::isfinite(p->dz) &&
+           (p->plane == 0 || p->plane == 1) &&
+           (double)p->n_snapshots * 6.0 * p->nz * (p->plane ? c->g.nx : 1) < 4e12;
+}
+
+static size_t btd_data_bytes(const pic_ctx *c, const pic_btd_params *p)
+{
+    return align_up((size_t)p->n_snapshots * 6 * p->nz * btd_nxs(c, p) * c->es);
+}
+
+extern "C" pic_status pic_btd_bytes(const pic_ctx *c, const pic_btd_params *p, size_t *bytes)
+{
+    if (!c || !p || !bytes) return PIC_ERR_ARG;
+    if (!btd_valid(c, p)) return PIC_ERR_ARG;
+    *bytes = btd_data_bytes(c, p) + align_up(sizeof(int) * (size_t)p->n_snapshots * p->nz);
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_btd_setup(pic_ctx *c, const pic_btd_params *p, void *buf, size_t bytes)
+{
+    if (!c) return PIC_ERR_ARG;
+    if (!p) {
+        c->btd_on = false;
+        c->btd_buf = nullptr;
+        return PIC_OK;
+    }
+    if (!c->bound) return fail(c, PIC_ERR_STATE, "bind buffers first");
+    if (!btd_valid(c, p)) return fail(c, PIC_ERR_ARG, "invalid snapshot parameters (a boosted grid is needed)");
+    size_t need = 0;
+    pic_btd_bytes(c, p, &need);
+    if (!buf || bytes < need || ((uintptr_t)buf % kAlign) != 0)
+        return fail(c, PIC_ERR_ARG, "snapshot buffer too small or not 256-byte aligned");
+    c->btd = *p;
+    c->btd_buf = (unsigned char *)buf;
+    c->btd_flags_off = btd_data_bytes(c, p);
+    CUDA_TRY(c, cudaMemsetAsync(buf, 0, need, c->stream));
+    c->btd_on = true;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_btd_get(pic_ctx *c, int j, void *dst, size_t dst_bytes, int dst_is_device)
+{
+    if (!c || !dst) return PIC_ERR_ARG;
+    if (!c->btd_on) return fail(c, PIC_ERR_STATE, "no snapshots are being taken");
+    const pic_btd_params &p = c->btd;
+    if (j < 0 || j >= p.n_snapshots) return fail(c, PIC_ERR_ARG, "snapshot index out of range");
+    const size_t nd = (size_t)6 * p.nz * btd_nxs(c, &p) * c->es, nf = sizeof(int) * (size_t)p.nz;
+    if (dst_bytes < nd + nf) return fail(c, PIC_ERR_ARG, "destination too small");
+    CUDA_TRY(c, cudaMemcpyAsync(dst, c->btd_buf + (size_t)j * nd, nd, kind_out(dst_is_device), c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync((unsigned char *)dst + nd, c->btd_buf + c->btd_flags_off + (size_t)j * nf, nf,
+                                kind_out(dst_is_device), c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return PIC_OK;
 }
 
 // -------------------------------------------------------------------- output

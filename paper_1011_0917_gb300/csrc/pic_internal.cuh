@@ -247,6 +247,20 @@ struct CompactArgs {     // copy tiles into a flat list
     const int64_t *offset;
 };
 
+template <typename real>
+struct BtdArgs {         // lab-frame snapshots filled during one step
+    Geom g;
+    const real *E0[3], *B0[3];  // fields at the start of the step
+    const real *E1[3], *B1[3];  // and at its end
+    real *data;                 // [nsnap][6][nz][nxs]
+    int *flags;                 // [nsnap][nz]
+    double gam, beta, hz;
+    double t0, dt;              // the step's simulation-frame interval [t0, t0 + dt)
+    double T0, dT, Z0, dZ;      // lab times and positions of the snapshots
+    int nsnap, nz, nxs;
+    int klo[64], kn[64];        // per snapshot, the lab points this step may fill
+};
+
 struct InjectArgs {      // lattice load / boosted injection, FP64
     Geom g;
     double hx, hy, hz, Lx, Ly, Lz, gam, beta;
@@ -279,6 +293,8 @@ template <typename real>
 void launch_particle_sums(const Geom &g, const Species<real> &sp, const int *lo, const int *hi, double q,
                           const real ion_u[3], double *partials, int nblocks, cudaStream_t s);
 void launch_inject(const InjectArgs &a, cudaStream_t s);
+template <typename real>
+void launch_btd(const BtdArgs<real> &a, cudaStream_t s);
 
 template <typename real>
 void launch_yee(const Geom &g, real *const F[9], real *const F1[6], double dt, double hx, double hy, double hz,

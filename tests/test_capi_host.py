@@ -104,3 +104,28 @@ def test_calls_before_bind_are_rejected(P):
 def test_status_strings(P):
     for s in range(8):
         assert P.pic_status_string(s)
+
+
+def test_btd_bytes_and_validation(P):
+    # lab-frame snapshots: [nsnap][6][nz][nxs] elements, then nsnap * nz int32
+    # flags at a 256-byte boundary; an unboosted grid has none
+    g = grid(P, gamma_boost=5.0, dx=1.0, dz=1 / 32, nx=48, nz=256)
+    ctx = P.pic_init_grid(g)
+    try:
+        for plane, nxs in ((0, 1), (1, 48)):
+            p = P.BtdParams(4, 100.0, 5.0, 10.0, 1 / 32, 300, plane)
+            data = 4 * 6 * 300 * nxs * 4
+            align = lambda b: (b + 255) // 256 * 256
+            assert P.pic_btd_bytes(ctx, p) == align(data) + align(4 * 4 * 300)
+        for bad in (P.BtdParams(0, 0.0, 1.0, 0.0, 0.1, 10, 0), P.BtdParams(65, 0.0, 1.0, 0.0, 0.1, 10, 0),
+                    P.BtdParams(2, 0.0, 1.0, 0.0, -0.1, 10, 0), P.BtdParams(2, 0.0, 1.0, 0.0, 0.1, 10, 2)):
+            with pytest.raises(P.PicError):
+                P.pic_btd_bytes(ctx, bad)
+    finally:
+        P.pic_destroy(ctx)
+    ctx = P.pic_init_grid(grid(P))
+    try:
+        with pytest.raises(P.PicError):
+            P.pic_btd_bytes(ctx, P.BtdParams(1, 0.0, 1.0, 0.0, 0.1, 10, 0))
+    finally:
+        P.pic_destroy(ctx)
