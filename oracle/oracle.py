@@ -165,6 +165,10 @@ def _load():
         lib.opic_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
         lib.opic_uniform.restype = C.c_double
         lib.opic_uniform.argtypes = [C.c_uint64, C.c_uint64]
+        lib.opic_set_window.restype = C.c_int
+        lib.opic_set_window.argtypes = [P, C.c_double, C.c_double, C.c_int]
+        lib.opic_window.restype = C.c_double
+        lib.opic_window.argtypes = [P]
         lib.opic_btd_setup.restype = C.c_int
         lib.opic_btd_setup.argtypes = [P, C.POINTER(_Btd)]
         lib.opic_btd_data.restype = D
@@ -312,6 +316,17 @@ class Oracle:
     def zero_fields(self):
         for c in COMPONENTS:
             self.field(c)[...] = 0.0
+
+    # ------------------------------------------------------- moving window
+    def set_window(self, v: float, t0: float, shift_cells: int):
+        """Window moving at v along +z from t0, in moves of shift_cells cells
+        (v = 0: off)."""
+        if self.lib.opic_set_window(self.h, v, t0, shift_cells) != 0:
+            raise ValueError("oracle rejected the moving window")
+
+    @property
+    def z_window(self) -> float:
+        return self.lib.opic_window(self.h)
 
     # ------------------------------------------------ back-transformed data
     def btd_setup(self, b: "BtdParams | None"):

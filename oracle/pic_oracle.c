@@ -62,6 +62,11 @@ struct opic {
     int ka;
     double t;
     int64_t step;
+    /* moving window */
+    int win_on;
+    double win_v, win_t0;
+    int win_S;
+    int64_t win_n;
     /* back-transformed snapshots */
     int btd_on;
     opic_btd btd;
@@ -322,14 +327,17 @@ int64_t opic_load_plasma(opic *s, const opic_plasma *p)
                 if (!(n > 0.0))
                     continue;
                 const double w = n * wfac;
-                /* simulation-frame position at the current time */
-                const double zb = zlab / s->gam - s->beta * s->t;
+                /* simulation-frame position at the current time, relative to
+                   the window */
+                const double zb = zlab / s->gam - s->beta * s->t - opic_window(s);
                 if (zb >= 0.0 && zb < s->Lz) {
                     species_push(&s->sp[0], x, y, zb, 0.0, 0.0, uz0, w, L);
                     if (drift_ions)
                         species_push(&s->sp[1], x, y, zb, 0.0, 0.0, uz0, w, L);
                     ++placed;
-                } else if (boosted && zb >= s->Lz) {
+                } else if (zb >= s->Lz) {
+                    /* ahead of the box: enters later (drifting in, or when the
+                       window moves over it) */
                     if (s->npend == s->cappend) {
                         s->cappend = s->cappend ? 2 * s->cappend : 1024;
                         s->pend = (pending_particle *)realloc(s->pend, (size_t)s->cappend * sizeof(pending_particle));
@@ -355,16 +363,16 @@ int64_t opic_load_plasma(opic *s, const opic_plasma *p)
     return placed;
 }
 
-/* plasma whose simulation-frame position z/gamma - beta t crosses z = Lz during
-   (t, t + dt] enters the box at its position at t + dt */
-static void inject(opic *s)
+/* plasma whose simulation-frame position z/gamma - beta t1, relative to the
+   window, is below Lz enters the box there: called for t1 = t + dt (the
+   plasma that crossed z = Lz during the step) and after a window move */
+static void inject_at(opic *s, double t1)
 {
-    const double t1 = s->t + s->dt;
     const double uz0 = -(s->gam * s->beta);
     int64_t k = 0;
     while (k < s->npend) {
         pending_particle *q = &s->pend[k];
-        const double zb = q->zlab / s->gam - s->beta * t1;
+        const double zb = q->zlab / s->gam - s->beta * t1 - opic_window(s);
         if (zb < s->Lz) {
             species_push(&s->sp[0], q->x, q->y, zb, 0.0, 0.0, uz0, q->w, q->id);
             if (s->has_ions)
@@ -375,6 +383,8 @@ static void inject(opic *s)
         }
     }
 }
+
+static void inject(opic *s) { inject_at(s, s->t + s->dt); }
 
 /* ------------------------------------------------------------------ laser */
 
@@ -401,6 +411,10 @@ void opic_set_laser(opic *s, const opic_laser *l)
    argument by D (plane-wave Doppler transform along the boost). */
 static void antenna(opic *s)
 {
+    /* the antenna stays where it was launched; the window moves past it */
+    const int64_t ka = s->ka - s->win_n * s->win_S;
+    if (ka < 2)
+        return;
     const opic_laser *l = &s->las;
     const double D = 1.0 / (s->gam * (1.0 + s->beta));
     const double tau = l->fwhm / sqrt(2.0 * log(2.0));
@@ -420,7 +434,7 @@ static void antenna(opic *s)
             double r2 = (x - l->xc) * (x - l->xc);
             if (s->g.dim == 3)
                 r2 += (y - l->yc) * (y - l->yc);
-            s->f[c][fidx(s, i, j, s->ka)] += j0 * exp(-r2 / (l->waist * l->waist));
+            s->f[c][fidx(s, i, j, ka)] += j0 * exp(-r2 / (l->waist * l->waist));
         }
     }
 }
@@ -918,6 +932,56 @@ static void yee_e(opic *s)
     }
 }
 
+/* ------------------------------------------------------------ moving window */
+
+int opic_set_window(opic *s, double v, double t0, int S)
+{
+    if (v == 0.0) {
+        s->win_on = 0;
+        return 0;
+    }
+    if (!(v > 0.0 && v <= 1.0) || !isfinite(t0) || S < 1 || S >= s->g.nz || s->g.bc_z != 1)
+        return -1;
+    s->win_on = 1;
+    s->win_v = v;
+    s->win_t0 = t0;
+    s->win_S = S;
+    return 0;
+}
+
+double opic_window(const opic *s) { return (double)s->win_n * s->win_S * s->hz; }
+
+/* move the window by S cells: fields, particles, then the plasma it now covers */
+static void window_move(opic *s)
+{
+    const int S = s->win_S;
+    const int64_t plane = (int64_t)s->ny * s->g.nx;
+    double *bufs[OPIC_NCOMP + 1];
+    for (int c = 0; c < OPIC_NCOMP; ++c)
+        bufs[c] = s->f[c];
+    bufs[OPIC_NCOMP] = s->rho_bg;
+    for (int c = 0; c <= OPIC_NCOMP; ++c) {
+        double *f = bufs[c];
+        for (int64_t k = 0; k <= s->g.nz; ++k)
+            for (int64_t o = 0; o < plane; ++o)
+                f[k * plane + o] = k + S <= s->g.nz ? f[(k + S) * plane + o] : 0.0;
+    }
+    const double dz = S * s->hz;
+    for (int sp = 0; sp < 2; ++sp) {
+        species *p = &s->sp[sp];
+        int64_t k = 0;
+        while (k < p->n) {
+            p->a[OPIC_PZ][k] -= dz;
+            if (p->a[OPIC_PZ][k] < 0.0)
+                species_remove(p, k);
+            else
+                ++k;
+        }
+    }
+    s->win_n += 1;
+    inject_at(s, s->t);
+}
+
 /* --------------------------------------------- back-transformed snapshots */
 
 int opic_btd_setup(opic *s, const opic_btd *b)
@@ -994,7 +1058,7 @@ static void btd_fill(opic *s, double t0)
             const double tp = gam * (T - beta * Z);
             if (!(tp >= t0 && tp < t0 + s->dt))
                 continue;
-            const double zp = gam * (Z - beta * T);
+            const double zp = gam * (Z - beta * T) - opic_window(s);
             const double th = (tp - t0) / s->dt;
             int ok = 1;
             double v[6][2];
@@ -1054,6 +1118,9 @@ void opic_step_phases(opic *s, unsigned mask)
     if (mask & OPIC_PH_TIME) {
         s->t += s->dt;
         s->step += 1;
+        if (s->win_on && s->t >= s->win_t0 &&
+            s->win_v * (s->t - s->win_t0) >= (double)(s->win_n + 1) * s->win_S * s->hz)
+            window_move(s);
     }
 }
 

@@ -126,6 +126,21 @@ double *opic_rho_background(opic *s);
 void opic_step(opic *s, int nsteps);
 void opic_step_phases(opic *s, unsigned mask);
 
+/* Moving window (the paper's gamma = 1 and 5 runs: "a moving window
+   propagating at the group velocity v_g", section "Effect of the hyperbolic
+   rotation in Minkowski space").  From time t0 on, the window (the grid) moves
+   along +z at velocity v (0 < v <= 1); whenever its displacement
+   v (t - t0) reaches (n + 1) S hz after the TIME phase, the window moves by S
+   cells at once (n counts the moves): every field plane k takes plane k + S,
+   the top S planes become zero, particle z decreases by S hz (particles below
+   z = 0 are removed), the antenna plane moves S planes down (it stops below
+   plane 2), and the plasma of the newly covered layer enters.  Positions stay
+   relative to the window; opic_window() is its displacement n S hz.  Parity
+   status: pinned (a pulse in the window matches the same pulse in a long
+   fixed box; a static plasma seen through the window is the lattice). */
+int opic_set_window(opic *s, double v, double t0, int S);   /* 0, or -1 on bad arguments */
+double opic_window(const opic *s);
+
 /* back-transformed snapshots: setup (0, or -1 on bad arguments or gamma = 1;
    NULL switches them off), then per snapshot j the fields [6][nz][nxs]
    (Ex Ey Ez Bx By Bz, nxs = 1 or nx) and nz fill flags */
