@@ -256,10 +256,13 @@ def run_ours(args, rank, world, local):
         gam, beta = g["gamma_boost"], sz.beta
         lz = g["nz"] * sz.hz
         tnow = sim.diagnostics().t
+        # snapshot j at lab time t_first + j (lambda0/c) covers lab z in
+        # [beta T_j, beta T_j + Lz / gamma]; the run is passing the events at
+        # the middle of the box for every one of them
         t_first = gam * (tnow + 0.5 * beta * lz)
         z0 = beta * t_first - 1.0
-        nz_lab = int((lz / gam + 2.0 + args.btd * sz.dt) / g["dz"])
-        sim.btd_setup(args.btd, t_first, gam * sz.dt, z0, g["dz"], nz_lab, 1)
+        nz_lab = int((lz / gam + 2.0 + args.btd * beta) / g["dz"])
+        sim.btd_setup(args.btd, t_first, 1.0, z0, g["dz"], nz_lab, 1)
         P.pic_step(ctx, k)
         btd_ms, btd_calls, _ = P.pic_profile_read(ctx)
         P.pic_profile(ctx, False)

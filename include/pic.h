@@ -165,6 +165,8 @@ typedef struct pic_diag {
     double field_energy;       /* (1/2) sum (E^2 + B^2) V, Kahan-compensated FP64   */
     double kinetic_energy;     /* sum w (gamma - 1) of the electrons, FP64 Kahan   */
     double charge;             /* sum q w of both species, FP64 Kahan              */
+    double z_window;           /* moving window displacement (positions, fields    */
+                               /* and rho are relative to it), lambda0             */
 } pic_diag;
 
 /* ---------------------------------------------------------------- set-up */
@@ -252,6 +254,24 @@ pic_status pic_get_rho(pic_ctx *ctx, void *dst, size_t dst_bytes, int dst_is_dev
 
 /* Time, counts and FP64 Kahan-compensated sums (synchronises the stream). */
 pic_status pic_get_diagnostics(pic_ctx *ctx, pic_diag *out);
+
+/* ---------------------------------------------------------- moving window */
+
+/* Moving window (the paper's gamma = 1 and gamma = 5 runs used "a moving
+   window propagating at the group velocity v_g of the laser in the plasma",
+   section "Effect of the hyperbolic rotation in Minkowski space").  From
+   simulation time t0 on the grid moves along +z at velocity v (0 < v <= 1, in
+   c): after the TIME phase of a step at which v (t - t0) >= (n + 1) S hz (n
+   the moves so far), it moves by shift_cells = S cells at once: every field
+   plane k takes plane k + S and the top S planes become zero, particles move
+   S cells down in the grid (those below z = 0 leave), the plasma of the newly
+   covered layer enters at its position at that time, and the antenna, which
+   stays where it was launched, is switched off once it is below plane 2.
+   Positions, fields, rho and snapshots are relative to the window; its
+   displacement n S hz is pic_diag.z_window.  S must be a positive multiple of
+   the tile's z extent (8 in 3D, 16 in 2D) below nz, and z absorbing
+   (PIC_BC_MUR); v = 0 switches the window off (PIC_ERR_ARG otherwise). */
+pic_status pic_set_moving_window(pic_ctx *ctx, double v, double t0, int shift_cells);
 
 /* ------------------------------------------------- lab-frame snapshots */
 

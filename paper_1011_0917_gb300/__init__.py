@@ -23,7 +23,7 @@ __all__ = [
     "pic_get_axis", "pic_get_particles", "pic_get_rho", "pic_get_diagnostics", "pic_state_bytes",
     "pic_get_state", "pic_set_state", "pic_last_error", "pic_status_string", "pic_destroy", "pic_profile",
     "pic_profile_read", "pic_filter_current_noalloc", "PIC_NOALLOC_MAX_NODES", "BtdParams", "pic_btd_bytes",
-    "pic_btd_setup", "pic_btd_get", "Simulation", "library_path",
+    "pic_btd_setup", "pic_btd_get", "pic_set_moving_window", "Simulation", "library_path",
 ]
 
 PIC_OK, PIC_ERR_ARG, PIC_ERR_STATE, PIC_ERR_CUDA = 0, 1, 2, 3
@@ -79,7 +79,7 @@ class LaserParams(C.Structure):
 
 class Diag(C.Structure):
     _fields_ = [("t", C.c_double), ("step", C.c_int64), ("n_particles", C.c_int64 * 2), ("n_paired", C.c_int64),
-                ("field_energy", C.c_double), ("kinetic_energy", C.c_double), ("charge", C.c_double)]
+                ("field_energy", C.c_double), ("kinetic_energy", C.c_double), ("charge", C.c_double), ("z_window", C.c_double)]
 
 
 _lib = None
@@ -128,6 +128,7 @@ def _load():
         "pic_profile": (S, [P, I]),
         "pic_profile_read": (S, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "pic_filter_current_noalloc": (S, [I, I, I, I, I, I, I, P, P, P, P]),
+        "pic_set_moving_window": (S, [P, C.c_double, C.c_double, I]),
         "pic_btd_bytes": (S, [P, C.POINTER(BtdParams), C.POINTER(C.c_size_t)]),
         "pic_btd_setup": (S, [P, C.POINTER(BtdParams), P, C.c_size_t]),
         "pic_btd_get": (S, [P, I, P, C.c_size_t, I]),
@@ -292,6 +293,10 @@ def pic_filter_current_noalloc(dim: int, nx: int, ny: int, nz: int, bc_z: int, p
         raise PicError(st, detail)
 
 
+def pic_set_moving_window(ctx, v: float, t0: float, shift_cells: int):
+    _check(ctx, _load().pic_set_moving_window(ctx, v, t0, shift_cells))
+
+
 def pic_btd_bytes(ctx, p: BtdParams) -> int:
     n = C.c_size_t(0)
     _check(ctx, _load().pic_btd_bytes(ctx, C.byref(p), C.byref(n)))
@@ -403,6 +408,9 @@ class Simulation:
 
     def diagnostics(self) -> Diag:
         return pic_get_diagnostics(self.ctx)
+
+    def set_moving_window(self, v, t0, shift_cells):
+        pic_set_moving_window(self.ctx, v, t0, shift_cells)
 
     def btd_setup(self, n_snapshots, t0, dt, z0, dz, nz, plane=0):
         """Lab-frame snapshots into a torch device buffer owned by this object."""

@@ -29,7 +29,7 @@ __global__ void btd_kernel(BtdArgs<real> a)
     const double Z = a.Z0 + k * a.dZ;
     const double tp = a.gam * (T - a.beta * Z);
     if (!(tp >= a.t0 && tp < a.t0 + a.dt)) return;
-    const double zp = a.gam * (Z - a.beta * T);
+    const double zp = a.gam * (Z - a.beta * T) - a.zwin;
     const double th = (tp - a.t0) / a.dt;
     const int i = a.nxs == 1 ? g.nx / 2 : is;
     const int jc = g.ny / 2;

@@ -46,7 +46,10 @@ struct StateHeader {
     pic_laser_params laser;
     int32_t cur[2];
     double wmax;  // bound of the particle weights (fixed-point current scales)
-    char pad[512 - 8 - 8 * 4 - 16 - 8 - 8 - sizeof(pic_laser_params) - 8 - 8];
+    double win_v, win_t0;
+    int32_t win_on, win_S;
+    int64_t win_n;
+    char pad[512 - 8 - 8 * 4 - 16 - 8 - 8 - sizeof(pic_laser_params) - 8 - 8 - 16 - 8 - 8];
 };
 static_assert(sizeof(StateHeader) == 512, "state header must be 512 bytes");
 
@@ -79,6 +82,13 @@ struct pic_ctx {
     // largest |weight| any particle loaded so far carries (weights never
     // change), the bound of the fixed-point current scales
     double wmax = 0;
+
+    // moving window: from t0 on it moves at v along +z, by S cells at a time
+    bool win_on = false;
+    double win_v = 0, win_t0 = 0;
+    int win_S = 0;
+    int64_t win_n = 0;  // moves so far
+    double zwin() const { return (double)win_n * win_S * hz; }
 
     // lab-frame snapshots (caller's device buffer)
     bool btd_on = false;
@@ -390,6 +400,8 @@ static void fill_inject_common(pic_ctx *c, InjectArgs &a)
     a.nprof = p.n_profile;
     for (int m = 0; m < 16; ++m) a.prof[m] = m < p.n_profile ? c->prof[m] : 0.0;
     a.seed = c->p.seed;
+    a.zwin = c->zwin();
+    a.zmin = 0.0;
     a.drift_ions = (p.ions && c->ions_species) ? 1 : 0;
     a.paired = (a.drift_ions && !c->p.explicit_ions) ? 1 : 0;
     a.precision = c->p.precision;
@@ -445,7 +457,8 @@ extern "C" pic_status pic_load_plasma(pic_ctx *c, const pic_plasma_params *p)
     a.t = c->t;
     a.t1 = c->t;
     // every lattice plane whose simulation-frame position lies in [0, Lz)
-    lattice_band(a, c->gam * (c->beta * c->t), c->gam * (c->Lz + c->beta * c->t), a.m_lo, a.m_hi);
+    lattice_band(a, c->gam * (c->zwin() + c->beta * c->t), c->gam * (c->zwin() + c->Lz + c->beta * c->t), a.m_lo,
+                 a.m_hi);
     launch_inject(a, c->stream);
     CUDA_TRY(c, cudaGetLastError());
     return check_device_error(c);
@@ -676,6 +689,55 @@ struct PhaseTimer {
     }
 };
 
+// Move the window by S cells: fields (E, B into the other buffer, J through
+// the scratch buffer), each species' buckets m = S / tz tile layers down, then
+// the plasma of the newly covered layer [Lz - S hz, Lz) (relative to the
+// moved window) at the current time.
+template <typename real>
+static void window_move(pic_ctx *c)
+{
+    const int S = c->win_S;
+    real *src[9], *dst[9];
+    for (int q = 0; q < 6; ++q) {
+        src[q] = (real *)field_ptr(c, q);
+        dst[q] = (real *)eb_other(c, q);
+    }
+    real *tmp = (real *)(c->scratch + c->off_tmp);
+    for (int q = 0; q < 3; ++q) {
+        src[6 + q] = (real *)field_ptr(c, 6 + q);
+        dst[6 + q] = tmp + (size_t)q * c->g.ncomp;
+    }
+    launch_window_fields<real>(c->g, src, dst, S, c->stream);
+    cudaMemcpyAsync(field_ptr(c, 6), tmp, (size_t)3 * c->g.ncomp * sizeof(real), cudaMemcpyDeviceToDevice,
+                    c->stream);
+    c->fset ^= 1;
+    c->kernels += 1;
+    const int m = S >> c->g.lt[2];
+    for (int sp = 0; sp < 2; ++sp) {
+        if (sp == 1 && !c->ions_species) break;
+        launch_window_particles<real>(c->g, species_view<real>(c, sp, c->cur[sp]),
+                                      species_view<real>(c, sp, c->cur[sp] ^ 1), counts(c, sp, c->cur[sp], 0),
+                                      counts(c, sp, c->cur[sp], 1), counts(c, sp, c->cur[sp] ^ 1, 0),
+                                      counts(c, sp, c->cur[sp] ^ 1, 1), m, S, c->stream);
+        cudaMemsetAsync(counts(c, sp, c->cur[sp], 0), 0, sizeof(int) * 2 * (size_t)c->g.ntiles, c->stream);
+        c->cur[sp] ^= 1;
+        c->kernels += 1;
+    }
+    c->win_n += 1;
+    if (c->plasma_loaded) {
+        InjectArgs a{};
+        fill_inject_common(c, a);
+        a.mode = 0;
+        a.t = c->t;
+        a.t1 = c->t;
+        a.zmin = c->Lz - S * c->hz;
+        lattice_band(a, c->gam * (c->zwin() + a.zmin + c->beta * c->t), c->gam * (c->zwin() + c->Lz + c->beta * c->t),
+                     a.m_lo, a.m_hi);
+        launch_inject(a, c->stream);
+        if (a.m_hi > a.m_lo) c->kernels += 1;
+    }
+}
+
 static int btd_nxs(const pic_ctx *c, const pic_btd_params *p) { return p->plane ? c->g.nx : 1; }
 
 // Lab snapshot points whose event falls in this step (E0, B0: the fields at
@@ -698,6 +760,7 @@ static int fill_btd(pic_ctx *c, real *const F0[9], real *const F1[6])
     a.gam = c->gam;
     a.beta = c->beta;
     a.hz = c->hz;
+    a.zwin = c->zwin();
     a.t0 = c->t;
     a.dt = c->dt;
     a.T0 = p.t0;
@@ -758,7 +821,9 @@ static void run_phases_t(pic_ctx *c, unsigned mask)
         c->cur[1] ^= 1;
         c->kernels += 1;
     }
-    if ((mask & PIC_PH_ANTENNA) && c->laser_on) {
+    // the antenna stays where it was launched; a moving window leaves it behind
+    const int64_t ka_rel = (int64_t)c->ka - c->win_n * c->win_S;
+    if ((mask & PIC_PH_ANTENNA) && c->laser_on && ka_rel >= 2) {
         PhaseTimer pt(c, 3);
         // the lab laser seen by an antenna at rest in the boosted frame:
         // amplitude and time argument scaled by D = gamma (1 - beta)
@@ -772,7 +837,7 @@ static void run_phases_t(pic_ctx *c, unsigned mask)
         const double amp = l.a0 * D * env * std::sin(kTwoPi * sr);
         const double j0 = -amp / (kPi * c->hz);
         const int comp = l.polarization == PIC_POL_X ? 0 : 1;
-        launch_antenna<real>(c->g, R[comp], l.polarization, c->ka, j0, c->hx, c->hy, l.x_center, l.y_center,
+        launch_antenna<real>(c->g, R[comp], l.polarization, (int)ka_rel, j0, c->hx, c->hy, l.x_center, l.y_center,
                              l.waist, c->stream);
         c->kernels += 1;
     }
@@ -803,13 +868,17 @@ static void run_phases_t(pic_ctx *c, unsigned mask)
         a.mode = 1;
         a.t = c->t;
         a.t1 = c->t + c->dt;
-        lattice_band(a, c->gam * (c->Lz + c->beta * a.t), c->gam * (c->Lz + c->beta * a.t1), a.m_lo, a.m_hi);
+        lattice_band(a, c->gam * (c->zwin() + c->Lz + c->beta * a.t), c->gam * (c->zwin() + c->Lz + c->beta * a.t1),
+                     a.m_lo, a.m_hi);
         launch_inject(a, c->stream);
         if (a.m_hi > a.m_lo) c->kernels += 1;
     }
     if (mask & PIC_PH_TIME) {
         c->t += c->dt;
         c->step += 1;
+        if (c->win_on && c->t >= c->win_t0 &&
+            c->win_v * (c->t - c->win_t0) >= (double)(c->win_n + 1) * c->win_S * c->hz)
+            window_move<real>(c);
     }
 }
 
@@ -833,6 +902,27 @@ extern "C" pic_status pic_step_phases(pic_ctx *c, unsigned mask)
 {
     if (mask & ~PIC_PH_ALL) return fail(c, PIC_ERR_ARG, "unknown phase bits");
     return run_steps(c, 1, mask, true);
+}
+
+// ---------------------------------------------------------- moving window
+
+extern "C" pic_status pic_set_moving_window(pic_ctx *c, double v, double t0, int shift_cells)
+{
+    if (!c) return PIC_ERR_ARG;
+    if (v == 0.0) {
+        c->win_on = false;
+        return PIC_OK;
+    }
+    const int tz = 1 << c->g.lt[2];
+    if (!(v > 0.0 && v <= 1.0) || !std::isfinite(t0) || shift_cells < tz || shift_cells % tz != 0 ||
+        shift_cells >= c->g.nz || c->g.bc_z != PIC_BC_MUR)
+        return fail(c, PIC_ERR_ARG, "moving window: 0 < v <= 1, absorbing z, and moves of a whole number of tile "
+                                    "layers smaller than the grid");
+    c->win_on = true;
+    c->win_v = v;
+    c->win_t0 = t0;
+    c->win_S = shift_cells;
+    return PIC_OK;
 }
 
 // ---------------------------------------------------------- lab snapshots
@@ -1160,6 +1250,7 @@ extern "C" pic_status pic_get_diagnostics(pic_ctx *c, pic_diag *out)
     std::memset(out, 0, sizeof(*out));
     out->t = c->t;
     out->step = c->step;
+    out->z_window = c->zwin();
     for (int sp = 0; sp < 2; ++sp) {
         if (sp == 1 && !c->ions_species) break;
         std::vector<int64_t> off;
@@ -1216,6 +1307,11 @@ static pic_status get_state_t(pic_ctx *c, unsigned char *dst, size_t dst_bytes, 
     h.step = c->step;
     h.laser = c->laser;
     h.wmax = c->wmax;
+    h.win_on = c->win_on;
+    h.win_v = c->win_v;
+    h.win_t0 = c->win_t0;
+    h.win_S = c->win_S;
+    h.win_n = c->win_n;
     int64_t n[2] = {0, 0};
     for (int sp = 0; sp < (c->ions_species ? 2 : 1); ++sp) {
         pic_status s = compact_t<real>(c, sp, n[sp]);
@@ -1287,6 +1383,11 @@ static pic_status set_state_t(pic_ctx *c, const unsigned char *src, size_t src_b
         if (s != PIC_OK) return s;
     }
     c->wmax = h.wmax;
+    c->win_on = h.win_on != 0;
+    c->win_v = h.win_v;
+    c->win_t0 = h.win_t0;
+    c->win_S = h.win_S;
+    c->win_n = h.win_n;
     c->t = h.t;
     c->step = h.step;
     c->laser_on = h.laser_on != 0;

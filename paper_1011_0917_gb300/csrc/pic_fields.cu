@@ -15,6 +15,11 @@
 namespace pic {
 
 template <typename real>
+struct Ptr9 {
+    real *p[9];
+};
+
+template <typename real>
 struct YeeArgs {
     Geom g;
     const real *E[3], *B[3];  // E^n, B^n
@@ -306,6 +311,32 @@ void launch_yee(const Geom &g, real *const F[9], real *const F1[6], double dt, d
             cudaFuncSetAttribute(yee_kernel<real, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         yee_kernel<real, 2><<<grid, 256, smem, s>>>(a);
     }
+}
+
+// ---------------------------------------------------------- moving window
+
+// dst plane k = src plane k + S (zero for k + S > nz), nine components
+template <typename real>
+__global__ void window_fields_kernel(Geom g, Ptr9<real> src, Ptr9<real> dst, int S)
+{
+    const int64_t n = 9 * g.ncomp;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(q / g.ncomp);
+        const int64_t o = q - c * g.ncomp;
+        const int64_t k = o / g.plane;
+        dst.p[c][o] = k + S <= g.nz ? src.p[c][o + S * g.plane] : real(0);
+    }
+}
+
+template <typename real>
+void launch_window_fields(const Geom &g, real *const src[9], real *const dst[9], int S, cudaStream_t s)
+{
+    Ptr9<real> a, b;
+    for (int c = 0; c < 9; ++c) {
+        a.p[c] = src[c];
+        b.p[c] = dst[c];
+    }
+    window_fields_kernel<real><<<grid_for(9 * g.ncomp, 256), 256, 0, s>>>(g, a, b, S);
 }
 
 // ---------------------------------------------------------------- filter
@@ -600,6 +631,7 @@ void launch_field_sums(const Geom &g, real *const F[9], double *partials, int nb
                                    double, cudaStream_t);                                               \
     template void launch_filter<real>(const Geom &, real *const[3], real *, int, cudaStream_t);         \
     template bool launch_filter_from<real>(const Geom &, const real *, real *const[3], int, cudaStream_t); \
+    template void launch_window_fields<real>(const Geom &, real *const[9], real *const[9], int, cudaStream_t); \
     template void launch_antenna<real>(const Geom &, real *, int, int, double, double, double, double,  \
                                        double, double, cudaStream_t);                                   \
     template void launch_field_sums<real>(const Geom &, real *const[9], double *, int, cudaStream_t);

@@ -117,12 +117,13 @@ __global__ void inject_kernel(InjectArgs a)
             if (n > 0.0) {
                 bool take;
                 double zb;
+                // simulation-frame positions relative to the (moving) window
                 if (a.mode == 0) {
-                    zb = zlab / a.gam - a.beta * a.t;
-                    take = zb >= 0.0 && zb < a.Lz;
+                    zb = zlab / a.gam - a.beta * a.t - a.zwin;
+                    take = zb >= a.zmin && zb < a.Lz;
                 } else {
-                    const double zb0 = zlab / a.gam - a.beta * a.t;
-                    zb = zlab / a.gam - a.beta * a.t1;
+                    const double zb0 = zlab / a.gam - a.beta * a.t - a.zwin;
+                    zb = zlab / a.gam - a.beta * a.t1 - a.zwin;
                     take = zb0 >= a.Lz && zb < a.Lz;
                 }
                 if (take) {

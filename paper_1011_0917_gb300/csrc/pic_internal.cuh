@@ -255,6 +255,7 @@ struct BtdArgs {         // lab-frame snapshots filled during one step
     real *data;                 // [nsnap][6][nz][nxs]
     int *flags;                 // [nsnap][nz]
     double gam, beta, hz;
+    double zwin;                // window displacement (simulation-frame positions are relative to it)
     double t0, dt;              // the step's simulation-frame interval [t0, t0 + dt)
     double T0, dT, Z0, dZ;      // lab times and positions of the snapshots
     int nsnap, nz, nxs;
@@ -270,8 +271,10 @@ struct InjectArgs {      // lattice load / boosted injection, FP64
     int nprof;
     double prof[16];
     uint64_t seed;
-    int mode;           // 0: in the box at t; 1: crossing z = Lz during (t, t1]
+    int mode;           // 0: in [zmin, Lz) at t; 1: crossing z = Lz during (t, t1]
     double t, t1;
+    double zwin;        // window displacement (positions are relative to it)
+    double zmin;        // lower end of a mode-0 load (0, or the layer a window move uncovers)
     int drift_ions;     // ions drift with the plasma
     int paired;         // electrons are placed paired with their ion (no ion record)
     int precision;      // 0 float, 1 double
@@ -295,6 +298,15 @@ void launch_particle_sums(const Geom &g, const Species<real> &sp, const int *lo,
 void launch_inject(const InjectArgs &a, cudaStream_t s);
 template <typename real>
 void launch_btd(const BtdArgs<real> &a, cudaStream_t s);
+// moving window: every field plane k of dst takes plane k + S of src (zero
+// above), for the nine components
+template <typename real>
+void launch_window_fields(const Geom &g, real *const src[9], real *const dst[9], int S, cudaStream_t s);
+// moving window: the bucket of tile t of the output side takes the bucket of
+// tile t + m ntx nty of the input side with every cell index S = m tz lower
+template <typename real>
+void launch_window_particles(const Geom &g, const Species<real> &in, const Species<real> &out, const int *in_lo,
+                             const int *in_hi, int *out_lo, int *out_hi, int m, int S, cudaStream_t s);
 
 template <typename real>
 void launch_yee(const Geom &g, real *const F[9], real *const F1[6], double dt, double hx, double hy, double hz,

@@ -822,6 +822,50 @@ static void dispatch_push(const PushArgs<real> &a, bool ions, cudaStream_t s)
 template <typename real> void launch_push(const PushArgs<real> &a, cudaStream_t s) { dispatch_push(a, false, s); }
 template <typename real> void launch_ions(const PushArgs<real> &a, cudaStream_t s) { dispatch_push(a, true, s); }
 
+// --------------------------------------------------------- moving window
+
+// One CTA per output tile: it copies the bucket of the input tile m layers
+// above (same slots, both runs) with the cell index S = m tz lower; the top m
+// layers are left empty and the bottom m layers of the input are dropped.
+template <typename real>
+__global__ void window_particles_kernel(Geom g, Species<real> in, Species<real> out, const int *in_lo,
+                                        const int *in_hi, int *out_lo, int *out_hi, int m, int S)
+{
+    const int64_t ntxy = (int64_t)g.nt[0] * g.nt[1];
+    const int64_t t = blockIdx.x;
+    const int64_t tz = t / ntxy;
+    int n_lo = 0, n_hi = 0;
+    if (tz + m < g.nt[2]) bucket_counts(in_lo, in_hi, t + m * ntxy, g.cap, n_lo, n_hi, nullptr);
+    if (threadIdx.x == 0) {
+        out_lo[t] = n_lo;
+        out_hi[t] = n_hi;
+    }
+    const int n = n_lo + n_hi;
+    const uint32_t dk = (uint32_t)S << (g.bx + g.by);
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        const int64_t d = bucket_slot(t, g.cap, n_lo, n_hi, p);
+        const int64_t s = d + m * ntxy * (int64_t)g.cap;
+        out.ox[d] = in.ox[s];
+        if (g.dim == 3) out.oy[d] = in.oy[s];
+        out.oz[d] = in.oz[s];
+        out.w[d] = in.w[s];
+        if (in.ux) {
+            out.ux[d] = in.ux[s];
+            out.uy[d] = in.uy[s];
+            out.uz[d] = in.uz[s];
+        }
+        out.cell[d] = (int32_t)((uint32_t)in.cell[s] - dk);  // keeps the pair bit
+        if (in.id) out.id[d] = in.id[s];
+    }
+}
+
+template <typename real>
+void launch_window_particles(const Geom &g, const Species<real> &in, const Species<real> &out, const int *in_lo,
+                             const int *in_hi, int *out_lo, int *out_hi, int m, int S, cudaStream_t s)
+{
+    window_particles_kernel<real><<<(unsigned)g.ntiles, 256, 0, s>>>(g, in, out, in_lo, in_hi, out_lo, out_hi, m, S);
+}
+
 // ------------------------------------------------------ bucket / compact
 
 template <typename real>
@@ -1017,6 +1061,8 @@ void launch_particle_sums(const Geom &g, const Species<real> &sp, const int *lo,
 
 #define PIC_INSTANTIATE(real)                                                                       \
     template void launch_push<real>(const PushArgs<real> &, cudaStream_t);                          \
+    template void launch_window_particles<real>(const Geom &, const Species<real> &, const Species<real> &, \
+                                                const int *, const int *, int *, int *, int, int, cudaStream_t); \
     template void launch_ions<real>(const PushArgs<real> &, cudaStream_t);                          \
     template void launch_bucket<real>(const BucketArgs<real> &, cudaStream_t);                      \
     template void launch_compact<real>(const CompactArgs<real> &, cudaStream_t);                    \

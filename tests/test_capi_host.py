@@ -129,3 +129,22 @@ def test_btd_bytes_and_validation(P):
             P.pic_btd_bytes(ctx, P.BtdParams(1, 0.0, 1.0, 0.0, 0.1, 10, 0))
     finally:
         P.pic_destroy(ctx)
+
+
+def test_moving_window_validation(P):
+    ctx = P.pic_init_grid(grid(P, nz=512))
+    try:
+        P.pic_set_moving_window(ctx, 0.99, 1.0, 16)      # one 2D tile layer
+        P.pic_set_moving_window(ctx, 1.0, 0.0, 32)
+        P.pic_set_moving_window(ctx, 0.0, 0.0, 0)        # off
+        for v, s in ((1.2, 16), (-0.5, 16), (0.9, 8), (0.9, 24), (0.9, 512)):
+            with pytest.raises(P.PicError):
+                P.pic_set_moving_window(ctx, v, 0.0, s)
+    finally:
+        P.pic_destroy(ctx)
+    ctx = P.pic_init_grid(grid(P, bc_z=0))
+    try:
+        with pytest.raises(P.PicError):
+            P.pic_set_moving_window(ctx, 0.9, 0.0, 16)   # periodic z has no window
+    finally:
+        P.pic_destroy(ctx)
