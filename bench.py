@@ -60,6 +60,8 @@ def parse():
                     help="skip the second, shorter timing of the same stage with explicit ion records")
     ap.add_argument("--btd", type=int, default=16,
                     help="lab-frame (x, z)-plane snapshots timed after the main measurement (0: none)")
+    ap.add_argument("--c4", type=int, default=64,
+                    help="runs of the batched scan timed after the main measurement (0: none)")
     return ap.parse_args()
 
 
@@ -303,6 +305,8 @@ def run_ours(args, rank, world, local):
                     "ions_ms_per_launch": xph[2] / max(xcalls[2], 1)}
         sim.close()
 
+    c4 = run_c4(P, torch, args.c4, args.warmup, max(1, min(args.steps, 10))) if args.c4 > 0 else None
+
     result = None
     if rank == 0:
         cpu = None if args.no_cpu_baseline else cpu_baseline(args.workload, steps=20)
@@ -335,11 +339,55 @@ def run_ours(args, rank, world, local):
             "adjoint_forward_ratio": None,
             "explicit_ion_records": explicit,
             "lab_frame_snapshots": btd,
+            "batched_c4": c4,
         }
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return result
+
+
+def run_c4(P, torch, nruns, warmup, steps):
+    """The batched scan: nruns independent 2D3V boosted runs (c4 recipe), each
+    on its own stream, stepped together by pic_batch_step; and the same runs
+    stepped one after another on one stream.  Aggregate electron
+    particle-steps/s of both."""
+    from paper_1011_0917_gb300 import workloads as W
+    sims = []
+    for r in range(nruns):
+        st = W.c4_run(r)
+        g = st.grid
+        sim = P.Simulation(dim=2, nx=g["nx"], ny=1, nz=g["nz"], dx=g["dx"], dz=g["dz"], cfl=g["cfl"],
+                           gamma_boost=g["gamma_boost"], filter_passes=g["filter_passes"], precision=P.PIC_FP32,
+                           seed=g["seed"], slots_per_cell=6.0, stream=torch.cuda.Stream())
+        p = st.plasma
+        sim.load_plasma(p["ne"], p["z_start"], p["z_end"], p["ramp"], p["ppc"], p["jitter"], p["profile"], p["ions"])
+        l = st.laser
+        sim.launch_laser(l["a0"], l["waist"], l["fwhm"], 0.0, -1.0, 1)
+        sims.append(sim)
+    batch = P.Batch(sims)
+    batch.step(warmup)
+    n0 = sum(s.diagnostics().n_particles[0] for s in sims)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batch.step(steps)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    # the same runs one after another on a single stream (each pic_step waits)
+    t0 = time.perf_counter()
+    for s in sims:
+        P.pic_step(s.ctx, steps)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    batch.close()
+    for s in sims:
+        s.close()
+    torch.cuda.empty_cache()
+    return {"runs": nruns, "steps": steps, "electrons": n0, "value": n0 * steps / t_batch,
+            "ms_per_step": 1e3 * t_batch / steps, "sequential_value": n0 * steps / t_seq,
+            "speedup_vs_sequential": t_seq / t_batch,
+            "note": "2D3V boosted runs, gamma in {5, 13, 30}, nz in [1024, 4096], nx = 128, 2x2 per cell, "
+                    "8-coefficient profile, a0 in [0.5, 2]; host wall clock around pic_batch_step"}
 
 
 def make_sim(P, st, slots_per_cell, stream, explicit_ions, advance):

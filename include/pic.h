@@ -255,6 +255,23 @@ pic_status pic_get_rho(pic_ctx *ctx, void *dst, size_t dst_bytes, int dst_is_dev
 /* Time, counts and FP64 Kahan-compensated sums (synchronises the stream). */
 pic_status pic_get_diagnostics(pic_ctx *ctx, pic_diag *out);
 
+/* ------------------------------------------------------------------ batch */
+
+/* Several independent runs stepped together (a scan over stage parameters:
+   different boosts, grid lengths, density profiles, laser amplitudes).
+   pic_batch_step issues one step of every context in turn before the next
+   step; each context's work goes on its own stream (pic_grid_params.stream:
+   give every context a distinct stream so that their kernels run
+   concurrently), and every context's device error word is checked at the end
+   (the first failure is returned; pic_last_error of each context has its
+   detail).  The batch holds pointers only: the contexts stay the caller's and
+   must outlive it.  PIC_ERR_STATE if a context is not bound, PIC_ERR_ARG for
+   n < 1 or a context listed twice. */
+typedef struct pic_batch pic_batch;
+pic_status pic_batch_create(pic_ctx *const *ctxs, int n, pic_batch **out);
+pic_status pic_batch_step(pic_batch *batch, int nsteps);
+void pic_batch_destroy(pic_batch *batch);
+
 /* ---------------------------------------------------------- moving window */
 
 /* Moving window (the paper's gamma = 1 and gamma = 5 runs used "a moving

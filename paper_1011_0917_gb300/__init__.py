@@ -23,7 +23,8 @@ __all__ = [
     "pic_get_axis", "pic_get_particles", "pic_get_rho", "pic_get_diagnostics", "pic_state_bytes",
     "pic_get_state", "pic_set_state", "pic_last_error", "pic_status_string", "pic_destroy", "pic_profile",
     "pic_profile_read", "pic_filter_current_noalloc", "PIC_NOALLOC_MAX_NODES", "BtdParams", "pic_btd_bytes",
-    "pic_btd_setup", "pic_btd_get", "pic_set_moving_window", "Simulation", "library_path",
+    "pic_btd_setup", "pic_btd_get", "pic_set_moving_window", "pic_batch_create", "pic_batch_step",
+    "pic_batch_destroy", "Simulation", "Batch", "library_path",
 ]
 
 PIC_OK, PIC_ERR_ARG, PIC_ERR_STATE, PIC_ERR_CUDA = 0, 1, 2, 3
@@ -129,6 +130,9 @@ def _load():
         "pic_profile_read": (S, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "pic_filter_current_noalloc": (S, [I, I, I, I, I, I, I, P, P, P, P]),
         "pic_set_moving_window": (S, [P, C.c_double, C.c_double, I]),
+        "pic_batch_create": (S, [C.POINTER(C.c_void_p), I, C.POINTER(C.c_void_p)]),
+        "pic_batch_step": (S, [P, I]),
+        "pic_batch_destroy": (None, [P]),
         "pic_btd_bytes": (S, [P, C.POINTER(BtdParams), C.POINTER(C.c_size_t)]),
         "pic_btd_setup": (S, [P, C.POINTER(BtdParams), P, C.c_size_t]),
         "pic_btd_get": (S, [P, I, P, C.c_size_t, I]),
@@ -293,6 +297,25 @@ def pic_filter_current_noalloc(dim: int, nx: int, ny: int, nz: int, bc_z: int, p
         raise PicError(st, detail)
 
 
+def pic_batch_create(ctxs) -> int:
+    arr = (C.c_void_p * len(ctxs))(*ctxs)
+    out = C.c_void_p()
+    st = _load().pic_batch_create(arr, len(ctxs), C.byref(out))
+    if st != PIC_OK:
+        raise PicError(st, _load().pic_status_string(st).decode())
+    return out.value
+
+
+def pic_batch_step(batch, nsteps: int):
+    st = _load().pic_batch_step(batch, nsteps)
+    if st != PIC_OK:
+        raise PicError(st, _load().pic_status_string(st).decode())
+
+
+def pic_batch_destroy(batch):
+    _load().pic_batch_destroy(batch)
+
+
 def pic_set_moving_window(ctx, v: float, t0: float, shift_cells: int):
     _check(ctx, _load().pic_set_moving_window(ctx, v, t0, shift_cells))
 
@@ -433,3 +456,25 @@ class Simulation:
         filled = host[nd:].view(np.int32) != 0
         names = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
         return {c: vals[q] for q, c in enumerate(names)}, filled
+
+
+class Batch:
+    """Steps several Simulations together (each on its own stream)."""
+
+    def __init__(self, sims):
+        self.sims = list(sims)
+        self.h = pic_batch_create([s.ctx for s in self.sims])
+
+    def step(self, nsteps: int = 1):
+        pic_batch_step(self.h, nsteps)
+
+    def close(self):
+        if getattr(self, "h", None):
+            pic_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

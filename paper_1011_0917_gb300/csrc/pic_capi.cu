@@ -896,6 +896,49 @@ static pic_status run_steps(pic_ctx *c, int nsteps, unsigned mask, bool check)
     return check_device_error(c);
 }
 
+// ------------------------------------------------------------------ batch
+
+struct pic_batch {
+    std::vector<pic_ctx *> ctx;
+};
+
+extern "C" pic_status pic_batch_create(pic_ctx *const *ctxs, int n, pic_batch **out)
+{
+    if (!out) return PIC_ERR_ARG;
+    *out = nullptr;
+    if (!ctxs || n < 1) return PIC_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i] || !ctxs[i]->bound) return PIC_ERR_STATE;
+        for (int k = 0; k < i; ++k)
+            if (ctxs[k] == ctxs[i]) return PIC_ERR_ARG;
+    }
+    pic_batch *b = new (std::nothrow) pic_batch;
+    if (!b) return PIC_ERR_ARG;
+    b->ctx.assign(ctxs, ctxs + n);
+    *out = b;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_batch_step(pic_batch *b, int nsteps)
+{
+    if (!b || nsteps < 0) return PIC_ERR_ARG;
+    // step n of every context before step n + 1 of any: the contexts' streams
+    // run concurrently, so the GPU holds the kernels of all of them at once
+    for (int n = 0; n < nsteps; ++n)
+        for (pic_ctx *c : b->ctx) {
+            pic_status s = run_steps(c, 1, PIC_PH_ALL, false);
+            if (s != PIC_OK) return s;
+        }
+    pic_status first = PIC_OK;
+    for (pic_ctx *c : b->ctx) {
+        pic_status s = check_device_error(c);
+        if (s != PIC_OK && first == PIC_OK) first = s;
+    }
+    return first;
+}
+
+extern "C" void pic_batch_destroy(pic_batch *b) { delete b; }
+
 extern "C" pic_status pic_step(pic_ctx *c, int nsteps) { return run_steps(c, nsteps, PIC_PH_ALL, true); }
 extern "C" pic_status pic_step_async(pic_ctx *c, int nsteps) { return run_steps(c, nsteps, PIC_PH_ALL, false); }
 extern "C" pic_status pic_step_phases(pic_ctx *c, unsigned mask)

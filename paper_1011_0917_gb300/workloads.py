@@ -21,6 +21,7 @@ at gamma_boost 130 stand behind these; no dataset is involved):
   c3  gamma_boost = 130, 2D3V, 512 x 16384, quadratic shape, 4 passes,
       n = 5.7e-5, 5 lambda0 ramp, laser a0 = 1.5, w0 = 50, FWHM 30; c3_small
       is the same stage on a 4x coarser grid (128 x 4096).
+  c4  the batched scan: 64 independent 2D3V boosted runs (c4_run).
 """
 from __future__ import annotations
 
@@ -84,6 +85,27 @@ def stage(name: str) -> Stage:
                      dict(ne=5.7e-5, z_start=6.0e5, z_end=1.6e6, ramp=5.0, ppc=(2, 1, 2), jitter=0.1, ions=1),
                      dict(a0=1.5, waist=50.0, fwhm=30.0, z_antenna=0.0, pol=1), steps=2000)
     raise KeyError(name)
+
+
+def c4_run(r: int, nz_range=(1024, 4096), nx: int = 128, steps: int = 400) -> Stage:
+    """Run r of the batched scan: 2D3V boosted-frame stage with gamma drawn
+    from {5, 13, 30}, nz uniform in nz_range, an 8-coefficient cosine density
+    profile around n/n_c = 0.001 (c_m = 0.2 u_m / 8, u_m uniform in [-1, 1], so
+    |dn/n| <= 20%) and a0 uniform in [0.5, 2]; seed 10110917 + 4 + 1000 r."""
+    seed = SEED0 + 4 + 1000 * r
+    rng = np.random.default_rng(seed)
+    gam = float(rng.choice([5.0, 13.0, 30.0]))
+    nz = int(rng.integers(nz_range[0], nz_range[1] + 1))
+    prof = tuple(float(c) for c in 0.2 * rng.uniform(-1.0, 1.0, 8) / 8.0)
+    a0 = float(rng.uniform(0.5, 2.0))
+    beta = math.sqrt(1.0 - 1.0 / gam ** 2)
+    hz = (1.0 / 32) * gam * (1.0 + beta)
+    g = _grid(nx=nx, nz=nz, dx=1.0, dz=1.0 / 32, gamma_boost=gam, filter_passes=2, seed=seed)
+    # plasma from 10 cells ahead of the antenna, streaming in for the whole run
+    p = dict(ne=0.001, z_start=gam * 10 * hz, z_end=gam * 10 * hz + 20000.0, ramp=2.0, ppc=(2, 1, 2), jitter=0.1,
+             ions=1, profile=prof)
+    laser = dict(a0=a0, waist=20.0, fwhm=10.0, z_antenna=0.0, pol=1)
+    return Stage(f"c4[{r}]", g, p, laser, steps)
 
 
 def scaled(st: Stage, **grid_overrides) -> Stage:
