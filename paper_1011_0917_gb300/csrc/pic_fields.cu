@@ -380,120 +380,111 @@ __global__ void filter_kernel(Geom g, const real *in0, const real *in1, const re
     }
 }
 
-// All passes of all axes in one kernel.  A CTA owns blocks of one component:
-// BX = 32 - 2H nodes along x (plus a halo of H = npass per side), 8 rows in
-// y (3D: BY = 8 consecutive y plus the halo; 2D: 8 independent x sub-blocks
-// side by side), BZ along z plus the halo.  x passes: one warp per row, a lane
-// per x node, neighbours by warp shuffle, all H passes in registers.  y and z
-// passes: a thread per column holds the column in registers.  The arithmetic
-// per pass and node is the one of filter_kernel, in the same order (x, then y,
-// then z); with absorbing z, nodes outside the component's valid z range are
-// zero before every z pass, as filter_kernel treats them.
-template <typename real, int DIM, int BZ, int H>
-__global__ void __launch_bounds__(256) filter_fused_kernel(Geom g, const real *in0, const real *in1, const real *in2,
-                                                           real *out0, real *out1, real *out2)
+// All H passes of all axes in one z-marching kernel.  A CTA owns a TX x TY
+// column of nodes (32 x 8 in 3D, 256 x 1 in 2D) of the three components and a
+// chunk of z planes.  Per plane it loads the column widened by H nodes in x
+// and y (periodic) into shared memory; H binomial passes along x and then
+// along y are, on a periodic axis, the binomial stencil of width 2H + 1
+// (weights C(2H, i) / 4^H, exact in binary), so each thread takes its node's
+// x-y filtered value as that stencil sum.  The z passes follow in registers,
+// one pass after the other as the march goes up, each on values that are zero
+// outside the component's valid z range (absorbing z) or wrapped (periodic).
+// The chunk starts H planes early and ends H planes late.
+template <typename real, int DIM, int H>
+__global__ void __launch_bounds__(256) filter_march_kernel(Geom g, const real *in, real *out, int cz, int nchunks)
 {
-    constexpr int AX = 32, BX = AX - 2 * H;
-    constexpr int BY = 8;                                   // y rows (3D) or x sub-blocks (2D)
-    constexpr int AY = DIM == 3 ? BY + 2 * H : BY, AZ = BZ + 2 * H;
-    constexpr int HY = DIM == 3 ? H : 0;
-    constexpr int SPAN = DIM == 3 ? BX : BY * BX;           // x nodes of one CTA's centre
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    real *A = reinterpret_cast<real *>(smem_raw);  // [AZ][AY][AX]
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int c = blockIdx.z;
-    const real *in = c == 0 ? in0 : (c == 1 ? in1 : in2);
-    real *out = c == 0 ? out0 : (c == 1 ? out1 : out2);
-    const int zmax = zmax_of(g, c == 2);
-    const int nbx = (g.nx + SPAN - 1) / SPAN;
-    const int bxi = blockIdx.x % nbx, byi = blockIdx.x / nbx;
-    const int x0 = bxi * SPAN, y0 = DIM == 3 ? byi * BY : 0, oz = blockIdx.y * BZ - H;
-
-    // load + x passes: warp per row
-    for (int row = warp; row < AY * AZ; row += 8) {
-        const int ly = row % AY, lz = row / AY;
-        const int gi = wrapi(x0 + (DIM == 3 ? 0 : ly * BX) - H + lane, g.nx);
-        const int gj = DIM == 3 ? wrapi(y0 - H + ly, g.ny) : 0;
-        const int gk = oz + lz;
-        real v = 0;
-        if (g.bc_z == 0) v = in[fidx(g, gi, gj, wrapi(gk, g.nz))];
-        else if (gk >= 0 && gk <= zmax) v = in[fidx(g, gi, gj, gk)];
-#pragma unroll
-        for (int p = 0; p < H; ++p) {
-            const real lo = __shfl_up_sync(0xffffffffu, v, 1), hi = __shfl_down_sync(0xffffffffu, v, 1);
-            if (lane != 0 && lane != 31) v = real(0.25) * lo + real(0.5) * v + real(0.25) * hi;
+    constexpr int TX = DIM == 3 ? 32 : 256, TY = DIM == 3 ? 8 : 1, HY = DIM == 3 ? H : 0;
+    constexpr int RX = TX + 2 * H, RY = TY + 2 * HY, RN = RX * RY;
+    constexpr int W = 2 * H + 1;
+    __shared__ real A[3][RN];
+    // binomial weights C(2H, i) / 4^H
+    real wb[W];
+    {
+        double c = 1.0;
+        for (int i = 0; i < W; ++i) {
+            wb[i] = (real)(c / (double)(1 << (2 * H)));
+            c = c * (double)(2 * H - i) / (double)(i + 1);
         }
-        A[row * AX + lane] = v;
     }
-    __syncthreads();
-
-    // y passes (3D): thread per (x, z) column
-    if (DIM == 3) {
-        for (int col = threadIdx.x; col < AX * AZ; col += 256) {
-            const int lx = col % AX, lz = col / AX;
-            real v[AY];
+    const bool per = g.bc_z == 0;
+    const int nbx = (g.nx + TX - 1) / TX;
+    const int x0 = (int)(blockIdx.x % nbx) * TX, y0 = (int)(blockIdx.x / nbx) * TY;
+    const int z0 = (int)blockIdx.y * cz;
+    const int z1 = (int)blockIdx.y == nchunks - 1 ? g.nz + 1 : z0 + cz;
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+    const bool own = x0 + tx < g.nx && (DIM == 2 || y0 + ty < g.ny);
+    const int64_t oown = own ? (int64_t)(y0 + ty) * g.nx + (x0 + tx) : 0;
+    // this thread's nodes of the widened plane (at most ceil(RN / 256) of them)
+    constexpr int NL = (RN + 255) / 256;
+    int off[NL];
 #pragma unroll
-            for (int l = 0; l < AY; ++l) v[l] = A[(lz * AY + l) * AX + lx];
+    for (int m = 0; m < NL; ++m) {
+        const int r = tid + 256 * m;
+        const int ly = r / RX, lx = r - ly * RX;
+        const int gx = wrapi(x0 - H + lx, g.nx);
+        const int gy = DIM == 3 ? wrapi(y0 - HY + ly, g.ny) : 0;
+        off[m] = r < RN ? gy * g.nx + gx : -1;
+    }
+    // per component, z windows: lev[c][p][0..2] = the values after p z passes
+    // at the last three planes they were computed for
+    real lev[3][H + 1][3];
 #pragma unroll
-            for (int p = 0; p < H; ++p) {
-                real prev = v[0];
+    for (int c = 0; c < 3; ++c)
 #pragma unroll
-                for (int l = 1; l < AY - 1; ++l) {
-                    const real cur = v[l];
-                    v[l] = real(0.25) * prev + real(0.5) * cur + real(0.25) * v[l + 1];
-                    prev = cur;
-                }
-            }
+        for (int p = 0; p <= H; ++p) lev[c][p][0] = lev[c][p][1] = lev[c][p][2] = real(0);
+    const int zmax_xy = zmax_of(g, false), zmax_z = zmax_of(g, true);
+    for (int k = z0 - H; k <= z1 - 1 + H; ++k) {
+        const int kk = per ? wrapi(k, g.nz) : k;
+        __syncthreads();  // previous plane consumed
 #pragma unroll
-            for (int l = 0; l < AY; ++l) A[(lz * AY + l) * AX + lx] = v[l];
+        for (int c = 0; c < 3; ++c) {
+            const bool have = per || (k >= 0 && k <= (c == 2 ? zmax_z : zmax_xy));
+            const real *src = in + (size_t)c * g.ncomp + (int64_t)kk * g.plane;
+#pragma unroll
+            for (int m = 0; m < NL; ++m)
+                if (off[m] >= 0) A[c][tid + 256 * m] = have ? src[off[m]] : real(0);
         }
         __syncthreads();
-    }
-
-    // z passes and the write of the block centre: thread per (x, row) column
-    for (int col = threadIdx.x; col < BX * BY; col += 256) {
-        const int lx = col % BX + H, ly = col / BX + HY;
-        const int gx = DIM == 3 ? x0 + lx - H : x0 + (ly * BX) + lx - H;
-        const int gy = DIM == 3 ? y0 + ly - H : 0;
-        real v[AZ];
+        const int ko = k - H;
 #pragma unroll
-        for (int l = 0; l < AZ; ++l) v[l] = A[(l * AY + ly) * AX + lx];
+        for (int c = 0; c < 3; ++c) {
+            const int zmax = c == 2 ? zmax_z : zmax_xy;
+            // x-y passes: the binomial stencil around this thread's node
+            real v = 0;
 #pragma unroll
-        for (int p = 0; p < H; ++p) {
-            real prev = v[0];
+            for (int j = 0; j < (DIM == 3 ? W : 1); ++j) {
+                real r = 0;
 #pragma unroll
-            for (int l = 1; l < AZ - 1; ++l) {
-                const real cur = v[l];
-                real nv = real(0.25) * prev + real(0.5) * cur + real(0.25) * v[l + 1];
-                if (g.bc_z != 0) {
-                    const int gk = oz + l;
-                    if (gk < 0 || gk > zmax) nv = 0;
-                }
-                v[l] = nv;
-                prev = cur;
+                for (int i = 0; i < W; ++i) r += wb[i] * A[c][(ty + j) * RX + tx + i];
+                v += (DIM == 3 ? wb[j] : real(1)) * r;
             }
-        }
-        if (gx >= g.nx || gy >= g.ny) continue;
+            // z passes, one level per pass, each centred one plane lower
 #pragma unroll
-        for (int l = H; l < H + BZ; ++l) {
-            const int gk = oz + l;
-            if (gk <= g.nz) out[fidx(g, gx, gy, gk)] = gk > zmax ? real(0) : v[l];
+            for (int p = 0; p <= H; ++p) {
+                lev[c][p][0] = lev[c][p][1];
+                lev[c][p][1] = lev[c][p][2];
+                const int kc = k - p;  // plane of the new level-p value
+                const bool in_range = per || (kc >= 0 && kc <= zmax);
+                const real nv = p == 0 ? v
+                                       : real(0.25) * lev[c][p - 1][0] + real(0.5) * lev[c][p - 1][1] +
+                                             real(0.25) * lev[c][p - 1][2];
+                lev[c][p][2] = in_range ? nv : real(0);
+            }
+            if (own && ko >= z0 && ko < z1)
+                out[(size_t)c * g.ncomp + (int64_t)ko * g.plane + oown] = ko > zmax ? real(0) : lev[c][H][2];
         }
     }
 }
 
-template <typename real, int DIM, int BZ, int H>
-static void launch_fused(const Geom &g, const real *in, real *out, cudaStream_t s)
+template <typename real, int DIM, int H>
+static void launch_march(const Geom &g, const real *in, real *out, cudaStream_t s)
 {
-    constexpr int BX = 32 - 2 * H, BY = 8;
-    constexpr int SPAN = DIM == 3 ? BX : BY * BX;
-    constexpr int AN = 32 * (DIM == 3 ? BY + 2 * H : BY) * (BZ + 2 * H);
-    const size_t smem = sizeof(real) * AN;
-    auto k = filter_fused_kernel<real, DIM, BZ, H>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const unsigned nbx = (g.nx + SPAN - 1) / SPAN, nby = DIM == 3 ? (g.ny + BY - 1) / BY : 1;
-    dim3 grid(nbx * nby, (g.nz + 1 + BZ - 1) / BZ, 3);
-    k<<<grid, 256, smem, s>>>(g, in, in + g.ncomp, in + 2 * g.ncomp, out, out + g.ncomp, out + 2 * g.ncomp);
+    constexpr int TX = DIM == 3 ? 32 : 256, TY = DIM == 3 ? 8 : 1;
+    const int nzo = g.nz + 1;
+    const int cz = nzo >= 128 ? 64 : (nzo >= 16 ? 8 : nzo);
+    const int nchunks = nzo / cz > 0 ? nzo / cz : 1;
+    const unsigned nb = (unsigned)(((g.nx + TX - 1) / TX) * (DIM == 3 ? (g.ny + TY - 1) / TY : 1));
+    filter_march_kernel<real, DIM, H><<<dim3(nb, (unsigned)nchunks, 1), 256, 0, s>>>(g, in, out, cz, nchunks);
 }
 
 template <typename real>
@@ -502,17 +493,17 @@ static bool fused_passes(const Geom &g, const real *in, real *out, int npass, cu
     if (npass < 1 || npass > 4) return false;
     if (g.dim == 3) {
         switch (npass) {
-        case 1: launch_fused<real, 3, 16, 1>(g, in, out, s); break;
-        case 2: launch_fused<real, 3, 16, 2>(g, in, out, s); break;
-        case 3: launch_fused<real, 3, 16, 3>(g, in, out, s); break;
-        default: launch_fused<real, 3, 16, 4>(g, in, out, s); break;
+        case 1: launch_march<real, 3, 1>(g, in, out, s); break;
+        case 2: launch_march<real, 3, 2>(g, in, out, s); break;
+        case 3: launch_march<real, 3, 3>(g, in, out, s); break;
+        default: launch_march<real, 3, 4>(g, in, out, s); break;
         }
     } else {
         switch (npass) {
-        case 1: launch_fused<real, 2, 32, 1>(g, in, out, s); break;
-        case 2: launch_fused<real, 2, 32, 2>(g, in, out, s); break;
-        case 3: launch_fused<real, 2, 32, 3>(g, in, out, s); break;
-        default: launch_fused<real, 2, 32, 4>(g, in, out, s); break;
+        case 1: launch_march<real, 2, 1>(g, in, out, s); break;
+        case 2: launch_march<real, 2, 2>(g, in, out, s); break;
+        case 3: launch_march<real, 2, 3>(g, in, out, s); break;
+        default: launch_march<real, 2, 4>(g, in, out, s); break;
         }
     }
     return true;
