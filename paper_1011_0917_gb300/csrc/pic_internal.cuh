@@ -155,6 +155,37 @@ __device__ __forceinline__ int spline_weights(real p, real w[S + 1])
     }
 }
 
+// The same at an in-cell offset o in [0, 1) (the particle's own cell, an
+// invariant of the store): for CIC the support starts at the cell's node, so
+// the floor is 0 and the weights are those of spline_weights<1>(o) bit for bit.
+template <int S, typename real>
+__device__ __forceinline__ int offset_weights(real o, real w[S + 1])
+{
+    if (S == 1) {
+        w[0] = real(1) - o;
+        w[1] = o;
+        return 0;
+    }
+    return spline_weights<S>(o, w);
+}
+
+// And at o - 1/2 (components staggered by half a cell), o in [0, 1): for CIC
+// the floor is -1 or 0; the weights are those of spline_weights<1>(o - 1/2)
+// bit for bit.
+template <int S, typename real>
+__device__ __forceinline__ int half_weights(real o, real w[S + 1])
+{
+    if (S == 1) {
+        const real p = o - real(0.5);
+        const bool lo = p < real(0);
+        const real d = lo ? p + real(1) : p;
+        w[0] = real(1) - d;
+        w[1] = d;
+        return lo ? -1 : 0;
+    }
+    return spline_weights<S>(o - real(0.5), w);
+}
+
 // ----------------------------------------------------------------- Boris
 
 // reciprocals used by the push: IEEE in FP64 (the debug path).  In FP32 the

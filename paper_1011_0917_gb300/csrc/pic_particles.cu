@@ -24,28 +24,6 @@ template <typename real> struct MinBlocks { static constexpr int value = sizeof(
 
 // ---------------------------------------------------------------- helpers
 
-// Esirkepov window along one axis: old offset x0 in [0,1), new position x1 =
-// x0 + d (|d| < 1), both relative to the old cell.  Returns the first node of a
-// window of S+2 nodes that holds both supports, with S0 and DS = S1 - S0 on it.
-template <int S, typename real>
-__device__ __forceinline__ int esirk_axis(real x0, real x1, real S0[S + 2], real DS[S + 2])
-{
-    real w0[S + 1], w1[S + 1];
-    const int b0 = spline_weights<S>(x0, w0);
-    const int b1 = spline_weights<S>(x1, w1);
-    const int anchor = b0 < b1 ? b0 : b1;
-    const bool s0 = b0 != anchor;  // support shifted one node up in the window
-    const bool s1 = b1 != anchor;
-#pragma unroll
-    for (int q = 0; q < S + 2; ++q) {
-        real v0 = s0 ? (q >= 1 ? w0[q - 1 < S ? q - 1 : S] : real(0)) : (q <= S ? w0[q <= S ? q : S] : real(0));
-        real v1 = s1 ? (q >= 1 ? w1[q - 1 < S ? q - 1 : S] : real(0)) : (q <= S ? w1[q <= S ? q : S] : real(0));
-        S0[q] = v0;
-        DS[q] = v1 - v0;
-    }
-    return anchor;
-}
-
 // Shared-memory current accumulators.  FP32 currents are accumulated exactly,
 // in 64-bit fixed point split over two 32-bit integer words per node: a
 // contribution p = a*b, already multiplied by the launch's fixed-point scale
@@ -222,13 +200,15 @@ __device__ __forceinline__ real gather_comp(const real *F, int FX, int FY, int i
 
 // --------------------------------------------------------- Esirkepov
 
-// Esirkepov window along one axis as esirk_axis, plus whether the particle's
-// support moved to another first node (the window then needs S+2 nodes).
+// Esirkepov window along one axis: old offset x0 in [0,1), new position x1 =
+// x0 + d (|d| < 1), both relative to the old cell.  Returns the first node of
+// a window of S+2 nodes that holds both supports, with S0 and DS = S1 - S0 on
+// it, and whether the support moved to another first node.
 template <int S, typename real>
 __device__ __forceinline__ int esirk_axis_c(real x0, real x1, real S0[S + 2], real DS[S + 2], bool &crossed)
 {
     real w0[S + 1], w1[S + 1];
-    const int b0 = spline_weights<S>(x0, w0);
+    const int b0 = offset_weights<S>(x0, w0);  // x0: the in-cell offset at the start
     const int b1 = spline_weights<S>(x1, w1);
     const int anchor = b0 < b1 ? b0 : b1;
     const bool s0 = b0 != anchor, s1 = b1 != anchor;
@@ -473,14 +453,14 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
             bool release = false;
             if (valid) {
                 real wxu[S + 1], wxh[S + 1], wyu[S + 1], wyh[S + 1], wzu[S + 1], wzh[S + 1];
-                const int bxu = spline_weights<S>(ox, wxu) + li + FL;
-                const int bxh = spline_weights<S>(ox - real(0.5), wxh) + li + FL;
-                const int bzu = spline_weights<S>(oz, wzu) + lk + FL;
-                const int bzh = spline_weights<S>(oz - real(0.5), wzh) + lk + FL;
+                const int bxu = offset_weights<S>(ox, wxu) + li + FL;
+                const int bxh = half_weights<S>(ox, wxh) + li + FL;
+                const int bzu = offset_weights<S>(oz, wzu) + lk + FL;
+                const int bzh = half_weights<S>(oz, wzh) + lk + FL;
                 int byu = 0, byh = 0;
                 if (DIM == 3) {
-                    byu = spline_weights<S>(oy, wyu) + lj + FL;
-                    byh = spline_weights<S>(oy - real(0.5), wyh) + lj + FL;
+                    byu = offset_weights<S>(oy, wyu) + lj + FL;
+                    byh = half_weights<S>(oy, wyh) + lj + FL;
                 } else {
 #pragma unroll
                     for (int q = 0; q <= S; ++q) wyu[q] = wyh[q] = real(q == 0);
@@ -701,9 +681,9 @@ __global__ void __launch_bounds__(kBlock) ion_kernel(PushArgs<real> a)
                     real S0z[S + 2], DSz[S + 2], wx[S + 1], wy[S + 1];
                     bool crossed;
                     const int az = esirk_axis_c<S>(oz, z1, S0z, DSz, crossed) + lk + JL;
-                    const int bx = spline_weights<S>(ox, wx) + li + JL;
+                    const int bx = offset_weights<S>(ox, wx) + li + JL;
                     int by = 0;
-                    if (DIM == 3) by = spline_weights<S>(oy, wy) + lj + JL;
+                    if (DIM == 3) by = offset_weights<S>(oy, wy) + lj + JL;
                     const real fz = a.jfac[2] * w * a.fx_scale[2];
                     real Pz[S + 2];
                     real acc = 0;
