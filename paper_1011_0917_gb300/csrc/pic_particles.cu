@@ -94,17 +94,21 @@ __device__ __forceinline__ void stage_tile(const Geom &g, const Ptr6<real> src, 
 {
     constexpr int FN = FX * FY * FZ;
     const bool tiny = g.nx < FX || (DIM == 3 && g.ny < FY);
-    for (int q = threadIdx.x; q < NC * FN; q += blockDim.x) {
-        const int c = q / FN, r = q - c * FN;
+    // each node of the box once, all components of it together
+    for (int r = threadIdx.x; r < FN; r += blockDim.x) {
         const int lz = r / (FX * FY), r2 = r - lz * (FX * FY);
         const int ly = r2 / FX, lx = r2 - ly * FX;
         int gk = loz - L + lz;
-        bool ok = true;
+        const bool inz = g.bc_z == 0 || gk >= 0;
         if (g.bc_z == 0) gk = wrapi(gk, g.nz);
-        else ok = gk >= 0 && gk <= zmax_of(g, (half_z >> c) & 1u);
         const int gi = tiny ? wrapi(lox - L + lx, g.nx) : wrap1(lox - L + lx, g.nx);
         const int gj = DIM == 3 ? (tiny ? wrapi(loy - L + ly, g.ny) : wrap1(loy - L + ly, g.ny)) : 0;
-        dst[q] = ok ? src[c][fidx(g, gi, gj, gk)] : real(0);
+        const int64_t o = fidx(g, gi, gj, inz ? gk : 0);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const bool ok = inz && (g.bc_z == 0 || gk <= zmax_of(g, (half_z >> c) & 1u));
+            dst[c * FN + r] = ok ? src[c][o] : real(0);
+        }
     }
 }
 
@@ -120,25 +124,33 @@ __device__ __forceinline__ void flush_tile(const Geom &g, const Ptr3<real> dstJ,
 {
     constexpr int QN = QX * QY * QZ;
     const bool tiny = g.nx < QX || (DIM == 3 && g.ny < QY);
-    for (int q = threadIdx.x; q < NC * QN; q += blockDim.x) {
-        real v;
-        if constexpr (sizeof(real) == 4) {
-            const int h = src[q], l = src[NC * QN + q];  // the node's "hi" and "lo" words
-            if ((h | l) == 0) continue;
-            v = fmaf((float)l, lo_inv, (float)h);
-        } else {
-            v = src[q];
-            if (v == real(0)) continue;
+    // each node of the box once, all components of it together
+    for (int r = threadIdx.x; r < QN; r += blockDim.x) {
+        real v[NC];
+        bool any = false;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            if constexpr (sizeof(real) == 4) {
+                const int h = src[c * QN + r], l = src[NC * QN + c * QN + r];  // "hi" and "lo" words
+                v[c] = (h | l) == 0 ? real(0) : fmaf((float)l, lo_inv, (float)h);
+            } else {
+                v[c] = src[c * QN + r];
+            }
+            any = any || v[c] != real(0);
         }
-        const int c = q / QN, r = q - c * QN;
+        if (!any) continue;
         const int lz = r / (QX * QY), r2 = r - lz * (QX * QY);
         const int ly = r2 / QX, lx = r2 - ly * QX;
         int gk = loz - L + lz;
         if (g.bc_z == 0) gk = wrapi(gk, g.nz);
-        else if (gk < 0 || gk > zmax_of(g, (half_z >> c) & 1u)) continue;
+        else if (gk < 0) continue;
         const int gi = tiny ? wrapi(lox - L + lx, g.nx) : wrap1(lox - L + lx, g.nx);
         const int gj = DIM == 3 ? (tiny ? wrapi(loy - L + ly, g.ny) : wrap1(loy - L + ly, g.ny)) : 0;
-        atomicAdd(dstJ[c] + fidx(g, gi, gj, gk), v * (c == 0 ? q0 : c == 1 ? q1 : q2));
+        const int64_t o = fidx(g, gi, gj, gk);
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            if (v[c] != real(0) && (g.bc_z == 0 || gk <= zmax_of(g, (half_z >> c) & 1u)))
+                atomicAdd(dstJ[c] + o, v[c] * (c == 0 ? q0 : c == 1 ? q1 : q2));
     }
 }
 
