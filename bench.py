@@ -37,8 +37,11 @@ METRIC = "particle-steps/s (gather+push+deposit+Yee), %HBM roofline, adjoint/for
 UNIT = "particle-steps/s"
 # algorithmic bytes per electron particle-step of the fused gather/push/deposit
 # kernel in 3D: particle state read 32 B + written 28 B, plus fields read
-# (24 B/cell) and current written (12 B/cell) amortised over ppc = 8
+# (24 B/cell) and current written (12 B/cell) amortised over ppc = 8; the same
+# kernel then moves each drifting-ion record of the tile: 20 B read + 20 B
+# written (the record moves to its output slot)
 BYTES_PER_PARTICLE_STEP_3D = 60.0 + 36.0 / 8.0
+BYTES_PER_ION_STEP_3D = 40.0
 
 
 def parse():
@@ -192,6 +195,9 @@ def run_ours(args, rank, world, local):
     d1 = sim.diagnostics()
     n_e = 0.5 * (d0.n_particles[0] + d1.n_particles[0])
     n_i = 0.5 * (d0.n_particles[1] + d1.n_particles[1])
+    # ion records the electron kernel moves (ions of paired electrons have none;
+    # explicit ions have their own kernel)
+    n_ir = 0.0 if args.explicit_ions else 0.5 * (d0.n_particles[1] - d0.n_paired + d1.n_particles[1] - d1.n_paired)
     # electrons still paired with their ion (plasma no field has reached yet:
     # the pair's current is exactly zero and is not deposited)
     paired = [d0.n_paired / max(d0.n_particles[0], 1), d1.n_paired / max(d1.n_particles[0], 1)]
@@ -210,7 +216,8 @@ def run_ours(args, rank, world, local):
 
     # roofline of the dominant kernel (the fused electron gather/push/deposit)
     push_ms = phase_ms[1] / max(phase_calls[1], 1)
-    algo_bytes = BYTES_PER_PARTICLE_STEP_3D * n_e if g["dim"] == 3 else (52.0 + 36.0 / 4) * n_e
+    algo_bytes = (BYTES_PER_PARTICLE_STEP_3D * n_e + BYTES_PER_ION_STEP_3D * n_ir if g["dim"] == 3
+                  else (52.0 + 36.0 / 4) * n_e + 32.0 * n_ir)
     achieved = algo_bytes / (push_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
     phases = ["zero_j", "push", "ions", "antenna", "filter", "yee", "inject", "time"]
@@ -328,8 +335,11 @@ def run_ours(args, rank, world, local):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": traffic_from_profiles("push_kernel<float,3,1>"),
-                         "kernel": "push_kernel<float,3,1> (gather+Boris+Esirkepov+re-bucket)",
-                         "bytes_per_unit": BYTES_PER_PARTICLE_STEP_3D, "unit_of_work": "electron particle-step",
+                         "kernel": "push_kernel<float,3,1> (electrons: gather+Boris+Esirkepov+re-bucket; "
+                                   "then the tile's drifting-ion records: move+Jz+re-bucket)",
+                         "bytes_per_unit": {"electron particle-step": BYTES_PER_PARTICLE_STEP_3D,
+                                            "ion record step": BYTES_PER_ION_STEP_3D},
+                         "units_per_launch": {"electrons": n_e, "ion_records": n_ir},
                          "ms_per_launch": push_ms},
             "phase_share": share,
             "e2e": e2e,

@@ -200,7 +200,10 @@ pic_status pic_load_plasma(pic_ctx *ctx, const pic_plasma_params *p);
 
 /* Appends n particles given as host FP64 arrays (simulation frame):
    state[a*n + i] for a = 0..6 = x, y, z, ux, uy, uz, w.  Ions take the
-   species' drift momentum and ignore ux, uy, uz.  ids (may be NULL) are kept
+   species' drift momentum and ignore ux, uy, uz.  (The device holds electron
+   momenta relative to the plasma drift, u - (0, 0, -gamma beta), so that the
+   working precision resolves the plasma's response; pic_get_particles adds
+   the drift back.)  ids (may be NULL) are kept
    when track_ids is set.  Positions outside the box are rejected
    (PIC_ERR_ARG); PIC_ERR_CAPACITY if a tile overflowed. */
 pic_status pic_load_particles(pic_ctx *ctx, int species, int64_t n, const double *state,

@@ -187,6 +187,15 @@ static cudaMemcpyKind kind_in(int src_is_device) { return src_is_device ? cudaMe
 
 static size_t attr_size(const pic_ctx *c, int a) { return a == 7 ? 4 : (a == 8 ? 8 : (size_t)c->es); }
 
+// the plasma's drift momentum U (u = (0, 0, U)) in the working precision:
+// -gamma beta in a boosted frame, 0 in the lab frame.  Electron records store
+// u - (0, 0, U); the drifting ions move with it.
+template <typename real>
+static real drift_u(const pic_ctx *c)
+{
+    return (real)(-(c->gam * c->beta));
+}
+
 static pic_status check_device_error(pic_ctx *c)
 {
     unsigned h = 0;
@@ -396,7 +405,6 @@ static void fill_inject_common(pic_ctx *c, InjectArgs &a)
     a.hz_lab = c->gam * c->hz;
     a.dzl = a.hz_lab / (double)a.ppz;
     a.wfac = c->gam * c->vol / (double)(a.ppx * a.ppy * a.ppz);
-    a.uz0 = -(c->gam * c->beta);
     a.nprof = p.n_profile;
     for (int m = 0; m < 16; ++m) a.prof[m] = m < p.n_profile ? c->prof[m] : 0.0;
     a.seed = c->p.seed;
@@ -544,10 +552,10 @@ static pic_status load_particles_t(pic_ctx *c, int sp, int64_t n, const double *
         R(2)[i] = oz;
         R(3)[i] = (real)state[6 * n + i];
         wmax = std::max(wmax, std::fabs(state[6 * n + i]) * (1.0 + 1e-6));
-        if (sp == 0) {
+        if (sp == 0) {  // stored relative to the plasma drift
             R(4)[i] = (real)state[3 * n + i];
             R(5)[i] = (real)state[4 * n + i];
-            R(6)[i] = (real)state[5 * n + i];
+            R(6)[i] = (real)(state[5 * n + i] - (double)drift_u<real>(c));
         }
         reinterpret_cast<int32_t *>(cols[7].data())[i] = pack_cell(c->g, ci, cj, ck);
         if (c->p.track_ids) reinterpret_cast<int64_t *>(cols[8].data())[i] = ids ? ids[i] : i;
@@ -600,14 +608,16 @@ extern "C" pic_status pic_launch_laser(pic_ctx *c, const pic_laser_params *p)
 // scales are the same for electrons and ions, so the contributions of an
 // electron and an ion on the same path cancel exactly.
 template <typename real>
-static void fixed_point_scales(const pic_ctx *c, real scale[3], real quant[3], real lo[2])
+static void fixed_point_scales(const pic_ctx *c, int nsources, real scale[3], real quant[3], real lo[2])
 {
     if (sizeof(real) != 4) {
         for (int q = 0; q < 3; ++q) scale[q] = quant[q] = real(1);
         lo[0] = lo[1] = real(1);
         return;
     }
-    const int cap = c->g.cap;
+    // a node of a current tile takes at most one contribution from each of
+    // the tile's records: nsources buckets of cap records each
+    const int cap = c->g.cap * nsources;
     int lg = 0;
     while ((1LL << lg) < (long long)cap) ++lg;  // ceil(log2 cap)
     const int k = std::min(22, 30 - lg);
@@ -650,16 +660,30 @@ static PushArgs<real> push_args(pic_ctx *c, int sp)
     a.jfac[1] = (real)(-q * c->hy / (c->dt * c->vol));
     a.jfac[2] = (real)(-q * c->hz / (c->dt * c->vol));
     a.jyfac = (real)(q / c->vol);
-    a.ion_u[0] = 0;
-    a.ion_u[1] = 0;
-    a.ion_u[2] = (real)(-(c->gam * c->beta));
-    fixed_point_scales(c, a.fx_scale, a.fx_quant, a.fx_lo);
+    a.u_drift = drift_u<real>(c);
+    fixed_point_scales(c, 1, a.fx_scale, a.fx_quant, a.fx_lo);
     if (c->ions_species) {
         a.ion_in = species_view<real>(c, 1, c->cur[1]);
         a.ion_in_hi = counts(c, 1, c->cur[1], 1);
     }
     a.err = reinterpret_cast<unsigned *>(c->scratch + c->off_err);
     return a;
+}
+
+// the drifting-ion species of this step: the side the step reads, the side
+// it writes, their bucket counters and the ions' current factor (q = +1)
+template <typename real>
+static IonSide<real> ion_side(pic_ctx *c)
+{
+    IonSide<real> s{};
+    s.in = species_view<real>(c, 1, c->cur[1]);
+    s.out = species_view<real>(c, 1, c->cur[1] ^ 1);
+    s.in_lo = counts(c, 1, c->cur[1], 0);
+    s.in_hi = counts(c, 1, c->cur[1], 1);
+    s.out_lo = counts(c, 1, c->cur[1] ^ 1, 0);
+    s.out_hi = counts(c, 1, c->cur[1] ^ 1, 1);
+    s.jfac_z = (real)(-1.0 * c->hz / (c->dt * c->vol));
+    return s;
 }
 
 // records an event pair around one phase when profiling is on
@@ -805,18 +829,35 @@ static void run_phases_t(pic_ctx *c, unsigned mask)
         PhaseTimer pt(c, 0);
         cudaMemsetAsync(R[0], 0, (size_t)3 * c->g.ncomp * sizeof(real), c->stream);
     }
+    // With ions paired to their electrons, the electron kernel also takes the
+    // tile's drifting ion records, so electron and ion currents add in one
+    // integer tile: a pair whose electron has not moved away from its ion
+    // flushes exactly zero, and no rounding residue of the global adds seeds
+    // fields ahead of the laser (such residues release pairs at the stencil's
+    // speed of 3 cells per step).  Explicit ions keep their own kernel, which
+    // measured faster when every tile holds a full bucket of both species.
+    const bool fused = (mask & PIC_PH_PUSH) && (mask & PIC_PH_IONS) && c->ions_species && !c->p.explicit_ions;
     if (mask & PIC_PH_PUSH) {
         PhaseTimer pt(c, 1);
         PushArgs<real> a = push_args<real>(c, 0);
         for (int q = 0; q < 3; ++q) a.J[q] = R[q];
+        if (fused) {
+            a.fuse_ions = 1;
+            a.ions = ion_side<real>(c);
+            // electrons and ions add into one integer tile: bound its sums
+            // by both species' bucket capacities
+            fixed_point_scales(c, 2, a.fx_scale, a.fx_quant, a.fx_lo);
+        }
         launch_push<real>(a, c->stream);
         c->cur[0] ^= 1;
+        if (fused) c->cur[1] ^= 1;
         c->kernels += 1;
     }
-    if ((mask & PIC_PH_IONS) && c->ions_species) {
+    if ((mask & PIC_PH_IONS) && c->ions_species && !fused) {
         PhaseTimer pt(c, 2);
         PushArgs<real> a = push_args<real>(c, 1);
         for (int q = 0; q < 3; ++q) a.J[q] = R[q];
+        a.ions = ion_side<real>(c);
         launch_ions<real>(a, c->stream);
         c->cur[1] ^= 1;
         c->kernels += 1;
@@ -1172,7 +1213,7 @@ static pic_status get_particles_t(pic_ctx *c, int sp, double *dst, size_t dst_by
     if (n_out) *n_out = n;
     if (!dst) return PIC_OK;
     if (dst_bytes < (size_t)n * 7 * sizeof(double)) return fail(c, PIC_ERR_ARG, "destination too small");
-    const double uz_ion = (double)(real)(-(c->gam * c->beta));
+    const double uz_ion = (double)drift_u<real>(c);
     int64_t row = 0;
     auto emit = [&](const std::vector<std::vector<unsigned char>> &h, int64_t p, bool electron) {
         auto R = [&](int a) { return reinterpret_cast<const real *>(h[a].data()); };
@@ -1184,7 +1225,7 @@ static pic_status get_particles_t(pic_ctx *c, int sp, double *dst, size_t dst_by
         if (electron) {
             dst[3 * n + row] = (double)R(4)[p];
             dst[4 * n + row] = (double)R(5)[p];
-            dst[5 * n + row] = (double)R(6)[p];
+            dst[5 * n + row] = uz_ion + (double)R(6)[p];
         } else {
             dst[3 * n + row] = 0.0;
             dst[4 * n + row] = 0.0;
@@ -1267,10 +1308,10 @@ static pic_status diagnostics_t(pic_ctx *c, pic_diag *out)
     out->field_energy = 0.5 * c->vol * kahan_sum(h.data(), kPartialBlocks, 1);
     out->kinetic_energy = 0;
     out->charge = 0;
-    const real ion_u[3] = {0, 0, (real)(-(c->gam * c->beta))};
+    const real u_drift[3] = {0, 0, drift_u<real>(c)};
     for (int sp = 0; sp < (c->ions_species ? 2 : 1); ++sp) {
         launch_particle_sums<real>(c->g, species_view<real>(c, sp, c->cur[sp]), counts(c, sp, c->cur[sp], 0),
-                                   counts(c, sp, c->cur[sp], 1), sp == 0 ? -1.0 : 1.0, ion_u, part, kPartialBlocks,
+                                   counts(c, sp, c->cur[sp], 1), sp == 0 ? -1.0 : 1.0, u_drift, part, kPartialBlocks,
                                    c->stream);
         CUDA_TRY(c, cudaGetLastError());
         CUDA_TRY(c, cudaMemcpyAsync(h.data(), part, sizeof(double) * 3 * kPartialBlocks, cudaMemcpyDeviceToHost, c->stream));
@@ -1337,7 +1378,7 @@ template <typename real>
 static pic_status get_state_t(pic_ctx *c, unsigned char *dst, size_t dst_bytes, int dst_is_device)
 {
     StateHeader h{};
-    std::memcpy(h.magic, "PICSTAT2", 8);
+    std::memcpy(h.magic, "PICSTAT3", 8);
     h.dim = c->g.dim;
     h.nx = c->g.nx;
     h.ny = c->g.ny;
@@ -1401,7 +1442,7 @@ static pic_status set_state_t(pic_ctx *c, const unsigned char *src, size_t src_b
     if (src_bytes < sizeof(h)) return fail(c, PIC_ERR_ARG, "snapshot too small");
     CUDA_TRY(c, cudaMemcpyAsync(&h, src, sizeof(h), src_is_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    if (std::memcmp(h.magic, "PICSTAT2", 8) != 0 || h.dim != c->g.dim || h.nx != c->g.nx || h.ny != c->g.ny ||
+    if (std::memcmp(h.magic, "PICSTAT3", 8) != 0 || h.dim != c->g.dim || h.nx != c->g.nx || h.ny != c->g.ny ||
         h.nz != c->g.nz || h.precision != c->p.precision || h.track_ids != c->p.track_ids ||
         h.has_ions != (int)c->ions_species || h.n[0] < 0 || h.n[1] < 0 || h.n[0] > c->slots || h.n[1] > c->slots ||
         !(h.wmax >= 0) || !std::isfinite(h.wmax))

@@ -65,17 +65,17 @@ __device__ __forceinline__ void to_cell(double x, double h, int n, bool periodic
 }
 
 template <typename real>
-__device__ __forceinline__ void store(void *const sp[9], int64_t d, real ox, real oy, real oz, real w, real uz,
-                                      int32_t cell, int64_t id, bool electron, bool dim3)
+__device__ __forceinline__ void store(void *const sp[9], int64_t d, real ox, real oy, real oz, real w, int32_t cell,
+                                      int64_t id, bool electron, bool dim3)
 {
     static_cast<real *>(sp[0])[d] = ox;
     if (dim3) static_cast<real *>(sp[1])[d] = oy;
     static_cast<real *>(sp[2])[d] = oz;
     static_cast<real *>(sp[3])[d] = w;
-    if (electron) {
+    if (electron) {  // momenta relative to the drift: the cold plasma has none
         static_cast<real *>(sp[4])[d] = real(0);
         static_cast<real *>(sp[5])[d] = real(0);
-        static_cast<real *>(sp[6])[d] = uz;
+        static_cast<real *>(sp[6])[d] = real(0);
     }
     static_cast<int32_t *>(sp[7])[d] = cell;
     if (sp[8]) static_cast<int64_t *>(sp[8])[d] = id;
@@ -146,13 +146,12 @@ __global__ void inject_kernel(InjectArgs a)
         // record for both until a field reaches them).
         const int32_t cell = pack_cell(a.g, ci, cj, ck);
         const int32_t ecell = (int32_t)((uint32_t)cell | (a.paired ? kPaired : 0u));
-        const real uz = (real)a.uz0;
         if (re < a.g.cap)
-            store<real>(a.sp_e, dest * (int64_t)a.g.cap + (a.g.cap - 1 - re), ox, oy, oz, wr, uz, ecell, L, true, dim3);
+            store<real>(a.sp_e, dest * (int64_t)a.g.cap + (a.g.cap - 1 - re), ox, oy, oz, wr, ecell, L, true, dim3);
         else atomicOr(a.err, ERR_CAPACITY);
         if (a.drift_ions && !a.paired) {
             if (ri < a.g.cap)
-                store<real>(a.sp_i, dest * (int64_t)a.g.cap + (a.g.cap - 1 - ri), ox, oy, oz, wr, uz, cell, L, false,
+                store<real>(a.sp_i, dest * (int64_t)a.g.cap + (a.g.cap - 1 - ri), ox, oy, oz, wr, cell, L, false,
                             dim3);
             else atomicOr(a.err, ERR_CAPACITY);
         }

@@ -203,13 +203,23 @@ __device__ __forceinline__ float rsqrt_p(float x)
 __device__ __forceinline__ double div_p(double a, double b) { return a / b; }
 __device__ __forceinline__ float div_p(float a, float b) { return a * __frcp_rn(b); }
 
-// relativistic Boris rotation for du/dt = 2 pi (q/m)(E + u x B / gamma);
-// eps = pi (q/m) dt is half the impulse factor
+// Momenta are stored relative to the plasma drift u_d = (0, 0, U) (U = 0 in
+// the lab frame, -gamma beta in the boosted frame): a record holds
+// du = u - u_d.  In FP32 a momentum near -gamma beta resolves changes of one
+// ulp of gamma beta, and v = u / gamma of it only ~6e-8, while a change du
+// moves v_z by du / gamma^3; relative storage and the velocity formula below
+// keep the plasma response at the relative precision of du itself.
+
+// relativistic Boris rotation for du/dt = 2 pi (q/m)(E + u x B / gamma) on
+// the stored du; eps = pi (q/m) dt is half the impulse factor.  The rotation
+// acts on the full u^- = u_d + du^-; its increments are added to du, so zero
+// fields leave du unchanged bit for bit.
 template <typename real>
-__device__ __forceinline__ void boris(real &ux, real &uy, real &uz, real ex, real ey, real ez,
+__device__ __forceinline__ void boris(real &dux, real &duy, real &duz, real U, real ex, real ey, real ez,
                                       real bx, real by, real bz, real eps)
 {
-    real umx = ux + eps * ex, umy = uy + eps * ey, umz = uz + eps * ez;
+    const real dmx = dux + eps * ex, dmy = duy + eps * ey, dmz = duz + eps * ez;
+    const real umx = dmx, umy = dmy, umz = U + dmz;
     real f = eps * rsqrt_p(real(1) + umx * umx + umy * umy + umz * umz);
     real tx = f * bx, ty = f * by, tz = f * bz;
     real t2 = tx * tx + ty * ty + tz * tz;
@@ -218,17 +228,56 @@ __device__ __forceinline__ void boris(real &ux, real &uy, real &uz, real ex, rea
     real upx = umx + (umy * tz - umz * ty);
     real upy = umy + (umz * tx - umx * tz);
     real upz = umz + (umx * ty - umy * tx);
-    ux = umx + (upy * sz - upz * sy) + eps * ex;
-    uy = umy + (upz * sx - upx * sz) + eps * ey;
-    uz = umz + (upx * sy - upy * sx) + eps * ez;
+    dux = dmx + (upy * sz - upz * sy) + eps * ex;
+    duy = dmy + (upz * sx - upx * sz) + eps * ey;
+    duz = dmz + (upx * sy - upy * sx) + eps * ez;
 }
 
-// inverse Lorentz factor of u; shared by electrons and drifting ions so that a
-// field-free electron and its ion partner move bit-identically
+// correctly rounded add and multiply that the compiler may not contract into
+// a fused multiply-add (the drift's displacement must round the same way in
+// every kernel that applies it)
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+// gamma_d^2 = 1 + U^2, 1 / gamma_d and the displacement per step dz (in
+// cells, dtdh = dt / h_z) of the drift; the drifting ions and the electrons
+// take all from here, and move by add_rn(offset, dz), so that a field-free
+// electron and its ion move bit-identically
 template <typename real>
-__device__ __forceinline__ real inv_gamma(real ux, real uy, real uz)
+struct Drift {
+    real U, g2, ig, g, dz;
+    __device__ __forceinline__ Drift(real u, real dtdh) : U(u)
+    {
+        g2 = add_rn(real(1), mul_rn(U, U));
+        ig = rsqrt_p(g2);
+        g = mul_rn(g2, ig);
+        dz = mul_rn(mul_rn(U, ig), dtdh);
+    }
+};
+
+// Velocity of a record with momentum u_d + du: returns v_z - v_d and sets
+// vx, vy.  With gamma^2 = gamma_d^2 + D, D = du_z (2U + du_z) + p2,
+// p2 = du_x^2 + du_y^2, and s = gamma + gamma_d,
+//   v_z - v_d = [du_z (2 + E) - U p2] / (gamma gamma_d s),
+//   E = gamma_d (gamma - gamma_d) - U du_z = (gamma_d (du_z^2 + p2) - U du_z D / s) / s,
+// an exact rearrangement in which no term cancels the drift (E is of second
+// order in du).  du = 0 gives exactly 0.  In the lab frame (U = 0) it is the
+// plain du_z / gamma.
+template <typename real>
+__device__ __forceinline__ real drift_velocity(const Drift<real> &d, real dux, real duy, real duz, real &vx,
+                                               real &vy)
 {
-    return rsqrt_p(real(1) + ux * ux + uy * uy + uz * uz);
+    const real p2 = dux * dux + duy * duy;
+    const real D = duz * (real(2) * d.U + duz) + p2;
+    const real ig = rsqrt_p(d.g2 + D);
+    vx = dux * ig;
+    vy = duy * ig;
+    if (d.U == real(0)) return duz * ig;
+    const real is = div_p(real(1), (d.g2 + D) * ig + d.g);
+    const real E = (d.g * (duz * duz + p2) - d.U * duz * D * is) * is;
+    return (duz * (real(2) + E) - d.U * p2) * (ig * d.ig * is);
 }
 
 // largest value below one, for offsets that round up to 1
@@ -237,6 +286,13 @@ template <> __host__ __device__ inline float below_one<float>() { return 0.99999
 template <> __host__ __device__ inline double below_one<double>() { return 0.99999999999999989; }
 
 // ---------------------------------------------------- kernel argument packs
+
+template <typename real>
+struct IonSide {         // the drifting-ion species of a step
+    Species<real> in, out;
+    int *in_lo, *in_hi, *out_lo, *out_hi;
+    real jfac_z;         // -q h_z / (dt V) of the ions
+};
 
 template <typename real>
 struct PushArgs {
@@ -250,7 +306,8 @@ struct PushArgs {
     real eps;           // pi (q/m) dt
     real jfac[3];       // -q h_d / (dt V): multiplied by w and the running sum
     real jyfac;         // q / V (2D out-of-plane current, times w vy)
-    real ion_u[3];      // drift momentum of the ion species
+    real u_drift;       // U: the plasma's drift momentum (0, 0, U); electron
+                        // records store u - (0, 0, U), ions move with it
     // fixed-point current accumulation (FP32; FP64 uses 1): the per-particle
     // factors of Jx, Jy (2D: the out-of-plane factor), Jz are multiplied by
     // fx_scale[c]; a shared-tile node's integer sum times fx_quant[c] =
@@ -258,6 +315,8 @@ struct PushArgs {
     real fx_scale[3], fx_quant[3], fx_lo[2];
     Species<real> ion_in;  // ion side the IONS phase reads next (released ions go there)
     int *ion_in_hi;        // its top-run lengths
+    int fuse_ions;         // 1: the same CTA then moves and deposits the tile's ions
+    IonSide<real> ions;    // (with fuse_ions) the ion sides and counters
     unsigned *err;
 };
 
@@ -298,7 +357,7 @@ struct InjectArgs {      // lattice load / boosted injection, FP64
     double hx, hy, hz, Lx, Ly, Lz, gam, beta;
     int ppx, ppy, ppz;
     int64_t NX, NY, m_lo, m_hi;
-    double z_start, z_end, ramp, ne, jitter, dzl, hz_lab, wfac, uz0;
+    double z_start, z_end, ramp, ne, jitter, dzl, hz_lab, wfac;
     int nprof;
     double prof[16];
     uint64_t seed;
@@ -325,7 +384,7 @@ void launch_rho(const Geom &g, const Species<real> &sp, const int *lo, const int
                 cudaStream_t s);
 template <typename real>
 void launch_particle_sums(const Geom &g, const Species<real> &sp, const int *lo, const int *hi, double q,
-                          const real ion_u[3], double *partials, int nblocks, cudaStream_t s);
+                          const real u_drift[3], double *partials, int nblocks, cudaStream_t s);
 void launch_inject(const InjectArgs &a, cudaStream_t s);
 template <typename real>
 void launch_btd(const BtdArgs<real> &a, cudaStream_t s);

@@ -370,6 +370,167 @@ __device__ __forceinline__ void deposit_sel(unsigned sel, typename Acc<real>::ty
 #undef PIC_DEP
 }
 
+// ------------------------------------------------------------- drifting ions
+
+// Ions immobile in the lab move at the species' constant u = (0, 0, -gamma
+// beta) in the boosted frame: every ion of a step moves by the same
+// dz = u_z dt / (gamma h_z), in (-1, 0) cells, and its transverse position
+// never changes.  So only Jz is deposited, Wz = DSz (S0x S0y) (the general
+// formula with DSx = DSy = 0, in the arithmetic order of the electrons'
+// z-only deposit), and an ion either stays in its tile or moves to the one
+// tile below it (the top tile when z wraps, none when it leaves the box):
+// one counter per warp reserves the slots of the leavers.
+// The ions of tile t (all threads of the CTA call it): their Jz into the
+// current tile at Jz (the "hi" words; the "lo" words LOFF further), records
+// into the output side.  sP holds kIonStages x 5 x kBlock prefetch slots
+// (the copies of two iterations are in flight while one is processed: the
+// ion loop moves little data per instruction).  Returns false (nothing done)
+// for an empty bucket.
+constexpr int kIonStages = 3;
+
+template <typename real, int DIM, int S, int TX, int TY, int TZ, int LOFF>
+__device__ __forceinline__ bool ions_of_tile(const Geom &g, const IonSide<real> &is, int64_t t,
+                                             typename Acc<real>::type *Jz, real *sP, real dz, real scale_z,
+                                             real lo_scale, unsigned *err, int *s_stay)
+{
+    constexpr int JL = S, JH = S + 1;
+    constexpr int QX = TX + JL + JH, QY = DIM == 3 ? TY + JL + JH : 1;
+    const unsigned lane = threadIdx.x & 31u;
+    int n_lo, n_hi;
+    bucket_counts(is.in_lo, is.in_hi, t, g.cap, n_lo, n_hi, err);
+    const int n = n_lo + n_hi;
+    if (n == 0) return false;
+    auto prefetch = [&](int it) {
+        const int p = it * kBlock + (int)threadIdx.x;
+        if (p < n) {
+            const int64_t s = bucket_slot(t, g.cap, n_lo, n_hi, p);
+            real *d = sP + (it % kIonStages) * 5 * kBlock + threadIdx.x;
+            __pipeline_memcpy_async(d + 0 * kBlock, is.in.ox + s, sizeof(real));
+            if (DIM == 3) __pipeline_memcpy_async(d + 1 * kBlock, is.in.oy + s, sizeof(real));
+            __pipeline_memcpy_async(d + 2 * kBlock, is.in.oz + s, sizeof(real));
+            __pipeline_memcpy_async(d + 3 * kBlock, is.in.w + s, sizeof(real));
+            __pipeline_memcpy_async(d + 4 * kBlock, is.in.cell + s, sizeof(int32_t));
+        }
+        __pipeline_commit();
+    };
+    const int64_t ntxy = (int64_t)g.nt[0] * g.nt[1];
+    const int tix = (int)(t % g.nt[0]);
+    const int tiy = (int)((t / g.nt[0]) % g.nt[1]);
+    const int tiz = (int)(t / ntxy);
+    const int lox = tix << g.lt[0], loy = tiy << g.lt[1], loz = tiz << g.lt[2];
+    // the tile an ion leaving this one through its lower z face enters
+    // (-1: it leaves the box)
+    const int64_t below = tiz > 0 ? t - ntxy : (g.bc_z == 0 ? t + (int64_t)(g.nt[2] - 1) * ntxy : -1);
+    __syncthreads();
+    if (threadIdx.x == 0) *s_stay = 0;
+    // each thread copies and reads only its own slots: no barrier between
+    // the stages
+    for (int it = 0; it < kIonStages - 1; ++it) prefetch(it);
+    __syncthreads();
+    for (int it = 0; it * kBlock < n; ++it) {
+        const int p = it * kBlock + threadIdx.x;
+        prefetch(it + kIonStages - 1);
+        __pipeline_wait_prior(kIonStages - 1);
+        bool stay = false, leave = false;
+        real ox = 0, oy = 0, oz = 0, w = 0;
+        int32_t cell = 0;
+        int64_t pid = 0;
+        if (p < n) {
+            const real *d = sP + (it % kIonStages) * 5 * kBlock + threadIdx.x;
+            int ci, cj, ck;
+            unpack_cell(g, *reinterpret_cast<const int32_t *>(d + 4 * kBlock), ci, cj, ck);
+            const int li = ci - lox, lj = cj - loy, lk = ck - loz;
+            if (li < 0 || li >= TX || lj < 0 || lj >= TY || lk < 0 || lk >= TZ) {
+                atomicOr(err, ERR_TILE);
+            } else {
+                ox = d[0 * kBlock];
+                oy = DIM == 3 ? d[1 * kBlock] : real(0);
+                oz = d[2 * kBlock];
+                w = d[3 * kBlock];
+                if (is.in.id) pid = is.in.id[bucket_slot(t, g.cap, n_lo, n_hi, p)];
+                const real z1 = add_rn(oz, dz);
+                real S0z[S + 2], DSz[S + 2], wx[S + 1], wy[S + 1];
+                bool crossed;
+                const int az = esirk_axis_c<S>(oz, z1, S0z, DSz, crossed) + lk + JL;
+                const int bx = offset_weights<S>(ox, wx) + li + JL;
+                int by = 0;
+                if (DIM == 3) by = offset_weights<S>(oy, wy) + lj + JL;
+                const real fz = is.jfac_z * w * scale_z;
+                real Pz[S + 2];
+                real acc = 0;
+#pragma unroll
+                for (int c = 0; c < S + 2; ++c) { acc += DSz[c]; Pz[c] = fz * acc; }
+#pragma unroll
+                for (int b = 0; b < (DIM == 3 ? S + 1 : 1); ++b) {
+#pragma unroll
+                    for (int q = 0; q < S + 1; ++q) {
+                        const real sxy = DIM == 3 ? wx[q] * wy[b] : wx[q];
+#pragma unroll
+                        for (int c = 0; c < S + 1; ++c)
+                            sh_acc<LOFF>(Jz + ((az + c) * QY + (by + b)) * QX + bx + q, Pz[c], sxy, lo_scale);
+                    }
+                }
+                // z1 in (-1, 1): the same cell or the one below; an offset
+                // that rounds to 1 stays in the cell with offset 0
+                int sz = 0;
+                oz = z1;
+                if (z1 < real(0)) {
+                    oz = z1 + real(1);
+                    sz = -1;
+                    if (oz >= real(1)) { oz = 0; sz = 0; }
+                }
+                int nk = ck + sz;
+                bool alive = true;
+                if (nk < 0) {
+                    if (g.bc_z == 0) nk += g.nz;
+                    else alive = false;
+                }
+                if (alive) {
+                    cell = pack_cell(g, ci, cj, nk);
+                    stay = lk + sz >= 0;
+                    leave = !stay;
+                }
+            }
+        }
+        // slots: stayers from the shared counter, leavers from the counter
+        // of the tile below (one atomic each per warp)
+        const unsigned ms = __ballot_sync(0xffffffffu, stay), ml = __ballot_sync(0xffffffffu, leave);
+        int bs = 0, bl = 0;
+        if (lane == 0) {
+            if (ms) bs = atomicAdd(s_stay, __popc(ms));
+            if (ml) bl = atomicAdd(&is.out_hi[below], __popc(ml));
+        }
+        bs = __shfl_sync(0xffffffffu, bs, 0);
+        bl = __shfl_sync(0xffffffffu, bl, 0);
+        const unsigned below_me = (1u << lane) - 1u;
+        int64_t d = -1;
+        if (stay) {
+            const int r = bs + __popc(ms & below_me);
+            if (r < g.cap) d = t * (int64_t)g.cap + r;
+            else atomicOr(err, ERR_CAPACITY);
+        } else if (leave) {
+            const int r = bl + __popc(ml & below_me);
+            if (r < g.cap) d = below * (int64_t)g.cap + (g.cap - 1 - r);
+            else atomicOr(err, ERR_CAPACITY);
+        }
+        if (d >= 0) {
+            is.out.ox[d] = ox;
+            if (DIM == 3) is.out.oy[d] = oy;
+            is.out.oz[d] = oz;
+            is.out.w[d] = w;
+            is.out.cell[d] = cell;
+            if (is.out.id) is.out.id[d] = pid;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        is.out_lo[t] = min(*s_stay, g.cap);
+        is.in_lo[t] = 0;
+        is.in_hi[t] = 0;
+    }
+    return true;
+}
+
 // ------------------------------------------------------------ push kernel
 
 template <typename real, int DIM, int S, int TX, int TY, int TZ>
@@ -391,13 +552,17 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
     // with cp.async while the current ones are pushed (two buffers of
     // 8 attributes x kBlock particles; each thread copies and reads its own)
     real *sP = reinterpret_cast<real *>(sJ + (sizeof(real) == 4 ? 6 : 3) * QN);
-    __shared__ int s_stay;
+    __shared__ int s_stay, s_stay_i;
+    // the plasma drift and its displacement per step (the drifting ions')
+    const Drift<real> drift(a.u_drift, a.dtdh[2]);
+    const real dz_drift = drift.dz;
 
     for (int64_t t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
         int n_lo, n_hi;
         bucket_counts(a.in_lo, a.in_hi, t, g.cap, n_lo, n_hi, a.err);
         const int n = n_lo + n_hi;
-        if (n == 0) continue;  // uniform over the CTA
+        // uniform over the CTA
+        if (n == 0 && !(a.fuse_ions && a.ions.in_lo[t] + a.ions.in_hi[t] > 0)) continue;
         auto prefetch = [&](int it) {
             const int p = it * kBlock + (int)threadIdx.x;
             if (p < n) {
@@ -488,19 +653,22 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
                 if (paired && (ex != real(0) || ey != real(0) || ez != real(0) || bx != real(0) ||
                                by != real(0) || bz != real(0)))
                     release = true;
-                boris(ux, uy, uz, ex, ey, ez, bx, by, bz, a.eps);
-                const real ig = inv_gamma(ux, uy, uz);
-                vy = uy * ig;
-                const real dx = ux * ig * a.dtdh[0];
-                const real dy = DIM == 3 ? uy * ig * a.dtdh[1] : real(0);
-                const real dz = uz * ig * a.dtdh[2];
+                boris(ux, uy, uz, drift.U, ex, ey, ez, bx, by, bz, a.eps);
+                real vx;
+                const real dvz = drift_velocity(drift, ux, uy, uz, vx, vy);
+                const real dx = vx * a.dtdh[0];
+                const real dy = DIM == 3 ? vy * a.dtdh[1] : real(0);
+                // the drift's displacement (the ions' own) plus the record's
+                // departure from it
+                const real ddz = dvz * a.dtdh[2];
+                const real dz = dz_drift + ddz;
                 if (!(fabs(dx) < real(1) && fabs(dy) < real(1) && fabs(dz) < real(1))) {
                     atomicOr(a.err, (dx == dx && dy == dy && dz == dz) ? ERR_CFL : ERR_NAN);
                     valid = false;
                 } else {
                     x1 = ox + dx;
                     y1 = oy + dy;
-                    z1 = oz + dz;
+                    z1 = add_rn(oz, dz_drift) + ddz;
                 }
             }
             // ---- released ion: a record at the pair's position x^n, in the ion
@@ -598,6 +766,11 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
             }
         }
         __syncthreads();
+        // the drifting ions of the tile, into the same current tile
+        if (a.fuse_ions) {
+            ions_of_tile<real, DIM, S, TX, TY, TZ, 3 * QN>(g, a.ions, t, sJ + 2 * QN, sP, dz_drift, a.fx_scale[2],
+                                                            a.fx_lo[0], a.err, &s_stay_i);
+        }
         // flush the J tile: one global add per non-zero node
         flush_tile<real, DIM, 3, QX, QY, QZ, JL>(g, Ptr3<real>{a.J[0], a.J[1], a.J[2]}, 0x4u, sJ, a.fx_quant[0],
                                                  a.fx_quant[1], a.fx_quant[2], a.fx_lo[1], lox, loy, loz);
@@ -611,14 +784,6 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
 
 // ----------------------------------------------------- drifting-ion kernel
 
-// Ions immobile in the lab move at the species' constant u = (0, 0, -gamma
-// beta) in the boosted frame: every ion of a step moves by the same
-// dz = u_z dt / (gamma h_z), in (-1, 0) cells, and its transverse position
-// never changes.  So only Jz is deposited, Wz = DSz (S0x S0y) (the general
-// formula with DSx = DSy = 0, in the arithmetic order of the electrons'
-// z-only deposit), and an ion either stays in its tile or moves to the one
-// tile below it (the top tile when z wraps, none when it leaves the box):
-// one counter per warp reserves the slots of the leavers.
 template <typename real, int DIM, int S, int TX, int TY, int TZ>
 __global__ void __launch_bounds__(kBlock) ion_kernel(PushArgs<real> a)
 {
@@ -630,147 +795,24 @@ __global__ void __launch_bounds__(kBlock) ion_kernel(PushArgs<real> a)
     using acc_t = typename Acc<real>::type;
     acc_t *sJ = reinterpret_cast<acc_t *>(smem_raw);
     // prefetched records after the J tile ("hi" and, in FP32, "lo" words):
-    // 2 buffers x 5 attributes x kBlock
+    // kIonStages buffers x 5 attributes x kBlock
     real *sP = reinterpret_cast<real *>(sJ + (sizeof(real) == 4 ? 2 : 1) * QN);
-    const real ig = inv_gamma(a.ion_u[0], a.ion_u[1], a.ion_u[2]);
-    const real dz = a.ion_u[2] * ig * a.dtdh[2];
-    const unsigned lane = threadIdx.x & 31u;
+    const Drift<real> drift(a.u_drift, a.dtdh[2]);
+    const real dz = drift.dz;
+    const IonSide<real> &is = a.ions;  // read from the parameter space
     __shared__ int s_stay;
 
     for (int64_t t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
-        int n_lo, n_hi;
-        bucket_counts(a.in_lo, a.in_hi, t, g.cap, n_lo, n_hi, a.err);
-        const int n = n_lo + n_hi;
-        if (n == 0) continue;
-        auto prefetch = [&](int it) {
-            const int p = it * kBlock + (int)threadIdx.x;
-            if (p < n) {
-                const int64_t s = bucket_slot(t, g.cap, n_lo, n_hi, p);
-                real *d = sP + (it & 1) * 5 * kBlock + threadIdx.x;
-                __pipeline_memcpy_async(d + 0 * kBlock, a.in.ox + s, sizeof(real));
-                if (DIM == 3) __pipeline_memcpy_async(d + 1 * kBlock, a.in.oy + s, sizeof(real));
-                __pipeline_memcpy_async(d + 2 * kBlock, a.in.oz + s, sizeof(real));
-                __pipeline_memcpy_async(d + 3 * kBlock, a.in.w + s, sizeof(real));
-                __pipeline_memcpy_async(d + 4 * kBlock, a.in.cell + s, sizeof(int32_t));
-            }
-            __pipeline_commit();
-        };
-        const int64_t ntxy = (int64_t)g.nt[0] * g.nt[1];
+        if (is.in_lo[t] + is.in_hi[t] == 0) continue;  // uniform over the CTA
         const int tix = (int)(t % g.nt[0]);
         const int tiy = (int)((t / g.nt[0]) % g.nt[1]);
-        const int tiz = (int)(t / ntxy);
+        const int tiz = (int)(t / ((int64_t)g.nt[0] * g.nt[1]));
         const int lox = tix << g.lt[0], loy = tiy << g.lt[1], loz = tiz << g.lt[2];
-        // the tile an ion leaving this one through its lower z face enters
-        // (-1: it leaves the box)
-        const int64_t below = tiz > 0 ? t - ntxy : (g.bc_z == 0 ? t + (int64_t)(g.nt[2] - 1) * ntxy : -1);
         __syncthreads();
-        if (threadIdx.x == 0) s_stay = 0;
         for (int q = threadIdx.x; q < (sizeof(real) == 4 ? 2 : 1) * QN; q += blockDim.x) sJ[q] = 0;
-        prefetch(0);
-        __syncthreads();
-        for (int it = 0; it * kBlock < n; ++it) {
-            const int p = it * kBlock + threadIdx.x;
-            prefetch(it + 1);
-            __pipeline_wait_prior(1);
-            bool stay = false, leave = false;
-            real ox = 0, oy = 0, oz = 0, w = 0;
-            int32_t cell = 0;
-            int64_t pid = 0;
-            if (p < n) {
-                const real *d = sP + (it & 1) * 5 * kBlock + threadIdx.x;
-                int ci, cj, ck;
-                unpack_cell(g, *reinterpret_cast<const int32_t *>(d + 4 * kBlock), ci, cj, ck);
-                const int li = ci - lox, lj = cj - loy, lk = ck - loz;
-                if (li < 0 || li >= TX || lj < 0 || lj >= TY || lk < 0 || lk >= TZ) {
-                    atomicOr(a.err, ERR_TILE);
-                } else {
-                    ox = d[0 * kBlock];
-                    oy = DIM == 3 ? d[1 * kBlock] : real(0);
-                    oz = d[2 * kBlock];
-                    w = d[3 * kBlock];
-                    if (a.in.id) pid = a.in.id[bucket_slot(t, g.cap, n_lo, n_hi, p)];
-                    const real z1 = oz + dz;
-                    real S0z[S + 2], DSz[S + 2], wx[S + 1], wy[S + 1];
-                    bool crossed;
-                    const int az = esirk_axis_c<S>(oz, z1, S0z, DSz, crossed) + lk + JL;
-                    const int bx = offset_weights<S>(ox, wx) + li + JL;
-                    int by = 0;
-                    if (DIM == 3) by = offset_weights<S>(oy, wy) + lj + JL;
-                    const real fz = a.jfac[2] * w * a.fx_scale[2];
-                    real Pz[S + 2];
-                    real acc = 0;
-#pragma unroll
-                    for (int c = 0; c < S + 2; ++c) { acc += DSz[c]; Pz[c] = fz * acc; }
-#pragma unroll
-                    for (int b = 0; b < (DIM == 3 ? S + 1 : 1); ++b) {
-#pragma unroll
-                        for (int q = 0; q < S + 1; ++q) {
-                            const real sxy = DIM == 3 ? wx[q] * wy[b] : wx[q];
-#pragma unroll
-                            for (int c = 0; c < S + 1; ++c)
-                                sh_acc<QN>(sJ + ((az + c) * QY + (by + b)) * QX + bx + q, Pz[c], sxy, a.fx_lo[0]);
-                        }
-                    }
-                    // z1 in (-1, 1): the same cell or the one below; an offset
-                    // that rounds to 1 stays in the cell with offset 0
-                    int sz = 0;
-                    oz = z1;
-                    if (z1 < real(0)) {
-                        oz = z1 + real(1);
-                        sz = -1;
-                        if (oz >= real(1)) { oz = 0; sz = 0; }
-                    }
-                    int nk = ck + sz;
-                    bool alive = true;
-                    if (nk < 0) {
-                        if (g.bc_z == 0) nk += g.nz;
-                        else alive = false;
-                    }
-                    if (alive) {
-                        cell = pack_cell(g, ci, cj, nk);
-                        stay = lk + sz >= 0;
-                        leave = !stay;
-                    }
-                }
-            }
-            // slots: stayers from the shared counter, leavers from the counter
-            // of the tile below (one atomic each per warp)
-            const unsigned ms = __ballot_sync(0xffffffffu, stay), ml = __ballot_sync(0xffffffffu, leave);
-            int bs = 0, bl = 0;
-            if (lane == 0) {
-                if (ms) bs = atomicAdd(&s_stay, __popc(ms));
-                if (ml) bl = atomicAdd(&a.out_hi[below], __popc(ml));
-            }
-            bs = __shfl_sync(0xffffffffu, bs, 0);
-            bl = __shfl_sync(0xffffffffu, bl, 0);
-            const unsigned below_me = (1u << lane) - 1u;
-            int64_t d = -1;
-            if (stay) {
-                const int r = bs + __popc(ms & below_me);
-                if (r < g.cap) d = t * (int64_t)g.cap + r;
-                else atomicOr(a.err, ERR_CAPACITY);
-            } else if (leave) {
-                const int r = bl + __popc(ml & below_me);
-                if (r < g.cap) d = below * (int64_t)g.cap + (g.cap - 1 - r);
-                else atomicOr(a.err, ERR_CAPACITY);
-            }
-            if (d >= 0) {
-                a.out.ox[d] = ox;
-                if (DIM == 3) a.out.oy[d] = oy;
-                a.out.oz[d] = oz;
-                a.out.w[d] = w;
-                a.out.cell[d] = cell;
-                if (a.out.id) a.out.id[d] = pid;
-            }
-        }
-        __syncthreads();
+        ions_of_tile<real, DIM, S, TX, TY, TZ, QN>(g, is, t, sJ, sP, dz, a.fx_scale[2], a.fx_lo[0], a.err, &s_stay);
         flush_tile<real, DIM, 1, QX, QY, QZ, JL>(g, Ptr3<real>{a.J[2], a.J[2], a.J[2]}, 0x1u, sJ, a.fx_quant[2],
                                                  a.fx_quant[2], a.fx_quant[2], a.fx_lo[1], lox, loy, loz);
-        if (threadIdx.x == 0) {
-            a.out_lo[t] = min(s_stay, g.cap);
-            a.in_lo[t] = 0;
-            a.in_hi[t] = 0;
-        }
     }
 }
 
@@ -785,7 +827,8 @@ static size_t push_smem(bool ions)
     const int QN = (TX + 2 * S + 1) * (DIM == 3 ? TY + 2 * S + 1 : 1) * (TZ + 2 * S + 1);
     // FP32 currents take two words per node ("hi" and "lo"), FP64 one
     const int JW = sizeof(real) == 4 ? 2 : 1;
-    return ions ? sizeof(real) * (size_t)(JW * QN + 2 * 5 * kBlock)
+    static_assert(kIonStages * 5 <= 2 * 8, "the ion stages fit in the electrons' prefetch buffers");
+    return ions ? sizeof(real) * (size_t)(JW * QN + kIonStages * 5 * kBlock)
                 : sizeof(real) * (size_t)(6 * FN + JW * 3 * QN + 2 * 8 * kBlock);
 }
 
@@ -1004,11 +1047,12 @@ __global__ void particle_sums_kernel(Geom g, Species<real> sp, const int *lo, co
         for (int p = threadIdx.x; p < n; p += blockDim.x) {
             const int64_t s = bucket_slot(t, g.cap, n_lo, n_hi, p);
             const double w = (double)sp.w[s];
+            // records hold u - u_drift; ions move with the drift itself
             double ux = iux, uy = iuy, uz = iuz;
             if (sp.ux) {
-                ux = (double)sp.ux[s];
-                uy = (double)sp.uy[s];
-                uz = (double)sp.uz[s];
+                ux += (double)sp.ux[s];
+                uy += (double)sp.uy[s];
+                uz += (double)sp.uz[s];
             }
             const double u2 = ux * ux + uy * uy + uz * uz;
             const double ke = w * (u2 / (sqrt(1.0 + u2) + 1.0));  // gamma - 1 without cancellation
@@ -1045,10 +1089,10 @@ __global__ void particle_sums_kernel(Geom g, Species<real> sp, const int *lo, co
 
 template <typename real>
 void launch_particle_sums(const Geom &g, const Species<real> &sp, const int *lo, const int *hi, double q,
-                          const real ion_u[3], double *partials, int nblocks, cudaStream_t s)
+                          const real u_drift[3], double *partials, int nblocks, cudaStream_t s)
 {
-    particle_sums_kernel<real><<<nblocks, 256, 0, s>>>(g, sp, lo, hi, q, (double)ion_u[0], (double)ion_u[1],
-                                                       (double)ion_u[2], partials);
+    particle_sums_kernel<real><<<nblocks, 256, 0, s>>>(g, sp, lo, hi, q, (double)u_drift[0], (double)u_drift[1],
+                                                       (double)u_drift[2], partials);
 }
 
 #define PIC_INSTANTIATE(real)                                                                       \
