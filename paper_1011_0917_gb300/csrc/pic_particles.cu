@@ -87,13 +87,14 @@ struct Ptr3 {
 // shared memory.  Element-wise over all threads with compile-time extents, so
 // the index decomposition is a few multiply-shifts; consecutive threads read
 // consecutive x.  Nodes outside the valid z range of a component (absorbing z)
-// are zero; x and y wrap.
+// are zero; x and y wrap.  Returns whether this thread staged a non-zero value.
 template <typename real, int DIM, int NC, int FX, int FY, int FZ, int L>
-__device__ __forceinline__ void stage_tile(const Geom &g, const Ptr6<real> src, unsigned half_z, real *dst, int lox,
+__device__ __forceinline__ bool stage_tile(const Geom &g, const Ptr6<real> src, unsigned half_z, real *dst, int lox,
                                            int loy, int loz)
 {
     constexpr int FN = FX * FY * FZ;
     const bool tiny = g.nx < FX || (DIM == 3 && g.ny < FY);
+    bool nonzero = false;
     // each node of the box once, all components of it together
     for (int r = threadIdx.x; r < FN; r += blockDim.x) {
         const int lz = r / (FX * FY), r2 = r - lz * (FX * FY);
@@ -107,9 +108,12 @@ __device__ __forceinline__ void stage_tile(const Geom &g, const Ptr6<real> src, 
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             const bool ok = inz && (g.bc_z == 0 || gk <= zmax_of(g, (half_z >> c) & 1u));
-            dst[c * FN + r] = ok ? src[c][o] : real(0);
+            const real v = ok ? src[c][o] : real(0);
+            dst[c * FN + r] = v;
+            nonzero = nonzero || v != real(0);
         }
     }
+    return nonzero;
 }
 
 // Add NC shared-memory tiles (box [lo - L, lo - L + Q) per axis) to the global
@@ -587,11 +591,11 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
         __syncthreads();  // previous tile finished with shared memory
         if (threadIdx.x == 0) s_stay = 0;
         // Ez, Bx, By live on half-integer z (bits 2, 3, 4)
-        stage_tile<real, DIM, 6, FX, FY, FZ, FL>(g, Ptr6<real>{a.E[0], a.E[1], a.E[2], a.B[0], a.B[1], a.B[2]},
-                                                 0x1Cu, sF, lox, loy, loz);
+        const bool staged_nonzero = stage_tile<real, DIM, 6, FX, FY, FZ, FL>(
+            g, Ptr6<real>{a.E[0], a.E[1], a.E[2], a.B[0], a.B[1], a.B[2]}, 0x1Cu, sF, lox, loy, loz);
         for (int q = threadIdx.x; q < (sizeof(real) == 4 ? 6 : 3) * QN; q += blockDim.x) sJ[q] = 0;
         prefetch(0);
-        __syncthreads();
+        const bool field_in_tile = __syncthreads_or(staged_nonzero) != 0;
 
         for (int it = 0; it * kBlock < n; ++it) {
             const int p = it * kBlock + threadIdx.x;
@@ -629,31 +633,35 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
             real x1 = 0, y1 = 0, z1 = 0, vy = 0;
             bool release = false;
             if (valid) {
-                real wxu[S + 1], wxh[S + 1], wyu[S + 1], wyh[S + 1], wzu[S + 1], wzh[S + 1];
-                const int bxu = offset_weights<S>(ox, wxu) + li + FL;
-                const int bxh = half_weights<S>(ox, wxh) + li + FL;
-                const int bzu = offset_weights<S>(oz, wzu) + lk + FL;
-                const int bzh = half_weights<S>(oz, wzh) + lk + FL;
-                int byu = 0, byh = 0;
-                if (DIM == 3) {
-                    byu = offset_weights<S>(oy, wyu) + lj + FL;
-                    byh = half_weights<S>(oy, wyh) + lj + FL;
-                } else {
+                // a tile whose staged E and B are all zero gathers exactly zero
+                // everywhere: Boris is then the identity and no pair is released
+                if (field_in_tile) {
+                    real wxu[S + 1], wxh[S + 1], wyu[S + 1], wyh[S + 1], wzu[S + 1], wzh[S + 1];
+                    const int bxu = offset_weights<S>(ox, wxu) + li + FL;
+                    const int bxh = half_weights<S>(ox, wxh) + li + FL;
+                    const int bzu = offset_weights<S>(oz, wzu) + lk + FL;
+                    const int bzh = half_weights<S>(oz, wzh) + lk + FL;
+                    int byu = 0, byh = 0;
+                    if (DIM == 3) {
+                        byu = offset_weights<S>(oy, wyu) + lj + FL;
+                        byh = half_weights<S>(oy, wyh) + lj + FL;
+                    } else {
 #pragma unroll
-                    for (int q = 0; q <= S; ++q) wyu[q] = wyh[q] = real(q == 0);
+                        for (int q = 0; q <= S; ++q) wyu[q] = wyh[q] = real(q == 0);
+                    }
+                    const real ex = gather_comp<DIM, S>(sF + 0 * FN, FX, FY, bxh, byu, bzu, wxh, wyu, wzu);
+                    const real ey = gather_comp<DIM, S>(sF + 1 * FN, FX, FY, bxu, byh, bzu, wxu, wyh, wzu);
+                    const real ez = gather_comp<DIM, S>(sF + 2 * FN, FX, FY, bxu, byu, bzh, wxu, wyu, wzh);
+                    const real bx = gather_comp<DIM, S>(sF + 3 * FN, FX, FY, bxu, byh, bzh, wxu, wyh, wzh);
+                    const real by = gather_comp<DIM, S>(sF + 4 * FN, FX, FY, bxh, byu, bzh, wxh, wyu, wzh);
+                    const real bz = gather_comp<DIM, S>(sF + 5 * FN, FX, FY, bxh, byh, bzu, wxh, wyh, wzu);
+                    // a paired electron that gathers a non-zero field leaves its
+                    // ion behind: the pair's current is no longer zero
+                    if (paired && (ex != real(0) || ey != real(0) || ez != real(0) || bx != real(0) ||
+                                   by != real(0) || bz != real(0)))
+                        release = true;
+                    boris(ux, uy, uz, drift.U, ex, ey, ez, bx, by, bz, a.eps);
                 }
-                const real ex = gather_comp<DIM, S>(sF + 0 * FN, FX, FY, bxh, byu, bzu, wxh, wyu, wzu);
-                const real ey = gather_comp<DIM, S>(sF + 1 * FN, FX, FY, bxu, byh, bzu, wxu, wyh, wzu);
-                const real ez = gather_comp<DIM, S>(sF + 2 * FN, FX, FY, bxu, byu, bzh, wxu, wyu, wzh);
-                const real bx = gather_comp<DIM, S>(sF + 3 * FN, FX, FY, bxu, byh, bzh, wxu, wyh, wzh);
-                const real by = gather_comp<DIM, S>(sF + 4 * FN, FX, FY, bxh, byu, bzh, wxh, wyu, wzh);
-                const real bz = gather_comp<DIM, S>(sF + 5 * FN, FX, FY, bxh, byh, bzu, wxh, wyh, wzu);
-                // a paired electron that gathers a non-zero field leaves its ion
-                // behind: the pair's current is no longer zero
-                if (paired && (ex != real(0) || ey != real(0) || ez != real(0) || bx != real(0) ||
-                               by != real(0) || bz != real(0)))
-                    release = true;
-                boris(ux, uy, uz, drift.U, ex, ey, ez, bx, by, bz, a.eps);
                 real vx;
                 const real dvz = drift_velocity(drift, ux, uy, uz, vx, vy);
                 const real dx = vx * a.dtdh[0];
