@@ -335,6 +335,43 @@ pic_status pic_btd_setup(pic_ctx *ctx, const pic_btd_params *p, void *buf, size_
    then its nz int32 flags (1: filled). */
 pic_status pic_btd_get(pic_ctx *ctx, int j, void *dst, size_t dst_bytes, int dst_is_device);
 
+/* ---------------------------------------------------------------- adjoint */
+
+/* Reverse-mode gradient of a run (2D3V, CIC shape, no moving window): the
+   library's own extension of the method, built from the transposes of the
+   step's maps (Yee with Mur's condition, filter, antenna, Esirkepov deposit,
+   gather, Boris rotation, move).  The objective is linear in the final fields,
+   L = sum(lambda_E E^N) + sum(lambda_B B^N) with caller-given cotangents; the
+   gradient is taken with respect to the plasma profile coefficients c_1..c_M
+   of pic_load_plasma (they scale every particle weight), the laser's a0 and
+   its waist w0.  The run starts right after pic_load_plasma and
+   pic_launch_laser (no step taken): pic_adjoint_forward regenerates the same
+   plasma in a fixed-order particle store (slot p is one particle for the whole
+   run), runs nsteps steps and keeps a checkpoint every checkpoint_every steps;
+   pic_adjoint_backward recomputes each segment from its checkpoint and runs it
+   backwards.  The context's own state is not changed. */
+typedef struct {
+    int nsteps;            /* N >= 1                                          */
+    int checkpoint_every;  /* K >= 1: checkpoints at steps 0, K, 2K, ...      */
+} pic_adjoint_params;
+
+/* Bytes of the device buffer an adjoint run needs (checkpoints, one segment
+   of K + 1 states, cotangents).  PIC_ERR_ARG for an unsupported run,
+   PIC_ERR_STATE if a step has been taken since pic_load_plasma. */
+pic_status pic_adjoint_bytes(pic_ctx *ctx, const pic_adjoint_params *p, size_t *bytes);
+
+/* The forward run into buf (device memory of at least pic_adjoint_bytes bytes,
+   owned by the caller and kept alive until pic_adjoint_backward).  fields_out
+   (device, may be NULL) receives E^N, B^N: six components of (nz+1) nx
+   elements, Ex Ey Ez Bx By Bz. */
+pic_status pic_adjoint_forward(pic_ctx *ctx, const pic_adjoint_params *p, void *buf, size_t bytes,
+                               void *fields_out);
+
+/* cot: device cotangents lambda_E, lambda_B of E^N, B^N (the layout of
+   fields_out).  grad (host, M + 2 doubles): dL/dc_1 .. dL/dc_M, dL/da0,
+   dL/dw0.  PIC_ERR_STATE without a preceding pic_adjoint_forward. */
+pic_status pic_adjoint_backward(pic_ctx *ctx, const void *cot, double *grad);
+
 /* ------------------------------------------------------------ checkpoint */
 
 /* Size of a compact snapshot (fields, live particles, time, laser) now. */

@@ -24,7 +24,8 @@ __all__ = [
     "pic_get_state", "pic_set_state", "pic_last_error", "pic_status_string", "pic_destroy", "pic_profile",
     "pic_profile_read", "pic_filter_current_noalloc", "PIC_NOALLOC_MAX_NODES", "BtdParams", "pic_btd_bytes",
     "pic_btd_setup", "pic_btd_get", "pic_set_moving_window", "pic_batch_create", "pic_batch_step",
-    "pic_batch_destroy", "Simulation", "Batch", "library_path",
+    "pic_batch_destroy", "Simulation", "Batch", "library_path", "AdjointParams", "pic_adjoint_bytes",
+    "pic_adjoint_forward", "pic_adjoint_backward", "StageGradient",
 ]
 
 PIC_OK, PIC_ERR_ARG, PIC_ERR_STATE, PIC_ERR_CUDA = 0, 1, 2, 3
@@ -96,6 +97,11 @@ class BtdParams(C.Structure):
                 ("dz", C.c_double), ("nz", C.c_int), ("plane", C.c_int)]
 
 
+class AdjointParams(C.Structure):
+    """pic_adjoint_params: N steps, a checkpoint every K."""
+    _fields_ = [("nsteps", C.c_int), ("checkpoint_every", C.c_int)]
+
+
 def _load():
     global _lib
     if _lib is not None:
@@ -136,6 +142,9 @@ def _load():
         "pic_btd_bytes": (S, [P, C.POINTER(BtdParams), C.POINTER(C.c_size_t)]),
         "pic_btd_setup": (S, [P, C.POINTER(BtdParams), P, C.c_size_t]),
         "pic_btd_get": (S, [P, I, P, C.c_size_t, I]),
+        "pic_adjoint_bytes": (S, [P, C.POINTER(AdjointParams), C.POINTER(C.c_size_t)]),
+        "pic_adjoint_forward": (S, [P, C.POINTER(AdjointParams), P, C.c_size_t, P]),
+        "pic_adjoint_backward": (S, [P, P, C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -335,6 +344,23 @@ def pic_btd_get(ctx, j: int, dst_ptr: int, dst_bytes: int, dst_is_device: bool):
     _check(ctx, _load().pic_btd_get(ctx, j, C.c_void_p(dst_ptr), dst_bytes, int(dst_is_device)))
 
 
+def pic_adjoint_bytes(ctx, p: AdjointParams) -> int:
+    n = C.c_size_t(0)
+    _check(ctx, _load().pic_adjoint_bytes(ctx, C.byref(p), C.byref(n)))
+    return n.value
+
+
+def pic_adjoint_forward(ctx, p: AdjointParams, buf_ptr: int, nbytes: int, fields_out_ptr: int):
+    _check(ctx, _load().pic_adjoint_forward(ctx, C.byref(p), C.c_void_p(buf_ptr), nbytes,
+                                            C.c_void_p(fields_out_ptr) if fields_out_ptr else None))
+
+
+def pic_adjoint_backward(ctx, cot_ptr: int, n_grad: int):
+    g = (C.c_double * n_grad)()
+    _check(ctx, _load().pic_adjoint_backward(ctx, C.c_void_p(cot_ptr), g))
+    return list(g)
+
+
 # --------------------------------------------------- torch-owned buffers
 
 
@@ -391,6 +417,7 @@ class Simulation:
     def load_plasma(self, ne, z_start, z_end, ramp=0.0, ppc=(2, 1, 2), jitter=0.1, profile=(), ions=1):
         prof = (C.c_double * max(1, len(profile)))(*profile) if len(profile) else None
         self._prof = prof
+        self._prof_n = len(profile)
         p = PlasmaParams(ne, z_start, z_end, ramp, (C.c_int * 3)(*ppc), jitter, len(profile),
                          C.cast(prof, C.POINTER(C.c_double)) if prof is not None else None, ions)
         pic_load_plasma(self.ctx, p)
@@ -456,6 +483,65 @@ class Simulation:
         filled = host[nd:].view(np.int32) != 0
         names = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
         return {c: vals[q] for q, c in enumerate(names)}, filled
+
+
+    def adjoint_forward(self, nsteps, checkpoint_every=50):
+        """Forward run of the adjoint (from right after load_plasma and
+        launch_laser): returns E^N, B^N as a (6, nz+1, nx) device tensor and
+        keeps the checkpoints for adjoint_backward."""
+        p = AdjointParams(int(nsteps), int(checkpoint_every))
+        nbytes = pic_adjoint_bytes(self.ctx, p)
+        self._adj = self.torch.empty(nbytes, dtype=self.torch.uint8, device=self.device)
+        self._adj_n = self._prof_n
+        out = self.torch.empty((6, self.shape3[0], self.shape3[2]), dtype=self.dtype, device=self.device)
+        pic_adjoint_forward(self.ctx, p, self._adj.data_ptr(), nbytes, out.data_ptr())
+        return out
+
+    def adjoint_backward(self, cot):
+        """Gradient of sum(cot * (E^N, B^N)) (cot shaped like adjoint_forward's
+        output) with respect to the profile coefficients, a0 and the waist:
+        a list [dL/dc_1, ..., dL/dc_M, dL/da0, dL/dw0]."""
+        cot = self.torch.as_tensor(cot, dtype=self.dtype, device=self.device).contiguous()
+        return pic_adjoint_backward(self.ctx, cot.data_ptr(), self._adj_n + 2)
+
+
+class StageGradient:
+    """torch.autograd.Function over one boosted stage: inputs the profile
+    coefficients (M,), a0 and w0 (0-d tensors); output E^N, B^N (6, nz+1, nx).
+    The forward builds the run from the fixed settings given to apply(); the
+    backward runs the library's adjoint."""
+
+    @staticmethod
+    def _function():
+        import torch
+
+        class _F(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, coef, a0, w0, settings):
+                sim = Simulation(**settings["grid"])
+                p = settings["plasma"]
+                sim.load_plasma(p["ne"], p["z_start"], p["z_end"], p.get("ramp", 0.0), p.get("ppc", (2, 1, 2)),
+                                p.get("jitter", 0.1), [float(v) for v in coef.detach().cpu()], p.get("ions", 1))
+                l = settings["laser"]
+                sim.launch_laser(float(a0), l["waist"] if w0 is None else float(w0), l["fwhm"],
+                                 l.get("z_antenna", 0.0), l.get("t_peak", -1.0), l.get("pol", PIC_POL_Y))
+                out = sim.adjoint_forward(settings["nsteps"], settings.get("checkpoint_every", 50))
+                ctx.sim = sim
+                ctx.m = coef.numel()
+                return out.clone()
+
+            @staticmethod
+            def backward(ctx, grad_out):
+                g = ctx.sim.adjoint_backward(grad_out)
+                m = ctx.m
+                dc = torch.tensor(g[:m], dtype=torch.float64)
+                return dc, torch.tensor(g[m], dtype=torch.float64), torch.tensor(g[m + 1], dtype=torch.float64), None
+
+        return _F
+
+    @classmethod
+    def apply(cls, coef, a0, w0, settings):
+        return cls._function().apply(coef, a0, w0, settings)
 
 
 class Batch:

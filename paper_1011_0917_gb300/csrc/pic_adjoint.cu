@@ -1,0 +1,682 @@
+// pic_adjoint.cu -- reverse mode (adjoint) of the 2D3V CIC step.
+//
+// The step is differentiated as the composition it is (section "Effect of the
+// hyperbolic rotation in Minkowski space" sets up the boosted-frame run; the
+// reverse mode is this library's own extension):
+//   gather  E_p = G(E^n, B^n; x^n)          Boris  du^{n+1/2} = R(du^{n-1/2}, E_p, B_p)
+//   move    x^{n+1} = x^n + dt v(du^{n+1/2}) deposit J = D(x^n, x^{n+1}, w, v_y)
+//   antenna J += A(t; a0, w0)                filter J_f = F J
+//   Yee     (E, B)^{n+1} = Y(E^n, B^n, J_f) (with Mur's condition on the z ends)
+//   inject  new particles at fixed positions with weights w(c_m).
+// Every map is transposed by hand: Y and F are linear (F is symmetric), the
+// particle maps are differentiated along each trajectory.  Particles live in
+// a fixed-order ("flat") store during an adjoint run, so that slot p is the
+// same particle at every step; the forward states of a segment of K steps are
+// recomputed from a checkpoint and kept while the segment is reversed.
+//
+// Units and layout are those of the forward path: positions as cell index
+// plus an offset in [0, 1) of the working precision, momenta relative to the
+// plasma drift, fields (nz+1) x nx per component (y absent).  Cotangents of
+// positions are per cell (d/d offset).  CIC only: every shape weight is
+// (1 - d, d) on two nodes, with derivative (-1, +1).
+#include "pic_internal.cuh"
+
+namespace pic {
+
+namespace {
+
+constexpr double kTwoPiD = 6.283185307179586;
+
+unsigned adj_grid(int64_t n, int block)
+{
+    int64_t b = (n + block - 1) / block;
+    const int64_t cap = 152LL * 32;
+    return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+// field value at node (i, k) of a component (x periodic; z periodic or zero
+// outside the component's valid range)
+template <typename real>
+__device__ __forceinline__ real fval(const Geom &g, const real *F, int i, int k, bool half_z)
+{
+    i = wrap1(i, g.nx);
+    if (g.bc_z == 0) k = wrapi(k, g.nz);
+    else if (k < 0 || k > zmax_of(g, half_z)) return real(0);
+    return F[(int64_t)k * g.nx + i];
+}
+
+// atomically add v at node (i, k) (dropped outside the valid z range)
+template <typename real>
+__device__ __forceinline__ void fadd(const Geom &g, real *F, int i, int k, bool half_z, real v)
+{
+    i = wrap1(i, g.nx);
+    if (g.bc_z == 0) k = wrapi(k, g.nz);
+    else if (k < 0 || k > zmax_of(g, half_z)) return;
+    atomicAdd(F + (int64_t)k * g.nx + i, v);
+}
+
+// CIC weights and their first node for one staggered axis: integer nodes
+// (half = false) or half-integer nodes (half = true, node index i for i + 1/2)
+template <typename real>
+__device__ __forceinline__ int axis_weights(real o, bool half, real w[2])
+{
+    return half ? half_weights<1>(o, w) : offset_weights<1>(o, w);
+}
+
+// the staggering of the six E, B components in 2D: x half?, z half?
+__device__ __forceinline__ bool hx_of(int c) { return c == 0 || c == 4 || c == 5; }
+__device__ __forceinline__ bool hz_of(int c) { return c == 2 || c == 3 || c == 4; }
+
+// The Boris rotation of boris() (same expressions, same rounding) with the
+// intermediate values its transpose needs
+template <typename real>
+struct BorisFwd {
+    real dm[3], um[3], igm, fb, t[3], s2, s[3], up[3], u[3];
+    __device__ __forceinline__ BorisFwd(const real du[3], real U, const real e[3], const real b[3], real eps)
+    {
+        dm[0] = du[0] + eps * e[0];
+        dm[1] = du[1] + eps * e[1];
+        dm[2] = du[2] + eps * e[2];
+        um[0] = dm[0];
+        um[1] = dm[1];
+        um[2] = U + dm[2];
+        igm = rsqrt_p(real(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+        fb = eps * igm;
+        t[0] = fb * b[0];
+        t[1] = fb * b[1];
+        t[2] = fb * b[2];
+        const real t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+        s2 = div_p(real(2), real(1) + t2);
+        s[0] = s2 * t[0];
+        s[1] = s2 * t[1];
+        s[2] = s2 * t[2];
+        up[0] = um[0] + (um[1] * t[2] - um[2] * t[1]);
+        up[1] = um[1] + (um[2] * t[0] - um[0] * t[2]);
+        up[2] = um[2] + (um[0] * t[1] - um[1] * t[0]);
+        u[0] = dm[0] + (up[1] * s[2] - up[2] * s[1]) + eps * e[0];
+        u[1] = dm[1] + (up[2] * s[0] - up[0] * s[2]) + eps * e[1];
+        u[2] = dm[2] + (up[0] * s[1] - up[1] * s[0]) + eps * e[2];
+    }
+};
+
+// gathered E (0..2) and B (3..5) at a particle, with the weights and first
+// nodes of every component (kept for the transpose)
+template <typename real>
+struct GatherFwd {
+    real wx[6][2], wz[6][2], f[6];
+    int bx[6], bz[6];
+    template <typename Args>
+    __device__ __forceinline__ GatherFwd(const Args &a, int ci, int ck, real ox, real oz)
+    {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            bx[c] = ci + axis_weights(ox, hx_of(c), wx[c]);
+            bz[c] = ck + axis_weights(oz, hz_of(c), wz[c]);
+            const real *F = c < 3 ? a.E[c] : a.B[c - 3];
+            real sum = 0;
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+                real r = 0;
+#pragma unroll
+                for (int q = 0; q < 2; ++q) r += wx[c][q] * fval(a.g, F, bx[c] + q, bz[c] + cc, hz_of(c));
+                sum += wz[c][cc] * r;
+            }
+            f[c] = sum;
+        }
+    }
+};
+
+}  // namespace
+
+// ------------------------------------------------------------ flat forward
+
+// One step of the electrons of the flat store: gather E^n, B^n at x^n, Boris,
+// move, Esirkepov deposit with global atomics, re-cell; state `in` -> `out`.
+template <typename real>
+__global__ void adj_push_kernel(AdjArgs<real> a)
+{
+    const Geom &g = a.g;
+    const Drift<real> drift(a.u_drift, a.dtdh[1]);
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
+        if (!a.in.alive[p]) {
+            a.out.alive[p] = 0;
+            continue;
+        }
+        const int ci = a.in.ci[p], ck = a.in.ck[p];
+        const real ox = a.in.ox[p], oz = a.in.oz[p], w = a.w[p];
+        const real du[3] = {a.in.ux[p], a.in.uy[p], a.in.uz[p]};
+        const GatherFwd<real> gf(a, ci, ck, ox, oz);
+        const BorisFwd<real> bf(du, drift.U, gf.f, gf.f + 3, a.eps);
+        const real ux = bf.u[0], uy = bf.u[1], uz = bf.u[2];
+        real vx, vy;
+        const real dvz = drift_velocity(drift, ux, uy, uz, vx, vy);
+        const real x1 = ox + vx * a.dtdh[0];
+        const real z1 = add_rn(oz, drift.dz) + dvz * a.dtdh[1];
+        // Esirkepov (2D3V): windows of 3 nodes per axis
+        real S0x[3], DSx[3], S0z[3], DSz[3];
+        bool cr;
+        const int ax = ci + esirk_axis_c<1>(ox, x1, S0x, DSx, cr);
+        const int az = ck + esirk_axis_c<1>(oz, z1, S0z, DSz, cr);
+        const real fx = a.jfac[0] * w, fz = a.jfac[2] * w, fyv = a.jyfac * w * vy;
+        real Rx = 0, Rz[3];
+        {
+            real acc = 0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) { acc += DSz[c]; Rz[c] = acc; }
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            Rx += DSx[q];
+            const real xa = S0x[q] + real(0.5) * DSx[q];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const real za = S0z[c] + real(0.5) * DSz[c], zb = real(0.5) * S0z[c] + real(1) / real(3) * DSz[c];
+                if (q < 2) fadd(g, a.J[0], ax + q, az + c, false, fx * Rx * za);
+                fadd(g, a.J[1], ax + q, az + c, false, fyv * (S0x[q] * za + DSx[q] * zb));
+                if (c < 2) fadd(g, a.J[2], ax + q, az + c, true, fz * Rz[c] * xa);
+            }
+        }
+        // new cell (an offset that rounds to 1 moves on)
+        int sx = (int)floor(x1), sz = (int)floor(z1);
+        real nox = x1 - real(sx), noz = z1 - real(sz);
+        if (nox >= real(1)) { sx += 1; nox = 0; }
+        if (noz >= real(1)) { sz += 1; noz = 0; }
+        int ni = wrapi(ci + sx, g.nx), nk = ck + sz;
+        bool alive = true;
+        if (g.bc_z == 0) nk = wrapi(nk, g.nz);
+        else if (nk < 0 || nk >= g.nz) alive = false;
+        a.out.alive[p] = alive ? 1 : 0;
+        a.out.ci[p] = ni;
+        a.out.ck[p] = nk;
+        a.out.ox[p] = nox;
+        a.out.oz[p] = noz;
+        a.out.ux[p] = ux;
+        a.out.uy[p] = uy;
+        a.out.uz[p] = uz;
+    }
+}
+
+// One step of the drifting ions of the flat store: z move by the drift's
+// displacement and the z-only deposit.
+template <typename real>
+__global__ void adj_ion_kernel(AdjArgs<real> a)
+{
+    const Geom &g = a.g;
+    const Drift<real> drift(a.u_drift, a.dtdh[1]);
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
+        if (!a.iin.alive[p]) {
+            a.iout.alive[p] = 0;
+            continue;
+        }
+        const int ci = a.ion_ci[p], ck = a.iin.ck[p];
+        const real ox = a.ion_ox[p], oz = a.iin.oz[p];
+        const real z1 = add_rn(oz, drift.dz);
+        real S0z[3], DSz[3], wx[2];
+        bool cr;
+        const int az = ck + esirk_axis_c<1>(oz, z1, S0z, DSz, cr);
+        offset_weights<1>(ox, wx);
+        const real fz = a.jfac_iz * a.w[p];
+        real acc = 0;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            acc += DSz[c];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) fadd(g, a.J[2], ci + q, az + c, true, fz * acc * wx[q]);
+        }
+        int sz = 0;
+        real noz = z1;
+        if (z1 < real(0)) {
+            noz = z1 + real(1);
+            sz = -1;
+            if (noz >= real(1)) { noz = 0; sz = 0; }
+        }
+        int nk = ck + sz;
+        bool alive = true;
+        if (nk < 0) {
+            if (g.bc_z == 0) nk += g.nz;
+            else alive = false;
+        }
+        a.iout.alive[p] = alive ? 1 : 0;
+        a.iout.ck[p] = nk;
+        a.iout.oz[p] = noz;
+    }
+}
+
+// ------------------------------------------------------------- reverse
+
+// Cotangents of one electron step.  Reads the state at n (x^n, du^{n-1/2}),
+// E^n, B^n, the filtered-and-transposed current cotangent lJ, and the
+// particle's cotangents of x^{n+1}, du^{n+1/2} (lx, lz, lu*); writes those of
+// x^n, du^{n-1/2} in their place, adds the gather's field cotangents to lE,
+// lB and the weight's cotangent to lw.
+template <typename real>
+__global__ void adj_push_vjp_kernel(AdjArgs<real> a)
+{
+    const Geom &g = a.g;
+    const Drift<real> drift(a.u_drift, a.dtdh[1]);
+    const real half = real(0.5), third = real(1) / real(3);
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
+        if (!a.in.alive[p]) continue;
+        const int ci = a.in.ci[p], ck = a.in.ck[p];
+        const real ox = a.in.ox[p], oz = a.in.oz[p], w = a.w[p];
+        const real dux0 = a.in.ux[p], duy0 = a.in.uy[p], duz0 = a.in.uz[p];
+        // ---- recompute the forward values of this step
+        const real du0[3] = {dux0, duy0, duz0};
+        const GatherFwd<real> gf(a, ci, ck, ox, oz);
+        const BorisFwd<real> bf(du0, drift.U, gf.f, gf.f + 3, a.eps);
+        const real eps = a.eps, U = drift.U;
+        const real ux = bf.u[0], uy = bf.u[1], uz = bf.u[2];
+        real vx, vy;
+        const real dvz = drift_velocity(drift, ux, uy, uz, vx, vy);
+        const real x1 = ox + vx * a.dtdh[0];
+        const real z1 = add_rn(oz, drift.dz) + dvz * a.dtdh[1];
+        // Esirkepov windows and their shape derivatives
+        real S0x[3], DSx[3], S0z[3], DSz[3];
+        bool cr;
+        real w0x[2], w1x[2], w0z[2], w1z[2];
+        const int b0x = offset_weights<1>(ox, w0x), b1x = spline_weights<1>(x1, w1x);
+        const int b0z = offset_weights<1>(oz, w0z), b1z = spline_weights<1>(z1, w1z);
+        const int anx = esirk_axis_c<1>(ox, x1, S0x, DSx, cr);
+        const int anz = esirk_axis_c<1>(oz, z1, S0z, DSz, cr);
+        const int ax = ci + anx, az = ck + anz;
+        // ---- deposit transposed: dL/dS0, dL/dS1 per window node, dL/dw, dL/dvy
+        real lJx[3][3], lJy[3][3], lJz[3][3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                lJx[q][c] = fval(g, (const real *)a.J[0], ax + q, az + c, false);
+                lJy[q][c] = fval(g, (const real *)a.J[1], ax + q, az + c, false);
+                lJz[q][c] = fval(g, (const real *)a.J[2], ax + q, az + c, true);
+            }
+        const real fx = a.jfac[0] * w, fz = a.jfac[2] * w, fy1 = a.jyfac * vy;  // Jy factor over w
+        real Rx[3], Rz[3];
+        {
+            real acc = 0;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) { acc += DSx[q]; Rx[q] = acc; }
+            acc = 0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) { acc += DSz[c]; Rz[c] = acc; }
+        }
+        real gS0x[3] = {0, 0, 0}, gDSx[3] = {0, 0, 0}, gS0z[3] = {0, 0, 0}, gDSz[3] = {0, 0, 0};
+        real gRx[3] = {0, 0, 0}, gRz[3] = {0, 0, 0};
+        real Lw = 0, Ly = 0;
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const real za = S0z[c] + half * DSz[c], zb = half * S0z[c] + third * DSz[c];
+                const real xa = S0x[q] + half * DSx[q];
+                if (q < 2) {
+                    // Jx(q, c) = fx Rx[q] za[c]
+                    const real l = lJx[q][c];
+                    gRx[q] += fx * za * l;
+                    gS0z[c] += fx * Rx[q] * l;
+                    gDSz[c] += half * fx * Rx[q] * l;
+                    Lw += a.jfac[0] * Rx[q] * za * l;
+                }
+                {
+                    // Jy(q, c) = fy1 w (S0x za + DSx zb)
+                    const real l = lJy[q][c];
+                    const real shape = S0x[q] * za + DSx[q] * zb;
+                    Ly += shape * l;
+                    const real k = fy1 * w * l;
+                    gS0x[q] += k * za;
+                    gDSx[q] += k * zb;
+                    gS0z[c] += k * (S0x[q] + half * DSx[q]);
+                    gDSz[c] += k * (half * S0x[q] + third * DSx[q]);
+                }
+                if (c < 2) {
+                    // Jz(q, c) = fz Rz[c] xa[q]
+                    const real l = lJz[q][c];
+                    gRz[c] += fz * xa * l;
+                    gS0x[q] += fz * Rz[c] * l;
+                    gDSx[q] += half * fz * Rz[c] * l;
+                    Lw += a.jfac[2] * Rz[c] * xa * l;
+                }
+            }
+        Lw += fy1 * Ly;
+        // running sums: R[q] = sum_{q' <= q} DS[q']
+        {
+            real acc = 0;
+#pragma unroll
+            for (int q = 2; q >= 0; --q) { acc += gRx[q]; gDSx[q] += acc; }
+            acc = 0;
+#pragma unroll
+            for (int c = 2; c >= 0; --c) { acc += gRz[c]; gDSz[c] += acc; }
+        }
+        // DS = S1 - S0 on the window: dL/dS1 = gDS, dL/dS0 = gS0 - gDS; map the
+        // window nodes back to the two support nodes of x0 and x1
+        real lx1 = 0, lz1 = 0, lx0 = 0, lz0 = 0;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            // x0's support nodes b0x, b0x + 1 relative to the cell; x1's b1x, b1x + 1
+            const int r0 = (ci + b0x) - ax, r1 = (ci + b1x) - ax;
+            const real d0 = (q == r0) ? real(-1) : (q == r0 + 1 ? real(1) : real(0));
+            const real d1 = (q == r1) ? real(-1) : (q == r1 + 1 ? real(1) : real(0));
+            lx0 += (gS0x[q] - gDSx[q]) * d0;
+            lx1 += gDSx[q] * d1;
+            const int s0 = (ck + b0z) - az, s1 = (ck + b1z) - az;
+            const real e0 = (q == s0) ? real(-1) : (q == s0 + 1 ? real(1) : real(0));
+            const real e1 = (q == s1) ? real(-1) : (q == s1 + 1 ? real(1) : real(0));
+            lz0 += (gS0z[q] - gDSz[q]) * e0;
+            lz1 += gDSz[q] * e1;
+        }
+        // ---- move transposed: x1 = ox + vx dtdh_x, z1 = oz + dz_d + dvz dtdh_z
+        lx1 += a.lx[p];
+        lz1 += a.lz[p];
+        const real lvx = a.dtdh[0] * lx1, lvz = a.dtdh[1] * lz1;
+        const real lvy = a.jyfac * w * Ly;
+        // velocity transposed: v = u / gamma (u the full momentum), d v / d du
+        // = (I - v v^T) / gamma; (I - v v^T) l = l / gamma^2 + v x (l x v)
+        // (no cancellation when v is nearly along z)
+        const real vz = U * drift.ig + dvz;  // full velocity (drift + departure)
+        const real ig = rsqrt_p(drift.g2 + (uz * (real(2) * U + uz) + ux * ux + uy * uy));
+        const real ig2 = ig * ig;
+        const real cx = lvy * vz - lvz * vy, cy = lvz * vx - lvx * vz, cz = lvx * vy - lvy * vx;  // l x v
+        real lux = a.lux[p] + ig * (lvx * ig2 + (vy * cz - vz * cy));
+        real luy = a.luy[p] + ig * (lvy * ig2 + (vz * cx - vx * cz));
+        real luz = a.luz[p] + ig * (lvz * ig2 + (vx * cy - vy * cx));
+        // ---- Boris transposed
+        const real sx = bf.s[0], sy = bf.s[1], sz = bf.s[2], tx = bf.t[0], ty = bf.t[1], tz = bf.t[2];
+        const real upx = bf.up[0], upy = bf.up[1], upz = bf.up[2];
+        const real umx = bf.um[0], umy = bf.um[1], umz = bf.um[2];
+        const real s2 = bf.s2, sden = real(0.5) * bf.s2, fb = bf.fb, igm = bf.igm;
+        real lE[3] = {eps * lux, eps * luy, eps * luz};  // the last half kick
+        real ldmx = lux, ldmy = luy, ldmz = luz;
+        // u += up x s: lup = s x lu, ls = lu x up
+        const real lupx = sy * luz - sz * luy, lupy = sz * lux - sx * luz, lupz = sx * luy - sy * lux;
+        const real lsx = luy * upz - luz * upy, lsy = luz * upx - lux * upz, lsz = lux * upy - luy * upx;
+        // up = um + um x t: lum += lup + t x lup, lt = lup x um
+        real lumx = lupx + (ty * lupz - tz * lupy);
+        real lumy = lupy + (tz * lupx - tx * lupz);
+        real lumz = lupz + (tx * lupy - ty * lupx);
+        real ltx = lupy * umz - lupz * umy, lty = lupz * umx - lupx * umz, ltz = lupx * umy - lupy * umx;
+        // s = s2 t, s2 = 2 / (1 + t^2): d s / d t = s2 I - 4 t t^T / (1 + t^2)^2
+        const real tl = tx * lsx + ty * lsy + tz * lsz;
+        ltx += s2 * lsx - real(2) * s2 * sden * tx * tl;
+        lty += s2 * lsy - real(2) * s2 * sden * ty * tl;
+        ltz += s2 * lsz - real(2) * s2 * sden * tz * tl;
+        // t = fb B, fb = eps / gamma_m
+        real lB[3] = {fb * ltx, fb * lty, fb * ltz};
+        const real lfb = gf.f[3] * ltx + gf.f[4] * lty + gf.f[5] * ltz;
+        const real kf = -lfb * fb * igm * igm;  // d fb / d um = -fb um / gamma_m^2
+        lumx += kf * umx;
+        lumy += kf * umy;
+        lumz += kf * umz;
+        ldmx += lumx;
+        ldmy += lumy;
+        ldmz += lumz;
+        lE[0] += eps * ldmx;
+        lE[1] += eps * ldmy;
+        lE[2] += eps * ldmz;
+        // ---- gather transposed: scatter lE, lB; position cotangents
+        const real lf[6] = {lE[0], lE[1], lE[2], lB[0], lB[1], lB[2]};
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const real *F = c < 3 ? a.E[c] : a.B[c - 3];
+            real *LF = c < 3 ? a.lE[c] : a.lB[c - 3];
+            const real l = lf[c];
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc)
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const real v = fval(g, F, gf.bx[c] + q, gf.bz[c] + cc, hz_of(c));
+                    lx0 += l * (q ? real(1) : real(-1)) * gf.wz[c][cc] * v;
+                    lz0 += l * gf.wx[c][q] * (cc ? real(1) : real(-1)) * v;
+                    fadd(g, LF, gf.bx[c] + q, gf.bz[c] + cc, hz_of(c), l * gf.wx[c][q] * gf.wz[c][cc]);
+                }
+        }
+        // ---- write the cotangents of x^n, du^{n-1/2}; the weight's
+        a.lx[p] = lx1 + lx0;
+        a.lz[p] = lz1 + lz0;
+        a.lux[p] = ldmx;
+        a.luy[p] = ldmy;
+        a.luz[p] = ldmz;
+        a.lw[p] += (double)Lw;
+    }
+}
+
+// Weight cotangents of the drifting ions of one step (their positions do not
+// depend on the parameters).
+template <typename real>
+__global__ void adj_ion_vjp_kernel(AdjArgs<real> a)
+{
+    const Geom &g = a.g;
+    const Drift<real> drift(a.u_drift, a.dtdh[1]);
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
+        if (!a.iin.alive[p]) continue;
+        const int ci = a.ion_ci[p], ck = a.iin.ck[p];
+        const real ox = a.ion_ox[p], oz = a.iin.oz[p];
+        const real z1 = add_rn(oz, drift.dz);
+        real S0z[3], DSz[3], wx[2];
+        bool cr;
+        const int az = ck + esirk_axis_c<1>(oz, z1, S0z, DSz, cr);
+        offset_weights<1>(ox, wx);
+        real acc = 0, L = 0;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            acc += DSz[c];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) L += acc * wx[q] * fval(g, (const real *)a.J[2], ci + q, az + c, true);
+        }
+        a.lw[p] += (double)(a.jfac_iz * L);
+    }
+}
+
+// lE += (transpose of B -= h curl E) applied to lB (2D): the gather form of
+// the scatter of every B update onto the E nodes it read.
+template <typename real>
+__global__ void adj_curl_e_t_kernel(Geom g, real *lEx, real *lEy, real *lEz, const real *lBx, const real *lBy,
+                                    const real *lBz, real hz_, real hx_)
+{
+    const bool per = g.bc_z == 0;
+    const int nk = per ? g.nz : g.nz + 1;
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < (int64_t)nk * g.nx;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(o % g.nx), k = (int)(o / g.nx);
+        const int im = i == 0 ? g.nx - 1 : i - 1;
+        // B components at half-integer z (Bx, By) exist for k' in [0, nz); Bz on
+        // the E planes
+        auto bh = [&](const real *B, int ii, int kk) -> real {
+            if (per) kk = wrapi(kk, g.nz);
+            else if (kk < 0 || kk >= g.nz) return real(0);
+            return B[(int64_t)kk * g.nx + ii];
+        };
+        auto bi = [&](const real *B, int ii, int kk) -> real {
+            return B[(int64_t)kk * g.nx + ii];
+        };
+        // Ex(i+1/2, k): By(i+1/2, k+1/2) -= h (Ex[k+1] - Ex[k]) / hz
+        lEx[o] += hz_ * (bh(lBy, i, k) - bh(lBy, i, k - 1));
+        // Ey(i, k): Bx(i, k+1/2) += h (Ey[k+1] - Ey[k]) / hz; Bz(i+1/2, k) -= h (Ey[i+1] - Ey[i]) / hx
+        lEy[o] += hz_ * (bh(lBx, i, k - 1) - bh(lBx, i, k)) + hx_ * (bi(lBz, i, k) - bi(lBz, im, k));
+        // Ez(i, k+1/2): By(i+1/2, k+1/2) += h (Ez[i+1] - Ez[i]) / hx
+        if (k < g.nz) lEz[o] += hx_ * (bi(lBy, im, k) - bi(lBy, i, k));
+    }
+}
+
+// The E update transposed (2D).  From lE1 (cotangent of E^{n+1} after the
+// B half step has been transposed) it forms the cotangent of the interior
+// update's output (Mur's condition transposed first: the boundary values were
+// computed from E^n and the new interior values next to them), the current
+// cotangent lJ = -2 pi dt lE1' and the cotangent of E^n, lE0.
+template <typename real>
+__global__ void adj_e_update_t_kernel(Geom g, const real *lE1x, const real *lE1y, const real *lE1z, real *pEx,
+                                      real *pEy, real *pEz, real *lE0x, real *lE0y, real *lE0z, real *lJx,
+                                      real *lJy, real *lJz, real cm, real m2pidt)
+{
+    const bool per = g.bc_z == 0;
+    const int nk = g.nz + 1;
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < (int64_t)nk * g.nx;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(o % g.nx), k = (int)(o / g.nx);
+        const int64_t top = (int64_t)g.nz * g.nx + i;
+        // Ex, Ey
+        for (int c = 0; c < 2; ++c) {
+            const real *L1 = c == 0 ? lE1x : lE1y;
+            real *P = c == 0 ? pEx : pEy;
+            real *L0 = c == 0 ? lE0x : lE0y;
+            real *LJ = c == 0 ? lJx : lJy;
+            real vp = 0, v0 = 0;
+            if (per) {
+                if (k < g.nz) vp = v0 = L1[o];
+            } else if (k >= 1 && k <= g.nz - 1) {
+                vp = L1[o];
+                v0 = L1[o];
+                if (k == 1) { vp += cm * L1[i]; v0 += cm * L1[i] + L1[i]; }
+                if (k == g.nz - 1) { vp += cm * L1[top]; v0 += cm * L1[top] + L1[top]; }
+            } else {
+                v0 = -cm * L1[o];  // k = 0 or nz: E^n of the boundary node itself
+            }
+            P[o] = vp;
+            L0[o] = v0;
+            LJ[o] = m2pidt * vp;
+        }
+        // Ez (k < nz), no boundary condition
+        const real vz = k < g.nz ? lE1z[o] : real(0);
+        pEz[o] = vz;
+        lE0z[o] = vz;
+        lJz[o] = m2pidt * vz;
+    }
+}
+
+// lB += dt (curl B)^T applied to lE' (2D): the gather form of the scatter of
+// the E interior updates onto the B nodes they read.
+template <typename real>
+__global__ void adj_curl_b_t_kernel(Geom g, const real *pEx, const real *pEy, const real *pEz, real *lBx,
+                                    real *lBy, real *lBz, real dthz, real dthx)
+{
+    const bool per = g.bc_z == 0;
+    const int nk = g.nz + 1;
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < (int64_t)nk * g.nx;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(o % g.nx), k = (int)(o / g.nx);
+        const int ip = i + 1 == g.nx ? 0 : i + 1;
+        auto pe = [&](const real *P, int ii, int kk) -> real {  // E' on the integer-z planes
+            if (per) kk = wrapi(kk, g.nz);
+            else if (kk < 0 || kk > g.nz) return real(0);
+            return P[(int64_t)kk * g.nx + ii];
+        };
+        if (k < g.nz) {
+            // By(i+1/2, k+1/2): Ex[k] -= dt (By[k] - By[k-1]) / hz; Ez[i] += dt (By[i] - By[i-1]) / hx
+            lBy[o] += dthz * (pe(pEx, i, k + 1) - pe(pEx, i, k)) + dthx * (pEz[o] - pEz[(int64_t)k * g.nx + ip]);
+            // Bx(i, k+1/2): Ey[k] += dt (Bx[k] - Bx[k-1]) / hz
+            lBx[o] += dthz * (pe(pEy, i, k) - pe(pEy, i, k + 1));
+        }
+        if (k < g.nz || !per) {
+            // Bz(i+1/2, k): Ey[i] -= dt (Bz[i] - Bz[i-1]) / hx
+            lBz[o] += dthx * (pEy[(int64_t)k * g.nx + ip] - pEy[o]);
+        }
+    }
+}
+
+// Sums over the antenna plane: s[0] += j0u sum lJ g, s[1] += j0w sum lJ g r^2
+// (g = exp(-r^2 / w0^2) as in the forward), for the a0 and w0 cotangents.
+template <typename real>
+__global__ void adj_antenna_kernel(Geom g, const real *lJ, int pol, int ka, double hx, double xc, double inv_w2,
+                                   double fa, double fw, double *s)
+{
+    double s0 = 0, s1 = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.nx; i += gridDim.x * blockDim.x) {
+        const double x = ((double)i + (pol == 0 ? 0.5 : 0.0)) * hx - xc;
+        const double r2 = x * x;
+        const double gg = exp(-r2 * inv_w2);
+        const double l = (double)lJ[(int64_t)ka * g.nx + i];
+        s0 += l * gg;
+        s1 += l * gg * r2;
+    }
+    atomicAdd(s, fa * s0);
+    atomicAdd(s + 1, fw * s1);
+}
+
+// dL/dc_m = sum_p lw_p w_p cos(m pi zeta_p) / (1 + sum_m' c_m' cos(m' pi zeta_p))
+__global__ void adj_profile_kernel(int64_t n, const double *lw, const void *w, int precision, const double *zeta,
+                                   int M, const double *coef, double *out)
+{
+    double acc[16];
+    for (int m = 0; m < 16; ++m) acc[m] = 0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        if (lw[p] == 0.0) continue;  // never alive, or no current
+        const double wp = precision ? ((const double *)w)[p] : (double)((const float *)w)[p];
+        const double l = lw[p] * wp;
+        double f = 1.0;
+        for (int m = 1; m <= M; ++m) f += coef[m - 1] * cos((double)m * 3.141592653589793 * zeta[p]);
+        for (int m = 1; m <= M; ++m) acc[m - 1] += l * cos((double)m * 3.141592653589793 * zeta[p]) / f;
+    }
+    for (int m = 0; m < M; ++m) atomicAdd(out + m, acc[m]);
+}
+
+// --------------------------------------------------------------- launchers
+
+template <typename real>
+void launch_adj_push(const AdjArgs<real> &a, cudaStream_t s)
+{
+    if (a.n > 0) adj_push_kernel<real><<<adj_grid(a.n, 256), 256, 0, s>>>(a);
+}
+template <typename real>
+void launch_adj_ions(const AdjArgs<real> &a, cudaStream_t s)
+{
+    if (a.n > 0) adj_ion_kernel<real><<<adj_grid(a.n, 256), 256, 0, s>>>(a);
+}
+template <typename real>
+void launch_adj_push_vjp(const AdjArgs<real> &a, cudaStream_t s)
+{
+    if (a.n > 0) adj_push_vjp_kernel<real><<<adj_grid(a.n, 256), 256, 0, s>>>(a);
+}
+template <typename real>
+void launch_adj_ion_vjp(const AdjArgs<real> &a, cudaStream_t s)
+{
+    if (a.n > 0) adj_ion_vjp_kernel<real><<<adj_grid(a.n, 256), 256, 0, s>>>(a);
+}
+
+// the Yee step transposed: (lE, lB) at n+1 -> (lE, lB) at n and lJ (the
+// cotangent of the filtered current); lE0 and pE are work components
+template <typename real>
+void launch_adj_yee(const Geom &g, real *lE[3], real *lB[3], real *lE0[3], real *pE[3], real *lJ[3], double dt,
+                    double hx, double hz, cudaStream_t s)
+{
+    const unsigned grid = adj_grid((int64_t)(g.nz + 1) * g.nx, 256);
+    const real h = (real)(0.5 * dt);
+    // B^{n+1} = B' - h curl E^{n+1}
+    adj_curl_e_t_kernel<real><<<grid, 256, 0, s>>>(g, lE[0], lE[1], lE[2], lB[0], lB[1], lB[2], (real)(h / hz),
+                                                  (real)(h / hx));
+    // E^{n+1} = E^n + dt (curl B' - 2 pi J), Mur on the z ends
+    adj_e_update_t_kernel<real><<<grid, 256, 0, s>>>(g, lE[0], lE[1], lE[2], pE[0], pE[1], pE[2], lE0[0], lE0[1],
+                                                    lE0[2], lJ[0], lJ[1], lJ[2], (real)((dt - hz) / (dt + hz)),
+                                                    (real)(-kTwoPiD * dt));
+    adj_curl_b_t_kernel<real><<<grid, 256, 0, s>>>(g, pE[0], pE[1], pE[2], lB[0], lB[1], lB[2], (real)(dt / hz),
+                                                  (real)(dt / hx));
+    // B' = B^n - h curl E^n
+    adj_curl_e_t_kernel<real><<<grid, 256, 0, s>>>(g, lE0[0], lE0[1], lE0[2], lB[0], lB[1], lB[2], (real)(h / hz),
+                                                  (real)(h / hx));
+}
+
+template <typename real>
+void launch_adj_antenna(const Geom &g, const real *lJ, int pol, int ka, double hx, double xc, double waist,
+                        double fa, double fw, double *s, cudaStream_t st)
+{
+    adj_antenna_kernel<real><<<adj_grid(g.nx, 256), 256, 0, st>>>(g, lJ, pol, ka, hx, xc, 1.0 / (waist * waist), fa,
+                                                                   fw, s);
+}
+
+void launch_adj_profile(int64_t n, const double *lw, const void *w, int precision, const double *zeta, int M,
+                        const double *coef, double *out, cudaStream_t s)
+{
+    if (n > 0 && M > 0) adj_profile_kernel<<<adj_grid(n, 256), 256, 0, s>>>(n, lw, w, precision, zeta, M, coef, out);
+}
+
+#define PIC_ADJ_INSTANTIATE(real)                                                                              \
+    template void launch_adj_push<real>(const AdjArgs<real> &, cudaStream_t);                                  \
+    template void launch_adj_ions<real>(const AdjArgs<real> &, cudaStream_t);                                  \
+    template void launch_adj_push_vjp<real>(const AdjArgs<real> &, cudaStream_t);                              \
+    template void launch_adj_ion_vjp<real>(const AdjArgs<real> &, cudaStream_t);                               \
+    template void launch_adj_yee<real>(const Geom &, real *[3], real *[3], real *[3], real *[3], real *[3],     \
+                                       double, double, double, cudaStream_t);                                  \
+    template void launch_adj_antenna<real>(const Geom &, const real *, int, int, double, double, double, double, \
+                                           double, double *, cudaStream_t);
+PIC_ADJ_INSTANTIATE(float)
+PIC_ADJ_INSTANTIATE(double)
+#undef PIC_ADJ_INSTANTIATE
+
+}  // namespace pic

@@ -108,6 +108,19 @@ struct pic_ctx {
     int64_t step = 0;
     std::string err;
 
+    // adjoint run: the flat store's bands (slot base and lattice planes of
+    // the load and of every step's injection), the step times, the caller's
+    // buffer holding the checkpoints between the forward and reverse calls
+    struct {
+        bool ready = false;
+        int N = 0, K = 0;
+        int64_t P = 0;
+        std::vector<int64_t> base, mlo, mhi;
+        std::vector<double> tn;
+        unsigned char *buf = nullptr;
+        size_t bytes = 0;
+    } adj;
+
     // profiling: event pairs recorded around phases, summed on read
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -423,6 +436,7 @@ static void fill_inject_common(pic_ctx *c, InjectArgs &a)
         a.hi_i = nullptr;
     }
     a.err = reinterpret_cast<unsigned *>(c->scratch + c->off_err);
+    a.flat_base = -1;  // into the tile buckets
 }
 
 // lattice planes whose lab z may fall in [zlo, zhi) after jitter
@@ -811,6 +825,22 @@ static int fill_btd(pic_ctx *c, real *const F0[9], real *const F1[6])
     return 1;
 }
 
+// The antenna's sheet current amplitude in the step starting at t: the lab
+// laser seen by an antenna at rest in the boosted frame, amplitude and time
+// argument scaled by D = gamma (1 - beta); J = -E_target / (pi hz).
+static double antenna_j0(const pic_ctx *c, double t, double a0)
+{
+    const pic_laser_params &l = c->laser;
+    const double D = 1.0 / (c->gam * (1.0 + c->beta));
+    const double tau = l.fwhm / std::sqrt(2.0 * std::log(2.0));
+    const double spk = l.t_peak >= 0.0 ? l.t_peak : 3.0 * tau;
+    const double th = t + 0.5 * c->dt;
+    const double sr = D * th - spk;
+    const double env = std::exp(-(sr / tau) * (sr / tau));
+    const double amp = a0 * D * env * std::sin(kTwoPi * sr);
+    return -amp / (kPi * c->hz);
+}
+
 template <typename real>
 static void run_phases_t(pic_ctx *c, unsigned mask)
 {
@@ -866,17 +896,8 @@ static void run_phases_t(pic_ctx *c, unsigned mask)
     const int64_t ka_rel = (int64_t)c->ka - c->win_n * c->win_S;
     if ((mask & PIC_PH_ANTENNA) && c->laser_on && ka_rel >= 2) {
         PhaseTimer pt(c, 3);
-        // the lab laser seen by an antenna at rest in the boosted frame:
-        // amplitude and time argument scaled by D = gamma (1 - beta)
         const pic_laser_params &l = c->laser;
-        const double D = 1.0 / (c->gam * (1.0 + c->beta));
-        const double tau = l.fwhm / std::sqrt(2.0 * std::log(2.0));
-        const double spk = l.t_peak >= 0.0 ? l.t_peak : 3.0 * tau;
-        const double th = c->t + 0.5 * c->dt;
-        const double sr = D * th - spk;
-        const double env = std::exp(-(sr / tau) * (sr / tau));
-        const double amp = l.a0 * D * env * std::sin(kTwoPi * sr);
-        const double j0 = -amp / (kPi * c->hz);
+        const double j0 = antenna_j0(c, c->t, l.a0);
         const int comp = l.polarization == PIC_POL_X ? 0 : 1;
         launch_antenna<real>(c->g, R[comp], l.polarization, (int)ka_rel, j0, c->hx, c->hy, l.x_center, l.y_center,
                              l.waist, c->stream);
@@ -1520,6 +1541,418 @@ extern "C" pic_status pic_profile_read(pic_ctx *c, double ms[8], int64_t calls[8
     if (kernels) *kernels = c->kernels;
     c->kernels = 0;
     return PIC_OK;
+}
+
+
+// ------------------------------------------------------------------ adjoint
+
+namespace {
+
+// byte layout of an adjoint run's buffer
+struct AdjLayout {
+    int64_t P = 0;
+    int N = 0, K = 0, C = 0;
+    size_t w = 0, zeta = 0, ion_ci = 0, ion_ox = 0;  // per slot, constant
+    size_t st = 0, fl = 0;                           // one particle state, one field state (6 comps)
+    size_t ckpt = 0, seg = 0;                        // C and K + 1 (state, fields) pairs
+    size_t J = 0, tmp = 0, lE = 0, lB = 0, lE0 = 0, pE = 0, lJ = 0;  // 3 components each
+    size_t lx = 0, lz = 0, lux = 0, luy = 0, luz = 0, lw = 0, acc = 0, coef = 0;
+    size_t total = 0;
+    // inside one particle state
+    size_t e_ci = 0, e_ck = 0, e_ox = 0, e_oz = 0, e_ux = 0, e_uy = 0, e_uz = 0, e_alive = 0;
+    size_t i_ck = 0, i_oz = 0, i_alive = 0;
+};
+
+AdjLayout adj_layout(int64_t P, int N, int K, size_t es, int64_t ncomp)
+{
+    AdjLayout L;
+    L.P = P;
+    L.N = N;
+    L.K = K;
+    L.C = (N + K - 1) / K;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o += align_up(bytes);
+        return at;
+    };
+    // one particle state
+    size_t q = 0;
+    auto sub = [&](size_t bytes) {
+        const size_t at = q;
+        q += align_up(bytes);
+        return at;
+    };
+    L.e_ci = sub(4 * P);
+    L.e_ck = sub(4 * P);
+    L.e_ox = sub(es * P);
+    L.e_oz = sub(es * P);
+    L.e_ux = sub(es * P);
+    L.e_uy = sub(es * P);
+    L.e_uz = sub(es * P);
+    L.e_alive = sub(P);
+    L.i_ck = sub(4 * P);
+    L.i_oz = sub(es * P);
+    L.i_alive = sub(P);
+    L.st = q;
+    L.fl = align_up(6 * es * ncomp);
+    L.w = take(es * P);
+    L.zeta = take(8 * P);
+    L.ion_ci = take(4 * P);
+    L.ion_ox = take(es * P);
+    L.ckpt = take((size_t)L.C * (L.st + L.fl));
+    L.seg = take((size_t)(K + 1) * (L.st + L.fl));
+    L.J = take(3 * es * ncomp);
+    L.tmp = take(3 * es * ncomp);
+    L.lE = take(3 * es * ncomp);
+    L.lB = take(3 * es * ncomp);
+    L.lE0 = take(3 * es * ncomp);
+    L.pE = take(3 * es * ncomp);
+    L.lJ = take(3 * es * ncomp);
+    L.lx = take(es * P);
+    L.lz = take(es * P);
+    L.lux = take(es * P);
+    L.luy = take(es * P);
+    L.luz = take(es * P);
+    L.lw = take(8 * P);
+    L.acc = take(8 * 2);
+    L.coef = take(8 * 32);
+    L.total = o;
+    return L;
+}
+
+template <typename real>
+FlatE<real> flat_e(unsigned char *st, const AdjLayout &L)
+{
+    FlatE<real> e;
+    e.ci = (int *)(st + L.e_ci);
+    e.ck = (int *)(st + L.e_ck);
+    e.ox = (real *)(st + L.e_ox);
+    e.oz = (real *)(st + L.e_oz);
+    e.ux = (real *)(st + L.e_ux);
+    e.uy = (real *)(st + L.e_uy);
+    e.uz = (real *)(st + L.e_uz);
+    e.alive = st + L.e_alive;
+    return e;
+}
+
+template <typename real>
+FlatI<real> flat_i(unsigned char *st, const AdjLayout &L)
+{
+    FlatI<real> i;
+    i.ck = (int *)(st + L.i_ck);
+    i.oz = (real *)(st + L.i_oz);
+    i.alive = st + L.i_alive;
+    return i;
+}
+
+}  // namespace
+
+// lattice bands of the load and of every step's injection, their slot bases,
+// and the step times (accumulated as the step does)
+static void adj_bands(pic_ctx *c, int N)
+{
+    auto &A = c->adj;
+    A.tn.assign(N + 1, 0.0);
+    A.tn[0] = c->t;
+    for (int n = 0; n < N; ++n) A.tn[n + 1] = A.tn[n] + c->dt;
+    InjectArgs a{};
+    fill_inject_common(c, a);
+    A.mlo.assign(N + 1, 0);
+    A.mhi.assign(N + 1, 0);
+    A.base.assign(N + 2, 0);
+    lattice_band(a, c->gam * (c->beta * A.tn[0]), c->gam * (c->Lz + c->beta * A.tn[0]), A.mlo[0], A.mhi[0]);
+    if (c->gam > 1.0)
+        for (int n = 0; n < N; ++n)
+            lattice_band(a, c->gam * (c->Lz + c->beta * A.tn[n]), c->gam * (c->Lz + c->beta * A.tn[n + 1]),
+                         A.mlo[n + 1], A.mhi[n + 1]);
+    for (int b = 0; b <= N; ++b) A.base[b + 1] = A.base[b] + (A.mhi[b] - A.mlo[b]) * a.NY * a.NX;
+    A.P = A.base[N + 1];
+}
+
+static pic_status adj_check(pic_ctx *c, const pic_adjoint_params *p)
+{
+    if (!c || !p) return PIC_ERR_ARG;
+    if (!c->bound) return fail(c, PIC_ERR_STATE, "bind buffers first");
+    if (p->nsteps < 1 || p->checkpoint_every < 1) return fail(c, PIC_ERR_ARG, "invalid adjoint parameters");
+    if (c->g.dim != 2 || c->p.shape_order != 1)
+        return fail(c, PIC_ERR_ARG, "the adjoint covers 2D3V runs with the CIC shape");
+    if (c->win_on) return fail(c, PIC_ERR_ARG, "the adjoint does not cover a moving window");
+    if (!c->plasma_loaded || c->step != 0)
+        return fail(c, PIC_ERR_STATE, "the adjoint starts right after pic_load_plasma (no step taken)");
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_adjoint_bytes(pic_ctx *c, const pic_adjoint_params *p, size_t *bytes)
+{
+    pic_status st = adj_check(c, p);
+    if (st != PIC_OK) return st;
+    if (!bytes) return PIC_ERR_ARG;
+    adj_bands(c, p->nsteps);
+    *bytes = adj_layout(c->adj.P, p->nsteps, p->checkpoint_every, (size_t)c->es, c->g.ncomp).total;
+    return PIC_OK;
+}
+
+// one flat step n: state/fields slot a -> slot b
+template <typename real>
+static void adj_step(pic_ctx *c, const AdjLayout &L, unsigned char *sa, unsigned char *sb, unsigned char *fa,
+                     unsigned char *fb, int n)
+{
+    unsigned char *B = c->adj.buf;
+    const int64_t nc = c->g.ncomp;
+    real *J = (real *)(B + L.J);
+    cudaMemsetAsync(J, 0, 3 * sizeof(real) * nc, c->stream);
+    AdjArgs<real> a{};
+    a.g = c->g;
+    for (int q = 0; q < 3; ++q) {
+        a.E[q] = (const real *)fa + q * nc;
+        a.B[q] = (const real *)fa + (3 + q) * nc;
+        a.J[q] = J + q * nc;
+    }
+    a.in = flat_e<real>(sa, L);
+    a.out = flat_e<real>(sb, L);
+    a.iin = flat_i<real>(sa, L);
+    a.iout = flat_i<real>(sb, L);
+    a.w = (const real *)(B + L.w);
+    a.ion_ci = (const int *)(B + L.ion_ci);
+    a.ion_ox = (const real *)(B + L.ion_ox);
+    a.n = L.P;
+    a.dtdh[0] = (real)(c->dt / c->hx);
+    a.dtdh[1] = (real)(c->dt / c->hz);
+    a.eps = (real)(kPi * -1.0 * c->dt);
+    a.u_drift = drift_u<real>(c);
+    a.jfac[0] = (real)(1.0 * c->hx / (c->dt * c->vol));
+    a.jfac[1] = (real)(1.0 * c->hy / (c->dt * c->vol));
+    a.jfac[2] = (real)(1.0 * c->hz / (c->dt * c->vol));
+    a.jyfac = (real)(-1.0 / c->vol);
+    a.jfac_iz = (real)(-1.0 * c->hz / (c->dt * c->vol));
+    launch_adj_push<real>(a, c->stream);
+    if (c->ions_species) launch_adj_ions<real>(a, c->stream);
+    real *Jc[3] = {J, J + nc, J + 2 * nc};
+    if (c->laser_on && c->ka >= 2) {
+        const pic_laser_params &l = c->laser;
+        const double j0 = antenna_j0(c, c->adj.tn[n], l.a0);
+        launch_antenna<real>(c->g, Jc[l.polarization == PIC_POL_X ? 0 : 1], l.polarization, c->ka, j0, c->hx, c->hy,
+                             l.x_center, l.y_center, l.waist, c->stream);
+    }
+    launch_filter<real>(c->g, Jc, (real *)(B + L.tmp), c->p.filter_passes, c->stream);
+    real *F[9], *F1[6];
+    for (int q = 0; q < 6; ++q) {
+        F[q] = (real *)fa + q * nc;
+        F1[q] = (real *)fb + q * nc;
+    }
+    for (int q = 0; q < 3; ++q) F[6 + q] = Jc[q];
+    launch_yee<real>(c->g, F, F1, c->dt, c->hx, c->hy, c->hz, c->stream);
+    if (c->gam > 1.0 && c->adj.mhi[n + 1] > c->adj.mlo[n + 1]) {
+        InjectArgs ia{};
+        fill_inject_common(c, ia);
+        ia.mode = 1;
+        ia.t = c->adj.tn[n];
+        ia.t1 = c->adj.tn[n + 1];
+        ia.m_lo = c->adj.mlo[n + 1];
+        ia.m_hi = c->adj.mhi[n + 1];
+        ia.flat_base = c->adj.base[n + 1];
+        FlatE<real> e = flat_e<real>(sb, L);
+        FlatI<real> i = flat_i<real>(sb, L);
+        ia.fe_ci = e.ci;
+        ia.fe_ck = e.ck;
+        ia.fe_ox = e.ox;
+        ia.fe_oz = e.oz;
+        ia.fe_ux = e.ux;
+        ia.fe_uy = e.uy;
+        ia.fe_uz = e.uz;
+        ia.fe_alive = e.alive;
+        ia.fi_ck = i.ck;
+        ia.fi_oz = i.oz;
+        ia.fi_alive = i.alive;
+        ia.f_ion_ci = (int *)(B + L.ion_ci);
+        ia.f_ion_ox = B + L.ion_ox;
+        ia.f_w = B + L.w;
+        ia.f_zeta = (double *)(B + L.zeta);
+        launch_inject(ia, c->stream);
+    }
+}
+
+template <typename real>
+static pic_status adj_forward_t(pic_ctx *c, const pic_adjoint_params *p, void *fields_out)
+{
+    auto &A = c->adj;
+    const AdjLayout L = adj_layout(A.P, p->nsteps, p->checkpoint_every, sizeof(real), c->g.ncomp);
+    unsigned char *B = A.buf;
+    unsigned char *seg = B + L.seg;
+    auto st = [&](int s) { return seg + (size_t)s * (L.st + L.fl); };
+    auto fl = [&](int s) { return seg + (size_t)s * (L.st + L.fl) + L.st; };
+    auto ck_st = [&](int q) { return B + L.ckpt + (size_t)q * (L.st + L.fl); };
+    const size_t fbytes = 6 * sizeof(real) * c->g.ncomp;
+    // state 0: the plasma as loaded (into its fixed slots), the current fields;
+    // slots no lattice point takes keep zero weights
+    CUDA_TRY(c, cudaMemsetAsync(B + L.w, 0, L.ckpt - L.w, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(st(0), 0, L.st, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(st(1), 0, L.st, c->stream));
+    for (int q = 0; q < 6; ++q)
+        CUDA_TRY(c, cudaMemcpyAsync(fl(0) + q * sizeof(real) * c->g.ncomp, field_ptr(c, q),
+                                    sizeof(real) * c->g.ncomp, cudaMemcpyDeviceToDevice, c->stream));
+    {
+        InjectArgs ia{};
+        fill_inject_common(c, ia);
+        ia.mode = 0;
+        ia.t = A.tn[0];
+        ia.t1 = A.tn[0];
+        ia.m_lo = A.mlo[0];
+        ia.m_hi = A.mhi[0];
+        ia.flat_base = 0;
+        FlatE<real> e = flat_e<real>(st(0), L);
+        FlatI<real> i = flat_i<real>(st(0), L);
+        ia.fe_ci = e.ci;
+        ia.fe_ck = e.ck;
+        ia.fe_ox = e.ox;
+        ia.fe_oz = e.oz;
+        ia.fe_ux = e.ux;
+        ia.fe_uy = e.uy;
+        ia.fe_uz = e.uz;
+        ia.fe_alive = e.alive;
+        ia.fi_ck = i.ck;
+        ia.fi_oz = i.oz;
+        ia.fi_alive = i.alive;
+        ia.f_ion_ci = (int *)(B + L.ion_ci);
+        ia.f_ion_ox = B + L.ion_ox;
+        ia.f_w = B + L.w;
+        ia.f_zeta = (double *)(B + L.zeta);
+        launch_inject(ia, c->stream);
+    }
+    for (int n = 0; n < L.N; ++n) {
+        const int a = n & 1, b = a ^ 1;
+        if (n % L.K == 0)
+            CUDA_TRY(c, cudaMemcpyAsync(ck_st(n / L.K), st(a), L.st + L.fl, cudaMemcpyDeviceToDevice, c->stream));
+        adj_step<real>(c, L, st(a), st(b), fl(a), fl(b), n);
+    }
+    CUDA_TRY(c, cudaGetLastError());
+    if (fields_out)
+        CUDA_TRY(c, cudaMemcpyAsync(fields_out, fl(L.N & 1), fbytes, cudaMemcpyDeviceToDevice, c->stream));
+    A.ready = true;
+    A.N = L.N;
+    A.K = L.K;
+    return check_device_error(c);
+}
+
+extern "C" pic_status pic_adjoint_forward(pic_ctx *c, const pic_adjoint_params *p, void *buf, size_t bytes,
+                                          void *fields_out)
+{
+    pic_status s = adj_check(c, p);
+    if (s != PIC_OK) return s;
+    if (!buf) return PIC_ERR_ARG;
+    adj_bands(c, p->nsteps);
+    if (bytes < adj_layout(c->adj.P, p->nsteps, p->checkpoint_every, (size_t)c->es, c->g.ncomp).total)
+        return fail(c, PIC_ERR_ARG, "adjoint buffer too small");
+    c->adj.buf = (unsigned char *)buf;
+    c->adj.bytes = bytes;
+    c->adj.ready = false;
+    return c->es == 4 ? adj_forward_t<float>(c, p, fields_out) : adj_forward_t<double>(c, p, fields_out);
+}
+
+template <typename real>
+static pic_status adj_backward_t(pic_ctx *c, const void *cot, double *grad)
+{
+    auto &A = c->adj;
+    const AdjLayout L = adj_layout(A.P, A.N, A.K, sizeof(real), c->g.ncomp);
+    unsigned char *B = A.buf;
+    const int64_t nc = c->g.ncomp;
+    unsigned char *seg = B + L.seg;
+    auto st = [&](int s) { return seg + (size_t)s * (L.st + L.fl); };
+    auto fl = [&](int s) { return seg + (size_t)s * (L.st + L.fl) + L.st; };
+    auto ck_st = [&](int q) { return B + L.ckpt + (size_t)q * (L.st + L.fl); };
+    real *lE[3], *lB[3], *lE0[3], *pE[3], *lJ[3];
+    for (int q = 0; q < 3; ++q) {
+        lE[q] = (real *)(B + L.lE) + q * nc;
+        lB[q] = (real *)(B + L.lB) + q * nc;
+        lE0[q] = (real *)(B + L.lE0) + q * nc;
+        pE[q] = (real *)(B + L.pE) + q * nc;
+        lJ[q] = (real *)(B + L.lJ) + q * nc;
+    }
+    const size_t cb = 3 * sizeof(real) * nc;
+    CUDA_TRY(c, cudaMemcpyAsync(lE[0], cot, cb, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(lB[0], (const unsigned char *)cot + cb, cb, cudaMemcpyDeviceToDevice, c->stream));
+    for (size_t off : {L.lx, L.lz, L.lux, L.luy, L.luz})
+        CUDA_TRY(c, cudaMemsetAsync(B + off, 0, sizeof(real) * L.P, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(B + L.lw, 0, 8 * L.P, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(B + L.acc, 0, 16, c->stream));
+    const pic_laser_params &l = c->laser;
+    const int comp = l.polarization == PIC_POL_X ? 0 : 1;
+    for (int sgi = L.C - 1; sgi >= 0; --sgi) {
+        const int n0 = sgi * L.K, n1 = std::min(L.N, n0 + L.K);
+        CUDA_TRY(c, cudaMemcpyAsync(st(0), ck_st(sgi), L.st + L.fl, cudaMemcpyDeviceToDevice, c->stream));
+        for (int s = 0; s < n1 - n0; ++s) adj_step<real>(c, L, st(s), st(s + 1), fl(s), fl(s + 1), n0 + s);
+        for (int s = n1 - n0 - 1; s >= 0; --s) {
+            const int n = n0 + s;
+            launch_adj_yee<real>(c->g, lE, lB, lE0, pE, lJ, c->dt, c->hx, c->hz, c->stream);
+            for (int q = 0; q < 3; ++q) std::swap(lE[q], lE0[q]);
+            launch_filter<real>(c->g, lJ, (real *)(B + L.tmp), c->p.filter_passes, c->stream);
+            if (c->laser_on && c->ka >= 2) {
+                const double j0 = antenna_j0(c, A.tn[n], l.a0);
+                // j0 is linear in a0; the profile exp(-r^2/w0^2) gives 2 r^2 / w0^3
+                const double ja = antenna_j0(c, A.tn[n], 1.0);
+                launch_adj_antenna<real>(c->g, lJ[comp], l.polarization, c->ka, c->hx, l.x_center, l.waist, ja,
+                                         j0 * 2.0 / (l.waist * l.waist * l.waist), (double *)(B + L.acc), c->stream);
+            }
+            AdjArgs<real> a{};
+            a.g = c->g;
+            for (int q = 0; q < 3; ++q) {
+                a.E[q] = (const real *)fl(s) + q * nc;
+                a.B[q] = (const real *)fl(s) + (3 + q) * nc;
+                a.J[q] = lJ[q];
+                a.lE[q] = lE[q];
+                a.lB[q] = lB[q];
+            }
+            a.in = flat_e<real>(st(s), L);
+            a.iin = flat_i<real>(st(s), L);
+            a.w = (const real *)(B + L.w);
+            a.ion_ci = (const int *)(B + L.ion_ci);
+            a.ion_ox = (const real *)(B + L.ion_ox);
+            a.n = L.P;
+            a.dtdh[0] = (real)(c->dt / c->hx);
+            a.dtdh[1] = (real)(c->dt / c->hz);
+            a.eps = (real)(kPi * -1.0 * c->dt);
+            a.u_drift = drift_u<real>(c);
+            a.jfac[0] = (real)(1.0 * c->hx / (c->dt * c->vol));
+            a.jfac[1] = (real)(1.0 * c->hy / (c->dt * c->vol));
+            a.jfac[2] = (real)(1.0 * c->hz / (c->dt * c->vol));
+            a.jyfac = (real)(-1.0 / c->vol);
+            a.jfac_iz = (real)(-1.0 * c->hz / (c->dt * c->vol));
+            a.lx = (real *)(B + L.lx);
+            a.lz = (real *)(B + L.lz);
+            a.lux = (real *)(B + L.lux);
+            a.luy = (real *)(B + L.luy);
+            a.luz = (real *)(B + L.luz);
+            a.lw = (double *)(B + L.lw);
+            if (c->ions_species) launch_adj_ion_vjp<real>(a, c->stream);
+            launch_adj_push_vjp<real>(a, c->stream);
+        }
+    }
+    // the profile coefficients enter through every weight
+    const int M = c->plasma.n_profile;
+    std::vector<double> h(2 + 16 + 16, 0.0);
+    if (M > 0) {
+        CUDA_TRY(c, cudaMemcpyAsync(B + L.coef, c->prof, 8 * 16, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(c, cudaMemsetAsync(B + L.coef + 8 * 16, 0, 8 * 16, c->stream));
+        launch_adj_profile(L.P, (const double *)(B + L.lw), B + L.w, sizeof(real) == 8 ? 1 : 0,
+                           (const double *)(B + L.zeta), M, (const double *)(B + L.coef),
+                           (double *)(B + L.coef + 8 * 16), c->stream);
+        CUDA_TRY(c, cudaMemcpyAsync(h.data() + 2, B + L.coef + 8 * 16, 8 * M, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(h.data(), B + L.acc, 16, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    CUDA_TRY(c, cudaGetLastError());
+    for (int m = 0; m < M; ++m) grad[m] = h[2 + m];
+    grad[M] = h[0];
+    grad[M + 1] = h[1];
+    return check_device_error(c);
+}
+
+extern "C" pic_status pic_adjoint_backward(pic_ctx *c, const void *cot, double *grad)
+{
+    if (!c || !cot || !grad) return PIC_ERR_ARG;
+    if (!c->adj.ready) return fail(c, PIC_ERR_STATE, "run pic_adjoint_forward first");
+    return c->es == 4 ? adj_backward_t<float>(c, cot, grad) : adj_backward_t<double>(c, cot, grad);
 }
 
 // ---------------------------------------------------------------------- misc

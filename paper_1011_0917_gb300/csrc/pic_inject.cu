@@ -93,6 +93,7 @@ __global__ void inject_kernel(InjectArgs a)
         int ci = 0, cj = 0, ck = 0;
         real ox = 0, oy = 0, oz = 0, wr = 0;
         int64_t L = 0;
+        double zeta = 0.0;
         if (q < total) {
             const int64_t ix = q % a.NX;
             const int64_t r = q / a.NX;
@@ -113,6 +114,7 @@ __global__ void inject_kernel(InjectArgs a)
             }
             const double zlab = a.z_start + ((double)m + 0.5) * a.dzl +
                                 (a.jitter * a.hz_lab) * (2.0 * uniform01(a.seed, c0 + 2ull) - 1.0);
+            zeta = (zlab - a.z_start) / (a.z_end - a.z_start);
             const double n = lab_density(a, zlab);
             if (n > 0.0) {
                 bool take;
@@ -134,6 +136,30 @@ __global__ void inject_kernel(InjectArgs a)
                     dest = tile_of(a.g, ci, cj, ck);
                 }
             }
+        }
+        if (a.flat_base >= 0) {  // the fixed-order store of an adjoint run (2D)
+            if (q < total) {
+                const int64_t sl = a.flat_base + q;
+                const bool in = dest >= 0;
+                a.fe_alive[sl] = in ? 1 : 0;
+                a.fi_alive[sl] = (in && a.drift_ions) ? 1 : 0;
+                if (in) {
+                    a.fe_ci[sl] = ci;
+                    a.fe_ck[sl] = ck;
+                    static_cast<real *>(a.fe_ox)[sl] = ox;
+                    static_cast<real *>(a.fe_oz)[sl] = oz;
+                    static_cast<real *>(a.fe_ux)[sl] = real(0);
+                    static_cast<real *>(a.fe_uy)[sl] = real(0);
+                    static_cast<real *>(a.fe_uz)[sl] = real(0);
+                    a.fi_ck[sl] = ck;
+                    static_cast<real *>(a.fi_oz)[sl] = oz;
+                    a.f_ion_ci[sl] = ci;
+                    static_cast<real *>(a.f_ion_ox)[sl] = ox;
+                    static_cast<real *>(a.f_w)[sl] = wr;
+                    a.f_zeta[sl] = zeta;
+                }
+            }
+            continue;
         }
         // appended to the top run of the destination bucket
         const int re = reserve_slot(a.hi_e, dest);

@@ -186,6 +186,35 @@ __device__ __forceinline__ int half_weights(real o, real w[S + 1])
     return spline_weights<S>(o - real(0.5), w);
 }
 
+// Esirkepov window along one axis: old offset x0 in [0,1), new position x1 =
+// x0 + d (|d| < 1), both relative to the old cell.  Returns the first node of
+// a window of S+2 nodes that holds both supports, with S0 and DS = S1 - S0 on
+// it, and whether the support moved to another first node.
+template <int S, typename real>
+__device__ __forceinline__ int esirk_axis_c(real x0, real x1, real S0[S + 2], real DS[S + 2], bool &crossed)
+{
+    real w0[S + 1], w1[S + 1];
+    const int b0 = offset_weights<S>(x0, w0);  // x0: the in-cell offset at the start
+    const int b1 = spline_weights<S>(x1, w1);
+    const int anchor = b0 < b1 ? b0 : b1;
+    const bool s0 = b0 != anchor, s1 = b1 != anchor;
+    crossed = b0 != b1;
+#pragma unroll
+    for (int q = 0; q < S + 2; ++q) {
+        const real v0 = s0 ? (q >= 1 ? w0[q - 1 < S ? q - 1 : S] : real(0)) : (q <= S ? w0[q <= S ? q : S] : real(0));
+        const real v1 = s1 ? (q >= 1 ? w1[q - 1 < S ? q - 1 : S] : real(0)) : (q <= S ? w1[q <= S ? q : S] : real(0));
+        S0[q] = v0;
+        DS[q] = v1 - v0;
+    }
+    return anchor;
+}
+
+// periodic index for i in [-n, 2n)
+__device__ __forceinline__ int wrap1(int i, int n)
+{
+    return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+
 // ----------------------------------------------------------------- Boris
 
 // reciprocals used by the push: IEEE in FP64 (the debug path).  In FP32 the
@@ -372,6 +401,52 @@ struct InjectArgs {      // lattice load / boosted injection, FP64
     void *sp_i[9];      // same for the ion side (ux..uz unused)
     int *hi_e, *hi_i;    // top-run lengths of the electron / ion sides
     unsigned *err;
+    // fixed-order ("flat") output of an adjoint run (flat_base >= 0, 2D):
+    // lattice point q of the band goes to slot flat_base + q, alive or not
+    int64_t flat_base;
+    int *fe_ci, *fe_ck;          // electron state
+    void *fe_ox, *fe_oz, *fe_ux, *fe_uy, *fe_uz;
+    unsigned char *fe_alive;
+    int *fi_ck;                  // ion state
+    void *fi_oz;
+    unsigned char *fi_alive;
+    int *f_ion_ci;               // per slot, constant: the ion's x cell and offset,
+    void *f_ion_ox, *f_w;        // the weight (shared by the pair)
+    double *f_zeta;              // and the lab profile coordinate
+};
+
+// One state of the flat particle store of an adjoint run (2D, slot p is the
+// same particle at every step)
+template <typename real>
+struct FlatE {
+    int *ci, *ck;
+    real *ox, *oz, *ux, *uy, *uz;   // offsets; momenta relative to the drift
+    unsigned char *alive;
+};
+template <typename real>
+struct FlatI {
+    int *ck;
+    real *oz;
+    unsigned char *alive;
+};
+
+template <typename real>
+struct AdjArgs {
+    Geom g;
+    const real *E[3], *B[3];        // E^n, B^n
+    real *J[3];                     // forward: current; reverse: its cotangent
+    FlatE<real> in, out;            // electron states n and n+1
+    FlatI<real> iin, iout;          // ion states n and n+1
+    const real *w;                  // weights per slot
+    const int *ion_ci;              // ion x cell / offset per slot
+    const real *ion_ox;
+    int64_t n;                      // slots
+    real dtdh[2];                   // dt / hx, dt / hz
+    real eps, u_drift;
+    real jfac[3], jyfac, jfac_iz;
+    real *lE[3], *lB[3];            // reverse: field cotangents at n
+    real *lx, *lz, *lux, *luy, *luz;  // reverse: particle cotangents
+    double *lw;                     // reverse: weight cotangents per slot
 };
 
 // host launchers (defined in the .cu files)
@@ -413,5 +488,18 @@ void launch_antenna(const Geom &g, real *J, int pol, int ka, double j0, double h
 template <typename real>
 void launch_field_sums(const Geom &g, real *const F[9], double *partials, int nblocks,
                        cudaStream_t s);
+// adjoint (2D CIC): flat forward steps and their transposes
+template <typename real> void launch_adj_push(const AdjArgs<real> &a, cudaStream_t s);
+template <typename real> void launch_adj_ions(const AdjArgs<real> &a, cudaStream_t s);
+template <typename real> void launch_adj_push_vjp(const AdjArgs<real> &a, cudaStream_t s);
+template <typename real> void launch_adj_ion_vjp(const AdjArgs<real> &a, cudaStream_t s);
+template <typename real>
+void launch_adj_yee(const Geom &g, real *lE[3], real *lB[3], real *lE0[3], real *pE[3], real *lJ[3], double dt,
+                    double hx, double hz, cudaStream_t s);
+template <typename real>
+void launch_adj_antenna(const Geom &g, const real *lJ, int pol, int ka, double hx, double xc, double waist,
+                        double fa, double fw, double *s, cudaStream_t st);
+void launch_adj_profile(int64_t n, const double *lw, const void *w, int precision, const double *zeta, int M,
+                        const double *coef, double *out, cudaStream_t s);
 
 }  // namespace pic

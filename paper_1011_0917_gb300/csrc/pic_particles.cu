@@ -62,11 +62,6 @@ __device__ __forceinline__ void sh_acc(double *p, double a, double b, double)
     if (v != 0.0) atomicAdd(p, v);
 }
 
-// periodic index for i in [-n, 2n)
-__device__ __forceinline__ int wrap1(int i, int n)
-{
-    return i < 0 ? i + n : (i >= n ? i - n : i);
-}
 
 template <typename real>
 struct Ptr6 {
@@ -215,29 +210,6 @@ __device__ __forceinline__ real gather_comp(const real *F, int FX, int FY, int i
 }
 
 // --------------------------------------------------------- Esirkepov
-
-// Esirkepov window along one axis: old offset x0 in [0,1), new position x1 =
-// x0 + d (|d| < 1), both relative to the old cell.  Returns the first node of
-// a window of S+2 nodes that holds both supports, with S0 and DS = S1 - S0 on
-// it, and whether the support moved to another first node.
-template <int S, typename real>
-__device__ __forceinline__ int esirk_axis_c(real x0, real x1, real S0[S + 2], real DS[S + 2], bool &crossed)
-{
-    real w0[S + 1], w1[S + 1];
-    const int b0 = offset_weights<S>(x0, w0);  // x0: the in-cell offset at the start
-    const int b1 = spline_weights<S>(x1, w1);
-    const int anchor = b0 < b1 ? b0 : b1;
-    const bool s0 = b0 != anchor, s1 = b1 != anchor;
-    crossed = b0 != b1;
-#pragma unroll
-    for (int q = 0; q < S + 2; ++q) {
-        const real v0 = s0 ? (q >= 1 ? w0[q - 1 < S ? q - 1 : S] : real(0)) : (q <= S ? w0[q <= S ? q : S] : real(0));
-        const real v1 = s1 ? (q >= 1 ? w1[q - 1 < S ? q - 1 : S] : real(0)) : (q <= S ? w1[q <= S ? q : S] : real(0));
-        S0[q] = v0;
-        DS[q] = v1 - v0;
-    }
-    return anchor;
-}
 
 // Current of one particle into the shared J tile.  Along an axis the window
 // has W nodes: S+1 when no lane of the warp moved its support to another first

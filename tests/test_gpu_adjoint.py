@@ -1,0 +1,125 @@
+"""The adjoint (reverse-mode gradient) of a boosted 2D3V run against central
+finite differences of the FP64 oracle.
+
+The objective is linear in the final fields, L = sum(lambda . (E^N, B^N)),
+with lambda on a few nodes behind the laser; its gradient is taken with
+respect to the plasma profile coefficients (through every particle weight),
+the laser's a0 and its waist (through the antenna current).  The oracle knows
+nothing of the adjoint: its objective is evaluated at theta +- h and the
+difference quotient is the reference.  Also checked: the adjoint's own forward
+run (a fixed-order particle store) reproduces the oracle's fields, the
+gradient does not depend on the checkpoint interval, and the FP32 gradient
+agrees with the FP64 one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from pairs import make_pair
+
+pytestmark = pytest.mark.gpu
+
+FP32, FP64 = 0, 1
+GAM = 5.0
+BETA = math.sqrt(1 - 1 / GAM ** 2)
+G = dict(dim=2, nx=16, nz=128, dx=1.0, dz=1 / 16, gamma_boost=GAM, filter_passes=1, seed=61)
+HZ = (1 / 16) * GAM * (1 + BETA)
+PLASMA = dict(ne=0.01, z_start=GAM * 8 * HZ, z_end=GAM * 2000 * HZ, ramp=1.0, ppc=(2, 1, 2), jitter=0.1, ions=1)
+LASER = dict(a0=2.0, waist=5.0, fwhm=2.0, t_peak=0.5, pol=1)
+COEF = (0.1, -0.05)
+NSTEPS = 60
+
+
+@pytest.fixture(scope="module")
+def O():
+    import oracle.oracle as O
+    O.build_oracle()
+    return O
+
+
+def cotangent(nz, nx):
+    lam = np.zeros((6, nz + 1, nx))
+    lam[2, 20:44, nx // 2] = 1.0            # Ez on axis behind the pulse
+    lam[0, 24:40, nx // 2 + 2] = 0.5        # Ex off axis
+    lam[1, 30:34, :] = 0.05                 # Ey across
+    return lam
+
+
+def oracle_objective(O, coef, a0, w0):
+    o = O.Oracle(O.GridParams(dim=2, nx=G["nx"], nz=G["nz"], dx=G["dx"], dz=G["dz"], gamma_boost=GAM,
+                              npass=G["filter_passes"], bc_z=1, seed=G["seed"]))
+    o.load_plasma(O.PlasmaParams(ne=PLASMA["ne"], z_start=PLASMA["z_start"], z_end=PLASMA["z_end"],
+                                 ramp=PLASMA["ramp"], ppc=PLASMA["ppc"], jitter=PLASMA["jitter"],
+                                 profile=tuple(coef), ions=1))
+    o.set_laser(O.LaserParams(a0=a0, waist=w0, fwhm=LASER["fwhm"], z_antenna=0.0, t_peak=LASER["t_peak"], pol=1))
+    o.step(NSTEPS)
+    lam = cotangent(G["nz"], G["nx"])
+    f = np.stack([o.field(c)[:, 0, :] for c in ("Ex", "Ey", "Ez", "Bx", "By", "Bz")])
+    return float(np.sum(lam * f)), f
+
+
+def gpu_run(O, prec, coef=COEF, a0=LASER["a0"], w0=LASER["waist"], K=20):
+    import torch
+    sim, _ = make_pair(O, G, prec)
+    sim.load_plasma(PLASMA["ne"], PLASMA["z_start"], PLASMA["z_end"], PLASMA["ramp"], PLASMA["ppc"],
+                    PLASMA["jitter"], coef, 1)
+    sim.launch_laser(a0, w0, LASER["fwhm"], 0.0, LASER["t_peak"], 1)
+    fields = sim.adjoint_forward(NSTEPS, K)
+    lam = torch.as_tensor(cotangent(G["nz"], G["nx"]), dtype=fields.dtype, device=fields.device)
+    grad = sim.adjoint_backward(lam)
+    return fields.double().cpu().numpy(), grad
+
+
+@pytest.fixture(scope="module")
+def reference(O):
+    """(L, fields) at theta and the central differences of the oracle."""
+    L0, f0 = oracle_objective(O, COEF, LASER["a0"], LASER["waist"])
+    fd = []
+    h = 1e-4
+    for m in range(len(COEF)):
+        cp, cm = list(COEF), list(COEF)
+        cp[m] += h
+        cm[m] -= h
+        fd.append((oracle_objective(O, cp, LASER["a0"], LASER["waist"])[0] -
+                   oracle_objective(O, cm, LASER["a0"], LASER["waist"])[0]) / (2 * h))
+    ha = 1e-4 * LASER["a0"]
+    fd.append((oracle_objective(O, COEF, LASER["a0"] + ha, LASER["waist"])[0] -
+               oracle_objective(O, COEF, LASER["a0"] - ha, LASER["waist"])[0]) / (2 * ha))
+    hw = 1e-4 * LASER["waist"]
+    fd.append((oracle_objective(O, COEF, LASER["a0"], LASER["waist"] + hw)[0] -
+               oracle_objective(O, COEF, LASER["a0"], LASER["waist"] - hw)[0]) / (2 * hw))
+    return L0, f0, np.array(fd)
+
+
+def test_adjoint_forward_matches_oracle(O, reference):
+    # the run the adjoint differentiates is the oracle's run (FP64: 1e-10)
+    _, f0, _ = reference
+    f, _ = gpu_run(O, FP64)
+    for q in range(6):
+        n = np.linalg.norm(f0[q])
+        if n > 1e-3 * np.linalg.norm(f0):
+            assert np.linalg.norm(f[q] - f0[q]) / n < 1e-10, q
+
+
+def test_gradient_matches_oracle_finite_differences(O, reference):
+    _, _, fd = reference
+    _, g = gpu_run(O, FP64)
+    g = np.array(g)
+    assert np.all(np.abs(fd) > 0)
+    rel = np.abs(g - fd) / np.abs(fd)
+    assert np.all(rel < 1e-3), (g, fd, rel)
+
+
+def test_gradient_independent_of_checkpoint_interval(O):
+    _, g1 = gpu_run(O, FP64, K=NSTEPS)
+    _, g2 = gpu_run(O, FP64, K=7)
+    assert np.allclose(g1, g2, rtol=1e-11, atol=0)
+
+
+def test_fp32_gradient_against_fp64(O):
+    _, g64 = gpu_run(O, FP64)
+    _, g32 = gpu_run(O, FP32)
+    g64, g32 = np.array(g64), np.array(g32)
+    rel = np.abs(g32 - g64) / np.abs(g64)
+    assert np.all(rel < 1e-3), (g32, g64, rel)
