@@ -63,6 +63,8 @@ def parse():
                     help="skip the second, shorter timing of the same stage with explicit ion records")
     ap.add_argument("--btd", type=int, default=16,
                     help="lab-frame (x, z)-plane snapshots timed after the main measurement (0: none)")
+    ap.add_argument("--adjoint-steps", type=int, default=400,
+                    help="steps of the adjoint/forward timing on one c4 run (0: skip)")
     ap.add_argument("--c4", type=int, default=64,
                     help="runs of the batched scan timed after the main measurement (0: none)")
     return ap.parse_args()
@@ -313,6 +315,7 @@ def run_ours(args, rank, world, local):
         sim.close()
 
     c4 = run_c4(P, torch, args.c4, args.warmup, max(1, min(args.steps, 10))) if args.c4 > 0 else None
+    adj = run_adjoint(P, torch, args.adjoint_steps, 50) if args.adjoint_steps > 0 else None
 
     result = None
     if rank == 0:
@@ -346,7 +349,8 @@ def run_ours(args, rank, world, local):
             "gpu_launches": int(kernels),
             "clocks": clock_info,
             "cpu_baseline": cpu,
-            "adjoint_forward_ratio": None,
+            "adjoint_forward_ratio": adj["ratio"] if adj else None,
+            "adjoint": adj,
             "explicit_ion_records": explicit,
             "lab_frame_snapshots": btd,
             "batched_c4": c4,
@@ -398,6 +402,60 @@ def run_c4(P, torch, nruns, warmup, steps):
             "speedup_vs_sequential": t_seq / t_batch,
             "note": "2D3V boosted runs, gamma in {5, 13, 30}, nz in [1024, 4096], nx = 128, 2x2 per cell, "
                     "8-coefficient profile, a0 in [0.5, 2]; host wall clock around pic_batch_step"}
+
+
+def run_adjoint(P, torch, steps, K, r=0):
+    """Adjoint/forward time on run r of the c4 scan: the gradient of the
+    on-axis Ez over planes 16..127 after `steps` steps with respect to the
+    8 profile coefficients, a0 and the waist (forward with a checkpoint every K
+    steps, then the reverse sweep recomputing each segment), against the
+    library's forward step over the same steps.  CUDA events on the run's
+    stream."""
+    from paper_1011_0917_gb300 import workloads as W
+    st = W.c4_run(r)
+    g = st.grid
+
+    def make():
+        sim = P.Simulation(dim=2, nx=g["nx"], ny=1, nz=g["nz"], dx=g["dx"], dz=g["dz"], cfl=g["cfl"],
+                           gamma_boost=g["gamma_boost"], filter_passes=g["filter_passes"], precision=P.PIC_FP32,
+                           seed=g["seed"], slots_per_cell=6.0, stream=torch.cuda.Stream())
+        p = st.plasma
+        sim.load_plasma(p["ne"], p["z_start"], p["z_end"], p["ramp"], p["ppc"], p["jitter"], p["profile"], p["ions"])
+        l = st.laser
+        sim.launch_laser(l["a0"], l["waist"], l["fwhm"], 0.0, -1.0, 1)
+        return sim
+
+    def timed(sim, fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(sim.stream)
+        out = fn()
+        e1.record(sim.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    sim = make()
+    n_e = sim.diagnostics().n_particles[0]
+    fwd_ms, _ = timed(sim, lambda: P.pic_step_async(sim.ctx, steps))
+    sim.close()
+    sim = make()
+    with torch.cuda.stream(sim.stream):
+        a_fwd_ms, fields = timed(sim, lambda: sim.adjoint_forward(steps, K))
+        cot = torch.zeros_like(fields)
+        cot[2, 16:128, g["nx"] // 2] = 1.0
+        a_bwd_ms, grad = timed(sim, lambda: sim.adjoint_backward(cot))
+    nbytes = sim._adj.numel()
+    sim.close()
+    del fields, cot
+    torch.cuda.empty_cache()
+    total = a_fwd_ms + a_bwd_ms
+    return {"run": f"c4[{r}]: gamma={g['gamma_boost']:g}, {g['nx']}x{g['nz']} cells, {n_e} electrons, {steps} steps, "
+                   f"checkpoint every {K}",
+            "forward_ms": fwd_ms, "adjoint_forward_ms": a_fwd_ms, "adjoint_reverse_ms": a_bwd_ms,
+            "ratio": total / fwd_ms, "buffer_bytes": int(nbytes),
+            "gradient": {"profile": grad[:-2], "a0": grad[-2], "w0": grad[-1]},
+            "objective": "sum of on-axis Ez over planes 16..127 (behind the antenna, inside the plasma) at the "
+                         "last step"}
 
 
 def make_sim(P, st, slots_per_cell, stream, explicit_ions, advance):
