@@ -275,6 +275,16 @@ pic_status pic_batch_create(pic_ctx *const *ctxs, int n, pic_batch **out);
 pic_status pic_batch_step(pic_batch *batch, int nsteps);
 void pic_batch_destroy(pic_batch *batch);
 
+/* Steps of a batch run as CUDA graphs of steps_per_graph steps of every
+   context (even; default 20; 0: streams only): pic_batch_step captures the
+   steps once per call and replays the graph nsteps / steps_per_graph times
+   (the remainder, and batches with a moving window, lab snapshots, phase
+   timing or a context on the legacy default stream, take the stream path).
+   The per-step values (antenna amplitude, injection band and times) are
+   refilled in pinned host memory before each replay and copied by the
+   graph's first nodes.  PIC_ERR_ARG for a negative or odd count. */
+pic_status pic_batch_set_graph(pic_batch *batch, int steps_per_graph);
+
 /* ---------------------------------------------------------- moving window */
 
 /* Moving window (the paper's gamma = 1 and gamma = 5 runs used "a moving

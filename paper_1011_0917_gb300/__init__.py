@@ -25,7 +25,7 @@ __all__ = [
     "pic_profile_read", "pic_filter_current_noalloc", "PIC_NOALLOC_MAX_NODES", "BtdParams", "pic_btd_bytes",
     "pic_btd_setup", "pic_btd_get", "pic_set_moving_window", "pic_batch_create", "pic_batch_step",
     "pic_batch_destroy", "Simulation", "Batch", "library_path", "AdjointParams", "pic_adjoint_bytes",
-    "pic_adjoint_forward", "pic_adjoint_backward", "StageGradient",
+    "pic_adjoint_forward", "pic_adjoint_backward", "StageGradient", "pic_batch_set_graph",
 ]
 
 PIC_OK, PIC_ERR_ARG, PIC_ERR_STATE, PIC_ERR_CUDA = 0, 1, 2, 3
@@ -139,6 +139,7 @@ def _load():
         "pic_batch_create": (S, [C.POINTER(C.c_void_p), I, C.POINTER(C.c_void_p)]),
         "pic_batch_step": (S, [P, I]),
         "pic_batch_destroy": (None, [P]),
+        "pic_batch_set_graph": (S, [P, I]),
         "pic_btd_bytes": (S, [P, C.POINTER(BtdParams), C.POINTER(C.c_size_t)]),
         "pic_btd_setup": (S, [P, C.POINTER(BtdParams), P, C.c_size_t]),
         "pic_btd_get": (S, [P, I, P, C.c_size_t, I]),
@@ -319,6 +320,12 @@ def pic_batch_step(batch, nsteps: int):
     st = _load().pic_batch_step(batch, nsteps)
     if st != PIC_OK:
         raise PicError(st, _load().pic_status_string(st).decode())
+
+
+def pic_batch_set_graph(batch, steps_per_graph: int):
+    s = _load().pic_batch_set_graph(batch, int(steps_per_graph))
+    if s != PIC_OK:
+        raise PicError(s, "pic_batch_set_graph: " + pic_status_string(s))
 
 
 def pic_batch_destroy(batch):
@@ -547,9 +554,10 @@ class StageGradient:
 class Batch:
     """Steps several Simulations together (each on its own stream)."""
 
-    def __init__(self, sims):
+    def __init__(self, sims, graph_steps=20):
         self.sims = list(sims)
         self.h = pic_batch_create([s.ctx for s in self.sims])
+        pic_batch_set_graph(self.h, graph_steps)
 
     def step(self, nsteps: int = 1):
         pic_batch_step(self.h, nsteps)

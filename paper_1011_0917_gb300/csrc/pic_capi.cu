@@ -121,6 +121,13 @@ struct pic_ctx {
         size_t bytes = 0;
     } adj;
 
+    // CUDA-graph capture of steps (batch): step cap_s of the graph being
+    // captured takes its per-step scalars from cap_scal[cap_s] (device)
+    bool capturing = false;
+    const StepScal *cap_scal = nullptr;
+    int cap_s = 0;
+    int64_t inj_planes_max = 0;  // bound of an injection band (lattice planes)
+
     // profiling: event pairs recorded around phases, summed on read
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -897,10 +904,10 @@ static void run_phases_t(pic_ctx *c, unsigned mask)
     if ((mask & PIC_PH_ANTENNA) && c->laser_on && ka_rel >= 2) {
         PhaseTimer pt(c, 3);
         const pic_laser_params &l = c->laser;
-        const double j0 = antenna_j0(c, c->t, l.a0);
+        const double j0 = c->capturing ? 0.0 : antenna_j0(c, c->t, l.a0);
         const int comp = l.polarization == PIC_POL_X ? 0 : 1;
         launch_antenna<real>(c->g, R[comp], l.polarization, (int)ka_rel, j0, c->hx, c->hy, l.x_center, l.y_center,
-                             l.waist, c->stream);
+                             l.waist, c->stream, c->capturing ? &c->cap_scal[c->cap_s].j0 : nullptr);
         c->kernels += 1;
     }
     if ((mask & PIC_PH_FILTER) && c->p.filter_passes > 0) {
@@ -930,12 +937,19 @@ static void run_phases_t(pic_ctx *c, unsigned mask)
         a.mode = 1;
         a.t = c->t;
         a.t1 = c->t + c->dt;
-        lattice_band(a, c->gam * (c->zwin() + c->Lz + c->beta * a.t), c->gam * (c->zwin() + c->Lz + c->beta * a.t1),
-                     a.m_lo, a.m_hi);
+        if (c->capturing) {
+            // the band comes from the step's scalars; the launch covers the bound
+            a.scal = &c->cap_scal[c->cap_s];
+            a.m_lo = 0;
+            a.m_hi = c->inj_planes_max;
+        } else {
+            lattice_band(a, c->gam * (c->zwin() + c->Lz + c->beta * a.t),
+                         c->gam * (c->zwin() + c->Lz + c->beta * a.t1), a.m_lo, a.m_hi);
+        }
         launch_inject(a, c->stream);
         if (a.m_hi > a.m_lo) c->kernels += 1;
     }
-    if (mask & PIC_PH_TIME) {
+    if ((mask & PIC_PH_TIME) && !c->capturing) {
         c->t += c->dt;
         c->step += 1;
         if (c->win_on && c->t >= c->win_t0 &&
@@ -962,7 +976,144 @@ static pic_status run_steps(pic_ctx *c, int nsteps, unsigned mask, bool check)
 
 struct pic_batch {
     std::vector<pic_ctx *> ctx;
+    int graph_steps = 20;  // steps per captured graph (even; 0: streams only)
 };
+
+// Whether the contexts' steps can be captured: nothing in them depends on the
+// host at run time except the per-step scalars of StepScal (no moving
+// window, no lab snapshots, no phase timing), and every context has a stream
+// of its own (the legacy default stream cannot be captured).
+static bool batch_capturable(const pic_batch *b)
+{
+    for (const pic_ctx *c : b->ctx)
+        if (c->win_on || c->btd_on || c->profiling || c->stream == nullptr) return false;
+    return true;
+}
+
+// Per-step scalars of steps [c->t, c->t + K dt) (times accumulated as the
+// step does) into host memory
+static void fill_step_scalars(pic_ctx *c, int K, StepScal *h)
+{
+    InjectArgs a{};
+    fill_inject_common(c, a);
+    double t = c->t;
+    for (int s = 0; s < K; ++s) {
+        const double t1 = t + c->dt;
+        h[s].j0 = c->laser_on ? antenna_j0(c, t, c->laser.a0) : 0.0;
+        h[s].t = t;
+        h[s].t1 = t1;
+        h[s].m_lo = h[s].m_hi = 0;
+        if (c->plasma_loaded && c->gam > 1.0)
+            lattice_band(a, c->gam * (c->zwin() + c->Lz + c->beta * t), c->gam * (c->zwin() + c->Lz + c->beta * t1),
+                         h[s].m_lo, h[s].m_hi);
+        t = t1;
+    }
+}
+
+// K steps of every context as one CUDA graph, replayed nsteps / K times; the
+// per-step scalars go through pinned host memory copied at the graph's start.
+// Returns the number of steps done (a multiple of K).
+static pic_status batch_graph_steps(pic_batch *b, int nsteps, int &done)
+{
+    done = 0;
+    const int K = b->graph_steps;
+    const int reps = nsteps / K;
+    if (reps < 1) return PIC_OK;
+    const size_t nctx = b->ctx.size();
+    std::vector<StepScal *> host(nctx, nullptr), dev(nctx, nullptr);
+    std::vector<cudaEvent_t> ev(nctx + 1, nullptr);
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    pic_status st = PIC_OK;
+    auto cleanup = [&]() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+        for (size_t i = 0; i < nctx; ++i) {
+            if (host[i]) cudaFreeHost(host[i]);
+            if (dev[i]) cudaFree(dev[i]);
+        }
+        if (cs) cudaStreamDestroy(cs);
+    };
+    pic_ctx *c0 = b->ctx[0];
+    auto bad = [&](cudaError_t e) {
+        if (e == cudaSuccess) return false;
+        c0->err = std::string("batch graph: ") + cudaGetErrorString(e);
+        st = PIC_ERR_CUDA;
+        return true;
+    };
+    if (bad(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking))) { cleanup(); return st; }
+    for (auto &e : ev)
+        if (bad(cudaEventCreateWithFlags(&e, cudaEventDisableTiming))) { cleanup(); return st; }
+    for (size_t i = 0; i < nctx; ++i) {
+        pic_ctx *c = b->ctx[i];
+        if (bad(cudaMallocHost(&host[i], sizeof(StepScal) * K)) || bad(cudaMalloc(&dev[i], sizeof(StepScal) * K))) {
+            cleanup();
+            return st;
+        }
+        // a band never spans more lattice planes than this (see lattice_band)
+        InjectArgs a{};
+        fill_inject_common(c, a);
+        const double jm = a.jitter * a.hz_lab + a.dzl;
+        c->inj_planes_max = (int64_t)std::ceil((c->gam * c->beta * c->dt + 2.0 * jm) / a.dzl) + 8;
+    }
+    // capture: fork every context's stream from cs, K steps each, join
+    if (bad(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed))) { cleanup(); return st; }
+    cudaEventRecord(ev[nctx], cs);
+    for (size_t i = 0; i < nctx; ++i) {
+        pic_ctx *c = b->ctx[i];
+        cudaStreamWaitEvent(c->stream, ev[nctx], 0);
+        cudaMemcpyAsync(dev[i], host[i], sizeof(StepScal) * K, cudaMemcpyHostToDevice, c->stream);
+    }
+    for (int s = 0; s < K; ++s)
+        for (size_t i = 0; i < nctx; ++i) {
+            pic_ctx *c = b->ctx[i];
+            c->capturing = true;
+            c->cap_scal = dev[i];
+            c->cap_s = s;
+            if (c->es == 4) run_phases_t<float>(c, PIC_PH_ALL);
+            else run_phases_t<double>(c, PIC_PH_ALL);
+            c->capturing = false;
+        }
+    for (size_t i = 0; i < nctx; ++i) {
+        cudaEventRecord(ev[i], b->ctx[i]->stream);
+        cudaStreamWaitEvent(cs, ev[i], 0);
+    }
+    if (bad(cudaStreamEndCapture(cs, &graph))) { cleanup(); return st; }
+    if (bad(cudaGraphInstantiate(&exec, graph, 0))) { cleanup(); return st; }
+    // the capture flipped every double buffer K times (K even: back where it
+    // was) and counted the kernels of K steps; replay
+    std::vector<int64_t> kern(nctx);
+    for (size_t i = 0; i < nctx; ++i) {
+        kern[i] = b->ctx[i]->kernels;
+        b->ctx[i]->kernels = 0;
+    }
+    for (int r = 0; r < reps; ++r) {
+        // the previous replay has read its scalars before they are rewritten
+        if (bad(cudaStreamSynchronize(cs))) { cleanup(); return st; }
+        for (size_t i = 0; i < nctx; ++i) fill_step_scalars(b->ctx[i], K, host[i]);
+        if (bad(cudaGraphLaunch(exec, cs))) { cleanup(); return st; }
+        for (size_t i = 0; i < nctx; ++i) {
+            pic_ctx *c = b->ctx[i];
+            for (int s = 0; s < K; ++s) c->t += c->dt;
+            c->step += K;
+            c->kernels += kern[i];
+        }
+        done += K;
+    }
+    if (bad(cudaStreamSynchronize(cs))) { cleanup(); return st; }
+    cleanup();
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_batch_set_graph(pic_batch *b, int steps_per_graph)
+{
+    if (!b || steps_per_graph < 0 || (steps_per_graph & 1)) return PIC_ERR_ARG;
+    b->graph_steps = steps_per_graph;
+    return PIC_OK;
+}
 
 extern "C" pic_status pic_batch_create(pic_ctx *const *ctxs, int n, pic_batch **out)
 {
@@ -984,9 +1135,14 @@ extern "C" pic_status pic_batch_create(pic_ctx *const *ctxs, int n, pic_batch **
 extern "C" pic_status pic_batch_step(pic_batch *b, int nsteps)
 {
     if (!b || nsteps < 0) return PIC_ERR_ARG;
+    int done = 0;
+    if (b->graph_steps > 0 && nsteps >= b->graph_steps && batch_capturable(b)) {
+        pic_status s = batch_graph_steps(b, nsteps, done);
+        if (s != PIC_OK) return s;
+    }
     // step n of every context before step n + 1 of any: the contexts' streams
     // run concurrently, so the GPU holds the kernels of all of them at once
-    for (int n = 0; n < nsteps; ++n)
+    for (int n = done; n < nsteps; ++n)
         for (pic_ctx *c : b->ctx) {
             pic_status s = run_steps(c, 1, PIC_PH_ALL, false);
             if (s != PIC_OK) return s;

@@ -555,8 +555,9 @@ void launch_filter(const Geom &g, real *const J[3], real *tmp, int npass, cudaSt
 // per step: the profile is evaluated in FP64 and rounded once.
 template <typename real>
 __global__ void antenna_kernel(Geom g, real *J, int pol, int ka, double j0, double hx, double hy, double xc,
-                               double yc, double inv_w2)
+                               double yc, double inv_w2, const double *j0p)
 {
+    if (j0p) j0 = *j0p;
     const int64_t n = g.plane;
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(o % g.nx), j = (int)(o / g.nx);
@@ -572,10 +573,10 @@ __global__ void antenna_kernel(Geom g, real *J, int pol, int ka, double j0, doub
 
 template <typename real>
 void launch_antenna(const Geom &g, real *J, int pol, int ka, double j0, double hx, double hy, double xc,
-                    double yc, double waist, cudaStream_t s)
+                    double yc, double waist, cudaStream_t s, const double *j0p)
 {
     antenna_kernel<real><<<grid_for(g.plane, 256), 256, 0, s>>>(g, J, pol, ka, j0, hx, hy, xc, yc,
-                                                               1.0 / (waist * waist));
+                                                               1.0 / (waist * waist), j0p);
 }
 
 // ------------------------------------------------------------ field sums
@@ -624,7 +625,7 @@ void launch_field_sums(const Geom &g, real *const F[9], double *partials, int nb
     template bool launch_filter_from<real>(const Geom &, const real *, real *const[3], int, cudaStream_t); \
     template void launch_window_fields<real>(const Geom &, real *const[9], real *const[9], int, cudaStream_t); \
     template void launch_antenna<real>(const Geom &, real *, int, int, double, double, double, double,  \
-                                       double, double, cudaStream_t);                                   \
+                                       double, double, cudaStream_t, const double *);                   \
     template void launch_field_sums<real>(const Geom &, real *const[9], double *, int, cudaStream_t);
 PIC_FIELDS_INSTANTIATE(float)
 PIC_FIELDS_INSTANTIATE(double)

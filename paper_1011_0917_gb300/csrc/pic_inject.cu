@@ -85,7 +85,10 @@ template <typename real>
 __global__ void inject_kernel(InjectArgs a)
 {
     const bool dim3 = a.g.dim == 3;
-    const int64_t total = (a.m_hi - a.m_lo) * a.NY * a.NX;
+    // the step's times and lattice band (from device memory in a captured step)
+    const double t = a.scal ? a.scal->t : a.t, t1 = a.scal ? a.scal->t1 : a.t1;
+    const int64_t m_lo = a.scal ? a.scal->m_lo : a.m_lo, m_hi = a.scal ? a.scal->m_hi : a.m_hi;
+    const int64_t total = (m_hi - m_lo) * a.NY * a.NX;
     const int64_t nround = (total + 31) / 32 * 32;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nround; q += stride) {
@@ -98,7 +101,7 @@ __global__ void inject_kernel(InjectArgs a)
             const int64_t ix = q % a.NX;
             const int64_t r = q / a.NX;
             const int64_t iy = r % a.NY;
-            const int64_t m = a.m_lo + r / a.NY;
+            const int64_t m = m_lo + r / a.NY;
             L = (m * a.NY + iy) * a.NX + ix;
             const uint64_t c0 = 3ull * (uint64_t)L;
             double x = ((double)ix + 0.5) * (a.hx / (double)a.ppx) +
@@ -121,11 +124,11 @@ __global__ void inject_kernel(InjectArgs a)
                 double zb;
                 // simulation-frame positions relative to the (moving) window
                 if (a.mode == 0) {
-                    zb = zlab / a.gam - a.beta * a.t - a.zwin;
+                    zb = zlab / a.gam - a.beta * t - a.zwin;
                     take = zb >= a.zmin && zb < a.Lz;
                 } else {
-                    const double zb0 = zlab / a.gam - a.beta * a.t - a.zwin;
-                    zb = zlab / a.gam - a.beta * a.t1 - a.zwin;
+                    const double zb0 = zlab / a.gam - a.beta * t - a.zwin;
+                    zb = zlab / a.gam - a.beta * t1 - a.zwin;
                     take = zb0 >= a.Lz && zb < a.Lz;
                 }
                 if (take) {

@@ -381,6 +381,14 @@ struct BtdArgs {         // lab-frame snapshots filled during one step
     int klo[64], kn[64];        // per snapshot, the lab points this step may fill
 };
 
+// per-step scalars of a captured step (CUDA graph): the antenna amplitude and
+// the injection's times and lattice band, read by the kernels from device
+// memory that the host refills before each replay
+struct StepScal {
+    double j0, t, t1;
+    int64_t m_lo, m_hi;
+};
+
 struct InjectArgs {      // lattice load / boosted injection, FP64
     Geom g;
     double hx, hy, hz, Lx, Ly, Lz, gam, beta;
@@ -413,6 +421,8 @@ struct InjectArgs {      // lattice load / boosted injection, FP64
     int *f_ion_ci;               // per slot, constant: the ion's x cell and offset,
     void *f_ion_ox, *f_w;        // the weight (shared by the pair)
     double *f_zeta;              // and the lab profile coordinate
+    const StepScal *scal;        // non-null: t, t1, m_lo, m_hi from here (a captured
+                                 // step; m_lo, m_hi above then bound the launch)
 };
 
 // One state of the flat particle store of an adjoint run (2D, slot p is the
@@ -482,9 +492,10 @@ void launch_filter(const Geom &g, real *const J[3], real *tmp, int npass, cudaSt
 // false (nothing launched) where only the per-pass path applies (npass > 4)
 template <typename real>
 bool launch_filter_from(const Geom &g, const real *src, real *const J[3], int npass, cudaStream_t s);
+// j0p non-null: the amplitude is read from device memory (a captured step)
 template <typename real>
 void launch_antenna(const Geom &g, real *J, int pol, int ka, double j0, double hx, double hy,
-                    double xc, double yc, double waist, cudaStream_t s);
+                    double xc, double yc, double waist, cudaStream_t s, const double *j0p = nullptr);
 template <typename real>
 void launch_field_sums(const Geom &g, real *const F[9], double *partials, int nblocks,
                        cudaStream_t s);

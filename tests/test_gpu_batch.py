@@ -1,7 +1,8 @@
 """The batched scan: independent boosted runs (different boosts, lengths,
 density profiles and laser amplitudes, the c4 recipe on smaller grids) stepped
-together through pic_batch_step, each on its own stream; every run matches its
-own FP64 oracle run (full-step tolerances: 1e-4 FP32, 1e-10 FP64)."""
+together through pic_batch_step, each on its own stream, as replays of a
+captured CUDA graph or launch by launch; every run matches its own FP64
+oracle run (full-step tolerances: 1e-4 FP32, 1e-10 FP64)."""
 import pytest
 
 from pairs import make_pair, vector_errors
@@ -20,8 +21,9 @@ def O():
     return O
 
 
+@pytest.mark.parametrize("graph_steps", [20, 0])
 @pytest.mark.parametrize("prec", [FP64, FP32])
-def test_batch_matches_each_run(O, prec):
+def test_batch_matches_each_run(O, prec, graph_steps):
     import torch
 
     import paper_1011_0917_gb300 as P
@@ -46,7 +48,8 @@ def test_batch_matches_each_run(O, prec):
         sims.append(sim)
         oracles.append(o)
     assert len({st.grid["gamma_boost"] for st in runs}) >= 2
-    batch = P.Batch(sims)
+    # 40 steps: two replays of a captured 20-step graph, or the stream path
+    batch = P.Batch(sims, graph_steps=graph_steps)
     batch.step(runs[0].steps)
     batch.close()
     for sim, o, st in zip(sims, oracles, runs):
