@@ -100,8 +100,9 @@ typedef struct pic_grid_params {
     int precision;          /* PIC_FP32 (production) or PIC_FP64 (debug)        */
     uint64_t seed;          /* SplitMix64 seed of the plasma jitter             */
     double slots_per_cell;  /* particle slots per cell and species, > 0         */
-    int tile[3];            /* tile shape in cells: 0 or the compiled shape,     */
-                            /* 8x8x8 in 3D, 16x1x16 in 2D (others: PIC_ERR_ARG) */
+    int tile[3];            /* tile shape in cells: 0 or a compiled shape:      */
+                            /* 8x8x8 in 3D; 16x1x16 in 2D, and with the CIC     */
+                            /* shape also 32x1x8, 8x1x32 (others: PIC_ERR_ARG)  */
     int track_ids;          /* 1: carry an int64 lattice id with each particle */
     int explicit_ions;      /* 1: store every drifting ion as its own record    */
                             /* (0: electron-ion pairs, see pic_load_plasma)     */
@@ -299,7 +300,7 @@ pic_status pic_batch_set_graph(pic_batch *batch, int steps_per_graph);
    stays where it was launched, is switched off once it is below plane 2.
    Positions, fields, rho and snapshots are relative to the window; its
    displacement n S hz is pic_diag.z_window.  S must be a positive multiple of
-   the tile's z extent (8 in 3D, 16 in 2D) below nz, and z absorbing
+   the tile's z extent (8 in 3D, that of the tile shape in 2D) below nz, and z absorbing
    (PIC_BC_MUR); v = 0 switches the window off (PIC_ERR_ARG otherwise). */
 pic_status pic_set_moving_window(pic_ctx *ctx, double v, double t0, int shift_cells);
 

@@ -1,0 +1,103 @@
+"""Autotuner of a run's launch configuration.
+
+Chooses, by timing a few steps of the run itself, among the configurations
+the library offers at run time:
+
+* the 2D particle tile shape: 16 x 16, 32 x 8 or 8 x 32 cells (x, z; the last
+  two with the CIC shape), which sets how many particles a CTA stages fields
+  and accumulates currents for, and how many leave their tile per step;
+* the bucket capacity (slots per cell), which sets the memory a tile's
+  particle records span;
+* for a batch of runs, the number of steps per captured CUDA graph.
+
+Particles are sorted into their tiles at every step, inside the push, so
+there is no sort interval to choose; the CTA shape (256 threads) is compiled.
+A candidate whose buckets overflow during the trial is discarded.
+"""
+from __future__ import annotations
+
+import itertools
+import time
+
+TILES_2D = ((16, 1, 16), (32, 1, 8), (8, 1, 32))
+SLOTS = (6.0, 8.0, 12.0)
+
+
+def _build(P, settings: dict, tile, slots, stream):
+    g = dict(settings["grid"])
+    g.update(tile=tile, slots_per_cell=slots, stream=stream)
+    sim = P.Simulation(**g)
+    p = settings["plasma"]
+    sim.load_plasma(p["ne"], p["z_start"], p["z_end"], p.get("ramp", 0.0), p.get("ppc", (2, 1, 2)),
+                    p.get("jitter", 0.1), p.get("profile", ()), p.get("ions", 1))
+    l = settings["laser"]
+    sim.launch_laser(l["a0"], l["waist"], l["fwhm"], l.get("z_antenna", 0.0), l.get("t_peak", -1.0),
+                     l.get("pol", P.PIC_POL_Y))
+    return sim
+
+
+def tune_run(settings: dict, steps: int = 8, warmup: int = 3, tiles=None, slots=SLOTS) -> dict:
+    """Time every (tile, slots_per_cell) candidate on `steps` steps of the run
+    described by settings = {"grid": Simulation kwargs, "plasma": ..., "laser":
+    ...} after `warmup` steps.  Returns {"tile", "slots_per_cell", "ms_per_step",
+    "trials": [...]} for the fastest candidate."""
+    import torch
+
+    import paper_1011_0917_gb300 as P
+    g = settings["grid"]
+    if tiles is None:
+        tiles = TILES_2D if g.get("dim", 2) == 2 and g.get("shape_order", 1) == 1 else ((0, 0, 0),)
+    trials = []
+    for tile, sl in itertools.product(tiles, slots):
+        stream = torch.cuda.Stream()
+        sim = None
+        try:
+            sim = _build(P, settings, tile, sl, stream)
+            P.pic_step(sim.ctx, warmup)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            P.pic_step_async(sim.ctx, steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            P.pic_step(sim.ctx, 0)  # the device error word of the timed steps
+            trials.append({"tile": tuple(tile), "slots_per_cell": sl, "ms_per_step": e0.elapsed_time(e1) / steps})
+        except P.PicError as e:
+            trials.append({"tile": tuple(tile), "slots_per_cell": sl, "error": str(e)})
+        finally:
+            if sim is not None:
+                sim.close()
+    ok = [t for t in trials if "ms_per_step" in t]
+    if not ok:
+        raise RuntimeError("autotune: no candidate ran: " + "; ".join(t.get("error", "") for t in trials))
+    best = min(ok, key=lambda t: t["ms_per_step"])
+    return dict(best, trials=trials)
+
+
+def tune_batch(settings_list, steps: int = 40, warmup: int = 3, graph_steps=(0, 20, 40), tile=(0, 0, 0),
+               slots: float = 8.0) -> dict:
+    """Time pic_batch_step of the runs with each number of steps per captured
+    graph (0: launch by launch); returns the fastest and all trials."""
+    import torch
+
+    import paper_1011_0917_gb300 as P
+    sims = [_build(P, s, tile, slots, torch.cuda.Stream()) for s in settings_list]
+    trials = []
+    try:
+        batch = P.Batch(sims, graph_steps=0)
+        batch.step(warmup)
+        for k in graph_steps:
+            # the runs' work spans their own streams: time on the host between
+            # two device-wide synchronisations
+            P.pic_batch_set_graph(batch.h, k)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            batch.step(steps)
+            torch.cuda.synchronize()
+            trials.append({"graph_steps": k, "ms_per_step": 1e3 * (time.perf_counter() - t0) / steps})
+        batch.close()
+    finally:
+        for s in sims:
+            s.close()
+    best = min(trials, key=lambda t: t["ms_per_step"])
+    return dict(best, trials=trials)

@@ -796,7 +796,8 @@ __global__ void __launch_bounds__(kBlock) ion_kernel(PushArgs<real> a)
     }
 }
 
-// the tile shapes the kernels are compiled for (pic_init_grid accepts these)
+// the tile shapes the kernels are compiled for (pic_init_grid accepts these):
+// 8 x 8 x 8 in 3D; 16 x 16 in 2D, and for CIC also 32 x 8 and 8 x 32 (x, z)
 constexpr int kTile3[3] = {8, 8, 8};
 constexpr int kTile2[3] = {16, 1, 16};
 
@@ -828,9 +829,14 @@ static void dispatch_push(const PushArgs<real> &a, bool ions, cudaStream_t s)
     if (a.g.dim == 3) {
         if (a.g.shape == 1) launch_push_t<real, 3, 1, kTile3[0], kTile3[1], kTile3[2]>(a, ions, s);
         else launch_push_t<real, 3, 2, kTile3[0], kTile3[1], kTile3[2]>(a, ions, s);
+    } else if (a.g.shape == 2) {
+        launch_push_t<real, 2, 2, kTile2[0], kTile2[1], kTile2[2]>(a, ions, s);
+    } else if (a.g.lt[0] == 5) {  // 32 x 8
+        launch_push_t<real, 2, 1, 32, 1, 8>(a, ions, s);
+    } else if (a.g.lt[0] == 3) {  // 8 x 32
+        launch_push_t<real, 2, 1, 8, 1, 32>(a, ions, s);
     } else {
-        if (a.g.shape == 1) launch_push_t<real, 2, 1, kTile2[0], kTile2[1], kTile2[2]>(a, ions, s);
-        else launch_push_t<real, 2, 2, kTile2[0], kTile2[1], kTile2[2]>(a, ions, s);
+        launch_push_t<real, 2, 1, kTile2[0], kTile2[1], kTile2[2]>(a, ions, s);
     }
 }
 

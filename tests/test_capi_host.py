@@ -65,6 +65,24 @@ def test_init_grid_rejects_invalid_parameters(P, bad, status):
     assert e.value.status == status
 
 
+@pytest.mark.parametrize("tile", [(16, 1, 16), (32, 1, 8), (8, 1, 32), (32, 0, 8)])
+def test_compiled_2d_tile_shapes_are_accepted(P, tile):
+    ctx = P.pic_init_grid(grid(P, tile=tile))
+    try:
+        s = P.pic_query_sizes(ctx)
+        assert (s.tile[0], s.tile[2]) == (tile[0], tile[2])
+        assert s.tile_capacity % 32 == 0 and s.tile_capacity >= 8 * tile[0] * tile[2]
+    finally:
+        P.pic_destroy(ctx)
+
+
+@pytest.mark.parametrize("tile,shape", [((32, 1, 8), 2), ((8, 1, 32), 2), ((32, 1, 16), 1), ((64, 1, 4), 1)])
+def test_other_2d_tile_shapes_are_rejected(P, tile, shape):
+    with pytest.raises(P.PicError) as e:
+        P.pic_init_grid(grid(P, tile=tile, shape_order=shape))
+    assert e.value.status == 1
+
+
 @pytest.mark.parametrize("kw", [
     dict(), dict(gamma_boost=13.0, dx=1.0, dz=1 / 32, nx=256, nz=8192),
     dict(dim=3, nx=32, ny=16, nz=64, dx=1.0, dy=1.0, dz=1 / 32, gamma_boost=13.0),

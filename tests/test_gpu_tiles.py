@@ -1,0 +1,59 @@
+"""The 2D tile-shape variants of the particle kernels (16 x 16, 32 x 8, 8 x 32
+cells) against the FP64 oracle, and the autotuner that picks among them.
+
+The tile shape changes only how particles are grouped for staging, deposit
+and re-bucketing, so every variant must match the oracle to the full-step
+tolerances (relative L2 1e-4 FP32, 1e-10 FP64) on the boosted 2D stage with
+plasma streaming in and a laser meeting it."""
+import math
+
+import pytest
+
+from pairs import make_pair, vector_errors
+
+pytestmark = pytest.mark.gpu
+
+FP32, FP64 = 0, 1
+TOL = {FP32: 1e-4, FP64: 1e-10}
+GAM = 13.0
+BETA = math.sqrt(1 - 1 / GAM ** 2)
+HZ = (1 / 32) * GAM * (1 + BETA)
+G = dict(dim=2, nx=32, nz=256, dx=1.0, dz=1 / 32, gamma_boost=GAM, filter_passes=2, seed=17)
+PLASMA = dict(ne=0.004, z_start=GAM * 10 * HZ, z_end=GAM * 600 * HZ, ramp=2.0, ppc=(2, 1, 2), jitter=0.1, ions=1)
+LASER = dict(a0=4.0, waist=8.0, fwhm=2.0, t_peak=0.5)
+
+
+@pytest.fixture(scope="module")
+def O():
+    import oracle.oracle as O
+    O.build_oracle()
+    return O
+
+
+@pytest.mark.parametrize("tile", [(32, 1, 8), (8, 1, 32)])
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_tile_variant_matches_oracle(O, prec, tile):
+    sim, o = make_pair(O, G, prec, tile=tile)
+    assert tuple(sim.sizes.tile) == tile
+    p = PLASMA
+    sim.load_plasma(p["ne"], p["z_start"], p["z_end"], p["ramp"], p["ppc"], p["jitter"], (), p["ions"])
+    o.load_plasma(O.PlasmaParams(ne=p["ne"], z_start=p["z_start"], z_end=p["z_end"], ramp=p["ramp"], ppc=p["ppc"],
+                                 jitter=p["jitter"], ions=p["ions"]))
+    sim.launch_laser(LASER["a0"], LASER["waist"], LASER["fwhm"], 0.0, LASER["t_peak"], 1)
+    o.set_laser(O.LaserParams(a0=LASER["a0"], waist=LASER["waist"], fwhm=LASER["fwhm"], t_peak=LASER["t_peak"],
+                              pol=1))
+    sim.step(50)
+    o.step(50)
+    err = vector_errors(sim, o)
+    assert max(err.values()) < TOL[prec], err
+    d = sim.diagnostics()
+    assert d.n_particles[0] == o.num(0) and d.n_particles[1] == o.num(1)
+
+
+def test_autotune_picks_a_compiled_configuration():
+    from paper_1011_0917_gb300 import autotune
+    settings = {"grid": dict(G, precision=FP32), "plasma": PLASMA, "laser": dict(LASER, pol=1)}
+    best = autotune.tune_run(settings, steps=4, warmup=2)
+    assert best["tile"] in autotune.TILES_2D and best["slots_per_cell"] in autotune.SLOTS
+    assert len(best["trials"]) == len(autotune.TILES_2D) * len(autotune.SLOTS)
+    assert best["ms_per_step"] == min(t["ms_per_step"] for t in best["trials"] if "ms_per_step" in t)
