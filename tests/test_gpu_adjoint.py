@@ -117,6 +117,41 @@ def test_gradient_independent_of_checkpoint_interval(O):
     assert np.allclose(g1, g2, rtol=1e-11, atol=0)
 
 
+def test_lab_frame_gradient_matches_oracle_finite_differences(O):
+    # the same objective in the lab frame (gamma = 1: immobile ions, no
+    # injection) on the c0 grid spacing, plasma from 6 cells on
+    g = dict(dim=2, nx=16, nz=96, dx=0.5, dz=1 / 16, gamma_boost=1.0, filter_passes=1, seed=63)
+    pl = dict(ne=0.01, z_start=6 / 16, z_end=40.0, ramp=0.5, ppc=(2, 1, 2), jitter=0.1)
+    # a short horizon and a gentle drive (a0 = 0.5), where the oracle's central
+    # differences agree across h = 1e-3 .. 1e-5 to 2e-5
+    coef, a0, w0, nsteps = (0.15,), 0.5, 3.0, 40
+    lam = np.zeros((6, g["nz"] + 1, g["nx"]))
+    lam[2, 10:60, :] = 1.0
+    lam[1, 20:40, :] = 0.1
+
+    def objective(c, a, w):
+        o = O.Oracle(O.GridParams(dim=2, nx=g["nx"], nz=g["nz"], dx=g["dx"], dz=g["dz"], npass=1, bc_z=1,
+                                  seed=g["seed"]))
+        o.load_plasma(O.PlasmaParams(profile=tuple(c), ions=1, **pl))
+        o.set_laser(O.LaserParams(a0=a, waist=w, fwhm=2.0, z_antenna=0.0, t_peak=0.5, pol=1))
+        o.step(nsteps)
+        return float(np.sum(lam * np.stack([o.field(q)[:, 0, :] for q in ("Ex", "Ey", "Ez", "Bx", "By", "Bz")])))
+
+    import torch
+    sim, _ = make_pair(O, g, FP64)
+    sim.load_plasma(pl["ne"], pl["z_start"], pl["z_end"], pl["ramp"], pl["ppc"], pl["jitter"], coef, 1)
+    sim.launch_laser(a0, w0, 2.0, 0.0, 0.5, 1)
+    sim.adjoint_forward(nsteps, 16)
+    grad = np.array(sim.adjoint_backward(torch.as_tensor(lam, device="cuda")))
+    h = 1e-4
+    fd = np.array([(objective((coef[0] + h,), a0, w0) - objective((coef[0] - h,), a0, w0)) / (2 * h),
+                   (objective(coef, a0 + h, w0) - objective(coef, a0 - h, w0)) / (2 * h),
+                   (objective(coef, a0, w0 + h) - objective(coef, a0, w0 - h)) / (2 * h)])
+    assert np.all(np.abs(fd) > 0)
+    rel = np.abs(grad - fd) / np.abs(fd)
+    assert np.all(rel < 1e-3), (grad, fd, rel)
+
+
 def test_fp32_gradient_against_fp64(O):
     _, g64 = gpu_run(O, FP64)
     _, g32 = gpu_run(O, FP32)
