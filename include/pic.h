@@ -348,7 +348,7 @@ pic_status pic_btd_get(pic_ctx *ctx, int j, void *dst, size_t dst_bytes, int dst
 
 /* ---------------------------------------------------------------- adjoint */
 
-/* Reverse-mode gradient of a run (2D3V, CIC shape, no moving window): the
+/* Reverse-mode gradient of a run (2D3V or 3D, CIC shape, no moving window): the
    library's own extension of the method, built from the transposes of the
    step's maps (Yee with Mur's condition, filter, antenna, Esirkepov deposit,
    gather, Boris rotation, move).  The objective is linear in the final fields,
@@ -373,8 +373,8 @@ pic_status pic_adjoint_bytes(pic_ctx *ctx, const pic_adjoint_params *p, size_t *
 
 /* The forward run into buf (device memory of at least pic_adjoint_bytes bytes,
    owned by the caller and kept alive until pic_adjoint_backward).  fields_out
-   (device, may be NULL) receives E^N, B^N: six components of (nz+1) nx
-   elements, Ex Ey Ez Bx By Bz. */
+   (device, may be NULL) receives E^N, B^N: six components of (nz+1) ny nx
+   elements (ny = 1 in 2D), Ex Ey Ez Bx By Bz. */
 pic_status pic_adjoint_forward(pic_ctx *ctx, const pic_adjoint_params *p, void *buf, size_t bytes,
                                void *fields_out);
 

@@ -494,13 +494,14 @@ class Simulation:
 
     def adjoint_forward(self, nsteps, checkpoint_every=50):
         """Forward run of the adjoint (from right after load_plasma and
-        launch_laser): returns E^N, B^N as a (6, nz+1, nx) device tensor and
-        keeps the checkpoints for adjoint_backward."""
+        launch_laser): returns E^N, B^N as a (6, nz+1, nx) device tensor in 2D,
+        (6, nz+1, ny, nx) in 3D, and keeps the checkpoints for adjoint_backward."""
         p = AdjointParams(int(nsteps), int(checkpoint_every))
         nbytes = pic_adjoint_bytes(self.ctx, p)
         self._adj = self.torch.empty(nbytes, dtype=self.torch.uint8, device=self.device)
         self._adj_n = self._prof_n
-        out = self.torch.empty((6, self.shape3[0], self.shape3[2]), dtype=self.dtype, device=self.device)
+        shape = (6,) + (self.shape3 if self.params.dim == 3 else (self.shape3[0], self.shape3[2]))
+        out = self.torch.empty(shape, dtype=self.dtype, device=self.device)
         pic_adjoint_forward(self.ctx, p, self._adj.data_ptr(), nbytes, out.data_ptr())
         return out
 

@@ -1,4 +1,4 @@
-// pic_adjoint.cu -- reverse mode (adjoint) of the 2D3V CIC step.
+// pic_adjoint.cu -- reverse mode (adjoint) of the CIC step, 2D3V and 3D.
 //
 // The step is differentiated as the composition it is (section "Effect of the
 // hyperbolic rotation in Minkowski space" sets up the boosted-frame run; the
@@ -16,9 +16,9 @@
 //
 // Units and layout are those of the forward path: positions as cell index
 // plus an offset in [0, 1) of the working precision, momenta relative to the
-// plasma drift, fields (nz+1) x nx per component (y absent).  Cotangents of
-// positions are per cell (d/d offset).  CIC only: every shape weight is
-// (1 - d, d) on two nodes, with derivative (-1, +1).
+// plasma drift, fields (nz+1) x ny x nx per component (ny = 1 in 2D).
+// Cotangents of positions are per cell (d/d offset).  CIC only: every shape
+// weight is (1 - d, d) on two nodes, with derivative (-1, +1).
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -34,25 +34,27 @@ unsigned adj_grid(int64_t n, int block)
     return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
-// field value at node (i, k) of a component (x periodic; z periodic or zero
-// outside the component's valid range)
+// field value at node (i, j, k) of a component (x, y periodic; z periodic or
+// zero outside the component's valid range)
 template <typename real>
-__device__ __forceinline__ real fval(const Geom &g, const real *F, int i, int k, bool half_z)
+__device__ __forceinline__ real fval(const Geom &g, const real *F, int i, int j, int k, bool half_z)
 {
     i = wrap1(i, g.nx);
+    j = g.dim == 3 ? wrap1(j, g.ny) : 0;
     if (g.bc_z == 0) k = wrapi(k, g.nz);
     else if (k < 0 || k > zmax_of(g, half_z)) return real(0);
-    return F[(int64_t)k * g.nx + i];
+    return F[((int64_t)k * g.ny + j) * g.nx + i];
 }
 
-// atomically add v at node (i, k) (dropped outside the valid z range)
+// atomically add v at node (i, j, k) (dropped outside the valid z range)
 template <typename real>
-__device__ __forceinline__ void fadd(const Geom &g, real *F, int i, int k, bool half_z, real v)
+__device__ __forceinline__ void fadd(const Geom &g, real *F, int i, int j, int k, bool half_z, real v)
 {
     i = wrap1(i, g.nx);
+    j = g.dim == 3 ? wrap1(j, g.ny) : 0;
     if (g.bc_z == 0) k = wrapi(k, g.nz);
     else if (k < 0 || k > zmax_of(g, half_z)) return;
-    atomicAdd(F + (int64_t)k * g.nx + i, v);
+    atomicAdd(F + ((int64_t)k * g.ny + j) * g.nx + i, v);
 }
 
 // CIC weights and their first node for one staggered axis: integer nodes
@@ -63,9 +65,18 @@ __device__ __forceinline__ int axis_weights(real o, bool half, real w[2])
     return half ? half_weights<1>(o, w) : offset_weights<1>(o, w);
 }
 
-// the staggering of the six E, B components in 2D: x half?, z half?
+// the staggering of the six E, B components: half-integer along x, y, z?
 __device__ __forceinline__ bool hx_of(int c) { return c == 0 || c == 4 || c == 5; }
+__device__ __forceinline__ bool hy_of(int c) { return c == 1 || c == 3 || c == 5; }
 __device__ __forceinline__ bool hz_of(int c) { return c == 2 || c == 3 || c == 4; }
+
+// T(u, v) = S0u (S0v + DSv / 2) + DSu (S0v / 2 + DSv / 3): the path-averaged
+// transverse shape product of Esirkepov's weights
+template <typename real>
+__device__ __forceinline__ real tshape(real s0u, real dsu, real s0v, real dsv)
+{
+    return s0u * (s0v + real(0.5) * dsv) + dsu * (real(0.5) * s0v + real(1) / real(3) * dsv);
+}
 
 // The Boris rotation of boris() (same expressions, same rounding) with the
 // intermediate values its transpose needs
@@ -100,26 +111,37 @@ struct BorisFwd {
 };
 
 // gathered E (0..2) and B (3..5) at a particle, with the weights and first
-// nodes of every component (kept for the transpose)
-template <typename real>
+// nodes of every component (kept for the transpose; y trivial in 2D)
+template <typename real, int DIM>
 struct GatherFwd {
-    real wx[6][2], wz[6][2], f[6];
-    int bx[6], bz[6];
+    real wx[6][2], wy[6][2], wz[6][2], f[6];
+    int bx[6], by[6], bz[6];
     template <typename Args>
-    __device__ __forceinline__ GatherFwd(const Args &a, int ci, int ck, real ox, real oz)
+    __device__ __forceinline__ GatherFwd(const Args &a, int ci, int cj, int ck, real ox, real oy, real oz)
     {
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             bx[c] = ci + axis_weights(ox, hx_of(c), wx[c]);
+            if (DIM == 3) {
+                by[c] = cj + axis_weights(oy, hy_of(c), wy[c]);
+            } else {
+                by[c] = 0;
+                wy[c][0] = real(1);
+                wy[c][1] = real(0);
+            }
             bz[c] = ck + axis_weights(oz, hz_of(c), wz[c]);
             const real *F = c < 3 ? a.E[c] : a.B[c - 3];
             real sum = 0;
 #pragma unroll
             for (int cc = 0; cc < 2; ++cc) {
-                real r = 0;
 #pragma unroll
-                for (int q = 0; q < 2; ++q) r += wx[c][q] * fval(a.g, F, bx[c] + q, bz[c] + cc, hz_of(c));
-                sum += wz[c][cc] * r;
+                for (int b = 0; b < (DIM == 3 ? 2 : 1); ++b) {
+                    real r = 0;
+#pragma unroll
+                    for (int q = 0; q < 2; ++q)
+                        r += wx[c][q] * fval(a.g, F, bx[c] + q, by[c] + b, bz[c] + cc, hz_of(c));
+                    sum += wz[c][cc] * wy[c][b] * r;
+                }
             }
             f[c] = sum;
         }
@@ -132,56 +154,72 @@ struct GatherFwd {
 
 // One step of the electrons of the flat store: gather E^n, B^n at x^n, Boris,
 // move, Esirkepov deposit with global atomics, re-cell; state `in` -> `out`.
-template <typename real>
+template <typename real, int DIM>
 __global__ void adj_push_kernel(AdjArgs<real> a)
 {
     const Geom &g = a.g;
-    const Drift<real> drift(a.u_drift, a.dtdh[1]);
+    const Drift<real> drift(a.u_drift, a.dtdh[2]);
+    const real half = real(0.5), third = real(1) / real(3);
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
         if (!a.in.alive[p]) {
             a.out.alive[p] = 0;
             continue;
         }
-        const int ci = a.in.ci[p], ck = a.in.ck[p];
-        const real ox = a.in.ox[p], oz = a.in.oz[p], w = a.w[p];
+        const int ci = a.in.ci[p], cj = DIM == 3 ? a.in.cj[p] : 0, ck = a.in.ck[p];
+        const real ox = a.in.ox[p], oy = DIM == 3 ? a.in.oy[p] : real(0), oz = a.in.oz[p], w = a.w[p];
         const real du[3] = {a.in.ux[p], a.in.uy[p], a.in.uz[p]};
-        const GatherFwd<real> gf(a, ci, ck, ox, oz);
+        const GatherFwd<real, DIM> gf(a, ci, cj, ck, ox, oy, oz);
         const BorisFwd<real> bf(du, drift.U, gf.f, gf.f + 3, a.eps);
         const real ux = bf.u[0], uy = bf.u[1], uz = bf.u[2];
         real vx, vy;
         const real dvz = drift_velocity(drift, ux, uy, uz, vx, vy);
         const real x1 = ox + vx * a.dtdh[0];
-        const real z1 = add_rn(oz, drift.dz) + dvz * a.dtdh[1];
-        // Esirkepov (2D3V): windows of 3 nodes per axis
-        real S0x[3], DSx[3], S0z[3], DSz[3];
+        const real y1 = DIM == 3 ? oy + vy * a.dtdh[1] : real(0);
+        const real z1 = add_rn(oz, drift.dz) + dvz * a.dtdh[2];
+        // Esirkepov: windows of 3 nodes per axis
+        real S0x[3], DSx[3], S0y[3] = {1, 0, 0}, DSy[3] = {0, 0, 0}, S0z[3], DSz[3];
         bool cr;
         const int ax = ci + esirk_axis_c<1>(ox, x1, S0x, DSx, cr);
+        const int ay = DIM == 3 ? cj + esirk_axis_c<1>(oy, y1, S0y, DSy, cr) : 0;
         const int az = ck + esirk_axis_c<1>(oz, z1, S0z, DSz, cr);
-        const real fx = a.jfac[0] * w, fz = a.jfac[2] * w, fyv = a.jyfac * w * vy;
-        real Rx = 0, Rz[3];
+        real Rx[3], Ry[3], Rz[3];
         {
-            real acc = 0;
+            real ax_ = 0, ay_ = 0, az_ = 0;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) { acc += DSz[c]; Rz[c] = acc; }
-        }
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            Rx += DSx[q];
-            const real xa = S0x[q] + real(0.5) * DSx[q];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const real za = S0z[c] + real(0.5) * DSz[c], zb = real(0.5) * S0z[c] + real(1) / real(3) * DSz[c];
-                if (q < 2) fadd(g, a.J[0], ax + q, az + c, false, fx * Rx * za);
-                fadd(g, a.J[1], ax + q, az + c, false, fyv * (S0x[q] * za + DSx[q] * zb));
-                if (c < 2) fadd(g, a.J[2], ax + q, az + c, true, fz * Rz[c] * xa);
+            for (int q = 0; q < 3; ++q) {
+                ax_ += DSx[q];
+                ay_ += DSy[q];
+                az_ += DSz[q];
+                Rx[q] = ax_;
+                Ry[q] = ay_;
+                Rz[q] = az_;
             }
         }
+        const real fx = a.jfac[0] * w, fy = a.jfac[1] * w, fz = a.jfac[2] * w, fyv = a.jyfac * w * vy;
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int b = 0; b < (DIM == 3 ? 3 : 1); ++b)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (q < 2) fadd(g, a.J[0], ax + q, ay + b, az + c, false, fx * Rx[q] * tshape(S0y[b], DSy[b], S0z[c], DSz[c]));
+                    if (DIM == 3) {
+                        if (b < 2) fadd(g, a.J[1], ax + q, ay + b, az + c, false, fy * Ry[b] * tshape(S0z[c], DSz[c], S0x[q], DSx[q]));
+                    } else {
+                        fadd(g, a.J[1], ax + q, 0, az + c, false, fyv * tshape(S0x[q], DSx[q], S0z[c], DSz[c]));
+                    }
+                    if (c < 2) fadd(g, a.J[2], ax + q, ay + b, az + c, true, fz * Rz[c] * tshape(S0x[q], DSx[q], S0y[b], DSy[b]));
+                }
+        (void)half;
+        (void)third;
         // new cell (an offset that rounds to 1 moves on)
-        int sx = (int)floor(x1), sz = (int)floor(z1);
-        real nox = x1 - real(sx), noz = z1 - real(sz);
+        int sx = (int)floor(x1), sy = DIM == 3 ? (int)floor(y1) : 0, sz = (int)floor(z1);
+        real nox = x1 - real(sx), noy = DIM == 3 ? y1 - real(sy) : real(0), noz = z1 - real(sz);
         if (nox >= real(1)) { sx += 1; nox = 0; }
+        if (DIM == 3 && noy >= real(1)) { sy += 1; noy = 0; }
         if (noz >= real(1)) { sz += 1; noz = 0; }
-        int ni = wrapi(ci + sx, g.nx), nk = ck + sz;
+        const int ni = wrapi(ci + sx, g.nx), nj = DIM == 3 ? wrapi(cj + sy, g.ny) : 0;
+        int nk = ck + sz;
         bool alive = true;
         if (g.bc_z == 0) nk = wrapi(nk, g.nz);
         else if (nk < 0 || nk >= g.nz) alive = false;
@@ -190,6 +228,10 @@ __global__ void adj_push_kernel(AdjArgs<real> a)
         a.out.ck[p] = nk;
         a.out.ox[p] = nox;
         a.out.oz[p] = noz;
+        if (DIM == 3) {
+            a.out.cj[p] = nj;
+            a.out.oy[p] = noy;
+        }
         a.out.ux[p] = ux;
         a.out.uy[p] = uy;
         a.out.uz[p] = uz;
@@ -198,30 +240,33 @@ __global__ void adj_push_kernel(AdjArgs<real> a)
 
 // One step of the drifting ions of the flat store: z move by the drift's
 // displacement and the z-only deposit.
-template <typename real>
+template <typename real, int DIM>
 __global__ void adj_ion_kernel(AdjArgs<real> a)
 {
     const Geom &g = a.g;
-    const Drift<real> drift(a.u_drift, a.dtdh[1]);
+    const Drift<real> drift(a.u_drift, a.dtdh[2]);
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
         if (!a.iin.alive[p]) {
             a.iout.alive[p] = 0;
             continue;
         }
-        const int ci = a.ion_ci[p], ck = a.iin.ck[p];
-        const real ox = a.ion_ox[p], oz = a.iin.oz[p];
+        const int ci = a.ion_ci[p], cj = DIM == 3 ? a.ion_cj[p] : 0, ck = a.iin.ck[p];
+        const real ox = a.ion_ox[p], oy = DIM == 3 ? a.ion_oy[p] : real(0), oz = a.iin.oz[p];
         const real z1 = add_rn(oz, drift.dz);
-        real S0z[3], DSz[3], wx[2];
+        real S0z[3], DSz[3], wx[2], wy[2] = {1, 0};
         bool cr;
         const int az = ck + esirk_axis_c<1>(oz, z1, S0z, DSz, cr);
         offset_weights<1>(ox, wx);
+        if (DIM == 3) offset_weights<1>(oy, wy);
         const real fz = a.jfac_iz * a.w[p];
         real acc = 0;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             acc += DSz[c];
 #pragma unroll
-            for (int q = 0; q < 2; ++q) fadd(g, a.J[2], ci + q, az + c, true, fz * acc * wx[q]);
+            for (int b = 0; b < (DIM == 3 ? 2 : 1); ++b)
+#pragma unroll
+                for (int q = 0; q < 2; ++q) fadd(g, a.J[2], ci + q, cj + b, az + c, true, fz * acc * wx[q] * wy[b]);
         }
         int sz = 0;
         real noz = z1;
@@ -244,130 +289,165 @@ __global__ void adj_ion_kernel(AdjArgs<real> a)
 
 // ------------------------------------------------------------- reverse
 
+// d/dx of a window node's CIC weight: the support of a position starts at node
+// r of the window (weights 1 - d, d on r, r + 1)
+template <typename real>
+__device__ __forceinline__ real dshape(int q, int r)
+{
+    return q == r ? real(-1) : (q == r + 1 ? real(1) : real(0));
+}
+
 // Cotangents of one electron step.  Reads the state at n (x^n, du^{n-1/2}),
 // E^n, B^n, the filtered-and-transposed current cotangent lJ, and the
-// particle's cotangents of x^{n+1}, du^{n+1/2} (lx, lz, lu*); writes those of
-// x^n, du^{n-1/2} in their place, adds the gather's field cotangents to lE,
-// lB and the weight's cotangent to lw.
-template <typename real>
+// particle's cotangents of x^{n+1}, du^{n+1/2}; writes those of x^n,
+// du^{n-1/2} in their place, adds the gather's field cotangents to lE, lB and
+// the weight's cotangent to lw.
+template <typename real, int DIM>
 __global__ void adj_push_vjp_kernel(AdjArgs<real> a)
 {
     const Geom &g = a.g;
-    const Drift<real> drift(a.u_drift, a.dtdh[1]);
+    const Drift<real> drift(a.u_drift, a.dtdh[2]);
     const real half = real(0.5), third = real(1) / real(3);
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
         if (!a.in.alive[p]) continue;
-        const int ci = a.in.ci[p], ck = a.in.ck[p];
-        const real ox = a.in.ox[p], oz = a.in.oz[p], w = a.w[p];
-        const real dux0 = a.in.ux[p], duy0 = a.in.uy[p], duz0 = a.in.uz[p];
+        const int ci = a.in.ci[p], cj = DIM == 3 ? a.in.cj[p] : 0, ck = a.in.ck[p];
+        const real ox = a.in.ox[p], oy = DIM == 3 ? a.in.oy[p] : real(0), oz = a.in.oz[p], w = a.w[p];
         // ---- recompute the forward values of this step
-        const real du0[3] = {dux0, duy0, duz0};
-        const GatherFwd<real> gf(a, ci, ck, ox, oz);
+        const real du0[3] = {a.in.ux[p], a.in.uy[p], a.in.uz[p]};
+        const GatherFwd<real, DIM> gf(a, ci, cj, ck, ox, oy, oz);
         const BorisFwd<real> bf(du0, drift.U, gf.f, gf.f + 3, a.eps);
         const real eps = a.eps, U = drift.U;
         const real ux = bf.u[0], uy = bf.u[1], uz = bf.u[2];
         real vx, vy;
         const real dvz = drift_velocity(drift, ux, uy, uz, vx, vy);
         const real x1 = ox + vx * a.dtdh[0];
-        const real z1 = add_rn(oz, drift.dz) + dvz * a.dtdh[1];
-        // Esirkepov windows and their shape derivatives
-        real S0x[3], DSx[3], S0z[3], DSz[3];
+        const real y1 = DIM == 3 ? oy + vy * a.dtdh[1] : real(0);
+        const real z1 = add_rn(oz, drift.dz) + dvz * a.dtdh[2];
+        real S0x[3], DSx[3], S0y[3] = {1, 0, 0}, DSy[3] = {0, 0, 0}, S0z[3], DSz[3];
         bool cr;
-        real w0x[2], w1x[2], w0z[2], w1z[2];
-        const int b0x = offset_weights<1>(ox, w0x), b1x = spline_weights<1>(x1, w1x);
-        const int b0z = offset_weights<1>(oz, w0z), b1z = spline_weights<1>(z1, w1z);
+        real wtmp[2];
+        const int b0x = offset_weights<1>(ox, wtmp), b1x = spline_weights<1>(x1, wtmp);
+        const int b0z = offset_weights<1>(oz, wtmp), b1z = spline_weights<1>(z1, wtmp);
         const int anx = esirk_axis_c<1>(ox, x1, S0x, DSx, cr);
         const int anz = esirk_axis_c<1>(oz, z1, S0z, DSz, cr);
-        const int ax = ci + anx, az = ck + anz;
-        // ---- deposit transposed: dL/dS0, dL/dS1 per window node, dL/dw, dL/dvy
-        real lJx[3][3], lJy[3][3], lJz[3][3];
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                lJx[q][c] = fval(g, (const real *)a.J[0], ax + q, az + c, false);
-                lJy[q][c] = fval(g, (const real *)a.J[1], ax + q, az + c, false);
-                lJz[q][c] = fval(g, (const real *)a.J[2], ax + q, az + c, true);
-            }
-        const real fx = a.jfac[0] * w, fz = a.jfac[2] * w, fy1 = a.jyfac * vy;  // Jy factor over w
-        real Rx[3], Rz[3];
-        {
-            real acc = 0;
-#pragma unroll
-            for (int q = 0; q < 3; ++q) { acc += DSx[q]; Rx[q] = acc; }
-            acc = 0;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) { acc += DSz[c]; Rz[c] = acc; }
+        int b0y = 0, b1y = 0, any_ = 0;
+        if (DIM == 3) {
+            b0y = offset_weights<1>(oy, wtmp);
+            b1y = spline_weights<1>(y1, wtmp);
+            any_ = esirk_axis_c<1>(oy, y1, S0y, DSy, cr);
         }
-        real gS0x[3] = {0, 0, 0}, gDSx[3] = {0, 0, 0}, gS0z[3] = {0, 0, 0}, gDSz[3] = {0, 0, 0};
-        real gRx[3] = {0, 0, 0}, gRz[3] = {0, 0, 0};
+        const int ax = ci + anx, ay = cj + any_, az = ck + anz;
+        real Rx[3], Ry[3], Rz[3];
+        {
+            real sx_ = 0, sy_ = 0, sz_ = 0;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                sx_ += DSx[q];
+                sy_ += DSy[q];
+                sz_ += DSz[q];
+                Rx[q] = sx_;
+                Ry[q] = sy_;
+                Rz[q] = sz_;
+            }
+        }
+        // ---- deposit transposed: dL/dS0, dL/dDS per window node, dL/dw, dL/dvy
+        const real fx = a.jfac[0] * w, fy = a.jfac[1] * w, fz = a.jfac[2] * w;
+        const real fy1 = a.jyfac * vy;  // 2D out-of-plane factor over w
+        real gS0x[3] = {0, 0, 0}, gDSx[3] = {0, 0, 0}, gS0y[3] = {0, 0, 0}, gDSy[3] = {0, 0, 0};
+        real gS0z[3] = {0, 0, 0}, gDSz[3] = {0, 0, 0};
+        real gRx[3] = {0, 0, 0}, gRy[3] = {0, 0, 0}, gRz[3] = {0, 0, 0};
         real Lw = 0, Ly = 0;
+        // derivatives of T(u, v) with respect to S0u, DSu (the same form in v)
+        auto dT0 = [&](real s0v, real dsv) { return s0v + half * dsv; };
+        auto dT1 = [&](real s0v, real dsv) { return half * s0v + third * dsv; };
 #pragma unroll
         for (int q = 0; q < 3; ++q)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const real za = S0z[c] + half * DSz[c], zb = half * S0z[c] + third * DSz[c];
-                const real xa = S0x[q] + half * DSx[q];
-                if (q < 2) {
-                    // Jx(q, c) = fx Rx[q] za[c]
-                    const real l = lJx[q][c];
-                    gRx[q] += fx * za * l;
-                    gS0z[c] += fx * Rx[q] * l;
-                    gDSz[c] += half * fx * Rx[q] * l;
-                    Lw += a.jfac[0] * Rx[q] * za * l;
+            for (int b = 0; b < (DIM == 3 ? 3 : 1); ++b)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (q < 2) {  // Jx = fx Rx[q] T(y_b, z_c)
+                        const real l = fval(g, (const real *)a.J[0], ax + q, ay + b, az + c, false);
+                        const real T = tshape(S0y[b], DSy[b], S0z[c], DSz[c]);
+                        gRx[q] += fx * T * l;
+                        Lw += a.jfac[0] * Rx[q] * T * l;
+                        const real k = fx * Rx[q] * l;
+                        gS0z[c] += k * dT0(S0y[b], DSy[b]);
+                        gDSz[c] += k * dT1(S0y[b], DSy[b]);
+                        if (DIM == 3) {
+                            gS0y[b] += k * dT0(S0z[c], DSz[c]);
+                            gDSy[b] += k * dT1(S0z[c], DSz[c]);
+                        }
+                    }
+                    if (DIM == 3) {
+                        if (b < 2) {  // Jy = fy Ry[b] T(z_c, x_q)
+                            const real l = fval(g, (const real *)a.J[1], ax + q, ay + b, az + c, false);
+                            const real T = tshape(S0z[c], DSz[c], S0x[q], DSx[q]);
+                            gRy[b] += fy * T * l;
+                            Lw += a.jfac[1] * Ry[b] * T * l;
+                            const real k = fy * Ry[b] * l;
+                            gS0z[c] += k * dT0(S0x[q], DSx[q]);
+                            gDSz[c] += k * dT1(S0x[q], DSx[q]);
+                            gS0x[q] += k * dT0(S0z[c], DSz[c]);
+                            gDSx[q] += k * dT1(S0z[c], DSz[c]);
+                        }
+                    } else {  // 2D out of plane: Jy = fy1 w T(x_q, z_c)
+                        const real l = fval(g, (const real *)a.J[1], ax + q, 0, az + c, false);
+                        Ly += tshape(S0x[q], DSx[q], S0z[c], DSz[c]) * l;
+                        const real k = fy1 * w * l;
+                        gS0x[q] += k * dT0(S0z[c], DSz[c]);
+                        gDSx[q] += k * dT1(S0z[c], DSz[c]);
+                        gS0z[c] += k * dT0(S0x[q], DSx[q]);
+                        gDSz[c] += k * dT1(S0x[q], DSx[q]);
+                    }
+                    if (c < 2) {  // Jz = fz Rz[c] T(x_q, y_b)
+                        const real l = fval(g, (const real *)a.J[2], ax + q, ay + b, az + c, true);
+                        const real T = tshape(S0x[q], DSx[q], S0y[b], DSy[b]);
+                        gRz[c] += fz * T * l;
+                        Lw += a.jfac[2] * Rz[c] * T * l;
+                        const real k = fz * Rz[c] * l;
+                        gS0x[q] += k * dT0(S0y[b], DSy[b]);
+                        gDSx[q] += k * dT1(S0y[b], DSy[b]);
+                        if (DIM == 3) {
+                            gS0y[b] += k * dT0(S0x[q], DSx[q]);
+                            gDSy[b] += k * dT1(S0x[q], DSx[q]);
+                        }
+                    }
                 }
-                {
-                    // Jy(q, c) = fy1 w (S0x za + DSx zb)
-                    const real l = lJy[q][c];
-                    const real shape = S0x[q] * za + DSx[q] * zb;
-                    Ly += shape * l;
-                    const real k = fy1 * w * l;
-                    gS0x[q] += k * za;
-                    gDSx[q] += k * zb;
-                    gS0z[c] += k * (S0x[q] + half * DSx[q]);
-                    gDSz[c] += k * (half * S0x[q] + third * DSx[q]);
-                }
-                if (c < 2) {
-                    // Jz(q, c) = fz Rz[c] xa[q]
-                    const real l = lJz[q][c];
-                    gRz[c] += fz * xa * l;
-                    gS0x[q] += fz * Rz[c] * l;
-                    gDSx[q] += half * fz * Rz[c] * l;
-                    Lw += a.jfac[2] * Rz[c] * xa * l;
-                }
-            }
-        Lw += fy1 * Ly;
+        if (DIM == 2) Lw += fy1 * Ly;
         // running sums: R[q] = sum_{q' <= q} DS[q']
         {
-            real acc = 0;
+            real sx_ = 0, sy_ = 0, sz_ = 0;
 #pragma unroll
-            for (int q = 2; q >= 0; --q) { acc += gRx[q]; gDSx[q] += acc; }
-            acc = 0;
-#pragma unroll
-            for (int c = 2; c >= 0; --c) { acc += gRz[c]; gDSz[c] += acc; }
+            for (int q = 2; q >= 0; --q) {
+                sx_ += gRx[q];
+                sy_ += gRy[q];
+                sz_ += gRz[q];
+                gDSx[q] += sx_;
+                gDSy[q] += sy_;
+                gDSz[q] += sz_;
+            }
         }
-        // DS = S1 - S0 on the window: dL/dS1 = gDS, dL/dS0 = gS0 - gDS; map the
-        // window nodes back to the two support nodes of x0 and x1
-        real lx1 = 0, lz1 = 0, lx0 = 0, lz0 = 0;
+        // DS = S1 - S0 on the window: dL/dS1 = gDS, dL/dS0 = gS0 - gDS; the
+        // supports of x0 and x1 start at window nodes b0 - an and b1 - an
+        real lx1 = 0, ly1 = 0, lz1 = 0, lx0 = 0, ly0 = 0, lz0 = 0;
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            // x0's support nodes b0x, b0x + 1 relative to the cell; x1's b1x, b1x + 1
-            const int r0 = (ci + b0x) - ax, r1 = (ci + b1x) - ax;
-            const real d0 = (q == r0) ? real(-1) : (q == r0 + 1 ? real(1) : real(0));
-            const real d1 = (q == r1) ? real(-1) : (q == r1 + 1 ? real(1) : real(0));
-            lx0 += (gS0x[q] - gDSx[q]) * d0;
-            lx1 += gDSx[q] * d1;
-            const int s0 = (ck + b0z) - az, s1 = (ck + b1z) - az;
-            const real e0 = (q == s0) ? real(-1) : (q == s0 + 1 ? real(1) : real(0));
-            const real e1 = (q == s1) ? real(-1) : (q == s1 + 1 ? real(1) : real(0));
-            lz0 += (gS0z[q] - gDSz[q]) * e0;
-            lz1 += gDSz[q] * e1;
+            lx0 += (gS0x[q] - gDSx[q]) * dshape<real>(q, b0x - anx);
+            lx1 += gDSx[q] * dshape<real>(q, b1x - anx);
+            lz0 += (gS0z[q] - gDSz[q]) * dshape<real>(q, b0z - anz);
+            lz1 += gDSz[q] * dshape<real>(q, b1z - anz);
+            if (DIM == 3) {
+                ly0 += (gS0y[q] - gDSy[q]) * dshape<real>(q, b0y - any_);
+                ly1 += gDSy[q] * dshape<real>(q, b1y - any_);
+            }
         }
-        // ---- move transposed: x1 = ox + vx dtdh_x, z1 = oz + dz_d + dvz dtdh_z
+        // ---- move transposed: x1 = ox + vx dtdh_x (and y), z1 = oz + dz_d + dvz dtdh_z
         lx1 += a.lx[p];
         lz1 += a.lz[p];
-        const real lvx = a.dtdh[0] * lx1, lvz = a.dtdh[1] * lz1;
-        const real lvy = a.jyfac * w * Ly;
+        if (DIM == 3) ly1 += a.ly[p];
+        const real lvx = a.dtdh[0] * lx1, lvz = a.dtdh[2] * lz1;
+        const real lvy = DIM == 3 ? a.dtdh[1] * ly1 : a.jyfac * w * Ly;
         // velocity transposed: v = u / gamma (u the full momentum), d v / d du
         // = (I - v v^T) / gamma; (I - v v^T) l = l / gamma^2 + v x (l x v)
         // (no cancellation when v is nearly along z)
@@ -375,14 +455,14 @@ __global__ void adj_push_vjp_kernel(AdjArgs<real> a)
         const real ig = rsqrt_p(drift.g2 + (uz * (real(2) * U + uz) + ux * ux + uy * uy));
         const real ig2 = ig * ig;
         const real cx = lvy * vz - lvz * vy, cy = lvz * vx - lvx * vz, cz = lvx * vy - lvy * vx;  // l x v
-        real lux = a.lux[p] + ig * (lvx * ig2 + (vy * cz - vz * cy));
-        real luy = a.luy[p] + ig * (lvy * ig2 + (vz * cx - vx * cz));
-        real luz = a.luz[p] + ig * (lvz * ig2 + (vx * cy - vy * cx));
+        const real lux = a.lux[p] + ig * (lvx * ig2 + (vy * cz - vz * cy));
+        const real luy = a.luy[p] + ig * (lvy * ig2 + (vz * cx - vx * cz));
+        const real luz = a.luz[p] + ig * (lvz * ig2 + (vx * cy - vy * cx));
         // ---- Boris transposed
         const real sx = bf.s[0], sy = bf.s[1], sz = bf.s[2], tx = bf.t[0], ty = bf.t[1], tz = bf.t[2];
         const real upx = bf.up[0], upy = bf.up[1], upz = bf.up[2];
         const real umx = bf.um[0], umy = bf.um[1], umz = bf.um[2];
-        const real s2 = bf.s2, sden = real(0.5) * bf.s2, fb = bf.fb, igm = bf.igm;
+        const real s2 = bf.s2, sden = half * bf.s2, fb = bf.fb, igm = bf.igm;
         real lE[3] = {eps * lux, eps * luy, eps * luz};  // the last half kick
         real ldmx = lux, ldmy = luy, ldmz = luz;
         // u += up x s: lup = s x lu, ls = lu x up
@@ -399,7 +479,7 @@ __global__ void adj_push_vjp_kernel(AdjArgs<real> a)
         lty += s2 * lsy - real(2) * s2 * sden * ty * tl;
         ltz += s2 * lsz - real(2) * s2 * sden * tz * tl;
         // t = fb B, fb = eps / gamma_m
-        real lB[3] = {fb * ltx, fb * lty, fb * ltz};
+        const real lB[3] = {fb * ltx, fb * lty, fb * ltz};
         const real lfb = gf.f[3] * ltx + gf.f[4] * lty + gf.f[5] * ltz;
         const real kf = -lfb * fb * igm * igm;  // d fb / d um = -fb um / gamma_m^2
         lumx += kf * umx;
@@ -421,16 +501,21 @@ __global__ void adj_push_vjp_kernel(AdjArgs<real> a)
 #pragma unroll
             for (int cc = 0; cc < 2; ++cc)
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const real v = fval(g, F, gf.bx[c] + q, gf.bz[c] + cc, hz_of(c));
-                    lx0 += l * (q ? real(1) : real(-1)) * gf.wz[c][cc] * v;
-                    lz0 += l * gf.wx[c][q] * (cc ? real(1) : real(-1)) * v;
-                    fadd(g, LF, gf.bx[c] + q, gf.bz[c] + cc, hz_of(c), l * gf.wx[c][q] * gf.wz[c][cc]);
-                }
+                for (int b = 0; b < (DIM == 3 ? 2 : 1); ++b)
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const real v = fval(g, F, gf.bx[c] + q, gf.by[c] + b, gf.bz[c] + cc, hz_of(c));
+                        const real wxq = gf.wx[c][q], wyb = gf.wy[c][b], wzc = gf.wz[c][cc];
+                        lx0 += l * (q ? real(1) : real(-1)) * wyb * wzc * v;
+                        if (DIM == 3) ly0 += l * wxq * (b ? real(1) : real(-1)) * wzc * v;
+                        lz0 += l * wxq * wyb * (cc ? real(1) : real(-1)) * v;
+                        fadd(g, LF, gf.bx[c] + q, gf.by[c] + b, gf.bz[c] + cc, hz_of(c), l * wxq * wyb * wzc);
+                    }
         }
         // ---- write the cotangents of x^n, du^{n-1/2}; the weight's
         a.lx[p] = lx1 + lx0;
         a.lz[p] = lz1 + lz0;
+        if (DIM == 3) a.ly[p] = ly1 + ly0;
         a.lux[p] = ldmx;
         a.luy[p] = ldmy;
         a.luz[p] = ldmz;
@@ -440,67 +525,70 @@ __global__ void adj_push_vjp_kernel(AdjArgs<real> a)
 
 // Weight cotangents of the drifting ions of one step (their positions do not
 // depend on the parameters).
-template <typename real>
+template <typename real, int DIM>
 __global__ void adj_ion_vjp_kernel(AdjArgs<real> a)
 {
     const Geom &g = a.g;
-    const Drift<real> drift(a.u_drift, a.dtdh[1]);
+    const Drift<real> drift(a.u_drift, a.dtdh[2]);
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
         if (!a.iin.alive[p]) continue;
-        const int ci = a.ion_ci[p], ck = a.iin.ck[p];
-        const real ox = a.ion_ox[p], oz = a.iin.oz[p];
+        const int ci = a.ion_ci[p], cj = DIM == 3 ? a.ion_cj[p] : 0, ck = a.iin.ck[p];
+        const real ox = a.ion_ox[p], oy = DIM == 3 ? a.ion_oy[p] : real(0), oz = a.iin.oz[p];
         const real z1 = add_rn(oz, drift.dz);
-        real S0z[3], DSz[3], wx[2];
+        real S0z[3], DSz[3], wx[2], wy[2] = {1, 0};
         bool cr;
         const int az = ck + esirk_axis_c<1>(oz, z1, S0z, DSz, cr);
         offset_weights<1>(ox, wx);
+        if (DIM == 3) offset_weights<1>(oy, wy);
         real acc = 0, L = 0;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             acc += DSz[c];
 #pragma unroll
-            for (int q = 0; q < 2; ++q) L += acc * wx[q] * fval(g, (const real *)a.J[2], ci + q, az + c, true);
+            for (int b = 0; b < (DIM == 3 ? 2 : 1); ++b)
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+                    L += acc * wx[q] * wy[b] * fval(g, (const real *)a.J[2], ci + q, cj + b, az + c, true);
         }
         a.lw[p] += (double)(a.jfac_iz * L);
     }
 }
 
-// lE += (transpose of B -= h curl E) applied to lB (2D): the gather form of
-// the scatter of every B update onto the E nodes it read.
+// lE += (transpose of B -= h curl E) applied to lB: the gather form of the
+// scatter of every B update onto the E nodes it read (hy_ unused in 2D).
 template <typename real>
 __global__ void adj_curl_e_t_kernel(Geom g, real *lEx, real *lEy, real *lEz, const real *lBx, const real *lBy,
-                                    const real *lBz, real hz_, real hx_)
+                                    const real *lBz, real hz_, real hx_, real hy_)
 {
-    const bool per = g.bc_z == 0;
+    const bool per = g.bc_z == 0, d3 = g.dim == 3;
     const int nk = per ? g.nz : g.nz + 1;
-    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < (int64_t)nk * g.nx;
+    const int64_t plane = g.plane;
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < (int64_t)nk * plane;
          o += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(o % g.nx), k = (int)(o / g.nx);
-        const int im = i == 0 ? g.nx - 1 : i - 1;
-        // B components at half-integer z (Bx, By) exist for k' in [0, nz); Bz on
-        // the E planes
-        auto bh = [&](const real *B, int ii, int kk) -> real {
+        const int i = (int)(o % g.nx), j = (int)((o / g.nx) % g.ny), k = (int)(o / plane);
+        const int im = i == 0 ? g.nx - 1 : i - 1, jm = j == 0 ? g.ny - 1 : j - 1;
+        // B on half-integer z (Bx, By) exists for k' in [0, nz); Bz on the E planes
+        auto bh = [&](const real *B, int ii, int jj, int kk) -> real {
             if (per) kk = wrapi(kk, g.nz);
             else if (kk < 0 || kk >= g.nz) return real(0);
-            return B[(int64_t)kk * g.nx + ii];
+            return B[((int64_t)kk * g.ny + jj) * g.nx + ii];
         };
-        auto bi = [&](const real *B, int ii, int kk) -> real {
-            return B[(int64_t)kk * g.nx + ii];
-        };
-        // Ex(i+1/2, k): By(i+1/2, k+1/2) -= h (Ex[k+1] - Ex[k]) / hz
-        lEx[o] += hz_ * (bh(lBy, i, k) - bh(lBy, i, k - 1));
-        // Ey(i, k): Bx(i, k+1/2) += h (Ey[k+1] - Ey[k]) / hz; Bz(i+1/2, k) -= h (Ey[i+1] - Ey[i]) / hx
-        lEy[o] += hz_ * (bh(lBx, i, k - 1) - bh(lBx, i, k)) + hx_ * (bi(lBz, i, k) - bi(lBz, im, k));
-        // Ez(i, k+1/2): By(i+1/2, k+1/2) += h (Ez[i+1] - Ez[i]) / hx
-        if (k < g.nz) lEz[o] += hx_ * (bi(lBy, im, k) - bi(lBy, i, k));
+        auto bi = [&](const real *B, int ii, int jj, int kk) -> real { return B[((int64_t)kk * g.ny + jj) * g.nx + ii]; };
+        lEx[o] += hz_ * (bh(lBy, i, j, k) - bh(lBy, i, j, k - 1));
+        lEy[o] += hz_ * (bh(lBx, i, j, k - 1) - bh(lBx, i, j, k)) + hx_ * (bi(lBz, i, j, k) - bi(lBz, im, j, k));
+        if (d3) lEx[o] += hy_ * (bi(lBz, i, jm, k) - bi(lBz, i, j, k));
+        if (k < g.nz) {
+            lEz[o] += hx_ * (bi(lBy, im, j, k) - bi(lBy, i, j, k));
+            if (d3) lEz[o] += hy_ * (bi(lBx, i, j, k) - bi(lBx, i, jm, k));
+        }
     }
 }
 
-// The E update transposed (2D).  From lE1 (cotangent of E^{n+1} after the
-// B half step has been transposed) it forms the cotangent of the interior
-// update's output (Mur's condition transposed first: the boundary values were
-// computed from E^n and the new interior values next to them), the current
-// cotangent lJ = -2 pi dt lE1' and the cotangent of E^n, lE0.
+// The E update transposed.  From lE1 (cotangent of E^{n+1} after the B half
+// step has been transposed) it forms the cotangent of the interior update's
+// output (Mur's condition transposed first: the boundary values were computed
+// from E^n and the new interior values next to them), the current cotangent
+// lJ = -2 pi dt lE1' and the cotangent of E^n, lE0.
 template <typename real>
 __global__ void adj_e_update_t_kernel(Geom g, const real *lE1x, const real *lE1y, const real *lE1z, real *pEx,
                                       real *pEy, real *pEz, real *lE0x, real *lE0y, real *lE0z, real *lJx,
@@ -508,11 +596,12 @@ __global__ void adj_e_update_t_kernel(Geom g, const real *lE1x, const real *lE1y
 {
     const bool per = g.bc_z == 0;
     const int nk = g.nz + 1;
-    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < (int64_t)nk * g.nx;
+    const int64_t plane = g.plane;
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < (int64_t)nk * plane;
          o += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(o % g.nx), k = (int)(o / g.nx);
-        const int64_t top = (int64_t)g.nz * g.nx + i;
-        // Ex, Ey
+        const int k = (int)(o / plane);
+        const int64_t r = o - (int64_t)k * plane;  // node within the plane
+        const int64_t top = (int64_t)g.nz * plane + r;
         for (int c = 0; c < 2; ++c) {
             const real *L1 = c == 0 ? lE1x : lE1y;
             real *P = c == 0 ? pEx : pEy;
@@ -524,7 +613,7 @@ __global__ void adj_e_update_t_kernel(Geom g, const real *lE1x, const real *lE1y
             } else if (k >= 1 && k <= g.nz - 1) {
                 vp = L1[o];
                 v0 = L1[o];
-                if (k == 1) { vp += cm * L1[i]; v0 += cm * L1[i] + L1[i]; }
+                if (k == 1) { vp += cm * L1[r]; v0 += cm * L1[r] + L1[r]; }
                 if (k == g.nz - 1) { vp += cm * L1[top]; v0 += cm * L1[top] + L1[top]; }
             } else {
                 v0 = -cm * L1[o];  // k = 0 or nz: E^n of the boundary node itself
@@ -533,7 +622,6 @@ __global__ void adj_e_update_t_kernel(Geom g, const real *lE1x, const real *lE1y
             L0[o] = v0;
             LJ[o] = m2pidt * vp;
         }
-        // Ez (k < nz), no boundary condition
         const real vz = k < g.nz ? lE1z[o] : real(0);
         pEz[o] = vz;
         lE0z[o] = vz;
@@ -541,48 +629,56 @@ __global__ void adj_e_update_t_kernel(Geom g, const real *lE1x, const real *lE1y
     }
 }
 
-// lB += dt (curl B)^T applied to lE' (2D): the gather form of the scatter of
-// the E interior updates onto the B nodes they read.
+// lB += dt (curl B)^T applied to lE': the gather form of the scatter of the E
+// interior updates onto the B nodes they read.
 template <typename real>
 __global__ void adj_curl_b_t_kernel(Geom g, const real *pEx, const real *pEy, const real *pEz, real *lBx,
-                                    real *lBy, real *lBz, real dthz, real dthx)
+                                    real *lBy, real *lBz, real dthz, real dthx, real dthy)
 {
-    const bool per = g.bc_z == 0;
+    const bool per = g.bc_z == 0, d3 = g.dim == 3;
     const int nk = g.nz + 1;
-    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < (int64_t)nk * g.nx;
+    const int64_t plane = g.plane;
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < (int64_t)nk * plane;
          o += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(o % g.nx), k = (int)(o / g.nx);
-        const int ip = i + 1 == g.nx ? 0 : i + 1;
-        auto pe = [&](const real *P, int ii, int kk) -> real {  // E' on the integer-z planes
+        const int i = (int)(o % g.nx), j = (int)((o / g.nx) % g.ny), k = (int)(o / plane);
+        const int ip = i + 1 == g.nx ? 0 : i + 1, jp = j + 1 == g.ny ? 0 : j + 1;
+        auto pe = [&](const real *P, int ii, int jj, int kk) -> real {  // E' on the integer-z planes
             if (per) kk = wrapi(kk, g.nz);
             else if (kk < 0 || kk > g.nz) return real(0);
-            return P[(int64_t)kk * g.nx + ii];
+            return P[((int64_t)kk * g.ny + jj) * g.nx + ii];
         };
+        auto at = [&](const real *P, int ii, int jj) -> real { return P[((int64_t)k * g.ny + jj) * g.nx + ii]; };
         if (k < g.nz) {
-            // By(i+1/2, k+1/2): Ex[k] -= dt (By[k] - By[k-1]) / hz; Ez[i] += dt (By[i] - By[i-1]) / hx
-            lBy[o] += dthz * (pe(pEx, i, k + 1) - pe(pEx, i, k)) + dthx * (pEz[o] - pEz[(int64_t)k * g.nx + ip]);
-            // Bx(i, k+1/2): Ey[k] += dt (Bx[k] - Bx[k-1]) / hz
-            lBx[o] += dthz * (pe(pEy, i, k) - pe(pEy, i, k + 1));
+            lBy[o] += dthz * (pe(pEx, i, j, k + 1) - pe(pEx, i, j, k)) + dthx * (at(pEz, i, j) - at(pEz, ip, j));
+            lBx[o] += dthz * (pe(pEy, i, j, k) - pe(pEy, i, j, k + 1));
+            if (d3) lBx[o] += dthy * (at(pEz, i, jp) - at(pEz, i, j));
         }
         if (k < g.nz || !per) {
-            // Bz(i+1/2, k): Ey[i] -= dt (Bz[i] - Bz[i-1]) / hx
-            lBz[o] += dthx * (pEy[(int64_t)k * g.nx + ip] - pEy[o]);
+            lBz[o] += dthx * (at(pEy, ip, j) - at(pEy, i, j));
+            if (d3) lBz[o] += dthy * (at(pEx, i, j) - at(pEx, i, jp));
         }
     }
 }
 
 // Sums over the antenna plane: s[0] += j0u sum lJ g, s[1] += j0w sum lJ g r^2
-// (g = exp(-r^2 / w0^2) as in the forward), for the a0 and w0 cotangents.
+// (g = exp(-r^2 / w0^2) at each node's own staggered transverse position, as
+// in the forward), for the a0 and w0 cotangents.
 template <typename real>
-__global__ void adj_antenna_kernel(Geom g, const real *lJ, int pol, int ka, double hx, double xc, double inv_w2,
-                                   double fa, double fw, double *s)
+__global__ void adj_antenna_kernel(Geom g, const real *lJ, int pol, int ka, double hx, double hy, double xc,
+                                   double yc, double inv_w2, double fa, double fw, double *s)
 {
     double s0 = 0, s1 = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.nx; i += gridDim.x * blockDim.x) {
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < g.plane;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(o % g.nx), j = (int)(o / g.nx);
         const double x = ((double)i + (pol == 0 ? 0.5 : 0.0)) * hx - xc;
-        const double r2 = x * x;
+        double r2 = x * x;
+        if (g.dim == 3) {
+            const double y = ((double)j + (pol == 1 ? 0.5 : 0.0)) * hy - yc;
+            r2 += y * y;
+        }
         const double gg = exp(-r2 * inv_w2);
-        const double l = (double)lJ[(int64_t)ka * g.nx + i];
+        const double l = (double)lJ[(int64_t)ka * g.plane + o];
         s0 += l * gg;
         s1 += l * gg * r2;
     }
@@ -609,55 +705,61 @@ __global__ void adj_profile_kernel(int64_t n, const double *lw, const void *w, i
 
 // --------------------------------------------------------------- launchers
 
+#define PIC_ADJ_LAUNCH(kernel)                                                                  \
+    if (a.n <= 0) return;                                                                       \
+    if (a.g.dim == 3) kernel<real, 3><<<adj_grid(a.n, 256), 256, 0, s>>>(a);                    \
+    else kernel<real, 2><<<adj_grid(a.n, 256), 256, 0, s>>>(a);
+
 template <typename real>
 void launch_adj_push(const AdjArgs<real> &a, cudaStream_t s)
 {
-    if (a.n > 0) adj_push_kernel<real><<<adj_grid(a.n, 256), 256, 0, s>>>(a);
+    PIC_ADJ_LAUNCH(adj_push_kernel)
 }
 template <typename real>
 void launch_adj_ions(const AdjArgs<real> &a, cudaStream_t s)
 {
-    if (a.n > 0) adj_ion_kernel<real><<<adj_grid(a.n, 256), 256, 0, s>>>(a);
+    PIC_ADJ_LAUNCH(adj_ion_kernel)
 }
 template <typename real>
 void launch_adj_push_vjp(const AdjArgs<real> &a, cudaStream_t s)
 {
-    if (a.n > 0) adj_push_vjp_kernel<real><<<adj_grid(a.n, 256), 256, 0, s>>>(a);
+    PIC_ADJ_LAUNCH(adj_push_vjp_kernel)
 }
 template <typename real>
 void launch_adj_ion_vjp(const AdjArgs<real> &a, cudaStream_t s)
 {
-    if (a.n > 0) adj_ion_vjp_kernel<real><<<adj_grid(a.n, 256), 256, 0, s>>>(a);
+    PIC_ADJ_LAUNCH(adj_ion_vjp_kernel)
 }
+#undef PIC_ADJ_LAUNCH
 
 // the Yee step transposed: (lE, lB) at n+1 -> (lE, lB) at n and lJ (the
 // cotangent of the filtered current); lE0 and pE are work components
 template <typename real>
 void launch_adj_yee(const Geom &g, real *lE[3], real *lB[3], real *lE0[3], real *pE[3], real *lJ[3], double dt,
-                    double hx, double hz, cudaStream_t s)
+                    double hx, double hy, double hz, cudaStream_t s)
 {
-    const unsigned grid = adj_grid((int64_t)(g.nz + 1) * g.nx, 256);
+    const unsigned grid = adj_grid((int64_t)(g.nz + 1) * g.plane, 256);
     const real h = (real)(0.5 * dt);
     // B^{n+1} = B' - h curl E^{n+1}
     adj_curl_e_t_kernel<real><<<grid, 256, 0, s>>>(g, lE[0], lE[1], lE[2], lB[0], lB[1], lB[2], (real)(h / hz),
-                                                  (real)(h / hx));
+                                                  (real)(h / hx), (real)(h / hy));
     // E^{n+1} = E^n + dt (curl B' - 2 pi J), Mur on the z ends
     adj_e_update_t_kernel<real><<<grid, 256, 0, s>>>(g, lE[0], lE[1], lE[2], pE[0], pE[1], pE[2], lE0[0], lE0[1],
                                                     lE0[2], lJ[0], lJ[1], lJ[2], (real)((dt - hz) / (dt + hz)),
                                                     (real)(-kTwoPiD * dt));
     adj_curl_b_t_kernel<real><<<grid, 256, 0, s>>>(g, pE[0], pE[1], pE[2], lB[0], lB[1], lB[2], (real)(dt / hz),
-                                                  (real)(dt / hx));
+                                                  (real)(dt / hx), (real)(dt / hy));
     // B' = B^n - h curl E^n
     adj_curl_e_t_kernel<real><<<grid, 256, 0, s>>>(g, lE0[0], lE0[1], lE0[2], lB[0], lB[1], lB[2], (real)(h / hz),
-                                                  (real)(h / hx));
+                                                  (real)(h / hx), (real)(h / hy));
 }
 
 template <typename real>
-void launch_adj_antenna(const Geom &g, const real *lJ, int pol, int ka, double hx, double xc, double waist,
-                        double fa, double fw, double *s, cudaStream_t st)
+void launch_adj_antenna(const Geom &g, const real *lJ, int pol, int ka, double hx, double hy, double xc, double yc,
+                        double waist, double fa, double fw, double *s, cudaStream_t st)
 {
-    adj_antenna_kernel<real><<<adj_grid(g.nx, 256), 256, 0, st>>>(g, lJ, pol, ka, hx, xc, 1.0 / (waist * waist), fa,
-                                                                   fw, s);
+    adj_antenna_kernel<real><<<adj_grid(g.plane, 256), 256, 0, st>>>(g, lJ, pol, ka, hx, hy, xc, yc,
+                                                                      1.0 / (waist * waist), fa, fw, s);
 }
 
 void launch_adj_profile(int64_t n, const double *lw, const void *w, int precision, const double *zeta, int M,
@@ -672,9 +774,9 @@ void launch_adj_profile(int64_t n, const double *lw, const void *w, int precisio
     template void launch_adj_push_vjp<real>(const AdjArgs<real> &, cudaStream_t);                              \
     template void launch_adj_ion_vjp<real>(const AdjArgs<real> &, cudaStream_t);                               \
     template void launch_adj_yee<real>(const Geom &, real *[3], real *[3], real *[3], real *[3], real *[3],     \
-                                       double, double, double, cudaStream_t);                                  \
+                                       double, double, double, double, cudaStream_t);                          \
     template void launch_adj_antenna<real>(const Geom &, const real *, int, int, double, double, double, double, \
-                                           double, double *, cudaStream_t);
+                                           double, double, double, double *, cudaStream_t);
 PIC_ADJ_INSTANTIATE(float)
 PIC_ADJ_INSTANTIATE(double)
 #undef PIC_ADJ_INSTANTIATE

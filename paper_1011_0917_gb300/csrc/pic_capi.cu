@@ -1721,19 +1721,20 @@ namespace {
 struct AdjLayout {
     int64_t P = 0;
     int N = 0, K = 0, C = 0;
-    size_t w = 0, zeta = 0, ion_ci = 0, ion_ox = 0;  // per slot, constant
+    size_t w = 0, zeta = 0, ion_ci = 0, ion_ox = 0, ion_cj = 0, ion_oy = 0;  // per slot, constant
     size_t st = 0, fl = 0;                           // one particle state, one field state (6 comps)
     size_t ckpt = 0, seg = 0;                        // C and K + 1 (state, fields) pairs
     size_t J = 0, tmp = 0, lE = 0, lB = 0, lE0 = 0, pE = 0, lJ = 0;  // 3 components each
-    size_t lx = 0, lz = 0, lux = 0, luy = 0, luz = 0, lw = 0, acc = 0, coef = 0;
+    size_t lx = 0, ly = 0, lz = 0, lux = 0, luy = 0, luz = 0, lw = 0, acc = 0, coef = 0;
     size_t total = 0;
     // inside one particle state
-    size_t e_ci = 0, e_ck = 0, e_ox = 0, e_oz = 0, e_ux = 0, e_uy = 0, e_uz = 0, e_alive = 0;
+    size_t e_ci = 0, e_cj = 0, e_ck = 0, e_ox = 0, e_oy = 0, e_oz = 0, e_ux = 0, e_uy = 0, e_uz = 0, e_alive = 0;
     size_t i_ck = 0, i_oz = 0, i_alive = 0;
 };
 
-AdjLayout adj_layout(int64_t P, int N, int K, size_t es, int64_t ncomp)
+AdjLayout adj_layout(int64_t P, int N, int K, size_t es, int64_t ncomp, bool dim3)
 {
+    const int64_t P3 = dim3 ? P : 0;  // y arrays only in 3D
     AdjLayout L;
     L.P = P;
     L.N = N;
@@ -1753,8 +1754,10 @@ AdjLayout adj_layout(int64_t P, int N, int K, size_t es, int64_t ncomp)
         return at;
     };
     L.e_ci = sub(4 * P);
+    L.e_cj = sub(4 * P3);
     L.e_ck = sub(4 * P);
     L.e_ox = sub(es * P);
+    L.e_oy = sub(es * P3);
     L.e_oz = sub(es * P);
     L.e_ux = sub(es * P);
     L.e_uy = sub(es * P);
@@ -1769,6 +1772,8 @@ AdjLayout adj_layout(int64_t P, int N, int K, size_t es, int64_t ncomp)
     L.zeta = take(8 * P);
     L.ion_ci = take(4 * P);
     L.ion_ox = take(es * P);
+    L.ion_cj = take(4 * P3);
+    L.ion_oy = take(es * P3);
     L.ckpt = take((size_t)L.C * (L.st + L.fl));
     L.seg = take((size_t)(K + 1) * (L.st + L.fl));
     L.J = take(3 * es * ncomp);
@@ -1779,6 +1784,7 @@ AdjLayout adj_layout(int64_t P, int N, int K, size_t es, int64_t ncomp)
     L.pE = take(3 * es * ncomp);
     L.lJ = take(3 * es * ncomp);
     L.lx = take(es * P);
+    L.ly = take(es * P3);
     L.lz = take(es * P);
     L.lux = take(es * P);
     L.luy = take(es * P);
@@ -1795,8 +1801,10 @@ FlatE<real> flat_e(unsigned char *st, const AdjLayout &L)
 {
     FlatE<real> e;
     e.ci = (int *)(st + L.e_ci);
+    e.cj = (int *)(st + L.e_cj);
     e.ck = (int *)(st + L.e_ck);
     e.ox = (real *)(st + L.e_ox);
+    e.oy = (real *)(st + L.e_oy);
     e.oz = (real *)(st + L.e_oz);
     e.ux = (real *)(st + L.e_ux);
     e.uy = (real *)(st + L.e_uy);
@@ -1844,8 +1852,7 @@ static pic_status adj_check(pic_ctx *c, const pic_adjoint_params *p)
     if (!c || !p) return PIC_ERR_ARG;
     if (!c->bound) return fail(c, PIC_ERR_STATE, "bind buffers first");
     if (p->nsteps < 1 || p->checkpoint_every < 1) return fail(c, PIC_ERR_ARG, "invalid adjoint parameters");
-    if (c->g.dim != 2 || c->p.shape_order != 1)
-        return fail(c, PIC_ERR_ARG, "the adjoint covers 2D3V runs with the CIC shape");
+    if (c->p.shape_order != 1) return fail(c, PIC_ERR_ARG, "the adjoint covers the CIC shape");
     if (c->win_on) return fail(c, PIC_ERR_ARG, "the adjoint does not cover a moving window");
     if (!c->plasma_loaded || c->step != 0)
         return fail(c, PIC_ERR_STATE, "the adjoint starts right after pic_load_plasma (no step taken)");
@@ -1858,8 +1865,61 @@ extern "C" pic_status pic_adjoint_bytes(pic_ctx *c, const pic_adjoint_params *p,
     if (st != PIC_OK) return st;
     if (!bytes) return PIC_ERR_ARG;
     adj_bands(c, p->nsteps);
-    *bytes = adj_layout(c->adj.P, p->nsteps, p->checkpoint_every, (size_t)c->es, c->g.ncomp).total;
+    *bytes = adj_layout(c->adj.P, p->nsteps, p->checkpoint_every, (size_t)c->es, c->g.ncomp, c->g.dim == 3).total;
     return PIC_OK;
+}
+
+// the arguments every adjoint kernel of a step shares
+template <typename real>
+static void adj_common(pic_ctx *c, const AdjLayout &L, AdjArgs<real> &a)
+{
+    unsigned char *B = c->adj.buf;
+    a.g = c->g;
+    a.w = (const real *)(B + L.w);
+    a.ion_ci = (const int *)(B + L.ion_ci);
+    a.ion_cj = (const int *)(B + L.ion_cj);
+    a.ion_ox = (const real *)(B + L.ion_ox);
+    a.ion_oy = (const real *)(B + L.ion_oy);
+    a.n = L.P;
+    a.dtdh[0] = (real)(c->dt / c->hx);
+    a.dtdh[1] = (real)(c->dt / c->hy);
+    a.dtdh[2] = (real)(c->dt / c->hz);
+    a.eps = (real)(kPi * -1.0 * c->dt);
+    a.u_drift = drift_u<real>(c);
+    // electrons (q = -1): -q h_d / (dt V); 2D out-of-plane q / V; ions (q = +1)
+    a.jfac[0] = (real)(1.0 * c->hx / (c->dt * c->vol));
+    a.jfac[1] = (real)(1.0 * c->hy / (c->dt * c->vol));
+    a.jfac[2] = (real)(1.0 * c->hz / (c->dt * c->vol));
+    a.jyfac = (real)(-1.0 / c->vol);
+    a.jfac_iz = (real)(-1.0 * c->hz / (c->dt * c->vol));
+}
+
+// the flat-output pointers of an injection into state st
+template <typename real>
+static void adj_inject_out(pic_ctx *c, const AdjLayout &L, unsigned char *st, InjectArgs &ia)
+{
+    unsigned char *B = c->adj.buf;
+    FlatE<real> e = flat_e<real>(st, L);
+    FlatI<real> i = flat_i<real>(st, L);
+    ia.fe_ci = e.ci;
+    ia.fe_cj = e.cj;
+    ia.fe_ck = e.ck;
+    ia.fe_ox = e.ox;
+    ia.fe_oy = e.oy;
+    ia.fe_oz = e.oz;
+    ia.fe_ux = e.ux;
+    ia.fe_uy = e.uy;
+    ia.fe_uz = e.uz;
+    ia.fe_alive = e.alive;
+    ia.fi_ck = i.ck;
+    ia.fi_oz = i.oz;
+    ia.fi_alive = i.alive;
+    ia.f_ion_ci = (int *)(B + L.ion_ci);
+    ia.f_ion_cj = (int *)(B + L.ion_cj);
+    ia.f_ion_ox = B + L.ion_ox;
+    ia.f_ion_oy = B + L.ion_oy;
+    ia.f_w = B + L.w;
+    ia.f_zeta = (double *)(B + L.zeta);
 }
 
 // one flat step n: state/fields slot a -> slot b
@@ -1882,19 +1942,7 @@ static void adj_step(pic_ctx *c, const AdjLayout &L, unsigned char *sa, unsigned
     a.out = flat_e<real>(sb, L);
     a.iin = flat_i<real>(sa, L);
     a.iout = flat_i<real>(sb, L);
-    a.w = (const real *)(B + L.w);
-    a.ion_ci = (const int *)(B + L.ion_ci);
-    a.ion_ox = (const real *)(B + L.ion_ox);
-    a.n = L.P;
-    a.dtdh[0] = (real)(c->dt / c->hx);
-    a.dtdh[1] = (real)(c->dt / c->hz);
-    a.eps = (real)(kPi * -1.0 * c->dt);
-    a.u_drift = drift_u<real>(c);
-    a.jfac[0] = (real)(1.0 * c->hx / (c->dt * c->vol));
-    a.jfac[1] = (real)(1.0 * c->hy / (c->dt * c->vol));
-    a.jfac[2] = (real)(1.0 * c->hz / (c->dt * c->vol));
-    a.jyfac = (real)(-1.0 / c->vol);
-    a.jfac_iz = (real)(-1.0 * c->hz / (c->dt * c->vol));
+    adj_common<real>(c, L, a);
     launch_adj_push<real>(a, c->stream);
     if (c->ions_species) launch_adj_ions<real>(a, c->stream);
     real *Jc[3] = {J, J + nc, J + 2 * nc};
@@ -1921,23 +1969,7 @@ static void adj_step(pic_ctx *c, const AdjLayout &L, unsigned char *sa, unsigned
         ia.m_lo = c->adj.mlo[n + 1];
         ia.m_hi = c->adj.mhi[n + 1];
         ia.flat_base = c->adj.base[n + 1];
-        FlatE<real> e = flat_e<real>(sb, L);
-        FlatI<real> i = flat_i<real>(sb, L);
-        ia.fe_ci = e.ci;
-        ia.fe_ck = e.ck;
-        ia.fe_ox = e.ox;
-        ia.fe_oz = e.oz;
-        ia.fe_ux = e.ux;
-        ia.fe_uy = e.uy;
-        ia.fe_uz = e.uz;
-        ia.fe_alive = e.alive;
-        ia.fi_ck = i.ck;
-        ia.fi_oz = i.oz;
-        ia.fi_alive = i.alive;
-        ia.f_ion_ci = (int *)(B + L.ion_ci);
-        ia.f_ion_ox = B + L.ion_ox;
-        ia.f_w = B + L.w;
-        ia.f_zeta = (double *)(B + L.zeta);
+        adj_inject_out<real>(c, L, sb, ia);
         launch_inject(ia, c->stream);
     }
 }
@@ -1946,7 +1978,7 @@ template <typename real>
 static pic_status adj_forward_t(pic_ctx *c, const pic_adjoint_params *p, void *fields_out)
 {
     auto &A = c->adj;
-    const AdjLayout L = adj_layout(A.P, p->nsteps, p->checkpoint_every, sizeof(real), c->g.ncomp);
+    const AdjLayout L = adj_layout(A.P, p->nsteps, p->checkpoint_every, sizeof(real), c->g.ncomp, c->g.dim == 3);
     unsigned char *B = A.buf;
     unsigned char *seg = B + L.seg;
     auto st = [&](int s) { return seg + (size_t)s * (L.st + L.fl); };
@@ -1970,23 +2002,7 @@ static pic_status adj_forward_t(pic_ctx *c, const pic_adjoint_params *p, void *f
         ia.m_lo = A.mlo[0];
         ia.m_hi = A.mhi[0];
         ia.flat_base = 0;
-        FlatE<real> e = flat_e<real>(st(0), L);
-        FlatI<real> i = flat_i<real>(st(0), L);
-        ia.fe_ci = e.ci;
-        ia.fe_ck = e.ck;
-        ia.fe_ox = e.ox;
-        ia.fe_oz = e.oz;
-        ia.fe_ux = e.ux;
-        ia.fe_uy = e.uy;
-        ia.fe_uz = e.uz;
-        ia.fe_alive = e.alive;
-        ia.fi_ck = i.ck;
-        ia.fi_oz = i.oz;
-        ia.fi_alive = i.alive;
-        ia.f_ion_ci = (int *)(B + L.ion_ci);
-        ia.f_ion_ox = B + L.ion_ox;
-        ia.f_w = B + L.w;
-        ia.f_zeta = (double *)(B + L.zeta);
+        adj_inject_out<real>(c, L, st(0), ia);
         launch_inject(ia, c->stream);
     }
     for (int n = 0; n < L.N; ++n) {
@@ -2011,7 +2027,7 @@ extern "C" pic_status pic_adjoint_forward(pic_ctx *c, const pic_adjoint_params *
     if (s != PIC_OK) return s;
     if (!buf) return PIC_ERR_ARG;
     adj_bands(c, p->nsteps);
-    if (bytes < adj_layout(c->adj.P, p->nsteps, p->checkpoint_every, (size_t)c->es, c->g.ncomp).total)
+    if (bytes < adj_layout(c->adj.P, p->nsteps, p->checkpoint_every, (size_t)c->es, c->g.ncomp, c->g.dim == 3).total)
         return fail(c, PIC_ERR_ARG, "adjoint buffer too small");
     c->adj.buf = (unsigned char *)buf;
     c->adj.bytes = bytes;
@@ -2023,7 +2039,7 @@ template <typename real>
 static pic_status adj_backward_t(pic_ctx *c, const void *cot, double *grad)
 {
     auto &A = c->adj;
-    const AdjLayout L = adj_layout(A.P, A.N, A.K, sizeof(real), c->g.ncomp);
+    const AdjLayout L = adj_layout(A.P, A.N, A.K, sizeof(real), c->g.ncomp, c->g.dim == 3);
     unsigned char *B = A.buf;
     const int64_t nc = c->g.ncomp;
     unsigned char *seg = B + L.seg;
@@ -2043,6 +2059,7 @@ static pic_status adj_backward_t(pic_ctx *c, const void *cot, double *grad)
     CUDA_TRY(c, cudaMemcpyAsync(lB[0], (const unsigned char *)cot + cb, cb, cudaMemcpyDeviceToDevice, c->stream));
     for (size_t off : {L.lx, L.lz, L.lux, L.luy, L.luz})
         CUDA_TRY(c, cudaMemsetAsync(B + off, 0, sizeof(real) * L.P, c->stream));
+    if (c->g.dim == 3) CUDA_TRY(c, cudaMemsetAsync(B + L.ly, 0, sizeof(real) * L.P, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(B + L.lw, 0, 8 * L.P, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(B + L.acc, 0, 16, c->stream));
     const pic_laser_params &l = c->laser;
@@ -2053,15 +2070,16 @@ static pic_status adj_backward_t(pic_ctx *c, const void *cot, double *grad)
         for (int s = 0; s < n1 - n0; ++s) adj_step<real>(c, L, st(s), st(s + 1), fl(s), fl(s + 1), n0 + s);
         for (int s = n1 - n0 - 1; s >= 0; --s) {
             const int n = n0 + s;
-            launch_adj_yee<real>(c->g, lE, lB, lE0, pE, lJ, c->dt, c->hx, c->hz, c->stream);
+            launch_adj_yee<real>(c->g, lE, lB, lE0, pE, lJ, c->dt, c->hx, c->hy, c->hz, c->stream);
             for (int q = 0; q < 3; ++q) std::swap(lE[q], lE0[q]);
             launch_filter<real>(c->g, lJ, (real *)(B + L.tmp), c->p.filter_passes, c->stream);
             if (c->laser_on && c->ka >= 2) {
                 const double j0 = antenna_j0(c, A.tn[n], l.a0);
                 // j0 is linear in a0; the profile exp(-r^2/w0^2) gives 2 r^2 / w0^3
                 const double ja = antenna_j0(c, A.tn[n], 1.0);
-                launch_adj_antenna<real>(c->g, lJ[comp], l.polarization, c->ka, c->hx, l.x_center, l.waist, ja,
-                                         j0 * 2.0 / (l.waist * l.waist * l.waist), (double *)(B + L.acc), c->stream);
+                launch_adj_antenna<real>(c->g, lJ[comp], l.polarization, c->ka, c->hx, c->hy, l.x_center,
+                                         l.y_center, l.waist, ja, j0 * 2.0 / (l.waist * l.waist * l.waist),
+                                         (double *)(B + L.acc), c->stream);
             }
             AdjArgs<real> a{};
             a.g = c->g;
@@ -2074,20 +2092,9 @@ static pic_status adj_backward_t(pic_ctx *c, const void *cot, double *grad)
             }
             a.in = flat_e<real>(st(s), L);
             a.iin = flat_i<real>(st(s), L);
-            a.w = (const real *)(B + L.w);
-            a.ion_ci = (const int *)(B + L.ion_ci);
-            a.ion_ox = (const real *)(B + L.ion_ox);
-            a.n = L.P;
-            a.dtdh[0] = (real)(c->dt / c->hx);
-            a.dtdh[1] = (real)(c->dt / c->hz);
-            a.eps = (real)(kPi * -1.0 * c->dt);
-            a.u_drift = drift_u<real>(c);
-            a.jfac[0] = (real)(1.0 * c->hx / (c->dt * c->vol));
-            a.jfac[1] = (real)(1.0 * c->hy / (c->dt * c->vol));
-            a.jfac[2] = (real)(1.0 * c->hz / (c->dt * c->vol));
-            a.jyfac = (real)(-1.0 / c->vol);
-            a.jfac_iz = (real)(-1.0 * c->hz / (c->dt * c->vol));
+            adj_common<real>(c, L, a);
             a.lx = (real *)(B + L.lx);
+            a.ly = (real *)(B + L.ly);
             a.lz = (real *)(B + L.lz);
             a.lux = (real *)(B + L.lux);
             a.luy = (real *)(B + L.luy);

@@ -140,7 +140,7 @@ __global__ void inject_kernel(InjectArgs a)
                 }
             }
         }
-        if (a.flat_base >= 0) {  // the fixed-order store of an adjoint run (2D)
+        if (a.flat_base >= 0) {  // the fixed-order store of an adjoint run
             if (q < total) {
                 const int64_t sl = a.flat_base + q;
                 const bool in = dest >= 0;
@@ -149,6 +149,12 @@ __global__ void inject_kernel(InjectArgs a)
                 if (in) {
                     a.fe_ci[sl] = ci;
                     a.fe_ck[sl] = ck;
+                    if (dim3) {
+                        a.fe_cj[sl] = cj;
+                        static_cast<real *>(a.fe_oy)[sl] = oy;
+                        a.f_ion_cj[sl] = cj;
+                        static_cast<real *>(a.f_ion_oy)[sl] = oy;
+                    }
                     static_cast<real *>(a.fe_ox)[sl] = ox;
                     static_cast<real *>(a.fe_oz)[sl] = oz;
                     static_cast<real *>(a.fe_ux)[sl] = real(0);

@@ -412,25 +412,26 @@ struct InjectArgs {      // lattice load / boosted injection, FP64
     // fixed-order ("flat") output of an adjoint run (flat_base >= 0, 2D):
     // lattice point q of the band goes to slot flat_base + q, alive or not
     int64_t flat_base;
-    int *fe_ci, *fe_ck;          // electron state
-    void *fe_ox, *fe_oz, *fe_ux, *fe_uy, *fe_uz;
+    int *fe_ci, *fe_cj, *fe_ck;  // electron state (cj, oy in 3D)
+    void *fe_ox, *fe_oy, *fe_oz, *fe_ux, *fe_uy, *fe_uz;
     unsigned char *fe_alive;
     int *fi_ck;                  // ion state
     void *fi_oz;
     unsigned char *fi_alive;
-    int *f_ion_ci;               // per slot, constant: the ion's x cell and offset,
-    void *f_ion_ox, *f_w;        // the weight (shared by the pair)
+    int *f_ion_ci, *f_ion_cj;    // per slot, constant: the ion's transverse cells
+    void *f_ion_ox, *f_ion_oy;   // and offsets,
+    void *f_w;                   // the weight (shared by the pair)
     double *f_zeta;              // and the lab profile coordinate
     const StepScal *scal;        // non-null: t, t1, m_lo, m_hi from here (a captured
                                  // step; m_lo, m_hi above then bound the launch)
 };
 
-// One state of the flat particle store of an adjoint run (2D, slot p is the
-// same particle at every step)
+// One state of the flat particle store of an adjoint run (slot p is the same
+// particle at every step; cj, oy only in 3D)
 template <typename real>
 struct FlatE {
-    int *ci, *ck;
-    real *ox, *oz, *ux, *uy, *uz;   // offsets; momenta relative to the drift
+    int *ci, *cj, *ck;
+    real *ox, *oy, *oz, *ux, *uy, *uz;  // offsets; momenta relative to the drift
     unsigned char *alive;
 };
 template <typename real>
@@ -448,14 +449,14 @@ struct AdjArgs {
     FlatE<real> in, out;            // electron states n and n+1
     FlatI<real> iin, iout;          // ion states n and n+1
     const real *w;                  // weights per slot
-    const int *ion_ci;              // ion x cell / offset per slot
-    const real *ion_ox;
+    const int *ion_ci, *ion_cj;     // ion transverse cells / offsets per slot
+    const real *ion_ox, *ion_oy;
     int64_t n;                      // slots
-    real dtdh[2];                   // dt / hx, dt / hz
+    real dtdh[3];                   // dt / h_d
     real eps, u_drift;
-    real jfac[3], jyfac, jfac_iz;
+    real jfac[3], jyfac, jfac_iz;   // electrons' -q h_d / (dt V), 2D q / V; ions' Jz factor
     real *lE[3], *lB[3];            // reverse: field cotangents at n
-    real *lx, *lz, *lux, *luy, *luz;  // reverse: particle cotangents
+    real *lx, *ly, *lz, *lux, *luy, *luz;  // reverse: particle cotangents
     double *lw;                     // reverse: weight cotangents per slot
 };
 
@@ -506,10 +507,10 @@ template <typename real> void launch_adj_push_vjp(const AdjArgs<real> &a, cudaSt
 template <typename real> void launch_adj_ion_vjp(const AdjArgs<real> &a, cudaStream_t s);
 template <typename real>
 void launch_adj_yee(const Geom &g, real *lE[3], real *lB[3], real *lE0[3], real *pE[3], real *lJ[3], double dt,
-                    double hx, double hz, cudaStream_t s);
+                    double hx, double hy, double hz, cudaStream_t s);
 template <typename real>
-void launch_adj_antenna(const Geom &g, const real *lJ, int pol, int ka, double hx, double xc, double waist,
-                        double fa, double fw, double *s, cudaStream_t st);
+void launch_adj_antenna(const Geom &g, const real *lJ, int pol, int ka, double hx, double hy, double xc, double yc,
+                        double waist, double fa, double fw, double *s, cudaStream_t st);
 void launch_adj_profile(int64_t n, const double *lw, const void *w, int precision, const double *zeta, int M,
                         const double *coef, double *out, cudaStream_t s);
 

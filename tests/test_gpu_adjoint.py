@@ -1,5 +1,5 @@
-"""The adjoint (reverse-mode gradient) of a boosted 2D3V run against central
-finite differences of the FP64 oracle.
+"""The adjoint (reverse-mode gradient) of boosted 2D3V and 3D runs, and of a
+lab-frame 2D3V run, against central finite differences of the FP64 oracle.
 
 The objective is linear in the final fields, L = sum(lambda . (E^N, B^N)),
 with lambda on a few nodes behind the laser; its gradient is taken with
@@ -148,6 +148,43 @@ def test_lab_frame_gradient_matches_oracle_finite_differences(O):
                    (objective(coef, a0 + h, w0) - objective(coef, a0 - h, w0)) / (2 * h),
                    (objective(coef, a0, w0 + h) - objective(coef, a0, w0 - h)) / (2 * h)])
     assert np.all(np.abs(fd) > 0)
+    rel = np.abs(grad - fd) / np.abs(fd)
+    assert np.all(rel < 1e-3), (grad, fd, rel)
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_3d_gradient_matches_oracle_finite_differences(O, prec):
+    # a 3D boosted run (gamma = 5, 8 x 8 x 48 cells, 2 x 2 x 2 per cell);
+    # the objective is Ez over a slab behind the antenna plus an Ey band
+    gam = 5.0
+    hz = (1 / 16) * gam * (1 + math.sqrt(1 - 1 / gam ** 2))
+    g = dict(dim=3, nx=8, ny=8, nz=48, dx=1.0, dy=1.0, dz=1 / 16, gamma_boost=gam, filter_passes=1, seed=65)
+    pl = dict(ne=0.01, z_start=gam * 6 * hz, z_end=gam * 600 * hz, ramp=1.0, ppc=(2, 2, 2), jitter=0.1)
+    coef, a0, w0, nsteps = (0.1,), 1.0, 3.0, 20
+    lam = np.zeros((6, g["nz"] + 1, g["ny"], g["nx"]))
+    lam[2, 4:36] = 1.0
+    lam[1, 10:30] = 0.05
+
+    def objective(c, a, w):
+        o = O.Oracle(O.GridParams(dim=3, nx=g["nx"], ny=g["ny"], nz=g["nz"], dx=g["dx"], dy=g["dy"], dz=g["dz"],
+                                  gamma_boost=gam, npass=1, bc_z=1, seed=g["seed"]))
+        o.load_plasma(O.PlasmaParams(profile=tuple(c), ions=1, **pl))
+        o.set_laser(O.LaserParams(a0=a, waist=w, fwhm=2.0, z_antenna=0.0, t_peak=0.5, pol=1))
+        o.step(nsteps)
+        return float(np.sum(lam * np.stack([o.field(q) for q in ("Ex", "Ey", "Ez", "Bx", "By", "Bz")])))
+
+    import torch
+    sim, _ = make_pair(O, g, prec)
+    sim.load_plasma(pl["ne"], pl["z_start"], pl["z_end"], pl["ramp"], pl["ppc"], pl["jitter"], coef, 1)
+    sim.launch_laser(a0, w0, 2.0, 0.0, 0.5, 1)
+    fields = sim.adjoint_forward(nsteps, 8)
+    cot = torch.as_tensor(lam.reshape(6, g["nz"] + 1, g["ny"] * g["nx"]), dtype=fields.dtype, device="cuda")
+    grad = np.array(sim.adjoint_backward(cot.reshape(fields.shape)))
+    # where the oracle's differences agree across h = 1e-3 .. 1e-5 to 2e-6
+    h = 1e-4
+    fd = np.array([(objective((coef[0] + h,), a0, w0) - objective((coef[0] - h,), a0, w0)) / (2 * h),
+                   (objective(coef, a0 + h, w0) - objective(coef, a0 - h, w0)) / (2 * h),
+                   (objective(coef, a0, w0 + h) - objective(coef, a0, w0 - h)) / (2 * h)])
     rel = np.abs(grad - fd) / np.abs(fd)
     assert np.all(rel < 1e-3), (grad, fd, rel)
 
