@@ -348,7 +348,7 @@ pic_status pic_btd_get(pic_ctx *ctx, int j, void *dst, size_t dst_bytes, int dst
 
 /* ---------------------------------------------------------------- adjoint */
 
-/* Reverse-mode gradient of a run (2D3V or 3D, CIC shape, no moving window): the
+/* Reverse-mode gradient of a run (2D3V or 3D, either shape, no moving window): the
    library's own extension of the method, built from the transposes of the
    step's maps (Yee with Mur's condition, filter, antenna, Esirkepov deposit,
    gather, Boris rotation, move).  The objective is linear in the final fields,

@@ -1,4 +1,5 @@
-// pic_adjoint.cu -- reverse mode (adjoint) of the CIC step, 2D3V and 3D.
+// pic_adjoint.cu -- reverse mode (adjoint) of the step, 2D3V and 3D, CIC and
+// quadratic shapes.
 //
 // The step is differentiated as the composition it is (section "Effect of the
 // hyperbolic rotation in Minkowski space" sets up the boosted-frame run; the
@@ -17,8 +18,9 @@
 // Units and layout are those of the forward path: positions as cell index
 // plus an offset in [0, 1) of the working precision, momenta relative to the
 // plasma drift, fields (nz+1) x ny x nx per component (ny = 1 in 2D).
-// Cotangents of positions are per cell (d/d offset).  CIC only: every shape
-// weight is (1 - d, d) on two nodes, with derivative (-1, +1).
+// Cotangents of positions are per cell (d/d offset): the shape weights are
+// differentiated on their own support (CIC: (1 - d, d) and (-1, +1);
+// quadratic: the three B-spline pieces and their slopes).
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -57,12 +59,29 @@ __device__ __forceinline__ void fadd(const Geom &g, real *F, int i, int j, int k
     atomicAdd(F + ((int64_t)k * g.ny + j) * g.nx + i, v);
 }
 
-// CIC weights and their first node for one staggered axis: integer nodes
-// (half = false) or half-integer nodes (half = true, node index i for i + 1/2)
-template <typename real>
-__device__ __forceinline__ int axis_weights(real o, bool half, real w[2])
+// shape weights of order S and their first node for one staggered axis:
+// integer nodes (half = false) or half-integer nodes (half = true, node index
+// i for i + 1/2)
+template <int S, typename real>
+__device__ __forceinline__ int axis_weights(real o, bool half, real w[S + 1])
 {
-    return half ? half_weights<1>(o, w) : offset_weights<1>(o, w);
+    return half ? half_weights<S>(o, w) : offset_weights<S>(o, w);
+}
+
+// d w / d p of the weights spline_weights<S>(p) gives (the same support):
+// CIC (-1, +1); quadratic (-(1/2 - d), -2 d, 1/2 + d), d = p - floor(p + 1/2)
+template <int S, typename real>
+__device__ __forceinline__ void spline_dw(real p, real dw[S + 1])
+{
+    if (S == 1) {
+        dw[0] = real(-1);
+        dw[1] = real(1);
+    } else {
+        const real d = p - floor(p + real(0.5));
+        dw[0] = -(real(0.5) - d);
+        dw[1] = real(-2) * d;
+        dw[2] = real(0.5) + d;
+    }
 }
 
 // the staggering of the six E, B components: half-integer along x, y, z?
@@ -112,33 +131,33 @@ struct BorisFwd {
 
 // gathered E (0..2) and B (3..5) at a particle, with the weights and first
 // nodes of every component (kept for the transpose; y trivial in 2D)
-template <typename real, int DIM>
+template <typename real, int DIM, int S>
 struct GatherFwd {
-    real wx[6][2], wy[6][2], wz[6][2], f[6];
+    real wx[6][S + 1], wy[6][S + 1], wz[6][S + 1], f[6];
     int bx[6], by[6], bz[6];
     template <typename Args>
     __device__ __forceinline__ GatherFwd(const Args &a, int ci, int cj, int ck, real ox, real oy, real oz)
     {
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            bx[c] = ci + axis_weights(ox, hx_of(c), wx[c]);
+            bx[c] = ci + axis_weights<S>(ox, hx_of(c), wx[c]);
             if (DIM == 3) {
-                by[c] = cj + axis_weights(oy, hy_of(c), wy[c]);
+                by[c] = cj + axis_weights<S>(oy, hy_of(c), wy[c]);
             } else {
                 by[c] = 0;
-                wy[c][0] = real(1);
-                wy[c][1] = real(0);
+#pragma unroll
+                for (int q = 0; q <= S; ++q) wy[c][q] = real(q == 0);
             }
-            bz[c] = ck + axis_weights(oz, hz_of(c), wz[c]);
+            bz[c] = ck + axis_weights<S>(oz, hz_of(c), wz[c]);
             const real *F = c < 3 ? a.E[c] : a.B[c - 3];
             real sum = 0;
 #pragma unroll
-            for (int cc = 0; cc < 2; ++cc) {
+            for (int cc = 0; cc <= S; ++cc) {
 #pragma unroll
-                for (int b = 0; b < (DIM == 3 ? 2 : 1); ++b) {
+                for (int b = 0; b < (DIM == 3 ? S + 1 : 1); ++b) {
                     real r = 0;
 #pragma unroll
-                    for (int q = 0; q < 2; ++q)
+                    for (int q = 0; q <= S; ++q)
                         r += wx[c][q] * fval(a.g, F, bx[c] + q, by[c] + b, bz[c] + cc, hz_of(c));
                     sum += wz[c][cc] * wy[c][b] * r;
                 }
@@ -154,12 +173,13 @@ struct GatherFwd {
 
 // One step of the electrons of the flat store: gather E^n, B^n at x^n, Boris,
 // move, Esirkepov deposit with global atomics, re-cell; state `in` -> `out`.
-template <typename real, int DIM>
+// Shape order S: supports of S + 1 nodes, Esirkepov windows of W = S + 2.
+template <typename real, int DIM, int S>
 __global__ void adj_push_kernel(AdjArgs<real> a)
 {
+    constexpr int W = S + 2, WY = DIM == 3 ? W : 1;
     const Geom &g = a.g;
     const Drift<real> drift(a.u_drift, a.dtdh[2]);
-    const real half = real(0.5), third = real(1) / real(3);
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
         if (!a.in.alive[p]) {
             a.out.alive[p] = 0;
@@ -168,7 +188,7 @@ __global__ void adj_push_kernel(AdjArgs<real> a)
         const int ci = a.in.ci[p], cj = DIM == 3 ? a.in.cj[p] : 0, ck = a.in.ck[p];
         const real ox = a.in.ox[p], oy = DIM == 3 ? a.in.oy[p] : real(0), oz = a.in.oz[p], w = a.w[p];
         const real du[3] = {a.in.ux[p], a.in.uy[p], a.in.uz[p]};
-        const GatherFwd<real, DIM> gf(a, ci, cj, ck, ox, oy, oz);
+        const GatherFwd<real, DIM, S> gf(a, ci, cj, ck, ox, oy, oz);
         const BorisFwd<real> bf(du, drift.U, gf.f, gf.f + 3, a.eps);
         const real ux = bf.u[0], uy = bf.u[1], uz = bf.u[2];
         real vx, vy;
@@ -176,42 +196,47 @@ __global__ void adj_push_kernel(AdjArgs<real> a)
         const real x1 = ox + vx * a.dtdh[0];
         const real y1 = DIM == 3 ? oy + vy * a.dtdh[1] : real(0);
         const real z1 = add_rn(oz, drift.dz) + dvz * a.dtdh[2];
-        // Esirkepov: windows of 3 nodes per axis
-        real S0x[3], DSx[3], S0y[3] = {1, 0, 0}, DSy[3] = {0, 0, 0}, S0z[3], DSz[3];
-        bool cr;
-        const int ax = ci + esirk_axis_c<1>(ox, x1, S0x, DSx, cr);
-        const int ay = DIM == 3 ? cj + esirk_axis_c<1>(oy, y1, S0y, DSy, cr) : 0;
-        const int az = ck + esirk_axis_c<1>(oz, z1, S0z, DSz, cr);
-        real Rx[3], Ry[3], Rz[3];
-        {
-            real ax_ = 0, ay_ = 0, az_ = 0;
+        real S0x[W], DSx[W], S0y[W], DSy[W], S0z[W], DSz[W];
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                ax_ += DSx[q];
-                ay_ += DSy[q];
-                az_ += DSz[q];
-                Rx[q] = ax_;
-                Ry[q] = ay_;
-                Rz[q] = az_;
+        for (int q = 0; q < W; ++q) {
+            S0y[q] = real(q == 0);
+            DSy[q] = real(0);
+        }
+        bool cr;
+        const int ax = ci + esirk_axis_c<S>(ox, x1, S0x, DSx, cr);
+        const int ay = DIM == 3 ? cj + esirk_axis_c<S>(oy, y1, S0y, DSy, cr) : 0;
+        const int az = ck + esirk_axis_c<S>(oz, z1, S0z, DSz, cr);
+        real Rx[W], Ry[W], Rz[W];
+        {
+            real sx_ = 0, sy_ = 0, sz_ = 0;
+#pragma unroll
+            for (int q = 0; q < W; ++q) {
+                sx_ += DSx[q];
+                sy_ += DSy[q];
+                sz_ += DSz[q];
+                Rx[q] = sx_;
+                Ry[q] = sy_;
+                Rz[q] = sz_;
             }
         }
         const real fx = a.jfac[0] * w, fy = a.jfac[1] * w, fz = a.jfac[2] * w, fyv = a.jyfac * w * vy;
 #pragma unroll
-        for (int q = 0; q < 3; ++q)
+        for (int q = 0; q < W; ++q)
 #pragma unroll
-            for (int b = 0; b < (DIM == 3 ? 3 : 1); ++b)
+            for (int b = 0; b < WY; ++b)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    if (q < 2) fadd(g, a.J[0], ax + q, ay + b, az + c, false, fx * Rx[q] * tshape(S0y[b], DSy[b], S0z[c], DSz[c]));
+                for (int c = 0; c < W; ++c) {
+                    if (q < W - 1)
+                        fadd(g, a.J[0], ax + q, ay + b, az + c, false, fx * Rx[q] * tshape(S0y[b], DSy[b], S0z[c], DSz[c]));
                     if (DIM == 3) {
-                        if (b < 2) fadd(g, a.J[1], ax + q, ay + b, az + c, false, fy * Ry[b] * tshape(S0z[c], DSz[c], S0x[q], DSx[q]));
+                        if (b < W - 1)
+                            fadd(g, a.J[1], ax + q, ay + b, az + c, false, fy * Ry[b] * tshape(S0z[c], DSz[c], S0x[q], DSx[q]));
                     } else {
                         fadd(g, a.J[1], ax + q, 0, az + c, false, fyv * tshape(S0x[q], DSx[q], S0z[c], DSz[c]));
                     }
-                    if (c < 2) fadd(g, a.J[2], ax + q, ay + b, az + c, true, fz * Rz[c] * tshape(S0x[q], DSx[q], S0y[b], DSy[b]));
+                    if (c < W - 1)
+                        fadd(g, a.J[2], ax + q, ay + b, az + c, true, fz * Rz[c] * tshape(S0x[q], DSx[q], S0y[b], DSy[b]));
                 }
-        (void)half;
-        (void)third;
         // new cell (an offset that rounds to 1 moves on)
         int sx = (int)floor(x1), sy = DIM == 3 ? (int)floor(y1) : 0, sz = (int)floor(z1);
         real nox = x1 - real(sx), noy = DIM == 3 ? y1 - real(sy) : real(0), noz = z1 - real(sz);
@@ -240,9 +265,10 @@ __global__ void adj_push_kernel(AdjArgs<real> a)
 
 // One step of the drifting ions of the flat store: z move by the drift's
 // displacement and the z-only deposit.
-template <typename real, int DIM>
+template <typename real, int DIM, int S>
 __global__ void adj_ion_kernel(AdjArgs<real> a)
 {
+    constexpr int W = S + 2;
     const Geom &g = a.g;
     const Drift<real> drift(a.u_drift, a.dtdh[2]);
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
@@ -253,20 +279,24 @@ __global__ void adj_ion_kernel(AdjArgs<real> a)
         const int ci = a.ion_ci[p], cj = DIM == 3 ? a.ion_cj[p] : 0, ck = a.iin.ck[p];
         const real ox = a.ion_ox[p], oy = DIM == 3 ? a.ion_oy[p] : real(0), oz = a.iin.oz[p];
         const real z1 = add_rn(oz, drift.dz);
-        real S0z[3], DSz[3], wx[2], wy[2] = {1, 0};
+        real S0z[W], DSz[W], wx[S + 1], wy[S + 1];
         bool cr;
-        const int az = ck + esirk_axis_c<1>(oz, z1, S0z, DSz, cr);
-        offset_weights<1>(ox, wx);
-        if (DIM == 3) offset_weights<1>(oy, wy);
+        const int az = ck + esirk_axis_c<S>(oz, z1, S0z, DSz, cr);
+        const int bx = ci + offset_weights<S>(ox, wx);
+        int by = 0;
+        if (DIM == 3) by = cj + offset_weights<S>(oy, wy);
+        else
+#pragma unroll
+            for (int q = 0; q <= S; ++q) wy[q] = real(q == 0);
         const real fz = a.jfac_iz * a.w[p];
         real acc = 0;
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
+        for (int c = 0; c < W - 1; ++c) {
             acc += DSz[c];
 #pragma unroll
-            for (int b = 0; b < (DIM == 3 ? 2 : 1); ++b)
+            for (int b = 0; b < (DIM == 3 ? S + 1 : 1); ++b)
 #pragma unroll
-                for (int q = 0; q < 2; ++q) fadd(g, a.J[2], ci + q, cj + b, az + c, true, fz * acc * wx[q] * wy[b]);
+                for (int q = 0; q <= S; ++q) fadd(g, a.J[2], bx + q, by + b, az + c, true, fz * acc * wx[q] * wy[b]);
         }
         int sz = 0;
         real noz = z1;
@@ -289,12 +319,15 @@ __global__ void adj_ion_kernel(AdjArgs<real> a)
 
 // ------------------------------------------------------------- reverse
 
-// d/dx of a window node's CIC weight: the support of a position starts at node
-// r of the window (weights 1 - d, d on r, r + 1)
-template <typename real>
-__device__ __forceinline__ real dshape(int q, int r)
+// d/dx of the window node q's weight, the support (S + 1 nodes) starting at
+// window node r with weight derivatives dw
+template <int S, typename real>
+__device__ __forceinline__ real dwin(int q, int r, const real dw[S + 1])
 {
-    return q == r ? real(-1) : (q == r + 1 ? real(1) : real(0));
+    real v = 0;
+#pragma unroll
+    for (int m = 0; m <= S; ++m) v = (q == r + m) ? dw[m] : v;
+    return v;
 }
 
 // Cotangents of one electron step.  Reads the state at n (x^n, du^{n-1/2}),
@@ -302,9 +335,10 @@ __device__ __forceinline__ real dshape(int q, int r)
 // particle's cotangents of x^{n+1}, du^{n+1/2}; writes those of x^n,
 // du^{n-1/2} in their place, adds the gather's field cotangents to lE, lB and
 // the weight's cotangent to lw.
-template <typename real, int DIM>
+template <typename real, int DIM, int S>
 __global__ void adj_push_vjp_kernel(AdjArgs<real> a)
 {
+    constexpr int W = S + 2, WY = DIM == 3 ? W : 1;
     const Geom &g = a.g;
     const Drift<real> drift(a.u_drift, a.dtdh[2]);
     const real half = real(0.5), third = real(1) / real(3);
@@ -314,7 +348,7 @@ __global__ void adj_push_vjp_kernel(AdjArgs<real> a)
         const real ox = a.in.ox[p], oy = DIM == 3 ? a.in.oy[p] : real(0), oz = a.in.oz[p], w = a.w[p];
         // ---- recompute the forward values of this step
         const real du0[3] = {a.in.ux[p], a.in.uy[p], a.in.uz[p]};
-        const GatherFwd<real, DIM> gf(a, ci, cj, ck, ox, oy, oz);
+        const GatherFwd<real, DIM, S> gf(a, ci, cj, ck, ox, oy, oz);
         const BorisFwd<real> bf(du0, drift.U, gf.f, gf.f + 3, a.eps);
         const real eps = a.eps, U = drift.U;
         const real ux = bf.u[0], uy = bf.u[1], uz = bf.u[2];
@@ -323,25 +357,36 @@ __global__ void adj_push_vjp_kernel(AdjArgs<real> a)
         const real x1 = ox + vx * a.dtdh[0];
         const real y1 = DIM == 3 ? oy + vy * a.dtdh[1] : real(0);
         const real z1 = add_rn(oz, drift.dz) + dvz * a.dtdh[2];
-        real S0x[3], DSx[3], S0y[3] = {1, 0, 0}, DSy[3] = {0, 0, 0}, S0z[3], DSz[3];
+        real S0x[W], DSx[W], S0y[W], DSy[W], S0z[W], DSz[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            S0y[q] = real(q == 0);
+            DSy[q] = real(0);
+        }
         bool cr;
-        real wtmp[2];
-        const int b0x = offset_weights<1>(ox, wtmp), b1x = spline_weights<1>(x1, wtmp);
-        const int b0z = offset_weights<1>(oz, wtmp), b1z = spline_weights<1>(z1, wtmp);
-        const int anx = esirk_axis_c<1>(ox, x1, S0x, DSx, cr);
-        const int anz = esirk_axis_c<1>(oz, z1, S0z, DSz, cr);
+        real wtmp[S + 1], dw0x[S + 1], dw1x[S + 1], dw0y[S + 1], dw1y[S + 1], dw0z[S + 1], dw1z[S + 1];
+        const int b0x = offset_weights<S>(ox, wtmp), b1x = spline_weights<S>(x1, wtmp);
+        const int b0z = offset_weights<S>(oz, wtmp), b1z = spline_weights<S>(z1, wtmp);
+        spline_dw<S>(ox, dw0x);
+        spline_dw<S>(x1, dw1x);
+        spline_dw<S>(oz, dw0z);
+        spline_dw<S>(z1, dw1z);
+        const int anx = esirk_axis_c<S>(ox, x1, S0x, DSx, cr);
+        const int anz = esirk_axis_c<S>(oz, z1, S0z, DSz, cr);
         int b0y = 0, b1y = 0, any_ = 0;
         if (DIM == 3) {
-            b0y = offset_weights<1>(oy, wtmp);
-            b1y = spline_weights<1>(y1, wtmp);
-            any_ = esirk_axis_c<1>(oy, y1, S0y, DSy, cr);
+            b0y = offset_weights<S>(oy, wtmp);
+            b1y = spline_weights<S>(y1, wtmp);
+            spline_dw<S>(oy, dw0y);
+            spline_dw<S>(y1, dw1y);
+            any_ = esirk_axis_c<S>(oy, y1, S0y, DSy, cr);
         }
         const int ax = ci + anx, ay = cj + any_, az = ck + anz;
-        real Rx[3], Ry[3], Rz[3];
+        real Rx[W], Ry[W], Rz[W];
         {
             real sx_ = 0, sy_ = 0, sz_ = 0;
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
+            for (int q = 0; q < W; ++q) {
                 sx_ += DSx[q];
                 sy_ += DSy[q];
                 sz_ += DSz[q];
@@ -353,20 +398,21 @@ __global__ void adj_push_vjp_kernel(AdjArgs<real> a)
         // ---- deposit transposed: dL/dS0, dL/dDS per window node, dL/dw, dL/dvy
         const real fx = a.jfac[0] * w, fy = a.jfac[1] * w, fz = a.jfac[2] * w;
         const real fy1 = a.jyfac * vy;  // 2D out-of-plane factor over w
-        real gS0x[3] = {0, 0, 0}, gDSx[3] = {0, 0, 0}, gS0y[3] = {0, 0, 0}, gDSy[3] = {0, 0, 0};
-        real gS0z[3] = {0, 0, 0}, gDSz[3] = {0, 0, 0};
-        real gRx[3] = {0, 0, 0}, gRy[3] = {0, 0, 0}, gRz[3] = {0, 0, 0};
+        real gS0x[W], gDSx[W], gS0y[W], gDSy[W], gS0z[W], gDSz[W], gRx[W], gRy[W], gRz[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q)
+            gS0x[q] = gDSx[q] = gS0y[q] = gDSy[q] = gS0z[q] = gDSz[q] = gRx[q] = gRy[q] = gRz[q] = real(0);
         real Lw = 0, Ly = 0;
         // derivatives of T(u, v) with respect to S0u, DSu (the same form in v)
         auto dT0 = [&](real s0v, real dsv) { return s0v + half * dsv; };
         auto dT1 = [&](real s0v, real dsv) { return half * s0v + third * dsv; };
 #pragma unroll
-        for (int q = 0; q < 3; ++q)
+        for (int q = 0; q < W; ++q)
 #pragma unroll
-            for (int b = 0; b < (DIM == 3 ? 3 : 1); ++b)
+            for (int b = 0; b < WY; ++b)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    if (q < 2) {  // Jx = fx Rx[q] T(y_b, z_c)
+                for (int c = 0; c < W; ++c) {
+                    if (q < W - 1) {  // Jx = fx Rx[q] T(y_b, z_c)
                         const real l = fval(g, (const real *)a.J[0], ax + q, ay + b, az + c, false);
                         const real T = tshape(S0y[b], DSy[b], S0z[c], DSz[c]);
                         gRx[q] += fx * T * l;
@@ -380,7 +426,7 @@ __global__ void adj_push_vjp_kernel(AdjArgs<real> a)
                         }
                     }
                     if (DIM == 3) {
-                        if (b < 2) {  // Jy = fy Ry[b] T(z_c, x_q)
+                        if (b < W - 1) {  // Jy = fy Ry[b] T(z_c, x_q)
                             const real l = fval(g, (const real *)a.J[1], ax + q, ay + b, az + c, false);
                             const real T = tshape(S0z[c], DSz[c], S0x[q], DSx[q]);
                             gRy[b] += fy * T * l;
@@ -400,7 +446,7 @@ __global__ void adj_push_vjp_kernel(AdjArgs<real> a)
                         gS0z[c] += k * dT0(S0x[q], DSx[q]);
                         gDSz[c] += k * dT1(S0x[q], DSx[q]);
                     }
-                    if (c < 2) {  // Jz = fz Rz[c] T(x_q, y_b)
+                    if (c < W - 1) {  // Jz = fz Rz[c] T(x_q, y_b)
                         const real l = fval(g, (const real *)a.J[2], ax + q, ay + b, az + c, true);
                         const real T = tshape(S0x[q], DSx[q], S0y[b], DSy[b]);
                         gRz[c] += fz * T * l;
@@ -419,7 +465,7 @@ __global__ void adj_push_vjp_kernel(AdjArgs<real> a)
         {
             real sx_ = 0, sy_ = 0, sz_ = 0;
 #pragma unroll
-            for (int q = 2; q >= 0; --q) {
+            for (int q = W - 1; q >= 0; --q) {
                 sx_ += gRx[q];
                 sy_ += gRy[q];
                 sz_ += gRz[q];
@@ -432,14 +478,14 @@ __global__ void adj_push_vjp_kernel(AdjArgs<real> a)
         // supports of x0 and x1 start at window nodes b0 - an and b1 - an
         real lx1 = 0, ly1 = 0, lz1 = 0, lx0 = 0, ly0 = 0, lz0 = 0;
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            lx0 += (gS0x[q] - gDSx[q]) * dshape<real>(q, b0x - anx);
-            lx1 += gDSx[q] * dshape<real>(q, b1x - anx);
-            lz0 += (gS0z[q] - gDSz[q]) * dshape<real>(q, b0z - anz);
-            lz1 += gDSz[q] * dshape<real>(q, b1z - anz);
+        for (int q = 0; q < W; ++q) {
+            lx0 += (gS0x[q] - gDSx[q]) * dwin<S>(q, b0x - anx, dw0x);
+            lx1 += gDSx[q] * dwin<S>(q, b1x - anx, dw1x);
+            lz0 += (gS0z[q] - gDSz[q]) * dwin<S>(q, b0z - anz, dw0z);
+            lz1 += gDSz[q] * dwin<S>(q, b1z - anz, dw1z);
             if (DIM == 3) {
-                ly0 += (gS0y[q] - gDSy[q]) * dshape<real>(q, b0y - any_);
-                ly1 += gDSy[q] * dshape<real>(q, b1y - any_);
+                ly0 += (gS0y[q] - gDSy[q]) * dwin<S>(q, b0y - any_, dw0y);
+                ly1 += gDSy[q] * dwin<S>(q, b1y - any_, dw1y);
             }
         }
         // ---- move transposed: x1 = ox + vx dtdh_x (and y), z1 = oz + dz_d + dvz dtdh_z
@@ -491,24 +537,29 @@ __global__ void adj_push_vjp_kernel(AdjArgs<real> a)
         lE[0] += eps * ldmx;
         lE[1] += eps * ldmy;
         lE[2] += eps * ldmz;
-        // ---- gather transposed: scatter lE, lB; position cotangents
+        // ---- gather transposed: scatter lE, lB; position cotangents (the
+        // weights' derivatives at each component's own staggered position)
         const real lf[6] = {lE[0], lE[1], lE[2], lB[0], lB[1], lB[2]};
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             const real *F = c < 3 ? a.E[c] : a.B[c - 3];
             real *LF = c < 3 ? a.lE[c] : a.lB[c - 3];
             const real l = lf[c];
+            real dwx[S + 1], dwy[S + 1], dwz[S + 1];
+            spline_dw<S>(hx_of(c) ? ox - half : ox, dwx);
+            spline_dw<S>(hz_of(c) ? oz - half : oz, dwz);
+            if (DIM == 3) spline_dw<S>(hy_of(c) ? oy - half : oy, dwy);
 #pragma unroll
-            for (int cc = 0; cc < 2; ++cc)
+            for (int cc = 0; cc <= S; ++cc)
 #pragma unroll
-                for (int b = 0; b < (DIM == 3 ? 2 : 1); ++b)
+                for (int b = 0; b < (DIM == 3 ? S + 1 : 1); ++b)
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) {
+                    for (int q = 0; q <= S; ++q) {
                         const real v = fval(g, F, gf.bx[c] + q, gf.by[c] + b, gf.bz[c] + cc, hz_of(c));
                         const real wxq = gf.wx[c][q], wyb = gf.wy[c][b], wzc = gf.wz[c][cc];
-                        lx0 += l * (q ? real(1) : real(-1)) * wyb * wzc * v;
-                        if (DIM == 3) ly0 += l * wxq * (b ? real(1) : real(-1)) * wzc * v;
-                        lz0 += l * wxq * wyb * (cc ? real(1) : real(-1)) * v;
+                        lx0 += l * dwx[q] * wyb * wzc * v;
+                        if (DIM == 3) ly0 += l * wxq * dwy[b] * wzc * v;
+                        lz0 += l * wxq * wyb * dwz[cc] * v;
                         fadd(g, LF, gf.bx[c] + q, gf.by[c] + b, gf.bz[c] + cc, hz_of(c), l * wxq * wyb * wzc);
                     }
         }
@@ -525,9 +576,10 @@ __global__ void adj_push_vjp_kernel(AdjArgs<real> a)
 
 // Weight cotangents of the drifting ions of one step (their positions do not
 // depend on the parameters).
-template <typename real, int DIM>
+template <typename real, int DIM, int S>
 __global__ void adj_ion_vjp_kernel(AdjArgs<real> a)
 {
+    constexpr int W = S + 2;
     const Geom &g = a.g;
     const Drift<real> drift(a.u_drift, a.dtdh[2]);
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
@@ -535,20 +587,24 @@ __global__ void adj_ion_vjp_kernel(AdjArgs<real> a)
         const int ci = a.ion_ci[p], cj = DIM == 3 ? a.ion_cj[p] : 0, ck = a.iin.ck[p];
         const real ox = a.ion_ox[p], oy = DIM == 3 ? a.ion_oy[p] : real(0), oz = a.iin.oz[p];
         const real z1 = add_rn(oz, drift.dz);
-        real S0z[3], DSz[3], wx[2], wy[2] = {1, 0};
+        real S0z[W], DSz[W], wx[S + 1], wy[S + 1];
         bool cr;
-        const int az = ck + esirk_axis_c<1>(oz, z1, S0z, DSz, cr);
-        offset_weights<1>(ox, wx);
-        if (DIM == 3) offset_weights<1>(oy, wy);
+        const int az = ck + esirk_axis_c<S>(oz, z1, S0z, DSz, cr);
+        const int bx = ci + offset_weights<S>(ox, wx);
+        int by = 0;
+        if (DIM == 3) by = cj + offset_weights<S>(oy, wy);
+        else
+#pragma unroll
+            for (int q = 0; q <= S; ++q) wy[q] = real(q == 0);
         real acc = 0, L = 0;
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
+        for (int c = 0; c < W - 1; ++c) {
             acc += DSz[c];
 #pragma unroll
-            for (int b = 0; b < (DIM == 3 ? 2 : 1); ++b)
+            for (int b = 0; b < (DIM == 3 ? S + 1 : 1); ++b)
 #pragma unroll
-                for (int q = 0; q < 2; ++q)
-                    L += acc * wx[q] * wy[b] * fval(g, (const real *)a.J[2], ci + q, cj + b, az + c, true);
+                for (int q = 0; q <= S; ++q)
+                    L += acc * wx[q] * wy[b] * fval(g, (const real *)a.J[2], bx + q, by + b, az + c, true);
         }
         a.lw[p] += (double)(a.jfac_iz * L);
     }
@@ -707,8 +763,14 @@ __global__ void adj_profile_kernel(int64_t n, const double *lw, const void *w, i
 
 #define PIC_ADJ_LAUNCH(kernel)                                                                  \
     if (a.n <= 0) return;                                                                       \
-    if (a.g.dim == 3) kernel<real, 3><<<adj_grid(a.n, 256), 256, 0, s>>>(a);                    \
-    else kernel<real, 2><<<adj_grid(a.n, 256), 256, 0, s>>>(a);
+    const unsigned grid = adj_grid(a.n, 256);                                                   \
+    if (a.g.dim == 3) {                                                                         \
+        if (a.g.shape == 1) kernel<real, 3, 1><<<grid, 256, 0, s>>>(a);                         \
+        else kernel<real, 3, 2><<<grid, 256, 0, s>>>(a);                                        \
+    } else {                                                                                    \
+        if (a.g.shape == 1) kernel<real, 2, 1><<<grid, 256, 0, s>>>(a);                         \
+        else kernel<real, 2, 2><<<grid, 256, 0, s>>>(a);                                        \
+    }
 
 template <typename real>
 void launch_adj_push(const AdjArgs<real> &a, cudaStream_t s)

@@ -1852,7 +1852,6 @@ static pic_status adj_check(pic_ctx *c, const pic_adjoint_params *p)
     if (!c || !p) return PIC_ERR_ARG;
     if (!c->bound) return fail(c, PIC_ERR_STATE, "bind buffers first");
     if (p->nsteps < 1 || p->checkpoint_every < 1) return fail(c, PIC_ERR_ARG, "invalid adjoint parameters");
-    if (c->p.shape_order != 1) return fail(c, PIC_ERR_ARG, "the adjoint covers the CIC shape");
     if (c->win_on) return fail(c, PIC_ERR_ARG, "the adjoint does not cover a moving window");
     if (!c->plasma_loaded || c->step != 0)
         return fail(c, PIC_ERR_STATE, "the adjoint starts right after pic_load_plasma (no step taken)");

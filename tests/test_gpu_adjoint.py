@@ -189,6 +189,43 @@ def test_3d_gradient_matches_oracle_finite_differences(O, prec):
     assert np.all(rel < 1e-3), (grad, fd, rel)
 
 
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_quadratic_shape_gradient_matches_oracle_finite_differences(O, prec):
+    # the quadratic shape (3-node supports, 4-node Esirkepov windows) with two
+    # filter passes, boosted 2D3V (gamma = 5)
+    gam = 5.0
+    hz = (1 / 16) * gam * (1 + math.sqrt(1 - 1 / gam ** 2))
+    g = dict(dim=2, nx=16, nz=128, dx=1.0, dz=1 / 16, gamma_boost=gam, shape_order=2, filter_passes=2, seed=67)
+    pl = dict(ne=0.01, z_start=gam * 8 * hz, z_end=gam * 2000 * hz, ramp=1.0, ppc=(2, 1, 2), jitter=0.1)
+    coef, a0, w0, nsteps = (0.1, -0.05), 1.5, 4.0, 40
+    lam = np.zeros((6, g["nz"] + 1, g["nx"]))
+    lam[2, 16:48] = 1.0
+    lam[1, 20:40] = 0.05
+
+    def objective(c, a, w):
+        o = O.Oracle(O.GridParams(dim=2, nx=g["nx"], nz=g["nz"], dx=g["dx"], dz=g["dz"], gamma_boost=gam, shape=2,
+                                  npass=2, bc_z=1, seed=g["seed"]))
+        o.load_plasma(O.PlasmaParams(profile=tuple(c), ions=1, **pl))
+        o.set_laser(O.LaserParams(a0=a, waist=w, fwhm=2.0, z_antenna=0.0, t_peak=0.5, pol=1))
+        o.step(nsteps)
+        return float(np.sum(lam * np.stack([o.field(q)[:, 0, :] for q in ("Ex", "Ey", "Ez", "Bx", "By", "Bz")])))
+
+    import torch
+    sim, _ = make_pair(O, g, prec)
+    sim.load_plasma(pl["ne"], pl["z_start"], pl["z_end"], pl["ramp"], pl["ppc"], pl["jitter"], coef, 1)
+    sim.launch_laser(a0, w0, 2.0, 0.0, 0.5, 1)
+    fields = sim.adjoint_forward(nsteps, 16)
+    grad = np.array(sim.adjoint_backward(torch.as_tensor(lam, dtype=fields.dtype, device="cuda")))
+    # the oracle's differences agree across h = 1e-3 .. 1e-5 to 3e-6 here
+    h = 1e-4
+    fd = np.array([(objective((coef[0] + h, coef[1]), a0, w0) - objective((coef[0] - h, coef[1]), a0, w0)) / (2 * h),
+                   (objective((coef[0], coef[1] + h), a0, w0) - objective((coef[0], coef[1] - h), a0, w0)) / (2 * h),
+                   (objective(coef, a0 + h, w0) - objective(coef, a0 - h, w0)) / (2 * h),
+                   (objective(coef, a0, w0 + h) - objective(coef, a0, w0 - h)) / (2 * h)])
+    rel = np.abs(grad - fd) / np.abs(fd)
+    assert np.all(rel < 1e-3), (grad, fd, rel)
+
+
 def test_fp32_gradient_against_fp64(O):
     _, g64 = gpu_run(O, FP64)
     _, g32 = gpu_run(O, FP32)
