@@ -48,10 +48,12 @@ __device__ __forceinline__ real fval(const Geom &g, const real *F, int i, int j,
     return F[((int64_t)k * g.ny + j) * g.nx + i];
 }
 
-// atomically add v at node (i, j, k) (dropped outside the valid z range)
+// atomically add v at node (i, j, k) (dropped outside the valid z range; an
+// exact zero, e.g. a window node outside both supports, is not added)
 template <typename real>
 __device__ __forceinline__ void fadd(const Geom &g, real *F, int i, int j, int k, bool half_z, real v)
 {
+    if (v == real(0)) return;
     i = wrap1(i, g.nx);
     j = g.dim == 3 ? wrap1(j, g.ny) : 0;
     if (g.bc_z == 0) k = wrapi(k, g.nz);
@@ -167,20 +169,132 @@ struct GatherFwd {
     }
 };
 
+// The gather of GatherFwd (same weights, same sums) together with the
+// gradient of every gathered component with respect to the particle's
+// position (d/dx, d/dy, d/dz of sum w F: the weights' slopes in place of the
+// weights along one axis), read from the same field values in one pass
+template <typename real, int DIM, int S>
+struct GatherGrad {
+    real wx[6][S + 1], wy[6][S + 1], wz[6][S + 1], f[6], gx[6], gy[6], gz[6];
+    int bx[6], by[6], bz[6];
+    template <typename Args>
+    __device__ __forceinline__ GatherGrad(const Args &a, int ci, int cj, int ck, real ox, real oy, real oz)
+    {
+        real dxi[S + 1], dxh[S + 1], dyi[S + 1], dyh[S + 1], dzi[S + 1], dzh[S + 1];
+        spline_dw<S>(ox, dxi);
+        spline_dw<S>(ox - real(0.5), dxh);
+        spline_dw<S>(oz, dzi);
+        spline_dw<S>(oz - real(0.5), dzh);
+        if (DIM == 3) {
+            spline_dw<S>(oy, dyi);
+            spline_dw<S>(oy - real(0.5), dyh);
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            bx[c] = ci + axis_weights<S>(ox, hx_of(c), wx[c]);
+            if (DIM == 3) {
+                by[c] = cj + axis_weights<S>(oy, hy_of(c), wy[c]);
+            } else {
+                by[c] = 0;
+#pragma unroll
+                for (int q = 0; q <= S; ++q) wy[c][q] = real(q == 0);
+            }
+            bz[c] = ck + axis_weights<S>(oz, hz_of(c), wz[c]);
+            const real *dwx = hx_of(c) ? dxh : dxi, *dwy = hy_of(c) ? dyh : dyi, *dwz = hz_of(c) ? dzh : dzi;
+            const real *F = c < 3 ? a.E[c] : a.B[c - 3];
+            real sum = 0, sx = 0, sy = 0, sz = 0;
+#pragma unroll
+            for (int cc = 0; cc <= S; ++cc) {
+#pragma unroll
+                for (int b = 0; b < (DIM == 3 ? S + 1 : 1); ++b) {
+                    real r = 0, rd = 0;
+#pragma unroll
+                    for (int q = 0; q <= S; ++q) {
+                        const real v = fval(a.g, F, bx[c] + q, by[c] + b, bz[c] + cc, hz_of(c));
+                        r += wx[c][q] * v;
+                        rd += dwx[q] * v;
+                    }
+                    sum += wz[c][cc] * wy[c][b] * r;
+                    sx += wz[c][cc] * wy[c][b] * rd;
+                    if (DIM == 3) sy += wz[c][cc] * dwy[b] * r;
+                    sz += dwz[cc] * wy[c][b] * r;
+                }
+            }
+            f[c] = sum;
+            gx[c] = sx;
+            gy[c] = sy;
+            gz[c] = sz;
+        }
+    }
+};
+
 }  // namespace
 
 // ------------------------------------------------------------ flat forward
+
+// One step of drifting ion p of the flat store: z move by the drift's
+// displacement and the z-only deposit (the electron kernel calls it for the
+// ion of every slot).
+template <typename real, int DIM, int S>
+__device__ __forceinline__ void adj_ion_step(const AdjArgs<real> &a, const Drift<real> &drift, int64_t p)
+{
+    constexpr int W = S + 2;
+    const Geom &g = a.g;
+    if (!a.iin.alive[p]) {
+        a.iout.alive[p] = 0;
+        return;
+    }
+    const int ci = a.ion_ci[p], cj = DIM == 3 ? a.ion_cj[p] : 0, ck = a.iin.ck[p];
+    const real ox = a.ion_ox[p], oy = DIM == 3 ? a.ion_oy[p] : real(0), oz = a.iin.oz[p];
+    const real z1 = add_rn(oz, drift.dz);
+    real S0z[W], DSz[W], wx[S + 1], wy[S + 1];
+    bool cr;
+    const int az = ck + esirk_axis_c<S>(oz, z1, S0z, DSz, cr);
+    const int bx = ci + offset_weights<S>(ox, wx);
+    int by = 0;
+    if (DIM == 3) by = cj + offset_weights<S>(oy, wy);
+    else
+#pragma unroll
+        for (int q = 0; q <= S; ++q) wy[q] = real(q == 0);
+    const real fz = a.jfac_iz * a.w[p];
+    real acc = 0;
+#pragma unroll
+    for (int c = 0; c < W - 1; ++c) {
+        acc += DSz[c];
+#pragma unroll
+        for (int b = 0; b < (DIM == 3 ? S + 1 : 1); ++b)
+#pragma unroll
+            for (int q = 0; q <= S; ++q) fadd(g, a.J[2], bx + q, by + b, az + c, true, fz * acc * wx[q] * wy[b]);
+    }
+    int sz = 0;
+    real noz = z1;
+    if (z1 < real(0)) {
+        noz = z1 + real(1);
+        sz = -1;
+        if (noz >= real(1)) { noz = 0; sz = 0; }
+    }
+    int nk = ck + sz;
+    bool alive = true;
+    if (nk < 0) {
+        if (g.bc_z == 0) nk += g.nz;
+        else alive = false;
+    }
+    a.iout.alive[p] = alive ? 1 : 0;
+    a.iout.ck[p] = nk;
+    a.iout.oz[p] = noz;
+}
 
 // One step of the electrons of the flat store: gather E^n, B^n at x^n, Boris,
 // move, Esirkepov deposit with global atomics, re-cell; state `in` -> `out`.
 // Shape order S: supports of S + 1 nodes, Esirkepov windows of W = S + 2.
 template <typename real, int DIM, int S>
-__global__ void adj_push_kernel(AdjArgs<real> a)
+__global__ void __launch_bounds__(256, 6) adj_push_kernel(AdjArgs<real> a)
 {
     constexpr int W = S + 2, WY = DIM == 3 ? W : 1;
     const Geom &g = a.g;
     const Drift<real> drift(a.u_drift, a.dtdh[2]);
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
+        if (a.with_ions) adj_ion_step<real, DIM, S>(a, drift, p);
         if (!a.in.alive[p]) {
             a.out.alive[p] = 0;
             continue;
@@ -263,60 +377,6 @@ __global__ void adj_push_kernel(AdjArgs<real> a)
     }
 }
 
-// One step of the drifting ions of the flat store: z move by the drift's
-// displacement and the z-only deposit.
-template <typename real, int DIM, int S>
-__global__ void adj_ion_kernel(AdjArgs<real> a)
-{
-    constexpr int W = S + 2;
-    const Geom &g = a.g;
-    const Drift<real> drift(a.u_drift, a.dtdh[2]);
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
-        if (!a.iin.alive[p]) {
-            a.iout.alive[p] = 0;
-            continue;
-        }
-        const int ci = a.ion_ci[p], cj = DIM == 3 ? a.ion_cj[p] : 0, ck = a.iin.ck[p];
-        const real ox = a.ion_ox[p], oy = DIM == 3 ? a.ion_oy[p] : real(0), oz = a.iin.oz[p];
-        const real z1 = add_rn(oz, drift.dz);
-        real S0z[W], DSz[W], wx[S + 1], wy[S + 1];
-        bool cr;
-        const int az = ck + esirk_axis_c<S>(oz, z1, S0z, DSz, cr);
-        const int bx = ci + offset_weights<S>(ox, wx);
-        int by = 0;
-        if (DIM == 3) by = cj + offset_weights<S>(oy, wy);
-        else
-#pragma unroll
-            for (int q = 0; q <= S; ++q) wy[q] = real(q == 0);
-        const real fz = a.jfac_iz * a.w[p];
-        real acc = 0;
-#pragma unroll
-        for (int c = 0; c < W - 1; ++c) {
-            acc += DSz[c];
-#pragma unroll
-            for (int b = 0; b < (DIM == 3 ? S + 1 : 1); ++b)
-#pragma unroll
-                for (int q = 0; q <= S; ++q) fadd(g, a.J[2], bx + q, by + b, az + c, true, fz * acc * wx[q] * wy[b]);
-        }
-        int sz = 0;
-        real noz = z1;
-        if (z1 < real(0)) {
-            noz = z1 + real(1);
-            sz = -1;
-            if (noz >= real(1)) { noz = 0; sz = 0; }
-        }
-        int nk = ck + sz;
-        bool alive = true;
-        if (nk < 0) {
-            if (g.bc_z == 0) nk += g.nz;
-            else alive = false;
-        }
-        a.iout.alive[p] = alive ? 1 : 0;
-        a.iout.ck[p] = nk;
-        a.iout.oz[p] = noz;
-    }
-}
-
 // ------------------------------------------------------------- reverse
 
 // d/dx of the window node q's weight, the support (S + 1 nodes) starting at
@@ -330,25 +390,83 @@ __device__ __forceinline__ real dwin(int q, int r, const real dw[S + 1])
     return v;
 }
 
+// Weight cotangent of drifting ion p in one step (its position does not
+// depend on the parameters); the electron VJP kernel calls it for every slot.
+template <typename real, int DIM, int S>
+__device__ __forceinline__ void adj_ion_vjp_one(const AdjArgs<real> &a, const Drift<real> &drift, int64_t p)
+{
+    constexpr int W = S + 2;
+    const Geom &g = a.g;
+    if (!a.iin.alive[p]) return;
+    const int ci = a.ion_ci[p], cj = DIM == 3 ? a.ion_cj[p] : 0, ck = a.iin.ck[p];
+    {
+        bool any = false;
+#pragma unroll
+        for (int d = -S - 2; d <= S + 2; ++d) {
+            int k = ck + d;
+            if (g.bc_z == 0) k = wrapi(k, g.nz);
+            if (k >= 0 && k <= g.nz && a.lj_plane[k]) any = true;
+        }
+        if (!any) return;  // no current cotangent where this ion deposits
+    }
+    const real ox = a.ion_ox[p], oy = DIM == 3 ? a.ion_oy[p] : real(0), oz = a.iin.oz[p];
+    const real z1 = add_rn(oz, drift.dz);
+    real S0z[W], DSz[W], wx[S + 1], wy[S + 1];
+    bool cr;
+    const int az = ck + esirk_axis_c<S>(oz, z1, S0z, DSz, cr);
+    const int bx = ci + offset_weights<S>(ox, wx);
+    int by = 0;
+    if (DIM == 3) by = cj + offset_weights<S>(oy, wy);
+    else
+#pragma unroll
+        for (int q = 0; q <= S; ++q) wy[q] = real(q == 0);
+    real acc = 0, L = 0;
+#pragma unroll
+    for (int c = 0; c < W - 1; ++c) {
+        acc += DSz[c];
+#pragma unroll
+        for (int b = 0; b < (DIM == 3 ? S + 1 : 1); ++b)
+#pragma unroll
+            for (int q = 0; q <= S; ++q)
+                L += acc * wx[q] * wy[b] * fval(g, (const real *)a.J[2], bx + q, by + b, az + c, true);
+    }
+    a.lw[p] += (double)(a.jfac_iz * L);
+}
+
 // Cotangents of one electron step.  Reads the state at n (x^n, du^{n-1/2}),
 // E^n, B^n, the filtered-and-transposed current cotangent lJ, and the
 // particle's cotangents of x^{n+1}, du^{n+1/2}; writes those of x^n,
 // du^{n-1/2} in their place, adds the gather's field cotangents to lE, lB and
 // the weight's cotangent to lw.
 template <typename real, int DIM, int S>
-__global__ void adj_push_vjp_kernel(AdjArgs<real> a)
+__global__ void __launch_bounds__(256, 3) adj_push_vjp_kernel(AdjArgs<real> a)
 {
     constexpr int W = S + 2, WY = DIM == 3 ? W : 1;
     const Geom &g = a.g;
     const Drift<real> drift(a.u_drift, a.dtdh[2]);
     const real half = real(0.5), third = real(1) / real(3);
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
+        if (a.with_ions) adj_ion_vjp_one<real, DIM, S>(a, drift, p);
         if (!a.in.alive[p]) continue;
         const int ci = a.in.ci[p], cj = DIM == 3 ? a.in.cj[p] : 0, ck = a.in.ck[p];
+        // a particle whose incoming cotangents are zero and whose deposit
+        // reaches no node with a current cotangent contributes nothing (its
+        // gather cotangents are then zero too): skip it
+        if (a.lx[p] == real(0) && a.lz[p] == real(0) && (DIM == 2 || a.ly[p] == real(0)) && a.lux[p] == real(0) &&
+            a.luy[p] == real(0) && a.luz[p] == real(0)) {
+            bool any = false;
+#pragma unroll
+            for (int d = -S - 2; d <= S + 2; ++d) {
+                int k = ck + d;
+                if (g.bc_z == 0) k = wrapi(k, g.nz);
+                if (k >= 0 && k <= g.nz && a.lj_plane[k]) any = true;
+            }
+            if (!any) continue;
+        }
         const real ox = a.in.ox[p], oy = DIM == 3 ? a.in.oy[p] : real(0), oz = a.in.oz[p], w = a.w[p];
         // ---- recompute the forward values of this step
         const real du0[3] = {a.in.ux[p], a.in.uy[p], a.in.uz[p]};
-        const GatherFwd<real, DIM, S> gf(a, ci, cj, ck, ox, oy, oz);
+        const GatherGrad<real, DIM, S> gf(a, ci, cj, ck, ox, oy, oz);
         const BorisFwd<real> bf(du0, drift.U, gf.f, gf.f + 3, a.eps);
         const real eps = a.eps, U = drift.U;
         const real ux = bf.u[0], uy = bf.u[1], uz = bf.u[2];
@@ -537,31 +655,24 @@ __global__ void adj_push_vjp_kernel(AdjArgs<real> a)
         lE[0] += eps * ldmx;
         lE[1] += eps * ldmy;
         lE[2] += eps * ldmz;
-        // ---- gather transposed: scatter lE, lB; position cotangents (the
-        // weights' derivatives at each component's own staggered position)
+        // ---- gather transposed: position cotangents from the gathered
+        // gradients; field cotangents scattered with the gather weights
         const real lf[6] = {lE[0], lE[1], lE[2], lB[0], lB[1], lB[2]};
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            const real *F = c < 3 ? a.E[c] : a.B[c - 3];
             real *LF = c < 3 ? a.lE[c] : a.lB[c - 3];
             const real l = lf[c];
-            real dwx[S + 1], dwy[S + 1], dwz[S + 1];
-            spline_dw<S>(hx_of(c) ? ox - half : ox, dwx);
-            spline_dw<S>(hz_of(c) ? oz - half : oz, dwz);
-            if (DIM == 3) spline_dw<S>(hy_of(c) ? oy - half : oy, dwy);
+            lx0 += l * gf.gx[c];
+            if (DIM == 3) ly0 += l * gf.gy[c];
+            lz0 += l * gf.gz[c];
 #pragma unroll
             for (int cc = 0; cc <= S; ++cc)
 #pragma unroll
                 for (int b = 0; b < (DIM == 3 ? S + 1 : 1); ++b)
 #pragma unroll
-                    for (int q = 0; q <= S; ++q) {
-                        const real v = fval(g, F, gf.bx[c] + q, gf.by[c] + b, gf.bz[c] + cc, hz_of(c));
-                        const real wxq = gf.wx[c][q], wyb = gf.wy[c][b], wzc = gf.wz[c][cc];
-                        lx0 += l * dwx[q] * wyb * wzc * v;
-                        if (DIM == 3) ly0 += l * wxq * dwy[b] * wzc * v;
-                        lz0 += l * wxq * wyb * dwz[cc] * v;
-                        fadd(g, LF, gf.bx[c] + q, gf.by[c] + b, gf.bz[c] + cc, hz_of(c), l * wxq * wyb * wzc);
-                    }
+                    for (int q = 0; q <= S; ++q)
+                        fadd(g, LF, gf.bx[c] + q, gf.by[c] + b, gf.bz[c] + cc, hz_of(c),
+                             l * gf.wx[c][q] * gf.wy[c][b] * gf.wz[c][cc]);
         }
         // ---- write the cotangents of x^n, du^{n-1/2}; the weight's
         a.lx[p] = lx1 + lx0;
@@ -571,42 +682,6 @@ __global__ void adj_push_vjp_kernel(AdjArgs<real> a)
         a.luy[p] = ldmy;
         a.luz[p] = ldmz;
         a.lw[p] += (double)Lw;
-    }
-}
-
-// Weight cotangents of the drifting ions of one step (their positions do not
-// depend on the parameters).
-template <typename real, int DIM, int S>
-__global__ void adj_ion_vjp_kernel(AdjArgs<real> a)
-{
-    constexpr int W = S + 2;
-    const Geom &g = a.g;
-    const Drift<real> drift(a.u_drift, a.dtdh[2]);
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
-        if (!a.iin.alive[p]) continue;
-        const int ci = a.ion_ci[p], cj = DIM == 3 ? a.ion_cj[p] : 0, ck = a.iin.ck[p];
-        const real ox = a.ion_ox[p], oy = DIM == 3 ? a.ion_oy[p] : real(0), oz = a.iin.oz[p];
-        const real z1 = add_rn(oz, drift.dz);
-        real S0z[W], DSz[W], wx[S + 1], wy[S + 1];
-        bool cr;
-        const int az = ck + esirk_axis_c<S>(oz, z1, S0z, DSz, cr);
-        const int bx = ci + offset_weights<S>(ox, wx);
-        int by = 0;
-        if (DIM == 3) by = cj + offset_weights<S>(oy, wy);
-        else
-#pragma unroll
-            for (int q = 0; q <= S; ++q) wy[q] = real(q == 0);
-        real acc = 0, L = 0;
-#pragma unroll
-        for (int c = 0; c < W - 1; ++c) {
-            acc += DSz[c];
-#pragma unroll
-            for (int b = 0; b < (DIM == 3 ? S + 1 : 1); ++b)
-#pragma unroll
-                for (int q = 0; q <= S; ++q)
-                    L += acc * wx[q] * wy[b] * fval(g, (const real *)a.J[2], bx + q, by + b, az + c, true);
-        }
-        a.lw[p] += (double)(a.jfac_iz * L);
     }
 }
 
@@ -742,7 +817,10 @@ __global__ void adj_antenna_kernel(Geom g, const real *lJ, int pol, int ka, doub
     atomicAdd(s + 1, fw * s1);
 }
 
-// dL/dc_m = sum_p lw_p w_p cos(m pi zeta_p) / (1 + sum_m' c_m' cos(m' pi zeta_p))
+// dL/dc_m = sum_p lw_p w_p cos(m pi zeta_p) / (1 + sum_m' c_m' cos(m' pi zeta_p)),
+// the cos(m pi zeta) by the recurrence cos((m+1) t) = 2 cos t cos(m t) - cos((m-1) t)
+// from one cosine per particle; block partial sums, one atomic per block and
+// coefficient
 __global__ void adj_profile_kernel(int64_t n, const double *lw, const void *w, int precision, const double *zeta,
                                    int M, const double *coef, double *out)
 {
@@ -752,11 +830,48 @@ __global__ void adj_profile_kernel(int64_t n, const double *lw, const void *w, i
         if (lw[p] == 0.0) continue;  // never alive, or no current
         const double wp = precision ? ((const double *)w)[p] : (double)((const float *)w)[p];
         const double l = lw[p] * wp;
+        double cm[16];
+        const double c1 = cos(3.141592653589793 * zeta[p]);
+        double prev = 1.0, cur = c1;
         double f = 1.0;
-        for (int m = 1; m <= M; ++m) f += coef[m - 1] * cos((double)m * 3.141592653589793 * zeta[p]);
-        for (int m = 1; m <= M; ++m) acc[m - 1] += l * cos((double)m * 3.141592653589793 * zeta[p]) / f;
+        for (int m = 1; m <= M; ++m) {
+            cm[m - 1] = cur;
+            f += coef[m - 1] * cur;
+            const double next = 2.0 * c1 * cur - prev;
+            prev = cur;
+            cur = next;
+        }
+        const double lf = l / f;
+        for (int m = 0; m < M; ++m) acc[m] += lf * cm[m];
     }
-    for (int m = 0; m < M; ++m) atomicAdd(out + m, acc[m]);
+    __shared__ double red[256];
+    for (int m = 0; m < M; ++m) {
+        red[threadIdx.x] = acc[m];
+        __syncthreads();
+        for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+            if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) atomicAdd(out + m, red[0]);
+        __syncthreads();
+    }
+}
+
+// planes[k] = 1 where lJ (three components) is not all zero on plane k
+template <typename real>
+__global__ void adj_planes_kernel(Geom g, const real *J0, const real *J1, const real *J2, unsigned char *planes)
+{
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < (int64_t)(g.nz + 1) * g.plane;
+         o += (int64_t)gridDim.x * blockDim.x)
+        if (J0[o] != real(0) || J1[o] != real(0) || J2[o] != real(0)) planes[o / g.plane] = 1;
+}
+
+template <typename real>
+void launch_adj_planes(const Geom &g, real *const lJ[3], unsigned char *planes, cudaStream_t s)
+{
+    cudaMemsetAsync(planes, 0, (size_t)g.nz + 1, s);
+    adj_planes_kernel<real><<<adj_grid((int64_t)(g.nz + 1) * g.plane, 256), 256, 0, s>>>(g, lJ[0], lJ[1], lJ[2],
+                                                                                           planes);
 }
 
 // --------------------------------------------------------------- launchers
@@ -777,21 +892,13 @@ void launch_adj_push(const AdjArgs<real> &a, cudaStream_t s)
 {
     PIC_ADJ_LAUNCH(adj_push_kernel)
 }
-template <typename real>
-void launch_adj_ions(const AdjArgs<real> &a, cudaStream_t s)
-{
-    PIC_ADJ_LAUNCH(adj_ion_kernel)
-}
+
 template <typename real>
 void launch_adj_push_vjp(const AdjArgs<real> &a, cudaStream_t s)
 {
     PIC_ADJ_LAUNCH(adj_push_vjp_kernel)
 }
-template <typename real>
-void launch_adj_ion_vjp(const AdjArgs<real> &a, cudaStream_t s)
-{
-    PIC_ADJ_LAUNCH(adj_ion_vjp_kernel)
-}
+
 #undef PIC_ADJ_LAUNCH
 
 // the Yee step transposed: (lE, lB) at n+1 -> (lE, lB) at n and lJ (the
@@ -832,11 +939,10 @@ void launch_adj_profile(int64_t n, const double *lw, const void *w, int precisio
 
 #define PIC_ADJ_INSTANTIATE(real)                                                                              \
     template void launch_adj_push<real>(const AdjArgs<real> &, cudaStream_t);                                  \
-    template void launch_adj_ions<real>(const AdjArgs<real> &, cudaStream_t);                                  \
     template void launch_adj_push_vjp<real>(const AdjArgs<real> &, cudaStream_t);                              \
-    template void launch_adj_ion_vjp<real>(const AdjArgs<real> &, cudaStream_t);                               \
     template void launch_adj_yee<real>(const Geom &, real *[3], real *[3], real *[3], real *[3], real *[3],     \
                                        double, double, double, double, cudaStream_t);                          \
+    template void launch_adj_planes<real>(const Geom &, real *const[3], unsigned char *, cudaStream_t);        \
     template void launch_adj_antenna<real>(const Geom &, const real *, int, int, double, double, double, double, \
                                            double, double, double, double *, cudaStream_t);
 PIC_ADJ_INSTANTIATE(float)

@@ -113,6 +113,7 @@ struct pic_ctx {
     // buffer holding the checkpoints between the forward and reverse calls
     struct {
         bool ready = false;
+        bool last_seg_ready = false;  // the forward left its last segment's states in place
         int N = 0, K = 0;
         int64_t P = 0;
         std::vector<int64_t> base, mlo, mhi;
@@ -1725,14 +1726,14 @@ struct AdjLayout {
     size_t st = 0, fl = 0;                           // one particle state, one field state (6 comps)
     size_t ckpt = 0, seg = 0;                        // C and K + 1 (state, fields) pairs
     size_t J = 0, tmp = 0, lE = 0, lB = 0, lE0 = 0, pE = 0, lJ = 0;  // 3 components each
-    size_t lx = 0, ly = 0, lz = 0, lux = 0, luy = 0, luz = 0, lw = 0, acc = 0, coef = 0;
+    size_t lx = 0, ly = 0, lz = 0, lux = 0, luy = 0, luz = 0, lw = 0, acc = 0, coef = 0, planes = 0;
     size_t total = 0;
     // inside one particle state
     size_t e_ci = 0, e_cj = 0, e_ck = 0, e_ox = 0, e_oy = 0, e_oz = 0, e_ux = 0, e_uy = 0, e_uz = 0, e_alive = 0;
     size_t i_ck = 0, i_oz = 0, i_alive = 0;
 };
 
-AdjLayout adj_layout(int64_t P, int N, int K, size_t es, int64_t ncomp, bool dim3)
+AdjLayout adj_layout(int64_t P, int N, int K, size_t es, int64_t ncomp, bool dim3, int64_t nz1)
 {
     const int64_t P3 = dim3 ? P : 0;  // y arrays only in 3D
     AdjLayout L;
@@ -1791,6 +1792,7 @@ AdjLayout adj_layout(int64_t P, int N, int K, size_t es, int64_t ncomp, bool dim
     L.luz = take(es * P);
     L.lw = take(8 * P);
     L.acc = take(8 * 2);
+    L.planes = take((size_t)nz1);
     L.coef = take(8 * 32);
     L.total = o;
     return L;
@@ -1864,7 +1866,9 @@ extern "C" pic_status pic_adjoint_bytes(pic_ctx *c, const pic_adjoint_params *p,
     if (st != PIC_OK) return st;
     if (!bytes) return PIC_ERR_ARG;
     adj_bands(c, p->nsteps);
-    *bytes = adj_layout(c->adj.P, p->nsteps, p->checkpoint_every, (size_t)c->es, c->g.ncomp, c->g.dim == 3).total;
+    *bytes = adj_layout(c->adj.P, p->nsteps, p->checkpoint_every, (size_t)c->es, c->g.ncomp, c->g.dim == 3,
+                        c->g.nz + 1)
+                 .total;
     return PIC_OK;
 }
 
@@ -1891,6 +1895,7 @@ static void adj_common(pic_ctx *c, const AdjLayout &L, AdjArgs<real> &a)
     a.jfac[2] = (real)(1.0 * c->hz / (c->dt * c->vol));
     a.jyfac = (real)(-1.0 / c->vol);
     a.jfac_iz = (real)(-1.0 * c->hz / (c->dt * c->vol));
+    a.with_ions = c->ions_species ? 1 : 0;
 }
 
 // the flat-output pointers of an injection into state st
@@ -1928,14 +1933,15 @@ static void adj_step(pic_ctx *c, const AdjLayout &L, unsigned char *sa, unsigned
 {
     unsigned char *B = c->adj.buf;
     const int64_t nc = c->g.ncomp;
-    real *J = (real *)(B + L.J);
-    cudaMemsetAsync(J, 0, 3 * sizeof(real) * nc, c->stream);
+    // the raw current goes to the filter's input buffer; the filter writes J
+    real *J = (real *)(B + L.J), *R = (real *)(B + L.tmp);
+    cudaMemsetAsync(R, 0, 3 * sizeof(real) * nc, c->stream);
     AdjArgs<real> a{};
     a.g = c->g;
     for (int q = 0; q < 3; ++q) {
         a.E[q] = (const real *)fa + q * nc;
         a.B[q] = (const real *)fa + (3 + q) * nc;
-        a.J[q] = J + q * nc;
+        a.J[q] = R + q * nc;
     }
     a.in = flat_e<real>(sa, L);
     a.out = flat_e<real>(sb, L);
@@ -1943,15 +1949,20 @@ static void adj_step(pic_ctx *c, const AdjLayout &L, unsigned char *sa, unsigned
     a.iout = flat_i<real>(sb, L);
     adj_common<real>(c, L, a);
     launch_adj_push<real>(a, c->stream);
-    if (c->ions_species) launch_adj_ions<real>(a, c->stream);
-    real *Jc[3] = {J, J + nc, J + 2 * nc};
+    real *Rc[3] = {R, R + nc, R + 2 * nc};
     if (c->laser_on && c->ka >= 2) {
         const pic_laser_params &l = c->laser;
         const double j0 = antenna_j0(c, c->adj.tn[n], l.a0);
-        launch_antenna<real>(c->g, Jc[l.polarization == PIC_POL_X ? 0 : 1], l.polarization, c->ka, j0, c->hx, c->hy,
+        launch_antenna<real>(c->g, Rc[l.polarization == PIC_POL_X ? 0 : 1], l.polarization, c->ka, j0, c->hx, c->hy,
                              l.x_center, l.y_center, l.waist, c->stream);
     }
-    launch_filter<real>(c->g, Jc, (real *)(B + L.tmp), c->p.filter_passes, c->stream);
+    real *Jc[3] = {J, J + nc, J + 2 * nc};
+    if (c->p.filter_passes == 0) {
+        for (int q = 0; q < 3; ++q) Jc[q] = Rc[q];
+    } else if (!launch_filter_from<real>(c->g, R, Jc, c->p.filter_passes, c->stream)) {
+        cudaMemcpyAsync(J, R, 3 * sizeof(real) * nc, cudaMemcpyDeviceToDevice, c->stream);
+        launch_filter<real>(c->g, Jc, R, c->p.filter_passes, c->stream);
+    }
     real *F[9], *F1[6];
     for (int q = 0; q < 6; ++q) {
         F[q] = (real *)fa + q * nc;
@@ -1977,7 +1988,8 @@ template <typename real>
 static pic_status adj_forward_t(pic_ctx *c, const pic_adjoint_params *p, void *fields_out)
 {
     auto &A = c->adj;
-    const AdjLayout L = adj_layout(A.P, p->nsteps, p->checkpoint_every, sizeof(real), c->g.ncomp, c->g.dim == 3);
+    const AdjLayout L =
+        adj_layout(A.P, p->nsteps, p->checkpoint_every, sizeof(real), c->g.ncomp, c->g.dim == 3, c->g.nz + 1);
     unsigned char *B = A.buf;
     unsigned char *seg = B + L.seg;
     auto st = [&](int s) { return seg + (size_t)s * (L.st + L.fl); };
@@ -2004,15 +2016,27 @@ static pic_status adj_forward_t(pic_ctx *c, const pic_adjoint_params *p, void *f
         adj_inject_out<real>(c, L, st(0), ia);
         launch_inject(ia, c->stream);
     }
+    // steps before the last segment alternate between slots 0 and 1; the last
+    // segment's states are kept in the slots the reverse sweep reads them
+    // from, so that its first segment needs no recomputation
+    const int nlast = (L.C - 1) * L.K;
     for (int n = 0; n < L.N; ++n) {
-        const int a = n & 1, b = a ^ 1;
+        int a = n & 1, b = a ^ 1;
+        if (n == nlast && a == 1) {
+            CUDA_TRY(c, cudaMemcpyAsync(st(0), st(1), L.st + L.fl, cudaMemcpyDeviceToDevice, c->stream));
+        }
+        if (n >= nlast) {
+            a = n - nlast;
+            b = a + 1;
+        }
         if (n % L.K == 0)
             CUDA_TRY(c, cudaMemcpyAsync(ck_st(n / L.K), st(a), L.st + L.fl, cudaMemcpyDeviceToDevice, c->stream));
         adj_step<real>(c, L, st(a), st(b), fl(a), fl(b), n);
     }
     CUDA_TRY(c, cudaGetLastError());
     if (fields_out)
-        CUDA_TRY(c, cudaMemcpyAsync(fields_out, fl(L.N & 1), fbytes, cudaMemcpyDeviceToDevice, c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(fields_out, fl(L.N - nlast), fbytes, cudaMemcpyDeviceToDevice, c->stream));
+    A.last_seg_ready = true;
     A.ready = true;
     A.N = L.N;
     A.K = L.K;
@@ -2026,7 +2050,9 @@ extern "C" pic_status pic_adjoint_forward(pic_ctx *c, const pic_adjoint_params *
     if (s != PIC_OK) return s;
     if (!buf) return PIC_ERR_ARG;
     adj_bands(c, p->nsteps);
-    if (bytes < adj_layout(c->adj.P, p->nsteps, p->checkpoint_every, (size_t)c->es, c->g.ncomp, c->g.dim == 3).total)
+    if (bytes < adj_layout(c->adj.P, p->nsteps, p->checkpoint_every, (size_t)c->es, c->g.ncomp, c->g.dim == 3,
+                           c->g.nz + 1)
+                    .total)
         return fail(c, PIC_ERR_ARG, "adjoint buffer too small");
     c->adj.buf = (unsigned char *)buf;
     c->adj.bytes = bytes;
@@ -2038,7 +2064,7 @@ template <typename real>
 static pic_status adj_backward_t(pic_ctx *c, const void *cot, double *grad)
 {
     auto &A = c->adj;
-    const AdjLayout L = adj_layout(A.P, A.N, A.K, sizeof(real), c->g.ncomp, c->g.dim == 3);
+    const AdjLayout L = adj_layout(A.P, A.N, A.K, sizeof(real), c->g.ncomp, c->g.dim == 3, c->g.nz + 1);
     unsigned char *B = A.buf;
     const int64_t nc = c->g.ncomp;
     unsigned char *seg = B + L.seg;
@@ -2065,13 +2091,18 @@ static pic_status adj_backward_t(pic_ctx *c, const void *cot, double *grad)
     const int comp = l.polarization == PIC_POL_X ? 0 : 1;
     for (int sgi = L.C - 1; sgi >= 0; --sgi) {
         const int n0 = sgi * L.K, n1 = std::min(L.N, n0 + L.K);
-        CUDA_TRY(c, cudaMemcpyAsync(st(0), ck_st(sgi), L.st + L.fl, cudaMemcpyDeviceToDevice, c->stream));
-        for (int s = 0; s < n1 - n0; ++s) adj_step<real>(c, L, st(s), st(s + 1), fl(s), fl(s + 1), n0 + s);
+        if (sgi == L.C - 1 && A.last_seg_ready) {
+            A.last_seg_ready = false;  // kept by the forward run, used once
+        } else {
+            CUDA_TRY(c, cudaMemcpyAsync(st(0), ck_st(sgi), L.st + L.fl, cudaMemcpyDeviceToDevice, c->stream));
+            for (int s = 0; s < n1 - n0; ++s) adj_step<real>(c, L, st(s), st(s + 1), fl(s), fl(s + 1), n0 + s);
+        }
         for (int s = n1 - n0 - 1; s >= 0; --s) {
             const int n = n0 + s;
             launch_adj_yee<real>(c->g, lE, lB, lE0, pE, lJ, c->dt, c->hx, c->hy, c->hz, c->stream);
             for (int q = 0; q < 3; ++q) std::swap(lE[q], lE0[q]);
             launch_filter<real>(c->g, lJ, (real *)(B + L.tmp), c->p.filter_passes, c->stream);
+            launch_adj_planes<real>(c->g, lJ, B + L.planes, c->stream);
             if (c->laser_on && c->ka >= 2) {
                 const double j0 = antenna_j0(c, A.tn[n], l.a0);
                 // j0 is linear in a0; the profile exp(-r^2/w0^2) gives 2 r^2 / w0^3
@@ -2099,7 +2130,7 @@ static pic_status adj_backward_t(pic_ctx *c, const void *cot, double *grad)
             a.luy = (real *)(B + L.luy);
             a.luz = (real *)(B + L.luz);
             a.lw = (double *)(B + L.lw);
-            if (c->ions_species) launch_adj_ion_vjp<real>(a, c->stream);
+            a.lj_plane = B + L.planes;
             launch_adj_push_vjp<real>(a, c->stream);
         }
     }

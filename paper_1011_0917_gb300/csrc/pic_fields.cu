@@ -289,13 +289,21 @@ void launch_yee(const Geom &g, real *const F[9], real *const F1[6], double dt, d
     a.twopi = (real)6.283185307179586;
     a.mur = (real)((dt - hz) / (dt + hz));
     const int nzo = g.bc_z == 0 ? g.nz : g.nz + 1;
-    // chunks of 32 planes (the last one takes the remainder, at least 2)
-    a.cz = nzo >= 64 ? 32 : (nzo >= 8 ? 4 : nzo);
-    a.nchunks = nzo / a.cz;
-    if (a.nchunks < 1) a.nchunks = 1;
     const bool is3 = g.dim == 3;
     const int TX = is3 ? YeeTile<3>::TX : YeeTile<2>::TX, TY = is3 ? YeeTile<3>::TY : YeeTile<2>::TY;
     const int HY = is3 ? 1 : 0;
+    // chunks of 4..32 planes, as long as there are about eight CTAs per SM (a
+    // narrow 2D grid has one column of CTAs: short chunks fill the GPU); the
+    // last chunk takes the remainder
+    if (nzo < 8) {
+        a.cz = nzo;
+    } else {
+        const int64_t ncol = (int64_t)((g.nx + TX - 1) / TX) * (is3 ? (g.ny + TY - 1) / TY : 1);
+        int64_t czl = (int64_t)nzo * ncol / (152 * 8);
+        a.cz = (int)(czl < 4 ? 4 : (czl > 32 ? 32 : czl));
+    }
+    a.nchunks = nzo / a.cz;
+    if (a.nchunks < 1) a.nchunks = 1;
     // E^n 4 planes, B^n and Bh 2 each, J 2, E' 3 (three components each)
     const size_t smem = sizeof(real) * 3 *
                         (4 * (size_t)(TX + 3) * (TY + 3 * HY) + 4 * (size_t)(TX + 2) * (TY + 2 * HY) +
@@ -481,9 +489,13 @@ static void launch_march(const Geom &g, const real *in, real *out, cudaStream_t 
 {
     constexpr int TX = DIM == 3 ? 32 : 256, TY = DIM == 3 ? 8 : 1;
     const int nzo = g.nz + 1;
-    const int cz = nzo >= 128 ? 64 : (nzo >= 16 ? 8 : nzo);
-    const int nchunks = nzo / cz > 0 ? nzo / cz : 1;
     const unsigned nb = (unsigned)(((g.nx + TX - 1) / TX) * (DIM == 3 ? (g.ny + TY - 1) / TY : 1));
+    // z chunks of 8..64 planes, as long as there are about eight CTAs per SM
+    // (a narrow 2D grid has one column of CTAs: short chunks fill the GPU)
+    int64_t czl = (int64_t)nzo * nb / (152 * 8);
+    czl = czl < 8 ? 8 : (czl > 64 ? 64 : czl);
+    const int cz = (int)(czl < nzo ? czl : nzo);
+    const int nchunks = nzo / cz > 0 ? nzo / cz : 1;
     filter_march_kernel<real, DIM, H><<<dim3(nb, (unsigned)nchunks, 1), 256, 0, s>>>(g, in, out, cz, nchunks);
 }
 

@@ -458,6 +458,8 @@ struct AdjArgs {
     real *lE[3], *lB[3];            // reverse: field cotangents at n
     real *lx, *ly, *lz, *lux, *luy, *luz;  // reverse: particle cotangents
     double *lw;                     // reverse: weight cotangents per slot
+    const unsigned char *lj_plane;  // reverse: 1 for the z planes where lJ is not all zero
+    int with_ions;                  // the drifting ion of every slot too
 };
 
 // host launchers (defined in the .cu files)
@@ -500,11 +502,9 @@ void launch_antenna(const Geom &g, real *J, int pol, int ka, double j0, double h
 template <typename real>
 void launch_field_sums(const Geom &g, real *const F[9], double *partials, int nblocks,
                        cudaStream_t s);
-// adjoint (2D CIC): flat forward steps and their transposes
+// adjoint: flat forward steps (electrons, and the slots' ions) and their transposes
 template <typename real> void launch_adj_push(const AdjArgs<real> &a, cudaStream_t s);
-template <typename real> void launch_adj_ions(const AdjArgs<real> &a, cudaStream_t s);
 template <typename real> void launch_adj_push_vjp(const AdjArgs<real> &a, cudaStream_t s);
-template <typename real> void launch_adj_ion_vjp(const AdjArgs<real> &a, cudaStream_t s);
 template <typename real>
 void launch_adj_yee(const Geom &g, real *lE[3], real *lB[3], real *lE0[3], real *pE[3], real *lJ[3], double dt,
                     double hx, double hy, double hz, cudaStream_t s);
@@ -513,5 +513,8 @@ void launch_adj_antenna(const Geom &g, const real *lJ, int pol, int ka, double h
                         double waist, double fa, double fw, double *s, cudaStream_t st);
 void launch_adj_profile(int64_t n, const double *lw, const void *w, int precision, const double *zeta, int M,
                         const double *coef, double *out, cudaStream_t s);
+// planes[k] = 1 where any of the three components of lJ is non-zero on plane k
+template <typename real>
+void launch_adj_planes(const Geom &g, real *const lJ[3], unsigned char *planes, cudaStream_t s);
 
 }  // namespace pic
