@@ -36,11 +36,24 @@ unsigned adj_grid(int64_t n, int block)
     return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
-// field value at node (i, j, k) of a component (x, y periodic; z periodic or
-// zero outside the component's valid range)
-template <typename real>
-__device__ __forceinline__ real fval(const Geom &g, const real *F, int i, int j, int k, bool half_z)
+// Is every node a particle in cell (ci, cj, ck) reads or deposits to (gather
+// supports, Esirkepov windows of a move of less than a cell) inside the grid,
+// with no wrap and no clipping?  Such a particle addresses its nodes directly.
+template <int DIM, int S>
+__device__ __forceinline__ bool inner_cell(const Geom &g, int ci, int cj, int ck)
 {
+    constexpr int M = S + 3;
+    return ci >= M && ci <= g.nx - M - 2 && (DIM == 2 || (cj >= M && cj <= g.ny - M - 2)) && ck >= M &&
+           ck <= g.nz - M - 2;
+}
+
+// field value at node (i, j, k) of a component (x, y periodic; z periodic or
+// zero outside the component's valid range; `inner`: the node is known to be
+// inside, see inner_cell)
+template <typename real>
+__device__ __forceinline__ real fval(const Geom &g, const real *F, int i, int j, int k, bool half_z, bool inner)
+{
+    if (inner) return F[(int64_t)k * g.plane + (j * g.nx + i)];
     i = wrap1(i, g.nx);
     j = g.dim == 3 ? wrap1(j, g.ny) : 0;
     if (g.bc_z == 0) k = wrapi(k, g.nz);
@@ -51,9 +64,13 @@ __device__ __forceinline__ real fval(const Geom &g, const real *F, int i, int j,
 // atomically add v at node (i, j, k) (dropped outside the valid z range; an
 // exact zero, e.g. a window node outside both supports, is not added)
 template <typename real>
-__device__ __forceinline__ void fadd(const Geom &g, real *F, int i, int j, int k, bool half_z, real v)
+__device__ __forceinline__ void fadd(const Geom &g, real *F, int i, int j, int k, bool half_z, real v, bool inner)
 {
     if (v == real(0)) return;
+    if (inner) {
+        atomicAdd(F + (int64_t)k * g.plane + (j * g.nx + i), v);
+        return;
+    }
     i = wrap1(i, g.nx);
     j = g.dim == 3 ? wrap1(j, g.ny) : 0;
     if (g.bc_z == 0) k = wrapi(k, g.nz);
@@ -138,7 +155,8 @@ struct GatherFwd {
     real wx[6][S + 1], wy[6][S + 1], wz[6][S + 1], f[6];
     int bx[6], by[6], bz[6];
     template <typename Args>
-    __device__ __forceinline__ GatherFwd(const Args &a, int ci, int cj, int ck, real ox, real oy, real oz)
+    __device__ __forceinline__ GatherFwd(const Args &a, int ci, int cj, int ck, real ox, real oy, real oz,
+                                         bool inner)
     {
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
@@ -160,7 +178,7 @@ struct GatherFwd {
                     real r = 0;
 #pragma unroll
                     for (int q = 0; q <= S; ++q)
-                        r += wx[c][q] * fval(a.g, F, bx[c] + q, by[c] + b, bz[c] + cc, hz_of(c));
+                        r += wx[c][q] * fval(a.g, F, bx[c] + q, by[c] + b, bz[c] + cc, hz_of(c), inner);
                     sum += wz[c][cc] * wy[c][b] * r;
                 }
             }
@@ -178,7 +196,8 @@ struct GatherGrad {
     real wx[6][S + 1], wy[6][S + 1], wz[6][S + 1], f[6], gx[6], gy[6], gz[6];
     int bx[6], by[6], bz[6];
     template <typename Args>
-    __device__ __forceinline__ GatherGrad(const Args &a, int ci, int cj, int ck, real ox, real oy, real oz)
+    __device__ __forceinline__ GatherGrad(const Args &a, int ci, int cj, int ck, real ox, real oy, real oz,
+                                          bool inner, bool load)
     {
         real dxi[S + 1], dxh[S + 1], dyi[S + 1], dyh[S + 1], dzi[S + 1], dzh[S + 1];
         spline_dw<S>(ox, dxi);
@@ -210,7 +229,7 @@ struct GatherGrad {
                     real r = 0, rd = 0;
 #pragma unroll
                     for (int q = 0; q <= S; ++q) {
-                        const real v = fval(a.g, F, bx[c] + q, by[c] + b, bz[c] + cc, hz_of(c));
+                        const real v = load ? fval(a.g, F, bx[c] + q, by[c] + b, bz[c] + cc, hz_of(c), inner) : real(0);
                         r += wx[c][q] * v;
                         rd += dwx[q] * v;
                     }
@@ -232,20 +251,43 @@ struct GatherGrad {
 
 // ------------------------------------------------------------ flat forward
 
-// One step of drifting ion p of the flat store: z move by the drift's
-// displacement and the z-only deposit (the electron kernel calls it for the
-// ion of every slot).
+// A slot's drifting-ion state, loaded with the electron's before either is
+// used so that the loads of both share one memory round trip.
+template <typename real, int DIM>
+struct IonSlot {
+    bool alive;
+    int ci, cj, ck;
+    real ox, oy, oz;
+    __device__ __forceinline__ IonSlot(const AdjArgs<real> &a, int64_t p)
+    {
+        alive = a.with_ions && a.iin.alive[p];
+        ci = cj = ck = 0;
+        ox = oy = oz = real(0);
+        if (a.with_ions) {
+            ci = a.ion_ci[p];
+            ck = a.iin.ck[p];
+            ox = a.ion_ox[p];
+            oz = a.iin.oz[p];
+            if (DIM == 3) {
+                cj = a.ion_cj[p];
+                oy = a.ion_oy[p];
+            }
+        }
+    }
+};
+
+// One step of drifting ion p of the flat store (alive, state i, weight w):
+// z move by the drift's displacement and the z-only deposit (the electron
+// kernel calls it for the ion of every slot).
 template <typename real, int DIM, int S>
-__device__ __forceinline__ void adj_ion_step(const AdjArgs<real> &a, const Drift<real> &drift, int64_t p)
+__device__ __forceinline__ void adj_ion_step(const AdjArgs<real> &a, const Drift<real> &drift, int64_t p,
+                                             const IonSlot<real, DIM> &i, real w, bool deposit)
 {
     constexpr int W = S + 2;
     const Geom &g = a.g;
-    if (!a.iin.alive[p]) {
-        a.iout.alive[p] = 0;
-        return;
-    }
-    const int ci = a.ion_ci[p], cj = DIM == 3 ? a.ion_cj[p] : 0, ck = a.iin.ck[p];
-    const real ox = a.ion_ox[p], oy = DIM == 3 ? a.ion_oy[p] : real(0), oz = a.iin.oz[p];
+    const int ci = i.ci, cj = i.cj, ck = i.ck;
+    const real ox = i.ox, oy = i.oy, oz = i.oz;
+    const bool inner = inner_cell<DIM, S>(g, ci, cj, ck);
     const real z1 = add_rn(oz, drift.dz);
     real S0z[W], DSz[W], wx[S + 1], wy[S + 1];
     bool cr;
@@ -256,15 +298,18 @@ __device__ __forceinline__ void adj_ion_step(const AdjArgs<real> &a, const Drift
     else
 #pragma unroll
         for (int q = 0; q <= S; ++q) wy[q] = real(q == 0);
-    const real fz = a.jfac_iz * a.w[p];
+    const real fz = a.jfac_iz * w;
     real acc = 0;
+    if (deposit) {
 #pragma unroll
-    for (int c = 0; c < W - 1; ++c) {
-        acc += DSz[c];
+        for (int c = 0; c < W - 1; ++c) {
+            acc += DSz[c];
 #pragma unroll
-        for (int b = 0; b < (DIM == 3 ? S + 1 : 1); ++b)
+            for (int b = 0; b < (DIM == 3 ? S + 1 : 1); ++b)
 #pragma unroll
-            for (int q = 0; q <= S; ++q) fadd(g, a.J[2], bx + q, by + b, az + c, true, fz * acc * wx[q] * wy[b]);
+                for (int q = 0; q <= S; ++q)
+                    fadd(g, a.J[2], bx + q, by + b, az + c, true, fz * acc * wx[q] * wy[b], inner);
+        }
     }
     int sz = 0;
     real noz = z1;
@@ -294,16 +339,37 @@ __global__ void __launch_bounds__(256, 6) adj_push_kernel(AdjArgs<real> a)
     const Geom &g = a.g;
     const Drift<real> drift(a.u_drift, a.dtdh[2]);
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
-        if (a.with_ions) adj_ion_step<real, DIM, S>(a, drift, p);
-        if (!a.in.alive[p]) {
-            a.out.alive[p] = 0;
-            continue;
-        }
+        // the slot's whole state first (a dead slot's values are not used)
+        const bool alive = a.in.alive[p];
         const int ci = a.in.ci[p], cj = DIM == 3 ? a.in.cj[p] : 0, ck = a.in.ck[p];
         const real ox = a.in.ox[p], oy = DIM == 3 ? a.in.oy[p] : real(0), oz = a.in.oz[p], w = a.w[p];
         const real du[3] = {a.in.ux[p], a.in.uy[p], a.in.uz[p]};
-        const GatherFwd<real, DIM, S> gf(a, ci, cj, ck, ox, oy, oz);
-        const BorisFwd<real> bf(du, drift.U, gf.f, gf.f + 3, a.eps);
+        const IonSlot<real, DIM> ion(a, p);
+        // no field within reach: the gather is zero (skipped); an electron
+        // at rest relative to the drift then moves with its drifting ion, bit
+        // for bit, and if the two share their position their deposits cancel
+        // exactly: neither is made
+        const bool field = alive && a.f_plane[ck];
+        const bool together = alive && ion.alive && !field && du[0] == real(0) && du[1] == real(0) &&
+                              du[2] == real(0) && ci == ion.ci && ck == ion.ck && ox == ion.ox && oz == ion.oz &&
+                              (DIM == 2 || (cj == ion.cj && oy == ion.oy));
+        if (ion.alive) adj_ion_step<real, DIM, S>(a, drift, p, ion, w, !together);
+        else if (a.with_ions) a.iout.alive[p] = 0;
+        if (!alive) {
+            a.out.alive[p] = 0;
+            continue;
+        }
+        const bool inner = inner_cell<DIM, S>(g, ci, cj, ck);
+        real fe[6];
+        if (field) {
+            const GatherFwd<real, DIM, S> gf(a, ci, cj, ck, ox, oy, oz, inner);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) fe[c] = gf.f[c];
+        } else {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) fe[c] = real(0);
+        }
+        const BorisFwd<real> bf(du, drift.U, fe, fe + 3, a.eps);
         const real ux = bf.u[0], uy = bf.u[1], uz = bf.u[2];
         real vx, vy;
         const real dvz = drift_velocity(drift, ux, uy, uz, vx, vy);
@@ -334,23 +400,29 @@ __global__ void __launch_bounds__(256, 6) adj_push_kernel(AdjArgs<real> a)
             }
         }
         const real fx = a.jfac[0] * w, fy = a.jfac[1] * w, fz = a.jfac[2] * w, fyv = a.jyfac * w * vy;
+        if (!together) {
 #pragma unroll
-        for (int q = 0; q < W; ++q)
+            for (int q = 0; q < W; ++q)
 #pragma unroll
-            for (int b = 0; b < WY; ++b)
+                for (int b = 0; b < WY; ++b)
 #pragma unroll
-                for (int c = 0; c < W; ++c) {
-                    if (q < W - 1)
-                        fadd(g, a.J[0], ax + q, ay + b, az + c, false, fx * Rx[q] * tshape(S0y[b], DSy[b], S0z[c], DSz[c]));
-                    if (DIM == 3) {
-                        if (b < W - 1)
-                            fadd(g, a.J[1], ax + q, ay + b, az + c, false, fy * Ry[b] * tshape(S0z[c], DSz[c], S0x[q], DSx[q]));
-                    } else {
-                        fadd(g, a.J[1], ax + q, 0, az + c, false, fyv * tshape(S0x[q], DSx[q], S0z[c], DSz[c]));
+                    for (int c = 0; c < W; ++c) {
+                        if (q < W - 1)
+                            fadd(g, a.J[0], ax + q, ay + b, az + c, false,
+                                 fx * Rx[q] * tshape(S0y[b], DSy[b], S0z[c], DSz[c]), inner);
+                        if (DIM == 3) {
+                            if (b < W - 1)
+                                fadd(g, a.J[1], ax + q, ay + b, az + c, false,
+                                     fy * Ry[b] * tshape(S0z[c], DSz[c], S0x[q], DSx[q]), inner);
+                        } else {
+                            fadd(g, a.J[1], ax + q, 0, az + c, false, fyv * tshape(S0x[q], DSx[q], S0z[c], DSz[c]),
+                                 inner);
+                        }
+                        if (c < W - 1)
+                            fadd(g, a.J[2], ax + q, ay + b, az + c, true,
+                                 fz * Rz[c] * tshape(S0x[q], DSx[q], S0y[b], DSy[b]), inner);
                     }
-                    if (c < W - 1)
-                        fadd(g, a.J[2], ax + q, ay + b, az + c, true, fz * Rz[c] * tshape(S0x[q], DSx[q], S0y[b], DSy[b]));
-                }
+        }
         // new cell (an offset that rounds to 1 moves on)
         int sx = (int)floor(x1), sy = DIM == 3 ? (int)floor(y1) : 0, sz = (int)floor(z1);
         real nox = x1 - real(sx), noy = DIM == 3 ? y1 - real(sy) : real(0), noz = z1 - real(sz);
@@ -359,10 +431,10 @@ __global__ void __launch_bounds__(256, 6) adj_push_kernel(AdjArgs<real> a)
         if (noz >= real(1)) { sz += 1; noz = 0; }
         const int ni = wrapi(ci + sx, g.nx), nj = DIM == 3 ? wrapi(cj + sy, g.ny) : 0;
         int nk = ck + sz;
-        bool alive = true;
+        bool stays = true;
         if (g.bc_z == 0) nk = wrapi(nk, g.nz);
-        else if (nk < 0 || nk >= g.nz) alive = false;
-        a.out.alive[p] = alive ? 1 : 0;
+        else if (nk < 0 || nk >= g.nz) stays = false;
+        a.out.alive[p] = stays ? 1 : 0;
         a.out.ci[p] = ni;
         a.out.ck[p] = nk;
         a.out.ox[p] = nox;
@@ -390,26 +462,19 @@ __device__ __forceinline__ real dwin(int q, int r, const real dw[S + 1])
     return v;
 }
 
-// Weight cotangent of drifting ion p in one step (its position does not
-// depend on the parameters); the electron VJP kernel calls it for every slot.
+// Weight cotangent of a slot's drifting ion (state i, alive) in one step (its
+// position does not depend on the parameters); the electron VJP kernel calls
+// it for every slot and adds the result to the slot's weight cotangent.
 template <typename real, int DIM, int S>
-__device__ __forceinline__ void adj_ion_vjp_one(const AdjArgs<real> &a, const Drift<real> &drift, int64_t p)
+__device__ __forceinline__ real adj_ion_vjp_one(const AdjArgs<real> &a, const Drift<real> &drift,
+                                                const IonSlot<real, DIM> &i)
 {
     constexpr int W = S + 2;
     const Geom &g = a.g;
-    if (!a.iin.alive[p]) return;
-    const int ci = a.ion_ci[p], cj = DIM == 3 ? a.ion_cj[p] : 0, ck = a.iin.ck[p];
-    {
-        bool any = false;
-#pragma unroll
-        for (int d = -S - 2; d <= S + 2; ++d) {
-            int k = ck + d;
-            if (g.bc_z == 0) k = wrapi(k, g.nz);
-            if (k >= 0 && k <= g.nz && a.lj_plane[k]) any = true;
-        }
-        if (!any) return;  // no current cotangent where this ion deposits
-    }
-    const real ox = a.ion_ox[p], oy = DIM == 3 ? a.ion_oy[p] : real(0), oz = a.iin.oz[p];
+    const int ci = i.ci, cj = i.cj, ck = i.ck;
+    const bool inner = inner_cell<DIM, S>(g, ci, cj, ck);
+    if (!a.lj_plane[ck]) return real(0);  // no current cotangent where this ion deposits
+    const real ox = i.ox, oy = i.oy, oz = i.oz;
     const real z1 = add_rn(oz, drift.dz);
     real S0z[W], DSz[W], wx[S + 1], wy[S + 1];
     bool cr;
@@ -428,9 +493,9 @@ __device__ __forceinline__ void adj_ion_vjp_one(const AdjArgs<real> &a, const Dr
         for (int b = 0; b < (DIM == 3 ? S + 1 : 1); ++b)
 #pragma unroll
             for (int q = 0; q <= S; ++q)
-                L += acc * wx[q] * wy[b] * fval(g, (const real *)a.J[2], bx + q, by + b, az + c, true);
+                L += acc * wx[q] * wy[b] * fval(g, (const real *)a.J[2], bx + q, by + b, az + c, true, inner);
     }
-    a.lw[p] += (double)(a.jfac_iz * L);
+    return a.jfac_iz * L;
 }
 
 // Cotangents of one electron step.  Reads the state at n (x^n, du^{n-1/2}),
@@ -446,27 +511,32 @@ __global__ void __launch_bounds__(256, 3) adj_push_vjp_kernel(AdjArgs<real> a)
     const Drift<real> drift(a.u_drift, a.dtdh[2]);
     const real half = real(0.5), third = real(1) / real(3);
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
-        if (a.with_ions) adj_ion_vjp_one<real, DIM, S>(a, drift, p);
-        if (!a.in.alive[p]) continue;
+        // the slot's whole state and cotangents first (a dead slot's values
+        // are not used)
+        const bool alive = a.in.alive[p];
         const int ci = a.in.ci[p], cj = DIM == 3 ? a.in.cj[p] : 0, ck = a.in.ck[p];
+        const real ox = a.in.ox[p], oy = DIM == 3 ? a.in.oy[p] : real(0), oz = a.in.oz[p], w = a.w[p];
+        const real du0[3] = {a.in.ux[p], a.in.uy[p], a.in.uz[p]};
+        const real clx = a.lx[p], cly = DIM == 3 ? a.ly[p] : real(0), clz = a.lz[p];
+        const real clux = a.lux[p], cluy = a.luy[p], cluz = a.luz[p];
+        const double lw0 = a.lw[p];
+        const IonSlot<real, DIM> ion(a, p);
+        const real Lwi = ion.alive ? adj_ion_vjp_one<real, DIM, S>(a, drift, ion) : real(0);
+        if (!alive) {
+            if (Lwi != real(0)) a.lw[p] = lw0 + (double)Lwi;
+            continue;
+        }
         // a particle whose incoming cotangents are zero and whose deposit
         // reaches no node with a current cotangent contributes nothing (its
         // gather cotangents are then zero too): skip it
-        if (a.lx[p] == real(0) && a.lz[p] == real(0) && (DIM == 2 || a.ly[p] == real(0)) && a.lux[p] == real(0) &&
-            a.luy[p] == real(0) && a.luz[p] == real(0)) {
-            bool any = false;
-#pragma unroll
-            for (int d = -S - 2; d <= S + 2; ++d) {
-                int k = ck + d;
-                if (g.bc_z == 0) k = wrapi(k, g.nz);
-                if (k >= 0 && k <= g.nz && a.lj_plane[k]) any = true;
-            }
-            if (!any) continue;
+        if (clx == real(0) && clz == real(0) && cly == real(0) && clux == real(0) && cluy == real(0) &&
+            cluz == real(0) && !a.lj_plane[ck]) {
+            if (Lwi != real(0)) a.lw[p] = lw0 + (double)Lwi;
+            continue;
         }
-        const real ox = a.in.ox[p], oy = DIM == 3 ? a.in.oy[p] : real(0), oz = a.in.oz[p], w = a.w[p];
         // ---- recompute the forward values of this step
-        const real du0[3] = {a.in.ux[p], a.in.uy[p], a.in.uz[p]};
-        const GatherGrad<real, DIM, S> gf(a, ci, cj, ck, ox, oy, oz);
+        const bool inner = inner_cell<DIM, S>(g, ci, cj, ck);
+        const GatherGrad<real, DIM, S> gf(a, ci, cj, ck, ox, oy, oz, inner, a.f_plane[ck] != 0);
         const BorisFwd<real> bf(du0, drift.U, gf.f, gf.f + 3, a.eps);
         const real eps = a.eps, U = drift.U;
         const real ux = bf.u[0], uy = bf.u[1], uz = bf.u[2];
@@ -531,7 +601,7 @@ __global__ void __launch_bounds__(256, 3) adj_push_vjp_kernel(AdjArgs<real> a)
 #pragma unroll
                 for (int c = 0; c < W; ++c) {
                     if (q < W - 1) {  // Jx = fx Rx[q] T(y_b, z_c)
-                        const real l = fval(g, (const real *)a.J[0], ax + q, ay + b, az + c, false);
+                        const real l = fval(g, (const real *)a.J[0], ax + q, ay + b, az + c, false, inner);
                         const real T = tshape(S0y[b], DSy[b], S0z[c], DSz[c]);
                         gRx[q] += fx * T * l;
                         Lw += a.jfac[0] * Rx[q] * T * l;
@@ -545,7 +615,7 @@ __global__ void __launch_bounds__(256, 3) adj_push_vjp_kernel(AdjArgs<real> a)
                     }
                     if (DIM == 3) {
                         if (b < W - 1) {  // Jy = fy Ry[b] T(z_c, x_q)
-                            const real l = fval(g, (const real *)a.J[1], ax + q, ay + b, az + c, false);
+                            const real l = fval(g, (const real *)a.J[1], ax + q, ay + b, az + c, false, inner);
                             const real T = tshape(S0z[c], DSz[c], S0x[q], DSx[q]);
                             gRy[b] += fy * T * l;
                             Lw += a.jfac[1] * Ry[b] * T * l;
@@ -556,7 +626,7 @@ __global__ void __launch_bounds__(256, 3) adj_push_vjp_kernel(AdjArgs<real> a)
                             gDSx[q] += k * dT1(S0z[c], DSz[c]);
                         }
                     } else {  // 2D out of plane: Jy = fy1 w T(x_q, z_c)
-                        const real l = fval(g, (const real *)a.J[1], ax + q, 0, az + c, false);
+                        const real l = fval(g, (const real *)a.J[1], ax + q, 0, az + c, false, inner);
                         Ly += tshape(S0x[q], DSx[q], S0z[c], DSz[c]) * l;
                         const real k = fy1 * w * l;
                         gS0x[q] += k * dT0(S0z[c], DSz[c]);
@@ -565,7 +635,7 @@ __global__ void __launch_bounds__(256, 3) adj_push_vjp_kernel(AdjArgs<real> a)
                         gDSz[c] += k * dT1(S0x[q], DSx[q]);
                     }
                     if (c < W - 1) {  // Jz = fz Rz[c] T(x_q, y_b)
-                        const real l = fval(g, (const real *)a.J[2], ax + q, ay + b, az + c, true);
+                        const real l = fval(g, (const real *)a.J[2], ax + q, ay + b, az + c, true, inner);
                         const real T = tshape(S0x[q], DSx[q], S0y[b], DSy[b]);
                         gRz[c] += fz * T * l;
                         Lw += a.jfac[2] * Rz[c] * T * l;
@@ -607,9 +677,9 @@ __global__ void __launch_bounds__(256, 3) adj_push_vjp_kernel(AdjArgs<real> a)
             }
         }
         // ---- move transposed: x1 = ox + vx dtdh_x (and y), z1 = oz + dz_d + dvz dtdh_z
-        lx1 += a.lx[p];
-        lz1 += a.lz[p];
-        if (DIM == 3) ly1 += a.ly[p];
+        lx1 += clx;
+        lz1 += clz;
+        if (DIM == 3) ly1 += cly;
         const real lvx = a.dtdh[0] * lx1, lvz = a.dtdh[2] * lz1;
         const real lvy = DIM == 3 ? a.dtdh[1] * ly1 : a.jyfac * w * Ly;
         // velocity transposed: v = u / gamma (u the full momentum), d v / d du
@@ -619,9 +689,9 @@ __global__ void __launch_bounds__(256, 3) adj_push_vjp_kernel(AdjArgs<real> a)
         const real ig = rsqrt_p(drift.g2 + (uz * (real(2) * U + uz) + ux * ux + uy * uy));
         const real ig2 = ig * ig;
         const real cx = lvy * vz - lvz * vy, cy = lvz * vx - lvx * vz, cz = lvx * vy - lvy * vx;  // l x v
-        const real lux = a.lux[p] + ig * (lvx * ig2 + (vy * cz - vz * cy));
-        const real luy = a.luy[p] + ig * (lvy * ig2 + (vz * cx - vx * cz));
-        const real luz = a.luz[p] + ig * (lvz * ig2 + (vx * cy - vy * cx));
+        const real lux = clux + ig * (lvx * ig2 + (vy * cz - vz * cy));
+        const real luy = cluy + ig * (lvy * ig2 + (vz * cx - vx * cz));
+        const real luz = cluz + ig * (lvz * ig2 + (vx * cy - vy * cx));
         // ---- Boris transposed
         const real sx = bf.s[0], sy = bf.s[1], sz = bf.s[2], tx = bf.t[0], ty = bf.t[1], tz = bf.t[2];
         const real upx = bf.up[0], upy = bf.up[1], upz = bf.up[2];
@@ -672,7 +742,7 @@ __global__ void __launch_bounds__(256, 3) adj_push_vjp_kernel(AdjArgs<real> a)
 #pragma unroll
                     for (int q = 0; q <= S; ++q)
                         fadd(g, LF, gf.bx[c] + q, gf.by[c] + b, gf.bz[c] + cc, hz_of(c),
-                             l * gf.wx[c][q] * gf.wy[c][b] * gf.wz[c][cc]);
+                             l * gf.wx[c][q] * gf.wy[c][b] * gf.wz[c][cc], inner);
         }
         // ---- write the cotangents of x^n, du^{n-1/2}; the weight's
         a.lx[p] = lx1 + lx0;
@@ -681,7 +751,7 @@ __global__ void __launch_bounds__(256, 3) adj_push_vjp_kernel(AdjArgs<real> a)
         a.lux[p] = ldmx;
         a.luy[p] = ldmy;
         a.luz[p] = ldmz;
-        a.lw[p] += (double)Lw;
+        a.lw[p] = lw0 + (double)Lwi + (double)Lw;
     }
 }
 
@@ -857,21 +927,37 @@ __global__ void adj_profile_kernel(int64_t n, const double *lw, const void *w, i
     }
 }
 
-// planes[k] = 1 where lJ (three components) is not all zero on plane k
+// near[k] = 1 for every cell plane k within S + 2 planes of a z plane on which
+// one of nc components (consecutive arrays of g.ncomp values) is not zero: a
+// particle in cell k reads and deposits only within that reach, so a particle
+// with near[k] = 0 sees zero there.  One CTA reduces one plane at a time.
 template <typename real>
-__global__ void adj_planes_kernel(Geom g, const real *J0, const real *J1, const real *J2, unsigned char *planes)
+__global__ void adj_planes_kernel(Geom g, const real *F, int nc, unsigned char *near)
 {
-    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < (int64_t)(g.nz + 1) * g.plane;
-         o += (int64_t)gridDim.x * blockDim.x)
-        if (J0[o] != real(0) || J1[o] != real(0) || J2[o] != real(0)) planes[o / g.plane] = 1;
+    const int R = g.shape + 2, nk = g.bc_z == 0 ? g.nz : g.nz + 1;
+    for (int k = (int)blockIdx.x; k < nk; k += (int)gridDim.x) {
+        int any = 0;
+        for (int c = 0; c < nc; ++c) {
+            const real *P = F + (int64_t)c * g.ncomp + (int64_t)k * g.plane;
+            for (int64_t o = threadIdx.x; o < g.plane; o += blockDim.x) any |= P[o] != real(0);
+        }
+        if (__syncthreads_or(any) && threadIdx.x == 0) {
+            for (int d = -R; d <= R; ++d) {
+                int kk = k + d;
+                if (g.bc_z == 0) kk = wrap1(kk, g.nz);
+                else if (kk < 0 || kk > g.nz) continue;
+                near[kk] = 1;
+            }
+        }
+    }
 }
 
 template <typename real>
-void launch_adj_planes(const Geom &g, real *const lJ[3], unsigned char *planes, cudaStream_t s)
+void launch_adj_planes(const Geom &g, const real *F, int nc, unsigned char *near, cudaStream_t s)
 {
-    cudaMemsetAsync(planes, 0, (size_t)g.nz + 1, s);
-    adj_planes_kernel<real><<<adj_grid((int64_t)(g.nz + 1) * g.plane, 256), 256, 0, s>>>(g, lJ[0], lJ[1], lJ[2],
-                                                                                           planes);
+    cudaMemsetAsync(near, 0, (size_t)g.nz + 1, s);
+    const int nk = g.nz + 1;
+    adj_planes_kernel<real><<<(unsigned)(nk < 152 * 16 ? nk : 152 * 16), 128, 0, s>>>(g, F, nc, near);
 }
 
 // --------------------------------------------------------------- launchers
@@ -942,7 +1028,7 @@ void launch_adj_profile(int64_t n, const double *lw, const void *w, int precisio
     template void launch_adj_push_vjp<real>(const AdjArgs<real> &, cudaStream_t);                              \
     template void launch_adj_yee<real>(const Geom &, real *[3], real *[3], real *[3], real *[3], real *[3],     \
                                        double, double, double, double, cudaStream_t);                          \
-    template void launch_adj_planes<real>(const Geom &, real *const[3], unsigned char *, cudaStream_t);        \
+    template void launch_adj_planes<real>(const Geom &, const real *, int, unsigned char *, cudaStream_t);     \
     template void launch_adj_antenna<real>(const Geom &, const real *, int, int, double, double, double, double, \
                                            double, double, double, double *, cudaStream_t);
 PIC_ADJ_INSTANTIATE(float)

@@ -1730,7 +1730,7 @@ struct AdjLayout {
     size_t total = 0;
     // inside one particle state
     size_t e_ci = 0, e_cj = 0, e_ck = 0, e_ox = 0, e_oy = 0, e_oz = 0, e_ux = 0, e_uy = 0, e_uz = 0, e_alive = 0;
-    size_t i_ck = 0, i_oz = 0, i_alive = 0;
+    size_t i_ck = 0, i_oz = 0, i_alive = 0, fm = 0;
 };
 
 AdjLayout adj_layout(int64_t P, int N, int K, size_t es, int64_t ncomp, bool dim3, int64_t nz1)
@@ -1767,6 +1767,7 @@ AdjLayout adj_layout(int64_t P, int N, int K, size_t es, int64_t ncomp, bool dim
     L.i_ck = sub(4 * P);
     L.i_oz = sub(es * P);
     L.i_alive = sub(P);
+    L.fm = sub(nz1);  // cells within reach of a nonzero field of the state
     L.st = q;
     L.fl = align_up(6 * es * ncomp);
     L.w = take(es * P);
@@ -1948,6 +1949,8 @@ static void adj_step(pic_ctx *c, const AdjLayout &L, unsigned char *sa, unsigned
     a.iin = flat_i<real>(sa, L);
     a.iout = flat_i<real>(sb, L);
     adj_common<real>(c, L, a);
+    launch_adj_planes<real>(c->g, (const real *)fa, 6, sa + L.fm, c->stream);
+    a.f_plane = sa + L.fm;
     launch_adj_push<real>(a, c->stream);
     real *Rc[3] = {R, R + nc, R + 2 * nc};
     if (c->laser_on && c->ka >= 2) {
@@ -2102,7 +2105,7 @@ static pic_status adj_backward_t(pic_ctx *c, const void *cot, double *grad)
             launch_adj_yee<real>(c->g, lE, lB, lE0, pE, lJ, c->dt, c->hx, c->hy, c->hz, c->stream);
             for (int q = 0; q < 3; ++q) std::swap(lE[q], lE0[q]);
             launch_filter<real>(c->g, lJ, (real *)(B + L.tmp), c->p.filter_passes, c->stream);
-            launch_adj_planes<real>(c->g, lJ, B + L.planes, c->stream);
+            launch_adj_planes<real>(c->g, lJ[0], 3, B + L.planes, c->stream);
             if (c->laser_on && c->ka >= 2) {
                 const double j0 = antenna_j0(c, A.tn[n], l.a0);
                 // j0 is linear in a0; the profile exp(-r^2/w0^2) gives 2 r^2 / w0^3
@@ -2131,6 +2134,7 @@ static pic_status adj_backward_t(pic_ctx *c, const void *cot, double *grad)
             a.luz = (real *)(B + L.luz);
             a.lw = (double *)(B + L.lw);
             a.lj_plane = B + L.planes;
+            a.f_plane = st(s) + L.fm;  // made by the forward step from this state
             launch_adj_push_vjp<real>(a, c->stream);
         }
     }

@@ -39,8 +39,18 @@ __device__ double lab_density(const InjectArgs &a, double z)
     if (a.ramp > 0.0 && z < a.z_start + a.ramp) r = (z - a.z_start) / a.ramp;
     double f = 1.0;
     if (a.nprof > 0) {
+        // cos(m pi zeta) by the recurrence cos(m t) = 2 cos t cos((m-1) t) -
+        // cos((m-2) t): one cosine per point (FP64 is the slow pipe here)
         const double zeta = (z - a.z_start) / (a.z_end - a.z_start);
-        for (int m = 1; m <= a.nprof; ++m) f += a.prof[m - 1] * cos((double)m * 3.141592653589793 * zeta);
+        const double c1 = cos(3.141592653589793 * zeta);
+        double cp = 1.0, cm = c1;
+        f += a.prof[0] * c1;
+        for (int m = 2; m <= a.nprof; ++m) {
+            const double cn = 2.0 * c1 * cm - cp;
+            f += a.prof[m - 1] * cn;
+            cp = cm;
+            cm = cn;
+        }
     }
     return a.ne * r * f;
 }
@@ -197,10 +207,13 @@ void launch_inject(const InjectArgs &a, cudaStream_t s)
 {
     const int64_t total = (a.m_hi - a.m_lo) * a.NY * a.NX;
     if (total <= 0) return;
-    int64_t blocks = (total + 255) / 256;
-    if (blocks > 152LL * 64) blocks = 152LL * 64;
-    if (a.precision == 0) inject_kernel<float><<<(unsigned)blocks, 256, 0, s>>>(a);
-    else inject_kernel<double><<<(unsigned)blocks, 256, 0, s>>>(a);
+    // the work per point is FP64 arithmetic, whose pipe is narrow: CTAs of
+    // two warps spread a step's thin band of lattice points over many SMs
+    constexpr int kThreads = 64;
+    int64_t blocks = (total + kThreads - 1) / kThreads;
+    if (blocks > 152LL * 128) blocks = 152LL * 128;
+    if (a.precision == 0) inject_kernel<float><<<(unsigned)blocks, kThreads, 0, s>>>(a);
+    else inject_kernel<double><<<(unsigned)blocks, kThreads, 0, s>>>(a);
 }
 
 }  // namespace pic

@@ -458,7 +458,8 @@ struct AdjArgs {
     real *lE[3], *lB[3];            // reverse: field cotangents at n
     real *lx, *ly, *lz, *lux, *luy, *luz;  // reverse: particle cotangents
     double *lw;                     // reverse: weight cotangents per slot
-    const unsigned char *lj_plane;  // reverse: 1 for the z planes where lJ is not all zero
+    const unsigned char *lj_plane;  // reverse: 1 for the cells ck within reach of a plane where lJ is not zero
+    const unsigned char *f_plane;   // 1 for the cells ck within reach of a plane where E or B is not zero
     int with_ions;                  // the drifting ion of every slot too
 };
 
@@ -515,6 +516,6 @@ void launch_adj_profile(int64_t n, const double *lw, const void *w, int precisio
                         const double *coef, double *out, cudaStream_t s);
 // planes[k] = 1 where any of the three components of lJ is non-zero on plane k
 template <typename real>
-void launch_adj_planes(const Geom &g, real *const lJ[3], unsigned char *planes, cudaStream_t s);
+void launch_adj_planes(const Geom &g, const real *F, int nc, unsigned char *near, cudaStream_t s);
 
 }  // namespace pic
