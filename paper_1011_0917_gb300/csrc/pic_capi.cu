@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <array>
 #include <new>
 #include <string>
 #include <vector>
@@ -106,6 +107,7 @@ struct pic_ctx {
 
     double t = 0;
     int64_t step = 0;
+    int64_t epoch = 0;  // bumped by every call that changes what a step launches
     std::string err;
 
     // adjoint run: the flat store's bands (slot base and lattice planes of
@@ -393,6 +395,7 @@ extern "C" pic_status pic_query_sizes(const pic_ctx *c, pic_sizes *s)
 extern "C" pic_status pic_bind_buffers(pic_ctx *c, const pic_buffers *b)
 {
     if (!c || !b) return PIC_ERR_ARG;
+    c->epoch += 1;
     if (c->bound) return fail(c, PIC_ERR_STATE, "buffers are already bound");
     auto aligned = [](const void *q) { return ((uintptr_t)q % kAlign) == 0; };
     if (!b->fields || !b->species[0] || !b->scratch) return fail(c, PIC_ERR_ARG, "null buffer");
@@ -477,6 +480,7 @@ static void lattice_band(const InjectArgs &a, double zlo, double zhi, int64_t &m
 extern "C" pic_status pic_load_plasma(pic_ctx *c, const pic_plasma_params *p)
 {
     if (!c || !p) return PIC_ERR_ARG;
+    c->epoch += 1;
     if (!c->bound) return fail(c, PIC_ERR_STATE, "bind buffers first");
     const bool dim3 = c->g.dim == 3;
     if (!(p->ne_over_nc >= 0) || !(p->z_end > p->z_start) || !(p->ramp_len >= 0) || p->ppc[0] < 1 ||
@@ -604,6 +608,7 @@ static pic_status load_particles_t(pic_ctx *c, int sp, int64_t n, const double *
 extern "C" pic_status pic_load_particles(pic_ctx *c, int sp, int64_t n, const double *state, const int64_t *ids)
 {
     if (!c || (sp != 0 && sp != 1) || n < 0 || (n > 0 && !state)) return PIC_ERR_ARG;
+    c->epoch += 1;
     if (!c->bound) return fail(c, PIC_ERR_STATE, "bind buffers first");
     if (sp == 1 && !c->ions_species) return fail(c, PIC_ERR_ARG, "drifting ions exist only in a boosted frame");
     if (n > c->slots) return fail(c, PIC_ERR_CAPACITY, "more particles than slots");
@@ -614,6 +619,7 @@ extern "C" pic_status pic_load_particles(pic_ctx *c, int sp, int64_t n, const do
 extern "C" pic_status pic_launch_laser(pic_ctx *c, const pic_laser_params *p)
 {
     if (!c || !p) return PIC_ERR_ARG;
+    c->epoch += 1;
     if (!(p->a0 >= 0) || !(p->waist > 0) || !(p->fwhm > 0) || !std::isfinite(p->z_antenna) ||
         (p->polarization != PIC_POL_X && p->polarization != PIC_POL_Y))
         return fail(c, PIC_ERR_ARG, "invalid laser parameters");
@@ -988,9 +994,48 @@ static pic_status run_steps(pic_ctx *c, int nsteps, unsigned mask, bool check)
 
 // ------------------------------------------------------------------ batch
 
+// The captured graph of a batch, kept between calls while the contexts are
+// where the capture left them: same configuration (epoch), same halves of
+// their double buffers, same window position.
+struct BatchGraph {
+    int K = 0;
+    std::vector<std::array<int64_t, 5>> sig;  // per context: epoch, fset, cur[0], cur[1], win_n
+    std::vector<int64_t> kern;                 // per context: kernels one replay launches
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    StepScal *dev = nullptr;   // nctx x K scalars the graph's kernels read
+    StepScal *host = nullptr;  // pinned: reps x nctx x K, one region per replay
+    size_t host_n = 0;
+    cudaEvent_t join = nullptr;
+    std::vector<cudaEvent_t> ev;  // one per context
+    void drop_graph()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (dev) cudaFree(dev);
+        exec = nullptr;
+        graph = nullptr;
+        dev = nullptr;
+        K = 0;
+        sig.clear();
+    }
+    ~BatchGraph()
+    {
+        if (cs) cudaStreamSynchronize(cs);
+        drop_graph();
+        if (host) cudaFreeHost(host);
+        if (join) cudaEventDestroy(join);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        if (cs) cudaStreamDestroy(cs);
+    }
+};
+
 struct pic_batch {
     std::vector<pic_ctx *> ctx;
     int graph_steps = 20;  // steps per captured graph (even; 0: streams only)
+    BatchGraph gr;
 };
 
 // Whether the contexts' steps can be captured: nothing in them depends on the
@@ -1024,101 +1069,139 @@ static void fill_step_scalars(pic_ctx *c, int K, StepScal *h)
     }
 }
 
-// K steps of every context as one CUDA graph, replayed nsteps / K times; the
-// per-step scalars go through pinned host memory copied at the graph's start.
-// Returns the number of steps done (a multiple of K).
-static pic_status batch_graph_steps(pic_batch *b, int nsteps, int &done)
+static std::array<int64_t, 5> ctx_signature(const pic_ctx *c)
 {
-    done = 0;
-    const int K = b->graph_steps;
-    const int reps = nsteps / K;
-    if (reps < 1) return PIC_OK;
+    return {c->epoch, c->fset, c->cur[0], c->cur[1], c->win_n};
+}
+
+// Capture K steps of every context as one graph on the batch's stream: fork
+// every context's stream from it, K steps each, join.  Step s of context i
+// reads its scalars from dev[i K + s].
+static pic_status batch_capture(pic_batch *b, int K)
+{
+    BatchGraph &G = b->gr;
     const size_t nctx = b->ctx.size();
-    std::vector<StepScal *> host(nctx, nullptr), dev(nctx, nullptr);
-    std::vector<cudaEvent_t> ev(nctx + 1, nullptr);
-    cudaStream_t cs = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    pic_status st = PIC_OK;
-    auto cleanup = [&]() {
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
-        for (auto &e : ev)
-            if (e) cudaEventDestroy(e);
-        for (size_t i = 0; i < nctx; ++i) {
-            if (host[i]) cudaFreeHost(host[i]);
-            if (dev[i]) cudaFree(dev[i]);
-        }
-        if (cs) cudaStreamDestroy(cs);
-    };
     pic_ctx *c0 = b->ctx[0];
     auto bad = [&](cudaError_t e) {
         if (e == cudaSuccess) return false;
         c0->err = std::string("batch graph: ") + cudaGetErrorString(e);
-        st = PIC_ERR_CUDA;
         return true;
     };
-    if (bad(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking))) { cleanup(); return st; }
-    for (auto &e : ev)
-        if (bad(cudaEventCreateWithFlags(&e, cudaEventDisableTiming))) { cleanup(); return st; }
+    G.drop_graph();
+    if (bad(cudaMalloc(&G.dev, sizeof(StepScal) * nctx * K))) return PIC_ERR_CUDA;
     for (size_t i = 0; i < nctx; ++i) {
         pic_ctx *c = b->ctx[i];
-        if (bad(cudaMallocHost(&host[i], sizeof(StepScal) * K)) || bad(cudaMalloc(&dev[i], sizeof(StepScal) * K))) {
-            cleanup();
-            return st;
-        }
         // a band never spans more lattice planes than this (see lattice_band)
         InjectArgs a{};
         fill_inject_common(c, a);
         const double jm = a.jitter * a.hz_lab + a.dzl;
         c->inj_planes_max = (int64_t)std::ceil((c->gam * c->beta * c->dt + 2.0 * jm) / a.dzl) + 8;
     }
-    // capture: fork every context's stream from cs, K steps each, join
-    if (bad(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed))) { cleanup(); return st; }
-    cudaEventRecord(ev[nctx], cs);
-    for (size_t i = 0; i < nctx; ++i) {
-        pic_ctx *c = b->ctx[i];
-        cudaStreamWaitEvent(c->stream, ev[nctx], 0);
-        cudaMemcpyAsync(dev[i], host[i], sizeof(StepScal) * K, cudaMemcpyHostToDevice, c->stream);
-    }
+    if (bad(cudaStreamBeginCapture(G.cs, cudaStreamCaptureModeRelaxed))) return PIC_ERR_CUDA;
+    cudaEventRecord(G.join, G.cs);
+    for (size_t i = 0; i < nctx; ++i) cudaStreamWaitEvent(b->ctx[i]->stream, G.join, 0);
+    std::vector<int64_t> k0(nctx);
+    for (size_t i = 0; i < nctx; ++i) k0[i] = b->ctx[i]->kernels;
     for (int s = 0; s < K; ++s)
         for (size_t i = 0; i < nctx; ++i) {
             pic_ctx *c = b->ctx[i];
             c->capturing = true;
-            c->cap_scal = dev[i];
+            c->cap_scal = G.dev + i * K;
             c->cap_s = s;
             if (c->es == 4) run_phases_t<float>(c, PIC_PH_ALL);
             else run_phases_t<double>(c, PIC_PH_ALL);
             c->capturing = false;
         }
     for (size_t i = 0; i < nctx; ++i) {
-        cudaEventRecord(ev[i], b->ctx[i]->stream);
-        cudaStreamWaitEvent(cs, ev[i], 0);
+        cudaEventRecord(G.ev[i], b->ctx[i]->stream);
+        cudaStreamWaitEvent(G.cs, G.ev[i], 0);
     }
-    if (bad(cudaStreamEndCapture(cs, &graph))) { cleanup(); return st; }
-    if (bad(cudaGraphInstantiate(&exec, graph, 0))) { cleanup(); return st; }
+    const cudaError_t e = cudaStreamEndCapture(G.cs, &G.graph);
     // the capture flipped every double buffer K times (K even: back where it
-    // was) and counted the kernels of K steps; replay
-    std::vector<int64_t> kern(nctx);
+    // was) and counted the kernels of K steps, which every replay adds
+    G.sig.assign(nctx, {});
+    G.kern.assign(nctx, 0);
     for (size_t i = 0; i < nctx; ++i) {
-        kern[i] = b->ctx[i]->kernels;
-        b->ctx[i]->kernels = 0;
+        pic_ctx *c = b->ctx[i];
+        G.kern[i] = c->kernels - k0[i];
+        c->kernels = k0[i];
+        G.sig[i] = ctx_signature(c);
     }
-    for (int r = 0; r < reps; ++r) {
-        // the previous replay has read its scalars before they are rewritten
-        if (bad(cudaStreamSynchronize(cs))) { cleanup(); return st; }
-        for (size_t i = 0; i < nctx; ++i) fill_step_scalars(b->ctx[i], K, host[i]);
-        if (bad(cudaGraphLaunch(exec, cs))) { cleanup(); return st; }
+    if (bad(e) || bad(cudaGraphInstantiate(&G.exec, G.graph, 0))) {
+        G.drop_graph();
+        return PIC_ERR_CUDA;
+    }
+    G.K = K;
+    return PIC_OK;
+}
+
+// K steps of every context as one CUDA graph, replayed nsteps / K times.  The
+// graph is captured once and kept while the contexts stay where it left them.
+// Each replay is preceded, on the batch's stream, by the copy of its own
+// region of per-step scalars from pinned host memory (all regions are filled
+// before the first replay), so no replay waits for the host.  Returns the
+// number of steps done (a multiple of K).
+static pic_status batch_graph_steps(pic_batch *b, int nsteps, int &done)
+{
+    done = 0;
+    BatchGraph &G = b->gr;
+    const int K = b->graph_steps;
+    const int reps = nsteps / K;
+    if (reps < 1) return PIC_OK;
+    const size_t nctx = b->ctx.size();
+    pic_ctx *c0 = b->ctx[0];
+    auto bad = [&](cudaError_t e) {
+        if (e == cudaSuccess) return false;
+        c0->err = std::string("batch graph: ") + cudaGetErrorString(e);
+        return true;
+    };
+    if (!G.cs) {
+        if (bad(cudaStreamCreateWithFlags(&G.cs, cudaStreamNonBlocking))) return PIC_ERR_CUDA;
+        if (bad(cudaEventCreateWithFlags(&G.join, cudaEventDisableTiming))) return PIC_ERR_CUDA;
+    }
+    while (G.ev.size() < nctx) {
+        cudaEvent_t e = nullptr;
+        if (bad(cudaEventCreateWithFlags(&e, cudaEventDisableTiming))) return PIC_ERR_CUDA;
+        G.ev.push_back(e);
+    }
+    // the previous call's copies out of the host regions are done
+    if (bad(cudaStreamSynchronize(G.cs))) return PIC_ERR_CUDA;
+    bool same = G.exec && G.K == K && G.sig.size() == nctx;
+    for (size_t i = 0; same && i < nctx; ++i) same = G.sig[i] == ctx_signature(b->ctx[i]);
+    if (!same) {
+        const pic_status st = batch_capture(b, K);
+        if (st != PIC_OK) return st;
+    }
+    const size_t per = nctx * (size_t)K;
+    if (G.host_n < per * reps) {
+        if (G.host) cudaFreeHost(G.host);
+        G.host = nullptr;
+        G.host_n = 0;
+        if (bad(cudaMallocHost(&G.host, sizeof(StepScal) * per * reps))) return PIC_ERR_CUDA;
+        G.host_n = per * reps;
+    }
+    for (int r = 0; r < reps; ++r)
         for (size_t i = 0; i < nctx; ++i) {
             pic_ctx *c = b->ctx[i];
+            fill_step_scalars(c, K, G.host + r * per + i * K);
             for (int s = 0; s < K; ++s) c->t += c->dt;
             c->step += K;
-            c->kernels += kern[i];
+            c->kernels += G.kern[i];
         }
+    // order after the work already queued on the contexts' streams
+    for (size_t i = 0; i < nctx; ++i) {
+        cudaEventRecord(G.ev[i], b->ctx[i]->stream);
+        cudaStreamWaitEvent(G.cs, G.ev[i], 0);
+    }
+    for (int r = 0; r < reps; ++r) {
+        if (bad(cudaMemcpyAsync(G.dev, G.host + r * per, sizeof(StepScal) * per, cudaMemcpyHostToDevice, G.cs)) ||
+            bad(cudaGraphLaunch(G.exec, G.cs)))
+            return PIC_ERR_CUDA;
         done += K;
     }
-    if (bad(cudaStreamSynchronize(cs))) { cleanup(); return st; }
-    cleanup();
+    // and the contexts' later work after the replays
+    cudaEventRecord(G.join, G.cs);
+    for (size_t i = 0; i < nctx; ++i) cudaStreamWaitEvent(b->ctx[i]->stream, G.join, 0);
     return PIC_OK;
 }
 
@@ -1184,6 +1267,7 @@ extern "C" pic_status pic_step_phases(pic_ctx *c, unsigned mask)
 extern "C" pic_status pic_set_moving_window(pic_ctx *c, double v, double t0, int shift_cells)
 {
     if (!c) return PIC_ERR_ARG;
+    c->epoch += 1;
     if (v == 0.0) {
         c->win_on = false;
         return PIC_OK;
@@ -1226,6 +1310,7 @@ extern "C" pic_status pic_btd_bytes(const pic_ctx *c, const pic_btd_params *p, s
 extern "C" pic_status pic_btd_setup(pic_ctx *c, const pic_btd_params *p, void *buf, size_t bytes)
 {
     if (!c) return PIC_ERR_ARG;
+    c->epoch += 1;
     if (!p) {
         c->btd_on = false;
         c->btd_buf = nullptr;
@@ -1677,6 +1762,7 @@ static pic_status set_state_t(pic_ctx *c, const unsigned char *src, size_t src_b
 extern "C" pic_status pic_set_state(pic_ctx *c, const void *src, size_t src_bytes, int src_is_device)
 {
     if (!c || !src) return PIC_ERR_ARG;
+    c->epoch += 1;
     if (!c->bound) return fail(c, PIC_ERR_STATE, "bind buffers first");
     return c->es == 4 ? set_state_t<float>(c, (const unsigned char *)src, src_bytes, src_is_device)
                       : set_state_t<double>(c, (const unsigned char *)src, src_bytes, src_is_device);
@@ -1687,6 +1773,7 @@ extern "C" pic_status pic_set_state(pic_ctx *c, const void *src, size_t src_byte
 extern "C" pic_status pic_profile(pic_ctx *c, int enable)
 {
     if (!c) return PIC_ERR_ARG;
+    c->epoch += 1;
     c->profiling = enable != 0;
     return PIC_OK;
 }
@@ -2051,6 +2138,7 @@ extern "C" pic_status pic_adjoint_forward(pic_ctx *c, const pic_adjoint_params *
 {
     pic_status s = adj_check(c, p);
     if (s != PIC_OK) return s;
+    c->epoch += 1;
     if (!buf) return PIC_ERR_ARG;
     adj_bands(c, p->nsteps);
     if (bytes < adj_layout(c->adj.P, p->nsteps, p->checkpoint_every, (size_t)c->es, c->g.ncomp, c->g.dim == 3,
@@ -2161,6 +2249,7 @@ static pic_status adj_backward_t(pic_ctx *c, const void *cot, double *grad)
 extern "C" pic_status pic_adjoint_backward(pic_ctx *c, const void *cot, double *grad)
 {
     if (!c || !cot || !grad) return PIC_ERR_ARG;
+    c->epoch += 1;
     if (!c->adj.ready) return fail(c, PIC_ERR_STATE, "run pic_adjoint_forward first");
     return c->es == 4 ? adj_backward_t<float>(c, cot, grad) : adj_backward_t<double>(c, cot, grad);
 }
