@@ -67,6 +67,10 @@ def parse():
                     help="steps of the adjoint/forward timing on one c4 run (0: skip)")
     ap.add_argument("--c4", type=int, default=64,
                     help="runs of the batched scan timed after the main measurement (0: none)")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="time only the adjoint/forward leg (one c4 run, --adjoint-steps steps, a checkpoint "
+                         "every --checkpoint-every) and print its record")
+    ap.add_argument("--checkpoint-every", type=int, default=50)
     return ap.parse_args()
 
 
@@ -315,7 +319,7 @@ def run_ours(args, rank, world, local):
         sim.close()
 
     c4 = run_c4(P, torch, args.c4, args.warmup, 200) if args.c4 > 0 else None
-    adj = run_adjoint(P, torch, args.adjoint_steps, 50) if args.adjoint_steps > 0 else None
+    adj = run_adjoint(P, torch, args.adjoint_steps, args.checkpoint_every) if args.adjoint_steps > 0 else None
 
     result = None
     if rank == 0:
@@ -564,6 +568,13 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         out = run_reference(args, rank, world)
+    elif args.adjoint_only:
+        out = None
+        if rank == 0:
+            import torch
+
+            import paper_1011_0917_gb300 as P
+            out = run_adjoint(P, torch, args.adjoint_steps, args.checkpoint_every)
     else:
         out = run_ours(args, rank, world, local)
     if rank == 0 and out is not None:

@@ -36,6 +36,24 @@ unsigned adj_grid(int64_t n, int block)
     return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
+// (i, j, k) of node o of a component; 32-bit division when the component
+// has fewer than 2^31 nodes (every grid that fits a GPU's memory here)
+__device__ __forceinline__ void node_ijk(const Geom &g, int64_t o, int &i, int &j, int &k)
+{
+    if (g.ncomp <= 0x7fffffffLL) {
+        const unsigned u = (unsigned)o, pl = (unsigned)g.plane, nx = (unsigned)g.nx;
+        const unsigned kk = u / pl, r = u - kk * pl, jj = r / nx;
+        k = (int)kk;
+        j = (int)jj;
+        i = (int)(r - jj * nx);
+    } else {
+        k = (int)(o / g.plane);
+        const int64_t r = o - (int64_t)k * g.plane;
+        j = (int)(r / g.nx);
+        i = (int)(r - (int64_t)j * g.nx);
+    }
+}
+
 // Is every node a particle in cell (ci, cj, ck) reads or deposits to (gather
 // supports, Esirkepov windows of a move of less than a cell) inside the grid,
 // with no wrap and no clipping?  Such a particle addresses its nodes directly.
@@ -766,7 +784,8 @@ __global__ void adj_curl_e_t_kernel(Geom g, real *lEx, real *lEy, real *lEz, con
     const int64_t plane = g.plane;
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < (int64_t)nk * plane;
          o += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(o % g.nx), j = (int)((o / g.nx) % g.ny), k = (int)(o / plane);
+        int i, j, k;
+        node_ijk(g, o, i, j, k);
         const int im = i == 0 ? g.nx - 1 : i - 1, jm = j == 0 ? g.ny - 1 : j - 1;
         // B on half-integer z (Bx, By) exists for k' in [0, nz); Bz on the E planes
         auto bh = [&](const real *B, int ii, int jj, int kk) -> real {
@@ -800,7 +819,8 @@ __global__ void adj_e_update_t_kernel(Geom g, const real *lE1x, const real *lE1y
     const int64_t plane = g.plane;
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < (int64_t)nk * plane;
          o += (int64_t)gridDim.x * blockDim.x) {
-        const int k = (int)(o / plane);
+        int i, j, k;
+        node_ijk(g, o, i, j, k);
         const int64_t r = o - (int64_t)k * plane;  // node within the plane
         const int64_t top = (int64_t)g.nz * plane + r;
         for (int c = 0; c < 2; ++c) {
@@ -841,7 +861,8 @@ __global__ void adj_curl_b_t_kernel(Geom g, const real *pEx, const real *pEy, co
     const int64_t plane = g.plane;
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < (int64_t)nk * plane;
          o += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(o % g.nx), j = (int)((o / g.nx) % g.ny), k = (int)(o / plane);
+        int i, j, k;
+        node_ijk(g, o, i, j, k);
         const int ip = i + 1 == g.nx ? 0 : i + 1, jp = j + 1 == g.ny ? 0 : j + 1;
         auto pe = [&](const real *P, int ii, int jj, int kk) -> real {  // E' on the integer-z planes
             if (per) kk = wrapi(kk, g.nz);
@@ -930,25 +951,48 @@ __global__ void adj_profile_kernel(int64_t n, const double *lw, const void *w, i
 // near[k] = 1 for every cell plane k within S + 2 planes of a z plane on which
 // one of nc components (consecutive arrays of g.ncomp values) is not zero: a
 // particle in cell k reads and deposits only within that reach, so a particle
-// with near[k] = 0 sees zero there.  One CTA reduces one plane at a time.
+// with near[k] = 0 sees zero there.
+__device__ __forceinline__ void mark_near(const Geom &g, int k, unsigned char *near)
+{
+    const int R = g.shape + 2;
+    for (int d = -R; d <= R; ++d) {
+        int kk = k + d;
+        if (g.bc_z == 0) kk = wrap1(kk, g.nz);
+        else if (kk < 0 || kk > g.nz) continue;
+        near[kk] = 1;
+    }
+}
+
+// wide planes: one CTA reduces one plane at a time
 template <typename real>
 __global__ void adj_planes_kernel(Geom g, const real *F, int nc, unsigned char *near)
 {
-    const int R = g.shape + 2, nk = g.bc_z == 0 ? g.nz : g.nz + 1;
+    const int nk = g.bc_z == 0 ? g.nz : g.nz + 1;
     for (int k = (int)blockIdx.x; k < nk; k += (int)gridDim.x) {
         int any = 0;
         for (int c = 0; c < nc; ++c) {
             const real *P = F + (int64_t)c * g.ncomp + (int64_t)k * g.plane;
             for (int64_t o = threadIdx.x; o < g.plane; o += blockDim.x) any |= P[o] != real(0);
         }
-        if (__syncthreads_or(any) && threadIdx.x == 0) {
-            for (int d = -R; d <= R; ++d) {
-                int kk = k + d;
-                if (g.bc_z == 0) kk = wrap1(kk, g.nz);
-                else if (kk < 0 || kk > g.nz) continue;
-                near[kk] = 1;
-            }
+        if (__syncthreads_or(any) && threadIdx.x == 0) mark_near(g, k, near);
+    }
+}
+
+// narrow planes (2D, small 3D sections): one warp per plane, every load of
+// the plane issued before the vote
+template <typename real>
+__global__ void adj_planes_warp_kernel(Geom g, const real *F, int nc, unsigned char *near)
+{
+    const int nk = g.bc_z == 0 ? g.nz : g.nz + 1;
+    const int lane = (int)(threadIdx.x & 31u), wpb = (int)(blockDim.x >> 5);
+    // k is the same on all lanes of a warp, so every vote has all 32
+    for (int k = (int)blockIdx.x * wpb + (int)(threadIdx.x >> 5); k < nk; k += (int)gridDim.x * wpb) {
+        int any = 0;
+        for (int c = 0; c < nc; ++c) {
+            const real *P = F + (int64_t)c * g.ncomp + (int64_t)k * g.plane;
+            for (int64_t o = lane; o < g.plane; o += 32) any |= P[o] != real(0);
         }
+        if (__any_sync(0xffffffffu, any) && lane == 0) mark_near(g, k, near);
     }
 }
 
@@ -957,7 +1001,13 @@ void launch_adj_planes(const Geom &g, const real *F, int nc, unsigned char *near
 {
     cudaMemsetAsync(near, 0, (size_t)g.nz + 1, s);
     const int nk = g.nz + 1;
-    adj_planes_kernel<real><<<(unsigned)(nk < 152 * 16 ? nk : 152 * 16), 128, 0, s>>>(g, F, nc, near);
+    if (g.plane <= 4096) {
+        const int blocks = (nk + 7) / 8;
+        adj_planes_warp_kernel<real><<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, s>>>(g, F, nc,
+                                                                                                      near);
+    } else {
+        adj_planes_kernel<real><<<(unsigned)(nk < 152 * 16 ? nk : 152 * 16), 128, 0, s>>>(g, F, nc, near);
+    }
 }
 
 // --------------------------------------------------------------- launchers

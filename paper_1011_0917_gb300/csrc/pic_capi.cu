@@ -2162,13 +2162,14 @@ static pic_status adj_backward_t(pic_ctx *c, const void *cot, double *grad)
     auto st = [&](int s) { return seg + (size_t)s * (L.st + L.fl); };
     auto fl = [&](int s) { return seg + (size_t)s * (L.st + L.fl) + L.st; };
     auto ck_st = [&](int q) { return B + L.ckpt + (size_t)q * (L.st + L.fl); };
-    real *lE[3], *lB[3], *lE0[3], *pE[3], *lJ[3];
+    real *lE[3], *lB[3], *lE0[3], *pE[3], *lJ[3], *lJr[3];
     for (int q = 0; q < 3; ++q) {
         lE[q] = (real *)(B + L.lE) + q * nc;
         lB[q] = (real *)(B + L.lB) + q * nc;
         lE0[q] = (real *)(B + L.lE0) + q * nc;
         pE[q] = (real *)(B + L.pE) + q * nc;
         lJ[q] = (real *)(B + L.lJ) + q * nc;
+        lJr[q] = (real *)(B + L.tmp) + q * nc;
     }
     const size_t cb = 3 * sizeof(real) * nc;
     CUDA_TRY(c, cudaMemcpyAsync(lE[0], cot, cb, cudaMemcpyDeviceToDevice, c->stream));
@@ -2190,9 +2191,14 @@ static pic_status adj_backward_t(pic_ctx *c, const void *cot, double *grad)
         }
         for (int s = n1 - n0 - 1; s >= 0; --s) {
             const int n = n0 + s;
-            launch_adj_yee<real>(c->g, lE, lB, lE0, pE, lJ, c->dt, c->hx, c->hy, c->hz, c->stream);
+            // the current cotangent before the filter goes to the scratch
+            // buffer, the filter (its own transpose) writes lJ
+            launch_adj_yee<real>(c->g, lE, lB, lE0, pE, lJr, c->dt, c->hx, c->hy, c->hz, c->stream);
             for (int q = 0; q < 3; ++q) std::swap(lE[q], lE0[q]);
-            launch_filter<real>(c->g, lJ, (real *)(B + L.tmp), c->p.filter_passes, c->stream);
+            if (c->p.filter_passes == 0 || !launch_filter_from<real>(c->g, lJr[0], lJ, c->p.filter_passes, c->stream)) {
+                CUDA_TRY(c, cudaMemcpyAsync(lJ[0], lJr[0], 3 * sizeof(real) * nc, cudaMemcpyDeviceToDevice, c->stream));
+                launch_filter<real>(c->g, lJ, lJr[0], c->p.filter_passes, c->stream);
+            }
             launch_adj_planes<real>(c->g, lJ[0], 3, B + L.planes, c->stream);
             if (c->laser_on && c->ka >= 2) {
                 const double j0 = antenna_j0(c, A.tn[n], l.a0);
