@@ -158,6 +158,22 @@ def traffic_from_profiles(kernel_key: str):
 # --------------------------------------------------------------------- ours
 
 
+def whole_job(elapsed: float, work: float, world: int, device: str) -> tuple[float, float]:
+    """Whole-job aggregation of N independent replicas: the slowest rank's
+    elapsed time (any unit) and the work of all ranks summed (two scalar
+    all-reduces outside the timed region; the replicas exchange nothing else).
+    device: "cuda" under NCCL, "cpu" under gloo."""
+    if world <= 1:
+        return elapsed, work
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([elapsed], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor([work], device=device, dtype=torch.float64)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(w.item())
+
+
 def run_ours(args, rank, world, local):
     import torch
     import paper_1011_0917_gb300 as P
@@ -210,14 +226,7 @@ def run_ours(args, rank, world, local):
     psteps = n_e * args.steps
 
     # whole-job aggregation: max time, summed work
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        w_ = torch.tensor([psteps], device="cuda", dtype=torch.float64)
-        dist.all_reduce(w_, op=dist.ReduceOp.SUM)
-        psteps = float(w_.item())
+    ms, psteps = whole_job(ms, psteps, world, "cuda")
     value = psteps / (ms * 1e-3)
 
     # roofline of the dominant kernel (the fused electron gather/push/deposit)
@@ -246,13 +255,8 @@ def run_ours(args, rank, world, local):
             P.pic_get_axis(ctx, 2, line.data_ptr(), line.numel() * 4, False)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        el = t1 - t0
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": (n_e * args.steps * world) / el, "unit": UNIT,
+        el, e2e_work = whole_job(t1 - t0, n_e * args.steps, world, "cuda")
+        e2e = {"value": e2e_work / el, "unit": UNIT,
                "h2d_bytes_per_step": int(nbytes // args.steps), "d2h_bytes_per_step": int(line.numel() * 4),
                "note": "initial state restored from pinned host memory once per job of --steps steps; "
                        "on-axis Ez line read back after every step"}
@@ -310,10 +314,10 @@ def run_ours(args, rank, world, local):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        xms = e0.elapsed_time(e1)
         xph, xcalls, _ = P.pic_profile_read(sim.ctx)
         dx_ = sim.diagnostics()
-        explicit = {"steps": k, "ms_per_step": xms / k, "value": dx_.n_particles[0] * k * world / (xms * 1e-3),
+        xms, xwork = whole_job(e0.elapsed_time(e1), dx_.n_particles[0] * k, world, "cuda")
+        explicit = {"steps": k, "ms_per_step": xms / k, "value": xwork / (xms * 1e-3),
                     "n_ion_records": dx_.n_particles[1], "push_ms_per_launch": xph[1] / max(xcalls[1], 1),
                     "ions_ms_per_launch": xph[2] / max(xcalls[2], 1)}
         sim.close()
