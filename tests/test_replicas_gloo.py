@@ -32,7 +32,7 @@ def _rank(rank, world, port, out):
 @pytest.mark.parametrize("world", [2, 3])
 def test_whole_job_max_time_summed_work(world):
     import torch.multiprocessing as mp
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.start_processes(_rank, args=(world, _free_port(), out), nprocs=world, start_method="spawn", join=True)
     want_t = 10.0 + (world - 1)
