@@ -277,13 +277,22 @@ pic_status pic_batch_step(pic_batch *batch, int nsteps);
 void pic_batch_destroy(pic_batch *batch);
 
 /* Steps of a batch run as CUDA graphs of steps_per_graph steps of every
-   context (even; default 20; 0: streams only): pic_batch_step captures the
-   steps once per call and replays the graph nsteps / steps_per_graph times
-   (the remainder, and batches with a moving window, lab snapshots, phase
-   timing or a context on the legacy default stream, take the stream path).
-   The per-step values (antenna amplitude, injection band and times) are
-   refilled in pinned host memory before each replay and copied by the
-   graph's first nodes.  PIC_ERR_ARG for a negative or odd count. */
+   context (even; default 20; 0: streams only): pic_batch_step replays the
+   graph nsteps / steps_per_graph times (the remainder, and batches with a
+   moving window, lab snapshots, phase timing or a context on the legacy
+   default stream, take the stream path).  The graph is captured by the
+   first call that needs it and kept by the batch while every context stays
+   as the capture left it: a call that changes what a context's step launches
+   (binding, plasma or particle load, laser, window, snapshots, state restore,
+   phase timing, an adjoint run) or an odd number of steps taken outside the
+   graph (the double buffers then start on their other halves) makes the
+   next call capture again.  The per-step values (antenna amplitude,
+   injection band and times) of all replays of a call are written to pinned
+   host memory first, one region per replay, each copied to the device on
+   the graph's stream just before its replay, so replays follow each other
+   without waiting for the host; the graph's stream is ordered after the work
+   already queued on the contexts' streams and before the work queued on them
+   later.  PIC_ERR_ARG for a negative or odd count. */
 pic_status pic_batch_set_graph(pic_batch *batch, int steps_per_graph);
 
 /* ---------------------------------------------------------- moving window */
