@@ -88,8 +88,11 @@ def tune_batch(settings_list, steps: int = 40, warmup: int = 3, graph_steps=(0, 
         batch.step(warmup)
         for k in graph_steps:
             # the runs' work spans their own streams: time on the host between
-            # two device-wide synchronisations
+            # two device-wide synchronisations; a graph is captured by an
+            # untimed first call of k steps and kept by the batch
             P.pic_batch_set_graph(batch.h, k)
+            if k > 0:
+                batch.step(k)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             batch.step(steps)
