@@ -166,3 +166,34 @@ def test_moving_window_validation(P):
             P.pic_set_moving_window(ctx, 0.9, 0.0, 16)   # periodic z has no window
     finally:
         P.pic_destroy(ctx)
+
+
+def test_batch_validation(P):
+    # a batch needs bound contexts, at least one, none twice; graphs of an
+    # even number of steps
+    ctx = P.pic_init_grid(grid(P))
+    try:
+        with pytest.raises(P.PicError) as e:
+            P.pic_batch_create([ctx])
+        assert e.value.status == 2  # PIC_ERR_STATE: not bound
+        with pytest.raises(P.PicError) as e:
+            P.pic_batch_create([])
+        assert e.value.status == 1
+    finally:
+        P.pic_destroy(ctx)
+    for k in (-2, 3):
+        with pytest.raises(P.PicError) as e:
+            P.pic_batch_set_graph(None, k)
+        assert e.value.status == 1
+
+
+def test_adjoint_validation(P):
+    # the adjoint needs bound buffers, then a loaded plasma and no step taken
+    ctx = P.pic_init_grid(grid(P, gamma_boost=5.0, dx=1.0, dz=1 / 32, nx=48, nz=256))
+    try:
+        with pytest.raises(P.PicError) as e:
+            P.pic_adjoint_bytes(ctx, P.AdjointParams(40, 20))
+        assert e.value.status == 2
+        assert "bind" in P.pic_last_error(ctx)
+    finally:
+        P.pic_destroy(ctx)
