@@ -197,3 +197,12 @@ def test_adjoint_validation(P):
         assert "bind" in P.pic_last_error(ctx)
     finally:
         P.pic_destroy(ctx)
+
+
+def test_simulation_refuses_without_a_gpu(P):
+    # the product path has no CPU fallback: without a CUDA device it raises
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(RuntimeError, match="no CPU path"):
+        P.Simulation(dim=2, nx=16, ny=1, nz=64, dx=0.5, dz=1 / 16)
