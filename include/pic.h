@@ -297,9 +297,9 @@ pic_status pic_batch_set_graph(pic_batch *batch, int steps_per_graph);
 
 /* ---------------------------------------------------------- moving window */
 
-/* Moving window (the paper's gamma = 1 and gamma = 5 runs used "a moving
-   window propagating at the group velocity v_g of the laser in the plasma",
-   section "Effect of the hyperbolic rotation in Minkowski space").  From
+/* Moving window (in the paper's gamma = 1 and gamma = 5 runs the box
+   follows the laser, moving at its group velocity v_g in the plasma; section
+   "Effect of the hyperbolic rotation in Minkowski space").  From
    simulation time t0 on the grid moves along +z at velocity v (0 < v <= 1, in
    c): after the TIME phase of a step at which v (t - t0) >= (n + 1) S hz (n
    the moves so far), it moves by shift_cells = S cells at once: every field

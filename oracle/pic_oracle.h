@@ -79,9 +79,9 @@ typedef struct opic_laser {
     double xc, yc;           /* transverse centre; NaN: box centre           */
 } opic_laser;
 
-/* Lab-frame snapshots of a boosted-frame run (the paper's boosted data
-   "plotted in laboratory coordinates after Lorentz transformation", section
-   "Effect of the hyperbolic rotation in Minkowski space", Fig. 2).  Snapshot j
+/* Lab-frame snapshots of a boosted-frame run (the paper shows its boosted
+   results transformed back to laboratory coordinates; section "Effect of the
+   hyperbolic rotation in Minkowski space", Fig. 2).  Snapshot j
    holds the lab-frame fields at lab time T_j = t0 + j dt on the lab points
    Z_k = z0 + k dz, k < nz; each is filled during the boosted step whose time
    interval [t'^n, t'^{n+1}) contains the event's boosted time.  Parity
@@ -126,9 +126,9 @@ double *opic_rho_background(opic *s);
 void opic_step(opic *s, int nsteps);
 void opic_step_phases(opic *s, unsigned mask);
 
-/* Moving window (the paper's gamma = 1 and 5 runs: "a moving window
-   propagating at the group velocity v_g", section "Effect of the hyperbolic
-   rotation in Minkowski space").  From time t0 on, the window (the grid) moves
+/* Moving window (in the paper's gamma = 1 and 5 runs the box moves with the
+   laser at its group velocity v_g; section "Effect of the hyperbolic rotation
+   in Minkowski space").  From time t0 on, the window (the grid) moves
    along +z at velocity v (0 < v <= 1); whenever its displacement
    v (t - t0) reaches (n + 1) S hz after the TIME phase, the window moves by S
    cells at once (n counts the moves): every field plane k takes plane k + S,

@@ -1,5 +1,5 @@
-"""Oracle pins of the moving window (the paper's gamma = 1 and 5 runs used "a
-moving window propagating at the group velocity"; section "Effect of the
+"""Oracle pins of the moving window (in the paper's gamma = 1 and 5 runs the
+box moves with the laser at its group velocity; section "Effect of the
 hyperbolic rotation in Minkowski space").
 
 What fixes them: a window moving at c over a pulse that travels at c sees the
