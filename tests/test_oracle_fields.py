@@ -212,3 +212,30 @@ def test_filter_is_its_own_transpose(oracle_mod, dim, bc, npass):
         lhs = float(np.sum(fx[c][m] * y[c][m]))
         rhs = float(np.sum(x[c][m] * fy[c][m]))
         assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + abs(rhs) + 1.0), (c, lhs, rhs)
+
+
+@pytest.mark.parametrize("pol", [0, 1])
+def test_antenna_beam_has_the_waist(oracle_mod, pol):
+    # A Gaussian beam launched by the antenna with field 1/e radius w0 = 4
+    # lambda0 keeps that transverse profile a wavelength ahead of it (the
+    # Rayleigh length pi w0^2 is 50 lambda0): the peak |E| over time at each
+    # transverse node of the probe plane follows exp(-(x - xc)^2 / w0^2), with
+    # x the node's own staggered position (Ex on half-integer x).
+    G, L = oracle_mod.GridParams, oracle_mod.LaserParams
+    w0 = 4.0
+    g = G(dim=2, nx=64, nz=256, dx=0.5, dz=1.0 / 16, cfl=0.99, bc_z=1, npass=0)
+    o = oracle_mod.Oracle(g)
+    o.set_laser(L(a0=1.0, waist=w0, fwhm=2.0, z_antenna=1.0, pol=pol))
+    comp = "Ex" if pol == 0 else "Ey"
+    kp = int(round(2.0 / o.hz))  # one wavelength ahead of the antenna
+    peak = np.zeros(g.nx)
+    while o.t < 14.0:
+        o.step(1)
+        peak = np.maximum(peak, np.abs(o.field(comp)[kp, 0, :]))
+    x = (np.arange(g.nx) + (0.5 if pol == 0 else 0.0)) * o.hx
+    xc = 0.5 * g.nx * o.hx
+    expect = np.exp(-((x - xc) / w0) ** 2)
+    near = np.abs(x - xc) < 2.0 * w0
+    ratio = peak / peak[np.argmin(np.abs(x - xc))]
+    assert peak.max() > 0.5
+    assert np.abs(ratio[near] - expect[near]).max() < 0.02, np.abs(ratio[near] - expect[near]).max()
