@@ -514,14 +514,21 @@ class Simulation:
 
 
 class StageGradient:
-    """torch.autograd.Function over one boosted stage: inputs the profile
-    coefficients (M,), a0 and w0 (0-d tensors); output E^N, B^N (6, nz+1, nx).
-    The forward builds the run from the fixed settings given to apply(); the
-    backward runs the library's adjoint."""
+    """torch.autograd.Function over one stage run: inputs the profile
+    coefficients (M,) and the laser's a0 and w0 (0-d tensors, or None for w0
+    to keep the waist of ``settings``); output E^N, B^N (6, nz+1, nx) in 2D,
+    (6, nz+1, ny, nx) in 3D, on the device.  The forward builds the run from
+    the fixed settings given to apply() and runs the library's adjoint forward
+    (checkpoints kept in a device buffer); the backward runs the reverse sweep
+    and returns each gradient on the device and in the dtype of its input, then
+    releases the run."""
 
     @staticmethod
     def _function():
         import torch
+
+        def _like(v, x):
+            return torch.as_tensor(v, dtype=x.dtype, device=x.device) if isinstance(x, torch.Tensor) else None
 
         class _F(torch.autograd.Function):
             @staticmethod
@@ -536,14 +543,21 @@ class StageGradient:
                 out = sim.adjoint_forward(settings["nsteps"], settings.get("checkpoint_every", 50))
                 ctx.sim = sim
                 ctx.m = coef.numel()
+                ctx.inputs = (coef, a0, w0)
                 return out.clone()
 
             @staticmethod
             def backward(ctx, grad_out):
-                g = ctx.sim.adjoint_backward(grad_out)
+                sim = ctx.sim
+                try:
+                    g = sim.adjoint_backward(grad_out)
+                finally:
+                    sim.close()
+                    ctx.sim = None
                 m = ctx.m
-                dc = torch.tensor(g[:m], dtype=torch.float64)
-                return dc, torch.tensor(g[m], dtype=torch.float64), torch.tensor(g[m + 1], dtype=torch.float64), None
+                coef, a0, w0 = ctx.inputs
+                dc = torch.as_tensor(g[:m], dtype=coef.dtype, device=coef.device).reshape(coef.shape)
+                return dc, _like(g[m], a0), _like(g[m + 1], w0), None
 
         return _F
 

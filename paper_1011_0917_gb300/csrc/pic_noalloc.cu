@@ -22,9 +22,11 @@ static __device__ __align__(256) double g_filter_scratch[PIC_NOALLOC_MAX_NODES];
 constexpr int kMaxDevices = 128;
 std::mutex g_lock;
 void *g_scratch[kMaxDevices] = {nullptr};
+int g_sms[kMaxDevices] = {0};
 
-// device address of the scratch array on the current device (looked up once)
-cudaError_t scratch_address(void **out)
+// device address of the scratch array on the current device and that
+// device's multiprocessor count (both looked up once per device)
+cudaError_t scratch_address(void **out, int *sms)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -35,9 +37,14 @@ cudaError_t scratch_address(void **out)
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_filter_scratch);
         if (e != cudaSuccess) return e;
+        int n = 0;
+        e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        g_sms[dev] = n > 0 ? n : 1;
         g_scratch[dev] = p;
     }
     *out = g_scratch[dev];
+    *sms = g_sms[dev];
     return cudaSuccess;
 }
 
@@ -75,10 +82,11 @@ __global__ void filter_one_kernel(pic::Geom g, const real *in, real *out, int ax
 }
 
 template <typename real>
-cudaError_t filter_all(const pic::Geom &g, int passes, real *const J[3], real *tmp, cudaStream_t s)
+cudaError_t filter_all(const pic::Geom &g, int passes, real *const J[3], real *tmp, int sms, cudaStream_t s)
 {
+    // a grid-stride loop: at most 8 resident CTAs of 256 threads per SM
     int64_t blocks = (g.ncomp + 255) / 256;
-    if (blocks > 152LL * 32) blocks = 152LL * 32;
+    if (blocks > 8LL * sms) blocks = 8LL * sms;
     for (int c = 0; c < 3; ++c) {
         real *src = J[c], *dst = tmp;
         int done = 0;
@@ -112,7 +120,8 @@ extern "C" pic_status pic_filter_current_noalloc(int dim, int nx, int ny, int nz
     if (nodes > (int64_t)PIC_NOALLOC_MAX_NODES) return PIC_ERR_ARG;
     if (passes == 0) return PIC_OK;
     void *scratch = nullptr;
-    if (scratch_address(&scratch) != cudaSuccess) return PIC_ERR_CUDA;
+    int sms = 1;
+    if (scratch_address(&scratch, &sms) != cudaSuccess) return PIC_ERR_CUDA;
     pic::Geom g{};
     g.dim = dim;
     g.nx = nx;
@@ -125,10 +134,10 @@ extern "C" pic_status pic_filter_current_noalloc(int dim, int nx, int ny, int nz
     cudaError_t e;
     if (precision == PIC_FP32) {
         float *J[3] = {(float *)jx, (float *)jy, (float *)jz};
-        e = filter_all<float>(g, passes, J, (float *)scratch, s);
+        e = filter_all<float>(g, passes, J, (float *)scratch, sms, s);
     } else {
         double *J[3] = {(double *)jx, (double *)jy, (double *)jz};
-        e = filter_all<double>(g, passes, J, (double *)scratch, s);
+        e = filter_all<double>(g, passes, J, (double *)scratch, sms, s);
     }
     return e == cudaSuccess ? PIC_OK : PIC_ERR_CUDA;
 }

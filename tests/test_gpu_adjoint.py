@@ -232,3 +232,55 @@ def test_fp32_gradient_against_fp64(O):
     g64, g32 = np.array(g64), np.array(g32)
     rel = np.abs(g32 - g64) / np.abs(g64)
     assert np.all(rel < 1e-3), (g32, g64, rel)
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_stage_gradient_autograd_matches_oracle_finite_differences(O, reference, prec):
+    """The torch.autograd.Function face of the adjoint: coefficients, a0 and
+    w0 as CUDA tensors with requires_grad, the objective built in torch from
+    the returned fields, .backward(); each .grad lands on its input's device
+    and dtype and matches the oracle's central differences (1e-3)."""
+    import torch
+
+    import paper_1011_0917_gb300 as P
+    _, _, fd = reference
+    dev = torch.device("cuda")
+    coef = torch.tensor(COEF, dtype=torch.float64, device=dev, requires_grad=True)
+    a0 = torch.tensor(LASER["a0"], dtype=torch.float64, device=dev, requires_grad=True)
+    w0 = torch.tensor(LASER["waist"], dtype=torch.float64, device=dev, requires_grad=True)
+    settings = dict(grid=dict(dim=2, nx=G["nx"], nz=G["nz"], dx=G["dx"], dz=G["dz"], gamma_boost=GAM,
+                              filter_passes=G["filter_passes"], seed=G["seed"], precision=prec, slots_per_cell=16.0),
+                    plasma=dict(ne=PLASMA["ne"], z_start=PLASMA["z_start"], z_end=PLASMA["z_end"],
+                                ramp=PLASMA["ramp"], ppc=PLASMA["ppc"], jitter=PLASMA["jitter"], ions=1),
+                    laser=dict(waist=LASER["waist"], fwhm=LASER["fwhm"], t_peak=LASER["t_peak"], pol=1),
+                    nsteps=NSTEPS, checkpoint_every=20)
+    out = P.StageGradient.apply(coef, a0, w0, settings)
+    assert out.is_cuda and out.shape == (6, G["nz"] + 1, G["nx"])
+    lam = torch.as_tensor(cotangent(G["nz"], G["nx"]), dtype=out.dtype, device=dev)
+    (lam * out).sum().backward()
+    for t in (coef, a0, w0):
+        assert t.grad is not None and t.grad.device == t.device and t.grad.dtype == t.dtype
+    g = np.concatenate([coef.grad.cpu().numpy(), [a0.grad.item(), w0.grad.item()]])
+    rel = np.abs(g - fd) / np.abs(fd)
+    assert np.all(rel < 1e-3), (g, fd, rel)
+
+
+def test_stage_gradient_without_waist_input(O, reference):
+    """w0 = None keeps the waist of the settings: its gradient slot is None."""
+    import torch
+
+    import paper_1011_0917_gb300 as P
+    _, _, fd = reference
+    coef = torch.tensor(COEF, dtype=torch.float64, device="cuda", requires_grad=True)
+    a0 = torch.tensor(LASER["a0"], dtype=torch.float64, device="cuda", requires_grad=True)
+    settings = dict(grid=dict(dim=2, nx=G["nx"], nz=G["nz"], dx=G["dx"], dz=G["dz"], gamma_boost=GAM,
+                              filter_passes=G["filter_passes"], seed=G["seed"], precision=FP64, slots_per_cell=16.0),
+                    plasma=dict(ne=PLASMA["ne"], z_start=PLASMA["z_start"], z_end=PLASMA["z_end"],
+                                ramp=PLASMA["ramp"], ppc=PLASMA["ppc"], jitter=PLASMA["jitter"], ions=1),
+                    laser=dict(waist=LASER["waist"], fwhm=LASER["fwhm"], t_peak=LASER["t_peak"], pol=1),
+                    nsteps=NSTEPS, checkpoint_every=NSTEPS)
+    out = P.StageGradient.apply(coef, a0, None, settings)
+    lam = torch.as_tensor(cotangent(G["nz"], G["nx"]), dtype=out.dtype, device="cuda")
+    (lam * out).sum().backward()
+    g = np.concatenate([coef.grad.cpu().numpy(), [a0.grad.item()]])
+    assert np.all(np.abs(g - fd[:-1]) / np.abs(fd[:-1]) < 1e-3)
