@@ -106,8 +106,27 @@ typedef struct pic_grid_params {
     int track_ids;          /* 1: carry an int64 lattice id with each particle */
     int explicit_ions;      /* 1: store every drifting ion as its own record    */
                             /* (0: electron-ion pairs, see pic_load_plasma)     */
+    int z_relative;         /* electron position storage: 0 automatic (relative */
+                            /* when gamma_boost >= 50), 1 relative, 2 absolute; */
+                            /* see the note below                               */
     void *stream;           /* cudaStream_t for all device work (NULL: legacy)  */
 } pic_grid_params;
+
+/* Relative positions.  In a frame boosted to gamma the plasma (electrons and
+   ions, gamma n each) streams through a good part of a cell every step, and
+   the wake is the small difference between the two species' currents: about
+   1 / (2 gamma^2) of the plasma's response in the lab, i.e. ~3e-8 of either
+   species' current at gamma = 130.  Positions rounded to FP32 (6e-8 cell)
+   and currents formed in FP32 then leave only rounding noise of the wake.
+   With z_relative an electron record holds, per axis, a reference offset --
+   along z it moves with exactly the arithmetic of a drifting ion, across z
+   it stays where the particle was placed, so it is the path of the
+   electron's own ion -- plus the departure from it in its own FP32 word
+   (relative precision); the currents of electrons and ions are formed in
+   FP64 from these exact positions and accumulated in the same fixed-point
+   words.  It costs 8 bytes (2D) or 12 bytes (3D) more per electron record in
+   FP32 and FP64 deposit arithmetic; the gather, the push and the fields keep
+   the working precision.  The method computed is the same either way. */
 
 /* Sizes of the caller-owned device buffers and derived quantities. */
 typedef struct pic_sizes {

@@ -173,6 +173,8 @@ def _load():
         lib.opic_btd_setup.argtypes = [P, C.POINTER(_Btd)]
         lib.opic_btd_data.restype = D
         lib.opic_btd_data.argtypes = [P, C.c_int]
+        lib.opic_diagnostics.argtypes = [P, D]
+        lib.opic_fields_lab.argtypes = [P, D]
         lib.opic_btd_filled.restype = C.POINTER(C.c_ubyte)
         lib.opic_btd_filled.argtypes = [P, C.c_int]
         _lib = lib
@@ -316,6 +318,20 @@ class Oracle:
     def zero_fields(self):
         for c in COMPONENTS:
             self.field(c)[...] = 0.0
+
+    # --------------------------------------------------------- diagnostics
+    def diagnostics(self) -> dict:
+        """FP64 Kahan sums: field_energy, kinetic_energy (electrons), charge."""
+        out = np.zeros(3)
+        self.lib.opic_diagnostics(self.h, _dptr(out))
+        return {"field_energy": float(out[0]), "kinetic_energy": float(out[1]), "charge": float(out[2])}
+
+    def fields_lab(self) -> dict:
+        """Lab-frame E, B on the simulation grid at the current time:
+        {Ex..Bz: (nz+1, ny, nx)} (a copy)."""
+        out = np.zeros((6,) + self.shape3)
+        self.lib.opic_fields_lab(self.h, _dptr(out))
+        return {c: out[q] for q, c in enumerate(COMPONENTS[:6])}
 
     # ------------------------------------------------------- moving window
     def set_window(self, v: float, t0: float, shift_cells: int):

@@ -1088,6 +1088,116 @@ static void btd_fill(opic *s, double t0)
     }
 }
 
+/* ------------------------------------------------------------ diagnostics */
+
+/* Kahan-compensated running sum (Kahan 1965): the rounding error of every
+   addition is carried into the next one */
+typedef struct kahan {
+    double s, c;
+} kahan;
+
+static void kahan_add(kahan *k, double v)
+{
+    const double y = v - k->c;
+    const double t = k->s + y;
+    k->c = (t - k->s) - y;
+    k->s = t;
+}
+
+/* out[0] field energy (1/2) sum (E^2 + B^2) V over each component's valid
+   nodes (E, B in m c omega0 / e: with n_c = eps0 m omega0^2 / e^2 the energy
+   density eps0 E^2 / 2 is n_c m c^2 E^2 / 2, so this is in n_c m c^2 lambda0^3);
+   out[1] electron kinetic energy sum w (gamma - 1), gamma - 1 formed as
+   u^2 / (gamma + 1) (same units: w counts physical electrons per n_c lambda0^3);
+   out[2] charge sum q w over the particle species (electrons q = -1, drifting
+   ions q = +1; the lab frame's immobile ions are a background, not particles).
+   Components in order, nodes and particles in storage order. */
+void opic_diagnostics(const opic *s, double out[3])
+{
+    kahan fe = {0, 0};
+    for (int c = 0; c < 6; ++c) {
+        const int km = zmax_of(s, STAG[c][2]);
+        for (int64_t k = 0; k <= km; ++k)
+            for (int64_t j = 0; j < s->ny; ++j)
+                for (int64_t i = 0; i < s->g.nx; ++i) {
+                    const double v = s->f[c][fidx(s, i, j, k)];
+                    kahan_add(&fe, v * v);
+                }
+    }
+    const double vol = s->hx * s->hy * s->hz;
+    out[0] = 0.5 * vol * fe.s;
+    kahan ke = {0, 0}, q = {0, 0};
+    const species *e = &s->sp[0];
+    for (int64_t p = 0; p < e->n; ++p) {
+        const double ux = e->a[OPIC_PUX][p], uy = e->a[OPIC_PUY][p], uz = e->a[OPIC_PUZ][p];
+        const double u2 = ux * ux + uy * uy + uz * uz;
+        kahan_add(&ke, e->a[OPIC_PW][p] * (u2 / (sqrt(1.0 + u2) + 1.0)));
+        kahan_add(&q, -e->a[OPIC_PW][p]);
+    }
+    const species *ion = &s->sp[1];
+    for (int64_t p = 0; p < ion->n; ++p)
+        kahan_add(&q, ion->a[OPIC_PW][p]);
+    out[1] = ke.s;
+    out[2] = q.s;
+}
+
+/* Lab-frame E and B on the simulation grid at the current simulation time
+   (the inverse of the boost along z, the hyperbolic rotation of section
+   "Effect of the hyperbolic rotation in Minkowski space"):
+     Ex = gamma (Ex' + beta By'), Ey = gamma (Ey' - beta Bx'), Ez = Ez',
+     Bx = gamma (Bx' - beta Ey'), By = gamma (By' + beta Ex'), Bz = Bz'.
+   Every component stays at its own Yee position; the partner it mixes with
+   sits half a cell away in z and is taken there as the mean of its two
+   neighbouring planes (the nearer plane alone at an absorbing z end; planes
+   wrap when z is periodic).  out: 6 arrays of nn values, Ex Ey Ez Bx By Bz. */
+static double zmean(const opic *s, const double *f, int c, int64_t i, int64_t j, int64_t k, int up)
+{
+    /* the partner c at the component's height: planes k-1, k (up = 0) or
+       k, k+1 (up = 1) of the partner's own index */
+    const int km = zmax_of(s, STAG[c][2]);
+    int64_t a = up ? k : k - 1, b = up ? k + 1 : k;
+    if (s->g.bc_z == 0) {
+        a = wrap_index(a, s->g.nz);
+        b = wrap_index(b, s->g.nz);
+    } else {
+        if (a < 0)
+            a = b;
+        if (b > km)
+            b = a;
+        if (a > km)
+            a = b = km;
+    }
+    return 0.5 * (f[fidx(s, i, j, a)] + f[fidx(s, i, j, b)]);
+}
+
+void opic_fields_lab(const opic *s, double *out)
+{
+    const double gam = s->gam, beta = s->beta;
+    for (int c = 0; c < 6; ++c) {
+        double *d = out + (size_t)c * s->nn;
+        const int km = zmax_of(s, STAG[c][2]);
+        for (int64_t k = 0; k <= s->g.nz; ++k)
+            for (int64_t j = 0; j < s->ny; ++j)
+                for (int64_t i = 0; i < s->g.nx; ++i) {
+                    const int64_t o = fidx(s, i, j, k);
+                    double v = 0.0;
+                    if (k <= km) {
+                        /* integer-z E components meet half-integer-z B partners
+                           (planes k-1, k) and the other way round (k, k+1) */
+                        switch (c) {
+                        case OPIC_EX: v = gam * (s->f[OPIC_EX][o] + beta * zmean(s, s->f[OPIC_BY], OPIC_BY, i, j, k, 0)); break;
+                        case OPIC_EY: v = gam * (s->f[OPIC_EY][o] - beta * zmean(s, s->f[OPIC_BX], OPIC_BX, i, j, k, 0)); break;
+                        case OPIC_EZ: v = s->f[OPIC_EZ][o]; break;
+                        case OPIC_BX: v = gam * (s->f[OPIC_BX][o] - beta * zmean(s, s->f[OPIC_EY], OPIC_EY, i, j, k, 1)); break;
+                        case OPIC_BY: v = gam * (s->f[OPIC_BY][o] + beta * zmean(s, s->f[OPIC_EX], OPIC_EX, i, j, k, 1)); break;
+                        default: v = s->f[OPIC_BZ][o]; break;
+                        }
+                    }
+                    d[o] = v;
+                }
+    }
+}
+
 /* ------------------------------------------------------------------- step */
 
 void opic_step_phases(opic *s, unsigned mask)

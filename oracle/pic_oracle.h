@@ -148,6 +148,23 @@ int opic_btd_setup(opic *s, const opic_btd *b);
 double *opic_btd_data(opic *s, int j);
 unsigned char *opic_btd_filled(opic *s, int j);
 
+/* Diagnostics of the state, FP64 Kahan-compensated sums: out[0] the field
+   energy (1/2) sum (E^2 + B^2) V, out[1] the electrons' kinetic energy
+   sum w (gamma - 1), out[2] the particles' charge sum q w (electrons -1,
+   drifting ions +1), all in n_c m c^2 lambda0^3 (charge in e n_c lambda0^3).
+   Parity status: pinned (energy of uniform and single-mode fields from
+   discrete orthogonality, kinetic energy and charge of a cold boosted plasma
+   from the Lorentz factor and the loaded density, and the conservation of
+   field plus kinetic energy through a plasma oscillation). */
+void opic_diagnostics(const opic *s, double out[3]);
+
+/* Lab-frame E, B on the simulation grid at the current time (inverse field
+   transformation of the boost; each component at its own Yee position, the
+   partner it mixes with averaged over its two planes around it):
+   out = 6 arrays of (nz+1)*ny*nx doubles, Ex Ey Ez Bx By Bz.  Parity status:
+   pinned (uniformly moving charges' fields and the invariants E.B, E^2-B^2). */
+void opic_fields_lab(const opic *s, double *out);
+
 /* building blocks exposed for the oracle's own pins */
 void opic_gather(const opic *s, int64_t n, const double *x, const double *y,
                  const double *z, double *eb /* n x 6 */);

@@ -53,7 +53,7 @@ class GridParams(C.Structure):
                 ("gamma_boost", C.c_double), ("shape_order", C.c_int), ("filter_passes", C.c_int),
                 ("bc_z", C.c_int), ("precision", C.c_int), ("seed", C.c_uint64),
                 ("slots_per_cell", C.c_double), ("tile", C.c_int * 3), ("track_ids", C.c_int),
-                ("explicit_ions", C.c_int), ("stream", C.c_void_p)]
+                ("explicit_ions", C.c_int), ("z_relative", C.c_int), ("stream", C.c_void_p)]
 
 
 class Sizes(C.Structure):
@@ -377,7 +377,7 @@ class Simulation:
     def __init__(self, *, dim=2, nx=64, ny=1, nz=512, dx=0.5, dy=1.0, dz=1.0 / 16, cfl=0.99,
                  gamma_boost=1.0, shape_order=1, filter_passes=1, bc_z=PIC_BC_MUR, precision=PIC_FP32,
                  seed=10110917, slots_per_cell=8.0, tile=(0, 0, 0), track_ids=False, explicit_ions=False,
-                 device="cuda", stream=None):
+                 z_relative=0, device="cuda", stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the PIC library needs a CUDA device; there is no CPU path")
@@ -386,7 +386,7 @@ class Simulation:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.params = GridParams(dim, nx, ny, nz, dx, dy, dz, cfl, gamma_boost, shape_order, filter_passes, bc_z,
                                  precision, seed, slots_per_cell, (C.c_int * 3)(*tile), int(track_ids),
-                                 int(explicit_ions), C.c_void_p(self.stream.cuda_stream))
+                                 int(explicit_ions), int(z_relative), C.c_void_p(self.stream.cuda_stream))
         self.ctx = pic_init_grid(self.params)
         self.sizes = pic_query_sizes(self.ctx)
         s = self.sizes

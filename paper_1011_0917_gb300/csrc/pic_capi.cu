@@ -33,8 +33,8 @@ int ceil_log2(int64_t n)
     return b;
 }
 
-struct SideLayout {  // byte offsets of the attribute arrays within one side
-    size_t off[9];   // ox oy oz w ux uy uz cell id (SIZE_MAX: absent)
+struct SideLayout {       // byte offsets of the attribute arrays within one side
+    size_t off[kAttrs];   // ox oy oz w ux uy uz cell id dz (SIZE_MAX: absent)
     size_t bytes;
 };
 
@@ -50,7 +50,8 @@ struct StateHeader {
     double win_v, win_t0;
     int32_t win_on, win_S;
     int64_t win_n;
-    char pad[512 - 8 - 8 * 4 - 16 - 8 - 8 - sizeof(pic_laser_params) - 8 - 8 - 16 - 8 - 8];
+    int32_t rel, pad0;  // electron records in relative form (their departure columns follow)
+    char pad[512 - 8 - 8 * 4 - 16 - 8 - 8 - sizeof(pic_laser_params) - 8 - 8 - 16 - 8 - 8 - 8];
 };
 static_assert(sizeof(StateHeader) == 512, "state header must be 512 bytes");
 
@@ -63,6 +64,7 @@ struct pic_ctx {
     double gam = 1, beta = 0, hx = 1, hy = 1, hz = 1, dt = 0, Lx = 0, Ly = 0, Lz = 0, vol = 1;
     int es = 4;  // element bytes
     bool ions_species = false;
+    bool rel = false;  // electron records in relative form (rel_actual)
 
     size_t field_bytes = 0, species_bytes[2] = {0, 0}, scratch_bytes = 0;
     int64_t slots = 0;
@@ -196,13 +198,17 @@ static Species<real> species_view(pic_ctx *c, int sp, int sidx)
     s.uz = (real *)at(6);
     s.cell = (int32_t *)at(7);
     s.id = (int64_t *)at(8);
+    s.dlx = (real *)at(9);
+    s.dly = (real *)at(10);
+    s.dlz = (real *)at(11);
     return s;
 }
 
-static void side_raw(pic_ctx *c, int sp, int sidx, void *out[9])
+static void side_raw(pic_ctx *c, int sp, int sidx, void *out[kAttrs])
 {
     unsigned char *base = c->species[sp] + (size_t)sidx * c->side[sp].bytes;
-    for (int a = 0; a < 9; ++a) out[a] = c->side[sp].off[a] == SIZE_MAX ? nullptr : (void *)(base + c->side[sp].off[a]);
+    for (int a = 0; a < kAttrs; ++a)
+        out[a] = c->side[sp].off[a] == SIZE_MAX ? nullptr : (void *)(base + c->side[sp].off[a]);
 }
 
 static cudaMemcpyKind kind_out(int dst_is_device) { return dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
@@ -252,6 +258,7 @@ extern "C" pic_status pic_init_grid(const pic_grid_params *p, pic_ctx **out)
     if (p->bc_z != PIC_BC_MUR && p->bc_z != PIC_BC_PERIODIC) return PIC_ERR_ARG;
     if (p->precision != PIC_FP32 && p->precision != PIC_FP64) return PIC_ERR_ARG;
     if (!(p->slots_per_cell > 0) || p->slots_per_cell > 4096) return PIC_ERR_ARG;
+    if (p->z_relative < 0 || p->z_relative > 2) return PIC_ERR_ARG;
     for (int d = 0; d < 3; ++d)
         if (p->tile[d] < 0 || (p->tile[d] & (p->tile[d] - 1))) return PIC_ERR_ARG;
 
@@ -276,6 +283,7 @@ extern "C" pic_status pic_init_grid(const pic_grid_params *p, pic_ctx **out)
     c->Lz = p->nz * c->hz;
     c->vol = p->dim == 3 ? c->hx * c->hy * c->hz : c->hx * c->hz;
     c->ions_species = c->gam > 1.0;
+    c->rel = p->z_relative == 1 || (p->z_relative == 0 && c->gam >= 50.0);
 
     Geom &g = c->g;
     g.dim = p->dim;
@@ -336,11 +344,13 @@ extern "C" pic_status pic_init_grid(const pic_grid_params *p, pic_ctx **out)
     for (int sp = 0; sp < 2; ++sp) {
         SideLayout &L = c->side[sp];
         size_t o = 0;
-        for (int a = 0; a < 9; ++a) {
+        for (int a = 0; a < kAttrs; ++a) {
             bool present = true;
             if (a == 1 && p->dim != 3) present = false;
             if (sp == 1 && a >= 4 && a <= 6) present = false;
             if (a == 8 && !p->track_ids) present = false;
+            if (a >= 9 && (sp == 1 || !c->rel)) present = false;  // departures dlx dly dlz
+            if (a == 10 && p->dim != 3) present = false;
             if (!present) {
                 L.off[a] = SIZE_MAX;
                 continue;
@@ -456,7 +466,7 @@ static void fill_inject_common(pic_ctx *c, InjectArgs &a)
         side_raw(c, 1, c->cur[1], a.sp_i);
         a.hi_i = counts(c, 1, c->cur[1], 1);
     } else {
-        for (int q = 0; q < 9; ++q) a.sp_i[q] = nullptr;
+        for (int q = 0; q < kAttrs; ++q) a.sp_i[q] = nullptr;
         a.hi_i = nullptr;
     }
     a.err = reinterpret_cast<unsigned *>(c->scratch + c->off_err);
@@ -553,11 +563,11 @@ static pic_status bucket_staged(pic_ctx *c, int sp, int64_t n)
 
 // copy flat columns (host or device) into the staging side, then bucket them
 template <typename real>
-static pic_status upload_flat(pic_ctx *c, int sp, int64_t n, const void *const cols[9], int src_is_device)
+static pic_status upload_flat(pic_ctx *c, int sp, int64_t n, const void *const cols[kAttrs], int src_is_device)
 {
-    void *dst[9];
+    void *dst[kAttrs];
     side_raw(c, sp, c->cur[sp] ^ 1, dst);
-    for (int a = 0; a < 9; ++a) {
+    for (int a = 0; a < kAttrs; ++a) {
         if (!dst[a]) continue;
         const size_t bytes = (size_t)n * attr_size(c, a);
         if (bytes == 0) continue;
@@ -570,8 +580,9 @@ template <typename real>
 static pic_status load_particles_t(pic_ctx *c, int sp, int64_t n, const double *state, const int64_t *ids)
 {
     const bool dim3 = c->g.dim == 3;
-    std::vector<std::vector<unsigned char>> cols(9);
-    for (int a = 0; a < 9; ++a)
+    // (zero-filled: a loaded electron sits on its drift reference, dz = 0)
+    std::vector<std::vector<unsigned char>> cols(kAttrs);
+    for (int a = 0; a < kAttrs; ++a)
         if (c->side[sp].off[a] != SIZE_MAX) cols[a].resize((size_t)n * attr_size(c, a));
     auto R = [&](int a) { return reinterpret_cast<real *>(cols[a].data()); };
     double wmax = 0;
@@ -599,8 +610,8 @@ static pic_status load_particles_t(pic_ctx *c, int sp, int64_t n, const double *
         reinterpret_cast<int32_t *>(cols[7].data())[i] = pack_cell(c->g, ci, cj, ck);
         if (c->p.track_ids) reinterpret_cast<int64_t *>(cols[8].data())[i] = ids ? ids[i] : i;
     }
-    const void *ptrs[9];
-    for (int a = 0; a < 9; ++a) ptrs[a] = cols[a].empty() ? nullptr : cols[a].data();
+    const void *ptrs[kAttrs];
+    for (int a = 0; a < kAttrs; ++a) ptrs[a] = cols[a].empty() ? nullptr : cols[a].data();
     c->wmax = std::max(c->wmax, wmax);
     return upload_flat<real>(c, sp, n, ptrs, 0);
 }
@@ -702,6 +713,7 @@ static PushArgs<real> push_args(pic_ctx *c, int sp)
     a.jfac[2] = (real)(-q * c->hz / (c->dt * c->vol));
     a.jyfac = (real)(q / c->vol);
     a.u_drift = drift_u<real>(c);
+    a.rel = c->rel ? 1 : 0;
     fixed_point_scales(c, 1, a.fx_scale, a.fx_quant, a.fx_lo);
     if (c->ions_species) {
         a.ion_in = species_view<real>(c, 1, c->cur[1]);
@@ -892,8 +904,12 @@ static void run_phases_t(pic_ctx *c, unsigned mask)
     // flushes exactly zero, and no rounding residue of the global adds seeds
     // fields ahead of the laser (such residues release pairs at the stencil's
     // speed of 3 cells per step).  Explicit ions keep their own kernel, which
-    // measured faster when every tile holds a full bucket of both species.
-    const bool fused = (mask & PIC_PH_PUSH) && (mask & PIC_PH_IONS) && c->ions_species && !c->p.explicit_ions;
+    // measured faster when every tile holds a full bucket of both species,
+    // except with records in relative form: there the two species' currents
+    // differ by ~1/(2 gamma^2) and must cancel in the integer tile, not in
+    // FP32 global adds.
+    const bool fused = (mask & PIC_PH_PUSH) && (mask & PIC_PH_IONS) && c->ions_species &&
+                       (!c->p.explicit_ions || c->rel);
     if (mask & PIC_PH_PUSH) {
         PhaseTimer pt(c, 1);
         PushArgs<real> a = push_args<real>(c, 0);
@@ -1456,10 +1472,10 @@ static pic_status download_species(pic_ctx *c, int sp, int64_t &n, std::vector<s
 {
     pic_status s = compact_t<real>(c, sp, n);
     if (s != PIC_OK) return s;
-    void *col[9];
+    void *col[kAttrs];
     side_raw(c, sp, c->cur[sp] ^ 1, col);
-    h.assign(9, {});
-    for (int a = 0; a < 9; ++a) {
+    h.assign(kAttrs, {});
+    for (int a = 0; a < kAttrs; ++a) {
         if (!col[a]) continue;
         h[a].resize((size_t)n * attr_size(c, a));
         if (n) CUDA_TRY(c, cudaMemcpyAsync(h[a].data(), col[a], h[a].size(), cudaMemcpyDeviceToHost, c->stream));
@@ -1495,9 +1511,22 @@ static pic_status get_particles_t(pic_ctx *c, int sp, double *dst, size_t dst_by
         auto R = [&](int a) { return reinterpret_cast<const real *>(h[a].data()); };
         int i, j, k;
         unpack_cell(c->g, reinterpret_cast<const int32_t *>(h[7].data())[p], i, j, k);
-        dst[0 * n + row] = ((double)i + (double)R(0)[p]) * c->hx;
-        dst[1 * n + row] = c->g.dim == 3 ? ((double)j + (double)R(1)[p]) * c->hy : 0.0;
-        dst[2 * n + row] = ((double)k + (double)R(2)[p]) * c->hz;
+        if (electron && !h[9].empty()) {
+            // relative form: reference cell + reference offset + departure
+            // (the reference cell is the stored one shifted by rel_actual's r)
+            auto coord = [&](int cell, int ao, int ad, double h_) {
+                int r;
+                (void)rel_actual<real>(R(ao)[p], R(ad)[p], r);
+                return ((double)(cell + r) + ((double)R(ao)[p] + (double)R(ad)[p])) * h_;
+            };
+            dst[0 * n + row] = coord(i, 0, 9, c->hx);
+            dst[1 * n + row] = c->g.dim == 3 ? coord(j, 1, 10, c->hy) : 0.0;
+            dst[2 * n + row] = coord(k, 2, 11, c->hz);
+        } else {
+            dst[0 * n + row] = ((double)i + (double)R(0)[p]) * c->hx;
+            dst[1 * n + row] = c->g.dim == 3 ? ((double)j + (double)R(1)[p]) * c->hy : 0.0;
+            dst[2 * n + row] = ((double)k + (double)R(2)[p]) * c->hz;
+        }
         if (electron) {
             dst[3 * n + row] = (double)R(4)[p];
             dst[4 * n + row] = (double)R(5)[p];
@@ -1629,7 +1658,7 @@ extern "C" pic_status pic_get_diagnostics(pic_ctx *c, pic_diag *out)
 static size_t species_state_bytes(const pic_ctx *c, int sp, int64_t n)
 {
     size_t b = 0;
-    for (int a = 0; a < 9; ++a)
+    for (int a = 0; a < kAttrs; ++a)
         if (c->side[sp].off[a] != SIZE_MAX) b += (size_t)n * attr_size(c, a);
     return b;
 }
@@ -1654,7 +1683,8 @@ template <typename real>
 static pic_status get_state_t(pic_ctx *c, unsigned char *dst, size_t dst_bytes, int dst_is_device)
 {
     StateHeader h{};
-    std::memcpy(h.magic, "PICSTAT3", 8);
+    std::memcpy(h.magic, "PICSTAT4", 8);
+    h.rel = c->rel;
     h.dim = c->g.dim;
     h.nx = c->g.nx;
     h.ny = c->g.ny;
@@ -1690,9 +1720,9 @@ static pic_status get_state_t(pic_ctx *c, unsigned char *dst, size_t dst_bytes, 
         o += per;
     }
     for (int sp = 0; sp < (c->ions_species ? 2 : 1); ++sp) {
-        void *col[9];
+        void *col[kAttrs];
         side_raw(c, sp, c->cur[sp] ^ 1, col);
-        for (int a = 0; a < 9; ++a) {
+        for (int a = 0; a < kAttrs; ++a) {
             if (!col[a]) continue;
             const size_t b = (size_t)n[sp] * attr_size(c, a);
             if (b) CUDA_TRY(c, cudaMemcpyAsync(dst + o, col[a], b, kind_out(dst_is_device), c->stream));
@@ -1718,7 +1748,7 @@ static pic_status set_state_t(pic_ctx *c, const unsigned char *src, size_t src_b
     if (src_bytes < sizeof(h)) return fail(c, PIC_ERR_ARG, "snapshot too small");
     CUDA_TRY(c, cudaMemcpyAsync(&h, src, sizeof(h), src_is_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    if (std::memcmp(h.magic, "PICSTAT3", 8) != 0 || h.dim != c->g.dim || h.nx != c->g.nx || h.ny != c->g.ny ||
+    if (std::memcmp(h.magic, "PICSTAT4", 8) != 0 || h.rel != (int)c->rel || h.dim != c->g.dim || h.nx != c->g.nx || h.ny != c->g.ny ||
         h.nz != c->g.nz || h.precision != c->p.precision || h.track_ids != c->p.track_ids ||
         h.has_ions != (int)c->ions_species || h.n[0] < 0 || h.n[1] < 0 || h.n[0] > c->slots || h.n[1] > c->slots ||
         !(h.wmax >= 0) || !std::isfinite(h.wmax))
@@ -1732,8 +1762,8 @@ static pic_status set_state_t(pic_ctx *c, const unsigned char *src, size_t src_b
     o += c->field_bytes;
     for (int sp = 0; sp < (c->ions_species ? 2 : 1); ++sp) {
         CUDA_TRY(c, cudaMemsetAsync(counts(c, sp, 0, 0), 0, sizeof(int) * 4 * (size_t)c->g.ntiles, c->stream));
-        const void *cols[9] = {nullptr};
-        for (int a = 0; a < 9; ++a) {
+        const void *cols[kAttrs] = {nullptr};
+        for (int a = 0; a < kAttrs; ++a) {
             if (c->side[sp].off[a] == SIZE_MAX) continue;
             cols[a] = src + o;
             o += (size_t)h.n[sp] * attr_size(c, a);

@@ -75,7 +75,7 @@ __device__ __forceinline__ void to_cell(double x, double h, int n, bool periodic
 }
 
 template <typename real>
-__device__ __forceinline__ void store(void *const sp[9], int64_t d, real ox, real oy, real oz, real w, int32_t cell,
+__device__ __forceinline__ void store(void *const sp[kAttrs], int64_t d, real ox, real oy, real oz, real w, int32_t cell,
                                       int64_t id, bool electron, bool dim3)
 {
     static_cast<real *>(sp[0])[d] = ox;
@@ -89,6 +89,10 @@ __device__ __forceinline__ void store(void *const sp[9], int64_t d, real ox, rea
     }
     static_cast<int32_t *>(sp[7])[d] = cell;
     if (sp[8]) static_cast<int64_t *>(sp[8])[d] = id;
+    if (electron) {  // relative form: on its reference
+        for (int q = 9; q < kAttrs; ++q)
+            if (sp[q]) static_cast<real *>(sp[q])[d] = real(0);
+    }
 }
 
 template <typename real>

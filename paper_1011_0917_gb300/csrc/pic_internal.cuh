@@ -15,7 +15,8 @@
 //            (particles that arrived from a neighbour, were loaded or were
 //            injected).  A particle is an int32 packed cell index plus its
 //            offsets in [0,1) inside that cell (real), its weight and
-//            (electrons) u = gamma v.
+//            (electrons) u = gamma v; with drift-relative z (below) an
+//            electron also carries its departure from the drift.
 //   scratch: per-side tile counters, the filter ping-pong buffer, per-tile
 //            offsets for compaction, reduction partials and the error word.
 #pragma once
@@ -48,13 +49,56 @@ struct Geom {
     int64_t ntiles;
 };
 
+// attribute arrays of a species side, in this order: ox oy oz w ux uy uz cell
+// id dlx dly dlz (absent ones are null)
+constexpr int kAttrs = 12;
+
 template <typename real>
 struct Species {
     real *ox, *oy, *oz, *w;     // oy is null in 2D
     real *ux, *uy, *uz;         // null for ions (constant drift)
     int32_t *cell;
     int64_t *id;                // null unless ids are tracked
+    real *dlx, *dly, *dlz;      // relative positions only (see rel_actual); dly null in 2D
 };
+
+// Relative positions of an electron record.  In a strongly boosted frame the
+// plasma (electrons and ions, gamma n each) streams through a good part of a
+// cell every step, while the wake is made of the difference between the two
+// species' currents: ~1/(2 gamma^2) of the plasma's response in the lab, so
+// at gamma = 130 about 3e-8 of either species' current.  Each particle's
+// current must then be formed from a position exact far beyond FP32, and in
+// FP64 arithmetic, or the difference is rounding noise.  A record in relative
+// form holds, per axis, a reference offset o in [0, 1) -- along z it moves
+// with exactly the arithmetic of a drifting ion, across it stays where the
+// particle was placed, i.e. it is its ion's path -- plus the departure dl
+// from it, |dl| <= 1/2 (whole cells move between dl and the reference cell,
+// which is exact).  The position is c_ref + o + dl with c_ref = c + r, c the
+// stored cell (the one the electron is in, so that tiles and stencils are as
+// for any record) and r the shift this function returns; its result is the
+// electron's offset in cell c, in [0, 1), for the gather.  The rounding of
+// o + dl here does not accumulate: it is redone from the exact pair every
+// step, and the current is deposited from the pair itself (in FP64).
+template <typename real>
+__host__ __device__ inline real rel_actual(real o, real dl, int &r)
+{
+    const real a = o + dl;
+    if (a < real(0)) {
+        const real t = a + real(1);
+        if (t < real(1)) {
+            r = 1;
+            return t;
+        }
+        r = 0;  // within rounding of the cell's lower face
+        return real(0);
+    }
+    if (a >= real(1)) {
+        r = -1;
+        return a - real(1);
+    }
+    r = 0;
+    return a;
+}
 
 __host__ __device__ inline int32_t pack_cell(const Geom &g, int i, int j, int k)
 {
@@ -209,6 +253,27 @@ __device__ __forceinline__ int esirk_axis_c(real x0, real x1, real S0[S + 2], re
     return anchor;
 }
 
+// The same for a start position x0 that need not lie in [0, 1) (within a
+// cell of it): both supports from the spline itself.
+template <int S, typename real>
+__device__ __forceinline__ int esirk_axis_g(real x0, real x1, real S0[S + 2], real DS[S + 2], bool &crossed)
+{
+    real w0[S + 1], w1[S + 1];
+    const int b0 = spline_weights<S>(x0, w0);
+    const int b1 = spline_weights<S>(x1, w1);
+    const int anchor = b0 < b1 ? b0 : b1;
+    const bool s0 = b0 != anchor, s1 = b1 != anchor;
+    crossed = b0 != b1;
+#pragma unroll
+    for (int q = 0; q < S + 2; ++q) {
+        const real v0 = s0 ? (q >= 1 ? w0[q - 1 < S ? q - 1 : S] : real(0)) : (q <= S ? w0[q <= S ? q : S] : real(0));
+        const real v1 = s1 ? (q >= 1 ? w1[q - 1 < S ? q - 1 : S] : real(0)) : (q <= S ? w1[q <= S ? q : S] : real(0));
+        S0[q] = v0;
+        DS[q] = v1 - v0;
+    }
+    return anchor;
+}
+
 // periodic index for i in [-n, 2n)
 __device__ __forceinline__ int wrap1(int i, int n)
 {
@@ -346,6 +411,8 @@ struct PushArgs {
     int *ion_in_hi;        // its top-run lengths
     int fuse_ions;         // 1: the same CTA then moves and deposits the tile's ions
     IonSide<real> ions;    // (with fuse_ions) the ion sides and counters
+    int rel;               // 1: electron records in relative form (rel_actual), currents
+                           //    of electrons and ions from FP64 arithmetic
     unsigned *err;
 };
 
@@ -405,8 +472,8 @@ struct InjectArgs {      // lattice load / boosted injection, FP64
     int drift_ions;     // ions drift with the plasma
     int paired;         // electrons are placed paired with their ion (no ion record)
     int precision;      // 0 float, 1 double
-    void *sp_e[9];      // ox oy oz w ux uy uz cell id of the electron side
-    void *sp_i[9];      // same for the ion side (ux..uz unused)
+    void *sp_e[kAttrs];  // ox oy oz w ux uy uz cell id dlx dly dlz of the electron side
+    void *sp_i[kAttrs];  // same for the ion side (ux..uz, dl* unused)
     int *hi_e, *hi_i;    // top-run lengths of the electron / ion sides
     unsigned *err;
     // fixed-order ("flat") output of an adjoint run (flat_base >= 0, 2D):

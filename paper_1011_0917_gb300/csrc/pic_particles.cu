@@ -12,6 +12,7 @@
 #include "pic_internal.cuh"
 
 #include <cuda_pipeline.h>
+#include <type_traits>
 
 namespace pic {
 
@@ -51,6 +52,19 @@ __device__ __forceinline__ void sh_acc(int *p, float a, float b, float lo_scale)
     const int h = __float_as_int(t) - kRoundMagicBits;
     const float r = v - (t - kRoundMagic);
     const int l = __float_as_int(fmaf(r, lo_scale, kRoundMagic)) - kRoundMagicBits;
+    if (h != 0) atomicAdd(p, h);
+    if (l != 0) atomicAdd(p + LOFF, l);
+}
+
+// FP64 contributions into the same fixed-point words (records in relative
+// form): h and the remainder's 2^K multiple rounded from the FP64 product
+template <int LOFF>
+__device__ __forceinline__ void sh_acc(int *p, double a, double b, double lo_scale)
+{
+    const double v = a * b;
+    const double hd = rint(v);
+    const int h = (int)hd;
+    const int l = (int)rint((v - hd) * lo_scale);
     if (h != 0) atomicAdd(p, h);
     if (l != 0) atomicAdd(p + LOFF, l);
 }
@@ -220,8 +234,8 @@ __device__ __forceinline__ real gather_comp(const real *F, int FX, int FY, int i
 // which is Esirkepov's decomposition rearranged; the last running sum of a
 // window is zero and is not added.  In 2D3V the out-of-plane current is the
 // path average of the shape times q w vy / V.
-template <typename real, int DIM, int S, int QX, int QY, int QN, int WX, int WY, int WZ>
-__device__ __forceinline__ void deposit_w(typename Acc<real>::type *sJ, const real *S0x, const real *DSx, const real *S0y,
+template <typename real, typename accT, int DIM, int S, int QX, int QY, int QN, int WX, int WY, int WZ>
+__device__ __forceinline__ void deposit_w(accT *sJ, const real *S0x, const real *DSx, const real *S0y,
                                           const real *DSy, const real *S0z, const real *DSz, int ax, int ay, int az,
                                           real fx, real fy, real fz, real fyv, real los)
 {
@@ -292,8 +306,8 @@ __device__ __forceinline__ void deposit_w(typename Acc<real>::type *sJ, const re
 // exactly, so Jx = Jy = 0 and Jz(q,b,c) = fz (sum_{c'<=c} DSz[c']) S0x[q] S0y[b]
 // -- the general formula's values with DSx = DSy = 0.  Windows along x and y
 // have S+1 nodes (their supports did not move).
-template <typename real, int S, int QX, int QY, int QN, int WZ>
-__device__ __forceinline__ void deposit_z(typename Acc<real>::type *sJ, const real *S0x, const real *S0y, const real *S0z,
+template <typename real, typename accT, int S, int QX, int QY, int QN, int WZ>
+__device__ __forceinline__ void deposit_z(accT *sJ, const real *S0x, const real *S0y, const real *S0z,
                                           const real *DSz, int ax, int ay, int az, real fz, real los)
 {
     constexpr int LOFF = 3 * QN;
@@ -316,14 +330,14 @@ __device__ __forceinline__ void deposit_z(typename Acc<real>::type *sJ, const re
 }
 
 // picks the window lengths for the warp: bit 2 x, bit 1 y, bit 0 z crossed
-template <typename real, int DIM, int S, int QX, int QY, int QN>
-__device__ __forceinline__ void deposit_sel(unsigned sel, typename Acc<real>::type *sJ, const real *S0x, const real *DSx, const real *S0y,
+template <typename real, typename accT, int DIM, int S, int QX, int QY, int QN>
+__device__ __forceinline__ void deposit_sel(unsigned sel, accT *sJ, const real *S0x, const real *DSx, const real *S0y,
                                             const real *DSy, const real *S0z, const real *DSz, int ax, int ay, int az,
                                             real fx, real fy, real fz, real fyv, real los)
 {
     constexpr int A = S + 1, B = S + 2;
 #define PIC_DEP(wx, wy, wz) \
-    deposit_w<real, DIM, S, QX, QY, QN, wx, wy, wz>(sJ, S0x, DSx, S0y, DSy, S0z, DSz, ax, ay, az, fx, fy, fz, fyv, los)
+    deposit_w<real, accT, DIM, S, QX, QY, QN, wx, wy, wz>(sJ, S0x, DSx, S0y, DSy, S0z, DSz, ax, ay, az, fx, fy, fz, fyv, los)
     if (DIM == 3) {
         switch (sel) {
         case 0: PIC_DEP(A, A, A); break;
@@ -364,13 +378,49 @@ __device__ __forceinline__ void deposit_sel(unsigned sel, typename Acc<real>::ty
 // for an empty bucket.
 constexpr int kIonStages = 3;
 
-template <typename real, int DIM, int S, int TX, int TY, int TZ, int LOFF>
+// Jz of one ion moving along z from z0 to z1 (both relative to its cell, z0 in
+// [0, 1)), in arithmetic ar, into the current tile Jz (QX x QY rows)
+template <typename ar, typename accT, int DIM, int S, int QX, int QY, int LOFF>
+__device__ __forceinline__ void ion_deposit(accT *Jz, ar z0, ar z1, ar ox, ar oy, int li, int lj, int lk, ar fz,
+                                            ar lo_scale)
+{
+    constexpr int JL = S;
+    ar S0z[S + 2], DSz[S + 2], wx[S + 1], wy[S + 1];
+    bool crossed;
+    const int az = esirk_axis_c<S>(z0, z1, S0z, DSz, crossed) + lk + JL;
+    const int bx = offset_weights<S>(ox, wx) + li + JL;
+    int by = 0;
+    if (DIM == 3) by = offset_weights<S>(oy, wy) + lj + JL;
+    ar Pz[S + 2];
+    ar run = 0;
+#pragma unroll
+    for (int c = 0; c < S + 2; ++c) {
+        run += DSz[c];
+        Pz[c] = fz * run;
+    }
+#pragma unroll
+    for (int b = 0; b < (DIM == 3 ? S + 1 : 1); ++b) {
+#pragma unroll
+        for (int q = 0; q < S + 1; ++q) {
+            const ar sxy = DIM == 3 ? wx[q] * wy[b] : wx[q];
+#pragma unroll
+            for (int c = 0; c < S + 1; ++c)
+                sh_acc<LOFF>(Jz + ((az + c) * QY + (by + b)) * QX + bx + q, Pz[c], sxy, lo_scale);
+        }
+    }
+}
+
+// REL: the tile's electrons are in relative form; the ions' currents are then
+// formed in FP64 from their stored positions (the end of one step's path is
+// exactly the start of the next one's)
+template <typename real, int DIM, int S, int TX, int TY, int TZ, int LOFF, bool REL>
 __device__ __forceinline__ bool ions_of_tile(const Geom &g, const IonSide<real> &is, int64_t t,
                                              typename Acc<real>::type *Jz, real *sP, real dz, real scale_z,
                                              real lo_scale, unsigned *err, int *s_stay)
 {
     constexpr int JL = S, JH = S + 1;
     constexpr int QX = TX + JL + JH, QY = DIM == 3 ? TY + JL + JH : 1;
+    using acc_t = typename Acc<real>::type;
     const unsigned lane = threadIdx.x & 31u;
     int n_lo, n_hi;
     bucket_counts(is.in_lo, is.in_hi, t, g.cap, n_lo, n_hi, err);
@@ -424,37 +474,25 @@ __device__ __forceinline__ bool ions_of_tile(const Geom &g, const IonSide<real> 
                 oz = d[2 * kBlock];
                 w = d[3 * kBlock];
                 if (is.in.id) pid = is.in.id[bucket_slot(t, g.cap, n_lo, n_hi, p)];
-                const real z1 = add_rn(oz, dz);
-                real S0z[S + 2], DSz[S + 2], wx[S + 1], wy[S + 1];
-                bool crossed;
-                const int az = esirk_axis_c<S>(oz, z1, S0z, DSz, crossed) + lk + JL;
-                const int bx = offset_weights<S>(ox, wx) + li + JL;
-                int by = 0;
-                if (DIM == 3) by = offset_weights<S>(oy, wy) + lj + JL;
-                const real fz = is.jfac_z * w * scale_z;
-                real Pz[S + 2];
-                real acc = 0;
-#pragma unroll
-                for (int c = 0; c < S + 2; ++c) { acc += DSz[c]; Pz[c] = fz * acc; }
-#pragma unroll
-                for (int b = 0; b < (DIM == 3 ? S + 1 : 1); ++b) {
-#pragma unroll
-                    for (int q = 0; q < S + 1; ++q) {
-                        const real sxy = DIM == 3 ? wx[q] * wy[b] : wx[q];
-#pragma unroll
-                        for (int c = 0; c < S + 1; ++c)
-                            sh_acc<LOFF>(Jz + ((az + c) * QY + (by + b)) * QX + bx + q, Pz[c], sxy, lo_scale);
-                    }
-                }
                 // z1 in (-1, 1): the same cell or the one below; an offset
                 // that rounds to 1 stays in the cell with offset 0
+                const real z1 = add_rn(oz, dz);
                 int sz = 0;
-                oz = z1;
+                real on = z1;
                 if (z1 < real(0)) {
-                    oz = z1 + real(1);
+                    on = z1 + real(1);
                     sz = -1;
-                    if (oz >= real(1)) { oz = 0; sz = 0; }
+                    if (on >= real(1)) { on = 0; sz = 0; }
                 }
+                if (REL) {
+                    ion_deposit<double, acc_t, DIM, S, QX, QY, LOFF>(
+                        Jz, (double)oz, (double)sz + (double)on, (double)ox, (double)oy, li, lj, lk,
+                        (double)is.jfac_z * (double)w * (double)scale_z, (double)lo_scale);
+                } else {
+                    ion_deposit<real, acc_t, DIM, S, QX, QY, LOFF>(Jz, oz, z1, ox, oy, li, lj, lk,
+                                                                   is.jfac_z * w * scale_z, lo_scale);
+                }
+                oz = on;
                 int nk = ck + sz;
                 bool alive = true;
                 if (nk < 0) {
@@ -509,7 +547,27 @@ __device__ __forceinline__ bool ions_of_tile(const Geom &g, const IonSide<real> 
 
 // ------------------------------------------------------------ push kernel
 
-template <typename real, int DIM, int S, int TX, int TY, int TZ>
+// one axis of a record in relative form: the departure takes the step's
+// displacement d; whole cells move to the reference (exact: |dl| <= 3/2)
+template <typename real>
+__device__ __forceinline__ real rel_step(real dl, real d, int &fold)
+{
+    real v = dl + d;
+    fold = 0;
+    if (v > real(0.5)) {
+        v = v - real(1);
+        fold = 1;
+    } else if (v < real(-0.5)) {
+        v = v + real(1);
+        fold = -1;
+    }
+    return v;
+}
+
+// REL: electron records in relative form (rel_actual): the gather uses the
+// offsets in the stored cell, the current is deposited in FP64 from the exact
+// positions reference + departure
+template <typename real, int DIM, int S, int TX, int TY, int TZ, bool REL>
 __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(PushArgs<real> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -522,11 +580,14 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
     constexpr int QX = TX + JL + JH, QY = DIM == 3 ? TY + JL + JH : 1, QZ = TZ + JL + JH;
     constexpr int FN = FX * FY * FZ, QN = QX * QY * QZ;
     using acc_t = typename Acc<real>::type;
+    // arithmetic of the deposit: FP64 for records in relative form
+    using dep_t = typename std::conditional<REL, double, real>::type;
     real *sF = reinterpret_cast<real *>(smem_raw);
     acc_t *sJ = reinterpret_cast<acc_t *>(sF + 6 * FN);
     // the next iteration's particle records are copied into shared memory
     // with cp.async while the current ones are pushed (two buffers of
-    // 8 attributes x kBlock particles; each thread copies and reads its own)
+    // NA attributes x kBlock particles; each thread copies and reads its own)
+    constexpr int NA = REL ? (DIM == 3 ? 11 : 10) : 8;
     real *sP = reinterpret_cast<real *>(sJ + (sizeof(real) == 4 ? 6 : 3) * QN);
     __shared__ int s_stay, s_stay_i;
     // the plasma drift and its displacement per step (the drifting ions')
@@ -543,7 +604,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
             const int p = it * kBlock + (int)threadIdx.x;
             if (p < n) {
                 const int64_t s = bucket_slot(t, g.cap, n_lo, n_hi, p);
-                real *d = sP + (it & 1) * 8 * kBlock + threadIdx.x;
+                real *d = sP + (it & 1) * NA * kBlock + threadIdx.x;
                 __pipeline_memcpy_async(d + 0 * kBlock, a.in.ox + s, sizeof(real));
                 if (DIM == 3) __pipeline_memcpy_async(d + 1 * kBlock, a.in.oy + s, sizeof(real));
                 __pipeline_memcpy_async(d + 2 * kBlock, a.in.oz + s, sizeof(real));
@@ -552,6 +613,11 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
                 __pipeline_memcpy_async(d + 5 * kBlock, a.in.uy + s, sizeof(real));
                 __pipeline_memcpy_async(d + 6 * kBlock, a.in.uz + s, sizeof(real));
                 __pipeline_memcpy_async(d + 7 * kBlock, a.in.cell + s, sizeof(int32_t));
+                if (REL) {
+                    __pipeline_memcpy_async(d + 8 * kBlock, a.in.dlx + s, sizeof(real));
+                    __pipeline_memcpy_async(d + 9 * kBlock, a.in.dlz + s, sizeof(real));
+                    if (DIM == 3) __pipeline_memcpy_async(d + 10 * kBlock, a.in.dly + s, sizeof(real));
+                }
             }
             __pipeline_commit();
         };
@@ -575,12 +641,16 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
             prefetch(it + 1);
             __pipeline_wait_prior(1);
             real ox = 0, oy = 0, oz = 0, w = 0, ux = 0, uy = 0, uz = 0;
+            // relative form: reference offsets, departures and the reference
+            // cell's shift from the stored cell, per axis
+            real orx = 0, ory = 0, orz = 0, dlx = 0, dly = 0, dlz = 0;
+            int rx = 0, ry = 0, rz = 0;
             int ci = 0, cj = 0, ck = 0, li = 0, lj = 0, lk = 0;
             int64_t pid = 0;
             bool paired = false;
             // ---- load (from the prefetched records)
             if (valid) {
-                const real *d = sP + (it & 1) * 8 * kBlock + threadIdx.x;
+                const real *d = sP + (it & 1) * NA * kBlock + threadIdx.x;
                 const int32_t word = *reinterpret_cast<const int32_t *>(d + 7 * kBlock);
                 paired = ((uint32_t)word & kPaired) != 0u;
                 unpack_cell(g, word, ci, cj, ck);
@@ -598,11 +668,28 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
                     ux = d[4 * kBlock];
                     uy = d[5 * kBlock];
                     uz = d[6 * kBlock];
+                    if (REL) {
+                        orx = ox;
+                        ory = oy;
+                        orz = oz;
+                        dlx = d[8 * kBlock];
+                        dlz = d[9 * kBlock];
+                        if (DIM == 3) dly = d[10 * kBlock];
+                        ox = rel_actual(orx, dlx, rx);
+                        oz = rel_actual(orz, dlz, rz);
+                        if (DIM == 3) oy = rel_actual(ory, dly, ry);
+                    }
                     if (a.in.id) pid = a.in.id[bucket_slot(t, g.cap, n_lo, n_hi, p)];
                 }
             }
             // ---- gather E^n, B^n at x^n, Boris, move
             real x1 = 0, y1 = 0, z1 = 0, vy = 0;
+            // relative form: new departures, new z reference, the new cell's
+            // shift per axis, and the exact (FP64) start and end of the path
+            // relative to the old cell
+            real dlx1 = 0, dly1 = 0, dlz1 = 0, orz1 = 0;
+            int mx = 0, my = 0, mz = 0;
+            double X0 = 0, X1 = 0, Y0 = 0, Y1 = 0, Z0 = 0, Z1 = 0;
             bool release = false;
             if (valid) {
                 // a tile whose staged E and B are all zero gathers exactly zero
@@ -645,6 +732,41 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
                 if (!(fabs(dx) < real(1) && fabs(dy) < real(1) && fabs(dz) < real(1))) {
                     atomicOr(a.err, (dx == dx && dy == dy && dz == dz) ? ERR_CFL : ERR_NAN);
                     valid = false;
+                } else if (REL) {
+                    // across z the reference stays, the departure moves
+                    int fx, r1;
+                    dlx1 = rel_step(dlx, dx, fx);
+                    (void)rel_actual(orx, dlx1, r1);
+                    mx = rx + fx - r1;
+                    X0 = (double)rx + ((double)orx + (double)dlx);
+                    X1 = (double)(rx + fx) + ((double)orx + (double)dlx1);
+                    if (DIM == 3) {
+                        int fy;
+                        dly1 = rel_step(dly, dy, fy);
+                        (void)rel_actual(ory, dly1, r1);
+                        my = ry + fy - r1;
+                        Y0 = (double)ry + ((double)ory + (double)dly);
+                        Y1 = (double)(ry + fy) + ((double)ory + (double)dly1);
+                    }
+                    // along z the reference moves exactly like a drifting ion
+                    // (same rounding, same cell changes)
+                    real sref = add_rn(orz, dz_drift);
+                    int sr = 0;
+                    if (sref < real(0)) {
+                        sref = sref + real(1);
+                        sr = -1;
+                        if (sref >= real(1)) { sref = 0; sr = 0; }
+                    } else if (sref >= real(1)) {
+                        sref = sref - real(1);
+                        sr = 1;
+                    }
+                    int fz;
+                    dlz1 = rel_step(dlz, ddz, fz);
+                    (void)rel_actual(sref, dlz1, r1);
+                    orz1 = sref;
+                    mz = rz + sr + fz - r1;
+                    Z0 = (double)rz + ((double)orz + (double)dlz);
+                    Z1 = (double)(rz + sr + fz) + ((double)sref + (double)dlz1);
                 } else {
                     x1 = ox + dx;
                     y1 = oy + dy;
@@ -659,10 +781,11 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
                     if (r >= g.cap) {
                         atomicOr(a.err, ERR_CAPACITY);
                     } else {
+                        // (a paired record sits on its reference: orx = ox, ...)
                         const int64_t d = t * (int64_t)g.cap + (g.cap - 1 - r);
-                        a.ion_in.ox[d] = ox;
-                        if (DIM == 3) a.ion_in.oy[d] = oy;
-                        a.ion_in.oz[d] = oz;
+                        a.ion_in.ox[d] = REL ? orx : ox;
+                        if (DIM == 3) a.ion_in.oy[d] = REL ? ory : oy;
+                        a.ion_in.oz[d] = REL ? orz : oz;
                         a.ion_in.w[d] = w;
                         a.ion_in.cell[d] = pack_cell(g, ci, cj, ck);
                         if (a.ion_in.id) a.ion_in.id[d] = pid;
@@ -671,48 +794,69 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
             }
             const bool keep_pair = valid && paired && !release;  // exactly zero net current
             // ---- Esirkepov windows; the warp agrees on their lengths
-            real S0x[S + 2], DSx[S + 2], S0y[S + 2], DSy[S + 2], S0z[S + 2], DSz[S + 2];
+            dep_t S0x[S + 2], DSx[S + 2], S0y[S + 2], DSy[S + 2], S0z[S + 2], DSz[S + 2];
             int ax = 0, ay = 0, az = 0;
             bool cx = false, cy = false, cz = false;
             if (valid && !keep_pair) {
-                ax = esirk_axis_c<S>(ox, x1, S0x, DSx, cx) + li + JL;
-                az = esirk_axis_c<S>(oz, z1, S0z, DSz, cz) + lk + JL;
-                if (DIM == 3) ay = esirk_axis_c<S>(oy, y1, S0y, DSy, cy) + lj + JL;
+                if (REL) {
+                    ax = esirk_axis_g<S, dep_t>((dep_t)X0, (dep_t)X1, S0x, DSx, cx) + li + JL;
+                    az = esirk_axis_g<S, dep_t>((dep_t)Z0, (dep_t)Z1, S0z, DSz, cz) + lk + JL;
+                    if (DIM == 3) ay = esirk_axis_g<S, dep_t>((dep_t)Y0, (dep_t)Y1, S0y, DSy, cy) + lj + JL;
+                } else {
+                    ax = esirk_axis_c<S, dep_t>(ox, x1, S0x, DSx, cx) + li + JL;
+                    az = esirk_axis_c<S, dep_t>(oz, z1, S0z, DSz, cz) + lk + JL;
+                    if (DIM == 3) ay = esirk_axis_c<S, dep_t>(oy, y1, S0y, DSy, cy) + lj + JL;
+                }
             }
             const unsigned sel = (__any_sync(0xffffffffu, cx) ? 4u : 0u) | (__any_sync(0xffffffffu, cy) ? 2u : 0u) |
                                  (__any_sync(0xffffffffu, cz) ? 1u : 0u);
             // 3D: no lane moved in x or y (e.g. plasma the laser has not reached)
             const bool z_only =
-                DIM == 3 && __all_sync(0xffffffffu, !valid || keep_pair || (x1 == ox && y1 == oy));
+                DIM == 3 && __all_sync(0xffffffffu, !valid || keep_pair ||
+                                                        (REL ? (X1 == X0 && Y1 == Y0) : (x1 == ox && y1 == oy)));
             int64_t dest = -1;
             int ni = 0, nj = 0, nk = 0;
             if (valid && keep_pair) {
                 // moved exactly like its ion: no deposit
             } else if (valid) {
-                const real fz = a.jfac[2] * w * a.fx_scale[2];
+                const dep_t los = (dep_t)a.fx_lo[0];
+                const dep_t fz = (dep_t)a.jfac[2] * (dep_t)w * (dep_t)a.fx_scale[2];
                 if (z_only) {
                     if (sel & 1u)
-                        deposit_z<real, S, QX, QY, QN, S + 2>(sJ, S0x, S0y, S0z, DSz, ax, ay, az, fz, a.fx_lo[0]);
+                        deposit_z<dep_t, acc_t, S, QX, QY, QN, S + 2>(sJ, S0x, S0y, S0z, DSz, ax, ay, az, fz, los);
                     else
-                        deposit_z<real, S, QX, QY, QN, S + 1>(sJ, S0x, S0y, S0z, DSz, ax, ay, az, fz, a.fx_lo[0]);
+                        deposit_z<dep_t, acc_t, S, QX, QY, QN, S + 1>(sJ, S0x, S0y, S0z, DSz, ax, ay, az, fz, los);
                 } else {
-                    deposit_sel<real, DIM, S, QX, QY, QN>(sel, sJ, S0x, DSx, S0y, DSy, S0z, DSz, ax, ay, az,
-                                                          a.jfac[0] * w * a.fx_scale[0],
-                                                          a.jfac[1] * w * a.fx_scale[1], fz,
-                                                          a.jyfac * w * vy * a.fx_scale[1], a.fx_lo[0]);
+                    deposit_sel<dep_t, acc_t, DIM, S, QX, QY, QN>(
+                        sel, sJ, S0x, DSx, S0y, DSy, S0z, DSz, ax, ay, az,
+                        (dep_t)a.jfac[0] * (dep_t)w * (dep_t)a.fx_scale[0],
+                        (dep_t)a.jfac[1] * (dep_t)w * (dep_t)a.fx_scale[1], fz,
+                        (dep_t)a.jyfac * (dep_t)w * (dep_t)vy * (dep_t)a.fx_scale[1], los);
                 }
             }
             if (valid) {
                 // new cell and offsets; an offset that rounds to 1 moves on
-                int sx = (int)floor(x1), sy = DIM == 3 ? (int)floor(y1) : 0, sz = (int)floor(z1);
-                ox = x1 - real(sx);
-                if (ox >= real(1)) { sx += 1; ox = 0; }
-                if (DIM == 3) {
-                    oy = y1 - real(sy);
-                    if (oy >= real(1)) { sy += 1; oy = 0; }
+                int sx, sy = 0, sz;
+                if (REL) {
+                    sx = mx;
+                    sy = my;
+                    sz = mz;
+                    oz = orz1;  // x, y references do not move
+                    ox = orx;
+                    oy = ory;
+                } else {
+                    sx = (int)floor(x1);
+                    sy = DIM == 3 ? (int)floor(y1) : 0;
+                    sz = (int)floor(z1);
+                    ox = x1 - real(sx);
+                    if (ox >= real(1)) { sx += 1; ox = 0; }
+                    if (DIM == 3) {
+                        oy = y1 - real(sy);
+                        if (oy >= real(1)) { sy += 1; oy = 0; }
+                    }
+                    oz = z1 - real(sz);
+                    if (oz >= real(1)) { sz += 1; oz = 0; }
                 }
-                oz = z1 - real(sz);
-                if (oz >= real(1)) { sz += 1; oz = 0; }
                 ni = ci + sx;
                 if (ni < 0) ni += g.nx; else if (ni >= g.nx) ni -= g.nx;
                 nj = cj + sy;
@@ -740,6 +884,11 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
                     a.out.ux[d] = ux;
                     a.out.uy[d] = uy;
                     a.out.uz[d] = uz;
+                    if (REL) {
+                        a.out.dlx[d] = dlx1;
+                        if (DIM == 3) a.out.dly[d] = dly1;
+                        a.out.dlz[d] = dlz1;
+                    }
                     a.out.cell[d] = (int32_t)((uint32_t)pack_cell(g, ni, nj, nk) | (keep_pair ? kPaired : 0u));
                     if (a.out.id) a.out.id[d] = pid;
                 }
@@ -748,8 +897,8 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
         __syncthreads();
         // the drifting ions of the tile, into the same current tile
         if (a.fuse_ions) {
-            ions_of_tile<real, DIM, S, TX, TY, TZ, 3 * QN>(g, a.ions, t, sJ + 2 * QN, sP, dz_drift, a.fx_scale[2],
-                                                            a.fx_lo[0], a.err, &s_stay_i);
+            ions_of_tile<real, DIM, S, TX, TY, TZ, 3 * QN, REL>(g, a.ions, t, sJ + 2 * QN, sP, dz_drift,
+                                                                 a.fx_scale[2], a.fx_lo[0], a.err, &s_stay_i);
         }
         // flush the J tile: one global add per non-zero node
         flush_tile<real, DIM, 3, QX, QY, QZ, JL>(g, Ptr3<real>{a.J[0], a.J[1], a.J[2]}, 0x4u, sJ, a.fx_quant[0],
@@ -764,7 +913,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
 
 // ----------------------------------------------------- drifting-ion kernel
 
-template <typename real, int DIM, int S, int TX, int TY, int TZ>
+template <typename real, int DIM, int S, int TX, int TY, int TZ, bool REL>
 __global__ void __launch_bounds__(kBlock) ion_kernel(PushArgs<real> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -790,7 +939,8 @@ __global__ void __launch_bounds__(kBlock) ion_kernel(PushArgs<real> a)
         const int lox = tix << g.lt[0], loy = tiy << g.lt[1], loz = tiz << g.lt[2];
         __syncthreads();
         for (int q = threadIdx.x; q < (sizeof(real) == 4 ? 2 : 1) * QN; q += blockDim.x) sJ[q] = 0;
-        ions_of_tile<real, DIM, S, TX, TY, TZ, QN>(g, is, t, sJ, sP, dz, a.fx_scale[2], a.fx_lo[0], a.err, &s_stay);
+        ions_of_tile<real, DIM, S, TX, TY, TZ, QN, REL>(g, is, t, sJ, sP, dz, a.fx_scale[2], a.fx_lo[0], a.err,
+                                                        &s_stay);
         flush_tile<real, DIM, 1, QX, QY, QZ, JL>(g, Ptr3<real>{a.J[2], a.J[2], a.J[2]}, 0x1u, sJ, a.fx_quant[2],
                                                  a.fx_quant[2], a.fx_quant[2], a.fx_lo[1], lox, loy, loz);
     }
@@ -801,7 +951,7 @@ __global__ void __launch_bounds__(kBlock) ion_kernel(PushArgs<real> a)
 constexpr int kTile3[3] = {8, 8, 8};
 constexpr int kTile2[3] = {16, 1, 16};
 
-template <typename real, int DIM, int S, int TX, int TY, int TZ>
+template <typename real, int DIM, int S, int TX, int TY, int TZ, bool REL>
 static size_t push_smem(bool ions)
 {
     const int FN = (TX + 1 + S) * (DIM == 3 ? TY + 1 + S : 1) * (TZ + 1 + S);
@@ -810,17 +960,25 @@ static size_t push_smem(bool ions)
     const int JW = sizeof(real) == 4 ? 2 : 1;
     static_assert(kIonStages * 5 <= 2 * 8, "the ion stages fit in the electrons' prefetch buffers");
     return ions ? sizeof(real) * (size_t)(JW * QN + kIonStages * 5 * kBlock)
-                : sizeof(real) * (size_t)(6 * FN + JW * 3 * QN + 2 * 8 * kBlock);
+                : sizeof(real) * (size_t)(6 * FN + JW * 3 * QN + 2 * (REL ? (DIM == 3 ? 11 : 10) : 8) * kBlock);
 }
 
-template <typename real, int DIM, int S, int TX, int TY, int TZ>
-static void launch_push_t(const PushArgs<real> &a, bool ions, cudaStream_t s)
+template <typename real, int DIM, int S, int TX, int TY, int TZ, bool REL>
+static void launch_push_z(const PushArgs<real> &a, bool ions, cudaStream_t s)
 {
-    const size_t smem = push_smem<real, DIM, S, TX, TY, TZ>(ions);
-    auto k = ions ? ion_kernel<real, DIM, S, TX, TY, TZ> : push_kernel<real, DIM, S, TX, TY, TZ>;
+    const size_t smem = push_smem<real, DIM, S, TX, TY, TZ, REL>(ions);
+    auto k = ions ? ion_kernel<real, DIM, S, TX, TY, TZ, REL> : push_kernel<real, DIM, S, TX, TY, TZ, REL>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int64_t grid = a.g.ntiles < 2147483647LL ? a.g.ntiles : 2147483647LL;
     k<<<(unsigned)grid, kBlock, smem, s>>>(a);
+}
+
+// records in relative form (and their ions) take the REL kernels
+template <typename real, int DIM, int S, int TX, int TY, int TZ>
+static void launch_push_t(const PushArgs<real> &a, bool ions, cudaStream_t s)
+{
+    if (a.rel) launch_push_z<real, DIM, S, TX, TY, TZ, true>(a, ions, s);
+    else launch_push_z<real, DIM, S, TX, TY, TZ, false>(a, ions, s);
 }
 
 template <typename real>
@@ -875,6 +1033,11 @@ __global__ void window_particles_kernel(Geom g, Species<real> in, Species<real> 
             out.uy[d] = in.uy[s];
             out.uz[d] = in.uz[s];
         }
+        if (in.dlx) {
+            out.dlx[d] = in.dlx[s];
+            if (in.dly) out.dly[d] = in.dly[s];
+            out.dlz[d] = in.dlz[s];
+        }
         out.cell[d] = (int32_t)((uint32_t)in.cell[s] - dk);  // keeps the pair bit
         if (in.id) out.id[d] = in.id[s];
     }
@@ -917,6 +1080,11 @@ __global__ void bucket_kernel(BucketArgs<real> a)
             a.dst.uy[d] = a.src.uy[p];
             a.dst.uz[d] = a.src.uz[p];
         }
+        if (a.dst.dlx) {
+            a.dst.dlx[d] = a.src.dlx[p];
+            if (a.dst.dly) a.dst.dly[d] = a.src.dly[p];
+            a.dst.dlz[d] = a.src.dlz[p];
+        }
         a.dst.cell[d] = a.src.cell[p];
         if (a.dst.id) a.dst.id[d] = a.src.id ? a.src.id[p] : 0;
     }
@@ -950,6 +1118,11 @@ __global__ void compact_kernel(CompactArgs<real> a)
                 a.dst.uy[d] = a.src.uy[s];
                 a.dst.uz[d] = a.src.uz[s];
             }
+            if (a.src.dlx) {
+                a.dst.dlx[d] = a.src.dlx[s];
+                if (a.src.dly) a.dst.dly[d] = a.src.dly[s];
+                a.dst.dlz[d] = a.src.dlz[s];
+            }
             a.dst.cell[d] = a.src.cell[s];
             if (a.src.id) a.dst.id[d] = a.src.id[s];
         }
@@ -978,10 +1151,17 @@ __global__ void rho_kernel(Geom g, Species<real> sp, const int *lo, const int *h
             int ci, cj, ck;
             unpack_cell(g, sp.cell[s], ci, cj, ck);
             real wx[S + 1], wy[S + 1], wz[S + 1];
-            const int bx = spline_weights<S>(sp.ox[s], wx) + ci;
-            const int bz = spline_weights<S>(sp.oz[s], wz) + ck;
+            real ox = sp.ox[s], oy = DIM == 3 ? sp.oy[s] : real(0), oz = sp.oz[s];
+            if (sp.dlx) {  // relative form: the offsets in the stored cell
+                int r;
+                ox = rel_actual(ox, sp.dlx[s], r);
+                oz = rel_actual(oz, sp.dlz[s], r);
+                if (DIM == 3) oy = rel_actual(oy, sp.dly[s], r);
+            }
+            const int bx = spline_weights<S>(ox, wx) + ci;
+            const int bz = spline_weights<S>(oz, wz) + ck;
             int by = 0;
-            if (DIM == 3) by = spline_weights<S>(sp.oy[s], wy) + cj;
+            if (DIM == 3) by = spline_weights<S>(oy, wy) + cj;
             const real q = qfac * sp.w[s];
             for (int c = 0; c <= S; ++c) {
                 int k = bz + c;

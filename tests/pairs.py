@@ -18,13 +18,16 @@ def oracle_grid(O, g: dict):
 
 
 def make_pair(O, g: dict, precision: int, track_ids: bool = True, slots_per_cell: float = 16.0, tile=(0, 0, 0),
-              explicit_ions: bool = False):
+              explicit_ions: bool = False, z_relative: int = 0):
+    """GPU context and oracle on the same grid.  z_relative: 0 automatic
+    (relative electron positions from gamma_boost 50 on), 1 on, 2 off."""
     import paper_1011_0917_gb300 as P
     sim = P.Simulation(dim=g["dim"], nx=g["nx"], ny=g.get("ny", 1), nz=g["nz"], dx=g["dx"], dy=g.get("dy", 1.0),
                        dz=g["dz"], cfl=g.get("cfl", 0.99), gamma_boost=g.get("gamma_boost", 1.0),
                        shape_order=g.get("shape_order", 1), filter_passes=g.get("filter_passes", 1),
                        bc_z=g.get("bc_z", 1), precision=precision, seed=g.get("seed", 1),
-                       slots_per_cell=slots_per_cell, track_ids=track_ids, tile=tile, explicit_ions=explicit_ions)
+                       slots_per_cell=slots_per_cell, track_ids=track_ids, tile=tile, explicit_ions=explicit_ions,
+                       z_relative=z_relative)
     o = O.Oracle(oracle_grid(O, g))
     assert sim.dt == o.dt
     return sim, o

@@ -45,18 +45,19 @@ def test_library_targets_sm_103a(P):
 
 def grid(P, **kw):
     d = dict(dim=2, nx=64, ny=1, nz=512, dx=0.5, dy=1.0, dz=1 / 16, cfl=0.99, gamma_boost=1.0, shape_order=1,
-             filter_passes=1, bc_z=1, precision=0, seed=1, slots_per_cell=8.0, tile=(0, 0, 0), track_ids=0)
+             filter_passes=1, bc_z=1, precision=0, seed=1, slots_per_cell=8.0, tile=(0, 0, 0), track_ids=0,
+             z_relative=0)
     d.update(kw)
     return P.GridParams(d["dim"], d["nx"], d["ny"], d["nz"], d["dx"], d["dy"], d["dz"], d["cfl"], d["gamma_boost"],
                         d["shape_order"], d["filter_passes"], d["bc_z"], d["precision"], d["seed"],
-                        d["slots_per_cell"], (C.c_int * 3)(*d["tile"]), d["track_ids"], 0, None)
+                        d["slots_per_cell"], (C.c_int * 3)(*d["tile"]), d["track_ids"], 0, d["z_relative"], None)
 
 
 @pytest.mark.parametrize("bad,status", [
     (dict(cfl=1.0), 5), (dict(cfl=1.2), 5), (dict(cfl=0.0), 1), (dict(dim=4), 1), (dict(nx=0), 1),
     (dict(ny=2), 1), (dict(shape_order=3), 1), (dict(gamma_boost=0.5), 1), (dict(tile=(3, 0, 0)), 1),
     (dict(precision=7), 1), (dict(slots_per_cell=0.0), 1), (dict(filter_passes=-1), 1), (dict(nz=2), 1),
-    (dict(tile=(8, 1, 8)), 1),
+    (dict(tile=(8, 1, 8)), 1), (dict(z_relative=3), 1), (dict(z_relative=-1), 1),
     (dict(dim=3, ny=4, dy=-1.0), 1),
 ])
 def test_init_grid_rejects_invalid_parameters(P, bad, status):
@@ -106,6 +107,31 @@ def test_derived_quantities_match_oracle(P, oracle_mod, kw):
         assert (s.species_bytes[1] > 0) == (g.gamma_boost > 1.0)
     finally:
         P.pic_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_relative_positions_add_departure_columns(P, prec, dim):
+    # z_relative: automatic (on from gamma_boost 50), forced on, forced off;
+    # on, the electron store holds one departure column per axis (x, z in
+    # 2D; x, y, z in 3D) of elem_bytes per slot and side (256-byte aligned);
+    # the ion store is unchanged
+    extra = dict(dim=3, ny=16, nz=64, dy=1.0) if dim == 3 else {}
+
+    def sizes(gam, mode):
+        ctx = P.pic_init_grid(grid(P, gamma_boost=gam, precision=prec, z_relative=mode, **extra))
+        try:
+            return P.pic_query_sizes(ctx)
+        finally:
+            P.pic_destroy(ctx)
+
+    off, on = sizes(130.0, 2), sizes(130.0, 1)
+    col = -(-off.slots[0] * off.elem_bytes // 256) * 256
+    assert on.species_bytes[0] == off.species_bytes[0] + 2 * dim * col
+    assert on.species_bytes[1] == off.species_bytes[1]
+    assert sizes(130.0, 0).species_bytes[0] == on.species_bytes[0]
+    assert sizes(50.0, 0).species_bytes[0] == sizes(50.0, 1).species_bytes[0]
+    assert sizes(30.0, 0).species_bytes[0] == sizes(30.0, 2).species_bytes[0]
 
 
 def test_calls_before_bind_are_rejected(P):

@@ -9,8 +9,10 @@ its ion, which moves with the drift: so each electron here is loaded with an
 ion at the same point, and the electron-ion separation after N steps is held
 against N dt (v - v_d).  (Zero weights: no current, no field, so the
 momenta stay as loaded.)  An error in the drift-relative
-velocity (a dropped term, a wrong sign) shows at once in FP64; FP32 is held
-to the rounding bound of its in-cell offsets.
+velocity (a dropped term, a wrong sign) shows at once in FP64; FP32 with
+absolute in-cell offsets is held to their rounding bound, and FP32 with
+relative positions (the departure from the reference path in its own word)
+to the relative precision of the departure itself.
 """
 import math
 
@@ -27,11 +29,12 @@ DU = [(0.0, 0.0, 1e-3), (0.0, 0.0, -1e-3), (0.0, 0.0, 3e-3), (0.0, 0.0, 1e-2), (
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
-def test_separation_from_the_drift(prec):
+@pytest.mark.parametrize("rel", [2, 1])
+def test_separation_from_the_drift(prec, rel):
     import paper_1011_0917_gb300 as P
     gam = 13.0
     sim = P.Simulation(dim=2, nx=16, nz=512, dx=1.0, dz=1 / 32, gamma_boost=gam, filter_passes=1,
-                       precision=prec, track_ids=True, explicit_ions=True, slots_per_cell=4.0)
+                       precision=prec, track_ids=True, explicit_ions=True, slots_per_cell=4.0, z_relative=rel)
     beta = math.sqrt(1 - 1 / gam ** 2)
     # the drift as the working precision holds it (the ions move with it)
     U = -gam * beta if prec == FP64 else float(np.float32(-gam * beta))
@@ -71,9 +74,22 @@ def test_separation_from_the_drift(prec):
         # in-cell offset: 2^-24 cell per step bounds the error (FP32; the
         # rounding is systematic for a constant velocity, so the bound is
         # linear in the steps).  FP64 resolves the formula itself.
-        bound = 1e-9 * abs(dz_exact) if prec == FP64 else nsteps * 2.0 ** -24 * hz + 1e-6 * abs(dz_exact)
+        # Relative positions: the electron's reference is its ion's path, so
+        # the separation is the departure alone, summed in its own FP32 word
+        # (at most ~ulp of the sum per step: 400 x 6e-8 relative).
+        if prec == FP64:
+            bound = 1e-9 * abs(dz_exact)
+        elif rel == 1:
+            bound = 4e-5 * abs(dz_exact)
+        else:
+            bound = nsteps * 2.0 ** -24 * hz + 1e-6 * abs(dz_exact)
         assert abs(dz - dz_exact) <= bound, (i, dz, dz_exact)
         if DU[i][0] != 0.0:  # one rounding of the offset per step (hx = 1)
-            bx = 1e-9 * abs(dx_exact) if prec == FP64 else nsteps * 2.0 ** -25 + 1e-6 * abs(dx_exact)
+            if prec == FP64:
+                bx = 1e-9 * abs(dx_exact)
+            elif rel == 1:
+                bx = 4e-5 * abs(dx_exact)
+            else:
+                bx = nsteps * 2.0 ** -25 + 1e-6 * abs(dx_exact)
             assert abs(dx - dx_exact) <= bx, (i, dx, dx_exact)
     sim.close()

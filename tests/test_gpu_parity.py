@@ -10,7 +10,10 @@ Full-step windows compare the E and B fields as vectors, and each component
 that carries at least 10% of its field's norm on its own (see
 pairs.vector_errors): a component the physics leaves at zero holds only
 round-off on both sides.
-Grids are chosen to span several tiles with ragged last tiles.
+Grids are chosen to span several tiles with ragged last tiles.  Cases marked
+"rel" run the electrons in relative form (reference path + departure, the
+currents in FP64; include/pic.h), which the library selects on its own from
+gamma_boost 50 on.
 """
 import math
 
@@ -113,10 +116,12 @@ def _compare_particles(sim, o, sp, prec, pos_tol=None, u_tol=None):
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
-@pytest.mark.parametrize("g,shape,bc", [(G2, 1, 1), (G2, 2, 1), (G2, 1, 0), (G3, 1, 1), (G3, 2, 0)])
-def test_push_deposit_phase(O, g, shape, bc, prec):
+@pytest.mark.parametrize("g,shape,bc,rel", [(G2, 1, 1, 2), (G2, 2, 1, 2), (G2, 1, 0, 2), (G3, 1, 1, 2),
+                                            (G3, 2, 0, 2), (G2, 2, 1, 1), (G2, 1, 0, 1), (G3, 1, 1, 1),
+                                            (G3, 2, 0, 1)])
+def test_push_deposit_phase(O, g, shape, bc, rel, prec):
     g = dict(g, shape_order=shape, bc_z=bc)
-    sim, o = make_pair(O, g, prec)
+    sim, o = make_pair(O, g, prec, z_relative=rel)
     n = 3000 if g["dim"] == 2 else 6000
     st = _random_state(o, g, n, seed=21 + shape)
     ids = np.arange(n, dtype=np.int64) * 7 + 3
@@ -132,10 +137,10 @@ def test_push_deposit_phase(O, g, shape, bc, prec):
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
-@pytest.mark.parametrize("g,shape", [(G2, 1), (G2, 2), (G3, 1)])
-def test_drifting_ion_phase(O, g, shape, prec):
+@pytest.mark.parametrize("g,shape,rel", [(G2, 1, 2), (G2, 2, 2), (G3, 1, 2), (G2, 2, 1), (G3, 1, 1)])
+def test_drifting_ion_phase(O, g, shape, rel, prec):
     g = dict(g, shape_order=shape, gamma_boost=5.0)
-    sim, o = make_pair(O, g, prec)
+    sim, o = make_pair(O, g, prec, z_relative=rel)
     n = 2000
     st = _random_state(o, g, n, seed=31)
     uz0 = -(5.0 * o.beta)
@@ -187,10 +192,10 @@ def test_plasma_load_matches_lattice(O, case, explicit, prec):
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
-@pytest.mark.parametrize("explicit", [False, True])
-def test_injection_matches_oracle(O, explicit, prec):
+@pytest.mark.parametrize("explicit,rel", [(False, 2), (True, 2), (False, 1)])
+def test_injection_matches_oracle(O, explicit, rel, prec):
     g = dict(dim=2, nx=12, nz=120, dx=1.0, dz=1 / 16, gamma_boost=5.0, filter_passes=1, seed=13)
-    sim, o = make_pair(O, g, prec, explicit_ions=explicit)
+    sim, o = make_pair(O, g, prec, explicit_ions=explicit, z_relative=rel)
     zs = 5.0 * (o.Lz - 2.0)
     p = dict(ne=0.002, z_start=zs, z_end=zs + 5.0 * 40.0, ramp=1.0, ppc=(2, 1, 2), jitter=0.1, ions=1)
     _plasma_both(sim, o, O, p)
@@ -208,8 +213,8 @@ def test_injection_matches_oracle(O, explicit, prec):
     _compare_particles(sim, o, 1, prec, pos_tol=tol)
 
 
-def _run_steps_parity(O, g, p, laser, nsteps, prec, slots=16.0, explicit=False):
-    sim, o = make_pair(O, g, prec, slots_per_cell=slots, explicit_ions=explicit)
+def _run_steps_parity(O, g, p, laser, nsteps, prec, slots=16.0, explicit=False, rel=0):
+    sim, o = make_pair(O, g, prec, slots_per_cell=slots, explicit_ions=explicit, z_relative=rel)
     if p is not None:
         _plasma_both(sim, o, O, p)
     if laser is not None:
@@ -267,8 +272,8 @@ def test_c0_window_laser_in_plasma(O, prec):
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
-@pytest.mark.parametrize("explicit", [False, True])
-def test_boosted_2d_50_steps_with_injection(O, explicit, prec):
+@pytest.mark.parametrize("explicit,rel", [(False, 0), (True, 0), (False, 1), (True, 1)])
+def test_boosted_2d_50_steps_with_injection(O, explicit, rel, prec):
     # gamma = 13, plasma 10 cells from the antenna streaming in through z = Lz;
     # the laser meets the plasma within the window
     g = dict(dim=2, nx=32, nz=256, dx=1.0, dz=1 / 32, gamma_boost=13.0, filter_passes=2, seed=17)
@@ -276,7 +281,7 @@ def test_boosted_2d_50_steps_with_injection(O, explicit, prec):
     hz = (1 / 32) * 13 * (1 + beta)
     p = dict(ne=0.004, z_start=13 * 10 * hz, z_end=13 * 600 * hz, ramp=2.0, ppc=(2, 1, 2), jitter=0.1, ions=1)
     laser = dict(a0=4.0, waist=8.0, fwhm=2.0, t_peak=0.5)
-    sim, o = _run_steps_parity(O, g, p, laser, 50, prec, explicit=explicit)
+    sim, o = _run_steps_parity(O, g, p, laser, 50, prec, explicit=explicit, rel=rel)
     err = vector_errors(sim, o)
     assert max(err.values()) < TOL50[prec], err
     d = sim.diagnostics()
@@ -288,90 +293,180 @@ def test_boosted_2d_50_steps_with_injection(O, explicit, prec):
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
-@pytest.mark.parametrize("explicit", [False, True])
-def test_3d_boosted_30_steps(O, explicit, prec):
+@pytest.mark.parametrize("explicit,rel", [(False, 0), (True, 0), (False, 1)])
+def test_3d_boosted_30_steps(O, explicit, rel, prec):
     g = dict(dim=3, nx=16, ny=16, nz=48, dx=1.0, dy=1.0, dz=1 / 32, gamma_boost=13.0, filter_passes=2, seed=19)
     beta = math.sqrt(1 - 1 / 169.0)
     hz = (1 / 32) * 13 * (1 + beta)
     p = dict(ne=0.004, z_start=13 * 6 * hz, z_end=13 * 200 * hz, ramp=2.0, ppc=(2, 2, 2), jitter=0.1, ions=1)
     laser = dict(a0=4.0, waist=4.0, fwhm=2.0, t_peak=0.5)
-    sim, o = _run_steps_parity(O, g, p, laser, 30, prec, explicit=explicit)
+    sim, o = _run_steps_parity(O, g, p, laser, 30, prec, explicit=explicit, rel=rel)
     err = vector_errors(sim, o)
     assert max(err.values()) < TOL50[prec], err
 
 
-@pytest.mark.parametrize("prec", [FP64, FP32])
-def test_quadratic_high_boost_small(O, prec):
+# the wake on its own: at gamma = 130 the oracle's own FP64 wake carries
+# ~1e-8 (the species' currents it subtracts are 1/(2 gamma^2) ~ 3e-8 of the
+# plasma response apart), so the FP64 build is held to 1e-7 there
+TOL_WAKE = {FP32: 1e-3, FP64: 1e-7}
+
+
+def _c3_small_window(O, a0, prec, explicit):
     # the gamma = 130, quadratic-shape, 4-pass stage on a 4x coarser grid; the
-    # plasma starts 3 cells from the antenna so the laser reaches it, and the
-    # drive is strong enough (a0 = 20) that the plasma response within the
-    # window is far above the FP32 resolution of in-cell offsets (6e-8 cell)
+    # plasma starts 3 cells from the antenna so the laser reaches it
     g = dict(dim=2, nx=32, nz=200, dx=4.0, dz=4 / 32, gamma_boost=130.0, shape_order=2, filter_passes=4, seed=23)
     beta = math.sqrt(1 - 1 / 130.0 ** 2)
     hz = (4 / 32) * 130 * (1 + beta)
     p = dict(ne=5.7e-5, z_start=130 * 3 * hz, z_end=130 * 400 * hz, ramp=5.0, ppc=(2, 1, 2), jitter=0.1, ions=1)
-    laser = dict(a0=20.0, waist=20.0, fwhm=4.0, t_peak=0.2)
-    sim, o = _run_steps_parity(O, g, p, laser, 50, prec)
-    err = vector_errors(sim, o)
-    # FP32 floor at gamma = 130: a momentum change du moves v_z by ~du/gamma^3
-    # (~4.5e-7 du) while FP32 resolves v_z ~ 1 to 6e-8, so the electron-ion
-    # current difference the plasma response is made of carries ~10% FP32
-    # round-off; in this window that is ~1e-4 of the field (measured 1.06e-4)
-    tol = 2e-4 if prec == FP32 else TOL50[prec]
-    assert max(err.values()) < tol, err
+    laser = dict(a0=a0, waist=20.0, fwhm=4.0, t_peak=0.2)
+    return _run_steps_parity(O, g, p, laser, 50, prec, explicit=explicit)
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
-def test_c3_stage_a0_1_5(O, prec):
+def test_quadratic_high_boost_small(O, prec):
+    # a strong drive (a0 = 20): relative electron positions are selected
+    # automatically at this boost
+    sim, o = _c3_small_window(O, 20.0, prec, False)
+    err = vector_errors(sim, o)
+    assert max(err.values()) < TOL50[prec], err
+    wake = field_errors(sim, o, ("Ex", "Ez", "By"))
+    assert max(wake.values()) < TOL_WAKE[prec], wake
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+@pytest.mark.parametrize("explicit", [False, True])
+def test_c3_stage_a0_1_5(O, explicit, prec):
     # the gamma = 130 stage at its own drive (a0 = 1.5) on the 4x coarser grid:
-    # the FP64 build meets the 1e-10 bar; in FP32 the laser fields (Ey, Bx, Bz)
-    # agree to 1e-5 while the plasma's longitudinal response is below the FP32
-    # resolution of v_z at this boost (du moves v_z by ~du / gamma^3), so the E
-    # vector is held to the measured floor (1.1e-3 / 1.3e-3 with / without
-    # electron-ion pairs) with a 2x margin
+    # the plasma's wake current is ~3e-8 of either species' current in this
+    # frame; with electrons in relative form and the currents formed in FP64,
+    # FP32 meets the same bar as everywhere else, and the wake fields (Ex, Ez,
+    # By: about a thousandth of the laser's) are checked on their own
+    sim, o = _c3_small_window(O, 1.5, prec, explicit)
+    err = vector_errors(sim, o)
+    assert max(err.values()) < TOL50[prec], err
+    wake = field_errors(sim, o, ("Ex", "Ez"))
+    assert np.abs(o.field("Ez")).max() > 1e-3 * np.abs(o.field("Ey")).max()  # a wake is there
+    assert max(wake.values()) < TOL_WAKE[prec] * (10 if prec == FP32 else 1), wake
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_c3_stage_absolute_positions_fall_short(O, prec):
+    # the same window with absolute FP32 offsets and FP32 currents (z_relative
+    # = 2): the wake drowns in rounding (measured: E as a vector 1e-3, Ez on
+    # its own ~70%); FP64 is unaffected
     g = dict(dim=2, nx=32, nz=200, dx=4.0, dz=4 / 32, gamma_boost=130.0, shape_order=2, filter_passes=4, seed=23)
     beta = math.sqrt(1 - 1 / 130.0 ** 2)
     hz = (4 / 32) * 130 * (1 + beta)
     p = dict(ne=5.7e-5, z_start=130 * 3 * hz, z_end=130 * 400 * hz, ramp=5.0, ppc=(2, 1, 2), jitter=0.1, ions=1)
     laser = dict(a0=1.5, waist=20.0, fwhm=4.0, t_peak=0.2)
-    sim, o = _run_steps_parity(O, g, p, laser, 50, prec)
+    sim, o = _run_steps_parity(O, g, p, laser, 50, prec, rel=2)
     err = vector_errors(sim, o)
     if prec == FP64:
         assert max(err.values()) < TOL50[prec], err
     else:
-        laser_f = field_errors(sim, o, ("Ey", "Bx", "Bz"))
-        assert max(laser_f.values()) < 1e-5, laser_f
-        assert err["E"] < 3e-3 and err["B"] < 1e-3, err
+        assert err["E"] > 1e-4, err  # the reason the relative form exists
+
+
+def test_c2_slab_at_bench_settings(O):
+    # the benchmarked 3D gamma = 13 stage (256 x 256 x 1024 in the bench) on a
+    # 32 x 32 x 64 slab with the bench's own settings: FP32, 10 slots per
+    # cell, electron-ion pairs, the stage's plasma (filling the box and
+    # streaming in) and laser (a0 = 1, waist 20, FWHM 10), its peak emitted
+    # early so that it drives the plasma within the window; compared after 40
+    # and after 60 steps, the wake field Ez also on its own
+    st = W.stage("c2")
+    g = dict(st.grid, nx=32, ny=32, nz=64)
+    laser = dict(st.laser, t_peak=1.0)
+    sim, o = make_pair(O, g, FP32, slots_per_cell=10.0)
+    _plasma_both(sim, o, O, st.plasma)
+    sim.launch_laser(laser["a0"], laser["waist"], laser["fwhm"], 0.0, laser["t_peak"], laser["pol"])
+    o.set_laser(O.LaserParams(a0=laser["a0"], waist=laser["waist"], fwhm=laser["fwhm"], z_antenna=0.0,
+                              t_peak=laser["t_peak"], pol=laser["pol"]))
+    for nsteps in (40, 20):
+        sim.step(nsteps)
+        o.step(nsteps)
+        err = vector_errors(sim, o)
+        assert max(err.values()) < TOL50[FP32], err
+        assert field_errors(sim, o, ("Ez",))["Ez"] < TOL50[FP32]
+    assert np.abs(o.field("Ez")).max() > 1e-3
+    d = sim.diagnostics()
+    assert d.n_particles[0] == o.num(0) and d.n_particles[1] == o.num(1)
+    assert 0 < d.n_paired < d.n_particles[0]
+
+
+class _FieldView:  # oracle-shaped view of GPU fields for the residual helpers
+    def __init__(self, f, hx, hy, hz):
+        self.f, self.hx, self.hy, self.hz = f, hx, hy, hz
+
+    def field(self, c):
+        return self.f[c]
+
+
+def _residual(sim, o, dim, npass, bc_z):
+    """div E - 2 pi F(rho) on the GPU's state, planes 6..nz-6 (away from the
+    antenna sheet, the Mur ends and the plasma entering through z = Lz)"""
+    from test_oracle_physics import _div_e, _filtered
+    f = {c: t.double().cpu().numpy() for c, t in sim.fields().items()}
+    rho = sim.rho().double().cpu().numpy()
+    v = _FieldView(f, o.hx, o.hy, o.hz)
+    return _div_e(v, dim)[6:-6] - 2 * math.pi * _filtered(rho, npass, dim, bc_z)[6:-6]
 
 
 def test_continuity_residual_fp32(O):
     # div E - 2 pi F(rho) stays constant; F = the same binomial passes on rho
-    from test_oracle_physics import _div_e, _filtered
+    from test_oracle_physics import _filtered
     g = dict(dim=2, nx=32, nz=96, dx=0.5, dz=0.125, filter_passes=2, seed=29)
     sim, o = make_pair(O, g, FP32)
-    p = dict(ne=0.02, z_start=2.0, z_end=9.0, ramp=0.5, ppc=(2, 1, 2), jitter=0.1, ions=1)
     st = W.random_particles(20000, (o.Lx, 1.0, 7.0), seed=30, u_scale=0.3)
     st[2] += 2.5
     st[6] = 0.02 * o.hx * o.hz / 4
     sim.load_particles(0, st, np.arange(st.shape[1]))
-
-    class View:  # oracle-shaped view of the GPU fields for the residual helpers
-        def __init__(self, f):
-            self.f, self.hx, self.hz = f, o.hx, o.hz
-
-        def field(self, c):
-            return self.f[c]
-
-    def resid():
-        f = {c: t.double().cpu().numpy() for c, t in sim.fields().items()}
-        rho = sim.rho().double().cpu().numpy()
-        return _div_e(View(f), 2)[6:-6] - 2 * math.pi * _filtered(rho, 2, 2, 1)[6:-6], rho
-
-    r0, rho0 = resid()
+    r0 = _residual(sim, o, 2, 2, 1)
+    rho0 = sim.rho().double().cpu().numpy()
     sim.step(30)
-    r1, _ = resid()
+    r1 = _residual(sim, o, 2, 2, 1)
     scale = 2 * math.pi * np.abs(_filtered(rho0, 2, 2, 1)).max()
     assert np.abs(r1 - r0).max() < 1e-5 * scale, np.abs(r1 - r0).max() / scale
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+@pytest.mark.parametrize("dim,shape,explicit,rel", [(2, 1, False, 0), (2, 2, False, 0), (2, 1, True, 0),
+                                                    (3, 1, False, 0), (3, 1, True, 0), (3, 2, False, 0),
+                                                    (2, 2, False, 1), (3, 1, False, 1)])
+def test_continuity_residual_boosted(O, dim, shape, explicit, rel, prec):
+    # the boosted frame (gamma = 13): plasma loaded and injected with drifting
+    # ions (paired or explicit records), a laser releasing pairs, CIC and
+    # quadratic shapes, 2D and 3D, absolute and relative electron positions:
+    # the residual's change over 30 steps, relative to the plasma's charge
+    # density 2 pi gamma n, stays at round-off (1e-5 FP32, 1e-13 FP64)
+    gam = 13.0
+    beta = math.sqrt(1 - 1 / gam ** 2)
+    dzl = 1 / 32
+    hz = dzl * gam * (1 + beta)
+    if dim == 2:
+        g = dict(dim=2, nx=32, nz=96, dx=1.0, dz=dzl, gamma_boost=gam, filter_passes=2, shape_order=shape, seed=41)
+        laser = dict(a0=4.0, waist=8.0, fwhm=2.0, t_peak=0.5, pol=1)
+    else:
+        g = dict(dim=3, nx=16, ny=16, nz=48, dx=1.0, dy=1.0, dz=dzl, gamma_boost=gam, filter_passes=2,
+                 shape_order=shape, seed=42)
+        laser = dict(a0=4.0, waist=4.0, fwhm=2.0, t_peak=0.5, pol=0)
+    ne = 0.004
+    p = dict(ne=ne, z_start=gam * 8 * hz, z_end=gam * 2000 * hz, ramp=0.0, ppc=(2, 2, 2) if dim == 3 else (2, 1, 2),
+             jitter=0.1, ions=1)
+    sim, o = make_pair(O, g, prec, explicit_ions=explicit, z_relative=rel)
+    _plasma_both(sim, o, O, p)
+    sim.launch_laser(laser["a0"], laser["waist"], laser["fwhm"], 0.0, laser["t_peak"], laser["pol"])
+    sim.step(5)
+    r0 = _residual(sim, o, dim, 2, 1)
+    sim.step(30)
+    r1 = _residual(sim, o, dim, 2, 1)
+    d = sim.diagnostics()
+    assert d.n_particles[0] > 1000
+    if not explicit:
+        assert d.n_paired < d.n_particles[0]  # the laser released pairs
+    scale = 2 * math.pi * gam * ne
+    tol = 1e-5 if prec == FP32 else 1e-13
+    assert np.abs(r1 - r0).max() < tol * scale, np.abs(r1 - r0).max() / scale
 
 
 def test_capacity_overflow_is_reported(O):
@@ -383,18 +478,18 @@ def test_capacity_overflow_is_reported(O):
     assert e.value.status == P.PIC_ERR_CAPACITY
 
 
-@pytest.mark.parametrize("on_device", [False, True])
-def test_state_roundtrip(O, on_device):
+@pytest.mark.parametrize("on_device,rel", [(False, 0), (True, 0), (True, 1)])
+def test_state_roundtrip(O, on_device, rel):
     import torch
     import paper_1011_0917_gb300 as P
     g = dict(dim=2, nx=32, nz=256, dx=1.0, dz=1 / 32, gamma_boost=13.0, filter_passes=2, seed=17)
     p = dict(ne=0.001, z_start=13 * 30 * 0.81, z_end=13 * 600 * 0.81, ramp=2.0, ppc=(2, 1, 2), jitter=0.1, ions=1)
     laser = dict(a0=2.0, waist=8.0, fwhm=2.0, t_peak=0.5)
-    sim, _ = _run_steps_parity(O, g, p, laser, 20, FP64)
+    sim, _ = _run_steps_parity(O, g, p, laser, 20, FP64, rel=rel)
     nb = P.pic_state_bytes(sim.ctx)
     buf = torch.empty(nb, dtype=torch.uint8, device="cuda" if on_device else "cpu")
     P.pic_get_state(sim.ctx, buf.data_ptr(), nb, on_device)
-    sim2, _ = make_pair(O, g, FP64)
+    sim2, _ = make_pair(O, g, FP64, z_relative=rel)
     sim2.load_plasma(p["ne"], p["z_start"], p["z_end"], p["ramp"], p["ppc"], p["jitter"], (), 1)
     P.pic_set_state(sim2.ctx, buf.data_ptr(), nb, on_device)
     sim.step(10)

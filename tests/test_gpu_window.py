@@ -22,8 +22,8 @@ def O():
     return O
 
 
-def _both(O, g, p, laser, window, nsteps, prec):
-    sim, o = make_pair(O, g, prec)
+def _both(O, g, p, laser, window, nsteps, prec, rel=0):
+    sim, o = make_pair(O, g, prec, z_relative=rel)
     sim.set_moving_window(*window)
     o.set_window(*window)
     if p is not None:
@@ -63,7 +63,8 @@ def test_window_lab_frame_2d(O, prec):
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
-def test_window_boosted_2d(O, prec):
+@pytest.mark.parametrize("rel", [0, 1])
+def test_window_boosted_2d(O, prec, rel):
     # gamma = 5 with the window at the laser's group velocity seen in that
     # frame (v_g' ~ 0.74 for gamma_g ~ 13); plasma drifting in at -beta
     g = dict(dim=2, nx=24, nz=128, dx=1.0, dz=1 / 32, gamma_boost=5.0, filter_passes=1, seed=47)
@@ -71,7 +72,7 @@ def test_window_boosted_2d(O, prec):
     hz = (1 / 32) * 5 * (1 + beta)
     p = dict(ne=0.004, z_start=5 * 8 * hz, z_end=5 * 900 * hz, ramp=1.0, ppc=(2, 1, 2), jitter=0.1, ions=1)
     laser = dict(a0=2.0, waist=6.0, fwhm=2.0, t_peak=0.5)
-    sim, o = _both(O, g, p, laser, (0.74, 3.0, 16), 120, prec)
+    sim, o = _both(O, g, p, laser, (0.74, 3.0, 16), 120, prec, rel)
     assert o.z_window > 0
     _check(sim, o, prec)
 

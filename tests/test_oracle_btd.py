@@ -119,3 +119,71 @@ def test_lab_and_boosted_runs_of_one_pulse_agree(oracle_mod):
     # and the pulse is not displaced: a one-cell shift is far worse
     worse = np.linalg.norm(a - ey[k + 1]) / np.linalg.norm(ey[k + 1])
     assert worse > 0.1
+
+
+def _wake_lab_vs_boost(O, gam, dzl=1 / 32, ne=0.01, zs=4.0, a0=1.0, fwhm=5.0, ahead=12.0):
+    """A plane laser pulse (a0, intensity FWHM `fwhm`) driving a wake in a
+    cold plasma at rest in the lab from z = zs (2 lambda0 ramp): the on-axis
+    Ez(Z) of a lab-frame run once the pulse peak is `ahead` lambda0 into the
+    plasma, and the same lab-frame line from a run boosted to `gam`, read off
+    its back-transformed snapshot.  The boosted run's antenna moves in the lab
+    (it is at rest in the boosted frame), so its plasma is placed `delta`
+    further along (the pulse is emitted in vacuum, the plasma enters the box
+    through z = Lz) and the lab events (Z, T) of the first run correspond to
+    (Z + delta, T + delta) of the second: a plane pulse in vacuum and a
+    plasma at rest are both unchanged by that shift."""
+    tau = fwhm / math.sqrt(2 * math.log(2))
+    lab = O.Oracle(O.GridParams(dim=2, nx=4, nz=int(round((zs + ahead + 8) / dzl)), dx=1.0, dz=dzl, npass=1,
+                                bc_z=1, seed=5))
+    lab.load_plasma(O.PlasmaParams(ne=ne, z_start=zs, z_end=zs + 400, ramp=2.0, ppc=(2, 1, 2), jitter=0.0, ions=1))
+    lab.set_laser(O.LaserParams(a0=a0, waist=1e9, fwhm=fwhm, pol=1))
+    lab.step(int(math.ceil((zs + ahead + 3 * tau) / lab.dt)))
+    T_lab = lab.t
+    ez_lab = lab.field("Ez")[:, 0, 2]
+    z_ez = (np.arange(len(ez_lab)) + 0.5) * lab.hz      # Ez sits at k + 1/2
+    beta = math.sqrt(1 - 1 / gam ** 2)
+    # the lab events to compare must lie ahead of the boosted antenna
+    # (z' > 0): (1 - beta) delta > beta T_lab - zs, with a margin
+    delta = math.ceil((beta * T_lab - zs + 4) / (1 - beta))
+    Ts, Z0, span = T_lab + delta, zs + delta - 2.0, ahead + 6.0
+    nzl = int(round(span / dzl))
+    hz = dzl * gam * (1 + beta)
+    nz = int(math.ceil((gam * (Z0 + span - beta * Ts) + 20) / hz))
+    bst = O.Oracle(O.GridParams(dim=2, nx=4, nz=nz, dx=1.0, dz=dzl, gamma_boost=gam, npass=1, bc_z=1, seed=5))
+    assert (zs + delta) / gam > bst.Lz  # all of the plasma is injected
+    bst.load_plasma(O.PlasmaParams(ne=ne, z_start=zs + delta, z_end=zs + delta + 400, ramp=2.0, ppc=(2, 1, 2),
+                                   jitter=0.0, ions=1))
+    bst.set_laser(O.LaserParams(a0=a0, waist=1e9, fwhm=fwhm, pol=1))
+    bst.btd_setup(O.BtdParams(nsnap=1, t0=Ts, dt=1.0, z0=Z0, dz=dzl, nz=nzl, plane=0))
+    bst.step(int(math.ceil((gam * (Ts - beta * Z0) + 2 * bst.dt) / bst.dt)))
+    f, filled = bst.btd_snapshot(0)
+    Z = Z0 + np.arange(nzl) * dzl - delta               # back in the first run's coordinates
+    ez_b = f["Ez"][:, 0]
+    ez_l = np.interp(Z, z_ez, ez_lab)
+    wake = filled & (Z >= zs) & (Z <= zs + ahead)       # behind the pulse peak
+    return Z, ez_l, ez_b, wake, filled
+
+
+@pytest.mark.parametrize("gam", [2.0, 3.0, 5.0])
+def test_boosted_wake_back_transformed_matches_lab_wake(oracle_mod, gam):
+    # The paper's central claim (section "Effect of the hyperbolic rotation in
+    # Minkowski space", Fig. 2): a stage computed in a boosted frame and
+    # transformed back to the lab reproduces the lab-frame computation.  Here
+    # with plasma: the peak wake field behind a plane a0 = 1 pulse in an
+    # n = 0.01 n_c plasma, computed at gamma = 1 and at gamma = 2, 3, 5
+    # (plasma contracted and drifting at -beta, injected through z = Lz,
+    # drifting ions, Doppler-shifted antenna, lab snapshot), agrees within 5%
+    # at the same lab position.  At 32 cells per wavelength the measured gap
+    # is 2.2%, 2.6%, 4.0% (it is discretisation: 7%, 8%, 19% at 16 cells); a
+    # wrong boosted density, drift or injection time moves or rescales the
+    # wake far beyond this.
+    O = oracle_mod
+    Z, ez_l, ez_b, wake, filled = _wake_lab_vs_boost(O, gam)
+    assert filled.mean() > 0.95
+    assert wake.sum() > 300
+    il = int(np.argmax(np.abs(ez_l * wake)))
+    ib = int(np.argmax(np.abs(ez_b * wake)))
+    assert abs(ez_l[il]) > 0.02                          # a nonlinear wake is there
+    assert abs(abs(ez_b[ib]) - abs(ez_l[il])) / abs(ez_l[il]) < 0.05
+    assert np.sign(ez_b[ib]) == np.sign(ez_l[il])
+    assert abs(Z[ib] - Z[il]) <= 2 * (1 / 32)            # the same lab position (two lab cells)
