@@ -247,11 +247,26 @@ pic_status pic_step_phases(pic_ctx *ctx, unsigned mask);
 
 /* --------------------------------------------------------------- output */
 
+/* Frames of pic_get_fields. */
+enum { PIC_FRAME_BOOST = 0, PIC_FRAME_LAB = 1 };
+
 /* Copies the components selected by mask, in component order, each as
    (nz+1) x ny x nx elements of elem_bytes in [k][j][i] order (the native
    layout; the plane k = nz of Ez, Bx, By, Jz is unused and zero).  dst may be
-   host (dst_is_device = 0) or device memory; dst_bytes must hold them all. */
-pic_status pic_get_fields(pic_ctx *ctx, unsigned mask, void *dst, size_t dst_bytes,
+   host (dst_is_device = 0) or device memory; dst_bytes must hold them all.
+   frame PIC_FRAME_BOOST: the simulation-frame fields as stored.
+   frame PIC_FRAME_LAB: E and B as the laboratory sees them on the same grid
+   nodes at the current simulation time (the inverse of the boost, the
+   paper's hyperbolic rotation; section "Effect of the hyperbolic rotation in
+   Minkowski space"): Ex = gamma (Ex' + beta By'), Ey = gamma (Ey' - beta Bx'),
+   Ez = Ez', Bx = gamma (Bx' - beta Ey'), By = gamma (By' + beta Ex'),
+   Bz = Bz', in FP64, each component at its own Yee position and the partner
+   it mixes with (half a cell away in z) taken as the mean of its two planes
+   around it (the nearer plane alone at an absorbing z end; planes wrap when
+   z is periodic).  Only E and B (mask bits 0..5; J bits: PIC_ERR_ARG); a
+   device dst must be aligned to elem_bytes.  With gamma_boost = 1 both
+   frames are the same.  For snapshots at a fixed lab time use pic_btd_*. */
+pic_status pic_get_fields(pic_ctx *ctx, unsigned mask, int frame, void *dst, size_t dst_bytes,
                           int dst_is_device);
 
 /* Overwrites the selected components from src, same layout as pic_get_fields. */
@@ -475,6 +490,20 @@ pic_status pic_profile_read(pic_ctx *ctx, double ms[8], int64_t calls[8], int64_
    pic_last_error detail. */
 pic_status pic_filter_current_noalloc(int dim, int nx, int ny, int nz, int bc_z, int passes, int precision,
                                       void *jx, void *jy, void *jz, void *stream);
+
+/* ------------------------------------------------------- bounded waits */
+
+/* Kernels that stage data with the tensor memory accelerator wait on
+   mbarriers; no such wait spins without limit: it gives up after a time
+   budget, the kernel stops issuing work, and the step reports
+   PIC_ERR_TIMEOUT instead of hanging.  This call checks that path on the
+   device: one CTA waits on an mbarrier that expects one arrival, which the
+   kernel makes (arrive = 1: PIC_OK) or withholds (arrive = 0: nothing ever
+   completes the phase, the wait runs out after budget_ms and the call
+   returns PIC_ERR_TIMEOUT).  No fault is raised either way.  budget_ms in
+   (0, 10000], else PIC_ERR_ARG; PIC_ERR_CUDA if a CUDA call fails.  The
+   paper has no counterpart: this is a check of the library's own waits. */
+pic_status pic_wait_check(int arrive, double budget_ms, void *stream);
 
 /* ------------------------------------------------------------------ misc */
 

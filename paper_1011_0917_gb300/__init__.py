@@ -25,7 +25,8 @@ __all__ = [
     "pic_profile_read", "pic_filter_current_noalloc", "PIC_NOALLOC_MAX_NODES", "BtdParams", "pic_btd_bytes",
     "pic_btd_setup", "pic_btd_get", "pic_set_moving_window", "pic_batch_create", "pic_batch_step",
     "pic_batch_destroy", "Simulation", "Batch", "library_path", "AdjointParams", "pic_adjoint_bytes",
-    "pic_adjoint_forward", "pic_adjoint_backward", "StageGradient", "pic_batch_set_graph",
+    "pic_adjoint_forward", "pic_adjoint_backward", "StageGradient", "pic_batch_set_graph", "pic_wait_check",
+    "PIC_FRAME_BOOST", "PIC_FRAME_LAB",
 ]
 
 PIC_OK, PIC_ERR_ARG, PIC_ERR_STATE, PIC_ERR_CUDA = 0, 1, 2, 3
@@ -34,6 +35,7 @@ PIC_BC_PERIODIC, PIC_BC_MUR = 0, 1
 PIC_FP32, PIC_FP64 = 0, 1
 PIC_ELECTRONS, PIC_IONS = 0, 1
 PIC_POL_X, PIC_POL_Y = 0, 1
+PIC_FRAME_BOOST, PIC_FRAME_LAB = 0, 1
 COMPONENTS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx", "Jy", "Jz")
 PH_ZERO_J, PH_PUSH, PH_IONS, PH_ANTENNA = 1, 2, 4, 8
 PH_FILTER, PH_YEE, PH_INJECT, PH_TIME = 16, 32, 64, 128
@@ -119,7 +121,7 @@ def _load():
         "pic_step": (S, [P, I]),
         "pic_step_async": (S, [P, I]),
         "pic_step_phases": (S, [P, U]),
-        "pic_get_fields": (S, [P, U, P, C.c_size_t, I]),
+        "pic_get_fields": (S, [P, U, I, P, C.c_size_t, I]),
         "pic_set_fields": (S, [P, U, P, C.c_size_t, I]),
         "pic_get_axis": (S, [P, I, P, C.c_size_t, I]),
         "pic_get_particles": (S, [P, I, C.POINTER(C.c_double), C.c_size_t, C.POINTER(C.c_int64),
@@ -146,6 +148,7 @@ def _load():
         "pic_adjoint_bytes": (S, [P, C.POINTER(AdjointParams), C.POINTER(C.c_size_t)]),
         "pic_adjoint_forward": (S, [P, C.POINTER(AdjointParams), P, C.c_size_t, P]),
         "pic_adjoint_backward": (S, [P, P, C.POINTER(C.c_double)]),
+        "pic_wait_check": (S, [I, C.c_double, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -217,8 +220,8 @@ def pic_step_phases(ctx, mask: int):
     _check(ctx, _load().pic_step_phases(ctx, int(mask)))
 
 
-def pic_get_fields(ctx, mask: int, dst_ptr: int, dst_bytes: int, dst_is_device: bool):
-    _check(ctx, _load().pic_get_fields(ctx, mask, C.c_void_p(dst_ptr), dst_bytes, int(dst_is_device)))
+def pic_get_fields(ctx, mask: int, frame: int, dst_ptr: int, dst_bytes: int, dst_is_device: bool):
+    _check(ctx, _load().pic_get_fields(ctx, mask, int(frame), C.c_void_p(dst_ptr), dst_bytes, int(dst_is_device)))
 
 
 def pic_set_fields(ctx, mask: int, src_ptr: int, src_bytes: int, src_is_device: bool):
@@ -305,6 +308,11 @@ def pic_filter_current_noalloc(dim: int, nx: int, ny: int, nz: int, bc_z: int, p
         if st == PIC_ERR_ARG and nodes > PIC_NOALLOC_MAX_NODES:
             detail = f"{nodes} nodes per component exceed the static scratch of {PIC_NOALLOC_MAX_NODES} nodes"
         raise PicError(st, detail)
+
+
+def pic_wait_check(arrive: bool, budget_ms: float, stream_ptr: int = 0) -> int:
+    """Status of the bounded-wait self-check (PIC_OK or PIC_ERR_TIMEOUT)."""
+    return int(_load().pic_wait_check(int(arrive), float(budget_ms), C.c_void_p(stream_ptr)))
 
 
 def pic_batch_create(ctxs) -> int:
@@ -439,11 +447,12 @@ class Simulation:
     def step_phases(self, mask):
         pic_step_phases(self.ctx, mask)
 
-    def fields(self, mask=0x1FF):
-        """dict component -> torch tensor (nz+1, ny, nx) on the device."""
+    def fields(self, mask=0x1FF, frame=0):
+        """dict component -> torch tensor (nz+1, ny, nx) on the device; frame
+        PIC_FRAME_LAB (1) gives the lab-frame E, B on the grid (mask <= 0x3F)."""
         comps = [c for q, c in enumerate(COMPONENTS) if mask >> q & 1]
         out = self.torch.empty((len(comps),) + self.shape3, dtype=self.dtype, device=self.device)
-        pic_get_fields(self.ctx, mask, out.data_ptr(), out.numel() * out.element_size(), True)
+        pic_get_fields(self.ctx, mask, frame, out.data_ptr(), out.numel() * out.element_size(), True)
         return {c: out[q] for q, c in enumerate(comps)}
 
     def set_fields(self, values: dict):

@@ -72,4 +72,70 @@ void launch_btd(const BtdArgs<real> &a, cudaStream_t s)
 template void launch_btd<float>(const BtdArgs<float> &, cudaStream_t);
 template void launch_btd<double>(const BtdArgs<double> &, cudaStream_t);
 
+// ----------------------------------------------- lab-frame view of the grid
+
+// partner component c at the height of a component of the other z
+// staggering: the mean of its planes k - 1, k (up = 0: the component is on
+// integer z, the partner on half-integer z) or k, k + 1 (up = 1); the nearer
+// plane alone at an absorbing end, planes wrap when z is periodic
+template <typename real>
+__device__ __forceinline__ double zmean(const Geom &g, const real *P, int i, int j, int k, int up, int km)
+{
+    int a = up ? k : k - 1, b = up ? k + 1 : k;
+    if (g.bc_z == 0) {
+        a = wrapi(a, g.nz);
+        b = wrapi(b, g.nz);
+    } else {
+        if (a < 0) a = b;
+        if (b > km) b = a;
+        if (a > km) a = b = km;
+    }
+    return 0.5 * ((double)P[fidx(g, i, j, a)] + (double)P[fidx(g, i, j, b)]);
+}
+
+// Component comp (0..5: Ex Ey Ez Bx By Bz) of the lab-frame fields on the
+// simulation grid at the current time, each at its own Yee position, by the
+// inverse field transformation (FP64): F the component, P the partner it
+// mixes with (By for Ex, Bx for Ey, Ey for Bx, Ex for By); nodes beyond the
+// component's z range are zero.
+template <typename real>
+__global__ void lab_fields_kernel(Geom g, const real *F, const real *P, int comp, real *out, double gam,
+                                  double beta)
+{
+    const bool half = comp == 2 || comp == 3 || comp == 4;
+    const int km = zmax_of(g, half);
+    const int kmp = zmax_of(g, !half);  // the partner's range
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < g.ncomp; r += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(r % g.nx);
+        const int j = (int)((r / g.nx) % g.ny);
+        const int k = (int)(r / g.plane);
+        double v = 0.0;
+        if (k <= km) {
+            const double f = (double)F[r];
+            switch (comp) {
+            case 0: v = gam * (f + beta * zmean(g, P, i, j, k, 0, kmp)); break;
+            case 1: v = gam * (f - beta * zmean(g, P, i, j, k, 0, kmp)); break;
+            case 3: v = gam * (f - beta * zmean(g, P, i, j, k, 1, kmp)); break;
+            case 4: v = gam * (f + beta * zmean(g, P, i, j, k, 1, kmp)); break;
+            default: v = f; break;
+            }
+        }
+        out[r] = (real)v;
+    }
+}
+
+template <typename real>
+void launch_lab_fields(const Geom &g, const real *F, const real *P, int comp, real *out, double gam, double beta,
+                       int sms, cudaStream_t s)
+{
+    int64_t blocks = (g.ncomp + 255) / 256;
+    if (blocks > 8LL * sms) blocks = 8LL * sms;
+    lab_fields_kernel<real><<<(unsigned)blocks, 256, 0, s>>>(g, F, P, comp, out, gam, beta);
+}
+
+template void launch_lab_fields<float>(const Geom &, const float *, const float *, int, float *, double, double, int,
+                                       cudaStream_t);
+template void launch_lab_fields<double>(const Geom &, const double *, const double *, int, double *, double, double,
+                                        int, cudaStream_t);
+
 }  // namespace pic

@@ -65,6 +65,7 @@ struct pic_ctx {
     int es = 4;  // element bytes
     bool ions_species = false;
     bool rel = false;  // electron records in relative form (rel_actual)
+    int sms = 152;     // multiprocessors of the device the buffers live on (set at binding)
 
     size_t field_bytes = 0, species_bytes[2] = {0, 0}, scratch_bytes = 0;
     int64_t slots = 0;
@@ -237,6 +238,7 @@ static pic_status check_device_error(pic_ctx *c)
     if (h & ERR_NAN) return fail(c, PIC_ERR_NAN, "a non-finite particle momentum or position was produced");
     if (h & ERR_CFL) return fail(c, PIC_ERR_CFL, "a particle moved one cell or more in one step");
     if (h & ERR_CAPACITY) return fail(c, PIC_ERR_CAPACITY, "a tile bucket overflowed (raise slots_per_cell)");
+    if (h & ERR_TIMEOUT) return fail(c, PIC_ERR_TIMEOUT, "a bounded device wait ran out (a staged copy did not land)");
     return fail(c, PIC_ERR_STATE, "a particle was found outside its tile bucket");
 }
 
@@ -420,6 +422,10 @@ extern "C" pic_status pic_bind_buffers(pic_ctx *c, const pic_buffers *b)
     CUDA_TRY(c, cudaMemsetAsync(c->fields, 0, c->field_bytes, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->scratch, 0, c->scratch_bytes, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+        c->sms = n;
     c->fset = 0;
     c->bound = true;
     return PIC_OK;
@@ -949,11 +955,12 @@ static void run_phases_t(pic_ctx *c, unsigned mask)
     if ((mask & PIC_PH_FILTER) && c->p.filter_passes > 0) {
         PhaseTimer pt(c, 4);
         real *J[3] = {F[6], F[7], F[8]};
+        unsigned *err = reinterpret_cast<unsigned *>(c->scratch + c->off_err);
         if (!raw_in_tmp) {
-            launch_filter<real>(c->g, J, tmp, c->p.filter_passes, c->stream);
-        } else if (!launch_filter_from<real>(c->g, tmp, J, c->p.filter_passes, c->stream)) {
+            launch_filter<real>(c->g, J, tmp, c->p.filter_passes, c->stream, err);
+        } else if (!launch_filter_from<real>(c->g, tmp, J, c->p.filter_passes, c->stream, err)) {
             cudaMemcpyAsync(J[0], tmp, (size_t)3 * c->g.ncomp * sizeof(real), cudaMemcpyDeviceToDevice, c->stream);
-            launch_filter<real>(c->g, J, tmp, c->p.filter_passes, c->stream);
+            launch_filter<real>(c->g, J, tmp, c->p.filter_passes, c->stream, err);
         }
         c->kernels += c->p.filter_passes <= 4 ? 1 : (int64_t)(c->g.dim == 3 ? 3 : 2) * c->p.filter_passes;
     }
@@ -1371,12 +1378,45 @@ static int popcount9(unsigned m)
     return n;
 }
 
-extern "C" pic_status pic_get_fields(pic_ctx *c, unsigned mask, void *dst, size_t dst_bytes, int dst_is_device)
+// lab-frame E, B components of mask (bits 0..5) into dst, one component at a
+// time through the scratch current buffer when dst is host memory
+template <typename real>
+static pic_status get_fields_lab_t(pic_ctx *c, unsigned mask, unsigned char *dst, int dst_is_device)
+{
+    const size_t per = (size_t)c->g.ncomp * c->es;
+    real *tmp = reinterpret_cast<real *>(c->scratch + c->off_tmp);
+    static const int partner[6] = {4, 3, -1, 1, 0, -1};  // By, Bx, -, Ey, Ex, -
+    size_t o = 0;
+    for (int q = 0; q < 6; ++q) {
+        if (!(mask >> q & 1u)) continue;
+        real *out = dst_is_device ? reinterpret_cast<real *>(dst + o) : tmp;
+        const real *F = (const real *)field_ptr(c, q);
+        const real *P = partner[q] >= 0 ? (const real *)field_ptr(c, partner[q]) : F;
+        launch_lab_fields<real>(c->g, F, P, q, out, c->gam, c->beta, c->sms, c->stream);
+        CUDA_TRY(c, cudaGetLastError());
+        if (!dst_is_device) CUDA_TRY(c, cudaMemcpyAsync(dst + o, tmp, per, cudaMemcpyDeviceToHost, c->stream));
+        o += per;
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_get_fields(pic_ctx *c, unsigned mask, int frame, void *dst, size_t dst_bytes,
+                                     int dst_is_device)
 {
     if (!c || !dst || (mask & ~0x1FFu) || mask == 0) return PIC_ERR_ARG;
+    if (frame != PIC_FRAME_BOOST && frame != PIC_FRAME_LAB) return fail(c, PIC_ERR_ARG, "unknown frame");
+    if (frame == PIC_FRAME_LAB && (mask & 0x1C0u))
+        return fail(c, PIC_ERR_ARG, "the lab-frame view holds E and B only");
     if (!c->bound) return fail(c, PIC_ERR_STATE, "bind buffers first");
     const size_t per = (size_t)c->g.ncomp * c->es;
     if (dst_bytes < per * popcount9(mask)) return fail(c, PIC_ERR_ARG, "destination too small");
+    if (frame == PIC_FRAME_LAB && c->gam > 1.0) {
+        if (dst_is_device && ((uintptr_t)dst % (uintptr_t)c->es) != 0)
+            return fail(c, PIC_ERR_ARG, "device destination not aligned to the element size");
+        return c->es == 4 ? get_fields_lab_t<float>(c, mask, (unsigned char *)dst, dst_is_device)
+                          : get_fields_lab_t<double>(c, mask, (unsigned char *)dst, dst_is_device);
+    }
     size_t o = 0;
     for (int q = 0; q < PIC_NCOMP; ++q) {
         if (!(mask >> q & 1u)) continue;

@@ -8,11 +8,46 @@
 // E^{n+1}, B^{n+1} to another (yee_kernel).  With absorbing z the tangential E
 // (Ex, Ey) on the end planes k = 0 and k = nz follows Mur's first-order
 // condition (Mur 1981).
+#include "pic.h"
 #include "pic_internal.cuh"
+#include "pic_tma.cuh"
 
 #include <cuda_pipeline.h>
+#include <mutex>
 
 namespace pic {
+
+// ----------------------------------------------------------- tensor maps
+
+bool encode_map_4d(CUtensorMap *map, const void *base, int elem, uint64_t n0, uint64_t n1, uint64_t n2,
+                   uint64_t count, uint32_t b0, uint32_t b1)
+{
+    using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Encode fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<Encode>(p);
+    });
+    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15u) || ((n0 * (uint64_t)elem) & 15u) ||
+        ((b0 * (uint32_t)elem) & 15u) || b0 > 256 || b1 > 256 || count > 256)
+        return false;
+    const cuuint64_t dims[4] = {n0, n1, n2, count};
+    const cuuint64_t strides[3] = {n0 * elem, n0 * n1 * elem, n0 * n1 * n2 * elem};
+    const cuuint32_t box[4] = {b0, b1, 1, (cuuint32_t)count};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = fn(map, elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                          const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
 
 template <typename real>
 struct Ptr9 {
@@ -484,6 +519,164 @@ __global__ void __launch_bounds__(256) filter_march_kernel(Geom g, const real *i
     }
 }
 
+// The same filter in 3D with its planes staged by TMA.  A CTA owns a 32 x 8
+// (x, y) column and a chunk of z planes; one tiled bulk tensor copy per plane
+// brings the three components of the column widened to x0 - 4 .. x0 + 35
+// (the copy's x start must be a multiple of 4 elements: the H <= 4 halo
+// nodes needed on each side lie inside) and y0 - H .. y0 + 7 + H into shared
+// memory, completing on that stage's mbarrier; NS planes are in flight while
+// one is filtered.  Nodes outside the grid in x or y arrive as zeros and are
+// replaced by their periodic images with plain loads (only CTAs at a grid
+// edge have any); z beyond the grid is zero (absorbing) or wrapped by the
+// copy's z coordinate (periodic).  The x-y stencil and the z passes are those
+// of filter_march_kernel.  A stage whose copy does not land within the wait
+// budget stops the CTA and records ERR_TIMEOUT.
+constexpr int kFilterStages = 4;
+
+template <typename real, int H>
+__global__ void __launch_bounds__(256) filter_tma_kernel(const __grid_constant__ CUtensorMap map, Geom g,
+                                                         const real *in, real *out, int cz, int nchunks,
+                                                         unsigned *err)
+{
+    constexpr int TX = 32, TY = 8, BX = TX + 8, BY = TY + 2 * H, PN = BX * BY;
+    constexpr int NS = kFilterStages, W = 2 * H + 1, XO = 4 - H;
+    constexpr uint32_t kBytes = 3u * PN * sizeof(real);
+    // a tensor copy's shared-memory destination must sit on a 128-byte
+    // boundary: stages are kStride elements apart, the base is rounded up
+    constexpr int kStride = (int)(((kBytes + 127u) / 128u) * 128u / sizeof(real));
+    extern __shared__ __align__(128) unsigned char smem_tma[];
+    real *stage = reinterpret_cast<real *>(smem_tma + ((128u - (smem_addr(smem_tma) & 127u)) & 127u));  // [NS][stride]
+    __shared__ __align__(8) uint64_t bar[NS];
+    real wb[W];
+    {
+        double c = 1.0;
+        for (int i = 0; i < W; ++i) {
+            wb[i] = (real)(c / (double)(1 << (2 * H)));
+            c = c * (double)(2 * H - i) / (double)(i + 1);
+        }
+    }
+    const bool per = g.bc_z == 0;
+    const int nbx = (g.nx + TX - 1) / TX;
+    const int x0 = (int)(blockIdx.x % nbx) * TX, y0 = (int)(blockIdx.x / nbx) * TY;
+    const int z0 = (int)blockIdx.y * cz;
+    const int z1 = (int)blockIdx.y == nchunks - 1 ? g.nz + 1 : z0 + cz;
+    const int kf = z0 - H, np = (z1 - 1 + H) - kf + 1;
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+    const bool own = x0 + tx < g.nx && y0 + ty < g.ny;
+    const int64_t oown = own ? (int64_t)(y0 + ty) * g.nx + (x0 + tx) : 0;
+    const bool edge = x0 - 4 < 0 || x0 + TX + 4 > g.nx || y0 - H < 0 || y0 + TY + H > g.ny;
+    const int zmax_xy = zmax_of(g, false), zmax_z = zmax_of(g, true);
+    if (tid == 0) {
+        for (int q = 0; q < NS; ++q) mbar_init(&bar[q], 1);
+        fence_proxy_async();
+    }
+    __syncthreads();
+    auto issue = [&](int q) {  // plane kf + q into stage q % NS
+        const int k = kf + q;
+        uint64_t *b = &bar[q % NS];
+        mbar_arrive_expect(b, kBytes);
+        tma_load_4d(stage + (size_t)(q % NS) * kStride, &map, x0 - 4, y0 - H, per ? wrapi(k, g.nz) : k, 0, b);
+    };
+    if (tid == 0)
+        for (int q = 0; q < NS && q < np; ++q) issue(q);
+    real lev[3][H + 1][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int p = 0; p <= H; ++p) lev[c][p][0] = lev[c][p][1] = lev[c][p][2] = real(0);
+    int q = 0;
+    for (; q < np; ++q) {
+        const int k = kf + q;
+        const int kk = per ? wrapi(k, g.nz) : k;
+        real *S = stage + (size_t)(q % NS) * kStride;
+        const bool ok = mbar_wait(&bar[q % NS], (uint32_t)(q / NS) & 1u, global_ns(), kWaitBudgetNs);
+        if (ok) {
+            // planes a component does not have are zero (Jz at k = nz)
+            if (!per && k == g.nz)
+                for (int r = tid; r < PN; r += 256) S[2 * PN + r] = real(0);
+            if (edge) {  // periodic images of the nodes outside the grid in x, y
+                for (int r = tid; r < 3 * PN; r += 256) {
+                    const int c = r / PN, rr = r - c * PN;
+                    const int ly = rr / BX, lx = rr - ly * BX;
+                    const int gx = x0 - 4 + lx, gy = y0 - H + ly;
+                    if (gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny) continue;
+                    const bool have = per || (k >= 0 && k <= (c == 2 ? zmax_z : zmax_xy));
+                    S[r] = have ? in[(size_t)c * g.ncomp + (int64_t)kk * g.plane + (int64_t)wrapi(gy, g.ny) * g.nx +
+                                     wrapi(gx, g.nx)]
+                                : real(0);
+                }
+            }
+        }
+        if (__syncthreads_or(!ok)) break;  // the CTA stops together
+        const int ko = k - H;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int zmax = c == 2 ? zmax_z : zmax_xy;
+            const real *A = S + c * PN;
+            real v = 0;
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                real r = 0;
+#pragma unroll
+                for (int i = 0; i < W; ++i) r += wb[i] * A[(ty + j) * BX + tx + XO + i];
+                v += wb[j] * r;
+            }
+#pragma unroll
+            for (int p = 0; p <= H; ++p) {
+                lev[c][p][0] = lev[c][p][1];
+                lev[c][p][1] = lev[c][p][2];
+                const int kc = k - p;
+                const bool in_range = per || (kc >= 0 && kc <= zmax);
+                const real nv = p == 0 ? v
+                                       : real(0.25) * lev[c][p - 1][0] + real(0.5) * lev[c][p - 1][1] +
+                                             real(0.25) * lev[c][p - 1][2];
+                lev[c][p][2] = in_range ? nv : real(0);
+            }
+            if (own && ko >= z0 && ko < z1)
+                out[(size_t)c * g.ncomp + (int64_t)ko * g.plane + oown] = ko > zmax ? real(0) : lev[c][H][2];
+        }
+        __syncthreads();  // every thread is done with this stage
+        if (tid == 0 && q + NS < np) {
+            fence_proxy_async();
+            issue(q + NS);
+        }
+    }
+    if (q < np) {
+        // a copy did not land: record it, then give the copies still in
+        // flight a bounded chance to finish before the CTA leaves
+        if (tid == 0) {
+            if (err) atomicOr(err, ERR_TIMEOUT);
+            const int last = np < q + NS ? np : q + NS;
+            for (int r = q; r < last; ++r)
+                (void)mbar_wait(&bar[r % NS], (uint32_t)(r / NS) & 1u, global_ns(), kWaitBudgetNs / 4);
+        }
+        __syncthreads();
+    }
+}
+
+template <typename real, int H>
+static bool launch_filter_tma(const Geom &g, const real *in, real *out, unsigned *err, cudaStream_t s)
+{
+    constexpr int TX = 32, TY = 8, BX = TX + 8, BY = TY + 2 * H;
+    CUtensorMap map;
+    if (!encode_map_4d(&map, in, (int)sizeof(real), (uint64_t)g.nx, (uint64_t)g.ny, (uint64_t)g.nz + 1, 3, BX, BY))
+        return false;
+    const int nzo = g.nz + 1;
+    const unsigned nb = (unsigned)(((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY));
+    // z chunks of 8..64 planes, as long as there are about eight CTAs per SM
+    int64_t czl = (int64_t)nzo * nb / (152 * 8);
+    czl = czl < 8 ? 8 : (czl > 64 ? 64 : czl);
+    const int cz = (int)(czl < nzo ? czl : nzo);
+    const int nchunks = nzo / cz > 0 ? nzo / cz : 1;
+    // stages on 128-byte boundaries, plus room to align the base
+    const size_t stage_bytes = ((size_t)3 * BX * BY * sizeof(real) + 127) / 128 * 128;
+    const size_t smem = (size_t)kFilterStages * stage_bytes + 128;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(filter_tma_kernel<real, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    filter_tma_kernel<real, H><<<dim3(nb, (unsigned)nchunks, 1), 256, smem, s>>>(map, g, in, out, cz, nchunks, err);
+    return true;
+}
+
 template <typename real, int DIM, int H>
 static void launch_march(const Geom &g, const real *in, real *out, cudaStream_t s)
 {
@@ -500,10 +693,20 @@ static void launch_march(const Geom &g, const real *in, real *out, cudaStream_t 
 }
 
 template <typename real>
-static bool fused_passes(const Geom &g, const real *in, real *out, int npass, cudaStream_t s)
+static bool fused_passes(const Geom &g, const real *in, real *out, int npass, cudaStream_t s, unsigned *err)
 {
     if (npass < 1 || npass > 4) return false;
     if (g.dim == 3) {
+        // TMA staging where the tensor map can be made (x extent a multiple
+        // of 16 bytes), else the plane loads of filter_march_kernel
+        bool done = false;
+        switch (npass) {
+        case 1: done = launch_filter_tma<real, 1>(g, in, out, err, s); break;
+        case 2: done = launch_filter_tma<real, 2>(g, in, out, err, s); break;
+        case 3: done = launch_filter_tma<real, 3>(g, in, out, err, s); break;
+        default: done = launch_filter_tma<real, 4>(g, in, out, err, s); break;
+        }
+        if (done) return true;
         switch (npass) {
         case 1: launch_march<real, 3, 1>(g, in, out, s); break;
         case 2: launch_march<real, 3, 2>(g, in, out, s); break;
@@ -522,20 +725,20 @@ static bool fused_passes(const Geom &g, const real *in, real *out, int npass, cu
 }
 
 template <typename real>
-bool launch_filter_from(const Geom &g, const real *src, real *const J[3], int npass, cudaStream_t s)
+bool launch_filter_from(const Geom &g, const real *src, real *const J[3], int npass, cudaStream_t s, unsigned *err)
 {
     const bool contiguous = J[1] == J[0] + g.ncomp && J[2] == J[1] + g.ncomp;
-    return contiguous && fused_passes<real>(g, src, J[0], npass, s);
+    return contiguous && fused_passes<real>(g, src, J[0], npass, s, err);
 }
 
 template <typename real>
-void launch_filter(const Geom &g, real *const J[3], real *tmp, int npass, cudaStream_t s)
+void launch_filter(const Geom &g, real *const J[3], real *tmp, int npass, cudaStream_t s, unsigned *err)
 {
     if (npass <= 0) return;
     // the three components are contiguous in the field buffer; the fused
     // kernel covers 1..4 passes, more fall back to one launch per pass
     const bool contiguous = J[1] == J[0] + g.ncomp && J[2] == J[1] + g.ncomp;
-    if (contiguous && fused_passes<real>(g, J[0], tmp, npass, s)) {
+    if (contiguous && fused_passes<real>(g, J[0], tmp, npass, s, err)) {
         cudaMemcpyAsync(J[0], tmp, 3 * sizeof(real) * g.ncomp, cudaMemcpyDeviceToDevice, s);
         return;
     }
@@ -633,8 +836,9 @@ void launch_field_sums(const Geom &g, real *const F[9], double *partials, int nb
 #define PIC_FIELDS_INSTANTIATE(real)                                                                    \
     template void launch_yee<real>(const Geom &, real *const[9], real *const[6], double, double, double, \
                                    double, cudaStream_t);                                               \
-    template void launch_filter<real>(const Geom &, real *const[3], real *, int, cudaStream_t);         \
-    template bool launch_filter_from<real>(const Geom &, const real *, real *const[3], int, cudaStream_t); \
+    template void launch_filter<real>(const Geom &, real *const[3], real *, int, cudaStream_t, unsigned *); \
+    template bool launch_filter_from<real>(const Geom &, const real *, real *const[3], int, cudaStream_t,  \
+                                           unsigned *);                                                   \
     template void launch_window_fields<real>(const Geom &, real *const[9], real *const[9], int, cudaStream_t); \
     template void launch_antenna<real>(const Geom &, real *, int, int, double, double, double, double,  \
                                        double, double, cudaStream_t, const double *);                   \
@@ -642,4 +846,45 @@ void launch_field_sums(const Geom &g, real *const F[9], double *partials, int nb
 PIC_FIELDS_INSTANTIATE(float)
 PIC_FIELDS_INSTANTIATE(double)
 
+// ------------------------------------------------ bounded-wait self-check
+
+namespace {
+__device__ unsigned g_wait_result;
+
+// one CTA: an mbarrier expecting one arrival, which this kernel makes or
+// withholds; the wait gives up after budget_ns
+__global__ void wait_check_kernel(int arrive, uint64_t budget_ns)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_proxy_async();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && arrive)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bar)) : "memory");
+    const bool ok = mbar_wait(&bar, 0u, global_ns(), budget_ns);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) g_wait_result = 1u;
+}
+}  // namespace
+
+}  // namespace pic
+
+extern "C" pic_status pic_wait_check(int arrive, double budget_ms, void *stream)
+{
+    if (!(budget_ms > 0.0) || budget_ms > 10000.0) return PIC_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const unsigned zero = 0u;
+    if (cudaMemcpyToSymbolAsync(pic::g_wait_result, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return PIC_ERR_CUDA;
+    pic::wait_check_kernel<<<1, 64, 0, s>>>(arrive ? 1 : 0, (uint64_t)(budget_ms * 1e6));
+    unsigned r = 0;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyFromSymbolAsync(&r, pic::g_wait_result, sizeof(r), 0, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return PIC_ERR_CUDA;
+    return r ? PIC_ERR_TIMEOUT : PIC_OK;
+}
+
+namespace pic {
 }  // namespace pic

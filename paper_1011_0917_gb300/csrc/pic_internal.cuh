@@ -26,7 +26,7 @@
 
 namespace pic {
 
-enum : unsigned { ERR_CAPACITY = 1u, ERR_CFL = 2u, ERR_NAN = 4u, ERR_TILE = 8u };
+enum : unsigned { ERR_CAPACITY = 1u, ERR_CFL = 2u, ERR_NAN = 4u, ERR_TILE = 8u, ERR_TIMEOUT = 16u };
 
 // Bit 31 of an electron's cell word: the electron is paired with a drifting ion
 // at its own position that has moved exactly like it since both were placed
@@ -544,6 +544,11 @@ void launch_particle_sums(const Geom &g, const Species<real> &sp, const int *lo,
 void launch_inject(const InjectArgs &a, cudaStream_t s);
 template <typename real>
 void launch_btd(const BtdArgs<real> &a, cudaStream_t s);
+// component comp (0..5) of the lab-frame E, B on the grid (F the component,
+// P its partner: By, Bx, -, Ey, Ex, -) into out; FP64 transformation
+template <typename real>
+void launch_lab_fields(const Geom &g, const real *F, const real *P, int comp, real *out, double gam, double beta,
+                       int sms, cudaStream_t s);
 // moving window: every field plane k of dst takes plane k + S of src (zero
 // above), for the nine components
 template <typename real>
@@ -557,12 +562,14 @@ void launch_window_particles(const Geom &g, const Species<real> &in, const Speci
 template <typename real>
 void launch_yee(const Geom &g, real *const F[9], real *const F1[6], double dt, double hx, double hy, double hz,
                 cudaStream_t s);
+// (err: the device error word for a bounded wait that ran out; may be null)
 template <typename real>
-void launch_filter(const Geom &g, real *const J[3], real *tmp, int npass, cudaStream_t s);
+void launch_filter(const Geom &g, real *const J[3], real *tmp, int npass, cudaStream_t s, unsigned *err = nullptr);
 // all passes from src (3 contiguous components, left unchanged) into J;
 // false (nothing launched) where only the per-pass path applies (npass > 4)
 template <typename real>
-bool launch_filter_from(const Geom &g, const real *src, real *const J[3], int npass, cudaStream_t s);
+bool launch_filter_from(const Geom &g, const real *src, real *const J[3], int npass, cudaStream_t s,
+                        unsigned *err = nullptr);
 // j0p non-null: the amplitude is read from device memory (a captured step)
 template <typename real>
 void launch_antenna(const Geom &g, real *J, int pol, int ka, double j0, double hx, double hy,

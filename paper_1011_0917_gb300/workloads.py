@@ -19,8 +19,11 @@ at gamma_boost 130 stand behind these; no dataset is involved):
       in through z = Lz for the whole run; the throughput workload.  c2_small
       is the same stage on a 128 x 128 x 256 box, for kernel profiles.
   c3  gamma_boost = 130, 2D3V, 512 x 16384, quadratic shape, 4 passes,
-      n = 5.7e-5, 5 lambda0 ramp, laser a0 = 1.5, w0 = 50, FWHM 30; c3_small
-      is the same stage on a 4x coarser grid (128 x 4096).
+      n = 5.7e-5 over 1e6 lambda0 (lab) with a 5 lambda0 ramp, starting 3e6
+      lambda0 ahead of the antenna (the boosted pulse, 2 gamma longer than in
+      the lab, is emitted before the plasma reaches it), laser a0 = 1.5,
+      w0 = 50, FWHM 30; 6500 steps take the pulse peak through the whole
+      plasma.  c3_small is the same stage on a 4x coarser grid (128 x 4096).
   c4  the batched scan: 64 independent 2D3V boosted runs (c4_run).
 """
 from __future__ import annotations
@@ -82,8 +85,8 @@ def stage(name: str) -> Stage:
         return Stage(name, _grid(nx=128 if small else 512, nz=4096 if small else 16384, dx=4.0 if small else 1.0,
                                  dz=(4.0 if small else 1.0) / 32, gamma_boost=130.0, shape_order=2,
                                  filter_passes=4, seed=SEED0 + 3),
-                     dict(ne=5.7e-5, z_start=6.0e5, z_end=1.6e6, ramp=5.0, ppc=(2, 1, 2), jitter=0.1, ions=1),
-                     dict(a0=1.5, waist=50.0, fwhm=30.0, z_antenna=0.0, pol=1), steps=2000)
+                     dict(ne=5.7e-5, z_start=3.0e6, z_end=4.0e6, ramp=5.0, ppc=(2, 1, 2), jitter=0.1, ions=1),
+                     dict(a0=1.5, waist=50.0, fwhm=30.0, z_antenna=0.0, pol=1), steps=6500)
     raise KeyError(name)
 
 

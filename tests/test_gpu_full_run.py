@@ -66,3 +66,53 @@ def test_c0_full_run_peak_wake_and_depletion(oracle_run, prec):
     assert peak_o > 1e-2 and ke_o > 0
     assert abs(peak - peak_o) <= 1e-2 * peak_o, (peak, peak_o)
     assert abs(ke - ke_o) <= 1e-2 * ke_o, (ke, ke_o)
+
+
+# ------------------------------------------------------ boosted-frame stages
+
+def _golden(name):
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "full_runs.json")
+    with open(path) as f:
+        return json.load(f)[name]
+
+
+@pytest.mark.parametrize("name", ["c1", "c3_small"])
+def test_boosted_stage_full_run_matches_oracle(name):
+    """The gamma = 13 stage (c1: 256 x 8192, 1800 steps, until the pulse peak
+    has crossed the 2000 lambda0 plasma) and the gamma = 130 stage on its 4x
+    coarser grid (c3_small: 128 x 4096, quadratic shape, 4 passes, 6500
+    steps), FP32, against the outcomes of the FP64 oracle's own whole runs
+    (tests/golden/full_runs.json, written by tests/golden/make_full_runs.py
+    from the oracle alone): the peak on-axis wake field over the run and the
+    energy the plasma electrons took from the laser, each within 1%."""
+    import fullrun
+    import paper_1011_0917_gb300 as P
+    ref = _golden(name)
+    st = W.stage(name)
+    g = st.grid
+    assert ref["steps"] == st.steps
+    sim = P.Simulation(dim=g["dim"], nx=g["nx"], ny=g["ny"], nz=g["nz"], dx=g["dx"], dy=g["dy"], dz=g["dz"],
+                       cfl=g["cfl"], gamma_boost=g["gamma_boost"], shape_order=g["shape_order"],
+                       filter_passes=g["filter_passes"], bc_z=g["bc_z"], precision=FP32, seed=g["seed"],
+                       slots_per_cell=8.0)
+    p = st.plasma
+    sim.load_plasma(p["ne"], p["z_start"], p["z_end"], p["ramp"], p["ppc"], p["jitter"], (), p["ions"])
+    l = st.laser
+    sim.launch_laser(l["a0"], l["waist"], l["fwhm"], l["z_antenna"], -1.0, l["pol"])
+    import torch
+    line = torch.empty(g["nz"] + 1, dtype=torch.float32)
+    peak = 0.0
+    for _ in range(st.steps // ref["sample"]):
+        sim.step(ref["sample"])
+        P.pic_get_axis(sim.ctx, 2, line.data_ptr(), line.numel() * 4, False)
+        peak = max(peak, float(line.abs().max()))
+    e, _ = sim.particles(0)
+    i, _ = sim.particles(1)
+    U = float(i[5, 0])  # the drift momentum as this side holds it
+    energy = fullrun.plasma_energy(e[6], e[3], e[4], e[5], U)
+    assert ref["peak_ez"] > 0 and ref["plasma_energy"] > 0
+    assert abs(peak - ref["peak_ez"]) <= 1e-2 * ref["peak_ez"], (peak, ref)
+    assert abs(energy - ref["plasma_energy"]) <= 1e-2 * ref["plasma_energy"], (energy, ref)
+    sim.close()
