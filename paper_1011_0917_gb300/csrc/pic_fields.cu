@@ -526,10 +526,12 @@ __global__ void __launch_bounds__(256) filter_march_kernel(Geom g, const real *i
 // nodes needed on each side lie inside) and y0 - H .. y0 + 7 + H into shared
 // memory, completing on that stage's mbarrier; NS planes are in flight while
 // one is filtered.  Nodes outside the grid in x or y arrive as zeros and are
-// replaced by their periodic images with plain loads (only CTAs at a grid
-// edge have any); z beyond the grid is zero (absorbing) or wrapped by the
-// copy's z coordinate (periodic).  The x-y stencil and the z passes are those
-// of filter_march_kernel.  A stage whose copy does not land within the wait
+// replaced by their periodic images, loaded into registers one plane ahead
+// (only CTAs at a grid edge have any); z beyond the grid is zero (absorbing)
+// or wrapped by the copy's z coordinate (periodic).  The x-y passes are the
+// binomial stencil of width 2H + 1 taken separably (x over the widened rows
+// into shared memory, then y), the z passes are those of
+// filter_march_kernel.  A stage whose copy does not land within the wait
 // budget stops the CTA and records ERR_TIMEOUT.
 constexpr int kFilterStages = 4;
 
@@ -544,8 +546,12 @@ __global__ void __launch_bounds__(256) filter_tma_kernel(const __grid_constant__
     // a tensor copy's shared-memory destination must sit on a 128-byte
     // boundary: stages are kStride elements apart, the base is rounded up
     constexpr int kStride = (int)(((kBytes + 127u) / 128u) * 128u / sizeof(real));
+    constexpr int XR = BY * TX;                  // x-filtered values per component
+    constexpr int NXP = (3 * XR + 255) / 256;    // of them per thread
+    constexpr int NP = (3 * PN + 255) / 256;     // box nodes per thread (periodic images)
     extern __shared__ __align__(128) unsigned char smem_tma[];
-    real *stage = reinterpret_cast<real *>(smem_tma + ((128u - (smem_addr(smem_tma) & 127u)) & 127u));  // [NS][stride]
+    real *stage = reinterpret_cast<real *>(smem_tma + ((128u - (smem_addr(smem_tma) & 127u)) & 127u));
+    real *xs = stage + (size_t)NS * kStride;     // [3][BY][TX]
     __shared__ __align__(8) uint64_t bar[NS];
     real wb[W];
     {
@@ -566,6 +572,32 @@ __global__ void __launch_bounds__(256) filter_tma_kernel(const __grid_constant__
     const int64_t oown = own ? (int64_t)(y0 + ty) * g.nx + (x0 + tx) : 0;
     const bool edge = x0 - 4 < 0 || x0 + TX + 4 > g.nx || y0 - H < 0 || y0 + TY + H > g.ny;
     const int zmax_xy = zmax_of(g, false), zmax_z = zmax_of(g, true);
+    // this thread's box nodes outside the grid in x or y: their periodic
+    // images' offsets within a plane
+    int poff[NP];
+    unsigned pmask = 0u;
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+        poff[m] = 0;
+        const int r = tid + 256 * m;
+        if (!edge || r >= 3 * PN) continue;
+        const int rr = r % PN, ly = rr / BX, lx = rr - ly * BX;
+        const int gx = x0 - 4 + lx, gy = y0 - H + ly;
+        if (gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny) continue;
+        poff[m] = wrapi(gy, g.ny) * g.nx + wrapi(gx, g.nx);
+        pmask |= 1u << m;
+    }
+    real pv[NP];
+    auto patch_load = [&](int k) {  // plane k's periodic images into registers
+        const int kk = per ? wrapi(k, g.nz) : k;
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+            if (!(pmask >> m & 1u)) continue;
+            const int c = (tid + 256 * m) / PN;
+            const bool have = per || (k >= 0 && k <= (c == 2 ? zmax_z : zmax_xy));
+            pv[m] = have ? in[(size_t)c * g.ncomp + (int64_t)kk * g.plane + poff[m]] : real(0);
+        }
+    };
     if (tid == 0) {
         for (int q = 0; q < NS; ++q) mbar_init(&bar[q], 1);
         fence_proxy_async();
@@ -579,6 +611,7 @@ __global__ void __launch_bounds__(256) filter_tma_kernel(const __grid_constant__
     };
     if (tid == 0)
         for (int q = 0; q < NS && q < np; ++q) issue(q);
+    if (pmask) patch_load(kf);
     real lev[3][H + 1][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -587,40 +620,46 @@ __global__ void __launch_bounds__(256) filter_tma_kernel(const __grid_constant__
     int q = 0;
     for (; q < np; ++q) {
         const int k = kf + q;
-        const int kk = per ? wrapi(k, g.nz) : k;
         real *S = stage + (size_t)(q % NS) * kStride;
         const bool ok = mbar_wait(&bar[q % NS], (uint32_t)(q / NS) & 1u, global_ns(), kWaitBudgetNs);
         if (ok) {
             // planes a component does not have are zero (Jz at k = nz)
             if (!per && k == g.nz)
                 for (int r = tid; r < PN; r += 256) S[2 * PN + r] = real(0);
-            if (edge) {  // periodic images of the nodes outside the grid in x, y
-                for (int r = tid; r < 3 * PN; r += 256) {
-                    const int c = r / PN, rr = r - c * PN;
-                    const int ly = rr / BX, lx = rr - ly * BX;
-                    const int gx = x0 - 4 + lx, gy = y0 - H + ly;
-                    if (gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny) continue;
-                    const bool have = per || (k >= 0 && k <= (c == 2 ? zmax_z : zmax_xy));
-                    S[r] = have ? in[(size_t)c * g.ncomp + (int64_t)kk * g.plane + (int64_t)wrapi(gy, g.ny) * g.nx +
-                                     wrapi(gx, g.nx)]
-                                : real(0);
-                }
+            if (pmask) {
+#pragma unroll
+                for (int m = 0; m < NP; ++m)
+                    if (pmask >> m & 1u) S[tid + 256 * m] = pv[m];
+                if (q + 1 < np) patch_load(k + 1);  // in flight while this plane is filtered
             }
         }
         if (__syncthreads_or(!ok)) break;  // the CTA stops together
+        // x passes over the widened rows
+#pragma unroll
+        for (int n = 0; n < NXP; ++n) {
+            const int idx = tid + 256 * n;
+            if (idx < 3 * XR) {
+                const int c = idx / XR, rr = idx - c * XR, row = rr / TX, col = rr - row * TX;
+                const real *A = S + c * PN + row * BX + col + XO;
+                real v = 0;
+#pragma unroll
+                for (int i = 0; i < W; ++i) v += wb[i] * A[i];
+                xs[idx] = v;
+            }
+        }
+        __syncthreads();  // the stage is consumed: refill it while the y and z passes run
+        if (tid == 0 && q + NS < np) {
+            fence_proxy_async();
+            issue(q + NS);
+        }
         const int ko = k - H;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const int zmax = c == 2 ? zmax_z : zmax_xy;
-            const real *A = S + c * PN;
+            const real *X = xs + c * XR + ty * TX + tx;
             real v = 0;
 #pragma unroll
-            for (int j = 0; j < W; ++j) {
-                real r = 0;
-#pragma unroll
-                for (int i = 0; i < W; ++i) r += wb[i] * A[(ty + j) * BX + tx + XO + i];
-                v += wb[j] * r;
-            }
+            for (int j = 0; j < W; ++j) v += wb[j] * X[j * TX];
 #pragma unroll
             for (int p = 0; p <= H; ++p) {
                 lev[c][p][0] = lev[c][p][1];
@@ -634,11 +673,6 @@ __global__ void __launch_bounds__(256) filter_tma_kernel(const __grid_constant__
             }
             if (own && ko >= z0 && ko < z1)
                 out[(size_t)c * g.ncomp + (int64_t)ko * g.plane + oown] = ko > zmax ? real(0) : lev[c][H][2];
-        }
-        __syncthreads();  // every thread is done with this stage
-        if (tid == 0 && q + NS < np) {
-            fence_proxy_async();
-            issue(q + NS);
         }
     }
     if (q < np) {
@@ -668,9 +702,10 @@ static bool launch_filter_tma(const Geom &g, const real *in, real *out, unsigned
     czl = czl < 8 ? 8 : (czl > 64 ? 64 : czl);
     const int cz = (int)(czl < nzo ? czl : nzo);
     const int nchunks = nzo / cz > 0 ? nzo / cz : 1;
-    // stages on 128-byte boundaries, plus room to align the base
+    // stages on 128-byte boundaries, plus room to align the base, then the
+    // x-filtered rows
     const size_t stage_bytes = ((size_t)3 * BX * BY * sizeof(real) + 127) / 128 * 128;
-    const size_t smem = (size_t)kFilterStages * stage_bytes + 128;
+    const size_t smem = (size_t)kFilterStages * stage_bytes + 128 + (size_t)3 * BY * TX * sizeof(real);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(filter_tma_kernel<real, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     filter_tma_kernel<real, H><<<dim3(nb, (unsigned)nchunks, 1), 256, smem, s>>>(map, g, in, out, cz, nchunks, err);

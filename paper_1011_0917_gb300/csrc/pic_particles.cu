@@ -474,9 +474,35 @@ __device__ __forceinline__ bool ions_of_tile(const Geom &g, const IonSide<real> 
                 oz = d[2 * kBlock];
                 w = d[3 * kBlock];
                 if (is.in.id) pid = is.in.id[bucket_slot(t, g.cap, n_lo, n_hi, p)];
+                const real z1 = add_rn(oz, dz);
+                if (!REL) {
+                    // written out here rather than through ion_deposit: the
+                    // inlined call measured more register spills in the
+                    // electron kernel that fuses this pass
+                    real S0z[S + 2], DSz[S + 2], wx[S + 1], wy[S + 1];
+                    bool crossed;
+                    const int az = esirk_axis_c<S>(oz, z1, S0z, DSz, crossed) + lk + JL;
+                    const int bx = offset_weights<S>(ox, wx) + li + JL;
+                    int by = 0;
+                    if (DIM == 3) by = offset_weights<S>(oy, wy) + lj + JL;
+                    const real fz = is.jfac_z * w * scale_z;
+                    real Pz[S + 2];
+                    real run = 0;
+#pragma unroll
+                    for (int c = 0; c < S + 2; ++c) { run += DSz[c]; Pz[c] = fz * run; }
+#pragma unroll
+                    for (int b = 0; b < (DIM == 3 ? S + 1 : 1); ++b) {
+#pragma unroll
+                        for (int q = 0; q < S + 1; ++q) {
+                            const real sxy = DIM == 3 ? wx[q] * wy[b] : wx[q];
+#pragma unroll
+                            for (int c = 0; c < S + 1; ++c)
+                                sh_acc<LOFF>(Jz + ((az + c) * QY + (by + b)) * QX + bx + q, Pz[c], sxy, lo_scale);
+                        }
+                    }
+                }
                 // z1 in (-1, 1): the same cell or the one below; an offset
                 // that rounds to 1 stays in the cell with offset 0
-                const real z1 = add_rn(oz, dz);
                 int sz = 0;
                 real on = z1;
                 if (z1 < real(0)) {
@@ -484,14 +510,10 @@ __device__ __forceinline__ bool ions_of_tile(const Geom &g, const IonSide<real> 
                     sz = -1;
                     if (on >= real(1)) { on = 0; sz = 0; }
                 }
-                if (REL) {
+                if (REL)  // from the stored position to the stored position
                     ion_deposit<double, acc_t, DIM, S, QX, QY, LOFF>(
                         Jz, (double)oz, (double)sz + (double)on, (double)ox, (double)oy, li, lj, lk,
                         (double)is.jfac_z * (double)w * (double)scale_z, (double)lo_scale);
-                } else {
-                    ion_deposit<real, acc_t, DIM, S, QX, QY, LOFF>(Jz, oz, z1, ox, oy, li, lj, lk,
-                                                                   is.jfac_z * w * scale_z, lo_scale);
-                }
                 oz = on;
                 int nk = ck + sz;
                 bool alive = true;
@@ -819,19 +841,22 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<real>::value) push_kernel(Pu
             if (valid && keep_pair) {
                 // moved exactly like its ion: no deposit
             } else if (valid) {
-                const dep_t los = (dep_t)a.fx_lo[0];
+                // (the fixed-point factors are read from the parameters at each
+                // use: held in registers they would cost spills here)
                 const dep_t fz = (dep_t)a.jfac[2] * (dep_t)w * (dep_t)a.fx_scale[2];
                 if (z_only) {
                     if (sel & 1u)
-                        deposit_z<dep_t, acc_t, S, QX, QY, QN, S + 2>(sJ, S0x, S0y, S0z, DSz, ax, ay, az, fz, los);
+                        deposit_z<dep_t, acc_t, S, QX, QY, QN, S + 2>(sJ, S0x, S0y, S0z, DSz, ax, ay, az, fz,
+                                                                      (dep_t)a.fx_lo[0]);
                     else
-                        deposit_z<dep_t, acc_t, S, QX, QY, QN, S + 1>(sJ, S0x, S0y, S0z, DSz, ax, ay, az, fz, los);
+                        deposit_z<dep_t, acc_t, S, QX, QY, QN, S + 1>(sJ, S0x, S0y, S0z, DSz, ax, ay, az, fz,
+                                                                      (dep_t)a.fx_lo[0]);
                 } else {
                     deposit_sel<dep_t, acc_t, DIM, S, QX, QY, QN>(
                         sel, sJ, S0x, DSx, S0y, DSy, S0z, DSz, ax, ay, az,
                         (dep_t)a.jfac[0] * (dep_t)w * (dep_t)a.fx_scale[0],
                         (dep_t)a.jfac[1] * (dep_t)w * (dep_t)a.fx_scale[1], fz,
-                        (dep_t)a.jyfac * (dep_t)w * (dep_t)vy * (dep_t)a.fx_scale[1], los);
+                        (dep_t)a.jyfac * (dep_t)w * (dep_t)vy * (dep_t)a.fx_scale[1], (dep_t)a.fx_lo[0]);
                 }
             }
             if (valid) {

@@ -19,11 +19,15 @@ at gamma_boost 130 stand behind these; no dataset is involved):
       in through z = Lz for the whole run; the throughput workload.  c2_small
       is the same stage on a 128 x 128 x 256 box, for kernel profiles.
   c3  gamma_boost = 130, 2D3V, 512 x 16384, quadratic shape, 4 passes,
-      n = 5.7e-5 over 1e6 lambda0 (lab) with a 5 lambda0 ramp, starting 3e6
-      lambda0 ahead of the antenna (the boosted pulse, 2 gamma longer than in
-      the lab, is emitted before the plasma reaches it), laser a0 = 1.5,
-      w0 = 50, FWHM 30; 6500 steps take the pulse peak through the whole
-      plasma.  c3_small is the same stage on a 4x coarser grid (128 x 4096).
+      n = 5.7e-5 over 1e6 lambda0 (lab) from 3e6 lambda0 with a 5 lambda0
+      ramp, laser a0 = 1.5, w0 = 50, FWHM 30; 6500 steps.  The boosted pulse
+      is 2 gamma longer than in the lab: its peak leaves the antenna only
+      after ~5000 steps, and the plasma streaming through the box meets it
+      near the end of the run.  Long before that the numerical instability
+      of the streaming plasma (the one the paper's mitigation section
+      treats) grows from round-off: with 4 filter passes it dominates the
+      fields from ~3500 steps on.  c3_small is the same stage on a 4x
+      coarser grid (128 x 4096).
   c4  the batched scan: 64 independent 2D3V boosted runs (c4_run).
 """
 from __future__ import annotations

@@ -78,41 +78,74 @@ def _golden(name):
         return json.load(f)[name]
 
 
-@pytest.mark.parametrize("name", ["c1", "c3_small"])
-def test_boosted_stage_full_run_matches_oracle(name):
-    """The gamma = 13 stage (c1: 256 x 8192, 1800 steps, until the pulse peak
-    has crossed the 2000 lambda0 plasma) and the gamma = 130 stage on its 4x
-    coarser grid (c3_small: 128 x 4096, quadratic shape, 4 passes, 6500
-    steps), FP32, against the outcomes of the FP64 oracle's own whole runs
-    (tests/golden/full_runs.json, written by tests/golden/make_full_runs.py
-    from the oracle alone): the peak on-axis wake field over the run and the
-    energy the plasma electrons took from the laser, each within 1%."""
-    import fullrun
+def _run_stage(name, sample, slots=8.0):
+    """The stage in FP32 on the GPU: the peak on-axis |E_z| every `sample`
+    steps, the electrons and ions at the end."""
+    import torch
+
     import paper_1011_0917_gb300 as P
-    ref = _golden(name)
     st = W.stage(name)
     g = st.grid
-    assert ref["steps"] == st.steps
     sim = P.Simulation(dim=g["dim"], nx=g["nx"], ny=g["ny"], nz=g["nz"], dx=g["dx"], dy=g["dy"], dz=g["dz"],
                        cfl=g["cfl"], gamma_boost=g["gamma_boost"], shape_order=g["shape_order"],
                        filter_passes=g["filter_passes"], bc_z=g["bc_z"], precision=FP32, seed=g["seed"],
-                       slots_per_cell=8.0)
+                       slots_per_cell=slots)
     p = st.plasma
     sim.load_plasma(p["ne"], p["z_start"], p["z_end"], p["ramp"], p["ppc"], p["jitter"], (), p["ions"])
     l = st.laser
     sim.launch_laser(l["a0"], l["waist"], l["fwhm"], l["z_antenna"], -1.0, l["pol"])
-    import torch
     line = torch.empty(g["nz"] + 1, dtype=torch.float32)
-    peak = 0.0
-    for _ in range(st.steps // ref["sample"]):
-        sim.step(ref["sample"])
+    steps, hist = [], []
+    for s in range(st.steps // sample):
+        sim.step(sample)
         P.pic_get_axis(sim.ctx, 2, line.data_ptr(), line.numel() * 4, False)
-        peak = max(peak, float(line.abs().max()))
+        steps.append((s + 1) * sample)
+        hist.append(float(line.abs().max()))
     e, _ = sim.particles(0)
     i, _ = sim.particles(1)
+    sim.close()
+    return st, steps, hist, e, i
+
+
+def test_c1_full_run_matches_oracle():
+    """The gamma = 13 stage (c1: 256 x 8192, 1800 steps, until the pulse peak
+    has crossed the 2000 lambda0 plasma), FP32, against the outcomes of the
+    FP64 oracle's own whole run (tests/golden/full_runs.json, written by
+    tests/golden/make_full_runs.py from the oracle alone): the peak on-axis
+    wake field over the run and the energy the plasma electrons took from the
+    laser, each within 1%."""
+    import fullrun
+    ref = _golden("c1")
+    st, steps, hist, e, i = _run_stage("c1", ref["sample"])
+    assert ref["steps"] == st.steps
+    peak = max(hist)
     U = float(i[5, 0])  # the drift momentum as this side holds it
     energy = fullrun.plasma_energy(e[6], e[3], e[4], e[5], U)
     assert ref["peak_ez"] > 0 and ref["plasma_energy"] > 0
     assert abs(peak - ref["peak_ez"]) <= 1e-2 * ref["peak_ez"], (peak, ref)
     assert abs(energy - ref["plasma_energy"]) <= 1e-2 * ref["plasma_energy"], (energy, ref)
-    sim.close()
+
+
+def test_c3_small_instability_growth_matches_oracle():
+    """The gamma = 130 stage on its 4x coarser grid (c3_small: 128 x 4096,
+    quadratic shape, 4 filter passes, 6500 steps), FP32.  In this frame the
+    streaming plasma is numerically unstable with 4 binomial passes (the
+    instability the paper's mitigation section treats): the on-axis E_z is
+    exactly zero until it grows from round-off, exponentially, long before
+    the pulse peak (emitted after ~5000 steps by the antenna) meets the
+    plasma.  Outcomes of the wake cannot be compared then; what both sides
+    must share is the instability's growth rate, a property of the discrete
+    scheme (the round-off that seeds it differs): within 10% of the FP64
+    oracle's (tests/golden/full_runs.json)."""
+    import math
+
+    import fullrun
+    ref = _golden("c3_small")
+    st, steps, hist, _, _ = _run_stage("c3_small", ref["sample"], slots=24.0)
+    assert ref["steps"] == st.steps
+    rate, used = fullrun.growth_rate(steps, hist)
+    assert ref["ez_growth_samples"] >= 10 and used >= 10, (used, ref["ez_growth_samples"])
+    assert ref["ez_growth_rate"] > 0.005
+    assert abs(rate - ref["ez_growth_rate"]) <= 0.1 * ref["ez_growth_rate"], (rate, ref["ez_growth_rate"])
+    # it is an instability: growth by orders of magnitude, not a wake
+    assert max(hist) > 1e3 * min(v for v in hist if v > 0) and math.isfinite(max(hist))
