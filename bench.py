@@ -71,6 +71,8 @@ def parse():
                     help="time only the adjoint/forward leg (one c4 run, --adjoint-steps steps, a checkpoint "
                          "every --checkpoint-every) and print its record")
     ap.add_argument("--checkpoint-every", type=int, default=50)
+    ap.add_argument("--adjoint-3d-steps", type=int, default=100,
+                    help="steps of the adjoint/forward timing on a 3D slab of the c2 stage (0: skip)")
     return ap.parse_args()
 
 
@@ -324,6 +326,7 @@ def run_ours(args, rank, world, local):
 
     c4 = run_c4(P, torch, args.c4, args.warmup, 200) if args.c4 > 0 else None
     adj = run_adjoint(P, torch, args.adjoint_steps, args.checkpoint_every) if args.adjoint_steps > 0 else None
+    adj3 = run_adjoint_3d(P, torch, args.adjoint_3d_steps) if args.adjoint_3d_steps > 0 else None
 
     result = None
     if rank == 0:
@@ -359,6 +362,7 @@ def run_ours(args, rank, world, local):
             "cpu_baseline": cpu,
             "adjoint_forward_ratio": adj["ratio"] if adj else None,
             "adjoint": adj,
+            "adjoint_3d": adj3,
             "explicit_ion_records": explicit,
             "lab_frame_snapshots": btd,
             "batched_c4": c4,
@@ -481,6 +485,58 @@ def run_adjoint(P, torch, steps, K, r=0):
             "gradient": {"profile": grad[:-2], "a0": grad[-2], "w0": grad[-1]},
             "objective": "sum of on-axis Ez over planes 16..127 (behind the antenna, inside the plasma) at the "
                          "last step"}
+
+
+def run_adjoint_3d(P, torch, steps, K=25, K2=5):
+    """Adjoint/forward time of a 3D run: the c2 stage (gamma = 13, CIC, 2
+    passes, 2x2x2 per cell, FP32) on a 96 x 96 x 192 slab, the gradient of the
+    on-axis Ez over planes 8..119 after `steps` steps with respect to a0 and
+    the waist (the c2 plasma has no profile coefficients); one-level
+    checkpoints every K steps and two-level ones (a sub-checkpoint every K2
+    steps: a smaller buffer for one more forward pass)."""
+    from paper_1011_0917_gb300 import workloads as W
+    st = W.stage("c2")
+    g = dict(st.grid, nx=96, ny=96, nz=192)
+
+    def make():
+        sim = P.Simulation(dim=3, nx=g["nx"], ny=g["ny"], nz=g["nz"], dx=g["dx"], dy=g["dy"], dz=g["dz"],
+                           cfl=g["cfl"], gamma_boost=g["gamma_boost"], filter_passes=g["filter_passes"],
+                           precision=P.PIC_FP32, seed=g["seed"], slots_per_cell=10.0, stream=torch.cuda.Stream())
+        p = st.plasma
+        sim.load_plasma(p["ne"], p["z_start"], p["z_end"], p["ramp"], p["ppc"], p["jitter"], (), p["ions"])
+        l = st.laser
+        sim.launch_laser(l["a0"], l["waist"], l["fwhm"], 0.0, 1.0, l["pol"])
+        return sim
+
+    def timed(sim, fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(sim.stream)
+        out = fn()
+        e1.record(sim.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    sim = make()
+    n_e = sim.diagnostics().n_particles[0]
+    fwd_ms, _ = timed(sim, lambda: P.pic_step_async(sim.ctx, steps))
+    sim.close()
+    out = {"run": f"c2 stage on a {g['nx']}x{g['ny']}x{g['nz']} slab, {n_e} electrons, {steps} steps, FP32",
+           "forward_ms": fwd_ms}
+    for name, k2 in (("one_level", 0), ("two_level", K2)):
+        sim = make()
+        with torch.cuda.stream(sim.stream):
+            a_fwd_ms, fields = timed(sim, lambda: sim.adjoint_forward(steps, K, k2))
+            cot = torch.zeros_like(fields)
+            cot[2, 8:120, g["ny"] // 2, g["nx"] // 2] = 1.0
+            a_bwd_ms, grad = timed(sim, lambda: sim.adjoint_backward(cot))
+        out[name] = {"checkpoint_every": K, "sub_checkpoint_every": k2, "adjoint_forward_ms": a_fwd_ms,
+                     "adjoint_reverse_ms": a_bwd_ms, "ratio": (a_fwd_ms + a_bwd_ms) / fwd_ms,
+                     "buffer_bytes": int(sim._adj.numel()), "gradient": {"a0": grad[-2], "w0": grad[-1]}}
+        sim.close()
+        del fields, cot
+        torch.cuda.empty_cache()
+    return out
 
 
 def make_sim(P, st, slots_per_cell, stream, explicit_ions, advance):

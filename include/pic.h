@@ -192,7 +192,11 @@ typedef struct pic_diag {
 /* ---------------------------------------------------------------- set-up */
 
 /* Validates the parameters and creates a context.  PIC_ERR_CFL if cfl >= 1,
-   PIC_ERR_ARG for any other invalid field.  *out is NULL on failure. */
+   PIC_ERR_ARG for any other invalid field.  *out is NULL on failure.
+   Paper: the stage is simulated in a frame boosted to gamma_boost along the
+   laser axis (introduction: the boost contracts the plasma and dilates the
+   laser, so far fewer steps are needed); the cell sizes keep the cells per
+   Doppler-stretched laser wavelength. */
 pic_status pic_init_grid(const pic_grid_params *p, pic_ctx **out);
 
 /* Buffer sizes and derived quantities of a context. */
@@ -203,7 +207,11 @@ pic_status pic_query_sizes(const pic_ctx *ctx, pic_sizes *out);
    at least the queried sizes.  May be called once per context. */
 pic_status pic_bind_buffers(pic_ctx *ctx, const pic_buffers *b);
 
-/* Generates the plasma on the device: every lattice point whose simulation-
+/* Paper: a plasma at rest in the laboratory, seen from the boosted frame
+   through the Lorentz transformation (the hyperbolic rotation of section
+   "Effect of the hyperbolic rotation in Minkowski space"): density gamma n,
+   drift -beta, contracted by gamma, entering the box as the frame moves.
+   Generates the plasma on the device: every lattice point whose simulation-
    frame position at the current time lies in the box becomes an electron
    (and, boosted with ions, a drifting ion at the same place); the rest of a
    boosted plasma is injected as it crosses z = Lz.  Lab-frame immobile ions
@@ -229,13 +237,21 @@ pic_status pic_load_plasma(pic_ctx *ctx, const pic_plasma_params *p);
 pic_status pic_load_particles(pic_ctx *ctx, int species, int64_t n, const double *state,
                               const int64_t *ids);
 
-/* Sets the laser; the antenna current is added in every later step. */
+/* Sets the laser; the antenna current is added in every later step.
+   Paper: the laser is launched in the boosted frame, its lab-frame pulse
+   Doppler-transformed (amplitude and frequency gamma (1 - beta), duration
+   gamma (1 + beta); section "Effect of the hyperbolic rotation in Minkowski
+   space"). */
 pic_status pic_launch_laser(pic_ctx *ctx, const pic_laser_params *p);
 
 /* ------------------------------------------------------------------ step */
 
 /* Advances nsteps full steps, synchronises the stream and checks the device
-   error word (PIC_ERR_CAPACITY / PIC_ERR_CFL / PIC_ERR_NAN). */
+   error word (PIC_ERR_CAPACITY / PIC_ERR_CFL / PIC_ERR_NAN / PIC_ERR_TIMEOUT).
+   Paper: one step of the particle-in-cell loop the paper's runs use (the
+   electromagnetic PIC method named in section "Effect of the hyperbolic
+   rotation in Minkowski space"), with the current filtered against short
+   wavelengths as in section "Mitigation of a numerical instability". */
 pic_status pic_step(pic_ctx *ctx, int nsteps);
 
 /* Same as pic_step without the synchronisation and the error check. */
@@ -279,7 +295,8 @@ pic_status pic_get_axis(pic_ctx *ctx, int component, void *dst, size_t dst_bytes
                         int dst_is_device);
 
 /* Live particles of a species as host FP64 arrays in the pic_load_particles
-   layout (order unspecified); *n_out receives the count.  With dst == NULL
+   layout (order unspecified); *n_out receives the count.  (Paper: the
+   macroparticles of the PIC method; simulation-frame positions and momenta.)  With dst == NULL
    only *n_out is set.  ids (may be NULL) receives the lattice ids when
    track_ids is set. */
 pic_status pic_get_particles(pic_ctx *ctx, int species, double *dst, size_t dst_bytes,
@@ -290,7 +307,12 @@ pic_status pic_get_particles(pic_ctx *ctx, int species, double *dst, size_t dst_
    device memory.  Lab-frame immobile ions are not included. */
 pic_status pic_get_rho(pic_ctx *ctx, void *dst, size_t dst_bytes, int dst_is_device);
 
-/* Time, counts and FP64 Kahan-compensated sums (synchronises the stream). */
+/* Time, counts and FP64 Kahan-compensated sums (synchronises the stream):
+   field energy (1/2) sum (E^2 + B^2) V over each component's valid nodes,
+   electron kinetic energy sum w (gamma - 1), charge sum q w (drifting ions
+   +1; lab-frame immobile ions are a background), both energies in units of
+   n_c m c^2 lambda0^3.  (Paper: no counterpart; the energy budget of the
+   stage.) */
 pic_status pic_get_diagnostics(pic_ctx *ctx, pic_diag *out);
 
 /* ------------------------------------------------------------------ batch */
@@ -407,10 +429,18 @@ pic_status pic_btd_get(pic_ctx *ctx, int j, void *dst, size_t dst_bytes, int dst
 typedef struct {
     int nsteps;            /* N >= 1                                          */
     int checkpoint_every;  /* K >= 1: checkpoints at steps 0, K, 2K, ...      */
+    int sub_checkpoint_every; /* K2: 0 (or >= K) one level: a segment's K + 1 */
+                           /* states are all kept while it is reversed;       */
+                           /* 0 < K2 < K: two levels: the segment is first    */
+                           /* recomputed once leaving a state every K2 steps, */
+                           /* then each K2-step piece is recomputed and       */
+                           /* reversed, so K2 + 1 + ceil(K / K2) states are   */
+                           /* kept instead of K + 1 (one more forward pass)   */
 } pic_adjoint_params;
 
-/* Bytes of the device buffer an adjoint run needs (checkpoints, one segment
-   of K + 1 states, cotangents).  PIC_ERR_ARG for an unsupported run,
+/* Bytes of the device buffer an adjoint run needs (ceil(N / K) checkpoints,
+   one segment of K + 1 states or, with sub-checkpoints, K2 + 1 states and
+   ceil(K / K2) sub-checkpoints, the cotangents).  PIC_ERR_ARG for an unsupported run,
    PIC_ERR_STATE if a step has been taken since pic_load_plasma. */
 pic_status pic_adjoint_bytes(pic_ctx *ctx, const pic_adjoint_params *p, size_t *bytes);
 

@@ -101,7 +101,7 @@ class BtdParams(C.Structure):
 
 class AdjointParams(C.Structure):
     """pic_adjoint_params: N steps, a checkpoint every K."""
-    _fields_ = [("nsteps", C.c_int), ("checkpoint_every", C.c_int)]
+    _fields_ = [("nsteps", C.c_int), ("checkpoint_every", C.c_int), ("sub_checkpoint_every", C.c_int)]
 
 
 def _load():
@@ -501,11 +501,11 @@ class Simulation:
         return {c: vals[q] for q, c in enumerate(names)}, filled
 
 
-    def adjoint_forward(self, nsteps, checkpoint_every=50):
+    def adjoint_forward(self, nsteps, checkpoint_every=50, sub_checkpoint_every=0):
         """Forward run of the adjoint (from right after load_plasma and
         launch_laser): returns E^N, B^N as a (6, nz+1, nx) device tensor in 2D,
         (6, nz+1, ny, nx) in 3D, and keeps the checkpoints for adjoint_backward."""
-        p = AdjointParams(int(nsteps), int(checkpoint_every))
+        p = AdjointParams(int(nsteps), int(checkpoint_every), int(sub_checkpoint_every))
         nbytes = pic_adjoint_bytes(self.ctx, p)
         self._adj = self.torch.empty(nbytes, dtype=self.torch.uint8, device=self.device)
         self._adj_n = self._prof_n
@@ -549,7 +549,8 @@ class StageGradient:
                 l = settings["laser"]
                 sim.launch_laser(float(a0), l["waist"] if w0 is None else float(w0), l["fwhm"],
                                  l.get("z_antenna", 0.0), l.get("t_peak", -1.0), l.get("pol", PIC_POL_Y))
-                out = sim.adjoint_forward(settings["nsteps"], settings.get("checkpoint_every", 50))
+                out = sim.adjoint_forward(settings["nsteps"], settings.get("checkpoint_every", 50),
+                                          settings.get("sub_checkpoint_every", 0))
                 ctx.sim = sim
                 ctx.m = coef.numel()
                 ctx.inputs = (coef, a0, w0)

@@ -119,7 +119,7 @@ struct pic_ctx {
     struct {
         bool ready = false;
         bool last_seg_ready = false;  // the forward left its last segment's states in place
-        int N = 0, K = 0;
+        int N = 0, K = 0, K2 = 0;
         int64_t P = 0;
         std::vector<int64_t> base, mlo, mhi;
         std::vector<double> tn;
@@ -1879,9 +1879,10 @@ namespace {
 struct AdjLayout {
     int64_t P = 0;
     int N = 0, K = 0, C = 0;
+    int K2 = 0, CS = 0;  // second level: sub-checkpoints every K2 steps of a segment (CS of them), 0: none
     size_t w = 0, zeta = 0, ion_ci = 0, ion_ox = 0, ion_cj = 0, ion_oy = 0;  // per slot, constant
     size_t st = 0, fl = 0;                           // one particle state, one field state (6 comps)
-    size_t ckpt = 0, seg = 0;                        // C and K + 1 (state, fields) pairs
+    size_t ckpt = 0, seg = 0, sub = 0;               // C, KS + 1 and CS (state, fields) pairs
     size_t J = 0, tmp = 0, lE = 0, lB = 0, lE0 = 0, pE = 0, lJ = 0;  // 3 components each
     size_t lx = 0, ly = 0, lz = 0, lux = 0, luy = 0, luz = 0, lw = 0, acc = 0, coef = 0, planes = 0;
     size_t total = 0;
@@ -1890,7 +1891,9 @@ struct AdjLayout {
     size_t i_ck = 0, i_oz = 0, i_alive = 0, fm = 0;
 };
 
-AdjLayout adj_layout(int64_t P, int N, int K, size_t es, int64_t ncomp, bool dim3, int64_t nz1)
+// K2 > 0 (and < K): segments are recomputed in two levels, so the segment
+// buffer holds K2 + 1 states and ceil(K / K2) sub-checkpoints instead of K + 1
+AdjLayout adj_layout(int64_t P, int N, int K, int K2, size_t es, int64_t ncomp, bool dim3, int64_t nz1)
 {
     const int64_t P3 = dim3 ? P : 0;  // y arrays only in 3D
     AdjLayout L;
@@ -1898,6 +1901,8 @@ AdjLayout adj_layout(int64_t P, int N, int K, size_t es, int64_t ncomp, bool dim
     L.N = N;
     L.K = K;
     L.C = (N + K - 1) / K;
+    L.K2 = (K2 > 0 && K2 < K) ? K2 : 0;
+    L.CS = L.K2 ? (K + L.K2 - 1) / L.K2 : 0;
     size_t o = 0;
     auto take = [&](size_t bytes) {
         const size_t at = o;
@@ -1934,7 +1939,8 @@ AdjLayout adj_layout(int64_t P, int N, int K, size_t es, int64_t ncomp, bool dim
     L.ion_cj = take(4 * P3);
     L.ion_oy = take(es * P3);
     L.ckpt = take((size_t)L.C * (L.st + L.fl));
-    L.seg = take((size_t)(K + 1) * (L.st + L.fl));
+    L.seg = take((size_t)((L.K2 ? L.K2 : K) + 1) * (L.st + L.fl));
+    L.sub = take((size_t)L.CS * (L.st + L.fl));
     L.J = take(3 * es * ncomp);
     L.tmp = take(3 * es * ncomp);
     L.lE = take(3 * es * ncomp);
@@ -2011,7 +2017,8 @@ static pic_status adj_check(pic_ctx *c, const pic_adjoint_params *p)
 {
     if (!c || !p) return PIC_ERR_ARG;
     if (!c->bound) return fail(c, PIC_ERR_STATE, "bind buffers first");
-    if (p->nsteps < 1 || p->checkpoint_every < 1) return fail(c, PIC_ERR_ARG, "invalid adjoint parameters");
+    if (p->nsteps < 1 || p->checkpoint_every < 1 || p->sub_checkpoint_every < 0)
+        return fail(c, PIC_ERR_ARG, "invalid adjoint parameters");
     if (c->win_on) return fail(c, PIC_ERR_ARG, "the adjoint does not cover a moving window");
     if (!c->plasma_loaded || c->step != 0)
         return fail(c, PIC_ERR_STATE, "the adjoint starts right after pic_load_plasma (no step taken)");
@@ -2024,8 +2031,8 @@ extern "C" pic_status pic_adjoint_bytes(pic_ctx *c, const pic_adjoint_params *p,
     if (st != PIC_OK) return st;
     if (!bytes) return PIC_ERR_ARG;
     adj_bands(c, p->nsteps);
-    *bytes = adj_layout(c->adj.P, p->nsteps, p->checkpoint_every, (size_t)c->es, c->g.ncomp, c->g.dim == 3,
-                        c->g.nz + 1)
+    *bytes = adj_layout(c->adj.P, p->nsteps, p->checkpoint_every, p->sub_checkpoint_every, (size_t)c->es,
+                        c->g.ncomp, c->g.dim == 3, c->g.nz + 1)
                  .total;
     return PIC_OK;
 }
@@ -2149,7 +2156,8 @@ static pic_status adj_forward_t(pic_ctx *c, const pic_adjoint_params *p, void *f
 {
     auto &A = c->adj;
     const AdjLayout L =
-        adj_layout(A.P, p->nsteps, p->checkpoint_every, sizeof(real), c->g.ncomp, c->g.dim == 3, c->g.nz + 1);
+        adj_layout(A.P, p->nsteps, p->checkpoint_every, p->sub_checkpoint_every, sizeof(real), c->g.ncomp,
+                   c->g.dim == 3, c->g.nz + 1);
     unsigned char *B = A.buf;
     unsigned char *seg = B + L.seg;
     auto st = [&](int s) { return seg + (size_t)s * (L.st + L.fl); };
@@ -2178,8 +2186,9 @@ static pic_status adj_forward_t(pic_ctx *c, const pic_adjoint_params *p, void *f
     }
     // steps before the last segment alternate between slots 0 and 1; the last
     // segment's states are kept in the slots the reverse sweep reads them
-    // from, so that its first segment needs no recomputation
-    const int nlast = (L.C - 1) * L.K;
+    // from, so that its first segment needs no recomputation (one-level
+    // schedule; with sub-checkpoints every step alternates)
+    const int nlast = L.K2 ? L.N + 1 : (L.C - 1) * L.K;
     for (int n = 0; n < L.N; ++n) {
         int a = n & 1, b = a ^ 1;
         if (n == nlast && a == 1) {
@@ -2195,11 +2204,13 @@ static pic_status adj_forward_t(pic_ctx *c, const pic_adjoint_params *p, void *f
     }
     CUDA_TRY(c, cudaGetLastError());
     if (fields_out)
-        CUDA_TRY(c, cudaMemcpyAsync(fields_out, fl(L.N - nlast), fbytes, cudaMemcpyDeviceToDevice, c->stream));
-    A.last_seg_ready = true;
+        CUDA_TRY(c, cudaMemcpyAsync(fields_out, fl(L.K2 ? (L.N & 1) : L.N - nlast), fbytes, cudaMemcpyDeviceToDevice,
+                                    c->stream));
+    A.last_seg_ready = L.K2 == 0;
     A.ready = true;
     A.N = L.N;
     A.K = L.K;
+    A.K2 = L.K2;
     return check_device_error(c);
 }
 
@@ -2211,8 +2222,8 @@ extern "C" pic_status pic_adjoint_forward(pic_ctx *c, const pic_adjoint_params *
     c->epoch += 1;
     if (!buf) return PIC_ERR_ARG;
     adj_bands(c, p->nsteps);
-    if (bytes < adj_layout(c->adj.P, p->nsteps, p->checkpoint_every, (size_t)c->es, c->g.ncomp, c->g.dim == 3,
-                           c->g.nz + 1)
+    if (bytes < adj_layout(c->adj.P, p->nsteps, p->checkpoint_every, p->sub_checkpoint_every, (size_t)c->es,
+                           c->g.ncomp, c->g.dim == 3, c->g.nz + 1)
                     .total)
         return fail(c, PIC_ERR_ARG, "adjoint buffer too small");
     c->adj.buf = (unsigned char *)buf;
@@ -2225,7 +2236,7 @@ template <typename real>
 static pic_status adj_backward_t(pic_ctx *c, const void *cot, double *grad)
 {
     auto &A = c->adj;
-    const AdjLayout L = adj_layout(A.P, A.N, A.K, sizeof(real), c->g.ncomp, c->g.dim == 3, c->g.nz + 1);
+    const AdjLayout L = adj_layout(A.P, A.N, A.K, A.K2, sizeof(real), c->g.ncomp, c->g.dim == 3, c->g.nz + 1);
     unsigned char *B = A.buf;
     const int64_t nc = c->g.ncomp;
     unsigned char *seg = B + L.seg;
@@ -2251,14 +2262,9 @@ static pic_status adj_backward_t(pic_ctx *c, const void *cot, double *grad)
     CUDA_TRY(c, cudaMemsetAsync(B + L.acc, 0, 16, c->stream));
     const pic_laser_params &l = c->laser;
     const int comp = l.polarization == PIC_POL_X ? 0 : 1;
-    for (int sgi = L.C - 1; sgi >= 0; --sgi) {
-        const int n0 = sgi * L.K, n1 = std::min(L.N, n0 + L.K);
-        if (sgi == L.C - 1 && A.last_seg_ready) {
-            A.last_seg_ready = false;  // kept by the forward run, used once
-        } else {
-            CUDA_TRY(c, cudaMemcpyAsync(st(0), ck_st(sgi), L.st + L.fl, cudaMemcpyDeviceToDevice, c->stream));
-            for (int s = 0; s < n1 - n0; ++s) adj_step<real>(c, L, st(s), st(s + 1), fl(s), fl(s + 1), n0 + s);
-        }
+    auto sub_st = [&](int q) { return B + L.sub + (size_t)q * (L.st + L.fl); };
+    // the reverse sweep over the states st(0..n1 - n0) of steps n0..n1 - 1
+    auto reverse = [&](int n0, int n1) -> pic_status {
         for (int s = n1 - n0 - 1; s >= 0; --s) {
             const int n = n0 + s;
             // the current cotangent before the filter goes to the scratch
@@ -2300,6 +2306,37 @@ static pic_status adj_backward_t(pic_ctx *c, const void *cot, double *grad)
             a.lj_plane = B + L.planes;
             a.f_plane = st(s) + L.fm;  // made by the forward step from this state
             launch_adj_push_vjp<real>(a, c->stream);
+        }
+        return PIC_OK;
+    };
+    for (int sgi = L.C - 1; sgi >= 0; --sgi) {
+        const int n0 = sgi * L.K, n1 = std::min(L.N, n0 + L.K);
+        if (sgi == L.C - 1 && A.last_seg_ready) {
+            A.last_seg_ready = false;  // kept by the forward run, used once
+            reverse(n0, n1);
+        } else if (!L.K2) {
+            CUDA_TRY(c, cudaMemcpyAsync(st(0), ck_st(sgi), L.st + L.fl, cudaMemcpyDeviceToDevice, c->stream));
+            for (int s = 0; s < n1 - n0; ++s) adj_step<real>(c, L, st(s), st(s + 1), fl(s), fl(s + 1), n0 + s);
+            reverse(n0, n1);
+        } else {
+            // two levels: the segment once through slots 0 and 1, leaving a
+            // sub-checkpoint every K2 steps, then each sub-segment again with
+            // all its states, backwards
+            CUDA_TRY(c, cudaMemcpyAsync(sub_st(0), ck_st(sgi), L.st + L.fl, cudaMemcpyDeviceToDevice, c->stream));
+            CUDA_TRY(c, cudaMemcpyAsync(st(0), ck_st(sgi), L.st + L.fl, cudaMemcpyDeviceToDevice, c->stream));
+            for (int s = 0; s + 1 < n1 - n0; ++s) {
+                const int a = s & 1, b = a ^ 1;
+                adj_step<real>(c, L, st(a), st(b), fl(a), fl(b), n0 + s);
+                if ((s + 1) % L.K2 == 0)
+                    CUDA_TRY(c, cudaMemcpyAsync(sub_st((s + 1) / L.K2), st(b), L.st + L.fl, cudaMemcpyDeviceToDevice,
+                                                c->stream));
+            }
+            for (int m = (n1 - n0 - 1) / L.K2; m >= 0; --m) {
+                const int m0 = n0 + m * L.K2, m1 = std::min(n1, m0 + L.K2);
+                CUDA_TRY(c, cudaMemcpyAsync(st(0), sub_st(m), L.st + L.fl, cudaMemcpyDeviceToDevice, c->stream));
+                for (int s = 0; s < m1 - m0; ++s) adj_step<real>(c, L, st(s), st(s + 1), fl(s), fl(s + 1), m0 + s);
+                reverse(m0, m1);
+            }
         }
     }
     // the profile coefficients enter through every weight

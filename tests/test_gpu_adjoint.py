@@ -117,6 +117,29 @@ def test_gradient_independent_of_checkpoint_interval(O):
     assert np.allclose(g1, g2, rtol=1e-11, atol=0)
 
 
+@pytest.mark.parametrize("K,K2", [(20, 5), (NSTEPS, 7), (25, 4)])
+def test_two_level_checkpoints_same_gradient_less_memory(O, K, K2):
+    # segments recomputed in two levels (a sub-checkpoint every K2 steps):
+    # the same gradient as with every state of a segment kept, from a
+    # smaller buffer (K2 + 1 + ceil(K / K2) states instead of K + 1)
+    import torch
+
+    import paper_1011_0917_gb300 as P
+    _, g1 = gpu_run(O, FP64, K=NSTEPS)
+    sim, _ = make_pair(O, G, FP64)
+    sim.load_plasma(PLASMA["ne"], PLASMA["z_start"], PLASMA["z_end"], PLASMA["ramp"], PLASMA["ppc"],
+                    PLASMA["jitter"], COEF, 1)
+    sim.launch_laser(LASER["a0"], LASER["waist"], LASER["fwhm"], 0.0, LASER["t_peak"], 1)
+    one = P.pic_adjoint_bytes(sim.ctx, P.AdjointParams(NSTEPS, K, 0))
+    two = P.pic_adjoint_bytes(sim.ctx, P.AdjointParams(NSTEPS, K, K2))
+    assert two < one
+    fields = sim.adjoint_forward(NSTEPS, K, K2)
+    assert sim._adj.numel() == two
+    lam = torch.as_tensor(cotangent(G["nz"], G["nx"]), dtype=fields.dtype, device=fields.device)
+    g2 = sim.adjoint_backward(lam)
+    assert np.allclose(g1, g2, rtol=1e-11, atol=0), (g1, g2)
+
+
 def test_lab_frame_gradient_matches_oracle_finite_differences(O):
     # the same objective in the lab frame (gamma = 1: immobile ions, no
     # injection) on the c0 grid spacing, plasma from 6 cells on
