@@ -25,13 +25,14 @@ def gamma_excess(ux, uy, uz, U: float) -> np.ndarray:
     return num / (np.sqrt(1.0 + ux * ux + uy * uy + uz * uz) + np.sqrt(1.0 + U * U))
 
 
-def growth_rate(steps, values, lo: float = 1e-12, hi: float = 1e-6):
+def growth_rate(steps, values, lo: float = 1e-7, hi: float = 1e-5):
     """Exponential growth rate per step of a sampled amplitude over the samples
     in (lo, hi) (least-squares slope of its logarithm), and the number of
-    samples used.  The on-axis Ez of the gamma = 130 stage is exactly zero
-    until the numerical instability of the streaming plasma sets in; its rate
-    of growth is a property of the discrete scheme, not of the round-off that
-    seeds it."""
+    samples used.  The on-axis Ez of the gamma = 130 stage holds only
+    round-off until the numerical instability of the streaming plasma sets
+    in; once its fastest mode dominates (the default window: two decades
+    below saturation, well above either side's round-off) the rate of growth
+    is a property of the discrete scheme, not of the round-off that seeds it."""
     s = np.asarray(steps, dtype=np.float64)
     v = np.asarray(values, dtype=np.float64)
     m = (v > lo) & (v < hi)

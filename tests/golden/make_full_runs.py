@@ -7,6 +7,7 @@ numerical instability that sets it at gamma = 130.  It calls only the oracle
 and the workload recipes; each run takes tens of minutes on one core.
 
     python tests/golden/make_full_runs.py [c1] [c3_small]
+    python tests/golden/make_full_runs.py --rates-only   (rates from the stored histories)
 """
 import json
 import os
@@ -53,9 +54,25 @@ def run(name: str) -> dict:
             "host": platform.machine()}
 
 
+def rates_only(path):
+    """Recompute the growth rates from the stored oracle histories (after a
+    change of the fit window; no oracle run)."""
+    out = json.load(open(path))
+    for name, res in out.items():
+        if isinstance(res, dict) and "ez_history" in res:
+            steps = [(i + 1) * res["sample"] for i in range(len(res["ez_history"]))]
+            res["ez_growth_rate"], res["ez_growth_samples"] = fullrun.growth_rate(steps, res["ez_history"])
+            print(name, res["ez_growth_rate"], res["ez_growth_samples"])
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1, sort_keys=True)
+
+
 def main():
     names = sys.argv[1:] or ["c1", "c3_small"]
     path = os.path.join(HERE, "full_runs.json")
+    if names == ["--rates-only"]:
+        rates_only(path)
+        return
     O.build_oracle()
     for name in names:
         res = run(name)
