@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--slots-per-cell", type=float, default=10.0)
+    ap.add_argument("--sort-every", type=int, default=0,
+                    help="order every tile's particles by cell before every N-th step (0: never)")
     ap.add_argument("--advance", type=int, default=-1,
                     help="stage steps run before the warm-up (default: half the stage, so that the timed window "
                          "sits in the middle of the stage, where the laser has reached the plasma in the box)")
@@ -191,6 +193,8 @@ def run_ours(args, rank, world, local):
     advance = st.steps // 2 if args.advance < 0 else args.advance
     sim = make_sim(P, st, args.slots_per_cell, stream, args.explicit_ions, advance)
     ctx = sim.ctx
+    if args.sort_every > 0:
+        P.pic_set_cell_sort(ctx, args.sort_every)
 
     def barrier():
         if world > 1:
@@ -237,8 +241,10 @@ def run_ours(args, rank, world, local):
                   else (52.0 + 36.0 / 4) * n_e + 32.0 * n_ir)
     achieved = algo_bytes / (push_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
-    phases = ["zero_j", "push", "ions", "antenna", "filter", "yee", "inject", "time"]
-    share = {phases[i]: round(phase_ms[i] / max(sum(phase_ms), 1e-30), 4) for i in range(7)}
+    # (slot 7, the TIME phase's, holds the cell sorts)
+    phases = ["zero_j", "push", "ions", "antenna", "filter", "yee", "inject", "cell_sort"]
+    share = {phases[i]: round(phase_ms[i] / max(sum(phase_ms), 1e-30), 4) for i in range(8)
+             if i < 7 or phase_calls[7] > 0}
 
     # end to end through the C ABI: restore the initial state from pinned host
     # memory, then each step read the on-axis E_z line back to the host
@@ -339,7 +345,7 @@ def run_ours(args, rank, world, local):
             "config": {"workload": workload_name(args.workload), "n_electrons": n_e, "n_drift_ions": n_i,
                        "grid": [g["nx"], g["ny"], g["nz"]], "gamma_boost": g["gamma_boost"],
                        "filter_passes": g["filter_passes"], "shape_order": g["shape_order"],
-                       "slots_per_cell": args.slots_per_cell,
+                       "slots_per_cell": args.slots_per_cell, "cell_sort_every": args.sort_every,
                        "timed_window": f"steps {advance + args.warmup}..{advance + args.warmup + args.steps - 1} "
                                        f"of the {st.steps}-step stage",
                        "ion_records": "explicit" if args.explicit_ions else "paired with electrons until released",
@@ -401,17 +407,24 @@ def run_c4(P, torch, nruns, warmup, steps, graph_steps=20):
     torch.cuda.synchronize()
     t_streams = time.perf_counter() - t0
     # the same steps as replays of a captured graph: a first call of
-    # graph_steps steps captures it (timed on its own), the batch keeps it
+    # graph_steps steps captures it (timed on its own), the batch keeps it;
+    # the per-context graph (every run's launches on its own stream), then
+    # the fused one (one launch per phase over all runs)
     P.pic_batch_set_graph(batch.h, graph_steps)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    batch.step(graph_steps)
-    torch.cuda.synchronize()
-    t_capture = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    batch.step(steps)
-    torch.cuda.synchronize()
-    t_batch = time.perf_counter() - t0
+    timings = {}
+    for fused in (False, True):
+        P.pic_batch_set_fused(batch.h, fused)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        batch.step(graph_steps)
+        torch.cuda.synchronize()
+        t_capture = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        batch.step(steps)
+        torch.cuda.synchronize()
+        timings[fused] = (time.perf_counter() - t0, t_capture, batch.graph_info())
+    t_batch, t_capture, info = timings[True]
+    t_ctx, t_capture_ctx, info_ctx = timings[False]
     # the same runs one after another on a single stream (each pic_step waits)
     t0 = time.perf_counter()
     for s in sims:
@@ -423,14 +436,21 @@ def run_c4(P, torch, nruns, warmup, steps, graph_steps=20):
         s.close()
     torch.cuda.empty_cache()
     return {"runs": nruns, "steps": steps, "electrons": n0, "value": n0 * steps / t_batch,
-            "ms_per_step": 1e3 * t_batch / steps, "graph_steps": graph_steps,
+            "ms_per_step": 1e3 * t_batch / steps, "graph_steps": graph_steps, "fused": info["fused"],
+            "launches_per_step": info["launches_per_replay"] / graph_steps,
             "first_call_ms": 1e3 * t_capture,
+            "per_context_graph_value": n0 * steps / t_ctx, "per_context_graph_ms_per_step": 1e3 * t_ctx / steps,
+            "per_context_launches_per_step": info_ctx["launches_per_replay"] / graph_steps,
+            "per_context_first_call_ms": 1e3 * t_capture_ctx,
             "streams_value": n0 * steps / t_streams, "streams_ms_per_step": 1e3 * t_streams / steps,
             "sequential_value": n0 * steps / t_seq, "speedup_vs_sequential": t_seq / t_batch,
             "note": "2D3V boosted runs, gamma in {5, 13, 30}, nz in [1024, 4096], nx = 128, 2x2 per cell, "
                     "8-coefficient profile, a0 in [0.5, 2]; host wall clock around pic_batch_step (graph: "
                     "graph_steps steps of all runs captured once as one CUDA graph by a first call, timed as "
-                    "first_call_ms, and kept by the batch; the timed call replays it)"}
+                    "first_call_ms, and kept by the batch; the timed call replays it).  value: the fused "
+                    "graph (one launch per phase over all runs, the push a persistent grid over (run, tile) "
+                    "items); per_context_graph: every run's launches on its own stream inside the graph; "
+                    "streams: launch by launch on the runs' streams"}
 
 
 def run_adjoint(P, torch, steps, K, r=0):

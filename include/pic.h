@@ -351,6 +351,29 @@ void pic_batch_destroy(pic_batch *batch);
    later.  PIC_ERR_ARG for a negative or odd count. */
 pic_status pic_batch_set_graph(pic_batch *batch, int steps_per_graph);
 
+/* The form of the captured graph.  fused = 1 (the default): where every
+   launch of every context's steps has a batched form (all do, except the
+   per-pass filter path for more than 4 passes), each phase of each step is
+   one launch over the work items of all the runs that issue it (runs whose
+   particle kernels differ in precision, dimension, shape order, tile shape
+   or position form get one launch per kind): the zeroing of the raw
+   currents, the particle push -- a persistent grid whose CTAs take
+   (run, tile) items from a device-wide counter, so runs of uneven size
+   share the GPU to the last tile -- the drifting ions, the antenna, the
+   filter (3D runs take the plane-load filter instead of the TMA one: a
+   tensor map is made per launch), the Yee update and the injection.  Each
+   item is processed by the same code and arithmetic as in a single run's
+   launch, so the results are identical to those of the per-context graph.
+   fused = 0: the per-context graph (every context's launches on its own
+   stream, forked from and joined to the graph's).  A change drops the kept
+   graph.  PIC_ERR_ARG for other values. */
+pic_status pic_batch_set_fused(pic_batch *batch, int fused);
+
+/* The graph the batch keeps (zeros before the first capture): whether it is
+   the fused form, the launches one replay issues (kernels and counter
+   resets) and the steps it covers. */
+pic_status pic_batch_graph_info(pic_batch *batch, int *fused, int64_t *launches_per_replay, int *steps);
+
 /* ---------------------------------------------------------- moving window */
 
 /* Moving window (in the paper's gamma = 1 and gamma = 5 runs the box
@@ -456,6 +479,19 @@ pic_status pic_adjoint_forward(pic_ctx *ctx, const pic_adjoint_params *p, void *
    dL/dw0.  PIC_ERR_STATE without a preceding pic_adjoint_forward. */
 pic_status pic_adjoint_backward(pic_ctx *ctx, const void *cot, double *grad);
 
+/* The gradients of every run of a batch (the scan's reverse mode): for run
+   i, pic_adjoint_forward with p[i] into bufs[i] (bytes[i], from
+   pic_adjoint_bytes) and pic_adjoint_backward with the device cotangents
+   cots[i], its M_i + 2 sums written to grads + i * grad_stride (host;
+   grad_stride >= max M_i + 2).  Every run's forward, then every run's
+   reverse sweep is queued on its own stream without waiting for any of
+   them, so the runs' adjoint kernels execute concurrently; the call returns
+   after one wait per stream, with the first failure (each context's
+   pic_last_error has its detail).  PIC_ERR_ARG for null arrays or too small
+   a stride. */
+pic_status pic_batch_adjoint(pic_batch *batch, const pic_adjoint_params *p, void *const *bufs,
+                             const size_t *bytes, const void *const *cots, double *grads, int grad_stride);
+
 /* ------------------------------------------------------------ checkpoint */
 
 /* Size of a compact snapshot (fields, live particles, time, laser) now. */
@@ -468,6 +504,23 @@ pic_status pic_get_state(pic_ctx *ctx, void *dst, size_t dst_bytes, int dst_is_d
    PIC_ERR_ARG if it does not match; PIC_ERR_CAPACITY on bucket overflow. */
 pic_status pic_set_state(pic_ctx *ctx, const void *src, size_t src_bytes, int src_is_device);
 
+/* ------------------------------------------------------------- cell order */
+
+/* Orders every tile's bucket of each species by cell (the cell's index in its
+   tile, x fastest, then y, then z; a counting sort per tile into the other
+   half of the double buffer, all of a tile's records then in its bottom
+   run).  The push writes the particles that stay in their tile in the order
+   it read them, so the order decays only by the particles that cross tiles.
+   The results of a step do not depend on the order (the deposit sums in
+   exact fixed point).  Synchronises the stream. */
+pic_status pic_sort_cells(pic_ctx *ctx);
+
+/* Sort by cell before every `every`-th step (the step count a multiple of
+   every; 0, the default: never).  A context that sorts is stepped launch by
+   launch (a batch does not capture it in a graph).  PIC_ERR_ARG for
+   every < 0. */
+pic_status pic_set_cell_sort(pic_ctx *ctx, int every);
+
 /* -------------------------------------------------------------- profiling */
 
 /* While enabled, every phase of later steps is bracketed by CUDA events on the
@@ -475,9 +528,10 @@ pic_status pic_set_state(pic_ctx *ctx, const void *src, size_t src_bytes, int sr
 pic_status pic_profile(pic_ctx *ctx, int enable);
 
 /* Accumulated device time since the last read: ms[i] milliseconds and calls[i]
-   runs of phase bit i (i = 0..7, PIC_PH_ZERO_J .. PIC_PH_TIME), *kernels the
-   number of kernel launches.  Synchronises the stream and resets the sums.
-   Any output pointer may be NULL. */
+   runs of phase bit i (i = 0..6, PIC_PH_ZERO_J .. PIC_PH_INJECT; slot 7, the
+   TIME phase's, which launches nothing, holds the cell sorts of
+   pic_set_cell_sort), *kernels the number of kernel launches.  Synchronises
+   the stream and resets the sums.  Any output pointer may be NULL. */
 pic_status pic_profile_read(pic_ctx *ctx, double ms[8], int64_t calls[8], int64_t *kernels);
 
 /* --------------------------------------------- allocation-free current filter */

@@ -26,6 +26,7 @@ __all__ = [
     "pic_btd_setup", "pic_btd_get", "pic_set_moving_window", "pic_batch_create", "pic_batch_step",
     "pic_batch_destroy", "Simulation", "Batch", "library_path", "AdjointParams", "pic_adjoint_bytes",
     "pic_adjoint_forward", "pic_adjoint_backward", "StageGradient", "pic_batch_set_graph", "pic_wait_check",
+    "pic_batch_set_fused", "pic_batch_graph_info", "pic_batch_adjoint", "pic_sort_cells", "pic_set_cell_sort",
     "PIC_FRAME_BOOST", "PIC_FRAME_LAB",
 ]
 
@@ -142,6 +143,12 @@ def _load():
         "pic_batch_step": (S, [P, I]),
         "pic_batch_destroy": (None, [P]),
         "pic_batch_set_graph": (S, [P, I]),
+        "pic_batch_set_fused": (S, [P, I]),
+        "pic_sort_cells": (S, [P]),
+        "pic_set_cell_sort": (S, [P, I]),
+        "pic_batch_adjoint": (S, [P, C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_size_t),
+                                  C.POINTER(C.c_void_p), C.POINTER(C.c_double), I]),
+        "pic_batch_graph_info": (S, [P, C.POINTER(I), C.POINTER(C.c_int64), C.POINTER(I)]),
         "pic_btd_bytes": (S, [P, C.POINTER(BtdParams), C.POINTER(C.c_size_t)]),
         "pic_btd_setup": (S, [P, C.POINTER(BtdParams), P, C.c_size_t]),
         "pic_btd_get": (S, [P, I, P, C.c_size_t, I]),
@@ -334,6 +341,44 @@ def pic_batch_set_graph(batch, steps_per_graph: int):
     s = _load().pic_batch_set_graph(batch, int(steps_per_graph))
     if s != PIC_OK:
         raise PicError(s, "pic_batch_set_graph: " + pic_status_string(s))
+
+
+def pic_sort_cells(ctx):
+    _check(ctx, _load().pic_sort_cells(ctx))
+
+
+def pic_set_cell_sort(ctx, every: int):
+    _check(ctx, _load().pic_set_cell_sort(ctx, int(every)))
+
+
+def pic_batch_set_fused(batch, fused: bool):
+    s = _load().pic_batch_set_fused(batch, 1 if fused else 0)
+    if s != PIC_OK:
+        raise PicError(s, "pic_batch_set_fused: " + pic_status_string(s))
+
+
+def pic_batch_graph_info(batch) -> dict:
+    """{"fused", "launches_per_replay", "steps"} of the graph the batch keeps."""
+    f, n, k = C.c_int(), C.c_int64(), C.c_int()
+    s = _load().pic_batch_graph_info(batch, C.byref(f), C.byref(n), C.byref(k))
+    if s != PIC_OK:
+        raise PicError(s, "pic_batch_graph_info: " + pic_status_string(s))
+    return {"fused": bool(f.value), "launches_per_replay": int(n.value), "steps": int(k.value)}
+
+
+def pic_batch_adjoint(batch, params, buf_ptrs, nbytes, cot_ptrs, grad_stride: int):
+    """Gradients of all runs of a batch (pic_batch_adjoint): a list of
+    grad_stride doubles per run."""
+    n = len(params)
+    parr = (AdjointParams * n)(*params)
+    bufs = (C.c_void_p * n)(*buf_ptrs)
+    sizes = (C.c_size_t * n)(*nbytes)
+    cots = (C.c_void_p * n)(*cot_ptrs)
+    g = (C.c_double * (n * grad_stride))()
+    s = _load().pic_batch_adjoint(batch, C.cast(parr, C.c_void_p), bufs, sizes, cots, g, int(grad_stride))
+    if s != PIC_OK:
+        raise PicError(s, "pic_batch_adjoint: " + pic_status_string(s))
+    return [list(g[i * grad_stride:(i + 1) * grad_stride]) for i in range(n)]
 
 
 def pic_batch_destroy(batch):
@@ -577,12 +622,37 @@ class StageGradient:
 
 
 class Batch:
-    """Steps several Simulations together (each on its own stream)."""
+    """Steps several Simulations together: captured graphs of graph_steps
+    steps, in the batched form (one launch per phase over all runs) when
+    fused, else each run's launches on its own stream."""
 
-    def __init__(self, sims, graph_steps=20):
+    def __init__(self, sims, graph_steps=20, fused=True):
         self.sims = list(sims)
         self.h = pic_batch_create([s.ctx for s in self.sims])
         pic_batch_set_graph(self.h, graph_steps)
+        pic_batch_set_fused(self.h, fused)
+
+    def graph_info(self) -> dict:
+        return pic_batch_graph_info(self.h)
+
+    def adjoint(self, nsteps, cots, checkpoint_every=50, sub_checkpoint_every=0):
+        """Gradient of every run's objective sum(cot_r * (E^N, B^N)) (cot_r
+        shaped like Simulation.adjoint_forward's output) with respect to its
+        profile coefficients, a0 and waist, all runs' forward and reverse
+        sweeps queued together (each run from right after its load_plasma and
+        launch_laser): a list per run [dL/dc_1 .. dL/dc_M, dL/da0, dL/dw0]."""
+        ps, bufs, cs = [], [], []
+        for sim, cot in zip(self.sims, cots):
+            p = AdjointParams(int(nsteps), int(checkpoint_every), int(sub_checkpoint_every))
+            nb = pic_adjoint_bytes(sim.ctx, p)
+            bufs.append(sim.torch.empty(nb, dtype=sim.torch.uint8, device=sim.device))
+            cs.append(sim.torch.as_tensor(cot, dtype=sim.dtype, device=sim.device).contiguous())
+            ps.append(p)
+        m = [sim._prof_n for sim in self.sims]
+        stride = max(m) + 2
+        g = pic_batch_adjoint(self.h, ps, [b.data_ptr() for b in bufs], [b.numel() for b in bufs],
+                              [c.data_ptr() for c in cs], stride)
+        return [g[i][:m[i] + 2] for i in range(len(self.sims))]
 
     def step(self, nsteps: int = 1):
         pic_batch_step(self.h, nsteps)

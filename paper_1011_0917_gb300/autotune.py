@@ -8,7 +8,10 @@ the library offers at run time:
   and accumulates currents for, and how many leave their tile per step;
 * the bucket capacity (slots per cell), which sets the memory a tile's
   particle records span;
-* for a batch of runs, the number of steps per captured CUDA graph.
+* for a batch of runs, the launch form: launch by launch on the runs'
+  streams, or captured CUDA graphs of a number of steps, fused (one launch
+  per phase over all runs, the particle push a persistent grid over
+  (run, tile) items) or per context.
 
 Particles are sorted into their tiles at every step, inside the push, so
 there is no sort interval to choose; the CTA shape (256 threads) is compiled.
@@ -74,10 +77,12 @@ def tune_run(settings: dict, steps: int = 8, warmup: int = 3, tiles=None, slots=
     return dict(best, trials=trials)
 
 
-def tune_batch(settings_list, steps: int = 40, warmup: int = 3, graph_steps=(0, 20, 40), tile=(0, 0, 0),
-               slots: float = 8.0) -> dict:
-    """Time pic_batch_step of the runs with each number of steps per captured
-    graph (0: launch by launch); returns the fastest and all trials."""
+def tune_batch(settings_list, steps: int = 40, warmup: int = 3, graph_steps=(0, 20, 40), fused=(True, False),
+               tile=(0, 0, 0), slots: float = 8.0) -> dict:
+    """Time pic_batch_step of the runs for every launch form: launch by launch
+    on the runs' streams (graph_steps 0), and for each number of steps per
+    captured graph, the fused graph (one launch per phase over all runs) and
+    the per-context graph.  Returns the fastest and all trials."""
     import torch
 
     import paper_1011_0917_gb300 as P
@@ -86,18 +91,22 @@ def tune_batch(settings_list, steps: int = 40, warmup: int = 3, graph_steps=(0, 
     try:
         batch = P.Batch(sims, graph_steps=0)
         batch.step(warmup)
-        for k in graph_steps:
+        forms = [(0, False)] + [(k, f) for k in graph_steps if k > 0 for f in fused]
+        for k, f in forms:
             # the runs' work spans their own streams: time on the host between
             # two device-wide synchronisations; a graph is captured by an
             # untimed first call of k steps and kept by the batch
             P.pic_batch_set_graph(batch.h, k)
+            P.pic_batch_set_fused(batch.h, f)
             if k > 0:
                 batch.step(k)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             batch.step(steps)
             torch.cuda.synchronize()
-            trials.append({"graph_steps": k, "ms_per_step": 1e3 * (time.perf_counter() - t0) / steps})
+            info = P.pic_batch_graph_info(batch.h)
+            trials.append({"graph_steps": k, "fused": bool(f and info["fused"]),
+                           "ms_per_step": 1e3 * (time.perf_counter() - t0) / steps})
         batch.close()
     finally:
         for s in sims:

@@ -20,8 +20,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libpic.so")
 
-SOURCES = ["pic_capi.cu", "pic_particles.cu", "pic_fields.cu", "pic_inject.cu", "pic_btd.cu", "pic_noalloc.cu",
-           "pic_adjoint.cu"]
+SOURCES = ["pic_capi.cu", "pic_particles.cu", "pic_batch.cu", "pic_fields.cu", "pic_inject.cu", "pic_btd.cu",
+           "pic_noalloc.cu", "pic_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -10,12 +10,31 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <array>
+#include <atomic>
 #include <new>
 #include <string>
 #include <vector>
 
 using namespace pic;
+
+namespace pic {
+thread_local BatchRecorder *g_rec = nullptr;
+
+int device_sms()
+{
+    constexpr int kDevices = 128;
+    static std::atomic<int> cache[kDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevices) return 1;
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n > 0) return n;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+    cache[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
+}  // namespace pic
 
 namespace {
 
@@ -111,6 +130,7 @@ struct pic_ctx {
     double t = 0;
     int64_t step = 0;
     int64_t epoch = 0;  // bumped by every call that changes what a step launches
+    int sort_every = 0; // order the buckets by cell before every sort_every-th step (0: never)
     std::string err;
 
     // adjoint run: the flat store's bands (slot base and lattice planes of
@@ -125,6 +145,7 @@ struct pic_ctx {
         std::vector<double> tn;
         unsigned char *buf = nullptr;
         size_t bytes = 0;
+        double *hgrad = nullptr;  // pinned: the reverse sweep's sums as they leave the device
     } adj;
 
     // CUDA-graph capture of steps (batch): step cap_s of the graph being
@@ -143,6 +164,7 @@ struct pic_ctx {
     ~pic_ctx()
     {
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+        if (adj.hgrad) cudaFreeHost(adj.hgrad);
     }
 };
 
@@ -886,9 +908,34 @@ static double antenna_j0(const pic_ctx *c, double t, double a0)
     return -amp / (kPi * c->hz);
 }
 
+// Every tile's bucket of each species ordered by cell (sort_cells_kernel),
+// into the other side of its double buffer
+template <typename real>
+static void sort_cells_t(pic_ctx *c)
+{
+    for (int sp = 0; sp < 2; ++sp) {
+        if (sp == 1 && !c->ions_species) break;
+        SortArgs<real> a{};
+        a.g = c->g;
+        a.in = species_view<real>(c, sp, c->cur[sp]);
+        a.out = species_view<real>(c, sp, c->cur[sp] ^ 1);
+        a.in_lo = counts(c, sp, c->cur[sp], 0);
+        a.in_hi = counts(c, sp, c->cur[sp], 1);
+        a.out_lo = counts(c, sp, c->cur[sp] ^ 1, 0);
+        a.err = reinterpret_cast<unsigned *>(c->scratch + c->off_err);
+        launch_sort_cells<real>(a, c->stream);
+        c->cur[sp] ^= 1;
+        c->kernels += 1;
+    }
+}
+
 template <typename real>
 static void run_phases_t(pic_ctx *c, unsigned mask)
 {
+    if ((mask & PIC_PH_PUSH) && c->sort_every > 0 && !c->capturing && c->step % c->sort_every == 0) {
+        PhaseTimer pt(c, 7);
+        sort_cells_t<real>(c);
+    }
     real *F[9];
     for (int q = 0; q < 9; ++q) F[q] = (real *)field_ptr(c, q);
     // When one call zeroes, deposits and filters the current, the raw current
@@ -902,7 +949,7 @@ static void run_phases_t(pic_ctx *c, unsigned mask)
         for (int q = 0; q < 3; ++q) R[q] = tmp + (size_t)q * c->g.ncomp;
     if (mask & PIC_PH_ZERO_J) {
         PhaseTimer pt(c, 0);
-        cudaMemsetAsync(R[0], 0, (size_t)3 * c->g.ncomp * sizeof(real), c->stream);
+        launch_zero<real>(R[0], (int64_t)3 * c->g.ncomp, c->stream);
     }
     // With ions paired to their electrons, the electron kernel also takes the
     // tile's drifting ion records, so electron and ion currents add in one
@@ -958,7 +1005,8 @@ static void run_phases_t(pic_ctx *c, unsigned mask)
         unsigned *err = reinterpret_cast<unsigned *>(c->scratch + c->off_err);
         if (!raw_in_tmp) {
             launch_filter<real>(c->g, J, tmp, c->p.filter_passes, c->stream, err);
-        } else if (!launch_filter_from<real>(c->g, tmp, J, c->p.filter_passes, c->stream, err)) {
+        } else if (!launch_filter_from<real>(c->g, tmp, J, c->p.filter_passes, c->stream, err) &&
+                   !record_unsupported()) {
             cudaMemcpyAsync(J[0], tmp, (size_t)3 * c->g.ncomp * sizeof(real), cudaMemcpyDeviceToDevice, c->stream);
             launch_filter<real>(c->g, J, tmp, c->p.filter_passes, c->stream, err);
         }
@@ -1032,14 +1080,21 @@ struct BatchGraph {
     size_t host_n = 0;
     cudaEvent_t join = nullptr;
     std::vector<cudaEvent_t> ev;  // one per context
+    bool fused = false;           // the graph is the batched form (one launch per phase and step)
+    void *fargs = nullptr;        // its argument structs, work-item prefix sums and queue counters
+    int64_t launches = 0;         // its launches per replay (batched kernels and counter resets)
     void drop_graph()
     {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         if (dev) cudaFree(dev);
+        if (fargs) cudaFree(fargs);
         exec = nullptr;
         graph = nullptr;
         dev = nullptr;
+        fargs = nullptr;
+        fused = false;
+        launches = 0;
         K = 0;
         sig.clear();
     }
@@ -1058,6 +1113,7 @@ struct BatchGraph {
 struct pic_batch {
     std::vector<pic_ctx *> ctx;
     int graph_steps = 20;  // steps per captured graph (even; 0: streams only)
+    int fused = 1;         // capture the batched form of the steps where every launch has one
     BatchGraph gr;
 };
 
@@ -1068,7 +1124,7 @@ struct pic_batch {
 static bool batch_capturable(const pic_batch *b)
 {
     for (const pic_ctx *c : b->ctx)
-        if (c->win_on || c->btd_on || c->profiling || c->stream == nullptr) return false;
+        if (c->win_on || c->btd_on || c->profiling || c->sort_every > 0 || c->stream == nullptr) return false;
     return true;
 }
 
@@ -1097,9 +1153,136 @@ static std::array<int64_t, 5> ctx_signature(const pic_ctx *c)
     return {c->epoch, c->fset, c->cur[0], c->cur[1], c->win_n};
 }
 
-// Capture K steps of every context as one graph on the batch's stream: fork
-// every context's stream from it, K steps each, join.  Step s of context i
-// reads its scalars from dev[i K + s].
+// The batched form of K steps of every context.  Each context's steps run on
+// the host with a launch recorder installed (nothing is launched; the
+// double buffers flip K times, K even, so every context ends where it
+// started).  The records are grouped by step, phase and kernel instance, in
+// the order the step issues its phases, and each group becomes one launch
+// over the work items of all its runs, captured on the batch's stream; the
+// persistent particle kernels take their items from a counter zeroed just
+// before them.  ok = false (nothing captured) where some step asked for a
+// launch without a batched form.
+static pic_status batch_capture_fused(pic_batch *b, int K, bool &ok)
+{
+    ok = false;
+    BatchGraph &G = b->gr;
+    const size_t nctx = b->ctx.size();
+    pic_ctx *c0 = b->ctx[0];
+    auto bad = [&](cudaError_t e) {
+        if (e == cudaSuccess) return false;
+        c0->err = std::string("batch graph: ") + cudaGetErrorString(e);
+        return true;
+    };
+    BatchRecorder rec;
+    rec.nctx = (int)nctx;
+    std::vector<int64_t> k0(nctx);
+    for (size_t i = 0; i < nctx; ++i) k0[i] = b->ctx[i]->kernels;
+    g_rec = &rec;
+    for (int s = 0; s < K; ++s)
+        for (size_t i = 0; i < nctx; ++i) {
+            pic_ctx *c = b->ctx[i];
+            rec.step = s;
+            c->capturing = true;
+            c->cap_scal = G.dev + i * K;
+            c->cap_s = s;
+            if (c->es == 4) run_phases_t<float>(c, PIC_PH_ALL);
+            else run_phases_t<double>(c, PIC_PH_ALL);
+            c->capturing = false;
+        }
+    g_rec = nullptr;
+    G.sig.assign(nctx, {});
+    G.kern.assign(nctx, 0);
+    for (size_t i = 0; i < nctx; ++i) {
+        pic_ctx *c = b->ctx[i];
+        G.kern[i] = c->kernels - k0[i];
+        c->kernels = k0[i];
+        G.sig[i] = ctx_signature(c);
+    }
+    if (rec.unsupported || rec.recs.empty()) return PIC_OK;
+    // groups: records of one step and phase with the same kernel instance
+    std::vector<size_t> order(rec.recs.size());
+    for (size_t j = 0; j < order.size(); ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+        const LaunchRecord &X = rec.recs[x], &Y = rec.recs[y];
+        return X.step != Y.step ? X.step < Y.step : X.phase < Y.phase;
+    });
+    struct Group {
+        BatchLaunch fn;
+        bool queue;
+        std::vector<size_t> idx;
+        size_t args_off = 0, start_off = 0, q_off = 0;
+        int64_t total = 0;
+    };
+    std::vector<Group> groups;
+    for (size_t a = 0; a < order.size();) {
+        size_t e = a;
+        const LaunchRecord &A = rec.recs[order[a]];
+        while (e < order.size() && rec.recs[order[e]].step == A.step && rec.recs[order[e]].phase == A.phase) ++e;
+        const size_t first = groups.size();
+        for (size_t j = a; j < e; ++j) {
+            const LaunchRecord &L = rec.recs[order[j]];
+            size_t gi = first;
+            while (gi < groups.size() && groups[gi].fn != L.fn) ++gi;
+            if (gi == groups.size()) groups.push_back(Group{L.fn, L.queue, {}});
+            groups[gi].idx.push_back(order[j]);
+        }
+        a = e;
+    }
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    size_t off = 0;
+    for (Group &g : groups) {
+        const size_t bytes = rec.recs[g.idx[0]].args.size();
+        g.args_off = off;
+        off += al(bytes * g.idx.size());
+        g.start_off = off;
+        off += al(sizeof(int64_t) * (g.idx.size() + 1));
+        if (g.queue) {
+            g.q_off = off;
+            off += 256;
+        }
+    }
+    std::vector<unsigned char> hb(off, 0);
+    for (Group &g : groups) {
+        const size_t bytes = rec.recs[g.idx[0]].args.size();
+        int64_t *st = reinterpret_cast<int64_t *>(hb.data() + g.start_off);
+        st[0] = 0;
+        for (size_t j = 0; j < g.idx.size(); ++j) {
+            const LaunchRecord &L = rec.recs[g.idx[j]];
+            std::memcpy(hb.data() + g.args_off + j * bytes, L.args.data(), bytes);
+            st[j + 1] = st[j] + L.items;
+        }
+        g.total = st[g.idx.size()];
+    }
+    if (bad(cudaMalloc(&G.fargs, off)) || bad(cudaMemcpy(G.fargs, hb.data(), off, cudaMemcpyHostToDevice)))
+        return PIC_ERR_CUDA;
+    unsigned char *d = static_cast<unsigned char *>(G.fargs);
+    if (bad(cudaStreamBeginCapture(G.cs, cudaStreamCaptureModeRelaxed))) return PIC_ERR_CUDA;
+    int64_t launches = 0;
+    for (const Group &g : groups) {
+        if (g.total <= 0) continue;
+        unsigned *q = g.queue ? reinterpret_cast<unsigned *>(d + g.q_off) : nullptr;
+        if (q) {
+            cudaMemsetAsync(q, 0, sizeof(unsigned), G.cs);
+            ++launches;
+        }
+        g.fn(d + g.args_off, reinterpret_cast<const int64_t *>(d + g.start_off), (int)g.idx.size(), g.total, q, G.cs);
+        ++launches;
+    }
+    const cudaError_t e = cudaStreamEndCapture(G.cs, &G.graph);
+    if (bad(e) || bad(cudaGetLastError()) || bad(cudaGraphInstantiate(&G.exec, G.graph, 0))) {
+        G.drop_graph();
+        return PIC_ERR_CUDA;
+    }
+    G.fused = true;
+    G.launches = launches;
+    G.K = K;
+    ok = true;
+    return PIC_OK;
+}
+
+// Capture K steps of every context as one graph on the batch's stream: the
+// batched form where it applies, else fork every context's stream from it,
+// K steps each, join.  Step s of context i reads its scalars from dev[i K + s].
 static pic_status batch_capture(pic_batch *b, int K)
 {
     BatchGraph &G = b->gr;
@@ -1119,6 +1302,11 @@ static pic_status batch_capture(pic_batch *b, int K)
         fill_inject_common(c, a);
         const double jm = a.jitter * a.hz_lab + a.dzl;
         c->inj_planes_max = (int64_t)std::ceil((c->gam * c->beta * c->dt + 2.0 * jm) / a.dzl) + 8;
+    }
+    if (b->fused) {
+        bool ok = false;
+        const pic_status st = batch_capture_fused(b, K, ok);
+        if (st != PIC_OK || ok) return st;
     }
     if (bad(cudaStreamBeginCapture(G.cs, cudaStreamCaptureModeRelaxed))) return PIC_ERR_CUDA;
     cudaEventRecord(G.join, G.cs);
@@ -1155,6 +1343,8 @@ static pic_status batch_capture(pic_batch *b, int K)
         return PIC_ERR_CUDA;
     }
     G.K = K;
+    G.launches = 0;
+    for (int64_t k : G.kern) G.launches += k;
     return PIC_OK;
 }
 
@@ -1235,6 +1425,26 @@ extern "C" pic_status pic_batch_set_graph(pic_batch *b, int steps_per_graph)
     return PIC_OK;
 }
 
+extern "C" pic_status pic_batch_set_fused(pic_batch *b, int fused)
+{
+    if (!b || (fused != 0 && fused != 1)) return PIC_ERR_ARG;
+    if (b->fused != fused) {
+        if (b->gr.cs) cudaStreamSynchronize(b->gr.cs);
+        b->gr.drop_graph();
+    }
+    b->fused = fused;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_batch_graph_info(pic_batch *b, int *fused, int64_t *launches_per_replay, int *steps)
+{
+    if (!b) return PIC_ERR_ARG;
+    if (fused) *fused = b->gr.exec && b->gr.fused ? 1 : 0;
+    if (launches_per_replay) *launches_per_replay = b->gr.exec ? b->gr.launches : 0;
+    if (steps) *steps = b->gr.exec ? b->gr.K : 0;
+    return PIC_OK;
+}
+
 extern "C" pic_status pic_batch_create(pic_ctx *const *ctxs, int n, pic_batch **out)
 {
     if (!out) return PIC_ERR_ARG;
@@ -1276,6 +1486,24 @@ extern "C" pic_status pic_batch_step(pic_batch *b, int nsteps)
 }
 
 extern "C" void pic_batch_destroy(pic_batch *b) { delete b; }
+
+extern "C" pic_status pic_sort_cells(pic_ctx *c)
+{
+    if (!c) return PIC_ERR_ARG;
+    if (!c->bound) return fail(c, PIC_ERR_STATE, "bind buffers first");
+    if (c->es == 4) sort_cells_t<float>(c);
+    else sort_cells_t<double>(c);
+    CUDA_TRY(c, cudaGetLastError());
+    return check_device_error(c);
+}
+
+extern "C" pic_status pic_set_cell_sort(pic_ctx *c, int every)
+{
+    if (!c || every < 0) return PIC_ERR_ARG;
+    c->sort_every = every;
+    c->epoch += 1;
+    return PIC_OK;
+}
 
 extern "C" pic_status pic_step(pic_ctx *c, int nsteps) { return run_steps(c, nsteps, PIC_PH_ALL, true); }
 extern "C" pic_status pic_step_async(pic_ctx *c, int nsteps) { return run_steps(c, nsteps, PIC_PH_ALL, false); }
@@ -2152,7 +2380,7 @@ static void adj_step(pic_ctx *c, const AdjLayout &L, unsigned char *sa, unsigned
 }
 
 template <typename real>
-static pic_status adj_forward_t(pic_ctx *c, const pic_adjoint_params *p, void *fields_out)
+static pic_status adj_forward_t(pic_ctx *c, const pic_adjoint_params *p, void *fields_out, bool defer)
 {
     auto &A = c->adj;
     const AdjLayout L =
@@ -2211,11 +2439,13 @@ static pic_status adj_forward_t(pic_ctx *c, const pic_adjoint_params *p, void *f
     A.N = L.N;
     A.K = L.K;
     A.K2 = L.K2;
-    return check_device_error(c);
+    return defer ? PIC_OK : check_device_error(c);
 }
 
-extern "C" pic_status pic_adjoint_forward(pic_ctx *c, const pic_adjoint_params *p, void *buf, size_t bytes,
-                                          void *fields_out)
+// defer: everything is queued on the context's stream, nothing waits for it
+// (a batch checks the device error word after all its runs)
+static pic_status adjoint_forward(pic_ctx *c, const pic_adjoint_params *p, void *buf, size_t bytes,
+                                  void *fields_out, bool defer)
 {
     pic_status s = adj_check(c, p);
     if (s != PIC_OK) return s;
@@ -2229,11 +2459,20 @@ extern "C" pic_status pic_adjoint_forward(pic_ctx *c, const pic_adjoint_params *
     c->adj.buf = (unsigned char *)buf;
     c->adj.bytes = bytes;
     c->adj.ready = false;
-    return c->es == 4 ? adj_forward_t<float>(c, p, fields_out) : adj_forward_t<double>(c, p, fields_out);
+    return c->es == 4 ? adj_forward_t<float>(c, p, fields_out, defer) : adj_forward_t<double>(c, p, fields_out, defer);
 }
 
+extern "C" pic_status pic_adjoint_forward(pic_ctx *c, const pic_adjoint_params *p, void *buf, size_t bytes,
+                                          void *fields_out)
+{
+    return adjoint_forward(c, p, buf, bytes, fields_out, false);
+}
+
+// The reverse sweep queued on the context's stream; its sums (dL/da0,
+// dL/dw0, then the M profile sums) are copied into the pinned adj.hgrad,
+// which the caller reads after synchronising the stream (adj_grad_out).
 template <typename real>
-static pic_status adj_backward_t(pic_ctx *c, const void *cot, double *grad)
+static pic_status adj_backward_t(pic_ctx *c, const void *cot)
 {
     auto &A = c->adj;
     const AdjLayout L = adj_layout(A.P, A.N, A.K, A.K2, sizeof(real), c->g.ncomp, c->g.dim == 3, c->g.nz + 1);
@@ -2341,18 +2580,26 @@ static pic_status adj_backward_t(pic_ctx *c, const void *cot, double *grad)
     }
     // the profile coefficients enter through every weight
     const int M = c->plasma.n_profile;
-    std::vector<double> h(2 + 16 + 16, 0.0);
+    if (!A.hgrad) CUDA_TRY(c, cudaMallocHost(&A.hgrad, sizeof(double) * (2 + 16 + 16)));
+    double *h = A.hgrad;
     if (M > 0) {
         CUDA_TRY(c, cudaMemcpyAsync(B + L.coef, c->prof, 8 * 16, cudaMemcpyHostToDevice, c->stream));
         CUDA_TRY(c, cudaMemsetAsync(B + L.coef + 8 * 16, 0, 8 * 16, c->stream));
         launch_adj_profile(L.P, (const double *)(B + L.lw), B + L.w, sizeof(real) == 8 ? 1 : 0,
                            (const double *)(B + L.zeta), M, (const double *)(B + L.coef),
                            (double *)(B + L.coef + 8 * 16), c->stream);
-        CUDA_TRY(c, cudaMemcpyAsync(h.data() + 2, B + L.coef + 8 * 16, 8 * M, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(h + 2, B + L.coef + 8 * 16, 8 * M, cudaMemcpyDeviceToHost, c->stream));
     }
-    CUDA_TRY(c, cudaMemcpyAsync(h.data(), B + L.acc, 16, cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(h, B + L.acc, 16, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaGetLastError());
+    return PIC_OK;
+}
+
+// after the stream has been synchronised: grad = dL/dc_1..M, dL/da0, dL/dw0
+static pic_status adj_grad_out(pic_ctx *c, double *grad)
+{
+    const int M = c->plasma.n_profile;
+    const double *h = c->adj.hgrad;
     for (int m = 0; m < M; ++m) grad[m] = h[2 + m];
     grad[M] = h[0];
     grad[M + 1] = h[1];
@@ -2364,7 +2611,47 @@ extern "C" pic_status pic_adjoint_backward(pic_ctx *c, const void *cot, double *
     if (!c || !cot || !grad) return PIC_ERR_ARG;
     c->epoch += 1;
     if (!c->adj.ready) return fail(c, PIC_ERR_STATE, "run pic_adjoint_forward first");
-    return c->es == 4 ? adj_backward_t<float>(c, cot, grad) : adj_backward_t<double>(c, cot, grad);
+    const pic_status s = c->es == 4 ? adj_backward_t<float>(c, cot) : adj_backward_t<double>(c, cot);
+    if (s != PIC_OK) return s;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return adj_grad_out(c, grad);
+}
+
+// The gradients of all runs of a batch: every run's forward, then every
+// run's reverse sweep, each queued on its own stream without waiting, so the
+// runs' adjoint kernels execute concurrently; one wait per stream at the end.
+extern "C" pic_status pic_batch_adjoint(pic_batch *b, const pic_adjoint_params *p, void *const *bufs,
+                                        const size_t *bytes, const void *const *cots, double *grads, int grad_stride)
+{
+    if (!b || !p || !bufs || !bytes || !cots || !grads || grad_stride < 2) return PIC_ERR_ARG;
+    const size_t n = b->ctx.size();
+    for (size_t i = 0; i < n; ++i)
+        if (b->ctx[i]->plasma.n_profile + 2 > grad_stride || !cots[i]) return PIC_ERR_ARG;
+    if (b->gr.cs) cudaStreamSynchronize(b->gr.cs);  // replays of the batch's graph are done
+    pic_status first = PIC_OK;
+    std::vector<char> ok(n, 0);
+    for (size_t i = 0; i < n; ++i) {
+        const pic_status s = adjoint_forward(b->ctx[i], &p[i], bufs[i], bytes[i], nullptr, true);
+        if (s != PIC_OK && first == PIC_OK) first = s;
+        ok[i] = s == PIC_OK;
+    }
+    for (size_t i = 0; i < n; ++i) {
+        if (!ok[i]) continue;
+        pic_ctx *c = b->ctx[i];
+        c->epoch += 1;
+        const pic_status s = c->es == 4 ? adj_backward_t<float>(c, cots[i]) : adj_backward_t<double>(c, cots[i]);
+        if (s != PIC_OK && first == PIC_OK) first = s;
+        ok[i] = s == PIC_OK;
+    }
+    for (size_t i = 0; i < n; ++i) {
+        if (!ok[i]) continue;
+        pic_ctx *c = b->ctx[i];
+        const cudaError_t e = cudaStreamSynchronize(c->stream);
+        pic_status s = e == cudaSuccess ? adj_grad_out(c, grads + i * (size_t)grad_stride)
+                                        : fail(c, PIC_ERR_CUDA, cudaGetErrorString(e));
+        if (s != PIC_OK && first == PIC_OK) first = s;
+    }
+    return first;
 }
 
 // ---------------------------------------------------------------------- misc

@@ -67,9 +67,9 @@ struct YeeArgs {
     int cz, nchunks;          // z planes per chunk, chunks
 };
 
-// column shape of a CTA: 32 x 8 (x, y) in 3D, 256 x 1 in 2D
+// column shape of a CTA of the marching Yee kernel (3D grids; 2D grids take
+// yee2d_kernel): 32 x 8 (x, y)
 template <int DIM> struct YeeTile { static constexpr int TX = 32, TY = 8, HY = 1; };
-template <> struct YeeTile<2> { static constexpr int TX = 256, TY = 1, HY = 0; };
 
 // One Yee step in one pass over the grid.  A CTA owns a column of TX x TY
 // nodes in (x, y) and a chunk of z planes; it marches up the chunk keeping a
@@ -94,7 +94,7 @@ template <> struct YeeTile<2> { static constexpr int TX = 256, TY = 1, HY = 0; }
 // term.  Planes a component does not have (Ez, Bx, By at k = nz; every
 // component at k = nz with periodic z) are neither read nor written.
 template <typename real, int DIM>
-__global__ void __launch_bounds__(256) yee_kernel(YeeArgs<real> a)
+__device__ __forceinline__ void yee_body(const YeeArgs<real> &a, const int bx_, const int by_)
 {
     constexpr int TX = YeeTile<DIM>::TX, TY = YeeTile<DIM>::TY, HY = YeeTile<DIM>::HY;
     constexpr int NT = 256;  // threads; every thread owns at most two nodes of each shared plane
@@ -114,10 +114,10 @@ __global__ void __launch_bounds__(256) yee_kernel(YeeArgs<real> a)
     const Geom &g = a.g;
     const bool per = g.bc_z == 0;
     const int nbx = (g.nx + TX - 1) / TX;
-    const int x0 = (int)(blockIdx.x % nbx) * TX, y0 = (int)(blockIdx.x / nbx) * TY;
+    const int x0 = (bx_ % nbx) * TX, y0 = (bx_ / nbx) * TY;
     const int nzo = per ? g.nz : g.nz + 1;  // planes written
-    const int z0 = (int)blockIdx.y * a.cz;
-    const int z1 = (int)blockIdx.y == a.nchunks - 1 ? nzo : z0 + a.cz;
+    const int z0 = by_ * a.cz;
+    const int z1 = by_ == a.nchunks - 1 ? nzo : z0 + a.cz;
     const int kb = z0 - 1;
     const int tid = (int)threadIdx.x;
     auto r2 = [&](int k) { return (k - kb) & 1; };
@@ -296,6 +296,221 @@ __global__ void __launch_bounds__(256) yee_kernel(YeeArgs<real> a)
     __pipeline_wait_prior(0);
 }
 
+template <typename real, int DIM>
+__global__ void __launch_bounds__(256) yee_kernel(YeeArgs<real> a)
+{
+    yee_body<real, DIM>(a, (int)blockIdx.x, (int)blockIdx.y);
+}
+
+// CTAs of one z column chunk per run of a batch: block b of run r is column
+// b % ncol, chunk b / ncol
+template <typename real, int DIM>
+__global__ void __launch_bounds__(256) yee_batch_kernel(const YeeArgs<real> *__restrict__ runs,
+                                                        const int64_t *__restrict__ start, int n)
+{
+    __shared__ __align__(16) YeeArgs<real> sa;
+    const int64_t b = batch_block(runs, start, n, &sa);
+    constexpr int TX = YeeTile<DIM>::TX, TY = YeeTile<DIM>::TY;
+    const int ncol = ((sa.g.nx + TX - 1) / TX) * (DIM == 3 ? (sa.g.ny + TY - 1) / TY : 1);
+    yee_body<real, DIM>(sa, (int)(b % ncol), (int)(b / ncol));
+}
+
+// ------------------------------------------------------- 2D tiled Yee
+
+// The same Yee step on 2D grids, without the march: a CTA owns a tile of
+// kY2X x kY2Z (x, z) nodes and copies, all at once with cp.async, E^n on
+// x0-1 .. x0+kY2X+1, z0-2 .. z0+kY2Z+1, B^n on x0-1 .. x0+kY2X,
+// z0-2 .. z0+kY2Z and J on x0 .. x0+kY2X, z0-1 .. z0+kY2Z into shared memory
+// (x wraps; planes a component does not have are zero), so that a tile
+// costs one load latency however narrow the grid is (the march pays one
+// per plane, which dominates on grids a few hundred nodes wide).  Then, in
+// shared memory and node by node with the march's arithmetic: Bh in place
+// of B^n, E' in place of E^n on the J region, Mur's condition for the end
+// planes (from the saved E^n of their inner neighbours), and E', B' of the
+// own nodes to the other buffer.  (d/dy = 0: the y derivatives of the 3D
+// formulas are zero terms.)
+constexpr int kY2X = 64, kY2Z = 16;
+constexpr int kY2EX = kY2X + 3, kY2EZ = kY2Z + 4;  // E^n region
+constexpr int kY2BX = kY2X + 2, kY2BZ = kY2Z + 3;  // B^n region
+constexpr int kY2JX = kY2X + 1, kY2JZ = kY2Z + 2;  // J region (where E' is computed)
+
+template <typename real>
+__device__ __forceinline__ void yee2d_body(const YeeArgs<real> &a, const int bx_, const int bz_)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    real *sE = reinterpret_cast<real *>(smem_raw);  // [3][kY2EZ][kY2EX], E^n then E'
+    real *sB = sE + 3 * kY2EZ * kY2EX;              // [3][kY2BZ][kY2BX], B^n then Bh
+    real *sJ = sB + 3 * kY2BZ * kY2BX;              // [3][kY2JZ][kY2JX]
+    real *sM = sJ + 3 * kY2JZ * kY2JX;              // [2 ends][2 comps][kY2EX]: E^n x, y of planes 1, nz-1
+    constexpr int PE = kY2EZ * kY2EX, PB = kY2BZ * kY2BX, PJ = kY2JZ * kY2JX;
+    const Geom &g = a.g;
+    const bool per = g.bc_z == 0;
+    const int nzo = per ? g.nz : g.nz + 1;
+    const int x0 = bx_ * kY2X, z0 = bz_ * kY2Z;
+    const int z1 = z0 + kY2Z < nzo ? z0 + kY2Z : nzo;
+    const int tid = (int)threadIdx.x, nt = (int)blockDim.x;
+    auto mem_plane = [&](int k, bool half) {
+        return per ? wrapi(k, g.nz) : (k >= 0 && k <= zmax_of(g, half) ? k : -1);
+    };
+    auto gx = [&](int x) { return x >= 0 && x < g.nx ? x : wrapi(x, g.nx); };
+    // ---- copy E^n (Ez half-z), B^n (Bx, By half-z), J (Jz half-z)
+    auto stage = [&](const real *src, real *dst, int nx_, int np, int xo, int zo, bool half) {
+        for (int r = tid; r < np; r += nt) {
+            const int pz = r / nx_, px = r - pz * nx_;
+            const int kk = mem_plane(zo + pz, half);
+            if (kk >= 0) __pipeline_memcpy_async(dst + r, src + (int64_t)kk * g.plane + gx(xo + px), sizeof(real));
+            else dst[r] = real(0);
+        }
+    };
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        stage(a.E[c], sE + c * PE, kY2EX, PE, x0 - 1, z0 - 2, c == 2);
+        stage(a.B[c], sB + c * PB, kY2BX, PB, x0 - 1, z0 - 2, c != 2);
+        stage(a.J[c], sJ + c * PJ, kY2JX, PJ, x0, z0 - 1, c == 2);
+    }
+    __pipeline_commit();
+    __pipeline_wait_prior(0);
+    __syncthreads();
+    // the E^n of the planes Mur's condition reads after E' has replaced them
+    const bool mur_lo = !per && z0 - 1 <= 0 && 0 <= z0 + kY2Z - 1;        // plane 0 is computed here
+    const bool mur_hi = !per && z0 - 1 <= g.nz - 1 && g.nz <= z0 + kY2Z;  // plane nz too
+    if (mur_lo || mur_hi) {
+        for (int r = tid; r < 2 * 2 * kY2EX; r += nt) {
+            const int end = r / (2 * kY2EX), c = (r / kY2EX) & 1, px = r % kY2EX;
+            const int k = end == 0 ? 1 : g.nz - 1;
+            const int pz = k - (z0 - 2);
+            sM[r] = (pz >= 0 && pz < kY2EZ) ? sE[c * PE + pz * kY2EX + px] : real(0);
+        }
+    }
+    // ---- Bh(k) = B^n(k) - (dt/2) curl E^n on the whole B region
+    const real zero = real(0);
+    for (int r = tid; r < PB; r += nt) {
+        const int pb = r / kY2BX, xb = r - pb * kY2BX;
+        const int k = z0 - 2 + pb;
+        const int o = pb * kY2EX + xb;  // the same node in the E region
+        const bool vxy = mem_plane(k, true) >= 0, vz = mem_plane(k, false) >= 0;
+        const real dEy_dz = (sE[PE + o + kY2EX] - sE[PE + o]) * a.ihz;
+        const real dEx_dz = (sE[o + kY2EX] - sE[o]) * a.ihz;
+        const real dEz_dx = (sE[2 * PE + o + 1] - sE[2 * PE + o]) * a.ihx;
+        const real dEy_dx = (sE[PE + o + 1] - sE[PE + o]) * a.ihx;
+        sB[r] = vxy ? sB[r] - a.hb * (zero - dEy_dz) : real(0);
+        sB[PB + r] = vxy ? sB[PB + r] - a.hb * (dEx_dz - dEz_dx) : real(0);
+        sB[2 * PB + r] = vz ? sB[2 * PB + r] - a.hb * (dEy_dx - zero) : real(0);
+    }
+    __syncthreads();
+    // ---- E'(k) = E^n(k) + dt (curl Bh - 2 pi J) on x0 .. x0+kY2X, z0-1 .. z0+kY2Z
+    for (int r = tid; r < PJ; r += nt) {
+        const int lz = r / kY2JX, lx = r - lz * kY2JX;
+        const int k = z0 - 1 + lz;
+        const int pe = lz + 1, xe = lx + 1;  // in the E region; the same indices in the B region
+        const int oe = pe * kY2EX + xe, ob = pe * kY2BX + xe;
+        const bool vz = mem_plane(k, true) >= 0;
+        const bool vxy = per || (k >= 1 && k <= g.nz - 1);
+        if (vxy) {
+            const real dBy_dz = (sB[PB + ob] - sB[PB + ob - kY2BX]) * a.ihz;
+            sE[oe] = sE[oe] + a.he * ((zero - dBy_dz) - a.twopi * sJ[r]);
+            const real dBx_dz = (sB[ob] - sB[ob - kY2BX]) * a.ihz;
+            const real dBz_dx = (sB[2 * PB + ob] - sB[2 * PB + ob - 1]) * a.ihx;
+            sE[PE + oe] = sE[PE + oe] + a.he * ((dBx_dz - dBz_dx) - a.twopi * sJ[PJ + r]);
+        }
+        const real dBy_dx = (sB[PB + ob] - sB[PB + ob - 1]) * a.ihx;
+        sE[2 * PE + oe] = vz ? sE[2 * PE + oe] + a.he * ((dBy_dx - zero) - a.twopi * sJ[2 * PJ + r]) : real(0);
+    }
+    __syncthreads();
+    // ---- Mur: Ex, Ey of plane kt from plane kn, its neighbour inside the box
+    if (mur_lo || mur_hi) {
+        for (int r = tid; r < 2 * (kY2X + 1); r += nt) {
+            const int end = r / (kY2X + 1), xe = r % (kY2X + 1) + 1;
+            if (end == 0 ? !mur_lo : !mur_hi) continue;
+            const int kt = end == 0 ? 0 : g.nz, kn = end == 0 ? 1 : g.nz - 1;
+            const int ot = (kt - (z0 - 2)) * kY2EX + xe, on = (kn - (z0 - 2)) * kY2EX + xe;
+            const real *old = sM + end * 2 * kY2EX;  // E^n of plane kn
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+                sE[c * PE + ot] = old[c * kY2EX + xe] + a.mur * (sE[c * PE + on] - sE[c * PE + ot]);
+        }
+        __syncthreads();
+    }
+    // ---- E', B' of the own nodes
+    for (int r = tid; r < kY2X * kY2Z; r += nt) {
+        const int lz = r / kY2X, lx = r - lz * kY2X;
+        const int k = z0 + lz, x = x0 + lx;
+        if (k >= z1 || x >= g.nx) continue;
+        const int pe = lz + 2, xe = lx + 1;
+        const int of = pe * kY2EX + xe, ob = pe * kY2BX + xe;
+        const int64_t o = (int64_t)k * g.plane + x;
+        const bool vxy = k <= zmax_of(g, false), vz = k <= zmax_of(g, true);
+        if (vxy) {
+            a.E1[0][o] = sE[of];
+            a.E1[1][o] = sE[PE + of];
+        }
+        if (vz) {
+            a.E1[2][o] = sE[2 * PE + of];
+            const real dEy_dz = (sE[PE + of + kY2EX] - sE[PE + of]) * a.ihz;
+            a.B1[0][o] = sB[ob] - a.hb * (zero - dEy_dz);
+            const real dEx_dz = (sE[of + kY2EX] - sE[of]) * a.ihz;
+            const real dEz_dx = (sE[2 * PE + of + 1] - sE[2 * PE + of]) * a.ihx;
+            a.B1[1][o] = sB[PB + ob] - a.hb * (dEx_dz - dEz_dx);
+        }
+        if (vxy) {
+            const real dEy_dx = (sE[PE + of + 1] - sE[PE + of]) * a.ihx;
+            a.B1[2][o] = sB[2 * PB + ob] - a.hb * (dEy_dx - zero);
+        }
+    }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(256) yee2d_kernel(YeeArgs<real> a)
+{
+    yee2d_body(a, (int)blockIdx.x, (int)blockIdx.y);
+}
+
+// (YeeArgs::nchunks holds the tiles along x here)
+template <typename real>
+__global__ void __launch_bounds__(256) yee2d_batch_kernel(const YeeArgs<real> *__restrict__ runs,
+                                                          const int64_t *__restrict__ start, int n)
+{
+    __shared__ __align__(16) YeeArgs<real> sa;
+    const int64_t b = batch_block(runs, start, n, &sa);
+    yee2d_body(sa, (int)(b % sa.nchunks), (int)(b / sa.nchunks));
+}
+
+template <typename real>
+static size_t yee2d_smem()
+{
+    return sizeof(real) * (3 * (size_t)kY2EZ * kY2EX + 3 * (size_t)kY2BZ * kY2BX + 3 * (size_t)kY2JZ * kY2JX +
+                           4 * (size_t)kY2EX);
+}
+
+template <typename real>
+static void launch_yee2d_batch(const void *args, const int64_t *start, int n, int64_t total, unsigned *,
+                               cudaStream_t s)
+{
+    const size_t smem = yee2d_smem<real>();
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(yee2d_batch_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    yee2d_batch_kernel<real><<<(unsigned)total, 256, smem, s>>>(static_cast<const YeeArgs<real> *>(args), start, n);
+}
+
+template <typename real, int DIM>
+static size_t yee_smem()
+{
+    constexpr int TX = YeeTile<DIM>::TX, TY = YeeTile<DIM>::TY, HY = YeeTile<DIM>::HY;
+    // E^n 4 planes, B^n and Bh 2 each, J 2, E' 3 (three components each)
+    return sizeof(real) * 3 *
+           (4 * (size_t)(TX + 3) * (TY + 3 * HY) + 4 * (size_t)(TX + 2) * (TY + 2 * HY) +
+            5 * (size_t)(TX + 1) * (TY + HY));
+}
+
+template <typename real, int DIM>
+static void launch_yee_batch(const void *args, const int64_t *start, int n, int64_t total, unsigned *, cudaStream_t s)
+{
+    const size_t smem = yee_smem<real, DIM>();
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(yee_batch_kernel<real, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    yee_batch_kernel<real, DIM><<<(unsigned)total, 256, smem, s>>>(static_cast<const YeeArgs<real> *>(args), start, n);
+}
+
 static unsigned grid_for(int64_t n, int block)
 {
     int64_t b = (n + block - 1) / block;
@@ -325,35 +540,35 @@ void launch_yee(const Geom &g, real *const F[9], real *const F1[6], double dt, d
     a.mur = (real)((dt - hz) / (dt + hz));
     const int nzo = g.bc_z == 0 ? g.nz : g.nz + 1;
     const bool is3 = g.dim == 3;
-    const int TX = is3 ? YeeTile<3>::TX : YeeTile<2>::TX, TY = is3 ? YeeTile<3>::TY : YeeTile<2>::TY;
-    const int HY = is3 ? 1 : 0;
-    // chunks of 4..32 planes, as long as there are about eight CTAs per SM (a
-    // narrow 2D grid has one column of CTAs: short chunks fill the GPU); the
-    // last chunk takes the remainder
+    if (!is3) {
+        const int ntx = (g.nx + kY2X - 1) / kY2X, ntz = (nzo + kY2Z - 1) / kY2Z;
+        a.cz = kY2Z;
+        a.nchunks = ntx;
+        if (record_launch(kBPYee, launch_yee2d_batch<real>, a, (int64_t)ntx * ntz)) return;
+        const size_t smem = yee2d_smem<real>();
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(yee2d_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        yee2d_kernel<real><<<dim3((unsigned)ntx, (unsigned)ntz), 256, smem, s>>>(a);
+        return;
+    }
+    constexpr int TX = YeeTile<3>::TX, TY = YeeTile<3>::TY;
+    // chunks of 4..32 planes, as long as there are about eight CTAs per SM;
+    // the last chunk takes the remainder
     if (nzo < 8) {
         a.cz = nzo;
     } else {
-        const int64_t ncol = (int64_t)((g.nx + TX - 1) / TX) * (is3 ? (g.ny + TY - 1) / TY : 1);
-        int64_t czl = (int64_t)nzo * ncol / (152 * 8);
+        const int64_t ncol = (int64_t)((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
+        int64_t czl = (int64_t)nzo * ncol * batch_runs() / ((int64_t)device_sms() * 8);
         a.cz = (int)(czl < 4 ? 4 : (czl > 32 ? 32 : czl));
     }
     a.nchunks = nzo / a.cz;
     if (a.nchunks < 1) a.nchunks = 1;
-    // E^n 4 planes, B^n and Bh 2 each, J 2, E' 3 (three components each)
-    const size_t smem = sizeof(real) * 3 *
-                        (4 * (size_t)(TX + 3) * (TY + 3 * HY) + 4 * (size_t)(TX + 2) * (TY + 2 * HY) +
-                         5 * (size_t)(TX + 1) * (TY + HY));
-    const unsigned nb = (unsigned)(((g.nx + TX - 1) / TX) * (is3 ? (g.ny + TY - 1) / TY : 1));
-    dim3 grid(nb, (unsigned)a.nchunks);
-    if (is3) {
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(yee_kernel<real, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        yee_kernel<real, 3><<<grid, 256, smem, s>>>(a);
-    } else {
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(yee_kernel<real, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        yee_kernel<real, 2><<<grid, 256, smem, s>>>(a);
-    }
+    const size_t smem = yee_smem<real, 3>();
+    const unsigned nb = (unsigned)(((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY));
+    if (record_launch(kBPYee, launch_yee_batch<real, 3>, a, (int64_t)nb * a.nchunks)) return;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(yee_kernel<real, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    yee_kernel<real, 3><<<dim3(nb, (unsigned)a.nchunks), 256, smem, s>>>(a);
 }
 
 // ---------------------------------------------------------- moving window
@@ -434,7 +649,8 @@ __global__ void filter_kernel(Geom g, const real *in0, const real *in1, const re
 // outside the component's valid z range (absorbing z) or wrapped (periodic).
 // The chunk starts H planes early and ends H planes late.
 template <typename real, int DIM, int H>
-__global__ void __launch_bounds__(256) filter_march_kernel(Geom g, const real *in, real *out, int cz, int nchunks)
+__device__ __forceinline__ void march_body(const Geom &g, const real *in, real *out, const int cz, const int nchunks,
+                                           const int bx_, const int by_)
 {
     constexpr int TX = DIM == 3 ? 32 : 256, TY = DIM == 3 ? 8 : 1, HY = DIM == 3 ? H : 0;
     constexpr int RX = TX + 2 * H, RY = TY + 2 * HY, RN = RX * RY;
@@ -451,9 +667,9 @@ __global__ void __launch_bounds__(256) filter_march_kernel(Geom g, const real *i
     }
     const bool per = g.bc_z == 0;
     const int nbx = (g.nx + TX - 1) / TX;
-    const int x0 = (int)(blockIdx.x % nbx) * TX, y0 = (int)(blockIdx.x / nbx) * TY;
-    const int z0 = (int)blockIdx.y * cz;
-    const int z1 = (int)blockIdx.y == nchunks - 1 ? g.nz + 1 : z0 + cz;
+    const int x0 = (bx_ % nbx) * TX, y0 = (bx_ / nbx) * TY;
+    const int z0 = by_ * cz;
+    const int z1 = by_ == nchunks - 1 ? g.nz + 1 : z0 + cz;
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
     const bool own = x0 + tx < g.nx && (DIM == 2 || y0 + ty < g.ny);
     const int64_t oown = own ? (int64_t)(y0 + ty) * g.nx + (x0 + tx) : 0;
@@ -517,6 +733,39 @@ __global__ void __launch_bounds__(256) filter_march_kernel(Geom g, const real *i
                 out[(size_t)c * g.ncomp + (int64_t)ko * g.plane + oown] = ko > zmax ? real(0) : lev[c][H][2];
         }
     }
+}
+
+template <typename real, int DIM, int H>
+__global__ void __launch_bounds__(256) filter_march_kernel(Geom g, const real *in, real *out, int cz, int nchunks)
+{
+    march_body<real, DIM, H>(g, in, out, cz, nchunks, (int)blockIdx.x, (int)blockIdx.y);
+}
+
+template <typename real>
+struct MarchArgs {
+    Geom g;
+    const real *in;
+    real *out;
+    int cz, nchunks;
+};
+
+template <typename real, int DIM, int H>
+__global__ void __launch_bounds__(256) filter_march_batch_kernel(const MarchArgs<real> *__restrict__ runs,
+                                                                 const int64_t *__restrict__ start, int n)
+{
+    __shared__ __align__(16) MarchArgs<real> sa;
+    const int64_t b = batch_block(runs, start, n, &sa);
+    constexpr int TX = DIM == 3 ? 32 : 256, TY = DIM == 3 ? 8 : 1;
+    const int ncol = ((sa.g.nx + TX - 1) / TX) * (DIM == 3 ? (sa.g.ny + TY - 1) / TY : 1);
+    march_body<real, DIM, H>(sa.g, sa.in, sa.out, sa.cz, sa.nchunks, (int)(b % ncol), (int)(b / ncol));
+}
+
+template <typename real, int DIM, int H>
+static void launch_march_batch(const void *args, const int64_t *start, int n, int64_t total, unsigned *,
+                               cudaStream_t s)
+{
+    filter_march_batch_kernel<real, DIM, H>
+        <<<(unsigned)total, 256, 0, s>>>(static_cast<const MarchArgs<real> *>(args), start, n);
 }
 
 // The same filter in 3D with its planes staged by TMA.  A CTA owns a 32 x 8
@@ -692,6 +941,8 @@ template <typename real, int H>
 static bool launch_filter_tma(const Geom &g, const real *in, real *out, unsigned *err, cudaStream_t s)
 {
     constexpr int TX = 32, TY = 8, BX = TX + 8, BY = TY + 2 * H;
+    // a batch of runs takes the plane-load kernel (one tensor map per launch)
+    if (g_rec) return false;
     CUtensorMap map;
     if (!encode_map_4d(&map, in, (int)sizeof(real), (uint64_t)g.nx, (uint64_t)g.ny, (uint64_t)g.nz + 1, 3, BX, BY))
         return false;
@@ -712,19 +963,155 @@ static bool launch_filter_tma(const Geom &g, const real *in, real *out, unsigned
     return true;
 }
 
+// The same H passes on 2D grids, without the march: a CTA owns kF2X x kF2Z
+// (x, z) nodes of the three components and copies, all at once with
+// cp.async into shared memory, their input
+// on x0 - H .. x0 + kF2X + H - 1 (wrapped) and z0 - H .. z0 + kF2Z + H - 1
+// (zero or wrapped beyond the grid); per component, the x passes are the
+// binomial stencil of width 2H + 1 (filter_march_kernel's sum), and the z
+// passes follow one level at a time in shared memory, each narrower by a
+// plane on both sides and zero outside the component's z range, as in the
+// march.
+constexpr int kF2X = 64, kF2Z = 32;
+
+template <typename real, int H>
+__device__ __forceinline__ void filter2d_body(const Geom &g, const real *in, real *out, const int bx_, const int bz_)
+{
+    constexpr int IX = kF2X + 2 * H, IZ = kF2Z + 2 * H, PI = IX * IZ, PL = kF2X * IZ;
+    constexpr int W = 2 * H + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    real *sI = reinterpret_cast<real *>(smem_raw);  // [3][IZ][IX] input
+    real *sL = sI + 3 * PI;                          // [2][IZ][kF2X] levels (ping-pong)
+    real wb[W];
+    {
+        double c = 1.0;
+        for (int i = 0; i < W; ++i) {
+            wb[i] = (real)(c / (double)(1 << (2 * H)));
+            c = c * (double)(2 * H - i) / (double)(i + 1);
+        }
+    }
+    const bool per = g.bc_z == 0;
+    const int x0 = bx_ * kF2X, z0 = bz_ * kF2Z;
+    const int tid = (int)threadIdx.x, nt = (int)blockDim.x;
+    const int zmax_xy = zmax_of(g, false), zmax_z = zmax_of(g, true);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int zmax = c == 2 ? zmax_z : zmax_xy;
+        for (int r = tid; r < PI; r += nt) {
+            const int pz = r / IX, px = r - pz * IX;
+            const int k = z0 - H + pz, x = x0 - H + px;
+            const bool have = per || (k >= 0 && k <= zmax);
+            const int kk = per ? wrapi(k, g.nz) : k;
+            const int xx = x >= 0 && x < g.nx ? x : wrapi(x, g.nx);
+            if (have)
+                __pipeline_memcpy_async(sI + c * PI + r, in + (size_t)c * g.ncomp + (int64_t)kk * g.plane + xx,
+                                        sizeof(real));
+            else sI[c * PI + r] = real(0);
+        }
+    }
+    __pipeline_commit();
+    __pipeline_wait_prior(0);
+    __syncthreads();
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        const int zmax = c == 2 ? zmax_z : zmax_xy;
+        const real *I = sI + c * PI;
+        real *L0 = sL, *L1 = sL + PL;
+        // level 0: the x stencil on every loaded plane
+        for (int r = tid; r < PL; r += nt) {
+            const int pz = r / kF2X, lx = r - pz * kF2X;
+            const int k = z0 - H + pz;
+            real v = 0;
+#pragma unroll
+            for (int i = 0; i < W; ++i) v += wb[i] * I[pz * IX + lx + i];
+            L0[r] = (per || (k >= 0 && k <= zmax)) ? v : real(0);
+        }
+        __syncthreads();
+        // level p on planes H - p .. IZ - 1 - (H - p) of the loaded range
+#pragma unroll
+        for (int p = 1; p <= H; ++p) {
+            for (int r = tid; r < PL; r += nt) {
+                const int pz = r / kF2X;
+                if (pz < p || pz >= IZ - p) continue;
+                const int k = z0 - H + pz;
+                const real nv = real(0.25) * L0[r - kF2X] + real(0.5) * L0[r] + real(0.25) * L0[r + kF2X];
+                L1[r] = (per || (k >= 0 && k <= zmax)) ? nv : real(0);
+            }
+            __syncthreads();
+            real *t = L0;
+            L0 = L1;
+            L1 = t;
+        }
+        for (int r = tid; r < kF2X * kF2Z; r += nt) {
+            const int lz = r / kF2X, lx = r - lz * kF2X;
+            const int k = z0 + lz, x = x0 + lx;
+            if (k > g.nz || x >= g.nx) continue;
+            out[(size_t)c * g.ncomp + (int64_t)k * g.plane + x] = k > zmax ? real(0) : L0[(lz + H) * kF2X + lx];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename real, int H>
+__global__ void __launch_bounds__(256) filter2d_kernel(Geom g, const real *in, real *out)
+{
+    filter2d_body<real, H>(g, in, out, (int)blockIdx.x, (int)blockIdx.y);
+}
+
+// (MarchArgs::cz holds the tiles along x here)
+template <typename real, int H>
+__global__ void __launch_bounds__(256) filter2d_batch_kernel(const MarchArgs<real> *__restrict__ runs,
+                                                             const int64_t *__restrict__ start, int n)
+{
+    __shared__ __align__(16) MarchArgs<real> sa;
+    const int64_t b = batch_block(runs, start, n, &sa);
+    filter2d_body<real, H>(sa.g, sa.in, sa.out, (int)(b % sa.cz), (int)(b / sa.cz));
+}
+
+template <typename real, int H>
+static size_t filter2d_smem()
+{
+    return sizeof(real) * (3 * (size_t)(kF2X + 2 * H) * (kF2Z + 2 * H) + 2 * (size_t)kF2X * (kF2Z + 2 * H));
+}
+
+template <typename real, int H>
+static void launch_filter2d_batch(const void *args, const int64_t *start, int n, int64_t total, unsigned *,
+                                  cudaStream_t s)
+{
+    const size_t smem = filter2d_smem<real, H>();
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(filter2d_batch_kernel<real, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    filter2d_batch_kernel<real, H>
+        <<<(unsigned)total, 256, smem, s>>>(static_cast<const MarchArgs<real> *>(args), start, n);
+}
+
 template <typename real, int DIM, int H>
 static void launch_march(const Geom &g, const real *in, real *out, cudaStream_t s)
 {
-    constexpr int TX = DIM == 3 ? 32 : 256, TY = DIM == 3 ? 8 : 1;
     const int nzo = g.nz + 1;
-    const unsigned nb = (unsigned)(((g.nx + TX - 1) / TX) * (DIM == 3 ? (g.ny + TY - 1) / TY : 1));
-    // z chunks of 8..64 planes, as long as there are about eight CTAs per SM
-    // (a narrow 2D grid has one column of CTAs: short chunks fill the GPU)
-    int64_t czl = (int64_t)nzo * nb / (152 * 8);
-    czl = czl < 8 ? 8 : (czl > 64 ? 64 : czl);
-    const int cz = (int)(czl < nzo ? czl : nzo);
-    const int nchunks = nzo / cz > 0 ? nzo / cz : 1;
-    filter_march_kernel<real, DIM, H><<<dim3(nb, (unsigned)nchunks, 1), 256, 0, s>>>(g, in, out, cz, nchunks);
+    if constexpr (DIM == 2) {
+        // the tiled kernel (2D grids)
+        const int ntx = (g.nx + kF2X - 1) / kF2X, ntz = (nzo + kF2Z - 1) / kF2Z;
+        if (record_launch(kBPFilter, launch_filter2d_batch<real, H>, MarchArgs<real>{g, in, out, ntx, ntz},
+                          (int64_t)ntx * ntz))
+            return;
+        const size_t smem = filter2d_smem<real, H>();
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(filter2d_kernel<real, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        filter2d_kernel<real, H><<<dim3((unsigned)ntx, (unsigned)ntz), 256, smem, s>>>(g, in, out);
+    } else {
+        constexpr int TX = 32, TY = 8;
+        const unsigned nb = (unsigned)(((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY));
+        // z chunks of 8..64 planes, as long as there are about eight CTAs per SM
+        int64_t czl = (int64_t)nzo * nb * batch_runs() / ((int64_t)device_sms() * 8);
+        czl = czl < 8 ? 8 : (czl > 64 ? 64 : czl);
+        const int cz = (int)(czl < nzo ? czl : nzo);
+        const int nchunks = nzo / cz > 0 ? nzo / cz : 1;
+        if (record_launch(kBPFilter, launch_march_batch<real, DIM, H>, MarchArgs<real>{g, in, out, cz, nchunks},
+                          (int64_t)nb * nchunks))
+            return;
+        filter_march_kernel<real, DIM, H><<<dim3(nb, (unsigned)nchunks, 1), 256, 0, s>>>(g, in, out, cz, nchunks);
+    }
 }
 
 template <typename real>
@@ -772,6 +1159,7 @@ void launch_filter(const Geom &g, real *const J[3], real *tmp, int npass, cudaSt
     if (npass <= 0) return;
     // the three components are contiguous in the field buffer; the fused
     // kernel covers 1..4 passes, more fall back to one launch per pass
+    if (record_unsupported()) return;  // (a copy back, or one launch per pass)
     const bool contiguous = J[1] == J[0] + g.ncomp && J[2] == J[1] + g.ncomp;
     if (contiguous && fused_passes<real>(g, J[0], tmp, npass, s, err)) {
         cudaMemcpyAsync(J[0], tmp, 3 * sizeof(real) * g.ncomp, cudaMemcpyDeviceToDevice, s);
@@ -804,29 +1192,94 @@ void launch_filter(const Geom &g, real *const J[3], real *tmp, int npass, cudaSt
 // polarisation component (its own staggered transverse position).  One plane
 // per step: the profile is evaluated in FP64 and rounded once.
 template <typename real>
-__global__ void antenna_kernel(Geom g, real *J, int pol, int ka, double j0, double hx, double hy, double xc,
-                               double yc, double inv_w2, const double *j0p)
+struct AntennaArgs {
+    Geom g;
+    real *J;
+    int pol, ka;
+    double j0, hx, hy, xc, yc, inv_w2;
+    const double *j0p;
+};
+
+template <typename real>
+__device__ __forceinline__ void antenna_body(const AntennaArgs<real> &a, int64_t b, int64_t nb)
 {
-    if (j0p) j0 = *j0p;
+    const Geom &g = a.g;
+    const double j0 = a.j0p ? *a.j0p : a.j0;
     const int64_t n = g.plane;
-    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t o = b * blockDim.x + threadIdx.x; o < n; o += nb * blockDim.x) {
         const int i = (int)(o % g.nx), j = (int)(o / g.nx);
-        const double x = ((double)i + (pol == 0 ? 0.5 : 0.0)) * hx - xc;
+        const double x = ((double)i + (a.pol == 0 ? 0.5 : 0.0)) * a.hx - a.xc;
         double r2 = x * x;
         if (g.dim == 3) {
-            const double y = ((double)j + (pol == 1 ? 0.5 : 0.0)) * hy - yc;
+            const double y = ((double)j + (a.pol == 1 ? 0.5 : 0.0)) * a.hy - a.yc;
             r2 += y * y;
         }
-        J[(int64_t)ka * g.plane + o] += (real)(j0 * exp(-r2 * inv_w2));
+        a.J[(int64_t)a.ka * g.plane + o] += (real)(j0 * exp(-r2 * a.inv_w2));
     }
+}
+
+template <typename real>
+__global__ void antenna_kernel(AntennaArgs<real> a)
+{
+    antenna_body(a, (int64_t)blockIdx.x, (int64_t)gridDim.x);
+}
+
+template <typename real>
+__global__ void antenna_batch_kernel(const AntennaArgs<real> *__restrict__ runs, const int64_t *__restrict__ start,
+                                     int n)
+{
+    __shared__ __align__(16) AntennaArgs<real> sa;
+    const int64_t b = batch_block(runs, start, n, &sa);
+    const int r = batch_run_of(start, n, (int64_t)blockIdx.x);
+    antenna_body(sa, b, start[r + 1] - start[r]);
+}
+
+template <typename real>
+static void launch_antenna_batch(const void *args, const int64_t *start, int n, int64_t total, unsigned *,
+                                 cudaStream_t s)
+{
+    antenna_batch_kernel<real><<<(unsigned)total, 256, 0, s>>>(static_cast<const AntennaArgs<real> *>(args), start, n);
 }
 
 template <typename real>
 void launch_antenna(const Geom &g, real *J, int pol, int ka, double j0, double hx, double hy, double xc,
                     double yc, double waist, cudaStream_t s, const double *j0p)
 {
-    antenna_kernel<real><<<grid_for(g.plane, 256), 256, 0, s>>>(g, J, pol, ka, j0, hx, hy, xc, yc,
-                                                               1.0 / (waist * waist), j0p);
+    const AntennaArgs<real> a{g, J, pol, ka, j0, hx, hy, xc, yc, 1.0 / (waist * waist), j0p};
+    const unsigned nb = grid_for(g.plane, 256);
+    if (record_launch(kBPAntenna, launch_antenna_batch<real>, a, (int64_t)nb)) return;
+    antenna_kernel<real><<<nb, 256, 0, s>>>(a);
+}
+
+// ---------------------------------------------------------------- zeroing
+
+// blocks of kZeroChunk elements; the batched form zeroes every run's buffer
+constexpr int kZeroChunk = 8192;
+
+template <typename real>
+__global__ void __launch_bounds__(256) zero_batch_kernel(const ZeroArgs<real> *__restrict__ runs,
+                                                         const int64_t *__restrict__ start, int n)
+{
+    __shared__ __align__(16) ZeroArgs<real> sa;
+    const int64_t b = batch_block(runs, start, n, &sa);
+    const int64_t lo = b * kZeroChunk;
+    const int64_t hi = lo + kZeroChunk < sa.n ? lo + kZeroChunk : sa.n;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) sa.p[i] = real(0);
+}
+
+template <typename real>
+static void launch_zero_batch(const void *args, const int64_t *start, int n, int64_t total, unsigned *, cudaStream_t s)
+{
+    zero_batch_kernel<real><<<(unsigned)total, 256, 0, s>>>(static_cast<const ZeroArgs<real> *>(args), start, n);
+}
+
+template <typename real>
+void launch_zero(real *p, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return;
+    if (record_launch(kBPZero, launch_zero_batch<real>, ZeroArgs<real>{p, n}, (n + kZeroChunk - 1) / kZeroChunk))
+        return;
+    cudaMemsetAsync(p, 0, (size_t)n * sizeof(real), s);
 }
 
 // ------------------------------------------------------------ field sums
@@ -877,7 +1330,8 @@ void launch_field_sums(const Geom &g, real *const F[9], double *partials, int nb
     template void launch_window_fields<real>(const Geom &, real *const[9], real *const[9], int, cudaStream_t); \
     template void launch_antenna<real>(const Geom &, real *, int, int, double, double, double, double,  \
                                        double, double, cudaStream_t, const double *);                   \
-    template void launch_field_sums<real>(const Geom &, real *const[9], double *, int, cudaStream_t);
+    template void launch_field_sums<real>(const Geom &, real *const[9], double *, int, cudaStream_t); \
+    template void launch_zero<real>(real *, int64_t, cudaStream_t);
 PIC_FIELDS_INSTANTIATE(float)
 PIC_FIELDS_INSTANTIATE(double)
 
@@ -920,6 +1374,3 @@ extern "C" pic_status pic_wait_check(int arrive, double budget_ms, void *stream)
         return PIC_ERR_CUDA;
     return r ? PIC_ERR_TIMEOUT : PIC_OK;
 }
-
-namespace pic {
-}  // namespace pic

@@ -96,7 +96,7 @@ __device__ __forceinline__ void store(void *const sp[kAttrs], int64_t d, real ox
 }
 
 template <typename real>
-__global__ void inject_kernel(InjectArgs a)
+__device__ __forceinline__ void inject_body(const InjectArgs &a, const int64_t b, const int64_t nb)
 {
     const bool dim3 = a.g.dim == 3;
     // the step's times and lattice band (from device memory in a captured step)
@@ -104,8 +104,8 @@ __global__ void inject_kernel(InjectArgs a)
     const int64_t m_lo = a.scal ? a.scal->m_lo : a.m_lo, m_hi = a.scal ? a.scal->m_hi : a.m_hi;
     const int64_t total = (m_hi - m_lo) * a.NY * a.NX;
     const int64_t nround = (total + 31) / 32 * 32;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nround; q += stride) {
+    const int64_t stride = nb * blockDim.x;
+    for (int64_t q = b * blockDim.x + threadIdx.x; q < nround; q += stride) {
         int64_t dest = -1;
         int ci = 0, cj = 0, ck = 0;
         real ox = 0, oy = 0, oz = 0, wr = 0;
@@ -207,17 +207,44 @@ __global__ void inject_kernel(InjectArgs a)
     }
 }
 
+template <typename real>
+__global__ void inject_kernel(InjectArgs a)
+{
+    inject_body<real>(a, (int64_t)blockIdx.x, (int64_t)gridDim.x);
+}
+
+template <typename real>
+__global__ void inject_batch_kernel(const InjectArgs *__restrict__ runs, const int64_t *__restrict__ start, int n)
+{
+    __shared__ __align__(16) InjectArgs sa;
+    const int64_t b = batch_block(runs, start, n, &sa);
+    const int r = batch_run_of(start, n, (int64_t)blockIdx.x);
+    inject_body<real>(sa, b, start[r + 1] - start[r]);
+}
+
+// the work per point is FP64 arithmetic, whose pipe is narrow: CTAs of two
+// warps spread a step's thin band of lattice points over many SMs
+constexpr int kInjectThreads = 64;
+
+template <typename real>
+static void launch_inject_batch(const void *args, const int64_t *start, int n, int64_t total, unsigned *,
+                                cudaStream_t s)
+{
+    inject_batch_kernel<real>
+        <<<(unsigned)total, kInjectThreads, 0, s>>>(static_cast<const InjectArgs *>(args), start, n);
+}
+
 void launch_inject(const InjectArgs &a, cudaStream_t s)
 {
     const int64_t total = (a.m_hi - a.m_lo) * a.NY * a.NX;
     if (total <= 0) return;
-    // the work per point is FP64 arithmetic, whose pipe is narrow: CTAs of
-    // two warps spread a step's thin band of lattice points over many SMs
-    constexpr int kThreads = 64;
-    int64_t blocks = (total + kThreads - 1) / kThreads;
-    if (blocks > 152LL * 128) blocks = 152LL * 128;
-    if (a.precision == 0) inject_kernel<float><<<(unsigned)blocks, kThreads, 0, s>>>(a);
-    else inject_kernel<double><<<(unsigned)blocks, kThreads, 0, s>>>(a);
+    int64_t blocks = (total + kInjectThreads - 1) / kInjectThreads;
+    if (blocks > (int64_t)device_sms() * 128) blocks = (int64_t)device_sms() * 128;
+    if (record_launch(kBPInject, a.precision == 0 ? launch_inject_batch<float> : launch_inject_batch<double>, a,
+                      blocks))
+        return;
+    if (a.precision == 0) inject_kernel<float><<<(unsigned)blocks, kInjectThreads, 0, s>>>(a);
+    else inject_kernel<double><<<(unsigned)blocks, kInjectThreads, 0, s>>>(a);
 }
 
 }  // namespace pic

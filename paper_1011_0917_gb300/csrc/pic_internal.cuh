@@ -22,7 +22,10 @@
 #pragma once
 
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
+#include <type_traits>
+#include <vector>
 
 namespace pic {
 
@@ -434,6 +437,14 @@ struct CompactArgs {     // copy tiles into a flat list
 };
 
 template <typename real>
+struct SortArgs {        // order every tile's bucket by cell (into the other side)
+    Geom g;
+    Species<real> in, out;
+    int *in_lo, *in_hi, *out_lo;
+    unsigned *err;
+};
+
+template <typename real>
 struct BtdArgs {         // lab-frame snapshots filled during one step
     Geom g;
     const real *E0[3], *B0[3];  // fields at the start of the step
@@ -530,11 +541,127 @@ struct AdjArgs {
     int with_ions;                  // the drifting ion of every slot too
 };
 
+// ------------------------------------------------- batched launch recording
+//
+// A batch of independent runs can step together with one launch per phase
+// over the work items of all of them.  Such a step is built by running each
+// run's own step on the host with a recorder installed on the calling
+// thread: every launch function then appends what it would launch -- its
+// phase, the batched form of its kernel, its argument struct and its number
+// of work items (blocks, or tiles for the persistent particle kernels) --
+// instead of launching.  A batched kernel maps its block (or the next item
+// of a device-wide queue) to (run, item) through the runs' prefix sums of
+// work items, copies that run's argument struct into shared memory and runs
+// the same per-block body as the single-run kernel, so both give identical
+// results.
+//
+// BatchLaunch(args, start, n, total, queue, stream): args = n argument
+// structs (device), start = n + 1 prefix sums of the runs' work items
+// (device), total = start[n], queue = a zeroed device counter (persistent
+// kernels) or null.
+using BatchLaunch = void (*)(const void *args, const int64_t *start, int n, int64_t total, unsigned *queue,
+                             cudaStream_t s);
+// phases in the order a step issues them
+enum BatchPhase : int { kBPZero = 0, kBPPush, kBPIons, kBPAntenna, kBPFilter, kBPYee, kBPInject, kBPCount };
+struct LaunchRecord {
+    int step, phase;
+    BatchLaunch fn;
+    std::vector<unsigned char> args;
+    int64_t items;
+    bool queue;  // the batched kernel pulls its items from a device counter
+};
+struct BatchRecorder {
+    int step = 0;
+    int nctx = 1;              // runs in the batch (field kernels size their z chunks for all of them)
+    bool unsupported = false;  // the step asked for something the batched step does not do
+    std::vector<LaunchRecord> recs;
+};
+extern thread_local BatchRecorder *g_rec;
+
+// true (and recorded) while a recorder is installed
+template <typename A>
+inline bool record_launch(int phase, BatchLaunch fn, const A &a, int64_t items, bool queue = false)
+{
+    static_assert(std::is_trivially_copyable<A>::value, "argument structs are copied as bytes");
+    BatchRecorder *r = g_rec;
+    if (!r) return false;
+    LaunchRecord L;
+    L.step = r->step;
+    L.phase = phase;
+    L.fn = fn;
+    L.args.resize(sizeof(A));
+    std::memcpy(L.args.data(), &a, sizeof(A));
+    L.items = items;
+    L.queue = queue;
+    r->recs.push_back(std::move(L));
+    return true;
+}
+// for launches with no batched form: true (the step is then not batched)
+// while a recorder is installed
+inline bool record_unsupported()
+{
+    if (!g_rec) return false;
+    g_rec->unsupported = true;
+    return true;
+}
+// runs whose field kernels share one launch (z chunks are sized for all)
+inline int batch_runs() { return g_rec ? g_rec->nctx : 1; }
+
+#ifdef __CUDACC__
+// the run owning work item `item`: the last r with start[r] <= item
+__device__ __forceinline__ int batch_run_of(const int64_t *start, int n, int64_t item)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// all threads of the CTA copy an argument struct (global -> shared)
+template <typename A>
+__device__ __forceinline__ void batch_copy_args(A *dst, const A *src)
+{
+    static_assert(sizeof(A) % 4 == 0, "argument structs are copied as words");
+    const int *s = reinterpret_cast<const int *>(src);
+    int *d = reinterpret_cast<int *>(dst);
+    for (int i = (int)threadIdx.x; i < (int)(sizeof(A) / 4); i += (int)blockDim.x) d[i] = s[i];
+}
+
+// block blockIdx.x of a batched launch with one block per work item: its
+// run's arguments into *sa (shared), returns the block's index in its run
+template <typename A>
+__device__ __forceinline__ int64_t batch_block(const A *runs, const int64_t *start, int n, A *sa)
+{
+    __shared__ int s_r;
+    if (threadIdx.x == 0) s_r = batch_run_of(start, n, (int64_t)blockIdx.x);
+    __syncthreads();
+    const int r = s_r;
+    batch_copy_args(sa, runs + r);
+    __syncthreads();
+    return (int64_t)blockIdx.x - start[r];
+}
+#endif
+
+// the zeroing of a current buffer as a batchable launch (cudaMemsetAsync
+// otherwise)
+template <typename real>
+struct ZeroArgs {
+    real *p;
+    int64_t n;
+};
+template <typename real> void launch_zero(real *p, int64_t n, cudaStream_t s);
+// SMs of the current device (cached per device)
+int device_sms();
+
 // host launchers (defined in the .cu files)
 template <typename real> void launch_push(const PushArgs<real> &a, cudaStream_t s);
 template <typename real> void launch_ions(const PushArgs<real> &a, cudaStream_t s);
 template <typename real> void launch_bucket(const BucketArgs<real> &a, cudaStream_t s);
 template <typename real> void launch_compact(const CompactArgs<real> &a, cudaStream_t s);
+template <typename real> void launch_sort_cells(const SortArgs<real> &a, cudaStream_t s);
 template <typename real>
 void launch_rho(const Geom &g, const Species<real> &sp, const int *lo, const int *hi, real qfac, real *rho,
                 cudaStream_t s);

@@ -307,3 +307,59 @@ def test_stage_gradient_without_waist_input(O, reference):
     (lam * out).sum().backward()
     g = np.concatenate([coef.grad.cpu().numpy(), [a0.grad.item()]])
     assert np.all(np.abs(g - fd[:-1]) / np.abs(fd[:-1]) < 1e-3)
+
+
+# ------------------------------------------------------------ batched
+
+BATCH_RUNS = [
+    dict(coef=COEF, a0=LASER["a0"], w0=LASER["waist"]),
+    dict(coef=(-0.08, 0.04, 0.02), a0=1.5, w0=6.0),
+    dict(coef=(0.05,), a0=2.5, w0=4.5),
+]
+
+
+def _oracle_fd(O, coef, a0, w0):
+    h = 1e-4
+    fd = []
+    for m in range(len(coef)):
+        cp, cm = list(coef), list(coef)
+        cp[m] += h
+        cm[m] -= h
+        fd.append((oracle_objective(O, cp, a0, w0)[0] - oracle_objective(O, cm, a0, w0)[0]) / (2 * h))
+    ha, hw = 1e-4 * a0, 1e-4 * w0
+    fd.append((oracle_objective(O, coef, a0 + ha, w0)[0] - oracle_objective(O, coef, a0 - ha, w0)[0]) / (2 * ha))
+    fd.append((oracle_objective(O, coef, a0, w0 + hw)[0] - oracle_objective(O, coef, a0, w0 - hw)[0]) / (2 * hw))
+    return np.array(fd)
+
+
+def test_batch_adjoint_matches_oracle_finite_differences(O, reference):
+    """The reverse mode of a scan: three runs with different profiles (M = 2,
+    3, 1 coefficients), laser amplitudes and waists, all gradients from one
+    pic_batch_adjoint call (every run's forward and reverse sweep queued on its
+    own stream), each against central differences of its own FP64 oracle
+    runs (1e-3), and run 0 the same as its single-run gradient."""
+    import torch
+
+    import paper_1011_0917_gb300 as P
+    sims = []
+    for r in BATCH_RUNS:
+        sim = P.Simulation(dim=2, nx=G["nx"], nz=G["nz"], dx=G["dx"], dz=G["dz"], gamma_boost=GAM,
+                           filter_passes=G["filter_passes"], precision=FP64, seed=G["seed"], slots_per_cell=16.0,
+                           stream=torch.cuda.Stream())
+        sim.load_plasma(PLASMA["ne"], PLASMA["z_start"], PLASMA["z_end"], PLASMA["ramp"], PLASMA["ppc"],
+                        PLASMA["jitter"], r["coef"], 1)
+        sim.launch_laser(r["a0"], r["w0"], LASER["fwhm"], 0.0, LASER["t_peak"], 1)
+        sims.append(sim)
+    batch = P.Batch(sims, graph_steps=0)
+    lam = cotangent(G["nz"], G["nx"])
+    grads = batch.adjoint(NSTEPS, [lam] * len(sims), checkpoint_every=20, sub_checkpoint_every=5)
+    batch.close()
+    _, single = gpu_run(O, FP64)
+    assert np.allclose(grads[0], single, rtol=1e-11, atol=0), (grads[0], single)
+    _, _, fd0 = reference
+    for i, r in enumerate(BATCH_RUNS):
+        fd = fd0 if i == 0 else _oracle_fd(O, r["coef"], r["a0"], r["w0"])
+        g = np.array(grads[i])
+        assert g.shape == fd.shape == (len(r["coef"]) + 2,)
+        rel = np.abs(g - fd) / np.abs(fd)
+        assert np.all(rel < 1e-3), (i, g, fd, rel)

@@ -57,3 +57,15 @@ def test_autotune_picks_a_compiled_configuration():
     assert best["tile"] in autotune.TILES_2D and best["slots_per_cell"] in autotune.SLOTS
     assert len(best["trials"]) == len(autotune.TILES_2D) * len(autotune.SLOTS)
     assert best["ms_per_step"] == min(t["ms_per_step"] for t in best["trials"] if "ms_per_step" in t)
+
+
+def test_autotune_batch_tries_every_launch_form():
+    """The batch autotuner times the stream path and, per graph length, the
+    fused and per-context graphs, and returns the fastest."""
+    from paper_1011_0917_gb300 import autotune
+    runs = [{"grid": dict(G, precision=FP32, seed=17 + r), "plasma": PLASMA, "laser": dict(LASER, pol=1)}
+            for r in range(3)]
+    best = autotune.tune_batch(runs, steps=10, warmup=2, graph_steps=(10,))
+    forms = {(t["graph_steps"], t["fused"]) for t in best["trials"]}
+    assert forms == {(0, False), (10, True), (10, False)}, best["trials"]
+    assert best["ms_per_step"] == min(t["ms_per_step"] for t in best["trials"])
