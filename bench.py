@@ -409,11 +409,11 @@ def run_c4(P, torch, nruns, warmup, steps, graph_steps=20):
     # the same steps as replays of a captured graph: a first call of
     # graph_steps steps captures it (timed on its own), the batch keeps it;
     # the per-context graph (every run's launches on its own stream), then
-    # the fused one (one launch per phase over all runs)
+    # the fused one with 1, 2, 4 and 8 launch chains
     P.pic_batch_set_graph(batch.h, graph_steps)
     timings = {}
-    for fused in (False, True):
-        P.pic_batch_set_fused(batch.h, fused)
+    for chains in (0, 1, 2, 4, 8):
+        P.pic_batch_set_fused(batch.h, chains)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         batch.step(graph_steps)
@@ -422,9 +422,10 @@ def run_c4(P, torch, nruns, warmup, steps, graph_steps=20):
         t0 = time.perf_counter()
         batch.step(steps)
         torch.cuda.synchronize()
-        timings[fused] = (time.perf_counter() - t0, t_capture, batch.graph_info())
-    t_batch, t_capture, info = timings[True]
-    t_ctx, t_capture_ctx, info_ctx = timings[False]
+        timings[chains] = (time.perf_counter() - t0, t_capture, batch.graph_info())
+    best = min((c for c in timings if c > 0), key=lambda c: timings[c][0])
+    t_batch, t_capture, info = timings[best]
+    t_ctx, t_capture_ctx, info_ctx = timings[0]
     # the same runs one after another on a single stream (each pic_step waits)
     t0 = time.perf_counter()
     for s in sims:
@@ -436,7 +437,8 @@ def run_c4(P, torch, nruns, warmup, steps, graph_steps=20):
         s.close()
     torch.cuda.empty_cache()
     return {"runs": nruns, "steps": steps, "electrons": n0, "value": n0 * steps / t_batch,
-            "ms_per_step": 1e3 * t_batch / steps, "graph_steps": graph_steps, "fused": info["fused"],
+            "ms_per_step": 1e3 * t_batch / steps, "graph_steps": graph_steps, "fused_chains": info["chains"],
+            "fused_ms_per_step_by_chains": {c: round(1e3 * timings[c][0] / steps, 4) for c in timings if c > 0},
             "launches_per_step": info["launches_per_replay"] / graph_steps,
             "first_call_ms": 1e3 * t_capture,
             "per_context_graph_value": n0 * steps / t_ctx, "per_context_graph_ms_per_step": 1e3 * t_ctx / steps,
@@ -448,9 +450,10 @@ def run_c4(P, torch, nruns, warmup, steps, graph_steps=20):
                     "8-coefficient profile, a0 in [0.5, 2]; host wall clock around pic_batch_step (graph: "
                     "graph_steps steps of all runs captured once as one CUDA graph by a first call, timed as "
                     "first_call_ms, and kept by the batch; the timed call replays it).  value: the fused "
-                    "graph (one launch per phase over all runs, the push a persistent grid over (run, tile) "
-                    "items); per_context_graph: every run's launches on its own stream inside the graph; "
-                    "streams: launch by launch on the runs' streams"}
+                    "graph with the fastest of 1, 2, 4, 8 launch chains (each chain one launch per phase over "
+                    "its runs, the push a persistent grid over (run, tile) items); per_context_graph: every "
+                    "run's launches on its own stream inside the graph; streams: launch by launch on the runs' "
+                    "streams"}
 
 
 def run_adjoint(P, torch, steps, K, r=0):

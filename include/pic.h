@@ -351,27 +351,31 @@ void pic_batch_destroy(pic_batch *batch);
    later.  PIC_ERR_ARG for a negative or odd count. */
 pic_status pic_batch_set_graph(pic_batch *batch, int steps_per_graph);
 
-/* The form of the captured graph.  fused = 1 (the default): where every
-   launch of every context's steps has a batched form (all do, except the
-   per-pass filter path for more than 4 passes), each phase of each step is
-   one launch over the work items of all the runs that issue it (runs whose
-   particle kernels differ in precision, dimension, shape order, tile shape
-   or position form get one launch per kind): the zeroing of the raw
-   currents, the particle push -- a persistent grid whose CTAs take
-   (run, tile) items from a device-wide counter, so runs of uneven size
-   share the GPU to the last tile -- the drifting ions, the antenna, the
-   filter (3D runs take the plane-load filter instead of the TMA one: a
-   tensor map is made per launch), the Yee update and the injection.  Each
-   item is processed by the same code and arithmetic as in a single run's
-   launch, so the results are identical to those of the per-context graph.
-   fused = 0: the per-context graph (every context's launches on its own
-   stream, forked from and joined to the graph's).  A change drops the kept
-   graph.  PIC_ERR_ARG for other values. */
+/* The form of the captured graph.  fused = S >= 1 (default 4): the
+   batched form, where every launch of every context's steps has one (all
+   do, except the per-pass filter path for more than 4 passes).  The runs are
+   spread over min(S, n) launch chains by size; each chain is a stream of its
+   own inside the graph (forked from and joined to the graph's stream) on
+   which each phase of each step is one launch over the work items of the
+   chain's runs (runs whose particle kernels differ in precision, dimension,
+   shape order, tile shape or position form get one launch per kind): the
+   zeroing of the raw currents, the particle push -- a persistent grid whose
+   CTAs take (run, tile) items from a device-wide counter, so runs of uneven
+   size share the GPU to the last tile -- the drifting ions, the antenna,
+   the filter (3D runs take the plane-load filter instead of the TMA one: a
+   tensor map is made per launch), the Yee update and the injection.  Chains
+   overlap one chain's field phases with another's push.  Each item is
+   processed by the same code and arithmetic as in a single run's launch, so
+   the results are those of the per-context graph (up to the order of the
+   floating-point additions of tiles into J).  fused = 0: the per-context
+   graph (every context's launches on its own stream, forked from and joined
+   to the graph's).  A change drops the kept graph.  PIC_ERR_ARG for
+   fused < 0. */
 pic_status pic_batch_set_fused(pic_batch *batch, int fused);
 
-/* The graph the batch keeps (zeros before the first capture): whether it is
-   the fused form, the launches one replay issues (kernels and counter
-   resets) and the steps it covers. */
+/* The graph the batch keeps (zeros before the first capture): its launch
+   chains if it is the fused form (0: per context), the launches one replay
+   issues (kernels and counter resets) and the steps it covers. */
 pic_status pic_batch_graph_info(pic_batch *batch, int *fused, int64_t *launches_per_replay, int *steps);
 
 /* ---------------------------------------------------------- moving window */

@@ -351,19 +351,24 @@ def pic_set_cell_sort(ctx, every: int):
     _check(ctx, _load().pic_set_cell_sort(ctx, int(every)))
 
 
-def pic_batch_set_fused(batch, fused: bool):
-    s = _load().pic_batch_set_fused(batch, 1 if fused else 0)
+def pic_batch_set_fused(batch, chains):
+    """chains: launch chains of the fused graph (0 or False: the per-context
+    graph; True: the library's default of 4)."""
+    n = (4 if chains else 0) if isinstance(chains, bool) else int(chains)
+    s = _load().pic_batch_set_fused(batch, n)
     if s != PIC_OK:
         raise PicError(s, "pic_batch_set_fused: " + pic_status_string(s))
 
 
 def pic_batch_graph_info(batch) -> dict:
-    """{"fused", "launches_per_replay", "steps"} of the graph the batch keeps."""
+    """{"fused", "chains", "launches_per_replay", "steps"} of the graph the
+    batch keeps (chains: launch chains of the fused form, 0 per context)."""
     f, n, k = C.c_int(), C.c_int64(), C.c_int()
     s = _load().pic_batch_graph_info(batch, C.byref(f), C.byref(n), C.byref(k))
     if s != PIC_OK:
         raise PicError(s, "pic_batch_graph_info: " + pic_status_string(s))
-    return {"fused": bool(f.value), "launches_per_replay": int(n.value), "steps": int(k.value)}
+    return {"fused": f.value > 0, "chains": int(f.value), "launches_per_replay": int(n.value),
+            "steps": int(k.value)}
 
 
 def pic_batch_adjoint(batch, params, buf_ptrs, nbytes, cot_ptrs, grad_stride: int):
@@ -623,8 +628,9 @@ class StageGradient:
 
 class Batch:
     """Steps several Simulations together: captured graphs of graph_steps
-    steps, in the batched form (one launch per phase over all runs) when
-    fused, else each run's launches on its own stream."""
+    steps, in the batched form when fused (the runs split into `fused` launch
+    chains, True: 4, each chain one launch per phase over its runs), else
+    each run's launches on its own stream."""
 
     def __init__(self, sims, graph_steps=20, fused=True):
         self.sims = list(sims)

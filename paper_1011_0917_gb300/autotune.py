@@ -9,9 +9,10 @@ the library offers at run time:
 * the bucket capacity (slots per cell), which sets the memory a tile's
   particle records span;
 * for a batch of runs, the launch form: launch by launch on the runs'
-  streams, or captured CUDA graphs of a number of steps, fused (one launch
-  per phase over all runs, the particle push a persistent grid over
-  (run, tile) items) or per context.
+  streams, or captured CUDA graphs of a number of steps, per context or
+  fused with a number of launch chains (each chain one launch per phase
+  over its runs, the particle push a persistent grid over (run, tile)
+  items).
 
 Particles are sorted into their tiles at every step, inside the push, so
 there is no sort interval to choose; the CTA shape (256 threads) is compiled.
@@ -77,12 +78,12 @@ def tune_run(settings: dict, steps: int = 8, warmup: int = 3, tiles=None, slots=
     return dict(best, trials=trials)
 
 
-def tune_batch(settings_list, steps: int = 40, warmup: int = 3, graph_steps=(0, 20, 40), fused=(True, False),
+def tune_batch(settings_list, steps: int = 40, warmup: int = 3, graph_steps=(0, 20, 40), chains=(0, 1, 2, 4, 8),
                tile=(0, 0, 0), slots: float = 8.0) -> dict:
     """Time pic_batch_step of the runs for every launch form: launch by launch
     on the runs' streams (graph_steps 0), and for each number of steps per
-    captured graph, the fused graph (one launch per phase over all runs) and
-    the per-context graph.  Returns the fastest and all trials."""
+    captured graph, the per-context graph (chains 0) and the fused graph with
+    each number of launch chains.  Returns the fastest and all trials."""
     import torch
 
     import paper_1011_0917_gb300 as P
@@ -91,13 +92,13 @@ def tune_batch(settings_list, steps: int = 40, warmup: int = 3, graph_steps=(0, 
     try:
         batch = P.Batch(sims, graph_steps=0)
         batch.step(warmup)
-        forms = [(0, False)] + [(k, f) for k in graph_steps if k > 0 for f in fused]
-        for k, f in forms:
+        forms = [(0, 0)] + [(k, m) for k in graph_steps if k > 0 for m in chains]
+        for k, m in forms:
             # the runs' work spans their own streams: time on the host between
             # two device-wide synchronisations; a graph is captured by an
             # untimed first call of k steps and kept by the batch
             P.pic_batch_set_graph(batch.h, k)
-            P.pic_batch_set_fused(batch.h, f)
+            P.pic_batch_set_fused(batch.h, m)
             if k > 0:
                 batch.step(k)
             torch.cuda.synchronize()
@@ -105,7 +106,7 @@ def tune_batch(settings_list, steps: int = 40, warmup: int = 3, graph_steps=(0, 
             batch.step(steps)
             torch.cuda.synchronize()
             info = P.pic_batch_graph_info(batch.h)
-            trials.append({"graph_steps": k, "fused": bool(f and info["fused"]),
+            trials.append({"graph_steps": k, "chains": info["chains"] if k > 0 else 0,
                            "ms_per_step": 1e3 * (time.perf_counter() - t0) / steps})
         batch.close()
     finally:

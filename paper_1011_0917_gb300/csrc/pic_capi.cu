@@ -1080,9 +1080,11 @@ struct BatchGraph {
     size_t host_n = 0;
     cudaEvent_t join = nullptr;
     std::vector<cudaEvent_t> ev;  // one per context
-    bool fused = false;           // the graph is the batched form (one launch per phase and step)
+    int fused = 0;                // the graph is the batched form with this many launch chains (0: per context)
     void *fargs = nullptr;        // its argument structs, work-item prefix sums and queue counters
     int64_t launches = 0;         // its launches per replay (batched kernels and counter resets)
+    std::vector<cudaStream_t> chain_cs;  // the chains' streams (capture only)
+    std::vector<cudaEvent_t> chain_ev;
     void drop_graph()
     {
         if (exec) cudaGraphExecDestroy(exec);
@@ -1093,7 +1095,7 @@ struct BatchGraph {
         graph = nullptr;
         dev = nullptr;
         fargs = nullptr;
-        fused = false;
+        fused = 0;
         launches = 0;
         K = 0;
         sig.clear();
@@ -1106,6 +1108,10 @@ struct BatchGraph {
         if (join) cudaEventDestroy(join);
         for (cudaEvent_t e : ev)
             if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : chain_ev)
+            if (e) cudaEventDestroy(e);
+        for (cudaStream_t x : chain_cs)
+            if (x) cudaStreamDestroy(x);
         if (cs) cudaStreamDestroy(cs);
     }
 };
@@ -1113,7 +1119,7 @@ struct BatchGraph {
 struct pic_batch {
     std::vector<pic_ctx *> ctx;
     int graph_steps = 20;  // steps per captured graph (even; 0: streams only)
-    int fused = 1;         // capture the batched form of the steps where every launch has one
+    int fused = 4;         // launch chains of the batched form of a captured step (0: per-context graph)
     BatchGraph gr;
 };
 
@@ -1173,14 +1179,31 @@ static pic_status batch_capture_fused(pic_batch *b, int K, bool &ok)
         c0->err = std::string("batch graph: ") + cudaGetErrorString(e);
         return true;
     };
+    // the runs spread over the chains by size (tiles), largest first onto the
+    // least loaded chain
+    const int S = (int)std::min<size_t>((size_t)b->fused, nctx);
+    std::vector<int> chain_of(nctx, 0);
+    {
+        std::vector<size_t> by(nctx);
+        for (size_t i = 0; i < nctx; ++i) by[i] = i;
+        std::stable_sort(by.begin(), by.end(),
+                         [&](size_t x, size_t y) { return b->ctx[x]->g.ntiles > b->ctx[y]->g.ntiles; });
+        std::vector<int64_t> load(S, 0);
+        for (size_t i : by) {
+            const int m = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            chain_of[i] = m;
+            load[m] += b->ctx[i]->g.ntiles;
+        }
+    }
     BatchRecorder rec;
-    rec.nctx = (int)nctx;
+    rec.nctx = (int)((nctx + S - 1) / S);
     std::vector<int64_t> k0(nctx);
     for (size_t i = 0; i < nctx; ++i) k0[i] = b->ctx[i]->kernels;
     g_rec = &rec;
     for (int s = 0; s < K; ++s)
         for (size_t i = 0; i < nctx; ++i) {
             pic_ctx *c = b->ctx[i];
+            rec.chain = chain_of[i];
             rec.step = s;
             c->capturing = true;
             c->cap_scal = G.dev + i * K;
@@ -1204,9 +1227,11 @@ static pic_status batch_capture_fused(pic_batch *b, int K, bool &ok)
     for (size_t j = 0; j < order.size(); ++j) order[j] = j;
     std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
         const LaunchRecord &X = rec.recs[x], &Y = rec.recs[y];
+        if (X.chain != Y.chain) return X.chain < Y.chain;
         return X.step != Y.step ? X.step < Y.step : X.phase < Y.phase;
     });
     struct Group {
+        int chain;
         BatchLaunch fn;
         bool queue;
         std::vector<size_t> idx;
@@ -1217,13 +1242,15 @@ static pic_status batch_capture_fused(pic_batch *b, int K, bool &ok)
     for (size_t a = 0; a < order.size();) {
         size_t e = a;
         const LaunchRecord &A = rec.recs[order[a]];
-        while (e < order.size() && rec.recs[order[e]].step == A.step && rec.recs[order[e]].phase == A.phase) ++e;
+        while (e < order.size() && rec.recs[order[e]].chain == A.chain && rec.recs[order[e]].step == A.step &&
+               rec.recs[order[e]].phase == A.phase)
+            ++e;
         const size_t first = groups.size();
         for (size_t j = a; j < e; ++j) {
             const LaunchRecord &L = rec.recs[order[j]];
             size_t gi = first;
             while (gi < groups.size() && groups[gi].fn != L.fn) ++gi;
-            if (gi == groups.size()) groups.push_back(Group{L.fn, L.queue, {}});
+            if (gi == groups.size()) groups.push_back(Group{A.chain, L.fn, L.queue, {}});
             groups[gi].idx.push_back(order[j]);
         }
         a = e;
@@ -1256,24 +1283,41 @@ static pic_status batch_capture_fused(pic_batch *b, int K, bool &ok)
     if (bad(cudaMalloc(&G.fargs, off)) || bad(cudaMemcpy(G.fargs, hb.data(), off, cudaMemcpyHostToDevice)))
         return PIC_ERR_CUDA;
     unsigned char *d = static_cast<unsigned char *>(G.fargs);
+    while ((int)G.chain_cs.size() < S) {
+        cudaStream_t x = nullptr;
+        cudaEvent_t ev = nullptr;
+        if (bad(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking)) ||
+            bad(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)))
+            return PIC_ERR_CUDA;
+        G.chain_cs.push_back(x);
+        G.chain_ev.push_back(ev);
+    }
+    // every chain forks from the batch's stream and joins it at the end
     if (bad(cudaStreamBeginCapture(G.cs, cudaStreamCaptureModeRelaxed))) return PIC_ERR_CUDA;
+    cudaEventRecord(G.join, G.cs);
+    for (int m = 0; m < S; ++m) cudaStreamWaitEvent(G.chain_cs[m], G.join, 0);
     int64_t launches = 0;
     for (const Group &g : groups) {
         if (g.total <= 0) continue;
+        cudaStream_t x = G.chain_cs[g.chain];
         unsigned *q = g.queue ? reinterpret_cast<unsigned *>(d + g.q_off) : nullptr;
         if (q) {
-            cudaMemsetAsync(q, 0, sizeof(unsigned), G.cs);
+            cudaMemsetAsync(q, 0, sizeof(unsigned), x);
             ++launches;
         }
-        g.fn(d + g.args_off, reinterpret_cast<const int64_t *>(d + g.start_off), (int)g.idx.size(), g.total, q, G.cs);
+        g.fn(d + g.args_off, reinterpret_cast<const int64_t *>(d + g.start_off), (int)g.idx.size(), g.total, q, x);
         ++launches;
+    }
+    for (int m = 0; m < S; ++m) {
+        cudaEventRecord(G.chain_ev[m], G.chain_cs[m]);
+        cudaStreamWaitEvent(G.cs, G.chain_ev[m], 0);
     }
     const cudaError_t e = cudaStreamEndCapture(G.cs, &G.graph);
     if (bad(e) || bad(cudaGetLastError()) || bad(cudaGraphInstantiate(&G.exec, G.graph, 0))) {
         G.drop_graph();
         return PIC_ERR_CUDA;
     }
-    G.fused = true;
+    G.fused = S;
     G.launches = launches;
     G.K = K;
     ok = true;
@@ -1427,7 +1471,7 @@ extern "C" pic_status pic_batch_set_graph(pic_batch *b, int steps_per_graph)
 
 extern "C" pic_status pic_batch_set_fused(pic_batch *b, int fused)
 {
-    if (!b || (fused != 0 && fused != 1)) return PIC_ERR_ARG;
+    if (!b || fused < 0) return PIC_ERR_ARG;
     if (b->fused != fused) {
         if (b->gr.cs) cudaStreamSynchronize(b->gr.cs);
         b->gr.drop_graph();
@@ -1439,7 +1483,7 @@ extern "C" pic_status pic_batch_set_fused(pic_batch *b, int fused)
 extern "C" pic_status pic_batch_graph_info(pic_batch *b, int *fused, int64_t *launches_per_replay, int *steps)
 {
     if (!b) return PIC_ERR_ARG;
-    if (fused) *fused = b->gr.exec && b->gr.fused ? 1 : 0;
+    if (fused) *fused = b->gr.exec ? b->gr.fused : 0;
     if (launches_per_replay) *launches_per_replay = b->gr.exec ? b->gr.launches : 0;
     if (steps) *steps = b->gr.exec ? b->gr.K : 0;
     return PIC_OK;

@@ -317,57 +317,87 @@ __global__ void __launch_bounds__(256) yee_batch_kernel(const YeeArgs<real> *__r
 
 // ------------------------------------------------------- 2D tiled Yee
 
+// Shared rows of the 2D tile kernels: x from x0 - 4 to x0 + 67 of a tile
+// whose own columns are x0 .. x0 + 63 (x0 a multiple of 64), kRowPitch
+// elements per row, so that every 16-byte chunk of a row is a 16-byte chunk
+// of the grid row (where the grid width is a multiple of 16 bytes).
+constexpr int kRowX = 64, kRowPitch = 72, kRowOrigin = 4;
+
+// Copies rows zo .. zo + nrows - 1 of one component into dst[row][x - x0 + 4]
+// with cp.async: 16-byte copies for the chunks inside the grid, element
+// copies (x wrapped) for the chunks across its periodic x edge; a row the
+// component does not have (plane(k) < 0) is zero.
+template <typename real, typename PlaneFn>
+__device__ __forceinline__ void stage_rows(real *dst, const real *src, int nrows, int zo, int x0, const Geom &g,
+                                           PlaneFn plane)
+{
+    constexpr int V = 16 / (int)sizeof(real), NCH = kRowPitch / V;
+    const bool vec = g.nx % V == 0 && (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
+    for (int q = (int)threadIdx.x; q < nrows * NCH; q += (int)blockDim.x) {
+        const int row = q / NCH, ch = q - row * NCH;
+        const int kk = plane(zo + row);
+        real *d = dst + row * kRowPitch + ch * V;
+        const int xs = x0 - kRowOrigin + ch * V;
+        if (kk < 0) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) d[v] = real(0);
+            continue;
+        }
+        const real *srow = src + (int64_t)kk * g.plane;
+        if (vec && xs >= 0 && xs + V <= g.nx) {
+            __pipeline_memcpy_async(d, srow + xs, 16);
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) __pipeline_memcpy_async(d + v, srow + wrapi(xs + v, g.nx), sizeof(real));
+        }
+    }
+}
+
 // The same Yee step on 2D grids, without the march: a CTA owns a tile of
-// kY2X x kY2Z (x, z) nodes and copies, all at once with cp.async, E^n on
-// x0-1 .. x0+kY2X+1, z0-2 .. z0+kY2Z+1, B^n on x0-1 .. x0+kY2X,
-// z0-2 .. z0+kY2Z and J on x0 .. x0+kY2X, z0-1 .. z0+kY2Z into shared memory
-// (x wraps; planes a component does not have are zero), so that a tile
-// costs one load latency however narrow the grid is (the march pays one
-// per plane, which dominates on grids a few hundred nodes wide).  Then, in
-// shared memory and node by node with the march's arithmetic: Bh in place
-// of B^n, E' in place of E^n on the J region, Mur's condition for the end
-// planes (from the saved E^n of their inner neighbours), and E', B' of the
-// own nodes to the other buffer.  (d/dy = 0: the y derivatives of the 3D
-// formulas are zero terms.)
-constexpr int kY2X = 64, kY2Z = 16;
-constexpr int kY2EX = kY2X + 3, kY2EZ = kY2Z + 4;  // E^n region
-constexpr int kY2BX = kY2X + 2, kY2BZ = kY2Z + 3;  // B^n region
-constexpr int kY2JX = kY2X + 1, kY2JZ = kY2Z + 2;  // J region (where E' is computed)
+// 64 x kY2Z (x, z) nodes and copies, all at once with cp.async (above),
+// x0 - 4 .. x0 + 67 of E^n on planes z0 - 2 .. z0 + kY2Z + 1, of B^n on
+// z0 - 2 .. z0 + kY2Z and of J on z0 - 1 .. z0 + kY2Z into shared memory
+// (planes a component does not have are zero), so that a tile costs one load
+// latency however narrow the grid is (the march pays one per plane, which
+// dominates on grids a few hundred nodes wide).  Then, in shared memory and
+// node by node with the march's arithmetic: Bh in place of B^n on
+// x0 - 1 .. x0 + 64, E' in place of E^n on x0 .. x0 + 64, z0 - 1 .. z0 + kY2Z,
+// Mur's condition for the end planes (from the saved E^n of their inner
+// neighbours), and E', B' of the own nodes to the other buffer.  (d/dy = 0:
+// the y derivatives of the 3D formulas are zero terms.)
+constexpr int kY2Z = 16;
+constexpr int kY2EZ = kY2Z + 4, kY2BZ = kY2Z + 3, kY2JZ = kY2Z + 2;  // rows of E^n, B^n, J
 
 template <typename real>
 __device__ __forceinline__ void yee2d_body(const YeeArgs<real> &a, const int bx_, const int bz_)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    real *sE = reinterpret_cast<real *>(smem_raw);  // [3][kY2EZ][kY2EX], E^n then E'
-    real *sB = sE + 3 * kY2EZ * kY2EX;              // [3][kY2BZ][kY2BX], B^n then Bh
-    real *sJ = sB + 3 * kY2BZ * kY2BX;              // [3][kY2JZ][kY2JX]
-    real *sM = sJ + 3 * kY2JZ * kY2JX;              // [2 ends][2 comps][kY2EX]: E^n x, y of planes 1, nz-1
-    constexpr int PE = kY2EZ * kY2EX, PB = kY2BZ * kY2BX, PJ = kY2JZ * kY2JX;
+    constexpr int W = kRowPitch;
+    constexpr int PE = kY2EZ * W, PB = kY2BZ * W, PJ = kY2JZ * W;
+    real *sE = reinterpret_cast<real *>(smem_raw);  // [3][kY2EZ][W], E^n then E'
+    real *sB = sE + 3 * PE;                          // [3][kY2BZ][W], B^n then Bh
+    real *sJ = sB + 3 * PB;                          // [3][kY2JZ][W]
+    real *sM = sJ + 3 * PJ;                          // [2 ends][2 comps][W]: E^n x, y of planes 1, nz-1
     const Geom &g = a.g;
     const bool per = g.bc_z == 0;
     const int nzo = per ? g.nz : g.nz + 1;
-    const int x0 = bx_ * kY2X, z0 = bz_ * kY2Z;
+    const int x0 = bx_ * kRowX, z0 = bz_ * kY2Z;
     const int z1 = z0 + kY2Z < nzo ? z0 + kY2Z : nzo;
     const int tid = (int)threadIdx.x, nt = (int)blockDim.x;
-    auto mem_plane = [&](int k, bool half) {
-        return per ? wrapi(k, g.nz) : (k >= 0 && k <= zmax_of(g, half) ? k : -1);
+    auto plane_of = [&](bool half) {
+        return [&g, per, half](int k) { return per ? wrapi(k, g.nz) : (k >= 0 && k <= zmax_of(g, half) ? k : -1); };
     };
-    auto gx = [&](int x) { return x >= 0 && x < g.nx ? x : wrapi(x, g.nx); };
+    const auto pint = plane_of(false), phalf = plane_of(true);
     // ---- copy E^n (Ez half-z), B^n (Bx, By half-z), J (Jz half-z)
-    auto stage = [&](const real *src, real *dst, int nx_, int np, int xo, int zo, bool half) {
-        for (int r = tid; r < np; r += nt) {
-            const int pz = r / nx_, px = r - pz * nx_;
-            const int kk = mem_plane(zo + pz, half);
-            if (kk >= 0) __pipeline_memcpy_async(dst + r, src + (int64_t)kk * g.plane + gx(xo + px), sizeof(real));
-            else dst[r] = real(0);
-        }
-    };
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        stage(a.E[c], sE + c * PE, kY2EX, PE, x0 - 1, z0 - 2, c == 2);
-        stage(a.B[c], sB + c * PB, kY2BX, PB, x0 - 1, z0 - 2, c != 2);
-        stage(a.J[c], sJ + c * PJ, kY2JX, PJ, x0, z0 - 1, c == 2);
-    }
+    stage_rows(sE, a.E[0], kY2EZ, z0 - 2, x0, g, pint);
+    stage_rows(sE + PE, a.E[1], kY2EZ, z0 - 2, x0, g, pint);
+    stage_rows(sE + 2 * PE, a.E[2], kY2EZ, z0 - 2, x0, g, phalf);
+    stage_rows(sB, a.B[0], kY2BZ, z0 - 2, x0, g, phalf);
+    stage_rows(sB + PB, a.B[1], kY2BZ, z0 - 2, x0, g, phalf);
+    stage_rows(sB + 2 * PB, a.B[2], kY2BZ, z0 - 2, x0, g, pint);
+    stage_rows(sJ, a.J[0], kY2JZ, z0 - 1, x0, g, pint);
+    stage_rows(sJ + PJ, a.J[1], kY2JZ, z0 - 1, x0, g, pint);
+    stage_rows(sJ + 2 * PJ, a.J[2], kY2JZ, z0 - 1, x0, g, phalf);
     __pipeline_commit();
     __pipeline_wait_prior(0);
     __syncthreads();
@@ -375,69 +405,73 @@ __device__ __forceinline__ void yee2d_body(const YeeArgs<real> &a, const int bx_
     const bool mur_lo = !per && z0 - 1 <= 0 && 0 <= z0 + kY2Z - 1;        // plane 0 is computed here
     const bool mur_hi = !per && z0 - 1 <= g.nz - 1 && g.nz <= z0 + kY2Z;  // plane nz too
     if (mur_lo || mur_hi) {
-        for (int r = tid; r < 2 * 2 * kY2EX; r += nt) {
-            const int end = r / (2 * kY2EX), c = (r / kY2EX) & 1, px = r % kY2EX;
-            const int k = end == 0 ? 1 : g.nz - 1;
-            const int pz = k - (z0 - 2);
-            sM[r] = (pz >= 0 && pz < kY2EZ) ? sE[c * PE + pz * kY2EX + px] : real(0);
+        for (int r = tid; r < 2 * 2 * W; r += nt) {
+            const int end = r / (2 * W), c = (r / W) & 1, j = r % W;
+            const int pz = (end == 0 ? 1 : g.nz - 1) - (z0 - 2);
+            sM[r] = (pz >= 0 && pz < kY2EZ) ? sE[c * PE + pz * W + j] : real(0);
         }
     }
-    // ---- Bh(k) = B^n(k) - (dt/2) curl E^n on the whole B region
+    // ---- Bh(k) = B^n(k) - (dt/2) curl E^n on every B row, x0 - 1 .. x0 + 64
     const real zero = real(0);
-    for (int r = tid; r < PB; r += nt) {
-        const int pb = r / kY2BX, xb = r - pb * kY2BX;
-        const int k = z0 - 2 + pb;
-        const int o = pb * kY2EX + xb;  // the same node in the E region
-        const bool vxy = mem_plane(k, true) >= 0, vz = mem_plane(k, false) >= 0;
-        const real dEy_dz = (sE[PE + o + kY2EX] - sE[PE + o]) * a.ihz;
-        const real dEx_dz = (sE[o + kY2EX] - sE[o]) * a.ihz;
-        const real dEz_dx = (sE[2 * PE + o + 1] - sE[2 * PE + o]) * a.ihx;
-        const real dEy_dx = (sE[PE + o + 1] - sE[PE + o]) * a.ihx;
-        sB[r] = vxy ? sB[r] - a.hb * (zero - dEy_dz) : real(0);
-        sB[PB + r] = vxy ? sB[PB + r] - a.hb * (dEx_dz - dEz_dx) : real(0);
-        sB[2 * PB + r] = vz ? sB[2 * PB + r] - a.hb * (dEy_dx - zero) : real(0);
+    {
+        constexpr int NX = kRowX + 2;
+        for (int r = tid; r < kY2BZ * NX; r += nt) {
+            const int pb = r / NX, j = r - pb * NX + kRowOrigin - 1;
+            const int k = z0 - 2 + pb;
+            const int o = pb * W + j;  // the same index in the E and B rows
+            const bool vxy = phalf(k) >= 0, vz = pint(k) >= 0;
+            const real dEy_dz = (sE[PE + o + W] - sE[PE + o]) * a.ihz;
+            const real dEx_dz = (sE[o + W] - sE[o]) * a.ihz;
+            const real dEz_dx = (sE[2 * PE + o + 1] - sE[2 * PE + o]) * a.ihx;
+            const real dEy_dx = (sE[PE + o + 1] - sE[PE + o]) * a.ihx;
+            sB[o] = vxy ? sB[o] - a.hb * (zero - dEy_dz) : real(0);
+            sB[PB + o] = vxy ? sB[PB + o] - a.hb * (dEx_dz - dEz_dx) : real(0);
+            sB[2 * PB + o] = vz ? sB[2 * PB + o] - a.hb * (dEy_dx - zero) : real(0);
+        }
     }
     __syncthreads();
-    // ---- E'(k) = E^n(k) + dt (curl Bh - 2 pi J) on x0 .. x0+kY2X, z0-1 .. z0+kY2Z
-    for (int r = tid; r < PJ; r += nt) {
-        const int lz = r / kY2JX, lx = r - lz * kY2JX;
-        const int k = z0 - 1 + lz;
-        const int pe = lz + 1, xe = lx + 1;  // in the E region; the same indices in the B region
-        const int oe = pe * kY2EX + xe, ob = pe * kY2BX + xe;
-        const bool vz = mem_plane(k, true) >= 0;
-        const bool vxy = per || (k >= 1 && k <= g.nz - 1);
-        if (vxy) {
-            const real dBy_dz = (sB[PB + ob] - sB[PB + ob - kY2BX]) * a.ihz;
-            sE[oe] = sE[oe] + a.he * ((zero - dBy_dz) - a.twopi * sJ[r]);
-            const real dBx_dz = (sB[ob] - sB[ob - kY2BX]) * a.ihz;
-            const real dBz_dx = (sB[2 * PB + ob] - sB[2 * PB + ob - 1]) * a.ihx;
-            sE[PE + oe] = sE[PE + oe] + a.he * ((dBx_dz - dBz_dx) - a.twopi * sJ[PJ + r]);
+    // ---- E'(k) = E^n(k) + dt (curl Bh - 2 pi J) on x0 .. x0 + 64, z0 - 1 .. z0 + kY2Z
+    {
+        constexpr int NX = kRowX + 1;
+        for (int r = tid; r < kY2JZ * NX; r += nt) {
+            const int lz = r / NX, j = r - lz * NX + kRowOrigin;
+            const int k = z0 - 1 + lz;
+            const int o = (lz + 1) * W + j;  // in the E and B rows
+            const int oj = lz * W + j;
+            const bool vz = phalf(k) >= 0;
+            const bool vxy = per || (k >= 1 && k <= g.nz - 1);
+            if (vxy) {
+                const real dBy_dz = (sB[PB + o] - sB[PB + o - W]) * a.ihz;
+                sE[o] = sE[o] + a.he * ((zero - dBy_dz) - a.twopi * sJ[oj]);
+                const real dBx_dz = (sB[o] - sB[o - W]) * a.ihz;
+                const real dBz_dx = (sB[2 * PB + o] - sB[2 * PB + o - 1]) * a.ihx;
+                sE[PE + o] = sE[PE + o] + a.he * ((dBx_dz - dBz_dx) - a.twopi * sJ[PJ + oj]);
+            }
+            const real dBy_dx = (sB[PB + o] - sB[PB + o - 1]) * a.ihx;
+            sE[2 * PE + o] = vz ? sE[2 * PE + o] + a.he * ((dBy_dx - zero) - a.twopi * sJ[2 * PJ + oj]) : real(0);
         }
-        const real dBy_dx = (sB[PB + ob] - sB[PB + ob - 1]) * a.ihx;
-        sE[2 * PE + oe] = vz ? sE[2 * PE + oe] + a.he * ((dBy_dx - zero) - a.twopi * sJ[2 * PJ + r]) : real(0);
     }
     __syncthreads();
     // ---- Mur: Ex, Ey of plane kt from plane kn, its neighbour inside the box
     if (mur_lo || mur_hi) {
-        for (int r = tid; r < 2 * (kY2X + 1); r += nt) {
-            const int end = r / (kY2X + 1), xe = r % (kY2X + 1) + 1;
+        for (int r = tid; r < 2 * (kRowX + 1); r += nt) {
+            const int end = r / (kRowX + 1), j = r % (kRowX + 1) + kRowOrigin;
             if (end == 0 ? !mur_lo : !mur_hi) continue;
             const int kt = end == 0 ? 0 : g.nz, kn = end == 0 ? 1 : g.nz - 1;
-            const int ot = (kt - (z0 - 2)) * kY2EX + xe, on = (kn - (z0 - 2)) * kY2EX + xe;
-            const real *old = sM + end * 2 * kY2EX;  // E^n of plane kn
+            const int ot = (kt - (z0 - 2)) * W + j, on = (kn - (z0 - 2)) * W + j;
+            const real *old = sM + end * 2 * W;  // E^n of plane kn
 #pragma unroll
             for (int c = 0; c < 2; ++c)
-                sE[c * PE + ot] = old[c * kY2EX + xe] + a.mur * (sE[c * PE + on] - sE[c * PE + ot]);
+                sE[c * PE + ot] = old[c * W + j] + a.mur * (sE[c * PE + on] - sE[c * PE + ot]);
         }
         __syncthreads();
     }
     // ---- E', B' of the own nodes
-    for (int r = tid; r < kY2X * kY2Z; r += nt) {
-        const int lz = r / kY2X, lx = r - lz * kY2X;
+    for (int r = tid; r < kRowX * kY2Z; r += nt) {
+        const int lz = r / kRowX, lx = r - lz * kRowX;
         const int k = z0 + lz, x = x0 + lx;
         if (k >= z1 || x >= g.nx) continue;
-        const int pe = lz + 2, xe = lx + 1;
-        const int of = pe * kY2EX + xe, ob = pe * kY2BX + xe;
+        const int of = (lz + 2) * W + lx + kRowOrigin;  // in the E and B rows
         const int64_t o = (int64_t)k * g.plane + x;
         const bool vxy = k <= zmax_of(g, false), vz = k <= zmax_of(g, true);
         if (vxy) {
@@ -446,15 +480,15 @@ __device__ __forceinline__ void yee2d_body(const YeeArgs<real> &a, const int bx_
         }
         if (vz) {
             a.E1[2][o] = sE[2 * PE + of];
-            const real dEy_dz = (sE[PE + of + kY2EX] - sE[PE + of]) * a.ihz;
-            a.B1[0][o] = sB[ob] - a.hb * (zero - dEy_dz);
-            const real dEx_dz = (sE[of + kY2EX] - sE[of]) * a.ihz;
+            const real dEy_dz = (sE[PE + of + W] - sE[PE + of]) * a.ihz;
+            a.B1[0][o] = sB[of] - a.hb * (zero - dEy_dz);
+            const real dEx_dz = (sE[of + W] - sE[of]) * a.ihz;
             const real dEz_dx = (sE[2 * PE + of + 1] - sE[2 * PE + of]) * a.ihx;
-            a.B1[1][o] = sB[PB + ob] - a.hb * (dEx_dz - dEz_dx);
+            a.B1[1][o] = sB[PB + of] - a.hb * (dEx_dz - dEz_dx);
         }
         if (vxy) {
             const real dEy_dx = (sE[PE + of + 1] - sE[PE + of]) * a.ihx;
-            a.B1[2][o] = sB[2 * PB + ob] - a.hb * (dEy_dx - zero);
+            a.B1[2][o] = sB[2 * PB + of] - a.hb * (dEy_dx - zero);
         }
     }
 }
@@ -478,8 +512,7 @@ __global__ void __launch_bounds__(256) yee2d_batch_kernel(const YeeArgs<real> *_
 template <typename real>
 static size_t yee2d_smem()
 {
-    return sizeof(real) * (3 * (size_t)kY2EZ * kY2EX + 3 * (size_t)kY2BZ * kY2BX + 3 * (size_t)kY2JZ * kY2JX +
-                           4 * (size_t)kY2EX);
+    return sizeof(real) * (size_t)kRowPitch * (3 * (kY2EZ + kY2BZ + kY2JZ) + 4);
 }
 
 template <typename real>
@@ -541,7 +574,7 @@ void launch_yee(const Geom &g, real *const F[9], real *const F1[6], double dt, d
     const int nzo = g.bc_z == 0 ? g.nz : g.nz + 1;
     const bool is3 = g.dim == 3;
     if (!is3) {
-        const int ntx = (g.nx + kY2X - 1) / kY2X, ntz = (nzo + kY2Z - 1) / kY2Z;
+        const int ntx = (g.nx + kRowX - 1) / kRowX, ntz = (nzo + kY2Z - 1) / kY2Z;
         a.cz = kY2Z;
         a.nchunks = ntx;
         if (record_launch(kBPYee, launch_yee2d_batch<real>, a, (int64_t)ntx * ntz)) return;
@@ -963,51 +996,42 @@ static bool launch_filter_tma(const Geom &g, const real *in, real *out, unsigned
     return true;
 }
 
-// The same H passes on 2D grids, without the march: a CTA owns kF2X x kF2Z
+// The same H passes on 2D grids, without the march: a CTA owns 64 x kF2Z
 // (x, z) nodes of the three components and copies, all at once with
-// cp.async into shared memory, their input
-// on x0 - H .. x0 + kF2X + H - 1 (wrapped) and z0 - H .. z0 + kF2Z + H - 1
-// (zero or wrapped beyond the grid); per component, the x passes are the
-// binomial stencil of width 2H + 1 (filter_march_kernel's sum), and the z
-// passes follow one level at a time in shared memory, each narrower by a
-// plane on both sides and zero outside the component's z range, as in the
-// march.
-constexpr int kF2X = 64, kF2Z = 32;
+// cp.async (stage_rows), x0 - 4 .. x0 + 67 of their input on planes
+// z0 - H .. z0 + kF2Z + H - 1 (zero or wrapped beyond the grid); per
+// component, the x passes are the binomial stencil of width 2H + 1
+// (filter_march_kernel's sum), and the z passes follow one level at a time in
+// shared memory, each narrower by a plane on both sides and zero outside the
+// component's z range, as in the march.
+constexpr int kF2Z = 32;
 
 template <typename real, int H>
 __device__ __forceinline__ void filter2d_body(const Geom &g, const real *in, real *out, const int bx_, const int bz_)
 {
-    constexpr int IX = kF2X + 2 * H, IZ = kF2Z + 2 * H, PI = IX * IZ, PL = kF2X * IZ;
-    constexpr int W = 2 * H + 1;
+    static_assert(H <= kRowOrigin, "the halo fits the staged rows");
+    constexpr int W = kRowPitch, IZ = kF2Z + 2 * H, PI = IZ * W, PL = kRowX * IZ;
+    constexpr int NW = 2 * H + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    real *sI = reinterpret_cast<real *>(smem_raw);  // [3][IZ][IX] input
-    real *sL = sI + 3 * PI;                          // [2][IZ][kF2X] levels (ping-pong)
-    real wb[W];
+    real *sI = reinterpret_cast<real *>(smem_raw);  // [3][IZ][W] input
+    real *sL = sI + 3 * PI;                          // [2][IZ][64] levels (ping-pong)
+    real wb[NW];
     {
         double c = 1.0;
-        for (int i = 0; i < W; ++i) {
+        for (int i = 0; i < NW; ++i) {
             wb[i] = (real)(c / (double)(1 << (2 * H)));
             c = c * (double)(2 * H - i) / (double)(i + 1);
         }
     }
     const bool per = g.bc_z == 0;
-    const int x0 = bx_ * kF2X, z0 = bz_ * kF2Z;
+    const int x0 = bx_ * kRowX, z0 = bz_ * kF2Z;
     const int tid = (int)threadIdx.x, nt = (int)blockDim.x;
     const int zmax_xy = zmax_of(g, false), zmax_z = zmax_of(g, true);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const int zmax = c == 2 ? zmax_z : zmax_xy;
-        for (int r = tid; r < PI; r += nt) {
-            const int pz = r / IX, px = r - pz * IX;
-            const int k = z0 - H + pz, x = x0 - H + px;
-            const bool have = per || (k >= 0 && k <= zmax);
-            const int kk = per ? wrapi(k, g.nz) : k;
-            const int xx = x >= 0 && x < g.nx ? x : wrapi(x, g.nx);
-            if (have)
-                __pipeline_memcpy_async(sI + c * PI + r, in + (size_t)c * g.ncomp + (int64_t)kk * g.plane + xx,
-                                        sizeof(real));
-            else sI[c * PI + r] = real(0);
-        }
+        stage_rows(sI + c * PI, in + (size_t)c * g.ncomp, IZ, z0 - H, x0, g,
+                   [&g, per, zmax](int k) { return per ? wrapi(k, g.nz) : (k >= 0 && k <= zmax ? k : -1); });
     }
     __pipeline_commit();
     __pipeline_wait_prior(0);
@@ -1017,24 +1041,24 @@ __device__ __forceinline__ void filter2d_body(const Geom &g, const real *in, rea
         const int zmax = c == 2 ? zmax_z : zmax_xy;
         const real *I = sI + c * PI;
         real *L0 = sL, *L1 = sL + PL;
-        // level 0: the x stencil on every loaded plane
+        // level 0: the x stencil on every staged plane
         for (int r = tid; r < PL; r += nt) {
-            const int pz = r / kF2X, lx = r - pz * kF2X;
+            const int pz = r / kRowX, lx = r - pz * kRowX;
             const int k = z0 - H + pz;
             real v = 0;
 #pragma unroll
-            for (int i = 0; i < W; ++i) v += wb[i] * I[pz * IX + lx + i];
+            for (int i = 0; i < NW; ++i) v += wb[i] * I[pz * W + lx + kRowOrigin - H + i];
             L0[r] = (per || (k >= 0 && k <= zmax)) ? v : real(0);
         }
         __syncthreads();
-        // level p on planes H - p .. IZ - 1 - (H - p) of the loaded range
+        // level p on planes p .. IZ - 1 - p of the staged range
 #pragma unroll
         for (int p = 1; p <= H; ++p) {
             for (int r = tid; r < PL; r += nt) {
-                const int pz = r / kF2X;
+                const int pz = r / kRowX;
                 if (pz < p || pz >= IZ - p) continue;
                 const int k = z0 - H + pz;
-                const real nv = real(0.25) * L0[r - kF2X] + real(0.5) * L0[r] + real(0.25) * L0[r + kF2X];
+                const real nv = real(0.25) * L0[r - kRowX] + real(0.5) * L0[r] + real(0.25) * L0[r + kRowX];
                 L1[r] = (per || (k >= 0 && k <= zmax)) ? nv : real(0);
             }
             __syncthreads();
@@ -1042,11 +1066,11 @@ __device__ __forceinline__ void filter2d_body(const Geom &g, const real *in, rea
             L0 = L1;
             L1 = t;
         }
-        for (int r = tid; r < kF2X * kF2Z; r += nt) {
-            const int lz = r / kF2X, lx = r - lz * kF2X;
+        for (int r = tid; r < kRowX * kF2Z; r += nt) {
+            const int lz = r / kRowX, lx = r - lz * kRowX;
             const int k = z0 + lz, x = x0 + lx;
             if (k > g.nz || x >= g.nx) continue;
-            out[(size_t)c * g.ncomp + (int64_t)k * g.plane + x] = k > zmax ? real(0) : L0[(lz + H) * kF2X + lx];
+            out[(size_t)c * g.ncomp + (int64_t)k * g.plane + x] = k > zmax ? real(0) : L0[(lz + H) * kRowX + lx];
         }
         __syncthreads();
     }
@@ -1071,7 +1095,7 @@ __global__ void __launch_bounds__(256) filter2d_batch_kernel(const MarchArgs<rea
 template <typename real, int H>
 static size_t filter2d_smem()
 {
-    return sizeof(real) * (3 * (size_t)(kF2X + 2 * H) * (kF2Z + 2 * H) + 2 * (size_t)kF2X * (kF2Z + 2 * H));
+    return sizeof(real) * (3 * (size_t)kRowPitch * (kF2Z + 2 * H) + 2 * (size_t)kRowX * (kF2Z + 2 * H));
 }
 
 template <typename real, int H>
@@ -1091,7 +1115,7 @@ static void launch_march(const Geom &g, const real *in, real *out, cudaStream_t 
     const int nzo = g.nz + 1;
     if constexpr (DIM == 2) {
         // the tiled kernel (2D grids)
-        const int ntx = (g.nx + kF2X - 1) / kF2X, ntz = (nzo + kF2Z - 1) / kF2Z;
+        const int ntx = (g.nx + kRowX - 1) / kRowX, ntz = (nzo + kF2Z - 1) / kF2Z;
         if (record_launch(kBPFilter, launch_filter2d_batch<real, H>, MarchArgs<real>{g, in, out, ntx, ntz},
                           (int64_t)ntx * ntz))
             return;

@@ -564,13 +564,14 @@ using BatchLaunch = void (*)(const void *args, const int64_t *start, int n, int6
 // phases in the order a step issues them
 enum BatchPhase : int { kBPZero = 0, kBPPush, kBPIons, kBPAntenna, kBPFilter, kBPYee, kBPInject, kBPCount };
 struct LaunchRecord {
-    int step, phase;
+    int chain, step, phase;
     BatchLaunch fn;
     std::vector<unsigned char> args;
     int64_t items;
     bool queue;  // the batched kernel pulls its items from a device counter
 };
 struct BatchRecorder {
+    int chain = 0;             // the launch chain (stream) the current run belongs to
     int step = 0;
     int nctx = 1;              // runs in the batch (field kernels size their z chunks for all of them)
     bool unsupported = false;  // the step asked for something the batched step does not do
@@ -586,6 +587,7 @@ inline bool record_launch(int phase, BatchLaunch fn, const A &a, int64_t items, 
     BatchRecorder *r = g_rec;
     if (!r) return false;
     LaunchRecord L;
+    L.chain = r->chain;
     L.step = r->step;
     L.phase = phase;
     L.fn = fn;

@@ -23,7 +23,7 @@ def O():
     return O
 
 
-@pytest.mark.parametrize("graph_steps,fused", [(10, True), (10, False), (0, True)])
+@pytest.mark.parametrize("graph_steps,fused", [(10, 2), (10, 0), (0, 1)])
 @pytest.mark.parametrize("prec", [FP64, FP32])
 def test_batch_matches_each_run(O, prec, graph_steps, fused):
     import torch
@@ -134,14 +134,14 @@ def test_fused_batch_mixed_kernels(O, prec):
     STEPS, K = 20, 10
     fused = [_mixed_run(P, torch, O, spec, prec, True) for spec in MIXED]
     plain = [_mixed_run(P, torch, O, spec, prec, False)[0] for spec in MIXED]
-    bf = P.Batch([s for s, _ in fused], graph_steps=K, fused=True)
+    bf = P.Batch([s for s, _ in fused], graph_steps=K, fused=1)
     bp = P.Batch(plain, graph_steps=K, fused=False)
     bf.step(STEPS)
     bp.step(STEPS)
     info_f, info_p = bf.graph_info(), bp.graph_info()
     bf.close()
     bp.close()
-    assert info_f["fused"] and not info_p["fused"] and info_f["steps"] == K
+    assert info_f["chains"] == 1 and not info_p["fused"] and info_f["steps"] == K
     # one launch per phase and instance, a counter reset per particle launch
     assert 0 < info_f["launches_per_replay"] < info_p["launches_per_replay"], (info_f, info_p)
     assert info_f["launches_per_replay"] <= K * (1 + 2 * 7 + 1 + 1 + 2 * 2 + 2 + 2 + 1), info_f

@@ -61,11 +61,12 @@ def test_autotune_picks_a_compiled_configuration():
 
 def test_autotune_batch_tries_every_launch_form():
     """The batch autotuner times the stream path and, per graph length, the
-    fused and per-context graphs, and returns the fastest."""
+    per-context graph and the fused graph with 1 and 2 launch chains, and
+    returns the fastest."""
     from paper_1011_0917_gb300 import autotune
     runs = [{"grid": dict(G, precision=FP32, seed=17 + r), "plasma": PLASMA, "laser": dict(LASER, pol=1)}
             for r in range(3)]
-    best = autotune.tune_batch(runs, steps=10, warmup=2, graph_steps=(10,))
-    forms = {(t["graph_steps"], t["fused"]) for t in best["trials"]}
-    assert forms == {(0, False), (10, True), (10, False)}, best["trials"]
+    best = autotune.tune_batch(runs, steps=10, warmup=2, graph_steps=(10,), chains=(0, 1, 2))
+    forms = {(t["graph_steps"], t["chains"]) for t in best["trials"]}
+    assert forms == {(0, 0), (10, 0), (10, 1), (10, 2)}, best["trials"]
     assert best["ms_per_step"] == min(t["ms_per_step"] for t in best["trials"])
