@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--slots-per-cell", type=float, default=10.0)
+    ap.add_argument("--touched-advance", type=int, default=300,
+                    help="steps further into the stage for the second push window that separates the cost of "
+                         "a field-touched electron from that of a paired one (0: skip)")
     ap.add_argument("--sort-every", type=int, default=0,
                     help="order every tile's particles by cell before every N-th step (0: never)")
     ap.add_argument("--advance", type=int, default=-1,
@@ -69,6 +72,8 @@ def parse():
                     help="steps of the adjoint/forward timing on one c4 run (0: skip)")
     ap.add_argument("--c4", type=int, default=64,
                     help="runs of the batched scan timed after the main measurement (0: none)")
+    ap.add_argument("--c4-only", action="store_true",
+                    help="time only the batched scan of --c4 runs (launch forms of pic_batch_step)")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="time only the adjoint/forward leg (one c4 run, --adjoint-steps steps, a checkpoint "
                          "every --checkpoint-every) and print its record")
@@ -153,7 +158,9 @@ def traffic_from_profiles(kernel_key: str):
         return None
     from paper_1011_0917_gb300 import build
     import hashlib
-    h = hashlib.sha256(open(os.path.join(build.CSRC, "pic_particles.cu"), "rb").read()).hexdigest()[:16]
+    # the electron kernel's sources: its per-tile body and the kernel itself
+    src = b"".join(open(os.path.join(build.CSRC, f), "rb").read() for f in ("pic_push.cuh", "pic_particles.cu"))
+    h = hashlib.sha256(src).hexdigest()[:16]
     if e.get("source_sha") != h:
         return None
     return e.get("dram_bytes_per_launch")
@@ -301,6 +308,37 @@ def run_ours(args, rank, world, local):
                "yee_phase_ms_with": yee, "yee_phase_ms_without": yee0, "added_ms_per_step": yee - yee0,
                "buffer_bytes": int(sim._btd.numel())}
         P.pic_btd_setup(ctx, None, 0, 0)
+
+    # the cost of a field-touched electron: the push timed again further into
+    # the stage, where fewer electrons are still paired with their ion; with
+    # push time = a * paired + b * released (b: a released electron together
+    # with the record of its ion), the two windows give a and b
+    touched = None
+    if args.touched_advance > 0 and g["gamma_boost"] > 1.0 and not args.explicit_ions:
+        P.pic_step(ctx, args.touched_advance)
+        k = max(1, min(args.steps, 8))
+        d2 = sim.diagnostics()
+        P.pic_profile(ctx, True)
+        P.pic_profile_read(ctx)
+        P.pic_step(ctx, k)
+        ph2, calls2, _ = P.pic_profile_read(ctx)
+        P.pic_profile(ctx, False)
+        d3 = sim.diagnostics()
+        p1 = 0.5 * (d0.n_paired + d1.n_paired)
+        r1 = n_e - p1
+        p2 = 0.5 * (d2.n_paired + d3.n_paired)
+        r2 = 0.5 * (d2.n_particles[0] + d3.n_particles[0]) - p2
+        t1, t2 = push_ms, ph2[1] / max(calls2[1], 1)
+        det = p1 * r2 - p2 * r1
+        if abs(det) > 1e-6 * max(p1 * r2, 1.0):
+            a_ms = (t1 * r2 - t2 * r1) / det
+            b_ms = (p1 * t2 - p2 * t1) / det
+            touched = {"windows_steps_from": [advance + args.warmup, int(round(d2.t / sim.dt))],
+                       "paired": [p1, p2], "released": [r1, r2], "push_ms": [t1, t2],
+                       "ns_per_paired_electron": a_ms * 1e6, "ns_per_released_electron": b_ms * 1e6,
+                       "released_electron_steps_per_s": 1e3 / b_ms if b_ms > 0 else None,
+                       "note": "push time per launch = a * paired electrons + b * released electrons (each with "
+                               "its released-ion record), solved from two windows of the stage"}
     sim.close()
     del sim
     torch.cuda.empty_cache()
@@ -362,6 +400,7 @@ def run_ours(args, rank, world, local):
                          "units_per_launch": {"electrons": n_e, "ion_records": n_ir},
                          "ms_per_launch": push_ms},
             "phase_share": share,
+            "field_touched_electron_cost": touched,
             "e2e": e2e,
             "gpu_launches": int(kernels),
             "clocks": clock_info,
@@ -436,8 +475,12 @@ def run_c4(P, torch, nruns, warmup, steps, graph_steps=20):
     for s in sims:
         s.close()
     torch.cuda.empty_cache()
-    return {"runs": nruns, "steps": steps, "electrons": n0, "value": n0 * steps / t_batch,
-            "ms_per_step": 1e3 * t_batch / steps, "graph_steps": graph_steps, "fused_chains": info["chains"],
+    forms = {"streams": t_streams, "per_context_graph": t_ctx, f"fused_graph_{best}_chains": t_batch}
+    fastest = min(forms, key=forms.get)
+    return {"runs": nruns, "steps": steps, "electrons": n0, "value": n0 * steps / forms[fastest],
+            "ms_per_step": 1e3 * forms[fastest] / steps, "form": fastest,
+            "fused_value": n0 * steps / t_batch, "fused_ms_per_step": 1e3 * t_batch / steps,
+            "graph_steps": graph_steps, "fused_chains": info["chains"],
             "fused_ms_per_step_by_chains": {c: round(1e3 * timings[c][0] / steps, 4) for c in timings if c > 0},
             "launches_per_step": info["launches_per_replay"] / graph_steps,
             "first_call_ms": 1e3 * t_capture,
@@ -445,24 +488,25 @@ def run_c4(P, torch, nruns, warmup, steps, graph_steps=20):
             "per_context_launches_per_step": info_ctx["launches_per_replay"] / graph_steps,
             "per_context_first_call_ms": 1e3 * t_capture_ctx,
             "streams_value": n0 * steps / t_streams, "streams_ms_per_step": 1e3 * t_streams / steps,
-            "sequential_value": n0 * steps / t_seq, "speedup_vs_sequential": t_seq / t_batch,
+            "sequential_value": n0 * steps / t_seq, "speedup_vs_sequential": t_seq / forms[fastest],
             "note": "2D3V boosted runs, gamma in {5, 13, 30}, nz in [1024, 4096], nx = 128, 2x2 per cell, "
                     "8-coefficient profile, a0 in [0.5, 2]; host wall clock around pic_batch_step (graph: "
                     "graph_steps steps of all runs captured once as one CUDA graph by a first call, timed as "
-                    "first_call_ms, and kept by the batch; the timed call replays it).  value: the fused "
-                    "graph with the fastest of 1, 2, 4, 8 launch chains (each chain one launch per phase over "
-                    "its runs, the push a persistent grid over (run, tile) items); per_context_graph: every "
-                    "run's launches on its own stream inside the graph; streams: launch by launch on the runs' "
-                    "streams"}
+                    "first_call_ms, and kept by the batch; the timed call replays it).  value: the fastest form "
+                    "(form): streams (launch by launch on the runs' streams), per_context_graph (every run's "
+                    "launches on its own stream inside the graph) or the fused graph with the fastest of 1, 2, "
+                    "4, 8 launch chains (each chain one launch per phase over its runs, the push a persistent "
+                    "grid over (run, tile) items; fused_value)"}
 
 
 def run_adjoint(P, torch, steps, K, r=0):
     """Adjoint/forward time on run r of the c4 scan: the gradient of the
     on-axis Ez over planes 16..127 after `steps` steps with respect to the
-    8 profile coefficients, a0 and the waist (forward with a checkpoint every K
-    steps, then the reverse sweep recomputing each segment), against the
-    library's forward step over the same steps.  CUDA events on the run's
-    stream."""
+    8 profile coefficients, a0 and the waist (forward with a checkpoint every
+    K steps, then the reverse sweep recomputing each segment), against the
+    library's forward step over the same steps; with the checkpoint interval
+    fitted to the device's memory and with the fixed interval K.  CUDA events
+    on the run's stream."""
     from paper_1011_0917_gb300 import workloads as W
     st = W.c4_run(r)
     g = st.grid
@@ -486,28 +530,55 @@ def run_adjoint(P, torch, steps, K, r=0):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1), out
 
+    # untimed warm-up of both paths (the first launch of each kernel in a
+    # process loads its module)
+    w = make()
+    with torch.cuda.stream(w.stream):
+        f = w.adjoint_forward(4, 2)
+        w.adjoint_backward(torch.zeros_like(f))
+    w.close()
+    w = make()
+    P.pic_step(w.ctx, 4)
+    w.close()
+    del f
     sim = make()
     n_e = sim.diagnostics().n_particles[0]
     fwd_ms, _ = timed(sim, lambda: P.pic_step_async(sim.ctx, steps))
     sim.close()
-    sim = make()
-    with torch.cuda.stream(sim.stream):
-        a_fwd_ms, fields = timed(sim, lambda: sim.adjoint_forward(steps, K))
-        cot = torch.zeros_like(fields)
-        cot[2, 16:128, g["nx"] // 2] = 1.0
-        a_bwd_ms, grad = timed(sim, lambda: sim.adjoint_backward(cot))
-    nbytes = sim._adj.numel()
-    sim.close()
-    del fields, cot
-    torch.cuda.empty_cache()
-    total = a_fwd_ms + a_bwd_ms
-    return {"run": f"c4[{r}]: gamma={g['gamma_boost']:g}, {g['nx']}x{g['nz']} cells, {n_e} electrons, {steps} steps, "
-                   f"checkpoint every {K}",
-            "forward_ms": fwd_ms, "adjoint_forward_ms": a_fwd_ms, "adjoint_reverse_ms": a_bwd_ms,
-            "ratio": total / fwd_ms, "buffer_bytes": int(nbytes),
-            "gradient": {"profile": grad[:-2], "a0": grad[-2], "w0": grad[-1]},
+
+    def adjoint(k):
+        sim = make()
+        if k is None:  # fitted to the device's memory
+            k = sim.adjoint_checkpoint_interval(steps)
+        with torch.cuda.stream(sim.stream):
+            # the adjoint's buffer allocated before the timing, as the forward's are
+            bufs = sim.adjoint_buffers(steps, k)
+            a_fwd_ms, fields = timed(sim, lambda: sim.adjoint_forward(steps, k, buffers=bufs))
+            cot = torch.zeros_like(fields)
+            cot[2, 16:128, g["nx"] // 2] = 1.0
+            a_bwd_ms, grad = timed(sim, lambda: sim.adjoint_backward(cot))
+        nbytes = sim._adj.numel()
+        sim.close()
+        del fields, cot, bufs
+        torch.cuda.empty_cache()
+        return {"checkpoint_every": k, "adjoint_forward_ms": a_fwd_ms, "adjoint_reverse_ms": a_bwd_ms,
+                "ratio": (a_fwd_ms + a_bwd_ms) / fwd_ms, "buffer_bytes": int(nbytes),
+                "gradient": {"profile": grad[:-2], "a0": grad[-2], "w0": grad[-1]}}
+
+    fixed = adjoint(K)
+    fitted = adjoint(None)
+    return {"run": f"c4[{r}]: gamma={g['gamma_boost']:g}, {g['nx']}x{g['nz']} cells, {n_e} electrons, {steps} steps",
+            "forward_ms": fwd_ms, "ratio": fixed["ratio"], "checkpoint_every": K,
+            "adjoint_forward_ms": fixed["adjoint_forward_ms"], "adjoint_reverse_ms": fixed["adjoint_reverse_ms"],
+            "buffer_bytes": fixed["buffer_bytes"], "gradient": fixed["gradient"],
+            "memory_fitted_interval": {k: v for k, v in fitted.items() if k != "gradient"},
             "objective": "sum of on-axis Ez over planes 16..127 (behind the antenna, inside the plasma) at the "
-                         "last step"}
+                         "last step",
+            "note": "CUDA events on the run's stream around the library's forward steps and around the adjoint "
+                    "forward and reverse calls; the adjoint's device buffer is allocated before its timing, as "
+                    "the forward's buffers are at binding; both paths warmed up (module loading) before.  ratio: "
+                    "with a checkpoint every --checkpoint-every steps; memory_fitted_interval: with the largest "
+                    "interval whose buffer fits half of the free HBM (Simulation.adjoint_checkpoint_interval)"}
 
 
 def run_adjoint_3d(P, torch, steps, K=25, K2=5):
@@ -540,6 +611,16 @@ def run_adjoint_3d(P, torch, steps, K=25, K2=5):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1), out
 
+    # untimed warm-up of both paths (module loading)
+    w = make()
+    with torch.cuda.stream(w.stream):
+        f = w.adjoint_forward(4, 2)
+        w.adjoint_backward(torch.zeros_like(f))
+    w.close()
+    w = make()
+    P.pic_step(w.ctx, 4)
+    w.close()
+    del f
     sim = make()
     n_e = sim.diagnostics().n_particles[0]
     fwd_ms, _ = timed(sim, lambda: P.pic_step_async(sim.ctx, steps))
@@ -549,7 +630,8 @@ def run_adjoint_3d(P, torch, steps, K=25, K2=5):
     for name, k2 in (("one_level", 0), ("two_level", K2)):
         sim = make()
         with torch.cuda.stream(sim.stream):
-            a_fwd_ms, fields = timed(sim, lambda: sim.adjoint_forward(steps, K, k2))
+            bufs = sim.adjoint_buffers(steps, K, k2)
+            a_fwd_ms, fields = timed(sim, lambda: sim.adjoint_forward(steps, K, k2, buffers=bufs))
             cot = torch.zeros_like(fields)
             cot[2, 8:120, g["ny"] // 2, g["nx"] // 2] = 1.0
             a_bwd_ms, grad = timed(sim, lambda: sim.adjoint_backward(cot))
@@ -557,7 +639,7 @@ def run_adjoint_3d(P, torch, steps, K=25, K2=5):
                      "adjoint_reverse_ms": a_bwd_ms, "ratio": (a_fwd_ms + a_bwd_ms) / fwd_ms,
                      "buffer_bytes": int(sim._adj.numel()), "gradient": {"a0": grad[-2], "w0": grad[-1]}}
         sim.close()
-        del fields, cot
+        del fields, cot, bufs
         torch.cuda.empty_cache()
     return out
 
@@ -727,6 +809,13 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         out = run_reference(args, rank, world)
+    elif args.c4_only:
+        out = None
+        if rank == 0:
+            import torch
+
+            import paper_1011_0917_gb300 as P
+            out = run_c4(P, torch, args.c4, args.warmup, 200)
     elif args.adjoint_only:
         out = None
         if rank == 0:

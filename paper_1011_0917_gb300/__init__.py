@@ -551,17 +551,37 @@ class Simulation:
         return {c: vals[q] for q, c in enumerate(names)}, filled
 
 
-    def adjoint_forward(self, nsteps, checkpoint_every=50, sub_checkpoint_every=0):
+    def adjoint_checkpoint_interval(self, nsteps, budget_bytes=None):
+        """The largest checkpoint interval K (nsteps, then halved) whose one-level
+        adjoint buffer fits budget_bytes (default: half of the device memory
+        free now): recomputation is traded for HBM only as far as needed."""
+        if budget_bytes is None:
+            free, _ = self.torch.cuda.mem_get_info(self.device)
+            budget_bytes = free // 2
+        k = int(nsteps)
+        while k > 1 and pic_adjoint_bytes(self.ctx, AdjointParams(int(nsteps), k, 0)) > budget_bytes:
+            k = (k + 1) // 2
+        return k
+
+    def adjoint_buffers(self, nsteps, checkpoint_every=50, sub_checkpoint_every=0):
+        """The device buffers of an adjoint run (checkpoints and states; E^N,
+        B^N), to be passed to adjoint_forward (allocated by it otherwise)."""
+        p = AdjointParams(int(nsteps), int(checkpoint_every), int(sub_checkpoint_every))
+        buf = self.torch.empty(pic_adjoint_bytes(self.ctx, p), dtype=self.torch.uint8, device=self.device)
+        shape = (6,) + (self.shape3 if self.params.dim == 3 else (self.shape3[0], self.shape3[2]))
+        return buf, self.torch.empty(shape, dtype=self.dtype, device=self.device)
+
+    def adjoint_forward(self, nsteps, checkpoint_every=50, sub_checkpoint_every=0, buffers=None):
         """Forward run of the adjoint (from right after load_plasma and
         launch_laser): returns E^N, B^N as a (6, nz+1, nx) device tensor in 2D,
-        (6, nz+1, ny, nx) in 3D, and keeps the checkpoints for adjoint_backward."""
+        (6, nz+1, ny, nx) in 3D, and keeps the checkpoints for adjoint_backward.
+        buffers: those of adjoint_buffers (same arguments), else allocated here."""
         p = AdjointParams(int(nsteps), int(checkpoint_every), int(sub_checkpoint_every))
-        nbytes = pic_adjoint_bytes(self.ctx, p)
-        self._adj = self.torch.empty(nbytes, dtype=self.torch.uint8, device=self.device)
+        if buffers is None:
+            buffers = self.adjoint_buffers(nsteps, checkpoint_every, sub_checkpoint_every)
+        self._adj, out = buffers
         self._adj_n = self._prof_n
-        shape = (6,) + (self.shape3 if self.params.dim == 3 else (self.shape3[0], self.shape3[2]))
-        out = self.torch.empty(shape, dtype=self.dtype, device=self.device)
-        pic_adjoint_forward(self.ctx, p, self._adj.data_ptr(), nbytes, out.data_ptr())
+        pic_adjoint_forward(self.ctx, p, self._adj.data_ptr(), self._adj.numel(), out.data_ptr())
         return out
 
     def adjoint_backward(self, cot):

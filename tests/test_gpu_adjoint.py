@@ -363,3 +363,20 @@ def test_batch_adjoint_matches_oracle_finite_differences(O, reference):
         assert g.shape == fd.shape == (len(r["coef"]) + 2,)
         rel = np.abs(g - fd) / np.abs(fd)
         assert np.all(rel < 1e-3), (i, g, fd, rel)
+
+
+def test_checkpoint_interval_fits_the_budget(O):
+    """The memory-fitted checkpoint interval: the whole run when it fits, and
+    otherwise the largest halving of it whose buffer fits the budget."""
+    import paper_1011_0917_gb300 as P
+    sim, _ = make_pair(O, G, FP64)
+    sim.load_plasma(PLASMA["ne"], PLASMA["z_start"], PLASMA["z_end"], PLASMA["ramp"], PLASMA["ppc"],
+                    PLASMA["jitter"], COEF, 1)
+    sim.launch_laser(LASER["a0"], LASER["waist"], LASER["fwhm"], 0.0, LASER["t_peak"], 1)
+    nbytes = lambda k: P.pic_adjoint_bytes(sim.ctx, P.AdjointParams(NSTEPS, k, 0))
+    assert sim.adjoint_checkpoint_interval(NSTEPS, budget_bytes=nbytes(NSTEPS)) == NSTEPS
+    k = sim.adjoint_checkpoint_interval(NSTEPS, budget_bytes=nbytes(NSTEPS) - 1)
+    assert k < NSTEPS and nbytes(k) <= nbytes(NSTEPS) - 1
+    _, g = gpu_run(O, FP64, K=k)
+    _, g1 = gpu_run(O, FP64, K=NSTEPS)
+    assert np.allclose(g, g1, rtol=1e-11, atol=0)
