@@ -315,214 +315,182 @@ __global__ void __launch_bounds__(256) yee_batch_kernel(const YeeArgs<real> *__r
     yee_body<real, DIM>(sa, (int)(b % ncol), (int)(b / ncol));
 }
 
-// ------------------------------------------------------- 2D tiled Yee
+// --------------------------------------------------- 2D Yee, column march
 
-// Shared rows of the 2D tile kernels: x from x0 - 4 to x0 + 67 of a tile
-// whose own columns are x0 .. x0 + 63 (x0 a multiple of 64), kRowPitch
-// elements per row, so that every 16-byte chunk of a row is a 16-byte chunk
-// of the grid row (where the grid width is a multiple of 16 bytes).
-constexpr int kRowX = 64, kRowPitch = 72, kRowOrigin = 4;
-
-// Copies rows zo .. zo + nrows - 1 of one component into dst[row][x - x0 + 4]
-// with cp.async: 16-byte copies for the chunks inside the grid, element
-// copies (x wrapped) for the chunks across its periodic x edge; a row the
-// component does not have (plane(k) < 0) is zero.
-template <typename real, typename PlaneFn>
-__device__ __forceinline__ void stage_rows(real *dst, const real *src, int nrows, int zo, int x0, const Geom &g,
-                                           PlaneFn plane)
-{
-    constexpr int V = 16 / (int)sizeof(real), NCH = kRowPitch / V;
-    const bool vec = g.nx % V == 0 && (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
-    for (int q = (int)threadIdx.x; q < nrows * NCH; q += (int)blockDim.x) {
-        const int row = q / NCH, ch = q - row * NCH;
-        const int kk = plane(zo + row);
-        real *d = dst + row * kRowPitch + ch * V;
-        const int xs = x0 - kRowOrigin + ch * V;
-        if (kk < 0) {
-#pragma unroll
-            for (int v = 0; v < V; ++v) d[v] = real(0);
-            continue;
-        }
-        const real *srow = src + (int64_t)kk * g.plane;
-        if (vec && xs >= 0 && xs + V <= g.nx) {
-            __pipeline_memcpy_async(d, srow + xs, 16);
-        } else {
-#pragma unroll
-            for (int v = 0; v < V; ++v) __pipeline_memcpy_async(d + v, srow + wrapi(xs + v, g.nx), sizeof(real));
-        }
-    }
-}
-
-// The same Yee step on 2D grids, without the march: a CTA owns a tile of
-// 64 x kY2Z (x, z) nodes and copies, all at once with cp.async (above),
-// x0 - 4 .. x0 + 67 of E^n on planes z0 - 2 .. z0 + kY2Z + 1, of B^n on
-// z0 - 2 .. z0 + kY2Z and of J on z0 - 1 .. z0 + kY2Z into shared memory
-// (planes a component does not have are zero), so that a tile costs one load
-// latency however narrow the grid is (the march pays one per plane, which
-// dominates on grids a few hundred nodes wide).  Then, in shared memory and
-// node by node with the march's arithmetic: Bh in place of B^n on
-// x0 - 1 .. x0 + 64, E' in place of E^n on x0 .. x0 + 64, z0 - 1 .. z0 + kY2Z,
-// Mur's condition for the end planes (from the saved E^n of their inner
-// neighbours), and E', B' of the own nodes to the other buffer.  (d/dy = 0:
-// the y derivatives of the 3D formulas are zero terms.)
-constexpr int kY2Z = 16;
-constexpr int kY2EZ = kY2Z + 4, kY2BZ = kY2Z + 3, kY2JZ = kY2Z + 2;  // rows of E^n, B^n, J
+// The Yee step on 2D grids with the planes in registers: a warp owns a strip
+// of kColOwn x columns and a chunk of z planes and marches up the chunk like
+// yee_kernel, one plane per iteration, each lane holding one column (lane l:
+// x = strip * kColOwn + l - 1, wrapped), so that every z neighbour is a
+// register of the previous iteration and every x neighbour a shuffle.  The
+// curls reach one column to each side: Bh is exact on lanes 0-30, E' on
+// lanes 1-30 and B' on lanes 1-29, the strip's own columns.  No shared
+// memory and no barrier: the warps of a CTA are independent, and the loads
+// of a plane are issued a plane ahead of their use.  At plane k of the march
+// (the arithmetic of yee_kernel node by node, d/dy = 0):
+//   Bh(k)   from B^n(k), E^n(k), E^n(k+1)
+//   E'(k)   from E^n(k), Bh(k), Bh(k-1), J(k); Mur's planes from E'(1),
+//           E'(nz-1) and the E^n around them
+//   B'(k-1) from Bh(k-1), E'(k-1), E'(k), written with E'(k-1)
+// The chunk [z0, z1) starts two planes early (E' of plane z0 - 1 for Mur's
+// upper plane when nz - 1 is the plane before the chunk) and ends one late.
+constexpr int kColOwn = 29;
 
 template <typename real>
-__device__ __forceinline__ void yee2d_body(const YeeArgs<real> &a, const int bx_, const int bz_)
+__device__ __forceinline__ void yee2d_body(const YeeArgs<real> &a, const int strip, const int chunk)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int W = kRowPitch;
-    constexpr int PE = kY2EZ * W, PB = kY2BZ * W, PJ = kY2JZ * W;
-    real *sE = reinterpret_cast<real *>(smem_raw);  // [3][kY2EZ][W], E^n then E'
-    real *sB = sE + 3 * PE;                          // [3][kY2BZ][W], B^n then Bh
-    real *sJ = sB + 3 * PB;                          // [3][kY2JZ][W]
-    real *sM = sJ + 3 * PJ;                          // [2 ends][2 comps][W]: E^n x, y of planes 1, nz-1
     const Geom &g = a.g;
     const bool per = g.bc_z == 0;
     const int nzo = per ? g.nz : g.nz + 1;
-    const int x0 = bx_ * kRowX, z0 = bz_ * kY2Z;
-    const int z1 = z0 + kY2Z < nzo ? z0 + kY2Z : nzo;
-    const int tid = (int)threadIdx.x, nt = (int)blockDim.x;
-    auto plane_of = [&](bool half) {
-        return [&g, per, half](int k) { return per ? wrapi(k, g.nz) : (k >= 0 && k <= zmax_of(g, half) ? k : -1); };
+    const unsigned lane = threadIdx.x & 31u;
+    const int x = strip * kColOwn + (int)lane - 1;
+    const int gx = x >= 0 && x < g.nx ? x : wrapi(x, g.nx);
+    const bool own = lane >= 1u && lane <= (unsigned)kColOwn && x < g.nx;
+    const int z0 = chunk * a.cz;
+    const int z1 = chunk == a.nchunks - 1 ? nzo : z0 + a.cz;
+    auto plane = [&](int k, bool half) {
+        return per ? wrapi(k, g.nz) : (k >= 0 && k <= zmax_of(g, half) ? k : -1);
     };
-    const auto pint = plane_of(false), phalf = plane_of(true);
-    // ---- copy E^n (Ez half-z), B^n (Bx, By half-z), J (Jz half-z)
-    stage_rows(sE, a.E[0], kY2EZ, z0 - 2, x0, g, pint);
-    stage_rows(sE + PE, a.E[1], kY2EZ, z0 - 2, x0, g, pint);
-    stage_rows(sE + 2 * PE, a.E[2], kY2EZ, z0 - 2, x0, g, phalf);
-    stage_rows(sB, a.B[0], kY2BZ, z0 - 2, x0, g, phalf);
-    stage_rows(sB + PB, a.B[1], kY2BZ, z0 - 2, x0, g, phalf);
-    stage_rows(sB + 2 * PB, a.B[2], kY2BZ, z0 - 2, x0, g, pint);
-    stage_rows(sJ, a.J[0], kY2JZ, z0 - 1, x0, g, pint);
-    stage_rows(sJ + PJ, a.J[1], kY2JZ, z0 - 1, x0, g, pint);
-    stage_rows(sJ + 2 * PJ, a.J[2], kY2JZ, z0 - 1, x0, g, phalf);
-    __pipeline_commit();
-    __pipeline_wait_prior(0);
-    __syncthreads();
-    // the E^n of the planes Mur's condition reads after E' has replaced them
-    const bool mur_lo = !per && z0 - 1 <= 0 && 0 <= z0 + kY2Z - 1;        // plane 0 is computed here
-    const bool mur_hi = !per && z0 - 1 <= g.nz - 1 && g.nz <= z0 + kY2Z;  // plane nz too
-    if (mur_lo || mur_hi) {
-        for (int r = tid; r < 2 * 2 * W; r += nt) {
-            const int end = r / (2 * W), c = (r / W) & 1, j = r % W;
-            const int pz = (end == 0 ? 1 : g.nz - 1) - (z0 - 2);
-            sM[r] = (pz >= 0 && pz < kY2EZ) ? sE[c * PE + pz * W + j] : real(0);
-        }
-    }
-    // ---- Bh(k) = B^n(k) - (dt/2) curl E^n on every B row, x0 - 1 .. x0 + 64
+    auto ld = [&](const real *p, int kk) { return kk >= 0 ? p[(int64_t)kk * g.plane + gx] : real(0); };
+    auto dn = [&](real v) { return __shfl_down_sync(0xffffffffu, v, 1); };  // the value at x + 1
+    auto up = [&](real v) { return __shfl_up_sync(0xffffffffu, v, 1); };    // the value at x - 1
     const real zero = real(0);
-    {
-        constexpr int NX = kRowX + 2;
-        for (int r = tid; r < kY2BZ * NX; r += nt) {
-            const int pb = r / NX, j = r - pb * NX + kRowOrigin - 1;
-            const int k = z0 - 2 + pb;
-            const int o = pb * W + j;  // the same index in the E and B rows
-            const bool vxy = phalf(k) >= 0, vz = pint(k) >= 0;
-            const real dEy_dz = (sE[PE + o + W] - sE[PE + o]) * a.ihz;
-            const real dEx_dz = (sE[o + W] - sE[o]) * a.ihz;
-            const real dEz_dx = (sE[2 * PE + o + 1] - sE[2 * PE + o]) * a.ihx;
-            const real dEy_dx = (sE[PE + o + 1] - sE[PE + o]) * a.ihx;
-            sB[o] = vxy ? sB[o] - a.hb * (zero - dEy_dz) : real(0);
-            sB[PB + o] = vxy ? sB[PB + o] - a.hb * (dEx_dz - dEz_dx) : real(0);
-            sB[2 * PB + o] = vz ? sB[2 * PB + o] - a.hb * (dEy_dx - zero) : real(0);
-        }
-    }
-    __syncthreads();
-    // ---- E'(k) = E^n(k) + dt (curl Bh - 2 pi J) on x0 .. x0 + 64, z0 - 1 .. z0 + kY2Z
-    {
-        constexpr int NX = kRowX + 1;
-        for (int r = tid; r < kY2JZ * NX; r += nt) {
-            const int lz = r / NX, j = r - lz * NX + kRowOrigin;
-            const int k = z0 - 1 + lz;
-            const int o = (lz + 1) * W + j;  // in the E and B rows
-            const int oj = lz * W + j;
-            const bool vz = phalf(k) >= 0;
-            const bool vxy = per || (k >= 1 && k <= g.nz - 1);
-            if (vxy) {
-                const real dBy_dz = (sB[PB + o] - sB[PB + o - W]) * a.ihz;
-                sE[o] = sE[o] + a.he * ((zero - dBy_dz) - a.twopi * sJ[oj]);
-                const real dBx_dz = (sB[o] - sB[o - W]) * a.ihz;
-                const real dBz_dx = (sB[2 * PB + o] - sB[2 * PB + o - 1]) * a.ihx;
-                sE[PE + o] = sE[PE + o] + a.he * ((dBx_dz - dBz_dx) - a.twopi * sJ[PJ + oj]);
+    const int kb = z0 - 2;
+    // E^n of planes k - 1 (for Mur), k and k + 1; B^n and J of plane k;
+    // Bh and E' of plane k - 1
+    real emx = 0, emy = 0;
+    real ex0 = ld(a.E[0], plane(kb, false)), ey0 = ld(a.E[1], plane(kb, false)), ez0 = ld(a.E[2], plane(kb, true));
+    real ex1 = ld(a.E[0], plane(kb + 1, false)), ey1 = ld(a.E[1], plane(kb + 1, false));
+    real ez1 = ld(a.E[2], plane(kb + 1, true));
+    real bx = ld(a.B[0], plane(kb, true)), by = ld(a.B[1], plane(kb, true)), bz = ld(a.B[2], plane(kb, false));
+    real jx = ld(a.J[0], plane(kb, false)), jy = ld(a.J[1], plane(kb, false)), jz = ld(a.J[2], plane(kb, true));
+    real bmx = 0, bmy = 0, bmz = 0, fpx = 0, fpy = 0, fpz = 0;
+    real murx = 0, mury = 0;  // E'(nz) x, y by Mur's condition (from plane nz - 1)
+    for (int k = kb; k <= z1; ++k) {
+        // the next plane's loads, used one iteration later
+        const int ke = plane(k + 2, false), keh = plane(k + 2, true);
+        const int kn = plane(k + 1, false), knh = plane(k + 1, true);
+        const real nex = ld(a.E[0], ke), ney = ld(a.E[1], ke), nez = ld(a.E[2], keh);
+        const real nbx = ld(a.B[0], knh), nby = ld(a.B[1], knh), nbz = ld(a.B[2], kn);
+        const real njx = ld(a.J[0], kn), njy = ld(a.J[1], kn), njz = ld(a.J[2], knh);
+        // ---- Bh(k)
+        const bool vxy = plane(k, true) >= 0, vz = plane(k, false) >= 0;
+        const real eyr = dn(ey0), ezr = dn(ez0);
+        const real dEy_dz = (ey1 - ey0) * a.ihz;
+        const real dEx_dz = (ex1 - ex0) * a.ihz;
+        const real dEz_dx = (ezr - ez0) * a.ihx;
+        const real dEy_dx = (eyr - ey0) * a.ihx;
+        const real hx = vxy ? bx - a.hb * (zero - dEy_dz) : real(0);
+        const real hy = vxy ? by - a.hb * (dEx_dz - dEz_dx) : real(0);
+        const real hz = vz ? bz - a.hb * (dEy_dx - zero) : real(0);
+        // ---- E'(k)
+        real fx = ex0, fy = ey0, fz = 0;
+        {
+            const real hyl = up(hy), hzl = up(hz);
+            const bool ve = per || (k >= 1 && k <= g.nz - 1), vze = plane(k, true) >= 0;
+            if (ve) {
+                const real dBy_dz = (hy - bmy) * a.ihz;
+                fx = ex0 + a.he * ((zero - dBy_dz) - a.twopi * jx);
+                const real dBx_dz = (hx - bmx) * a.ihz;
+                const real dBz_dx = (hz - hzl) * a.ihx;
+                fy = ey0 + a.he * ((dBx_dz - dBz_dx) - a.twopi * jy);
             }
-            const real dBy_dx = (sB[PB + o] - sB[PB + o - 1]) * a.ihx;
-            sE[2 * PE + o] = vz ? sE[2 * PE + o] + a.he * ((dBy_dx - zero) - a.twopi * sJ[2 * PJ + oj]) : real(0);
+            const real dBy_dx = (hy - hyl) * a.ihx;
+            fz = vze ? ez0 + a.he * ((dBy_dx - zero) - a.twopi * jz) : real(0);
+            if (!per) {
+                if (k == 1) {  // E'(0) x, y from plane 1
+                    fpx = ex0 + a.mur * (fx - emx);
+                    fpy = ey0 + a.mur * (fy - emy);
+                }
+                if (k == g.nz - 1) {  // E'(nz) x, y from plane nz - 1
+                    murx = ex0 + a.mur * (fx - ex1);
+                    mury = ey0 + a.mur * (fy - ey1);
+                }
+                if (k == g.nz) {
+                    fx = murx;
+                    fy = mury;
+                }
+            }
         }
+        // ---- E'(k - 1), B'(k - 1) of the own columns
+        {
+            const int kw = k - 1;
+            const real fpyr = dn(fpy), fpzr = dn(fpz);
+            if (kw >= z0 && kw < z1 && own) {
+                const int64_t o = (int64_t)kw * g.plane + x;
+                const bool wxy = kw <= zmax_of(g, false), wz = kw <= zmax_of(g, true);
+                if (wxy) {
+                    a.E1[0][o] = fpx;
+                    a.E1[1][o] = fpy;
+                }
+                if (wz) {
+                    a.E1[2][o] = fpz;
+                    const real dEy_dz1 = (fy - fpy) * a.ihz;
+                    a.B1[0][o] = bmx - a.hb * (zero - dEy_dz1);
+                    const real dEx_dz1 = (fx - fpx) * a.ihz;
+                    const real dEz_dx1 = (fpzr - fpz) * a.ihx;
+                    a.B1[1][o] = bmy - a.hb * (dEx_dz1 - dEz_dx1);
+                }
+                if (wxy) {
+                    const real dEy_dx1 = (fpyr - fpy) * a.ihx;
+                    a.B1[2][o] = bmz - a.hb * (dEy_dx1 - zero);
+                }
+            }
+        }
+        // ---- shift the march by one plane
+        emx = ex0;
+        emy = ey0;
+        ex0 = ex1;
+        ey0 = ey1;
+        ez0 = ez1;
+        ex1 = nex;
+        ey1 = ney;
+        ez1 = nez;
+        bx = nbx;
+        by = nby;
+        bz = nbz;
+        jx = njx;
+        jy = njy;
+        jz = njz;
+        bmx = hx;
+        bmy = hy;
+        bmz = hz;
+        fpx = fx;
+        fpy = fy;
+        fpz = fz;
     }
-    __syncthreads();
-    // ---- Mur: Ex, Ey of plane kt from plane kn, its neighbour inside the box
-    if (mur_lo || mur_hi) {
-        for (int r = tid; r < 2 * (kRowX + 1); r += nt) {
-            const int end = r / (kRowX + 1), j = r % (kRowX + 1) + kRowOrigin;
-            if (end == 0 ? !mur_lo : !mur_hi) continue;
-            const int kt = end == 0 ? 0 : g.nz, kn = end == 0 ? 1 : g.nz - 1;
-            const int ot = (kt - (z0 - 2)) * W + j, on = (kn - (z0 - 2)) * W + j;
-            const real *old = sM + end * 2 * W;  // E^n of plane kn
-#pragma unroll
-            for (int c = 0; c < 2; ++c)
-                sE[c * PE + ot] = old[c * W + j] + a.mur * (sE[c * PE + on] - sE[c * PE + ot]);
-        }
-        __syncthreads();
-    }
-    // ---- E', B' of the own nodes
-    for (int r = tid; r < kRowX * kY2Z; r += nt) {
-        const int lz = r / kRowX, lx = r - lz * kRowX;
-        const int k = z0 + lz, x = x0 + lx;
-        if (k >= z1 || x >= g.nx) continue;
-        const int of = (lz + 2) * W + lx + kRowOrigin;  // in the E and B rows
-        const int64_t o = (int64_t)k * g.plane + x;
-        const bool vxy = k <= zmax_of(g, false), vz = k <= zmax_of(g, true);
-        if (vxy) {
-            a.E1[0][o] = sE[of];
-            a.E1[1][o] = sE[PE + of];
-        }
-        if (vz) {
-            a.E1[2][o] = sE[2 * PE + of];
-            const real dEy_dz = (sE[PE + of + W] - sE[PE + of]) * a.ihz;
-            a.B1[0][o] = sB[of] - a.hb * (zero - dEy_dz);
-            const real dEx_dz = (sE[of + W] - sE[of]) * a.ihz;
-            const real dEz_dx = (sE[2 * PE + of + 1] - sE[2 * PE + of]) * a.ihx;
-            a.B1[1][o] = sB[PB + of] - a.hb * (dEx_dz - dEz_dx);
-        }
-        if (vxy) {
-            const real dEy_dx = (sE[PE + of + 1] - sE[PE + of]) * a.ihx;
-            a.B1[2][o] = sB[2 * PB + of] - a.hb * (dEy_dx - zero);
-        }
-    }
+}
+
+// one warp per (strip, chunk) item; YeeArgs::cz holds the planes per chunk,
+// nchunks the chunks (the strips follow from the grid)
+template <typename real>
+__device__ __forceinline__ void yee2d_items(const YeeArgs<real> &a, int64_t item, int64_t nitems)
+{
+    if (item >= nitems) return;
+    const int nstrip = (a.g.nx + kColOwn - 1) / kColOwn;
+    yee2d_body(a, (int)(item % nstrip), (int)(item / nstrip));
 }
 
 template <typename real>
-__global__ void __launch_bounds__(256) yee2d_kernel(YeeArgs<real> a)
+__global__ void __launch_bounds__(256) yee2d_kernel(YeeArgs<real> a, int64_t nitems)
 {
-    yee2d_body(a, (int)blockIdx.x, (int)blockIdx.y);
+    yee2d_items(a, (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5), nitems);
 }
 
-// (YeeArgs::nchunks holds the tiles along x here)
 template <typename real>
 __global__ void __launch_bounds__(256) yee2d_batch_kernel(const YeeArgs<real> *__restrict__ runs,
                                                           const int64_t *__restrict__ start, int n)
 {
     __shared__ __align__(16) YeeArgs<real> sa;
     const int64_t b = batch_block(runs, start, n, &sa);
-    yee2d_body(sa, (int)(b % sa.nchunks), (int)(b / sa.nchunks));
-}
-
-template <typename real>
-static size_t yee2d_smem()
-{
-    return sizeof(real) * (size_t)kRowPitch * (3 * (kY2EZ + kY2BZ + kY2JZ) + 4);
+    const int nstrip = (sa.g.nx + kColOwn - 1) / kColOwn;
+    yee2d_items(sa, b * 8 + (threadIdx.x >> 5), (int64_t)nstrip * sa.nchunks);
 }
 
 template <typename real>
 static void launch_yee2d_batch(const void *args, const int64_t *start, int n, int64_t total, unsigned *,
                                cudaStream_t s)
 {
-    const size_t smem = yee2d_smem<real>();
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(yee2d_batch_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    yee2d_batch_kernel<real><<<(unsigned)total, 256, smem, s>>>(static_cast<const YeeArgs<real> *>(args), start, n);
+    yee2d_batch_kernel<real><<<(unsigned)total, 256, 0, s>>>(static_cast<const YeeArgs<real> *>(args), start, n);
 }
 
 template <typename real, int DIM>
@@ -574,14 +542,15 @@ void launch_yee(const Geom &g, real *const F[9], real *const F1[6], double dt, d
     const int nzo = g.bc_z == 0 ? g.nz : g.nz + 1;
     const bool is3 = g.dim == 3;
     if (!is3) {
-        const int ntx = (g.nx + kRowX - 1) / kRowX, ntz = (nzo + kY2Z - 1) / kY2Z;
-        a.cz = kY2Z;
-        a.nchunks = ntx;
-        if (record_launch(kBPYee, launch_yee2d_batch<real>, a, (int64_t)ntx * ntz)) return;
-        const size_t smem = yee2d_smem<real>();
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(yee2d_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        yee2d_kernel<real><<<dim3((unsigned)ntx, (unsigned)ntz), 256, smem, s>>>(a);
+        // chunks of 12..64 planes, as many as leave about 24 warps per SM
+        const int nstrip = (g.nx + kColOwn - 1) / kColOwn;
+        int64_t czl = (int64_t)nzo * nstrip * batch_runs() / ((int64_t)device_sms() * 24);
+        a.cz = (int)(czl < 12 ? 12 : (czl > 64 ? 64 : czl));
+        if (a.cz > nzo) a.cz = nzo;
+        a.nchunks = (nzo + a.cz - 1) / a.cz;
+        const int64_t nitems = (int64_t)nstrip * a.nchunks, nblocks = (nitems + 7) / 8;
+        if (record_launch(kBPYee, launch_yee2d_batch<real>, a, nblocks)) return;
+        yee2d_kernel<real><<<(unsigned)nblocks, 256, 0, s>>>(a, nitems);
         return;
     }
     constexpr int TX = YeeTile<3>::TX, TY = YeeTile<3>::TY;
@@ -996,25 +965,18 @@ static bool launch_filter_tma(const Geom &g, const real *in, real *out, unsigned
     return true;
 }
 
-// The same H passes on 2D grids, without the march: a CTA owns 64 x kF2Z
-// (x, z) nodes of the three components and copies, all at once with
-// cp.async (stage_rows), x0 - 4 .. x0 + 67 of their input on planes
-// z0 - H .. z0 + kF2Z + H - 1 (zero or wrapped beyond the grid); per
-// component, the x passes are the binomial stencil of width 2H + 1
-// (filter_march_kernel's sum), and the z passes follow one level at a time in
-// shared memory, each narrower by a plane on both sides and zero outside the
-// component's z range, as in the march.
-constexpr int kF2Z = 32;
-
+// The same H passes on 2D grids with the planes in registers: a warp owns a
+// strip of 32 - 2H x columns and a chunk of z planes (lane l: x = strip
+// (32 - 2H) + l - H, wrapped; lanes H .. 31 - H own their column), marches
+// up the chunk like filter_march_kernel and takes the x passes (the binomial
+// stencil of width 2H + 1) over the lanes l - H .. l + H by shuffles; the z
+// passes are the march's register levels.  No shared memory, no barrier; a
+// plane's loads are issued an iteration ahead of their use.
 template <typename real, int H>
-__device__ __forceinline__ void filter2d_body(const Geom &g, const real *in, real *out, const int bx_, const int bz_)
+__device__ __forceinline__ void filter2d_body(const Geom &g, const real *in, real *out, const int strip,
+                                              const int chunk, const int cz, const int nchunks)
 {
-    static_assert(H <= kRowOrigin, "the halo fits the staged rows");
-    constexpr int W = kRowPitch, IZ = kF2Z + 2 * H, PI = IZ * W, PL = kRowX * IZ;
-    constexpr int NW = 2 * H + 1;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    real *sI = reinterpret_cast<real *>(smem_raw);  // [3][IZ][W] input
-    real *sL = sI + 3 * PI;                          // [2][IZ][64] levels (ping-pong)
+    constexpr int OWN = 32 - 2 * H, NW = 2 * H + 1;
     real wb[NW];
     {
         double c = 1.0;
@@ -1024,89 +986,91 @@ __device__ __forceinline__ void filter2d_body(const Geom &g, const real *in, rea
         }
     }
     const bool per = g.bc_z == 0;
-    const int x0 = bx_ * kRowX, z0 = bz_ * kF2Z;
-    const int tid = (int)threadIdx.x, nt = (int)blockDim.x;
+    const int lane = (int)(threadIdx.x & 31u);
+    const int x = strip * OWN + lane - H;
+    const int gx = x >= 0 && x < g.nx ? x : wrapi(x, g.nx);
+    const bool own = lane >= H && lane < 32 - H && x < g.nx;
+    const int z0 = chunk * cz;
+    const int z1 = chunk == nchunks - 1 ? g.nz + 1 : z0 + cz;
     const int zmax_xy = zmax_of(g, false), zmax_z = zmax_of(g, true);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
+    auto load = [&](int c, int k) {
         const int zmax = c == 2 ? zmax_z : zmax_xy;
-        stage_rows(sI + c * PI, in + (size_t)c * g.ncomp, IZ, z0 - H, x0, g,
-                   [&g, per, zmax](int k) { return per ? wrapi(k, g.nz) : (k >= 0 && k <= zmax ? k : -1); });
-    }
-    __pipeline_commit();
-    __pipeline_wait_prior(0);
-    __syncthreads();
-#pragma unroll 1
-    for (int c = 0; c < 3; ++c) {
-        const int zmax = c == 2 ? zmax_z : zmax_xy;
-        const real *I = sI + c * PI;
-        real *L0 = sL, *L1 = sL + PL;
-        // level 0: the x stencil on every staged plane
-        for (int r = tid; r < PL; r += nt) {
-            const int pz = r / kRowX, lx = r - pz * kRowX;
-            const int k = z0 - H + pz;
-            real v = 0;
+        const bool have = per || (k >= 0 && k <= zmax);
+        const int kk = per ? wrapi(k, g.nz) : k;
+        return have ? in[(size_t)c * g.ncomp + (int64_t)kk * g.plane + gx] : real(0);
+    };
+    real lev[3][H + 1][3];
 #pragma unroll
-            for (int i = 0; i < NW; ++i) v += wb[i] * I[pz * W + lx + kRowOrigin - H + i];
-            L0[r] = (per || (k >= 0 && k <= zmax)) ? v : real(0);
-        }
-        __syncthreads();
-        // level p on planes p .. IZ - 1 - p of the staged range
+    for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int p = 1; p <= H; ++p) {
-            for (int r = tid; r < PL; r += nt) {
-                const int pz = r / kRowX;
-                if (pz < p || pz >= IZ - p) continue;
-                const int k = z0 - H + pz;
-                const real nv = real(0.25) * L0[r - kRowX] + real(0.5) * L0[r] + real(0.25) * L0[r + kRowX];
-                L1[r] = (per || (k >= 0 && k <= zmax)) ? nv : real(0);
+        for (int p = 0; p <= H; ++p) lev[c][p][0] = lev[c][p][1] = lev[c][p][2] = real(0);
+    real cur[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) cur[c] = load(c, z0 - H);
+    for (int k = z0 - H; k <= z1 - 1 + H; ++k) {
+        real nxt[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) nxt[c] = k + 1 <= z1 - 1 + H ? load(c, k + 1) : real(0);
+        const int ko = k - H;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int zmax = c == 2 ? zmax_z : zmax_xy;
+            // x passes: the binomial stencil around this lane's column
+            real r = 0;
+#pragma unroll
+            for (int i = 0; i < NW; ++i) r += wb[i] * __shfl_sync(0xffffffffu, cur[c], lane - H + i);
+            const real v = real(0) + real(1) * r;
+            // z passes, one level per pass, each centred one plane lower
+#pragma unroll
+            for (int p = 0; p <= H; ++p) {
+                lev[c][p][0] = lev[c][p][1];
+                lev[c][p][1] = lev[c][p][2];
+                const int kc = k - p;
+                const bool in_range = per || (kc >= 0 && kc <= zmax);
+                const real nv = p == 0 ? v
+                                       : real(0.25) * lev[c][p - 1][0] + real(0.5) * lev[c][p - 1][1] +
+                                             real(0.25) * lev[c][p - 1][2];
+                lev[c][p][2] = in_range ? nv : real(0);
             }
-            __syncthreads();
-            real *t = L0;
-            L0 = L1;
-            L1 = t;
+            if (own && ko >= z0 && ko < z1)
+                out[(size_t)c * g.ncomp + (int64_t)ko * g.plane + x] = ko > zmax ? real(0) : lev[c][H][2];
         }
-        for (int r = tid; r < kRowX * kF2Z; r += nt) {
-            const int lz = r / kRowX, lx = r - lz * kRowX;
-            const int k = z0 + lz, x = x0 + lx;
-            if (k > g.nz || x >= g.nx) continue;
-            out[(size_t)c * g.ncomp + (int64_t)k * g.plane + x] = k > zmax ? real(0) : L0[(lz + H) * kRowX + lx];
-        }
-        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < 3; ++c) cur[c] = nxt[c];
     }
+}
+
+// one warp per (strip, chunk) item
+template <typename real, int H>
+__device__ __forceinline__ void filter2d_items(const Geom &g, const real *in, real *out, int cz, int nchunks,
+                                               int64_t item)
+{
+    const int nstrip = (g.nx + (32 - 2 * H) - 1) / (32 - 2 * H);
+    if (item >= (int64_t)nstrip * nchunks) return;
+    filter2d_body<real, H>(g, in, out, (int)(item % nstrip), (int)(item / nstrip), cz, nchunks);
 }
 
 template <typename real, int H>
-__global__ void __launch_bounds__(256) filter2d_kernel(Geom g, const real *in, real *out)
+__global__ void __launch_bounds__(256) filter2d_kernel(Geom g, const real *in, real *out, int cz, int nchunks)
 {
-    filter2d_body<real, H>(g, in, out, (int)blockIdx.x, (int)blockIdx.y);
+    filter2d_items<real, H>(g, in, out, cz, nchunks, (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5));
 }
 
-// (MarchArgs::cz holds the tiles along x here)
 template <typename real, int H>
 __global__ void __launch_bounds__(256) filter2d_batch_kernel(const MarchArgs<real> *__restrict__ runs,
                                                              const int64_t *__restrict__ start, int n)
 {
     __shared__ __align__(16) MarchArgs<real> sa;
     const int64_t b = batch_block(runs, start, n, &sa);
-    filter2d_body<real, H>(sa.g, sa.in, sa.out, (int)(b % sa.cz), (int)(b / sa.cz));
-}
-
-template <typename real, int H>
-static size_t filter2d_smem()
-{
-    return sizeof(real) * (3 * (size_t)kRowPitch * (kF2Z + 2 * H) + 2 * (size_t)kRowX * (kF2Z + 2 * H));
+    filter2d_items<real, H>(sa.g, sa.in, sa.out, sa.cz, sa.nchunks, b * 8 + (threadIdx.x >> 5));
 }
 
 template <typename real, int H>
 static void launch_filter2d_batch(const void *args, const int64_t *start, int n, int64_t total, unsigned *,
                                   cudaStream_t s)
 {
-    const size_t smem = filter2d_smem<real, H>();
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(filter2d_batch_kernel<real, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     filter2d_batch_kernel<real, H>
-        <<<(unsigned)total, 256, smem, s>>>(static_cast<const MarchArgs<real> *>(args), start, n);
+        <<<(unsigned)total, 256, 0, s>>>(static_cast<const MarchArgs<real> *>(args), start, n);
 }
 
 template <typename real, int DIM, int H>
@@ -1114,15 +1078,19 @@ static void launch_march(const Geom &g, const real *in, real *out, cudaStream_t 
 {
     const int nzo = g.nz + 1;
     if constexpr (DIM == 2) {
-        // the tiled kernel (2D grids)
-        const int ntx = (g.nx + kRowX - 1) / kRowX, ntz = (nzo + kF2Z - 1) / kF2Z;
-        if (record_launch(kBPFilter, launch_filter2d_batch<real, H>, MarchArgs<real>{g, in, out, ntx, ntz},
-                          (int64_t)ntx * ntz))
+        // the register march (2D grids): chunks of 12..64 planes, as many as
+        // leave about 24 warps per SM
+        constexpr int OWN = 32 - 2 * H;
+        const int nstrip = (g.nx + OWN - 1) / OWN;
+        int64_t czl = (int64_t)nzo * nstrip * batch_runs() / ((int64_t)device_sms() * 24);
+        int cz = (int)(czl < 12 ? 12 : (czl > 64 ? 64 : czl));
+        if (cz > nzo) cz = nzo;
+        const int nchunks = (nzo + cz - 1) / cz;
+        const int64_t nblocks = ((int64_t)nstrip * nchunks + 7) / 8;
+        if (record_launch(kBPFilter, launch_filter2d_batch<real, H>, MarchArgs<real>{g, in, out, cz, nchunks},
+                          nblocks))
             return;
-        const size_t smem = filter2d_smem<real, H>();
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(filter2d_kernel<real, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        filter2d_kernel<real, H><<<dim3((unsigned)ntx, (unsigned)ntz), 256, smem, s>>>(g, in, out);
+        filter2d_kernel<real, H><<<(unsigned)nblocks, 256, 0, s>>>(g, in, out, cz, nchunks);
     } else {
         constexpr int TX = 32, TY = 8;
         const unsigned nb = (unsigned)(((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY));
