@@ -14,8 +14,9 @@ the library offers at run time:
   over its runs, the particle push a persistent grid over (run, tile)
   items).
 
-Particles are sorted into their tiles at every step, inside the push, so
-there is no sort interval to choose; the CTA shape (256 threads) is compiled.
+Particles are sorted into their tiles at every step, inside the push; the
+order by cell inside a tile (pic_set_cell_sort) is a candidate too (its
+interval, 0 for never).  The CTA shape (256 threads) is compiled.
 A candidate whose buckets overflow during the trial is discarded.
 """
 from __future__ import annotations
@@ -40,11 +41,13 @@ def _build(P, settings: dict, tile, slots, stream):
     return sim
 
 
-def tune_run(settings: dict, steps: int = 8, warmup: int = 3, tiles=None, slots=SLOTS) -> dict:
-    """Time every (tile, slots_per_cell) candidate on `steps` steps of the run
-    described by settings = {"grid": Simulation kwargs, "plasma": ..., "laser":
-    ...} after `warmup` steps.  Returns {"tile", "slots_per_cell", "ms_per_step",
-    "trials": [...]} for the fastest candidate."""
+def tune_run(settings: dict, steps: int = 8, warmup: int = 3, tiles=None, slots=SLOTS, sort_every=(0,)) -> dict:
+    """Time every (tile, slots_per_cell, sort_every) candidate on `steps` steps
+    of the run described by settings = {"grid": Simulation kwargs, "plasma":
+    ..., "laser": ...} after `warmup` steps (sort_every: order the particle
+    store by cell before every n-th step, 0 never).  Returns {"tile",
+    "slots_per_cell", "sort_every", "ms_per_step", "trials": [...]} for the
+    fastest candidate."""
     import torch
 
     import paper_1011_0917_gb300 as P
@@ -52,12 +55,14 @@ def tune_run(settings: dict, steps: int = 8, warmup: int = 3, tiles=None, slots=
     if tiles is None:
         tiles = TILES_2D if g.get("dim", 2) == 2 and g.get("shape_order", 1) == 1 else ((0, 0, 0),)
     trials = []
-    for tile, sl in itertools.product(tiles, slots):
+    for tile, sl, srt in itertools.product(tiles, slots, sort_every):
         stream = torch.cuda.Stream()
         sim = None
+        cand = {"tile": tuple(tile), "slots_per_cell": sl, "sort_every": srt}
         try:
             sim = _build(P, settings, tile, sl, stream)
             P.pic_step(sim.ctx, warmup)
+            P.pic_set_cell_sort(sim.ctx, srt)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record(stream)
@@ -65,9 +70,9 @@ def tune_run(settings: dict, steps: int = 8, warmup: int = 3, tiles=None, slots=
             e1.record(stream)
             torch.cuda.synchronize()
             P.pic_step(sim.ctx, 0)  # the device error word of the timed steps
-            trials.append({"tile": tuple(tile), "slots_per_cell": sl, "ms_per_step": e0.elapsed_time(e1) / steps})
+            trials.append(dict(cand, ms_per_step=e0.elapsed_time(e1) / steps))
         except P.PicError as e:
-            trials.append({"tile": tuple(tile), "slots_per_cell": sl, "error": str(e)})
+            trials.append(dict(cand, error=str(e)))
         finally:
             if sim is not None:
                 sim.close()

@@ -48,6 +48,9 @@ def _compare(sim, o, prec, n_charge_scale):
     fe = abs(d.field_energy - ref["field_energy"]) / ref["field_energy"]
     ke = abs(d.kinetic_energy - ref["kinetic_energy"]) / ref["kinetic_energy"]
     q = abs(d.charge - ref["charge"]) / n_charge_scale
+    # (the measured errors, for the record: pytest -s shows them)
+    print(f"diagnostics vs oracle ({'FP64' if prec == FP64 else 'FP32'}): field energy {fe:.2e}, "
+          f"kinetic energy {ke:.2e}, charge {q:.2e}")
     assert fe < TOL_FE[prec] and ke < TOL_KQ[prec] and q < TOL_KQ[prec], (fe, ke, q, d.field_energy, ref)
     return fe, ke, q
 

@@ -70,3 +70,11 @@ def test_autotune_batch_tries_every_launch_form():
     forms = {(t["graph_steps"], t["chains"]) for t in best["trials"]}
     assert forms == {(0, 0), (10, 0), (10, 1), (10, 2)}, best["trials"]
     assert best["ms_per_step"] == min(t["ms_per_step"] for t in best["trials"])
+
+
+def test_autotune_tries_the_cell_sort_interval():
+    from paper_1011_0917_gb300 import autotune
+    settings = {"grid": dict(G, precision=FP32), "plasma": PLASMA, "laser": dict(LASER, pol=1)}
+    best = autotune.tune_run(settings, steps=4, warmup=2, tiles=((16, 1, 16),), slots=(8.0,), sort_every=(0, 2))
+    assert {t["sort_every"] for t in best["trials"]} == {0, 2}
+    assert best["sort_every"] in (0, 2) and all("ms_per_step" in t for t in best["trials"])
