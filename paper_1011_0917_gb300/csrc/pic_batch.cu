@@ -71,8 +71,7 @@ __global__ void __launch_bounds__(kBlock)
     batch_tiles<real, DIM, S, TX, TY, TZ, REL, true>(runs, start, n, queue, smem_raw);
 }
 
-// batched form: a persistent grid of as many CTAs as fit on the device (its
-// share of them when several launch chains run side by side)
+// batched form: a persistent grid of as many CTAs as fit on the device
 template <typename real, int DIM, int S, int TX, int TY, int TZ, bool REL, bool IONS>
 void launch_push_batch(const void *args, const int64_t *start, int n, int64_t total, unsigned *queue,
                               cudaStream_t s)
@@ -83,8 +82,7 @@ void launch_push_batch(const void *args, const int64_t *start, int n, int64_t to
     int per_sm = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kBlock, smem) != cudaSuccess || per_sm < 1)
         per_sm = 1;
-    // a chain's share of the SMs, so that the chains of a batched step run side by side
-    int64_t grid = (int64_t)per_sm * device_sms() / (g_batch_chains > 1 ? g_batch_chains : 1);
+    int64_t grid = (int64_t)per_sm * device_sms();
     if (grid > total) grid = total;
     if (grid < 1) grid = 1;
     k<<<(unsigned)grid, kBlock, smem, s>>>(static_cast<const PushArgs<real> *>(args), start, n, queue);

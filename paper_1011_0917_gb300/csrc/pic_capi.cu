@@ -21,7 +21,6 @@ using namespace pic;
 
 namespace pic {
 thread_local BatchRecorder *g_rec = nullptr;
-thread_local int g_batch_chains = 1;
 
 int device_sms()
 {
@@ -1298,7 +1297,6 @@ static pic_status batch_capture_fused(pic_batch *b, int K, bool &ok)
     cudaEventRecord(G.join, G.cs);
     for (int m = 0; m < S; ++m) cudaStreamWaitEvent(G.chain_cs[m], G.join, 0);
     int64_t launches = 0;
-    g_batch_chains = S;
     for (const Group &g : groups) {
         if (g.total <= 0) continue;
         cudaStream_t x = G.chain_cs[g.chain];
@@ -1310,7 +1308,6 @@ static pic_status batch_capture_fused(pic_batch *b, int K, bool &ok)
         g.fn(d + g.args_off, reinterpret_cast<const int64_t *>(d + g.start_off), (int)g.idx.size(), g.total, q, x);
         ++launches;
     }
-    g_batch_chains = 1;
     for (int m = 0; m < S; ++m) {
         cudaEventRecord(G.chain_ev[m], G.chain_cs[m]);
         cudaStreamWaitEvent(G.cs, G.chain_ev[m], 0);

@@ -608,9 +608,6 @@ inline bool record_unsupported()
 }
 // runs whose field kernels share one launch (z chunks are sized for all)
 inline int batch_runs() { return g_rec ? g_rec->nctx : 1; }
-// while a batched step is being captured: the launch chains that run side by
-// side (a persistent grid takes its share of the SMs)
-extern thread_local int g_batch_chains;
 
 #ifdef __CUDACC__
 // the run owning work item `item`: the last r with start[r] <= item
