@@ -306,6 +306,10 @@ def test_boosted_2d_50_steps_with_injection(O, explicit, rel, prec):
     sim, o = _run_steps_parity(O, g, p, laser, 50, prec, explicit=explicit, rel=rel)
     err = vector_errors(sim, o)
     assert max(err.values()) < TOL50[prec], err
+    # the plasma's own Ez (the wake the laser starts), far below the laser's
+    # Ey, on its own
+    assert np.abs(o.field("Ez")).max() > 1e-6 * np.abs(o.field("Ey")).max()
+    assert field_errors(sim, o, ("Ez",))["Ez"] < TOL50[prec]
     d = sim.diagnostics()
     assert d.n_particles[0] == o.num(0) and d.n_particles[1] == o.num(1)
     if explicit:
@@ -325,6 +329,8 @@ def test_3d_boosted_30_steps(O, explicit, rel, prec):
     sim, o = _run_steps_parity(O, g, p, laser, 30, prec, explicit=explicit, rel=rel)
     err = vector_errors(sim, o)
     assert max(err.values()) < TOL50[prec], err
+    assert np.abs(o.field("Ez")).max() > 1e-6 * np.abs(o.field("Ey")).max()
+    assert field_errors(sim, o, ("Ez",))["Ez"] < TOL50[prec]
 
 
 # the wake on its own: at gamma = 130 the oracle's own FP64 wake carries
