@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--touched-advance", type=int, default=300,
                     help="steps further into the stage for the second push window that separates the cost of "
                          "a field-touched electron from that of a paired one (0: skip)")
+    ap.add_argument("--tile", default="",
+                    help="particle tile shape x,y,z (a compiled one; default: the library's)")
     ap.add_argument("--sort-every", type=int, default=0,
                     help="order every tile's particles by cell before every N-th step (0: never)")
     ap.add_argument("--advance", type=int, default=-1,
@@ -198,7 +200,8 @@ def run_ours(args, rank, world, local):
     g = st.grid
     stream = torch.cuda.Stream()
     advance = st.steps // 2 if args.advance < 0 else args.advance
-    sim = make_sim(P, st, args.slots_per_cell, stream, args.explicit_ions, advance)
+    tile = tuple(int(v) for v in args.tile.split(",")) if args.tile else (0, 0, 0)
+    sim = make_sim(P, st, args.slots_per_cell, stream, args.explicit_ions, advance, tile)
     ctx = sim.ctx
     if args.sort_every > 0:
         P.pic_set_cell_sort(ctx, args.sort_every)
@@ -225,6 +228,7 @@ def run_ours(args, rank, world, local):
     clock_info = clocks.stop()
     barrier()
     ms = e0.elapsed_time(e1)
+    sim_tile = tuple(sim.sizes.tile)
     phase_ms, phase_calls, kernels = P.pic_profile_read(ctx)
     P.pic_profile(ctx, False)
     d1 = sim.diagnostics()
@@ -384,6 +388,7 @@ def run_ours(args, rank, world, local):
                        "grid": [g["nx"], g["ny"], g["nz"]], "gamma_boost": g["gamma_boost"],
                        "filter_passes": g["filter_passes"], "shape_order": g["shape_order"],
                        "slots_per_cell": args.slots_per_cell, "cell_sort_every": args.sort_every,
+                       "tile": list(sim_tile),
                        "timed_window": f"steps {advance + args.warmup}..{advance + args.warmup + args.steps - 1} "
                                        f"of the {st.steps}-step stage",
                        "ion_records": "explicit" if args.explicit_ions else "paired with electrons until released",
@@ -644,12 +649,12 @@ def run_adjoint_3d(P, torch, steps, K=25, K2=5):
     return out
 
 
-def make_sim(P, st, slots_per_cell, stream, explicit_ions, advance):
+def make_sim(P, st, slots_per_cell, stream, explicit_ions, advance, tile=(0, 0, 0)):
     g = st.grid
     sim = P.Simulation(dim=g["dim"], nx=g["nx"], ny=g["ny"], nz=g["nz"], dx=g["dx"], dy=g["dy"], dz=g["dz"],
                        cfl=g["cfl"], gamma_boost=g["gamma_boost"], shape_order=g["shape_order"],
                        filter_passes=g["filter_passes"], bc_z=g["bc_z"], precision=P.PIC_FP32, seed=g["seed"],
-                       slots_per_cell=slots_per_cell, explicit_ions=explicit_ions, stream=stream)
+                       slots_per_cell=slots_per_cell, explicit_ions=explicit_ions, stream=stream, tile=tile)
     p = st.plasma
     sim.load_plasma(p["ne"], p["z_start"], p["z_end"], p["ramp"], p["ppc"], p["jitter"], (), p["ions"])
     l = st.laser

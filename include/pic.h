@@ -101,8 +101,9 @@ typedef struct pic_grid_params {
     uint64_t seed;          /* SplitMix64 seed of the plasma jitter             */
     double slots_per_cell;  /* particle slots per cell and species, > 0         */
     int tile[3];            /* tile shape in cells: 0 or a compiled shape:      */
-                            /* 8x8x8 in 3D; 16x1x16 in 2D, and with the CIC     */
-                            /* shape also 32x1x8, 8x1x32 (others: PIC_ERR_ARG)  */
+                            /* 8x8x8 in 3D (CIC also 8x8x4); 16x1x16 in 2D,     */
+                            /* with the CIC shape also 32x1x8, 8x1x32 (others:  */
+                            /* PIC_ERR_ARG)                                      */
     int track_ids;          /* 1: carry an int64 lattice id with each particle */
     int explicit_ions;      /* 1: store every drifting ion as its own record    */
                             /* (0: electron-ion pairs, see pic_load_plasma)     */

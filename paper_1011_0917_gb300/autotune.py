@@ -3,9 +3,10 @@
 Chooses, by timing a few steps of the run itself, among the configurations
 the library offers at run time:
 
-* the 2D particle tile shape: 16 x 16, 32 x 8 or 8 x 32 cells (x, z; the last
-  two with the CIC shape), which sets how many particles a CTA stages fields
-  and accumulates currents for, and how many leave their tile per step;
+* the particle tile shape: in 2D 16 x 16, 32 x 8 or 8 x 32 cells (x, z; the
+  last two with the CIC shape), in 3D 8 x 8 x 8 or (CIC) 8 x 8 x 4, which
+  sets how many particles a CTA stages fields and accumulates currents for,
+  and how many leave their tile per step;
 * the bucket capacity (slots per cell), which sets the memory a tile's
   particle records span;
 * for a batch of runs, the launch form: launch by launch on the runs'
@@ -25,6 +26,7 @@ import itertools
 import time
 
 TILES_2D = ((16, 1, 16), (32, 1, 8), (8, 1, 32))
+TILES_3D = ((8, 8, 8), (8, 8, 4))
 SLOTS = (6.0, 8.0, 12.0)
 
 
@@ -53,7 +55,8 @@ def tune_run(settings: dict, steps: int = 8, warmup: int = 3, tiles=None, slots=
     import paper_1011_0917_gb300 as P
     g = settings["grid"]
     if tiles is None:
-        tiles = TILES_2D if g.get("dim", 2) == 2 and g.get("shape_order", 1) == 1 else ((0, 0, 0),)
+        cic = g.get("shape_order", 1) == 1
+        tiles = (TILES_2D if g.get("dim", 2) == 2 else TILES_3D) if cic else ((0, 0, 0),)
     trials = []
     for tile, sl, srt in itertools.product(tiles, slots, sort_every):
         stream = torch.cuda.Stream()

@@ -138,4 +138,13 @@ template void launch_push_batch<double, 2, 1, 16, 1, 16, true, false>(const void
 template void launch_push_batch<double, 2, 1, 16, 1, 16, false, true>(const void *, const int64_t *, int, int64_t, unsigned *, cudaStream_t);
 template void launch_push_batch<double, 2, 1, 16, 1, 16, false, false>(const void *, const int64_t *, int, int64_t, unsigned *, cudaStream_t);
 
+template void launch_push_batch<float, 3, 1, 8, 8, 4, true, true>(const void *, const int64_t *, int, int64_t, unsigned *, cudaStream_t);
+template void launch_push_batch<float, 3, 1, 8, 8, 4, true, false>(const void *, const int64_t *, int, int64_t, unsigned *, cudaStream_t);
+template void launch_push_batch<float, 3, 1, 8, 8, 4, false, true>(const void *, const int64_t *, int, int64_t, unsigned *, cudaStream_t);
+template void launch_push_batch<float, 3, 1, 8, 8, 4, false, false>(const void *, const int64_t *, int, int64_t, unsigned *, cudaStream_t);
+template void launch_push_batch<double, 3, 1, 8, 8, 4, true, true>(const void *, const int64_t *, int, int64_t, unsigned *, cudaStream_t);
+template void launch_push_batch<double, 3, 1, 8, 8, 4, true, false>(const void *, const int64_t *, int, int64_t, unsigned *, cudaStream_t);
+template void launch_push_batch<double, 3, 1, 8, 8, 4, false, true>(const void *, const int64_t *, int, int64_t, unsigned *, cudaStream_t);
+template void launch_push_batch<double, 3, 1, 8, 8, 4, false, false>(const void *, const int64_t *, int, int64_t, unsigned *, cudaStream_t);
+
 }  // namespace pic

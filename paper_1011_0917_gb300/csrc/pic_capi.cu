@@ -323,11 +323,19 @@ extern "C" pic_status pic_init_grid(const pic_grid_params *p, pic_ctx **out)
         delete c;
         return PIC_ERR_ARG;
     }
-    // the particle kernels are compiled for one tile shape in 3D (8 x 8 x 8)
-    // and three in 2D (16 x 16, 32 x 8, 8 x 32 cells along x, z; the last
-    // two for the CIC shape only); a zero entry takes the default
+    // the particle kernels are compiled for two tile shapes in 3D (8 x 8 x 8,
+    // and for the CIC shape 8 x 8 x 4) and three in 2D (16 x 16, 32 x 8,
+    // 8 x 32 cells along x, z; the last two for the CIC shape only); a zero
+    // entry takes the default
     int def2[3] = {16, 1, 16};
-    const int def3[3] = {8, 8, 8};
+    int def3[3] = {8, 8, 8};
+    if (p->dim == 3 && p->tile[2] == 4) {
+        if (p->shape_order != 1) {
+            delete c;
+            return PIC_ERR_ARG;
+        }
+        def3[2] = 4;
+    }
     if (p->dim == 2 && (p->tile[0] != 0 || p->tile[2] != 0)) {
         const int tx = p->tile[0] ? p->tile[0] : 16, tz = p->tile[2] ? p->tile[2] : 16;
         const bool ok = (tx == 16 && tz == 16) || (p->shape_order == 1 && ((tx == 32 && tz == 8) || (tx == 8 && tz == 32)));

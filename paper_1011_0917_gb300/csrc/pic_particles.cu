@@ -47,8 +47,9 @@ template <typename real>
 static void dispatch_push(const PushArgs<real> &a, bool ions, cudaStream_t s)
 {
     if (a.g.dim == 3) {
-        if (a.g.shape == 1) launch_push_t<real, 3, 1, kTile3[0], kTile3[1], kTile3[2]>(a, ions, s);
-        else launch_push_t<real, 3, 2, kTile3[0], kTile3[1], kTile3[2]>(a, ions, s);
+        if (a.g.shape == 2) launch_push_t<real, 3, 2, kTile3[0], kTile3[1], kTile3[2]>(a, ions, s);
+        else if (a.g.lt[2] == 2) launch_push_t<real, 3, 1, 8, 8, 4>(a, ions, s);  // 8 x 8 x 4
+        else launch_push_t<real, 3, 1, kTile3[0], kTile3[1], kTile3[2]>(a, ions, s);
     } else if (a.g.shape == 2) {
         launch_push_t<real, 2, 2, kTile2[0], kTile2[1], kTile2[2]>(a, ions, s);
     } else if (a.g.lt[0] == 5) {  // 32 x 8

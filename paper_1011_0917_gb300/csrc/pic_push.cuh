@@ -974,7 +974,8 @@ __device__ __forceinline__ void ion_tile(const PushArgs<real> &a, const int64_t 
 }
 
 // the tile shapes the kernels are compiled for (pic_init_grid accepts these):
-// 8 x 8 x 8 in 3D; 16 x 16 in 2D, and for CIC also 32 x 8 and 8 x 32 (x, z)
+// 8 x 8 x 8 in 3D, and for CIC also 8 x 8 x 4; 16 x 16 in 2D, and for CIC
+// also 32 x 8 and 8 x 32 (x, z)
 constexpr int kTile3[3] = {8, 8, 8};
 constexpr int kTile2[3] = {16, 1, 16};
 

@@ -232,3 +232,21 @@ def test_simulation_refuses_without_a_gpu(P):
         pytest.skip("a CUDA device is present")
     with pytest.raises(RuntimeError, match="no CPU path"):
         P.Simulation(dim=2, nx=16, ny=1, nz=64, dx=0.5, dz=1 / 16)
+
+
+@pytest.mark.parametrize("tile,shape,ok", [((8, 8, 8), 1, True), ((8, 8, 4), 1, True), ((0, 0, 4), 1, True),
+                                           ((8, 8, 4), 2, False), ((8, 8, 16), 1, False), ((16, 8, 4), 1, False)])
+def test_3d_tile_shapes(P, tile, shape, ok):
+    g = grid(P, dim=3, nx=32, ny=16, nz=64, dx=1.0, dy=1.0, dz=1 / 32, gamma_boost=13.0, tile=tile,
+             shape_order=shape)
+    if not ok:
+        with pytest.raises(P.PicError) as e:
+            P.pic_init_grid(g)
+        assert e.value.status == 1
+        return
+    ctx = P.pic_init_grid(g)
+    try:
+        s = P.pic_query_sizes(ctx)
+        assert (s.tile[0], s.tile[1], s.tile[2]) == (8, 8, tile[2] if tile[2] else 8)
+    finally:
+        P.pic_destroy(ctx)

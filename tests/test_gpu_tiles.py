@@ -1,5 +1,6 @@
-"""The 2D tile-shape variants of the particle kernels (16 x 16, 32 x 8, 8 x 32
-cells) against the FP64 oracle, and the autotuner that picks among them.
+"""The tile-shape variants of the particle kernels (2D: 16 x 16, 32 x 8, 8 x 32
+cells; 3D: 8 x 8 x 8, 8 x 8 x 4) against the FP64 oracle, and the autotuners
+that pick among them and among the batch's launch forms.
 
 The tile shape changes only how particles are grouped for staging, deposit
 and re-bucketing, so every variant must match the oracle to the full-step
@@ -78,3 +79,28 @@ def test_autotune_tries_the_cell_sort_interval():
     best = autotune.tune_run(settings, steps=4, warmup=2, tiles=((16, 1, 16),), slots=(8.0,), sort_every=(0, 2))
     assert {t["sort_every"] for t in best["trials"]} == {0, 2}
     assert best["sort_every"] in (0, 2) and all("ms_per_step" in t for t in best["trials"])
+
+
+G3 = dict(dim=3, nx=16, ny=16, nz=48, dx=1.0, dy=1.0, dz=1 / 32, gamma_boost=GAM, filter_passes=2, seed=19)
+PLASMA3 = dict(ne=0.004, z_start=GAM * 6 * HZ, z_end=GAM * 200 * HZ, ramp=2.0, ppc=(2, 2, 2), jitter=0.1, ions=1)
+
+
+@pytest.mark.parametrize("explicit", [False, True])
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_3d_tile_variant_matches_oracle(O, prec, explicit):
+    """The 8 x 8 x 4 tile of the 3D CIC kernels against the oracle (30 steps,
+    the laser in the plasma, both ion modes)."""
+    sim, o = make_pair(O, G3, prec, tile=(8, 8, 4), explicit_ions=explicit)
+    assert tuple(sim.sizes.tile) == (8, 8, 4)
+    p = PLASMA3
+    sim.load_plasma(p["ne"], p["z_start"], p["z_end"], p["ramp"], p["ppc"], p["jitter"], (), p["ions"])
+    o.load_plasma(O.PlasmaParams(ne=p["ne"], z_start=p["z_start"], z_end=p["z_end"], ramp=p["ramp"], ppc=p["ppc"],
+                                 jitter=p["jitter"], ions=p["ions"]))
+    sim.launch_laser(LASER["a0"], 4.0, LASER["fwhm"], 0.0, LASER["t_peak"], 1)
+    o.set_laser(O.LaserParams(a0=LASER["a0"], waist=4.0, fwhm=LASER["fwhm"], t_peak=LASER["t_peak"], pol=1))
+    sim.step(30)
+    o.step(30)
+    err = vector_errors(sim, o)
+    assert max(err.values()) < TOL[prec], err
+    d = sim.diagnostics()
+    assert d.n_particles[0] == o.num(0) and d.n_particles[1] == o.num(1)
