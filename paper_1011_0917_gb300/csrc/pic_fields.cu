@@ -347,33 +347,36 @@ __device__ __forceinline__ void yee2d_body(const YeeArgs<real> &a, const int str
     const bool own = lane >= 1u && lane <= (unsigned)kColOwn && x < g.nx;
     const int z0 = chunk * a.cz;
     const int z1 = chunk == a.nchunks - 1 ? nzo : z0 + a.cz;
-    auto plane = [&](int k, bool half) {
-        return per ? wrapi(k, g.nz) : (k >= 0 && k <= zmax_of(g, half) ? k : -1);
+    // offset of this lane's node of plane k of a component with integer
+    // (half = false) or half-integer z, -1 where the component has no plane k
+    auto off = [&](int k, bool half) -> int64_t {
+        const int kk = per ? wrapi(k, g.nz) : (k >= 0 && k <= zmax_of(g, half) ? k : -1);
+        return kk >= 0 ? (int64_t)kk * g.plane + gx : int64_t(-1);
     };
-    auto ld = [&](const real *p, int kk) { return kk >= 0 ? p[(int64_t)kk * g.plane + gx] : real(0); };
+    auto ld = [&](const real *p, int64_t o) { return o >= 0 ? p[o] : real(0); };
     auto dn = [&](real v) { return __shfl_down_sync(0xffffffffu, v, 1); };  // the value at x + 1
     auto up = [&](real v) { return __shfl_up_sync(0xffffffffu, v, 1); };    // the value at x - 1
     const real zero = real(0);
     const int kb = z0 - 2;
+    // offsets of planes k and k + 1 (carried along the march)
+    int64_t oi0 = off(kb, false), oh0 = off(kb, true), oi1 = off(kb + 1, false), oh1 = off(kb + 1, true);
     // E^n of planes k - 1 (for Mur), k and k + 1; B^n and J of plane k;
     // Bh and E' of plane k - 1
     real emx = 0, emy = 0;
-    real ex0 = ld(a.E[0], plane(kb, false)), ey0 = ld(a.E[1], plane(kb, false)), ez0 = ld(a.E[2], plane(kb, true));
-    real ex1 = ld(a.E[0], plane(kb + 1, false)), ey1 = ld(a.E[1], plane(kb + 1, false));
-    real ez1 = ld(a.E[2], plane(kb + 1, true));
-    real bx = ld(a.B[0], plane(kb, true)), by = ld(a.B[1], plane(kb, true)), bz = ld(a.B[2], plane(kb, false));
-    real jx = ld(a.J[0], plane(kb, false)), jy = ld(a.J[1], plane(kb, false)), jz = ld(a.J[2], plane(kb, true));
+    real ex0 = ld(a.E[0], oi0), ey0 = ld(a.E[1], oi0), ez0 = ld(a.E[2], oh0);
+    real ex1 = ld(a.E[0], oi1), ey1 = ld(a.E[1], oi1), ez1 = ld(a.E[2], oh1);
+    real bx = ld(a.B[0], oh0), by = ld(a.B[1], oh0), bz = ld(a.B[2], oi0);
+    real jx = ld(a.J[0], oi0), jy = ld(a.J[1], oi0), jz = ld(a.J[2], oh0);
     real bmx = 0, bmy = 0, bmz = 0, fpx = 0, fpy = 0, fpz = 0;
     real murx = 0, mury = 0;  // E'(nz) x, y by Mur's condition (from plane nz - 1)
     for (int k = kb; k <= z1; ++k) {
         // the next plane's loads, used one iteration later
-        const int ke = plane(k + 2, false), keh = plane(k + 2, true);
-        const int kn = plane(k + 1, false), knh = plane(k + 1, true);
-        const real nex = ld(a.E[0], ke), ney = ld(a.E[1], ke), nez = ld(a.E[2], keh);
-        const real nbx = ld(a.B[0], knh), nby = ld(a.B[1], knh), nbz = ld(a.B[2], kn);
-        const real njx = ld(a.J[0], kn), njy = ld(a.J[1], kn), njz = ld(a.J[2], knh);
+        const int64_t oi2 = off(k + 2, false), oh2 = off(k + 2, true);
+        const real nex = ld(a.E[0], oi2), ney = ld(a.E[1], oi2), nez = ld(a.E[2], oh2);
+        const real nbx = ld(a.B[0], oh1), nby = ld(a.B[1], oh1), nbz = ld(a.B[2], oi1);
+        const real njx = ld(a.J[0], oi1), njy = ld(a.J[1], oi1), njz = ld(a.J[2], oh1);
         // ---- Bh(k)
-        const bool vxy = plane(k, true) >= 0, vz = plane(k, false) >= 0;
+        const bool vxy = oh0 >= 0, vz = oi0 >= 0;
         const real eyr = dn(ey0), ezr = dn(ez0);
         const real dEy_dz = (ey1 - ey0) * a.ihz;
         const real dEx_dz = (ex1 - ex0) * a.ihz;
@@ -386,7 +389,7 @@ __device__ __forceinline__ void yee2d_body(const YeeArgs<real> &a, const int str
         real fx = ex0, fy = ey0, fz = 0;
         {
             const real hyl = up(hy), hzl = up(hz);
-            const bool ve = per || (k >= 1 && k <= g.nz - 1), vze = plane(k, true) >= 0;
+            const bool ve = per || (k >= 1 && k <= g.nz - 1), vze = oh0 >= 0;
             if (ve) {
                 const real dBy_dz = (hy - bmy) * a.ihz;
                 fx = ex0 + a.he * ((zero - dBy_dz) - a.twopi * jx);
@@ -437,6 +440,10 @@ __device__ __forceinline__ void yee2d_body(const YeeArgs<real> &a, const int str
             }
         }
         // ---- shift the march by one plane
+        oi0 = oi1;
+        oh0 = oh1;
+        oi1 = oi2;
+        oh1 = oh2;
         emx = ex0;
         emy = ey0;
         ex0 = ex1;
@@ -993,11 +1000,14 @@ __device__ __forceinline__ void filter2d_body(const Geom &g, const real *in, rea
     const int z0 = chunk * cz;
     const int z1 = chunk == nchunks - 1 ? g.nz + 1 : z0 + cz;
     const int zmax_xy = zmax_of(g, false), zmax_z = zmax_of(g, true);
-    auto load = [&](int c, int k) {
-        const int zmax = c == 2 ? zmax_z : zmax_xy;
-        const bool have = per || (k >= 0 && k <= zmax);
+    // the three components of plane k (Jx, Jy on integer z, Jz on half-integer z)
+    auto load3 = [&](int k, real v[3]) {
         const int kk = per ? wrapi(k, g.nz) : k;
-        return have ? in[(size_t)c * g.ncomp + (int64_t)kk * g.plane + gx] : real(0);
+        const int64_t o = (int64_t)kk * g.plane + gx;
+        const bool hxy = per || (k >= 0 && k <= zmax_xy), hz = per || (k >= 0 && k <= zmax_z);
+        v[0] = hxy ? in[o] : real(0);
+        v[1] = hxy ? in[g.ncomp + o] : real(0);
+        v[2] = hz ? in[2 * g.ncomp + o] : real(0);
     };
     real lev[3][H + 1][3];
 #pragma unroll
@@ -1005,12 +1015,10 @@ __device__ __forceinline__ void filter2d_body(const Geom &g, const real *in, rea
 #pragma unroll
         for (int p = 0; p <= H; ++p) lev[c][p][0] = lev[c][p][1] = lev[c][p][2] = real(0);
     real cur[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) cur[c] = load(c, z0 - H);
+    load3(z0 - H, cur);
     for (int k = z0 - H; k <= z1 - 1 + H; ++k) {
-        real nxt[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) nxt[c] = k + 1 <= z1 - 1 + H ? load(c, k + 1) : real(0);
+        real nxt[3] = {real(0), real(0), real(0)};
+        if (k + 1 <= z1 - 1 + H) load3(k + 1, nxt);
         const int ko = k - H;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
