@@ -467,6 +467,207 @@ __device__ __forceinline__ void yee2d_body(const YeeArgs<real> &a, const int str
     }
 }
 
+// ------------------------------------------------------ 3D Yee, column march
+
+// The Yee step on 3D grids with the planes in registers: a CTA of 16 warps
+// owns kCol3Y x kColOwn (y, x) columns and a chunk of z planes; warp w holds
+// row y = y0 + w - 1 and lane l column x = x0 + l - 1 (both wrapped), so that
+// the x neighbours are shuffles and the y neighbours come through shared
+// memory, two exchanges per plane (E^n(k) and E'(k-1) with the row above;
+// Bh(k) with the row below).  Bh is exact on lanes 0-30 and warps 0-14, E' on
+// lanes 1-30 and warps 1-14, B' on lanes 1-29 and warps 1-13, the own
+// columns.  The march, its chunk ends and Mur's planes are yee2d_body's, the
+// arithmetic node by node yee_kernel's.
+constexpr int kCol3Y = 13, kCol3Warps = 16;
+
+template <typename real>
+__device__ __forceinline__ void yee3d_body(const YeeArgs<real> &a, const int sx, const int sy, const int chunk)
+{
+    __shared__ real xs[2][6][kCol3Warps][32];  // per parity: Ex, Ez, E'x, E'z of each row; Bh x, z
+    const Geom &g = a.g;
+    const bool per = g.bc_z == 0;
+    const int nzo = per ? g.nz : g.nz + 1;
+    const unsigned lane = threadIdx.x & 31u;
+    const int w = (int)(threadIdx.x >> 5);
+    const int x = sx * kColOwn + (int)lane - 1, y = sy * kCol3Y + w - 1;
+    const int gx = x >= 0 && x < g.nx ? x : wrapi(x, g.nx);
+    const int gy = y >= 0 && y < g.ny ? y : wrapi(y, g.ny);
+    const int64_t col = (int64_t)gy * g.nx + gx;
+    const bool own = lane >= 1u && lane <= (unsigned)kColOwn && w >= 1 && w <= kCol3Y && x < g.nx && y < g.ny;
+    const int wu = w + 1 < kCol3Warps ? w + 1 : w, wd = w >= 1 ? w - 1 : w;  // rows above and below (halo: own)
+    const int z0 = chunk * a.cz;
+    const int z1 = chunk == a.nchunks - 1 ? nzo : z0 + a.cz;
+    auto off = [&](int k, bool half) -> int64_t {
+        const int kk = per ? wrapi(k, g.nz) : (k >= 0 && k <= zmax_of(g, half) ? k : -1);
+        return kk >= 0 ? (int64_t)kk * g.plane + col : int64_t(-1);
+    };
+    auto ld = [&](const real *p, int64_t o) { return o >= 0 ? p[o] : real(0); };
+    auto dn = [&](real v) { return __shfl_down_sync(0xffffffffu, v, 1); };  // x + 1
+    auto up = [&](real v) { return __shfl_up_sync(0xffffffffu, v, 1); };    // x - 1
+    const real zero = real(0);
+    const int kb = z0 - 2;
+    int64_t oi0 = off(kb, false), oh0 = off(kb, true), oi1 = off(kb + 1, false), oh1 = off(kb + 1, true);
+    real emx = 0, emy = 0;
+    real ex0 = ld(a.E[0], oi0), ey0 = ld(a.E[1], oi0), ez0 = ld(a.E[2], oh0);
+    real ex1 = ld(a.E[0], oi1), ey1 = ld(a.E[1], oi1), ez1 = ld(a.E[2], oh1);
+    real bx = ld(a.B[0], oh0), by = ld(a.B[1], oh0), bz = ld(a.B[2], oi0);
+    real jx = ld(a.J[0], oi0), jy = ld(a.J[1], oi0), jz = ld(a.J[2], oh0);
+    real bmx = 0, bmy = 0, bmz = 0, fpx = 0, fpy = 0, fpz = 0;
+    real murx = 0, mury = 0;
+    for (int k = kb; k <= z1; ++k) {
+        const int P = k & 1;
+        const int64_t oi2 = off(k + 2, false), oh2 = off(k + 2, true);
+        const real nex = ld(a.E[0], oi2), ney = ld(a.E[1], oi2), nez = ld(a.E[2], oh2);
+        const real nbx = ld(a.B[0], oh1), nby = ld(a.B[1], oh1), nbz = ld(a.B[2], oi1);
+        const real njx = ld(a.J[0], oi1), njy = ld(a.J[1], oi1), njz = ld(a.J[2], oh1);
+        // ---- exchange 1: E^n(k) and E'(k - 1) with the row above
+        xs[P][0][w][lane] = ex0;
+        xs[P][1][w][lane] = ez0;
+        xs[P][2][w][lane] = fpx;
+        xs[P][3][w][lane] = fpz;
+        __syncthreads();
+        const real exu = xs[P][0][wu][lane], ezu = xs[P][1][wu][lane];
+        const real fpxu = xs[P][2][wu][lane], fpzu = xs[P][3][wu][lane];
+        // ---- Bh(k)
+        const bool vxy = oh0 >= 0, vz = oi0 >= 0;
+        const real eyr = dn(ey0), ezr = dn(ez0);
+        const real dEz_dy = (ezu - ez0) * a.ihy;
+        const real dEx_dy = (exu - ex0) * a.ihy;
+        const real dEy_dz = (ey1 - ey0) * a.ihz;
+        const real dEx_dz = (ex1 - ex0) * a.ihz;
+        const real dEz_dx = (ezr - ez0) * a.ihx;
+        const real dEy_dx = (eyr - ey0) * a.ihx;
+        const real hx = vxy ? bx - a.hb * (dEz_dy - dEy_dz) : real(0);
+        const real hy = vxy ? by - a.hb * (dEx_dz - dEz_dx) : real(0);
+        const real hz = vz ? bz - a.hb * (dEy_dx - dEx_dy) : real(0);
+        // ---- exchange 2: Bh(k) with the row below
+        xs[P][4][w][lane] = hx;
+        xs[P][5][w][lane] = hz;
+        __syncthreads();
+        const real hxd = xs[P][4][wd][lane], hzd = xs[P][5][wd][lane];
+        // ---- E'(k)
+        real fx = ex0, fy = ey0, fz = 0;
+        {
+            const real hyl = up(hy), hzl = up(hz);
+            const bool ve = per || (k >= 1 && k <= g.nz - 1), vze = oh0 >= 0;
+            if (ve) {
+                const real dBz_dy = (hz - hzd) * a.ihy;
+                const real dBy_dz = (hy - bmy) * a.ihz;
+                fx = ex0 + a.he * ((dBz_dy - dBy_dz) - a.twopi * jx);
+                const real dBx_dz = (hx - bmx) * a.ihz;
+                const real dBz_dx = (hz - hzl) * a.ihx;
+                fy = ey0 + a.he * ((dBx_dz - dBz_dx) - a.twopi * jy);
+            }
+            const real dBy_dx = (hy - hyl) * a.ihx;
+            const real dBx_dy = (hx - hxd) * a.ihy;
+            fz = vze ? ez0 + a.he * ((dBy_dx - dBx_dy) - a.twopi * jz) : real(0);
+            if (!per) {
+                if (k == 1) {
+                    fpx = ex0 + a.mur * (fx - emx);
+                    fpy = ey0 + a.mur * (fy - emy);
+                }
+                if (k == g.nz - 1) {
+                    murx = ex0 + a.mur * (fx - ex1);
+                    mury = ey0 + a.mur * (fy - ey1);
+                }
+                if (k == g.nz) {
+                    fx = murx;
+                    fy = mury;
+                }
+            }
+        }
+        // ---- E'(k - 1), B'(k - 1) of the own columns.  At k = 1 Mur's
+        // condition has just set E'(0) x, y: the row above's E'x(0), which B'z
+        // reads, is exchanged again (k is the same for the whole CTA)
+        real fpxu2 = fpxu;
+        if (!per && k == 1) {
+            xs[P][2][w][lane] = fpx;
+            __syncthreads();
+            fpxu2 = xs[P][2][wu][lane];
+        }
+        {
+            const int kw = k - 1;
+            const real fpyr = dn(fpy), fpzr = dn(fpz);
+            if (kw >= z0 && kw < z1 && own) {
+                const int64_t o = (int64_t)kw * g.plane + col;
+                const bool wxy = kw <= zmax_of(g, false), wz = kw <= zmax_of(g, true);
+                if (wxy) {
+                    a.E1[0][o] = fpx;
+                    a.E1[1][o] = fpy;
+                }
+                if (wz) {
+                    a.E1[2][o] = fpz;
+                    const real dEz_dy1 = (fpzu - fpz) * a.ihy;
+                    const real dEy_dz1 = (fy - fpy) * a.ihz;
+                    a.B1[0][o] = bmx - a.hb * (dEz_dy1 - dEy_dz1);
+                    const real dEx_dz1 = (fx - fpx) * a.ihz;
+                    const real dEz_dx1 = (fpzr - fpz) * a.ihx;
+                    a.B1[1][o] = bmy - a.hb * (dEx_dz1 - dEz_dx1);
+                }
+                if (wxy) {
+                    const real dEy_dx1 = (fpyr - fpy) * a.ihx;
+                    const real dEx_dy1 = (fpxu2 - fpx) * a.ihy;
+                    a.B1[2][o] = bmz - a.hb * (dEy_dx1 - dEx_dy1);
+                }
+            }
+        }
+        oi0 = oi1;
+        oh0 = oh1;
+        oi1 = oi2;
+        oh1 = oh2;
+        emx = ex0;
+        emy = ey0;
+        ex0 = ex1;
+        ey0 = ey1;
+        ez0 = ez1;
+        ex1 = nex;
+        ey1 = ney;
+        ez1 = nez;
+        bx = nbx;
+        by = nby;
+        bz = nbz;
+        jx = njx;
+        jy = njy;
+        jz = njz;
+        bmx = hx;
+        bmy = hy;
+        bmz = hz;
+        fpx = fx;
+        fpy = fy;
+        fpz = fz;
+    }
+}
+
+template <typename real>
+__device__ __forceinline__ void yee3d_item(const YeeArgs<real> &a, int64_t item)
+{
+    const int nsx = (a.g.nx + kColOwn - 1) / kColOwn, nsy = (a.g.ny + kCol3Y - 1) / kCol3Y;
+    const int sx = (int)(item % nsx), sy = (int)((item / nsx) % nsy), ch = (int)(item / ((int64_t)nsx * nsy));
+    yee3d_body(a, sx, sy, ch);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(512, 2) yee3d_kernel(YeeArgs<real> a)
+{
+    yee3d_item(a, (int64_t)blockIdx.x);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(512, 2) yee3d_batch_kernel(const YeeArgs<real> *__restrict__ runs,
+                                                             const int64_t *__restrict__ start, int n)
+{
+    __shared__ __align__(16) YeeArgs<real> sa;
+    const int64_t b = batch_block(runs, start, n, &sa);
+    yee3d_item(sa, b);
+}
+
+template <typename real>
+static void launch_yee3d_batch(const void *args, const int64_t *start, int n, int64_t total, unsigned *,
+                               cudaStream_t s)
+{
+    yee3d_batch_kernel<real><<<(unsigned)total, 512, 0, s>>>(static_cast<const YeeArgs<real> *>(args), start, n);
+}
+
 // one warp per (strip, chunk) item; YeeArgs::cz holds the planes per chunk,
 // nchunks the chunks (the strips follow from the grid)
 template <typename real>
@@ -558,6 +759,19 @@ void launch_yee(const Geom &g, real *const F[9], real *const F1[6], double dt, d
         const int64_t nitems = (int64_t)nstrip * a.nchunks, nblocks = (nitems + 7) / 8;
         if (record_launch(kBPYee, launch_yee2d_batch<real>, a, nblocks)) return;
         yee2d_kernel<real><<<(unsigned)nblocks, 256, 0, s>>>(a, nitems);
+        return;
+    }
+    {
+        // the column march: chunks of 16..64 planes, as many as leave about
+        // four CTAs of 16 warps per SM
+        const int64_t ncol = (int64_t)((g.nx + kColOwn - 1) / kColOwn) * ((g.ny + kCol3Y - 1) / kCol3Y);
+        int64_t czl = (int64_t)nzo * ncol * batch_runs() / ((int64_t)device_sms() * 4);
+        a.cz = (int)(czl < 16 ? 16 : (czl > 64 ? 64 : czl));
+        if (a.cz > nzo) a.cz = nzo;
+        a.nchunks = (nzo + a.cz - 1) / a.cz;
+        const int64_t nblocks = ncol * a.nchunks;
+        if (record_launch(kBPYee, launch_yee3d_batch<real>, a, nblocks)) return;
+        yee3d_kernel<real><<<(unsigned)nblocks, 512, 0, s>>>(a);
         return;
     }
     constexpr int TX = YeeTile<3>::TX, TY = YeeTile<3>::TY;
