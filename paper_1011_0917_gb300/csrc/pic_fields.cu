@@ -5,9 +5,9 @@
 // steps so that E and B both live at integer times:
 //   B -= (dt/2) curl E;   E += dt (curl B - 2 pi J);   B -= (dt/2) curl E,
 // all three in one kernel that reads E^n, B^n from one field buffer and writes
-// E^{n+1}, B^{n+1} to another (yee_kernel).  With absorbing z the tangential E
-// (Ex, Ey) on the end planes k = 0 and k = nz follows Mur's first-order
-// condition (Mur 1981).
+// E^{n+1}, B^{n+1} to another (yee2d_kernel, yee3d_kernel).  With absorbing z
+// the tangential E (Ex, Ey) on the end planes k = 0 and k = nz follows Mur's
+// first-order condition (Mur 1981).
 #include "pic.h"
 #include "pic_internal.cuh"
 #include "pic_tma.cuh"
@@ -67,272 +67,41 @@ struct YeeArgs {
     int cz, nchunks;          // z planes per chunk, chunks
 };
 
-// column shape of a CTA of the marching Yee kernel (3D grids; 2D grids take
-// yee2d_kernel): 32 x 8 (x, y)
-template <int DIM> struct YeeTile { static constexpr int TX = 32, TY = 8, HY = 1; };
-
-// One Yee step in one pass over the grid.  A CTA owns a column of TX x TY
-// nodes in (x, y) and a chunk of z planes; it marches up the chunk keeping a
-// few planes of E^n, B^n, J, of the half-step B (Bh) and of E^{n+1} (E') in
-// shared memory.  At plane k of the march:
-//   Bh(k)   = B^n(k) - (dt/2) curl E^n      (E^n at k and k+1)
-//   E'(k)   = E^n(k) + dt (curl Bh - 2 pi J) (Bh at k and k-1)
-//   B'(k-1) = Bh(k-1) - (dt/2) curl E'      (E' at k-1 and k)
-// while the planes the next step of the march reads (E^n(k+2), B^n(k+1),
-// J(k+1)) are copied into shared memory with cp.async.  Each curl takes the
-// next (x, y) neighbour on one side, so Bh is updated on the column widened
-// by one node on both sides, E' widened by one node above, and neighbouring
-// columns recompute the widened nodes; E' and B' of the column's own nodes
-// are written to the other field buffer, so no CTA reads a value another one
-// writes.  The chunk starts one plane early (the Bh plane below its first E'
-// plane) and ends one plane late (the E' plane above its last B' plane).
-// With absorbing z the tangential E (Ex, Ey) of the end planes follows Mur's
-// first-order condition
-//   E0^{n+1} = E1^n + (dt - dz)/(dt + dz) (E1^{n+1} - E0^n)
-// (Mur 1981), evaluated once E' of the neighbouring plane is known.  The
-// arithmetic per node is that of the split-B leapfrog written out term by
-// term.  Planes a component does not have (Ez, Bx, By at k = nz; every
-// component at k = nz with periodic z) are neither read nor written.
-template <typename real, int DIM>
-__device__ __forceinline__ void yee_body(const YeeArgs<real> &a, const int bx_, const int by_)
+// CTAs of a grid-stride loop over n items: all of them, at most 32 per SM
+static unsigned grid_for(int64_t n, int block)
 {
-    constexpr int TX = YeeTile<DIM>::TX, TY = YeeTile<DIM>::TY, HY = YeeTile<DIM>::HY;
-    constexpr int NT = 256;  // threads; every thread owns at most two nodes of each shared plane
-    // shared planes: E^n on x0-1 .. x0+TX+1, y0-HY .. y0+TY-1+2HY; B^n and Bh
-    // on x0-1 .. x0+TX, y0-HY .. y0+TY-1+HY; J and E' on x0 .. x0+TX,
-    // y0 .. y0+TY-1+HY
-    constexpr int NX0 = TX + 3, NY0 = TY + 3 * HY, P0 = NX0 * NY0;
-    constexpr int NX1 = TX + 2, NY1 = TY + 2 * HY, P1 = NX1 * NY1;
-    constexpr int NX2 = TX + 1, NY2 = TY + HY, P2 = NX2 * NY2;
-    static_assert(P0 <= 2 * NT && TX * TY == NT, "plane regions must fit two nodes per thread");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    real *sE = reinterpret_cast<real *>(smem_raw);  // E^n: [4 planes][3 components][P0]
-    real *sN = sE + 12 * P0;                         // B^n: [2][3][P1]
-    real *sJ = sN + 6 * P1;                          // J:   [2][3][P2]
-    real *sB = sJ + 6 * P2;                          // Bh:  [2][3][P1]
-    real *sF = sB + 6 * P1;                          // E':  [3][3][P2]
-    const Geom &g = a.g;
-    const bool per = g.bc_z == 0;
-    const int nbx = (g.nx + TX - 1) / TX;
-    const int x0 = (bx_ % nbx) * TX, y0 = (bx_ / nbx) * TY;
-    const int nzo = per ? g.nz : g.nz + 1;  // planes written
-    const int z0 = by_ * a.cz;
-    const int z1 = by_ == a.nchunks - 1 ? nzo : z0 + a.cz;
-    const int kb = z0 - 1;
-    const int tid = (int)threadIdx.x;
-    auto r2 = [&](int k) { return (k - kb) & 1; };
-    auto r3 = [&](int k) { return (k - kb) % 3; };
-    auto r4 = [&](int k) { return (k - kb) & 3; };
-    // plane k of a component in memory (-1: the component has no plane k)
-    auto mem_plane = [&](int k, bool half) {
-        return per ? wrapi(k, g.nz) : (k >= 0 && k <= zmax_of(g, half) ? k : -1);
-    };
-    // periodic x, y (columns of grids narrower than a CTA wrap more than once)
-    auto gxw = [&](int x) { return x >= 0 && x < g.nx ? x : wrapi(x, g.nx); };
-    auto gyw = [&](int y) { return DIM == 3 ? (y >= 0 && y < g.ny ? y : wrapi(y, g.ny)) : 0; };
-    // this thread's nodes r = tid, tid + NT of a region (nx_ wide, np nodes,
-    // origin (xo, yo)): their offsets within a plane in memory (-1: none)
-    auto offs = [&](int nx_, int np, int xo, int yo, int o[2]) {
-#pragma unroll
-        for (int m = 0; m < 2; ++m) {
-            const int r = tid + m * NT;
-            const int ly = r / nx_, lx = r - ly * nx_;
-            o[m] = r < np ? gyw(yo + ly) * g.nx + gxw(xo + lx) : -1;
-        }
-    };
-    int oE[2], oB[2], oJ[2];
-    offs(NX0, P0, x0 - 1, y0 - HY, oE);
-    offs(NX1, P1, x0 - 1, y0 - HY, oB);
-    offs(NX2, P2, x0, y0, oJ);
-    // copy plane k of three components into shared memory (this thread's
-    // nodes); planes a component does not have are zero
-    auto fetch = [&](const real *const src[3], real *dst, int k, int np, const int o[2], bool e_half) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const int kk = mem_plane(k, e_half ? c == 2 : c != 2);
-            const real *base = src[c] + (int64_t)kk * g.plane;
-#pragma unroll
-            for (int m = 0; m < 2; ++m) {
-                if (o[m] < 0) continue;
-                real *d = dst + c * np + tid + m * NT;
-                if (kk >= 0) __pipeline_memcpy_async(d, base + o[m], sizeof(real));
-                else *d = real(0);
-            }
-        }
-    };
-    auto fetch_all = [&](int ke, int kbj) {
-        fetch(a.E, sE + r4(ke) * 3 * P0, ke, P0, oE, true);
-        fetch(a.B, sN + r2(kbj) * 3 * P1, kbj, P1, oB, false);
-        fetch(a.J, sJ + r2(kbj) * 3 * P2, kbj, P2, oJ, true);
-    };
-
-    // Bh(k) on its widened column
-    auto half_b = [&](int k) {
-        const real *e0 = sE + r4(k) * 3 * P0, *e1 = sE + r4(k + 1) * 3 * P0, *bn = sN + r2(k) * 3 * P1;
-        real *dst = sB + r2(k) * 3 * P1;
-        const bool vxy = mem_plane(k, true) >= 0, vz = mem_plane(k, false) >= 0;
-#pragma unroll
-        for (int m = 0; m < 2; ++m) {
-            const int r = tid + m * NT;
-            if (r >= P1) continue;
-            const int ly = r / NX1, lx = r - ly * NX1;
-            const int o = ly * NX0 + lx;  // the same node in the E^n plane
-            real dEz_dy = 0, dEx_dy = 0;
-            if (DIM == 3) {
-                dEz_dy = (e0[2 * P0 + o + NX0] - e0[2 * P0 + o]) * a.ihy;
-                dEx_dy = (e0[o + NX0] - e0[o]) * a.ihy;
-            }
-            const real dEy_dz = (e1[P0 + o] - e0[P0 + o]) * a.ihz;
-            const real dEx_dz = (e1[o] - e0[o]) * a.ihz;
-            const real dEz_dx = (e0[2 * P0 + o + 1] - e0[2 * P0 + o]) * a.ihx;
-            const real dEy_dx = (e0[P0 + o + 1] - e0[P0 + o]) * a.ihx;
-            dst[r] = vxy ? bn[r] - a.hb * (dEz_dy - dEy_dz) : real(0);
-            dst[P1 + r] = vxy ? bn[P1 + r] - a.hb * (dEx_dz - dEz_dx) : real(0);
-            dst[2 * P1 + r] = vz ? bn[2 * P1 + r] - a.hb * (dEy_dx - dEx_dy) : real(0);
-        }
-    };
-    // E'(k) on its widened column (Ampere; Ex, Ey of the Mur planes are set
-    // apart by the boundary condition)
-    auto full_e = [&](int k) {
-        const real *e0 = sE + r4(k) * 3 * P0, *jj = sJ + r2(k) * 3 * P2;
-        const real *b0 = sB + r2(k) * 3 * P1, *bm = sB + r2(k - 1) * 3 * P1;
-        real *dst = sF + r3(k) * 3 * P2;
-        const bool vz = mem_plane(k, true) >= 0;
-        const bool vxy = per || (k >= 1 && k <= g.nz - 1);
-#pragma unroll
-        for (int m = 0; m < 2; ++m) {
-            const int r = tid + m * NT;
-            if (r >= P2) continue;
-            const int ly = r / NX2, lx = r - ly * NX2;
-            const int ob = (ly + HY) * NX1 + lx + 1;  // the node in the Bh plane
-            const int oe = (ly + HY) * NX0 + lx + 1;  // and in the E^n plane
-            real dBz_dy = 0, dBx_dy = 0;
-            if (DIM == 3) {
-                dBz_dy = (b0[2 * P1 + ob] - b0[2 * P1 + ob - NX1]) * a.ihy;
-                dBx_dy = (b0[ob] - b0[ob - NX1]) * a.ihy;
-            }
-            if (vxy) {
-                const real dBy_dz = (b0[P1 + ob] - bm[P1 + ob]) * a.ihz;
-                dst[r] = e0[oe] + a.he * ((dBz_dy - dBy_dz) - a.twopi * jj[r]);
-                const real dBx_dz = (b0[ob] - bm[ob]) * a.ihz;
-                const real dBz_dx = (b0[2 * P1 + ob] - b0[2 * P1 + ob - 1]) * a.ihx;
-                dst[P2 + r] = e0[P0 + oe] + a.he * ((dBx_dz - dBz_dx) - a.twopi * jj[P2 + r]);
-            }
-            const real dBy_dx = (b0[P1 + ob] - b0[P1 + ob - 1]) * a.ihx;
-            dst[2 * P2 + r] = vz ? e0[2 * P0 + oe] + a.he * ((dBy_dx - dBx_dy) - a.twopi * jj[2 * P2 + r]) : real(0);
-        }
-    };
-    // Mur: Ex, Ey of plane kt from plane kn (its neighbour inside the box)
-    auto mur = [&](int kt, int kn) {
-        const real *et = sE + r4(kt) * 3 * P0, *en = sE + r4(kn) * 3 * P0;
-        const real *fn = sF + r3(kn) * 3 * P2;
-        real *ft = sF + r3(kt) * 3 * P2;
-#pragma unroll
-        for (int m = 0; m < 2; ++m) {
-            const int r = tid + m * NT;
-            if (r >= P2) continue;
-            const int ly = r / NX2, lx = r - ly * NX2;
-            const int oe = (ly + HY) * NX0 + lx + 1;
-            ft[r] = en[oe] + a.mur * (fn[r] - et[oe]);
-            ft[P2 + r] = en[P0 + oe] + a.mur * (fn[P2 + r] - et[P0 + oe]);
-        }
-    };
-    // B'(k) and E'(k) of the column's own node of this thread to memory
-    const int lxo = tid % TX, lyo = tid / TX;
-    const bool own = x0 + lxo < g.nx && (DIM == 2 || y0 + lyo < g.ny);
-    const int64_t oxy = own ? (int64_t)(y0 + lyo) * g.nx + (x0 + lxo) : 0;
-    auto write_out = [&](int k) {
-        if (!own) return;
-        const real *b0 = sB + r2(k) * 3 * P1;
-        const real *f0 = sF + r3(k) * 3 * P2, *f1 = sF + r3(k + 1) * 3 * P2;
-        const int64_t o = (int64_t)k * g.plane + oxy;
-        const int of = lyo * NX2 + lxo;               // the node in the E' plane
-        const int ob = (lyo + HY) * NX1 + lxo + 1;    // and in the Bh plane
-        const bool vxy = k <= zmax_of(g, false), vz = k <= zmax_of(g, true);
-        if (vxy) {
-            a.E1[0][o] = f0[of];
-            a.E1[1][o] = f0[P2 + of];
-        }
-        if (vz) {
-            a.E1[2][o] = f0[2 * P2 + of];
-            real dEz_dy = 0;
-            if (DIM == 3) dEz_dy = (f0[2 * P2 + of + NX2] - f0[2 * P2 + of]) * a.ihy;
-            const real dEy_dz = (f1[P2 + of] - f0[P2 + of]) * a.ihz;
-            a.B1[0][o] = b0[ob] - a.hb * (dEz_dy - dEy_dz);
-            const real dEx_dz = (f1[of] - f0[of]) * a.ihz;
-            const real dEz_dx = (f0[2 * P2 + of + 1] - f0[2 * P2 + of]) * a.ihx;
-            a.B1[1][o] = b0[P1 + ob] - a.hb * (dEx_dz - dEz_dx);
-        }
-        if (vxy) {
-            const real dEy_dx = (f0[P2 + of + 1] - f0[P2 + of]) * a.ihx;
-            real dEx_dy = 0;
-            if (DIM == 3) dEx_dy = (f0[of + NX2] - f0[of]) * a.ihy;
-            a.B1[2][o] = b0[2 * P1 + ob] - a.hb * (dEy_dx - dEx_dy);
-        }
-    };
-
-    fetch(a.E, sE + r4(kb) * 3 * P0, kb, P0, oE, true);
-    fetch_all(kb + 1, kb);
-    __pipeline_commit();
-    for (int k = kb; k <= z1; ++k) {
-        // the planes the next step reads, while this one is computed
-        fetch_all(k + 2, k + 1);
-        __pipeline_commit();
-        __pipeline_wait_prior(1);
-        __syncthreads();
-        half_b(k);
-        __syncthreads();
-        if (k >= z0) {
-            full_e(k);
-            __syncthreads();
-            if (!per && (k == 1 || k == g.nz - 1)) {
-                if (k == 1) mur(0, 1);
-                if (k == g.nz - 1) mur(g.nz, g.nz - 1);
-                __syncthreads();
-            }
-        }
-        if (k >= z0 + 1) write_out(k - 1);
-    }
-    __pipeline_wait_prior(0);
-}
-
-template <typename real, int DIM>
-__global__ void __launch_bounds__(256) yee_kernel(YeeArgs<real> a)
-{
-    yee_body<real, DIM>(a, (int)blockIdx.x, (int)blockIdx.y);
-}
-
-// CTAs of one z column chunk per run of a batch: block b of run r is column
-// b % ncol, chunk b / ncol
-template <typename real, int DIM>
-__global__ void __launch_bounds__(256) yee_batch_kernel(const YeeArgs<real> *__restrict__ runs,
-                                                        const int64_t *__restrict__ start, int n)
-{
-    __shared__ __align__(16) YeeArgs<real> sa;
-    const int64_t b = batch_block(runs, start, n, &sa);
-    constexpr int TX = YeeTile<DIM>::TX, TY = YeeTile<DIM>::TY;
-    const int ncol = ((sa.g.nx + TX - 1) / TX) * (DIM == 3 ? (sa.g.ny + TY - 1) / TY : 1);
-    yee_body<real, DIM>(sa, (int)(b % ncol), (int)(b / ncol));
+    int64_t b = (n + block - 1) / block;
+    const int64_t cap = (int64_t)device_sms() * 32;
+    return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
 // --------------------------------------------------- 2D Yee, column march
 
-// The Yee step on 2D grids with the planes in registers: a warp owns a strip
-// of kColOwn x columns and a chunk of z planes and marches up the chunk like
-// yee_kernel, one plane per iteration, each lane holding one column (lane l:
-// x = strip * kColOwn + l - 1, wrapped), so that every z neighbour is a
-// register of the previous iteration and every x neighbour a shuffle.  The
-// curls reach one column to each side: Bh is exact on lanes 0-30, E' on
-// lanes 1-30 and B' on lanes 1-29, the strip's own columns.  No shared
-// memory and no barrier: the warps of a CTA are independent, and the loads
-// of a plane are issued a plane ahead of their use.  At plane k of the march
-// (the arithmetic of yee_kernel node by node, d/dy = 0):
-//   Bh(k)   from B^n(k), E^n(k), E^n(k+1)
-//   E'(k)   from E^n(k), Bh(k), Bh(k-1), J(k); Mur's planes from E'(1),
-//           E'(nz-1) and the E^n around them
-//   B'(k-1) from Bh(k-1), E'(k-1), E'(k), written with E'(k-1)
-// The chunk [z0, z1) starts two planes early (E' of plane z0 - 1 for Mur's
-// upper plane when nz - 1 is the plane before the chunk) and ends one late.
+// One Yee step in one pass over the grid, as a march up z with the planes in
+// registers: each thread holds one (x, y) column and a chunk of z planes,
+// and at plane k of the march computes
+//   Bh(k)   = B^n(k) - (dt/2) curl E^n       (E^n at k and k+1)
+//   E'(k)   = E^n(k) + dt (curl Bh - 2 pi J)  (Bh at k and k-1)
+//   B'(k-1) = Bh(k-1) - (dt/2) curl E'       (E' at k-1 and k)
+// and writes E'(k-1), B'(k-1) to the other field buffer, so that no thread
+// reads a value another one writes.  Every z neighbour is a register of the
+// previous iteration, every x neighbour a warp shuffle (lane l holds column
+// x0 + l - 1), and the loads of a plane are issued an iteration ahead of
+// their use.  Each curl takes the next neighbour on one side, so the columns
+// at a strip's edges are its halo: Bh is exact on lanes 0-30, E' on lanes
+// 1-30 and B' on lanes 1-29, the strip's own kColOwn columns.  With absorbing
+// z the tangential E (Ex, Ey) of the end planes follows Mur's first-order
+// condition
+//   E0^{n+1} = E1^n + (dt - dz)/(dt + dz) (E1^{n+1} - E0^n)
+// (Mur 1981), evaluated from the registers once E' of the neighbouring plane
+// is known.  The chunk [z0, z1) starts two planes early (E' of plane z0 - 1
+// for Mur's upper plane when nz - 1 is the plane before the chunk) and ends
+// one late.  The arithmetic per node is that of the split-B leapfrog written
+// out term by term; planes a component does not have (Ez, Bx, By at k = nz;
+// every component at k = nz with periodic z) are neither read nor written.
+//
+// In 2D (d/dy = 0) a warp is independent of the others: no shared memory
+// and no barrier.
 constexpr int kColOwn = 29;
 
 template <typename real>
@@ -476,8 +245,8 @@ __device__ __forceinline__ void yee2d_body(const YeeArgs<real> &a, const int str
 // memory, two exchanges per plane (E^n(k) and E'(k-1) with the row above;
 // Bh(k) with the row below).  Bh is exact on lanes 0-30 and warps 0-14, E' on
 // lanes 1-30 and warps 1-14, B' on lanes 1-29 and warps 1-13, the own
-// columns.  The march, its chunk ends and Mur's planes are yee2d_body's, the
-// arithmetic node by node yee_kernel's.
+// columns.  The march, its chunk ends, Mur's planes and the arithmetic are
+// yee2d_body's with the y terms of the curls.
 constexpr int kCol3Y = 13, kCol3Warps = 16;
 
 template <typename real>
@@ -701,32 +470,6 @@ static void launch_yee2d_batch(const void *args, const int64_t *start, int n, in
     yee2d_batch_kernel<real><<<(unsigned)total, 256, 0, s>>>(static_cast<const YeeArgs<real> *>(args), start, n);
 }
 
-template <typename real, int DIM>
-static size_t yee_smem()
-{
-    constexpr int TX = YeeTile<DIM>::TX, TY = YeeTile<DIM>::TY, HY = YeeTile<DIM>::HY;
-    // E^n 4 planes, B^n and Bh 2 each, J 2, E' 3 (three components each)
-    return sizeof(real) * 3 *
-           (4 * (size_t)(TX + 3) * (TY + 3 * HY) + 4 * (size_t)(TX + 2) * (TY + 2 * HY) +
-            5 * (size_t)(TX + 1) * (TY + HY));
-}
-
-template <typename real, int DIM>
-static void launch_yee_batch(const void *args, const int64_t *start, int n, int64_t total, unsigned *, cudaStream_t s)
-{
-    const size_t smem = yee_smem<real, DIM>();
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(yee_batch_kernel<real, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    yee_batch_kernel<real, DIM><<<(unsigned)total, 256, smem, s>>>(static_cast<const YeeArgs<real> *>(args), start, n);
-}
-
-static unsigned grid_for(int64_t n, int block)
-{
-    int64_t b = (n + block - 1) / block;
-    const int64_t cap = 152LL * 32;
-    return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
-}
-
 template <typename real>
 void launch_yee(const Geom &g, real *const F[9], real *const F1[6], double dt, double hx, double hy, double hz,
                 cudaStream_t s)
@@ -772,26 +515,7 @@ void launch_yee(const Geom &g, real *const F[9], real *const F1[6], double dt, d
         const int64_t nblocks = ncol * a.nchunks;
         if (record_launch(kBPYee, launch_yee3d_batch<real>, a, nblocks)) return;
         yee3d_kernel<real><<<(unsigned)nblocks, 512, 0, s>>>(a);
-        return;
     }
-    constexpr int TX = YeeTile<3>::TX, TY = YeeTile<3>::TY;
-    // chunks of 4..32 planes, as long as there are about eight CTAs per SM;
-    // the last chunk takes the remainder
-    if (nzo < 8) {
-        a.cz = nzo;
-    } else {
-        const int64_t ncol = (int64_t)((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
-        int64_t czl = (int64_t)nzo * ncol * batch_runs() / ((int64_t)device_sms() * 8);
-        a.cz = (int)(czl < 4 ? 4 : (czl > 32 ? 32 : czl));
-    }
-    a.nchunks = nzo / a.cz;
-    if (a.nchunks < 1) a.nchunks = 1;
-    const size_t smem = yee_smem<real, 3>();
-    const unsigned nb = (unsigned)(((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY));
-    if (record_launch(kBPYee, launch_yee_batch<real, 3>, a, (int64_t)nb * a.nchunks)) return;
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(yee_kernel<real, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    yee_kernel<real, 3><<<dim3(nb, (unsigned)a.nchunks), 256, smem, s>>>(a);
 }
 
 // ---------------------------------------------------------- moving window
