@@ -32,7 +32,7 @@ constexpr double kTwoPiD = 6.283185307179586;
 unsigned adj_grid(int64_t n, int block)
 {
     int64_t b = (n + block - 1) / block;
-    const int64_t cap = 152LL * 32;
+    const int64_t cap = (int64_t)device_sms() * 32;
     return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
@@ -1001,12 +1001,12 @@ void launch_adj_planes(const Geom &g, const real *F, int nc, unsigned char *near
 {
     cudaMemsetAsync(near, 0, (size_t)g.nz + 1, s);
     const int nk = g.nz + 1;
+    const int cap = device_sms() * 16;
     if (g.plane <= 4096) {
         const int blocks = (nk + 7) / 8;
-        adj_planes_warp_kernel<real><<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, s>>>(g, F, nc,
-                                                                                                      near);
+        adj_planes_warp_kernel<real><<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(g, F, nc, near);
     } else {
-        adj_planes_kernel<real><<<(unsigned)(nk < 152 * 16 ? nk : 152 * 16), 128, 0, s>>>(g, F, nc, near);
+        adj_planes_kernel<real><<<(unsigned)(nk < cap ? nk : cap), 128, 0, s>>>(g, F, nc, near);
     }
 }
 

@@ -727,12 +727,40 @@ static void launch_march_batch(const void *args, const int64_t *start, int n, in
 // or wrapped by the copy's z coordinate (periodic).  The x-y passes are the
 // binomial stencil of width 2H + 1 taken separably (x over the widened rows
 // into shared memory, then y), the z passes are those of
-// filter_march_kernel.  A stage whose copy does not land within the wait
-// budget stops the CTA and records ERR_TIMEOUT.
+// filter_march_kernel.  The x pass works on 16-byte groups of consecutive
+// outputs (their inputs read as 16-byte vectors); the z levels sit in a ring
+// of three register slots, the march unrolled by three so that the slot of
+// each plane is a compile-time index and no value is moved between planes.
+// A stage whose copy does not land within the wait budget stops the CTA and
+// records ERR_TIMEOUT.
 constexpr int kFilterStages = 4;
 
+template <typename real> struct Vec16;
+template <> struct Vec16<float> { using type = float4; };
+template <> struct Vec16<double> { using type = double2; };
+__device__ __forceinline__ void unpack16(const float4 &t, float *o)
+{
+    o[0] = t.x;
+    o[1] = t.y;
+    o[2] = t.z;
+    o[3] = t.w;
+}
+__device__ __forceinline__ void unpack16(const double2 &t, double *o)
+{
+    o[0] = t.x;
+    o[1] = t.y;
+}
+__device__ __forceinline__ float4 pack16(const float *o) { return make_float4(o[0], o[1], o[2], o[3]); }
+__device__ __forceinline__ double2 pack16(const double *o) { return make_double2(o[0], o[1]); }
+template <int N> struct Slot { static constexpr int value = N; };
+
+// CTAs per SM the register budget allows without spills
+template <typename real, int H> struct FilterTmaBlocks {
+    static constexpr int value = sizeof(real) == 4 ? (H <= 2 ? 4 : 3) : (H <= 2 ? 3 : 2);
+};
+
 template <typename real, int H>
-__global__ void __launch_bounds__(256) filter_tma_kernel(const __grid_constant__ CUtensorMap map, Geom g,
+__global__ void __launch_bounds__(256, (FilterTmaBlocks<real, H>::value)) filter_tma_kernel(const __grid_constant__ CUtensorMap map, Geom g,
                                                          const real *in, real *out, int cz, int nchunks,
                                                          unsigned *err)
 {
@@ -743,7 +771,13 @@ __global__ void __launch_bounds__(256) filter_tma_kernel(const __grid_constant__
     // boundary: stages are kStride elements apart, the base is rounded up
     constexpr int kStride = (int)(((kBytes + 127u) / 128u) * 128u / sizeof(real));
     constexpr int XR = BY * TX;                  // x-filtered values per component
-    constexpr int NXP = (3 * XR + 255) / 256;    // of them per thread
+    // x-pass groups: VW consecutive outputs of one row, from the VW + 8
+    // inputs starting at the group's own column (16-byte aligned: stages,
+    // components and rows all start on 16-byte boundaries)
+    constexpr int VW = 16 / (int)sizeof(real), NV = (VW + 8) / VW, GR = TX / VW;
+    constexpr int XG = 3 * BY * GR, NXG = (XG + 255) / 256;
+    static_assert(TX % VW == 0 && BX % VW == 0 && H <= 4, "x-pass groups");
+    using vec_t = typename Vec16<real>::type;
     constexpr int NP = (3 * PN + 255) / 256;     // box nodes per thread (periodic images)
     extern __shared__ __align__(128) unsigned char smem_tma[];
     real *stage = reinterpret_cast<real *>(smem_tma + ((128u - (smem_addr(smem_tma) & 127u)) & 127u));
@@ -808,13 +842,17 @@ __global__ void __launch_bounds__(256) filter_tma_kernel(const __grid_constant__
     if (tid == 0)
         for (int q = 0; q < NS && q < np; ++q) issue(q);
     if (pmask) patch_load(kf);
+    // z levels: level p taken at march plane k (its value belongs to plane
+    // k - p) sits in slot (k - kf) % 3
     real lev[3][H + 1][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int p = 0; p <= H; ++p) lev[c][p][0] = lev[c][p][1] = lev[c][p][2] = real(0);
-    int q = 0;
-    for (; q < np; ++q) {
+    // one plane of the march; false once a copy has not landed (the CTA
+    // stops together)
+    auto plane = [&](const int q, auto slot) -> bool {
+        constexpr int PH = decltype(slot)::value, P1 = (PH + 1) % 3, P2 = (PH + 2) % 3;  // planes q, q-2, q-1
         const int k = kf + q;
         real *S = stage + (size_t)(q % NS) * kStride;
         const bool ok = mbar_wait(&bar[q % NS], (uint32_t)(q / NS) & 1u, global_ns(), kWaitBudgetNs);
@@ -829,18 +867,26 @@ __global__ void __launch_bounds__(256) filter_tma_kernel(const __grid_constant__
                 if (q + 1 < np) patch_load(k + 1);  // in flight while this plane is filtered
             }
         }
-        if (__syncthreads_or(!ok)) break;  // the CTA stops together
+        if (__syncthreads_or(!ok)) return false;
         // x passes over the widened rows
 #pragma unroll
-        for (int n = 0; n < NXP; ++n) {
-            const int idx = tid + 256 * n;
-            if (idx < 3 * XR) {
-                const int c = idx / XR, rr = idx - c * XR, row = rr / TX, col = rr - row * TX;
-                const real *A = S + c * PN + row * BX + col + XO;
-                real v = 0;
+        for (int n = 0; n < NXG; ++n) {
+            const int gi = tid + 256 * n;
+            if (gi < XG) {
+                const int c = gi / (BY * GR), rr = gi - c * (BY * GR), row = rr / GR, cv = rr - row * GR;
+                const vec_t *A = reinterpret_cast<const vec_t *>(S + c * PN + row * BX + cv * VW);
+                real in[NV * VW];
 #pragma unroll
-                for (int i = 0; i < W; ++i) v += wb[i] * A[i];
-                xs[idx] = v;
+                for (int m = 0; m < NV; ++m) unpack16(A[m], in + m * VW);
+                real o[VW];
+#pragma unroll
+                for (int j = 0; j < VW; ++j) {
+                    real v = 0;
+#pragma unroll
+                    for (int i = 0; i < W; ++i) v += wb[i] * in[j + XO + i];
+                    o[j] = v;
+                }
+                *reinterpret_cast<vec_t *>(xs + c * XR + row * TX + cv * VW) = pack16(o);
             }
         }
         __syncthreads();  // the stage is consumed: refill it while the y and z passes run
@@ -858,18 +904,26 @@ __global__ void __launch_bounds__(256) filter_tma_kernel(const __grid_constant__
             for (int j = 0; j < W; ++j) v += wb[j] * X[j * TX];
 #pragma unroll
             for (int p = 0; p <= H; ++p) {
-                lev[c][p][0] = lev[c][p][1];
-                lev[c][p][1] = lev[c][p][2];
                 const int kc = k - p;
                 const bool in_range = per || (kc >= 0 && kc <= zmax);
                 const real nv = p == 0 ? v
-                                       : real(0.25) * lev[c][p - 1][0] + real(0.5) * lev[c][p - 1][1] +
-                                             real(0.25) * lev[c][p - 1][2];
-                lev[c][p][2] = in_range ? nv : real(0);
+                                       : real(0.25) * lev[c][p - 1][P1] + real(0.5) * lev[c][p - 1][P2] +
+                                             real(0.25) * lev[c][p - 1][PH];
+                lev[c][p][PH] = in_range ? nv : real(0);
             }
             if (own && ko >= z0 && ko < z1)
-                out[(size_t)c * g.ncomp + (int64_t)ko * g.plane + oown] = ko > zmax ? real(0) : lev[c][H][2];
+                out[(size_t)c * g.ncomp + (int64_t)ko * g.plane + oown] = ko > zmax ? real(0) : lev[c][H][PH];
         }
+        return true;
+    };
+    int q = 0;
+    while (q < np) {
+        if (!plane(q, Slot<0>())) break;
+        if (++q >= np) break;
+        if (!plane(q, Slot<1>())) break;
+        if (++q >= np) break;
+        if (!plane(q, Slot<2>())) break;
+        ++q;
     }
     if (q < np) {
         // a copy did not land: record it, then give the copies still in
@@ -896,7 +950,7 @@ static bool launch_filter_tma(const Geom &g, const real *in, real *out, unsigned
     const int nzo = g.nz + 1;
     const unsigned nb = (unsigned)(((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY));
     // z chunks of 8..64 planes, as long as there are about eight CTAs per SM
-    int64_t czl = (int64_t)nzo * nb / (152 * 8);
+    int64_t czl = (int64_t)nzo * nb / ((int64_t)device_sms() * 8);
     czl = czl < 8 ? 8 : (czl > 64 ? 64 : czl);
     const int cz = (int)(czl < nzo ? czl : nzo);
     const int nchunks = nzo / cz > 0 ? nzo / cz : 1;

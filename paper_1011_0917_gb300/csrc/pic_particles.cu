@@ -158,7 +158,7 @@ void launch_bucket(const BucketArgs<real> &a, cudaStream_t s)
 {
     if (a.n <= 0) return;
     int64_t blocks = (a.n + 255) / 256;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks > (int64_t)device_sms() * 64) blocks = (int64_t)device_sms() * 64;
     bucket_kernel<real><<<(unsigned)blocks, 256, 0, s>>>(a);
 }
 
