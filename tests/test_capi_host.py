@@ -37,6 +37,12 @@ def test_library_exports_every_declared_symbol(P):
     assert not missing, missing
 
 
+def test_binding_names_every_declared_call(P):
+    # the Python binding carries each C-ABI call under the same name
+    missing = [n for n in declared_functions() if not callable(getattr(P, n, None))]
+    assert not missing, missing
+
+
 def test_library_targets_sm_103a(P):
     # the build line passes exactly one -gencode for compute_103a / sm_103a
     from paper_1011_0917_gb300 import build
