@@ -10,6 +10,8 @@ Closed forms and invariants used:
   density gamma n and every electron the Lorentz factor gamma: kinetic energy
   (gamma - 1) gamma n V, net charge 0 with its drifting ions; in the lab
   frame its charge is -n times the volume it fills;
+* a compensated sum keeps terms below half an ulp of the running total that a
+  plain running sum drops (one unit term followed by many of 1e-17);
 * energy moves between the electrons and the field in a plasma oscillation:
   the field energy at the turning point equals the initial kinetic energy
   (this fixes the relative normalisation of the two sums);
@@ -77,6 +79,25 @@ def test_kinetic_energy_and_charge_of_a_cold_plasma(oracle_mod, gam):
         assert abs(d["kinetic_energy"] - expect_ke) <= 1e-12 * expect_ke, (d, expect_ke)
         assert abs(d["charge"]) <= 1e-12 * n_boost * V   # electrons and their drifting ions
         assert o.num(0) == o.num(1) == 2 * 2 * o.grid.nx * o.grid.nz
+
+
+def test_field_energy_sum_is_compensated(oracle_mod):
+    # one node of unit field first in storage order, every other valid node a
+    # value whose square is below half an ulp of 1: a plain running sum stays
+    # at exactly 1, the compensated sum keeps all N - 1 small terms
+    O = oracle_mod
+    nx, nz = 128, 256
+    o = O.Oracle(O.GridParams(dim=2, nx=nx, nz=nz, dx=0.5, dz=0.25, bc_z=1))
+    v = math.sqrt(1e-17)
+    for c in COMPS:
+        o.field(c)[...] = v
+    o.field("Ex")[0, 0, 0] = 1.0
+    n_small = sum(_planes(c, nz, 1) * nx for c in COMPS) - 1
+    V = o.hx * o.hz
+    expect = 0.5 * V * (1.0 + n_small * (v * v))
+    got = o.diagnostics()["field_energy"]
+    assert n_small * v * v > 1e-12                       # far above the sum's own rounding
+    assert abs(got - expect) <= 1e-14 * expect, (got, expect, 0.5 * V)
 
 
 def test_energy_moves_between_electrons_and_field(oracle_mod):

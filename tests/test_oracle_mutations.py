@@ -1,0 +1,218 @@
+"""Planted mistakes in the oracle, each caught by its pins.
+
+Each case copies oracle/pic_oracle.c, replaces one snippet of it (a wrong
+sign, factor, index or constant, a dropped term, a step taken a step late),
+compiles the copy with the oracle's own flags and runs the listed pin tests
+of tests/test_oracle_*.py against it: at least one of them must fail.  The
+unplanted oracle passes the same pins in those files.  This is the check
+that the pins constrain every routine of the oracle, not only its shape."""
+import importlib.util
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ORACLE = os.path.join(ROOT, "oracle")
+TESTS = os.path.dirname(os.path.abspath(__file__))
+
+# (what the mistake is, the text in pic_oracle.c, its replacement,
+#  the pins that must catch it: (file, test function, parameters))
+CASES = [
+    ("SplitMix64: first xor-shift by 31 instead of 30",
+     "z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;", "z = (z ^ (z >> 31)) * 0xBF58476D1CE4E5B9ull;",
+     [("test_oracle_basics", "test_splitmix64_published_vector", {})]),
+    ("linear shape: 1 - d^2 instead of 1 - |d|",
+     "return a < 1.0 ? 1.0 - a : 0.0;", "return a < 1.0 ? 1.0 - a * a : 0.0;",
+     [("test_oracle_basics", "test_shape_partition_of_unity_and_moments", {"order": 1})]),
+    ("quadratic shape: centre piece 3/4 - d^2/2",
+     "return 0.75 - a * a;", "return 0.75 - 0.5 * a * a;",
+     [("test_oracle_basics", "test_shape_partition_of_unity_and_moments", {"order": 2})]),
+    ("density profile: cos(2 m pi zeta)",
+     "cos((double)m * PI_ * zeta)", "cos((double)m * TWO_PI * zeta)",
+     [("test_oracle_basics", "test_density_profile", {})]),
+    ("gather: Ex at integer x",
+     "{0.5, 0.0, 0.0}, /* Ex (i+1/2, j,     k    ) */", "{0.0, 0.0, 0.0}, /* Ex */",
+     [("test_oracle_basics", "test_gather_reproduces_linear_fields", {"dim": 2, "order": 1})]),
+    ("gather: support starting one node too low (the top node of the quadratic shape lost)",
+     "const int64_t bx = (int64_t)floor(xi) - 1, bz = (int64_t)floor(zi) - 1;\n    const int zmax",
+     "const int64_t bx = (int64_t)floor(xi) - 2, bz = (int64_t)floor(zi) - 1;\n    const int zmax",
+     [("test_oracle_basics", "test_gather_reproduces_linear_fields", {"dim": 2, "order": 2})]),
+    ("Boris: full instead of half electric impulse",
+     "const double eps = PI_ * q_over_m * dt;", "const double eps = TWO_PI * q_over_m * dt;",
+     [("test_oracle_particles", "test_boris_uniform_e", {}),
+      ("test_oracle_particles", "test_boris_uniform_b_rotation", {})]),
+    ("Boris: sign of one component of u- x t",
+     "up[0] = um[0] + (um[1] * t[2] - um[2] * t[1]);", "up[0] = um[0] - (um[1] * t[2] - um[2] * t[1]);",
+     [("test_oracle_particles", "test_boris_uniform_b_rotation", {})]),
+    ("Boris: s = t / (1 + t^2) (factor 2 dropped)",
+     "sv[d] = 2.0 * t[d] / (1.0 + t2);", "sv[d] = t[d] / (1.0 + t2);",
+     [("test_oracle_particles", "test_boris_uniform_b_rotation", {})]),
+    ("Boris: t without the Lorentz factor",
+     "t[d] = eps * b[d] / gm;", "t[d] = eps * b[d];",
+     [("test_oracle_particles", "test_boris_uniform_b_rotation", {}),
+      ("test_oracle_particles", "test_boris_orbit_radius_through_step", {})]),
+    ("Esirkepov 3D: DSy DSz / 2 instead of / 3 in Wx",
+     "0.5 * S0[1][b] * DS[2][c] + DS[1][b] * DS[2][c] / 3.0);",
+     "0.5 * S0[1][b] * DS[2][c] + DS[1][b] * DS[2][c] / 2.0);",
+     [("test_oracle_particles", "test_esirkepov_continuity_and_total_current", {"dim": 3, "order": 1})]),
+    ("Esirkepov 2D: Jz weight S0x + DSx (half dropped)",
+     "acc += DS[2][c] * (S0[0][a] + 0.5 * DS[0][a]);", "acc += DS[2][c] * (S0[0][a] + DS[0][a]);",
+     [("test_oracle_particles", "test_esirkepov_continuity_and_total_current", {"dim": 2, "order": 1})]),
+    ("Esirkepov: sign of the z current factor",
+     "const double cz = -qw * s->hz / (s->dt * vol);", "const double cz = qw * s->hz / (s->dt * vol);",
+     [("test_oracle_particles", "test_esirkepov_continuity_and_total_current", {"dim": 2, "order": 1})]),
+    ("electron push: force of a positive charge",
+     "opic_boris(u, eb, eb + 3, -1.0, s->dt);", "opic_boris(u, eb, eb + 3, 1.0, s->dt);",
+     [("test_oracle_physics", "test_cold_plasma_oscillation", {})]),
+    ("electron push: deposit with the ion's sign",
+     "opic_deposit_current(s, -p->a[OPIC_PW][n], x0, x1, u[1] / g);",
+     "opic_deposit_current(s, p->a[OPIC_PW][n], x0, x1, u[1] / g);",
+     [("test_oracle_physics", "test_cold_plasma_oscillation", {}),
+      ("test_oracle_physics", "test_continuity_through_the_loop", {"dim": 2, "order": 1, "npass": 1})]),
+    ("filter: weights (1/4, 1/2, 1/2)",
+     "0.25 * lo + 0.5 * tmp[fidx(s, i, j, k)] + 0.25 * hi;", "0.25 * lo + 0.5 * tmp[fidx(s, i, j, k)] + 0.5 * hi;",
+     [("test_oracle_fields", "test_filter_transfer_function", {})]),
+    ("filter: absorbing z end mirrored instead of zero",
+     "lo = k > 0 ? tmp[fidx(s, i, j, k - 1)] : 0.0;", "lo = k > 0 ? tmp[fidx(s, i, j, k - 1)] : tmp[fidx(s, i, j, k)];",
+     [("test_oracle_fields", "test_filter_absorbing_z_boundary_and_dc", {})]),
+    ("filter: y passes skipped in 3D",
+     "if (ax == 1 && s->g.dim != 3)", "if (ax == 1)",
+     [("test_oracle_fields", "test_filter_transfer_function", {}),
+      ("test_oracle_physics", "test_continuity_through_the_loop", {"dim": 3, "order": 1, "npass": 1})]),
+    ("Yee: sign of dEy/dz in the Bx update",
+     "Bx[o] -= h * (dEz_dy - dEy_dz);", "Bx[o] -= h * (dEz_dy + dEy_dz);",
+     [("test_oracle_fields", "test_yee_discrete_eigenmode", {"dim": 3, "pol": "A"}),
+      ("test_oracle_fields", "test_yee_discrete_eigenmode", {"dim": 3, "pol": "B"}),
+      ("test_oracle_fields", "test_yee_discrete_eigenmode", {"dim": 2, "pol": "TE"}),
+      ("test_oracle_fields", "test_yee_discrete_eigenmode", {"dim": 2, "pol": "TM"})]),
+    ("Yee: current term pi J instead of 2 pi J in Ez",
+     "Ez[o] += dt * ((dBy_dx - dBx_dy) - TWO_PI * Jz[o]);", "Ez[o] += dt * ((dBy_dx - dBx_dy) - PI_ * Jz[o]);",
+     [("test_oracle_physics", "test_cold_plasma_oscillation", {}),
+      ("test_oracle_physics", "test_continuity_through_the_loop", {"dim": 2, "order": 1, "npass": 1})]),
+    ("Yee: dBz/dx taken forward instead of backward in Ey",
+     "double dBz_dx = (Bz[o] - Bz[fidx(s, im, j, k)]) / s->hx;",
+     "double dBz_dx = (Bz[fidx(s, (i + 1) % nx, j, k)] - Bz[o]) / s->hx;",
+     [("test_oracle_fields", "test_yee_discrete_eigenmode", {"dim": 2, "pol": "TE"}),
+      ("test_oracle_fields", "test_yee_discrete_eigenmode", {"dim": 2, "pol": "TM"})]),
+    ("Yee: full instead of half B steps",
+     "        yee_b(s, 0.5 * s->dt);\n        yee_e(s);\n        yee_b(s, 0.5 * s->dt);",
+     "        yee_b(s, s->dt);\n        yee_e(s);\n        yee_b(s, 0.5 * s->dt);",
+     [("test_oracle_fields", "test_yee_discrete_eigenmode", {"dim": 2, "pol": "TE"}),
+      ("test_oracle_fields", "test_yee_discrete_eigenmode", {"dim": 2, "pol": "TM"})]),
+    ("Mur: coefficient of the wrong sign",
+     "const double cm = (dt - s->hz) / (dt + s->hz);", "const double cm = (s->hz - dt) / (dt + s->hz);",
+     [("test_oracle_fields", "test_mur_absorbs_normal_pulse", {"pol": 0}),
+      ("test_oracle_fields", "test_mur_absorbs_normal_pulse", {"pol": 1})]),
+    ("antenna: sheet current 1/(2 pi hz)",
+     "const double j0 = -amp / (PI_ * s->hz);", "const double j0 = -amp / (TWO_PI * s->hz);",
+     [("test_oracle_fields", "test_antenna_amplitude_and_carrier", {})]),
+    ("antenna: no Doppler factor in the boosted frame",
+     "const double D = 1.0 / (s->gam * (1.0 + s->beta));", "const double D = 1.0;",
+     [("test_oracle_physics", "test_boosted_antenna_doppler", {})]),
+    ("antenna: waist taken as exp(-r^2 / (2 w0^2))",
+     "exp(-r2 / (l->waist * l->waist))", "exp(-r2 / (2.0 * l->waist * l->waist))",
+     [("test_oracle_fields", "test_antenna_beam_has_the_waist", {"pol": 0}),
+      ("test_oracle_fields", "test_antenna_beam_has_the_waist", {"pol": 1})]),
+    ("boosted load: weight without the density's factor gamma",
+     "const double wfac = s->gam * vol / (double)(ppx * ppy * ppz);",
+     "const double wfac = vol / (double)(ppx * ppy * ppz);",
+     [("test_oracle_physics", "test_boosted_load_density_and_contraction", {})]),
+    ("boosted load: lab z not contracted",
+     "const double zb = zlab / s->gam - s->beta * s->t - opic_window(s);",
+     "const double zb = zlab - s->beta * s->t - opic_window(s);",
+     [("test_oracle_physics", "test_boosted_load_density_and_contraction", {})]),
+    ("injection: plasma entering a step late",
+     "static void inject(opic *s) { inject_at(s, s->t + s->dt); }",
+     "static void inject(opic *s) { inject_at(s, s->t); }",
+     [("test_oracle_physics", "test_boosted_injection_flux_and_positions", {}),
+      ("test_oracle_physics", "test_injected_plasma_matches_free_drift", {})]),
+    ("snapshots: event time gamma (T + beta Z)",
+     "const double tp = gam * (T - beta * Z);", "const double tp = gam * (T + beta * Z);",
+     [("test_oracle_btd", "test_snapshot_coverage", {}),
+      ("test_oracle_btd", "test_lab_and_boosted_runs_of_one_pulse_agree", {})]),
+    ("snapshots: Ex = gamma (Ex' - beta By')",
+     "const double lab[6] = {gam * (e[0] + beta * e[4])", "const double lab[6] = {gam * (e[0] - beta * e[4])",
+     [("test_oracle_btd", "test_static_fields_seen_from_the_lab", {"e": (0.0, 0.0, 0.0), "b": (0.4, 0.9, -0.2)}),
+      ("test_oracle_btd", "test_lab_and_boosted_runs_of_one_pulse_agree", {})]),
+    ("diagnostics: field energy without the 1/2",
+     "out[0] = 0.5 * vol * fe.s;", "out[0] = vol * fe.s;",
+     [("test_oracle_diagnostics", "test_field_energy_of_modes_and_uniform_fields", {"dim": 2, "bc_z": 1})]),
+    ("diagnostics: u^2 / gamma instead of gamma - 1",
+     "(u2 / (sqrt(1.0 + u2) + 1.0))", "(u2 / sqrt(1.0 + u2))",
+     [("test_oracle_diagnostics", "test_kinetic_energy_and_charge_of_a_cold_plasma", {"gam": 13.0})]),
+    ("diagnostics: plain instead of compensated sum",
+     "k->c = (t - k->s) - y;", "k->c = 0.0;",
+     [("test_oracle_diagnostics", "test_field_energy_sum_is_compensated", {})]),
+    ("lab view: By = gamma (By' - beta Ex')",
+     "case OPIC_BY: v = gam * (s->f[OPIC_BY][o] + beta", "case OPIC_BY: v = gam * (s->f[OPIC_BY][o] - beta",
+     [("test_oracle_diagnostics", "test_lab_fields_of_uniform_fields", {"gam": 3.0})]),
+    ("moving window: fields shifted by S - 1 planes",
+     "f[k * plane + o] = k + S <= s->g.nz ? f[(k + S) * plane + o] : 0.0;",
+     "f[k * plane + o] = k + S <= s->g.nz ? f[(k + S - 1) * plane + o] : 0.0;",
+     [("test_oracle_window", "test_pulse_in_window_matches_long_box", {})]),
+]
+
+
+def _module(name: str, path: str):
+    # a fresh instance of a module file (registered, as dataclasses need)
+    spec = importlib.util.spec_from_file_location(name, path)
+    mod = importlib.util.module_from_spec(spec)
+    sys.modules[name] = mod
+    spec.loader.exec_module(mod)
+    return mod
+
+
+@pytest.fixture(scope="module")
+def source():
+    with open(os.path.join(ORACLE, "pic_oracle.c")) as f:
+        return f.read()
+
+
+def test_every_planted_text_occurs_once(source):
+    for what, old, new, pins in CASES:
+        assert source.count(old) == 1, what
+        assert old != new and pins, what
+
+
+def _run_pins(source: str, tmp_path, tag: str, pins) -> list:
+    """Compile `source` as the oracle, run the pins against it and return
+    the names of those that failed."""
+    src = tmp_path / "pic_oracle.c"
+    src.write_text(source)
+    so = str(tmp_path / "liboracle_planted.so")
+    # the oracle's own flags (oracle.build_oracle)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                    "-I", ORACLE, "-o", so, str(src), "-lm"], check=True)
+    O = _module(f"oracle_planted_{tag}", os.path.join(ORACLE, "oracle.py"))
+    O.build_oracle = lambda force=False: so
+    failed = []
+    for fname, test, params in pins:
+        fn = getattr(_module(f"pins_{fname}_{tag}", os.path.join(TESTS, fname + ".py")), test)
+        try:
+            fn(O, **params)
+        except (AssertionError, ArithmeticError, ValueError):
+            # a failed check, or arithmetic the pin cannot even complete
+            failed.append(test)
+    # the pins ran on the compiled copy, not on the oracle's own build
+    assert O._lib is not None and O._lib._name == so
+    return failed
+
+
+def test_unplanted_copy_passes_every_pin(source, tmp_path):
+    # the same harness on an unchanged copy: every pin used below passes
+    pins, seen = [], set()
+    for _, _, _, ps in CASES:
+        for fname, test, params in ps:
+            key = (fname, test, tuple(sorted(params.items())))
+            if key not in seen:
+                seen.add(key)
+                pins.append((fname, test, params))
+    assert _run_pins(source + "\n/* unchanged */\n", tmp_path, "control", pins) == []
+
+
+@pytest.mark.parametrize("case", range(len(CASES)), ids=[c[0] for c in CASES])
+def test_planted_mistake_fails_a_pin(source, tmp_path, case):
+    what, old, new, pins = CASES[case]
+    assert _run_pins(source.replace(old, new, 1), tmp_path, str(case), pins), f"no pin caught: {what}"
