@@ -152,6 +152,64 @@ CASES = [
      "f[k * plane + o] = k + S <= s->g.nz ? f[(k + S) * plane + o] : 0.0;",
      "f[k * plane + o] = k + S <= s->g.nz ? f[(k + S - 1) * plane + o] : 0.0;",
      [("test_oracle_window", "test_pulse_in_window_matches_long_box", {})]),
+    ("ion push: deposit with the electron's sign",
+     "opic_deposit_current(s, p->a[OPIC_PW][n], x0, x1, u[1] / g);",
+     "opic_deposit_current(s, -p->a[OPIC_PW][n], x0, x1, u[1] / g);",
+     [("test_oracle_physics", "test_boosted_plasma_without_laser_stays_field_free", {})]),
+    ("ion push: half the drift per step",
+     "x1[2] = x0[2] + s->dt * u[2] / g;\n        opic_deposit_current(s, p->a",
+     "x1[2] = x0[2] + 0.5 * s->dt * u[2] / g;\n        opic_deposit_current(s, p->a",
+     [("test_oracle_physics", "test_boosted_plasma_without_laser_stays_field_free", {})]),
+    ("injection: the ions of the entering plasma left out",
+     "            if (s->has_ions)\n                species_push(&s->sp[1], q->x, q->y, zb, 0.0, 0.0, uz0, q->w, q->id);\n",
+     "",
+     [("test_oracle_physics", "test_boosted_injection_flux_and_positions", {}),
+      ("test_oracle_physics", "test_boosted_plasma_without_laser_stays_field_free", {})]),
+    ("lattice jitter: U(0, J) instead of U(-J, J) in x",
+     "(p->jitter * s->hx) * (2.0 * opic_uniform(s->g.seed, c0) - 1.0)",
+     "(p->jitter * s->hx) * opic_uniform(s->g.seed, c0)",
+     [("test_oracle_physics", "test_lattice_jitter_is_symmetric_and_bounded", {})]),
+    ("density ramp: half its slope",
+     "r = (z - p->z_start) / p->ramp;", "r = 0.5 * (z - p->z_start) / p->ramp;",
+     [("test_oracle_basics", "test_density_profile", {})]),
+    ("boosted frame: cells stretched by gamma instead of gamma (1 + beta)",
+     "s->hz = g->dz * (s->gam * (1.0 + s->beta));", "s->hz = g->dz * s->gam;",
+     [("test_oracle_physics", "test_boosted_load_density_and_contraction", {}),
+      ("test_oracle_physics", "test_boosted_antenna_doppler", {})]),
+    ("time step in 3D without the y cell",
+     "s->dt = g->cfl / sqrt(1.0 / (s->hx * s->hx) + 1.0 / (s->hy * s->hy) + 1.0 / (s->hz * s->hz));",
+     "s->dt = g->cfl / sqrt(1.0 / (s->hx * s->hx) + 1.0 / (s->hz * s->hz));",
+     [("test_oracle_fields", "test_yee_discrete_eigenmode", {"dim": 3, "pol": "A"}),
+      ("test_oracle_fields", "test_yee_discrete_eigenmode", {"dim": 3, "pol": "B"})]),
+    ("Boris: second half of the electric impulse dropped",
+     "u[d] = upl[d] + eps * e[d];", "u[d] = upl[d];",
+     [("test_oracle_particles", "test_boris_uniform_e", {})]),
+    ("Esirkepov: window starting at the lower cell instead of one below",
+     "lo[d] = (int64_t)floor(a < b ? a : b) - 1;", "lo[d] = (int64_t)floor(a < b ? a : b);",
+     [("test_oracle_particles", "test_esirkepov_continuity_and_total_current", {"dim": 2, "order": 2})]),
+    ("Esirkepov 2D: out-of-plane current without 1/V",
+     "const double cyv = qw * vy / vol;", "const double cyv = qw * vy;",
+     [("test_oracle_particles", "test_esirkepov_continuity_and_total_current", {"dim": 2, "order": 1})]),
+    ("charge density without 1/V",
+     "const double qw = q * p->a[OPIC_PW][n] / vol;", "const double qw = q * p->a[OPIC_PW][n];",
+     [("test_oracle_physics", "test_continuity_through_the_loop", {"dim": 2, "order": 1, "npass": 1})]),
+    ("valid z planes: half-integer components given the top plane too",
+     "return sz > 0.0 ? s->g.nz - 1 : s->g.nz;", "return s->g.nz;",
+     [("test_oracle_fields", "test_filter_absorbing_z_boundary_and_dc", {}),
+      ("test_oracle_diagnostics", "test_field_energy_of_modes_and_uniform_fields", {"dim": 2, "bc_z": 1})]),
+    ("antenna: Jx sheet at integer x",
+     "const double sx = l->pol == 0 ? 0.5 : 0.0;", "const double sx = 0.0;",
+     [("test_oracle_fields", "test_antenna_beam_has_the_waist", {"pol": 0})]),
+    ("lab view: partner taken from one plane instead of the mean of two",
+     "return 0.5 * (f[fidx(s, i, j, a)] + f[fidx(s, i, j, b)]);", "return f[fidx(s, i, j, b)];",
+     [("test_oracle_diagnostics", "test_lab_fields_pair_each_component_with_its_staggered_partner", {})]),
+    ("snapshots: z interpolation weights swapped",
+     "*out = (1.0 - fz) * f[fidx(s, i, j, k)] + fz * f[fidx(s, i, j, k + 1)];",
+     "*out = fz * f[fidx(s, i, j, k)] + (1.0 - fz) * f[fidx(s, i, j, k + 1)];",
+     [("test_oracle_btd", "test_lab_and_boosted_runs_of_one_pulse_agree", {})]),
+    ("moving window: particles shifted one cell short",
+     "p->a[OPIC_PZ][k] -= dz;", "p->a[OPIC_PZ][k] -= dz - s->hz;",
+     [("test_oracle_window", "test_static_plasma_through_window_is_the_lattice", {})]),
 ]
 
 

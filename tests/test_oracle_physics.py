@@ -11,7 +11,11 @@ Closed forms / invariants used:
 * 1D linear quasi-static wake of a Gaussian pulse (oracle.units);
 * a plasma at rest in the lab is seen in the boosted frame with density
   gamma n, drift -beta, contracted length L / gamma, and enters the box at
-  z' = z_lab / gamma - beta t.
+  z' = z_lab / gamma - beta t;
+* electrons and ions on the same paths carry no net current: a boosted
+  plasma without a laser stays field-free;
+* the lattice jitter U(-J, J) per axis is bounded by J, reaches it on both
+  sides and has mean zero.
 """
 import math
 
@@ -268,3 +272,41 @@ def test_boosted_antenna_doppler(oracle_mod):
     core = slice(int((t[i0] - tau / D) / o.dt), int((t[i0] + tau / D) / o.dt))
     slope = np.polyfit(t[core], ph[core], 1)[0]
     assert abs(slope / (2 * math.pi) - D) / D < 2e-3
+
+
+def test_boosted_plasma_without_laser_stays_field_free(oracle_mod):
+    # electrons and their drifting ions start at the same lattice points with
+    # the same velocity, enter together and leave together: their currents
+    # cancel to round-off on every node and no field grows, through full
+    # steps with the filter, Yee, Mur and injection
+    G, P = oracle_mod.GridParams, oracle_mod.PlasmaParams
+    gam = 5.0
+    o = oracle_mod.Oracle(G(dim=2, nx=8, nz=64, dx=1.0, dz=1.0 / 16, gamma_boost=gam, bc_z=1, npass=1))
+    ne = 0.01
+    o.load_plasma(P(ne=ne, z_start=0.0, z_end=gam * (o.Lz + 10.0), ramp=0.0, ppc=(2, 1, 2), jitter=0.1, ions=1))
+    assert o.pending() > 0
+    j_species = gam * ne * o.beta            # one species' current density
+    n_in = o.num(0)
+    for _ in range(40):
+        o.step(1)
+    assert o.num(0) == o.num(1) and o.num(0) != n_in
+    worst = max(float(np.abs(o.field(c)).max()) for c in ("Ex", "Ey", "Ez", "Bx", "By", "Bz"))
+    # an uncancelled species would drive E ~ 2 pi j t ~ 1 here
+    assert worst < 1e-12 * 2 * math.pi * j_species * o.t, worst
+
+
+def test_lattice_jitter_is_symmetric_and_bounded(oracle_mod):
+    # each lattice point is displaced by U(-J, J) cells per axis: the offsets
+    # from the points fill (-J, J) on both sides with mean zero
+    G, P = oracle_mod.GridParams, oracle_mod.PlasmaParams
+    o = oracle_mod.Oracle(G(dim=3, nx=16, ny=12, nz=24, dx=0.5, dy=0.7, dz=0.25, bc_z=1))
+    J, ppc = 0.1, (2, 2, 2)
+    o.load_plasma(P(ne=0.01, z_start=0.0, z_end=o.Lz, ramp=0.0, ppc=ppc, jitter=J, ions=0))
+    p = o.particles(0)
+    for ax, h, n in (("x", o.hx, ppc[0]), ("y", o.hy, ppc[1]), ("z", o.hz, ppc[2])):
+        u = p[ax] / (h / n) - 0.5                  # in lattice spacings, points at integers
+        off = (u - np.round(u)) / n                # in cells (no point is near enough an edge to wrap)
+        assert np.abs(off).max() <= J * (1 + 1e-12)
+        assert off.max() > 0.95 * J and off.min() < -0.95 * J, (ax, off.min(), off.max())
+        sigma = J / math.sqrt(3.0)
+        assert abs(off.mean()) < 4 * sigma / math.sqrt(off.size), (ax, off.mean())
