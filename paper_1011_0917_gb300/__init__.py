@@ -462,6 +462,10 @@ class Simulation:
         pic_bind_buffers(self.ctx, b)
         self.dtype = torch.float64 if s.elem_bytes == 8 else torch.float32
         self.shape3 = (nz + 1, ny if dim == 3 else 1, nx)
+        # profile coefficients loaded, and those of the adjoint forward run
+        # (the library reports a backward pass without a forward one)
+        self._prof_n = 0
+        self._adj_n = 0
 
     # derived
     @property
