@@ -481,7 +481,9 @@ pic_status pic_adjoint_forward(pic_ctx *ctx, const pic_adjoint_params *p, void *
 
 /* cot: device cotangents lambda_E, lambda_B of E^N, B^N (the layout of
    fields_out).  grad (host, M + 2 doubles): dL/dc_1 .. dL/dc_M, dL/da0,
-   dL/dw0.  PIC_ERR_STATE without a preceding pic_adjoint_forward. */
+   dL/dw0.  PIC_ERR_STATE without a preceding pic_adjoint_forward, or when
+   pic_load_plasma or pic_launch_laser has been called since it (the gradient
+   would belong to another run). */
 pic_status pic_adjoint_backward(pic_ctx *ctx, const void *cot, double *grad);
 
 /* The gradients of every run of a batch (the scan's reverse mode): for run

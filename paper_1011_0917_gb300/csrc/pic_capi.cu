@@ -534,6 +534,7 @@ extern "C" pic_status pic_load_plasma(pic_ctx *c, const pic_plasma_params *p)
         p->n_profile > 16 || (p->n_profile > 0 && !p->profile))
         return fail(c, PIC_ERR_ARG, "invalid plasma parameters");
     c->plasma = *p;
+    c->adj.ready = false;  // an adjoint forward run recorded before this is another run's
     for (int m = 0; m < 16; ++m) c->prof[m] = m < p->n_profile ? p->profile[m] : 0.0;
     c->plasma.profile = c->prof;
     c->plasma_loaded = true;
@@ -671,6 +672,7 @@ extern "C" pic_status pic_launch_laser(pic_ctx *c, const pic_laser_params *p)
         (p->polarization != PIC_POL_X && p->polarization != PIC_POL_Y))
         return fail(c, PIC_ERR_ARG, "invalid laser parameters");
     c->laser = *p;
+    c->adj.ready = false;  // as in pic_load_plasma
     int ka = (int)std::floor(p->z_antenna / c->hz + 0.5);
     if (ka < 2) ka = 2;
     if (ka > c->g.nz - 2) ka = c->g.nz - 2;

@@ -231,6 +231,18 @@ def test_adjoint_validation(P):
         P.pic_destroy(ctx)
 
 
+def test_adjoint_backward_needs_a_forward_run(P):
+    ctx = P.pic_init_grid(grid(P, gamma_boost=5.0, dx=1.0, dz=1 / 32, nx=48, nz=256))
+    try:
+        cot = (C.c_double * 8)()
+        with pytest.raises(P.PicError) as e:
+            P.pic_adjoint_backward(ctx, C.addressof(cot), 2)
+        assert e.value.status == 2
+        assert "pic_adjoint_forward" in P.pic_last_error(ctx)
+    finally:
+        P.pic_destroy(ctx)
+
+
 def test_simulation_refuses_without_a_gpu(P):
     # the product path has no CPU fallback: without a CUDA device it raises
     import torch

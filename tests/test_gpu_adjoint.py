@@ -380,3 +380,19 @@ def test_checkpoint_interval_fits_the_budget(O):
     _, g = gpu_run(O, FP64, K=k)
     _, g1 = gpu_run(O, FP64, K=NSTEPS)
     assert np.allclose(g, g1, rtol=1e-11, atol=0)
+
+
+def test_backward_refused_after_the_run_changed(O):
+    """A new laser (or plasma) after the adjoint's forward run makes its
+    gradient another run's: the backward pass is refused with PIC_ERR_STATE."""
+    import torch
+    import paper_1011_0917_gb300 as P
+    sim, _ = make_pair(O, G, FP64)
+    sim.load_plasma(PLASMA["ne"], PLASMA["z_start"], PLASMA["z_end"], PLASMA["ramp"], PLASMA["ppc"],
+                    PLASMA["jitter"], COEF, 1)
+    sim.launch_laser(LASER["a0"], LASER["waist"], LASER["fwhm"], 0.0, LASER["t_peak"], 1)
+    fields = sim.adjoint_forward(8, 4)
+    sim.launch_laser(LASER["a0"] * 1.5, LASER["waist"], LASER["fwhm"], 0.0, LASER["t_peak"], 1)
+    with pytest.raises(P.PicError) as e:
+        sim.adjoint_backward(torch.zeros_like(fields))
+    assert e.value.status == 2
