@@ -219,6 +219,29 @@ def test_batch_validation(P):
         assert e.value.status == 1
 
 
+def test_cell_order_and_fused_batch_validation(P):
+    # cell sorting needs bound buffers and a non-negative interval; the fused
+    # form of a batch needs a batch and a non-negative chain count
+    ctx = P.pic_init_grid(grid(P))
+    try:
+        with pytest.raises(P.PicError) as e:
+            P.pic_sort_cells(ctx)
+        assert e.value.status == 2 and "bind" in P.pic_last_error(ctx)
+        with pytest.raises(P.PicError) as e:
+            P.pic_set_cell_sort(ctx, -1)
+        assert e.value.status == 1
+        P.pic_set_cell_sort(ctx, 0)
+    finally:
+        P.pic_destroy(ctx)
+    for chains in (2, -1):
+        with pytest.raises(P.PicError) as e:
+            P.pic_batch_set_fused(None, chains)
+        assert e.value.status == 1
+    with pytest.raises(P.PicError) as e:
+        P.pic_batch_graph_info(None)
+    assert e.value.status == 1
+
+
 def test_adjoint_validation(P):
     # the adjoint needs bound buffers, then a loaded plasma and no step taken
     ctx = P.pic_init_grid(grid(P, gamma_boost=5.0, dx=1.0, dz=1 / 32, nx=48, nz=256))
