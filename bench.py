@@ -150,7 +150,7 @@ def measured_peaks():
 def traffic_from_profiles(kernel_key: str):
     """DRAM bytes per launch of the kernel from the committed ncu summary, if
     that summary is for the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "push_kernel_traffic.txt")
+    p = os.path.join(ROOT, "profiles", "push_kernel_traffic_c2_small.txt")
     if not os.path.exists(p):
         return None
     with open(p) as f:
