@@ -376,7 +376,8 @@ pic_status pic_batch_set_fused(pic_batch *batch, int fused);
 
 /* The graph the batch keeps (zeros before the first capture): its launch
    chains if it is the fused form (0: per context), the launches one replay
-   issues (kernels and counter resets) and the steps it covers. */
+   issues (kernels and counter resets) and the steps it covers.  Any output
+   pointer may be NULL; PIC_ERR_ARG for a null batch. */
 pic_status pic_batch_graph_info(pic_batch *batch, int *fused, int64_t *launches_per_replay, int *steps);
 
 /* ---------------------------------------------------------- moving window */
@@ -519,7 +520,8 @@ pic_status pic_set_state(pic_ctx *ctx, const void *src, size_t src_bytes, int sr
    run).  The push writes the particles that stay in their tile in the order
    it read them, so the order decays only by the particles that cross tiles.
    The results of a step do not depend on the order (the deposit sums in
-   exact fixed point).  Synchronises the stream. */
+   exact fixed point).  Synchronises the stream.  PIC_ERR_STATE before
+   pic_bind_buffers; the device error word is checked as after a step. */
 pic_status pic_sort_cells(pic_ctx *ctx);
 
 /* Sort by cell before every `every`-th step (the step count a multiple of
