@@ -210,6 +210,39 @@ CASES = [
     ("moving window: particles shifted one cell short",
      "p->a[OPIC_PZ][k] -= dz;", "p->a[OPIC_PZ][k] -= dz - s->hz;",
      [("test_oracle_window", "test_static_plasma_through_window_is_the_lattice", {})]),
+    ("uniform deviate from 52 instead of 53 bits (values in [0, 1/2))",
+     "return (double)(opic_splitmix64(seed, counter) >> 11) * (1.0 / 9007199254740992.0);",
+     "return (double)(opic_splitmix64(seed, counter) >> 12) * (1.0 / 9007199254740992.0);",
+     [("test_oracle_physics", "test_lattice_jitter_is_symmetric_and_bounded", {})]),
+    ("Mur at the top end: old planes swapped",
+     "Ex[(int64_t)nz * plane + q] = exm + cm * (Ex[(int64_t)(nz - 1) * plane + q] - exn);",
+     "Ex[(int64_t)nz * plane + q] = exn + cm * (Ex[(int64_t)(nz - 1) * plane + q] - exm);",
+     [("test_oracle_fields", "test_mur_absorbs_normal_pulse", {"pol": 0}),
+      ("test_oracle_fields", "test_mur_absorbs_normal_pulse", {"pol": 1})]),
+    ("antenna: sheet evaluated at t^n instead of t^{n+1/2}",
+     "const double th = s->t + 0.5 * s->dt;", "const double th = s->t;",
+     [("test_oracle_fields", "test_antenna_carrier_phase_and_plane", {})]),
+    ("antenna: plane below z_antenna instead of the nearest",
+     "int ka = (int)floor(l->z_antenna / s->hz + 0.5);", "int ka = (int)floor(l->z_antenna / s->hz);",
+     [("test_oracle_fields", "test_antenna_carrier_phase_and_plane", {})]),
+    ("antenna: FWHM read as the field's instead of the intensity's",
+     "const double tau = l->fwhm / sqrt(2.0 * log(2.0));", "const double tau = l->fwhm / (2.0 * sqrt(log(2.0)));",
+     [("test_oracle_fields", "test_antenna_amplitude_and_carrier", {})]),
+    ("Yee 3D: sign of dBx/dy in the Ez update",
+     "double dBx_dy = dim3 ? (Bx[o] - Bx[fidx(s, i, jm, k)]) / s->hy : 0.0;\n                    Ez",
+     "double dBx_dy = dim3 ? (Bx[fidx(s, i, jm, k)] - Bx[o]) / s->hy : 0.0;\n                    Ez",
+     [("test_oracle_fields", "test_yee_discrete_eigenmode", {"dim": 3, "pol": "A"}),
+      ("test_oracle_fields", "test_yee_discrete_eigenmode", {"dim": 3, "pol": "B"})]),
+    ("Esirkepov 3D: DSx S0y / 2 dropped from Wz",
+     "acc += DS[2][c] * (S0[0][a] * S0[1][b] + 0.5 * DS[0][a] * S0[1][b] +",
+     "acc += DS[2][c] * (S0[0][a] * S0[1][b] +",
+     [("test_oracle_particles", "test_esirkepov_continuity_and_total_current", {"dim": 3, "order": 1})]),
+    ("snapshots: Bx = gamma (Bx' + beta Ey')",
+     "gam * (e[3] - beta * e[1])", "gam * (e[3] + beta * e[1])",
+     [("test_oracle_btd", "test_static_fields_seen_from_the_lab", {"e": (0.3, -0.7, 0.25), "b": (0.0, 0.0, 0.0)})]),
+    ("moving window: plasma it moves over placed a step ahead",
+     "    s->win_n += 1;\n    inject_at(s, s->t);", "    s->win_n += 1;\n    inject_at(s, s->t + s->dt);",
+     [("test_oracle_window", "test_boosted_plasma_through_window_matches_long_box", {})]),
 ]
 
 

@@ -4,8 +4,9 @@ hyperbolic rotation in Minkowski space").
 
 What fixes them: a window moving at c over a pulse that travels at c sees the
 same fields as a long fixed box at the same absolute positions (up to the
-pulse's Gaussian tails reaching the window's ends), and a plasma at rest seen
-through the window is the lattice of a long box, point for point.
+pulse's Gaussian tails reaching the window's ends), a plasma at rest seen
+through the window is the lattice of a long box, point for point, and so is
+a boosted plasma drifting through a moving window.
 """
 import numpy as np
 
@@ -54,3 +55,34 @@ def test_static_plasma_through_window_is_the_lattice(oracle_mod):
     assert np.allclose(a["z"][ia] + zw, b["z"][inwin][ib], atol=1e-12, rtol=0)
     assert np.array_equal(a["x"][ia], b["x"][inwin][ib])
     assert np.array_equal(a["w"][ia], b["w"][inwin][ib])
+
+
+def test_boosted_plasma_through_window_matches_long_box(oracle_mod):
+    # a boosted plasma (drifting at -beta, streaming in at the top) seen
+    # through a window moving at +v: every particle the window holds is where
+    # the same lattice particle is in a long fixed box, both the ones that
+    # drifted in through the window's top and the ones the window moved over
+    O = oracle_mod
+    g = dict(dim=2, nx=4, dx=1.0, dz=1 / 16, gamma_boost=5.0, npass=0, bc_z=1)
+    win = O.Oracle(O.GridParams(nz=96, **g))
+    big = O.Oracle(O.GridParams(nz=480, **g))
+    p = O.PlasmaParams(ne=0.01, z_start=0.0, z_end=5.0 * big.Lz * 2, ramp=0.0, ppc=(2, 1, 2), jitter=0.1, ions=1)
+    win.set_window(0.6, 0.5, 8)
+    win.load_plasma(p)
+    big.load_plasma(p)
+    mask = O.PH_PUSH | O.PH_IONS | O.PH_INJECT | O.PH_TIME   # field-free: every particle drifts at -beta
+    for _ in range(int(60.0 / win.dt)):
+        win.step_phases(mask)
+        big.step_phases(mask)
+    zw = win.z_window
+    assert zw >= 5 * 8 * win.hz - 1e-9 and zw + win.Lz < big.Lz   # several moves, inside the long box
+    for sp in (0, 1):
+        a, b = win.particles(sp), big.particles(sp)
+        pos = dict(zip(b["id"].tolist(), b["z"]))
+        assert len(a["id"]) > 1000
+        for pid, z in zip(a["id"].tolist(), a["z"]):
+            assert abs(z + zw - pos[pid]) < 1e-9, (sp, pid, z + zw, pos[pid])
+        # and nothing the long box holds inside the window is missing from it
+        ids = set(a["id"].tolist())
+        inner = (b["z"] > zw + 1e-9) & (b["z"] < zw + win.Lz - 1e-9)
+        assert all(i in ids for i in b["id"][inner].tolist())
