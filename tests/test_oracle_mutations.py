@@ -243,6 +243,36 @@ CASES = [
     ("moving window: plasma it moves over placed a step ahead",
      "    s->win_n += 1;\n    inject_at(s, s->t);", "    s->win_n += 1;\n    inject_at(s, s->t + s->dt);",
      [("test_oracle_window", "test_boosted_plasma_through_window_matches_long_box", {})]),
+    ("electron push: particles past the top end kept",
+     "        } else if (x1[2] < 0.0 || x1[2] >= s->Lz) {\n            species_remove(p, n);\n            continue;\n"
+     "        }\n        p->a[OPIC_PX][n] = x1[0];\n        p->a[OPIC_PY][n] = x1[1];\n        p->a[OPIC_PZ][n] = x1[2];\n"
+     "        ++n;\n    }\n}\n\n/* ions",
+     "        } else if (x1[2] < 0.0) {\n            species_remove(p, n);\n            continue;\n"
+     "        }\n        p->a[OPIC_PX][n] = x1[0];\n        p->a[OPIC_PY][n] = x1[1];\n        p->a[OPIC_PZ][n] = x1[2];\n"
+     "        ++n;\n    }\n}\n\n/* ions",
+     [("test_oracle_particles", "test_particles_leaving_through_absorbing_ends_are_removed", {"sp": 0})]),
+    ("ion move: particles past the bottom end kept",
+     "        } else if (x1[2] < 0.0 || x1[2] >= s->Lz) {\n            species_remove(p, n);\n            continue;\n"
+     "        }\n        p->a[OPIC_PX][n] = x1[0];\n        p->a[OPIC_PY][n] = x1[1];\n        p->a[OPIC_PZ][n] = x1[2];\n"
+     "        ++n;\n    }\n}\n\n/* ------",
+     "        } else if (x1[2] >= s->Lz) {\n            species_remove(p, n);\n            continue;\n"
+     "        }\n        p->a[OPIC_PX][n] = x1[0];\n        p->a[OPIC_PY][n] = x1[1];\n        p->a[OPIC_PZ][n] = x1[2];\n"
+     "        ++n;\n    }\n}\n\n/* ------",
+     [("test_oracle_particles", "test_particles_leaving_through_absorbing_ends_are_removed", {"sp": 1}),
+      ("test_oracle_physics", "test_boosted_plasma_without_laser_stays_field_free", {})]),
+    ("boosted load: ion weight halved",
+     "species_push(&s->sp[1], x, y, zb, 0.0, 0.0, uz0, w, L);", "species_push(&s->sp[1], x, y, zb, 0.0, 0.0, uz0, 0.5 * w, L);",
+     [("test_oracle_physics", "test_boosted_plasma_without_laser_stays_field_free", {}),
+      ("test_oracle_diagnostics", "test_kinetic_energy_and_charge_of_a_cold_plasma", {"gam": 13.0})]),
+    ("lattice points at the cell's corner instead of its centre",
+     "double x = ((double)ix + 0.5) * (s->hx / (double)ppx) +", "double x = ((double)ix) * (s->hx / (double)ppx) +",
+     [("test_oracle_physics", "test_lattice_jitter_is_symmetric_and_bounded", {})]),
+    ("diagnostics: drifting ions counted with the electrons' charge",
+     "kahan_add(&q, ion->a[OPIC_PW][p]);", "kahan_add(&q, -ion->a[OPIC_PW][p]);",
+     [("test_oracle_diagnostics", "test_kinetic_energy_and_charge_of_a_cold_plasma", {"gam": 13.0})]),
+    ("snapshots: no interpolation in time within the step",
+     "const double th = (tp - t0) / s->dt;", "const double th = 0.0;",
+     [("test_oracle_btd", "test_lab_and_boosted_runs_of_one_pulse_agree", {})]),
 ]
 
 

@@ -160,3 +160,27 @@ def test_esirkepov_static_and_one_axis(oracle_mod):
         for (k, wz) in ((1, 0.5), (2, 0.5)):
             assert abs(jx[k, j, 2] - (-1.0) * vx * wy * wz) < 1e-13
     assert np.count_nonzero(o.field("Jy")) == 0 and np.count_nonzero(o.field("Jz")) == 0
+
+
+@pytest.mark.parametrize("sp", [0, 1])
+def test_particles_leaving_through_absorbing_ends_are_removed(oracle_mod, sp):
+    # without fields every particle moves by dt u / gamma; with absorbing z
+    # exactly those whose new z lies outside [0, Lz) leave the store, at
+    # either end, and the others are where the free motion puts them
+    O = oracle_mod
+    o = O.Oracle(O.GridParams(dim=2, nx=4, nz=16, dx=1.0, dz=0.25, bc_z=1, npass=0))
+    rng = np.random.default_rng(5 + sp)
+    n = 400
+    z = np.concatenate([rng.uniform(0, 0.3, n // 2), rng.uniform(o.Lz - 0.3, o.Lz, n // 2)])
+    uz = np.concatenate([rng.uniform(-20, 5, n // 2), rng.uniform(-5, 20, n // 2)])
+    x = rng.uniform(0, o.Lx, n)
+    ids = np.arange(n)
+    o.add_particles(sp, x, 0 * x, z, 0 * x, 0 * x, uz, np.full(n, 1e-3), ids)
+    o.step_phases(O.PH_PUSH if sp == 0 else O.PH_IONS)
+    z1 = z + o.dt * uz / np.sqrt(1 + uz ** 2)
+    stay = (z1 >= 0) & (z1 < o.Lz)
+    assert 0 < stay.sum() < n and (z1 >= o.Lz).any() and (z1 < 0).any()
+    p = o.particles(sp)
+    assert np.array_equal(np.sort(p["id"]), ids[stay])
+    got = dict(zip(p["id"].tolist(), p["z"]))
+    assert max(abs(got[i] - z1[i]) for i in ids[stay]) < 1e-12
