@@ -273,6 +273,19 @@ CASES = [
     ("snapshots: no interpolation in time within the step",
      "const double th = (tp - t0) / s->dt;", "const double th = 0.0;",
      [("test_oracle_btd", "test_lab_and_boosted_runs_of_one_pulse_agree", {})]),
+    ("lab plasma: immobile ions' background with the electrons' sign",
+     "deposit_rho_species(s, &s->sp[0], 1.0, s->rho_bg);", "deposit_rho_species(s, &s->sp[0], -1.0, s->rho_bg);",
+     [("test_oracle_physics", "test_plasma_with_its_ions_is_neutral", {"gam": 1.0})]),
+    ("charge density: drifting ions with the electrons' sign",
+     "        deposit_rho_species(s, &s->sp[1], 1.0, rho);", "        deposit_rho_species(s, &s->sp[1], -1.0, rho);",
+     [("test_oracle_physics", "test_plasma_with_its_ions_is_neutral", {"gam": 5.0})]),
+    ("moving window: first move as soon as it starts (one step of S ahead)",
+     "s->win_v * (s->t - s->win_t0) >= (double)(s->win_n + 1) * s->win_S * s->hz",
+     "s->win_v * (s->t - s->win_t0) >= (double)(s->win_n) * s->win_S * s->hz",
+     [("test_oracle_window", "test_antenna_stays_put_as_the_window_moves", {})]),
+    ("moving window: antenna carried along with the window",
+     "const int64_t ka = s->ka - s->win_n * s->win_S;", "const int64_t ka = s->ka;",
+     [("test_oracle_window", "test_antenna_stays_put_as_the_window_moves", {})]),
 ]
 
 

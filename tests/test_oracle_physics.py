@@ -310,3 +310,26 @@ def test_lattice_jitter_is_symmetric_and_bounded(oracle_mod):
         assert off.max() > 0.95 * J and off.min() < -0.95 * J, (ax, off.min(), off.max())
         sigma = J / math.sqrt(3.0)
         assert abs(off.mean()) < 4 * sigma / math.sqrt(off.size), (ax, off.mean())
+
+
+@pytest.mark.parametrize("gam", [1.0, 5.0])
+def test_plasma_with_its_ions_is_neutral(oracle_mod, gam):
+    # lab frame: the immobile ions are a background equal and opposite to the
+    # electrons' charge at load; boosted frame: every electron has its
+    # drifting ion at the same point.  Either way the charge density is zero
+    # on every node, and the ions' density is +gamma n inside the plasma
+    O = oracle_mod
+    o = O.Oracle(O.GridParams(dim=2, nx=8, nz=96, dx=0.5, dz=0.25, gamma_boost=gam, bc_z=1, npass=0))
+    ne = 0.01
+    z0, z1 = 0.15 * o.Lz, 0.85 * o.Lz                    # simulation-frame extent of the plasma
+    o.load_plasma(O.PlasmaParams(ne=ne, z_start=gam * z0, z_end=gam * z1, ramp=0.0, ppc=(2, 1, 2), jitter=0.1,
+                                 ions=1))
+    rho = o.rho()
+    assert np.abs(rho).max() <= 1e-14 * gam * ne
+    if gam == 1.0:
+        inner = o.rho_background()[int((z0 + 2.0) / o.hz):int((z1 - 2.0) / o.hz)]
+        assert abs(inner.mean() - ne) < 1e-2 * ne
+    else:
+        e, i = o.particles(0), o.particles(1)
+        assert np.array_equal(e["id"], i["id"]) and np.array_equal(e["w"], i["w"])
+        assert np.array_equal(e["z"], i["z"])

@@ -8,6 +8,8 @@ pulse's Gaussian tails reaching the window's ends), a plasma at rest seen
 through the window is the lattice of a long box, point for point, and so is
 a boosted plasma drifting through a moving window.
 """
+import math
+
 import numpy as np
 
 
@@ -86,3 +88,31 @@ def test_boosted_plasma_through_window_matches_long_box(oracle_mod):
         ids = set(a["id"].tolist())
         inner = (b["z"] > zw + 1e-9) & (b["z"] < zw + win.Lz - 1e-9)
         assert all(i in ids for i in b["id"][inner].tolist())
+
+
+def test_antenna_stays_put_as_the_window_moves(oracle_mod):
+    # the window starts moving (at c) while the antenna, 25 lambda0 into the
+    # box, is still emitting: the antenna stays at its launch position, so the
+    # forward pulse in the window's upper half is the long box's, node for
+    # node; and the window has moved by whole steps of S cells, one each time
+    # v (t - t0) reached the next multiple of S hz
+    O = oracle_mod
+    dz, nz, S = 1 / 16, 512, 16
+    laser = O.LaserParams(a0=1.0, waist=1e9, fwhm=3.0, z_antenna=25.0, pol=1)
+    win = O.Oracle(O.GridParams(dim=2, nx=4, nz=nz, dx=1.0, dz=dz, npass=0, bc_z=1))
+    big = O.Oracle(O.GridParams(dim=2, nx=4, nz=3 * nz, dx=1.0, dz=dz, npass=0, bc_z=1))
+    for o in (win, big):
+        o.set_laser(laser)
+    v, t0 = 1.0, 4.0
+    win.set_window(v, t0, S)
+    n = int(30 / win.dt)
+    win.step(n)
+    big.step(n)
+    zw = win.z_window
+    assert zw == S * dz * math.floor(v * (n * win.dt - t0) / (S * dz))
+    kw = int(round(zw / dz))
+    up = slice(nz // 2, nz - 4)                 # the forward pulse; the backward one left through the bottom
+    for c in ("Ey", "Bx"):
+        a, b = win.field(c)[up], big.field(c)[kw:kw + nz + 1][up]
+        assert np.abs(b).max() > 0.9
+        assert np.abs(a - b).max() < 1e-12 * np.abs(b).max(), c
