@@ -115,3 +115,38 @@ def test_gather_reproduces_linear_fields(oracle_mod, dim, order):
         a, b, cc, d = coefs[c]
         expect = a + b * px + (cc * py if dim == 3 else 0.0) + d * pz
         np.testing.assert_allclose(eb[:, c], expect, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("dim,order", [(2, 1), (2, 2), (3, 1)])
+def test_gather_wraps_periodic_boundaries(oracle_mod, dim, order):
+    # with periodic x (y) and z the gather is the sum over every node of the
+    # grid of F times the shape of the particle's periodic distance to it:
+    # brute force over all nodes, at particles next to the box's faces
+    G = oracle_mod.GridParams
+    g = G(dim=dim, nx=6, ny=5 if dim == 3 else 1, nz=7, dx=0.7, dy=0.9, dz=0.3, shape=order, bc_z=0)
+    o = oracle_mod.Oracle(g)
+    rng = np.random.default_rng(17 + order)
+    for c in range(6):
+        o.field(c)[...] = rng.normal(size=o.field(c).shape)
+        o.field(c)[g.nz] = 1e3                       # the unused plane of a periodic grid: never read
+    n = 60
+    eps = 0.05                                       # within eps cells of the x faces
+    px = np.where(rng.uniform(size=n) < 0.5, rng.uniform(0, eps, n) * o.hx, o.Lx - rng.uniform(0, eps, n) * o.hx)
+    pz = np.where(rng.uniform(size=n) < 0.5, rng.uniform(0, 0.6, n) * o.hz, o.Lz - rng.uniform(0, 0.6, n) * o.hz)
+    py = rng.uniform(0, o.Ly, n) if dim == 3 else np.zeros(n)
+    eb = o.gather(px, py, pz)
+
+    def periodic_weights(xi, m):
+        d = xi - np.arange(m)
+        d = d - m * np.round(d / m)                   # the periodic distance, in (-m/2, m/2]
+        return np.array([oracle_mod.shape(order, v) for v in d])
+
+    for p in range(n):
+        for c in range(6):
+            sx, sy, sz = COMP_STAG[c]
+            wx = periodic_weights(px[p] / o.hx - sx, g.nx)
+            wz = periodic_weights(pz[p] / o.hz - sz, g.nz)
+            wy = periodic_weights(py[p] / o.hy - sy, o.ny) if dim == 3 else np.ones(1)
+            f = o.field(c)[:g.nz]
+            expect = np.einsum("kji,k,j,i->", f, wz, wy, wx)
+            assert abs(eb[p, c] - expect) < 1e-12 * (1 + abs(expect)), (p, c, eb[p, c], expect)

@@ -286,6 +286,16 @@ CASES = [
     ("moving window: antenna carried along with the window",
      "const int64_t ka = s->ka - s->win_n * s->win_S;", "const int64_t ka = s->ka;",
      [("test_oracle_window", "test_antenna_stays_put_as_the_window_moves", {})]),
+    ("Boris: rotation with gamma of u^{n-1/2} instead of u-",
+     "const double gm = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);",
+     "const double gm = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);",
+     [("test_oracle_particles", "test_boris_step_satisfies_its_implicit_form", {})]),
+    ("gather: periodic z wrapped over nz + 1 planes",
+     "        if (s->g.bc_z == 0)\n            k = wrap_index(k, s->g.nz);\n        else if (k < 0 || k > zmax)\n"
+     "            continue;\n        for (int cy",
+     "        if (s->g.bc_z == 0)\n            k = wrap_index(k, s->g.nz + 1);\n        else if (k < 0 || k > zmax)\n"
+     "            continue;\n        for (int cy",
+     [("test_oracle_basics", "test_gather_wraps_periodic_boundaries", {"dim": 2, "order": 1})]),
 ]
 
 

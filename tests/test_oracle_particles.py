@@ -184,3 +184,24 @@ def test_particles_leaving_through_absorbing_ends_are_removed(oracle_mod, sp):
     assert np.array_equal(np.sort(p["id"]), ids[stay])
     got = dict(zip(p["id"].tolist(), p["z"]))
     assert max(abs(got[i] - z1[i]) for i in ids[stay]) < 1e-12
+
+
+def test_boris_step_satisfies_its_implicit_form(oracle_mod):
+    # Boris (1970): with u- = u + eps E and u+ = u_new - eps E (eps = pi (q/m)
+    # dt, the half impulse), the magnetic part is the rotation defined
+    # implicitly by u+ - u- = (u+ + u-) x t, t = eps B / gamma(u-), so that
+    # |u+| = |u-|.  Checked on relativistic particles in strong fields, where
+    # taking gamma anywhere else than at u- is far outside round-off.
+    rng = np.random.default_rng(23)
+    dt = 0.05
+    for q_over_m in (-1.0, 1.0):
+        eps = math.pi * q_over_m * dt
+        for _ in range(50):
+            u = rng.normal(scale=5.0, size=3)
+            e = rng.normal(scale=10.0, size=3)
+            b = rng.normal(scale=10.0, size=3)
+            un = np.asarray(oracle_mod.boris(u, e, b, q_over_m, dt))
+            um, up = u + eps * e, un - eps * e
+            t = eps * b / math.sqrt(1.0 + um @ um)
+            assert abs(up @ up - um @ um) <= 1e-12 * (um @ um)
+            assert np.abs((up - um) - np.cross(up + um, t)).max() <= 1e-12 * (1.0 + np.abs(um).max())
