@@ -187,3 +187,35 @@ def test_boosted_wake_back_transformed_matches_lab_wake(oracle_mod, gam):
     assert abs(abs(ez_b[ib]) - abs(ez_l[il])) / abs(ez_l[il]) < 0.05
     assert np.sign(ez_b[ib]) == np.sign(ez_l[il])
     assert abs(Z[ib] - Z[il]) <= 2 * (1 / 32)            # the same lab position (two lab cells)
+
+
+def test_snapshots_of_a_windowed_run_match_the_long_box(oracle_mod):
+    # A boosted pulse followed by a window moving at c once the antenna has
+    # stopped emitting: the lab snapshot points the window fills carry the
+    # same fields as those of a long fixed box (the window holds the long
+    # box's fields at the same absolute positions), so both snapshots agree
+    # wherever both are filled.
+    O = oracle_mod
+    gam, dzl = 1.5, 1 / 32
+    laser = O.LaserParams(a0=1.0, waist=1e9, fwhm=1.0, z_antenna=0.0, pol=1)
+    win = O.Oracle(O.GridParams(dim=2, nx=4, nz=400, dx=1.0, dz=dzl, gamma_boost=gam, npass=0, bc_z=1))
+    big = O.Oracle(O.GridParams(dim=2, nx=4, nz=1200, dx=1.0, dz=dzl, gamma_boost=gam, npass=0, bc_z=1))
+    T, Z0, nzl = 97.0, 80.0, int(30 / dzl)
+    for o in (win, big):
+        o.set_laser(laser)
+        o.btd_setup(O.BtdParams(nsnap=1, t0=T, dt=1.0, z0=Z0, dz=dzl, nz=nzl, plane=0))
+    win.set_window(1.0, 16.0, 16)
+    beta = win.beta
+    t_last = gam * (T - beta * Z0) + 2.0                 # the latest event of the snapshot
+    n = int(t_last / win.dt) + 2
+    win.step(n)
+    big.step(n)
+    assert win.z_window > 0.5 * win.Lz
+    fa, ma = win.btd_snapshot(0)
+    fb, mb = big.btd_snapshot(0)
+    both = ma & mb
+    assert both.sum() > 300
+    for c in ("Ey", "Bx"):
+        a, b = fa[c][both, 0], fb[c][both, 0]
+        assert np.abs(b).max() > 0.5
+        assert np.abs(a - b).max() < 1e-4 * np.abs(b).max(), c

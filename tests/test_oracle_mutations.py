@@ -296,6 +296,9 @@ CASES = [
      "        if (s->g.bc_z == 0)\n            k = wrap_index(k, s->g.nz + 1);\n        else if (k < 0 || k > zmax)\n"
      "            continue;\n        for (int cy",
      [("test_oracle_basics", "test_gather_wraps_periodic_boundaries", {"dim": 2, "order": 1})]),
+    ("snapshots: event height not taken relative to the moving window",
+     "const double zp = gam * (Z - beta * T) - opic_window(s);", "const double zp = gam * (Z - beta * T);",
+     [("test_oracle_btd", "test_snapshots_of_a_windowed_run_match_the_long_box", {})]),
 ]
 
 
