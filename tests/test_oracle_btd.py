@@ -219,3 +219,28 @@ def test_snapshots_of_a_windowed_run_match_the_long_box(oracle_mod):
         a, b = fa[c][both, 0], fb[c][both, 0]
         assert np.abs(b).max() > 0.5
         assert np.abs(a - b).max() < 1e-4 * np.abs(b).max(), c
+
+
+def test_on_axis_snapshot_is_the_middle_column(oracle_mod):
+    # an electrostatic field varying across x, Ex'(x) = cos(2 pi x / Lx) at
+    # Ex's own staggered x (static: its curl is zero), seen from the lab: the
+    # on-axis snapshot is the column nx/2 of the full-plane one, and both are
+    # gamma Ex' with By = gamma beta Ex' there
+    O = oracle_mod
+    gam, nx = 3.0, 8
+    g = O.GridParams(dim=2, nx=nx, nz=96, dx=1.0, dz=1 / 16, gamma_boost=gam, npass=0, bc_z=1)
+    runs = []
+    for plane in (0, 1):
+        o = O.Oracle(g)
+        x = (np.arange(nx) + 0.5) * o.hx
+        o.field("Ex")[...] = np.cos(2 * math.pi * x / o.Lx)
+        T0 = gam * o.beta * o.Lz
+        o.btd_setup(O.BtdParams(nsnap=1, t0=T0, dt=1.0, z0=o.beta * T0 - 2.0, dz=1 / 16, nz=200, plane=plane))
+        o.step(int((gam * T0 + 5.0) / o.dt) + 1)
+        runs.append(o.btd_snapshot(0))
+    (f0, m0), (f1, m1) = runs
+    assert m0.sum() > 50 and np.array_equal(m0, m1)
+    ex_mid = math.cos(2 * math.pi * (nx // 2 + 0.5) / nx)
+    assert np.allclose(f0["Ex"][m0, 0], f1["Ex"][m1, nx // 2], atol=1e-13, rtol=0)
+    assert np.allclose(f0["Ex"][m0, 0], gam * ex_mid, atol=1e-12, rtol=0)
+    assert np.allclose(f0["By"][m0, 0], gam * o.beta * ex_mid, atol=1e-12, rtol=0)

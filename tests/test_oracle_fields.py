@@ -271,3 +271,30 @@ def test_antenna_beam_has_the_waist(oracle_mod, pol):
     ratio = peak / peak[np.argmin(np.abs(x - xc))]
     assert peak.max() > 0.5
     assert np.abs(ratio[near] - expect[near]).max() < 0.02, np.abs(ratio[near] - expect[near]).max()
+
+
+
+def test_antenna_beam_has_the_waist_across_y(oracle_mod):
+    # the same in 3D for a beam polarised along y: its Ey sits on
+    # half-integer y, and the peak |Ey| a wavelength ahead follows
+    # exp(-((x - xc)^2 + (y - yc)^2) / w0^2) at those staggered points
+    G, L = oracle_mod.GridParams, oracle_mod.LaserParams
+    w0 = 4.0
+    g = G(dim=3, nx=24, ny=48, nz=128, dx=1.0, dy=0.5, dz=1.0 / 16, cfl=0.99, bc_z=1, npass=0)
+    o = oracle_mod.Oracle(g)
+    o.set_laser(L(a0=1.0, waist=w0, fwhm=2.0, z_antenna=1.0, pol=1))
+    kp = int(round(2.0 / o.hz))
+    peak = np.zeros((g.ny, g.nx))
+    while o.t < 12.0:
+        o.step(1)
+        peak = np.maximum(peak, np.abs(o.field("Ey")[kp]))
+    x = np.arange(g.nx) * o.hx
+    y = (np.arange(g.ny) + 0.5) * o.hy
+    xc, yc = 0.5 * g.nx * o.hx, 0.5 * g.ny * o.hy
+    ic = int(np.argmin(np.abs(x - xc)))
+    col = peak[:, ic]                                    # the profile across y through the axis
+    expect = np.exp(-((y - yc) / w0) ** 2)
+    near = np.abs(y - yc) < 2.0 * w0
+    ratio = col / col.max() * expect[np.argmax(col)]
+    assert peak.max() > 0.5
+    assert np.abs(ratio[near] - expect[near]).max() < 0.02, np.abs(ratio[near] - expect[near]).max()

@@ -299,6 +299,43 @@ CASES = [
     ("snapshots: event height not taken relative to the moving window",
      "const double zp = gam * (Z - beta * T) - opic_window(s);", "const double zp = gam * (Z - beta * T);",
      [("test_oracle_btd", "test_snapshots_of_a_windowed_run_match_the_long_box", {})]),
+    ("antenna 3D: Jy sheet at integer y",
+     "const double sy = (l->pol == 1 && s->g.dim == 3) ? 0.5 : 0.0;", "const double sy = 0.0;",
+     [("test_oracle_fields", "test_antenna_beam_has_the_waist_across_y", {})]),
+    ("snapshots: on-axis line taken at x = 0 instead of the middle column",
+     "const int64_t i = nxs == 1 ? s->g.nx / 2 : is;", "const int64_t i = nxs == 1 ? 0 : is;",
+     [("test_oracle_btd", "test_on_axis_snapshot_is_the_middle_column", {})]),
+    ("filter: x neighbour two nodes away",
+     "lo = tmp[fidx(s, wrap_index(i - 1, nx), j, k)];", "lo = tmp[fidx(s, wrap_index(i - 2, nx), j, k)];",
+     [("test_oracle_fields", "test_filter_transfer_function", {}),
+      ("test_oracle_fields", "test_filter_is_its_own_transpose", {"dim": 2, "bc": 1, "npass": 1})]),
+    ("time step in 2D with half the z term",
+     "s->dt = g->cfl / sqrt(1.0 / (s->hx * s->hx) + 1.0 / (s->hz * s->hz));",
+     "s->dt = g->cfl / sqrt(1.0 / (s->hx * s->hx) + 0.5 / (s->hz * s->hz));",
+     [("test_oracle_fields", "test_yee_discrete_eigenmode", {"dim": 2, "pol": "TE"}),
+      ("test_oracle_fields", "test_yee_discrete_eigenmode", {"dim": 2, "pol": "TM"}),
+      ("test_oracle_physics", "test_cold_plasma_oscillation", {})]),
+    ("Yee: sign of dEx/dy in the Bz update",
+     "Bz[o] -= h * (dEy_dx - dEx_dy);", "Bz[o] -= h * (dEy_dx + dEx_dy);",
+     [("test_oracle_fields", "test_yee_discrete_eigenmode", {"dim": 3, "pol": "A"}),
+      ("test_oracle_fields", "test_yee_discrete_eigenmode", {"dim": 3, "pol": "B"})]),
+    ("Mur at the bottom end: old planes swapped for Ey",
+     "Ey[q] = ey1 + cm * (Ey[plane + q] - ey0);", "Ey[q] = ey0 + cm * (Ey[plane + q] - ey1);",
+     [("test_oracle_fields", "test_mur_absorbs_normal_pulse", {"pol": 1})]),
+    ("injection: entering ions at rest instead of drifting",
+     "                species_push(&s->sp[1], q->x, q->y, zb, 0.0, 0.0, uz0, q->w, q->id);",
+     "                species_push(&s->sp[1], q->x, q->y, zb, 0.0, 0.0, 0.0, q->w, q->id);",
+     [("test_oracle_physics", "test_injected_plasma_matches_free_drift", {}),
+      ("test_oracle_physics", "test_boosted_plasma_without_laser_stays_field_free", {})]),
+    ("lab view: By's partner Ex taken from the planes below",
+     "case OPIC_BY: v = gam * (s->f[OPIC_BY][o] + beta * zmean(s, s->f[OPIC_EX], OPIC_EX, i, j, k, 1)); break;",
+     "case OPIC_BY: v = gam * (s->f[OPIC_BY][o] + beta * zmean(s, s->f[OPIC_EX], OPIC_EX, i, j, k, 0)); break;",
+     [("test_oracle_diagnostics", "test_lab_fields_pair_each_component_with_its_staggered_partner", {})]),
+    ("moving window: particles within a cell of the bottom removed too",
+     "            if (p->a[OPIC_PZ][k] < 0.0)\n                species_remove(p, k);",
+     "            if (p->a[OPIC_PZ][k] < s->hz)\n                species_remove(p, k);",
+     [("test_oracle_window", "test_static_plasma_through_window_is_the_lattice", {}),
+      ("test_oracle_window", "test_boosted_plasma_through_window_matches_long_box", {})]),
 ]
 
 
@@ -339,8 +376,9 @@ def _run_pins(source: str, tmp_path, tag: str, pins) -> list:
         fn = getattr(_module(f"pins_{fname}_{tag}", os.path.join(TESTS, fname + ".py")), test)
         try:
             fn(O, **params)
-        except (AssertionError, ArithmeticError, ValueError):
-            # a failed check, or arithmetic the pin cannot even complete
+        except (AssertionError, ArithmeticError, ValueError, RuntimeError):
+            # a failed check, or arithmetic (a fit, a bound) the pin cannot
+            # even complete on the planted copy
             failed.append(test)
     # the pins ran on the compiled copy, not on the oracle's own build
     assert O._lib is not None and O._lib._name == so
@@ -359,6 +397,7 @@ def test_unplanted_copy_passes_every_pin(source, tmp_path):
     assert _run_pins(source + "\n/* unchanged */\n", tmp_path, "control", pins) == []
 
 
+@pytest.mark.filterwarnings("ignore::RuntimeWarning")   # (overflow in a pin's fit on an unstable copy)
 @pytest.mark.parametrize("case", range(len(CASES)), ids=[c[0] for c in CASES])
 def test_planted_mistake_fails_a_pin(source, tmp_path, case):
     what, old, new, pins = CASES[case]
