@@ -57,6 +57,7 @@ struct opic {
     int64_t npend, cappend;
     double ion_u[3];
     int has_ions;
+    int bg_ions;          /* lab frame: immobile ions as a static background */
     int laser_on;
     opic_laser las;
     int ka;
@@ -279,7 +280,7 @@ double opic_density(const opic_plasma *p, double z)
     return p->ne * r * f;
 }
 
-static void deposit_rho_species(const opic *s, const species *p, double q, double *rho);
+static void deposit_rho_species(const opic *s, const species *p, int64_t from, double q, double *rho);
 
 int64_t opic_load_plasma(opic *s, const opic_plasma *p)
 {
@@ -358,7 +359,8 @@ int64_t opic_load_plasma(opic *s, const opic_plasma *p)
         /* immobile lab-frame ions: a static background equal and opposite to
            the electron charge at load time */
         memset(s->rho_bg, 0, (size_t)s->nn * sizeof(double));
-        deposit_rho_species(s, &s->sp[0], 1.0, s->rho_bg);
+        deposit_rho_species(s, &s->sp[0], 0, 1.0, s->rho_bg);
+        s->bg_ions = 1;
     }
     return placed;
 }
@@ -647,14 +649,15 @@ void opic_deposit_current(opic *s, double qw, const double x0[3], const double x
     }
 }
 
-/* nodal charge density q w S S S / V of one species (diagnostic) */
-static void deposit_rho_species(const opic *s, const species *p, double q, double *rho)
+/* nodal charge density q w S S S / V of the particles from index `from` on of
+   one species (diagnostic) */
+static void deposit_rho_species(const opic *s, const species *p, int64_t from, double q, double *rho)
 {
     const int S = s->g.shape;
     const int dim3 = s->g.dim == 3;
     const double vol = dim3 ? s->hx * s->hy * s->hz : s->hx * s->hz;
     const int zmax = zmax_of(s, 0.0);
-    for (int64_t n = 0; n < p->n; ++n) {
+    for (int64_t n = from; n < p->n; ++n) {
         const double xi = p->a[OPIC_PX][n] / s->hx, zi = p->a[OPIC_PZ][n] / s->hz;
         const double yi = dim3 ? p->a[OPIC_PY][n] / s->hy : 0.0;
         const double qw = q * p->a[OPIC_PW][n] / vol;
@@ -696,9 +699,9 @@ void opic_deposit_rho(const opic *s, double *rho)
 {
     for (int64_t n = 0; n < s->nn; ++n)
         rho[n] = s->rho_bg[n];
-    deposit_rho_species(s, &s->sp[0], -1.0, rho);
+    deposit_rho_species(s, &s->sp[0], 0, -1.0, rho);
     if (s->sp[1].n > 0)
-        deposit_rho_species(s, &s->sp[1], 1.0, rho);
+        deposit_rho_species(s, &s->sp[1], 0, 1.0, rho);
 }
 
 /* --------------------------------------------------------------- push */
@@ -979,7 +982,12 @@ static void window_move(opic *s)
         }
     }
     s->win_n += 1;
+    const int64_t n0 = s->sp[0].n;
     inject_at(s, s->t);
+    /* the plasma the window now covers brings its immobile ions along: their
+       background is that of its electrons, as at load */
+    if (s->bg_ions)
+        deposit_rho_species(s, &s->sp[0], n0, 1.0, s->rho_bg);
 }
 
 /* --------------------------------------------- back-transformed snapshots */

@@ -116,3 +116,20 @@ def test_antenna_stays_put_as_the_window_moves(oracle_mod):
         a, b = win.field(c)[up], big.field(c)[kw:kw + nz + 1][up]
         assert np.abs(b).max() > 0.9
         assert np.abs(a - b).max() < 1e-12 * np.abs(b).max(), c
+
+
+def test_lab_plasma_with_immobile_ions_stays_neutral_through_the_window(oracle_mod):
+    # the immobile ions of a lab plasma are its neutralising background: the
+    # plasma a moving window brings into view brings its background along, so
+    # the charge density stays zero as the window moves, on every node but
+    # the bottom one (whose electrons just below the window have left it
+    # while their background share on that node stays)
+    O = oracle_mod
+    o = O.Oracle(O.GridParams(dim=2, nx=8, nz=128, dx=0.5, dz=1 / 16, npass=0, bc_z=1))
+    o.load_plasma(O.PlasmaParams(ne=0.01, z_start=1.0, z_end=30.0, ramp=0.5, ppc=(2, 1, 3), jitter=0.2, ions=1))
+    o.set_window(0.9, 1.5, 16)
+    assert np.abs(o.rho()).max() <= 1e-14 * 0.01
+    o.step(int(20.0 / o.dt))
+    assert o.z_window > 10.0
+    assert np.abs(o.rho_background()).max() > 0.5 * 0.01
+    assert np.abs(o.rho()[1:]).max() <= 1e-14 * 0.01
