@@ -134,10 +134,13 @@ void opic_step_phases(opic *s, unsigned mask);
    cells at once (n counts the moves): every field plane k takes plane k + S,
    the top S planes become zero, particle z decreases by S hz (particles below
    z = 0 are removed), the antenna plane moves S planes down (it stops below
-   plane 2), and the plasma of the newly covered layer enters.  Positions stay
+   plane 2), and the plasma of the newly covered layer enters (in the lab
+   frame with its immobile ions' background, as at load).  Positions stay
    relative to the window; opic_window() is its displacement n S hz.  Parity
    status: pinned (a pulse in the window matches the same pulse in a long
-   fixed box; a static plasma seen through the window is the lattice). */
+   fixed box, also while the antenna still emits; a static plasma seen through
+   the window is the lattice, a boosted one the long box's, and a lab plasma
+   stays neutral; the moves follow the schedule). */
 int opic_set_window(opic *s, double v, double t0, int S);   /* 0, or -1 on bad arguments */
 double opic_window(const opic *s);
 
