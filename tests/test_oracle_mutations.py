@@ -346,6 +346,35 @@ CASES = [
     ("moving window: the covered plasma brought in without its ions' background",
      "    if (s->bg_ions)\n        deposit_rho_species(s, &s->sp[0], n0, 1.0, s->rho_bg);", "",
      [("test_oracle_window", "test_lab_plasma_with_immobile_ions_stays_neutral_through_the_window", {})]),
+    ("antenna: envelope peak at 2 tau instead of 3 tau",
+     "const double spk = l->t_peak >= 0.0 ? l->t_peak : 3.0 * tau;",
+     "const double spk = l->t_peak >= 0.0 ? l->t_peak : 2.0 * tau;",
+     [("test_oracle_fields", "test_antenna_amplitude_and_carrier", {})]),
+    ("antenna: polarisations swapped",
+     "const int c = l->pol == 0 ? OPIC_JX : OPIC_JY;", "const int c = l->pol == 0 ? OPIC_JY : OPIC_JX;",
+     [("test_oracle_fields", "test_antenna_amplitude_and_carrier", {})]),
+    ("antenna: allowed on plane 1",
+     "    if (ka < 2)\n        ka = 2;\n    if (ka > s->g.nz - 2)", "    if (ka < 1)\n        ka = 1;\n    if (ka > s->g.nz - 2)",
+     [("test_oracle_fields", "test_antenna_amplitude_and_carrier", {})]),
+    ("antenna: default centre half a cell off the box's middle",
+     "        s->las.xc = 0.5 * s->Lx;", "        s->las.xc = 0.5 * s->Lx + 0.5 * s->hx;",
+     [("test_oracle_fields", "test_antenna_beam_has_the_waist", {"pol": 0})]),
+    ("Mur: old E taken from plane nz - 2",
+     "const int planes[4] = {0, 1, nz - 1, nz};", "const int planes[4] = {0, 1, nz - 2, nz};",
+     [("test_oracle_fields", "test_mur_absorbs_normal_pulse", {"pol": 1})]),
+    ("filter: every component given the integer-z planes",
+     "    const int zmax = zmax_of(s, STAG[c][2]);\n    memcpy(tmp", "    const int zmax = zmax_of(s, 0.0);\n    memcpy(tmp",
+     [("test_oracle_fields", "test_filter_absorbing_z_boundary_and_dc", {})]),
+    ("Boris: second half impulse subtracted",
+     "        u[d] = upl[d] + eps * e[d];", "        u[d] = upl[d] - eps * e[d];",
+     [("test_oracle_particles", "test_boris_uniform_e", {})]),
+    ("diagnostics: electrons counted with positive charge",
+     "        kahan_add(&q, -e->a[OPIC_PW][p]);", "        kahan_add(&q, e->a[OPIC_PW][p]);",
+     [("test_oracle_diagnostics", "test_kinetic_energy_and_charge_of_a_cold_plasma", {"gam": 13.0})]),
+    ("snapshots: points marked filled although a component was out of range",
+     "            if (ok)\n                s->btd_fill[(size_t)js * b->nz + k] = 1;",
+     "            s->btd_fill[(size_t)js * b->nz + k] = 1;",
+     [("test_oracle_btd", "test_snapshot_coverage", {})]),
 ]
 
 
