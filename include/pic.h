@@ -200,12 +200,16 @@ typedef struct pic_diag {
    Doppler-stretched laser wavelength. */
 pic_status pic_init_grid(const pic_grid_params *p, pic_ctx **out);
 
-/* Buffer sizes and derived quantities of a context. */
+/* Buffer sizes and derived quantities of a context (the simulation-frame cell
+   sizes and time step of pic_init_grid).  No counterpart in the paper: the
+   library's memory contract.  PIC_ERR_ARG for a NULL argument. */
 pic_status pic_query_sizes(const pic_ctx *ctx, pic_sizes *out);
 
 /* Binds the caller-owned device buffers and clears them (fields, particle
    counts, error word) on the stream.  Pointers must be 256-byte aligned and
-   at least the queried sizes.  May be called once per context. */
+   at least the queried sizes.  May be called once per context.  No
+   counterpart in the paper.  PIC_ERR_ARG for a NULL or misaligned buffer,
+   PIC_ERR_STATE if buffers are already bound. */
 pic_status pic_bind_buffers(pic_ctx *ctx, const pic_buffers *b);
 
 /* Paper: a plasma at rest in the laboratory, seen from the boosted frame
@@ -255,11 +259,14 @@ pic_status pic_launch_laser(pic_ctx *ctx, const pic_laser_params *p);
    wavelengths as in section "Mitigation of a numerical instability". */
 pic_status pic_step(pic_ctx *ctx, int nsteps);
 
-/* Same as pic_step without the synchronisation and the error check. */
+/* Same as pic_step without the synchronisation and the error check (read
+   the device error word later with pic_step(ctx, 0)).  PIC_ERR_ARG for
+   nsteps < 0, PIC_ERR_STATE before pic_bind_buffers. */
 pic_status pic_step_async(pic_ctx *ctx, int nsteps);
 
 /* One step restricted to the phases in mask (PIC_PH_* bits), synchronised
-   and checked like pic_step.  Used to test each phase on its own. */
+   and checked like pic_step.  Used to test each phase on its own (the phases
+   are those of pic_step).  PIC_ERR_ARG for unknown bits. */
 pic_status pic_step_phases(pic_ctx *ctx, unsigned mask);
 
 /* --------------------------------------------------------------- output */
@@ -286,12 +293,17 @@ enum { PIC_FRAME_BOOST = 0, PIC_FRAME_LAB = 1 };
 pic_status pic_get_fields(pic_ctx *ctx, unsigned mask, int frame, void *dst, size_t dst_bytes,
                           int dst_is_device);
 
-/* Overwrites the selected components from src, same layout as pic_get_fields. */
+/* Overwrites the selected components from src, same layout as pic_get_fields
+   (simulation frame).  No counterpart in the paper: initial and test
+   conditions.  PIC_ERR_ARG for a NULL src, an empty or unknown mask or too
+   small a source, PIC_ERR_STATE before pic_bind_buffers. */
 pic_status pic_set_fields(pic_ctx *ctx, unsigned mask, const void *src, size_t src_bytes,
                           int src_is_device);
 
 /* Component c on the line i = nx/2, j = ny/2, k = 0..nz (nz+1 elements of
-   elem_bytes): the on-axis field history diagnostic of the paper's Fig. 2. */
+   elem_bytes): the on-axis field history diagnostic of the paper's Fig. 2.
+   PIC_ERR_ARG for a NULL dst, an unknown component or too small a
+   destination, PIC_ERR_STATE before pic_bind_buffers. */
 pic_status pic_get_axis(pic_ctx *ctx, int component, void *dst, size_t dst_bytes,
                         int dst_is_device);
 
@@ -305,7 +317,11 @@ pic_status pic_get_particles(pic_ctx *ctx, int species, double *dst, size_t dst_
 
 /* Nodal charge density (nz+1) x ny x nx of the particles (electrons and
    drifting ions, shape of the grid's order), elem_bytes each, into host or
-   device memory.  Lab-frame immobile ions are not included. */
+   device memory.  Lab-frame immobile ions are not included.  A diagnostic of
+   the charge that Esirkepov's deposition conserves (the continuity the
+   method's current deposition satisfies; no printed formula in the paper).
+   PIC_ERR_ARG for a NULL dst or too small a destination, PIC_ERR_STATE before
+   pic_bind_buffers. */
 pic_status pic_get_rho(pic_ctx *ctx, void *dst, size_t dst_bytes, int dst_is_device);
 
 /* Time, counts and FP64 Kahan-compensated sums (synchronises the stream):
@@ -327,7 +343,8 @@ pic_status pic_get_diagnostics(pic_ctx *ctx, pic_diag *out);
    (the first failure is returned; pic_last_error of each context has its
    detail).  The batch holds pointers only: the contexts stay the caller's and
    must outlive it.  PIC_ERR_STATE if a context is not bound, PIC_ERR_ARG for
-   n < 1 or a context listed twice. */
+   n < 1 or a context listed twice.  No counterpart in the paper, which runs
+   one stage at a time: the batch is the library's scan over stages. */
 typedef struct pic_batch pic_batch;
 pic_status pic_batch_create(pic_ctx *const *ctxs, int n, pic_batch **out);
 pic_status pic_batch_step(pic_batch *batch, int nsteps);
@@ -437,7 +454,9 @@ pic_status pic_btd_bytes(const pic_ctx *ctx, const pic_btd_params *p, size_t *by
 pic_status pic_btd_setup(pic_ctx *ctx, const pic_btd_params *p, void *buf, size_t bytes);
 
 /* Copies snapshot j to host or device memory: its [6][nz][nxs] elements,
-   then its nz int32 flags (1: filled). */
+   then its nz int32 flags (1: filled).  PIC_ERR_STATE when no snapshots are
+   being taken, PIC_ERR_ARG for a NULL dst, j out of range or too small a
+   destination. */
 pic_status pic_btd_get(pic_ctx *ctx, int j, void *dst, size_t dst_bytes, int dst_is_device);
 
 /* ---------------------------------------------------------------- adjoint */
@@ -502,7 +521,10 @@ pic_status pic_batch_adjoint(pic_batch *batch, const pic_adjoint_params *p, void
 
 /* ------------------------------------------------------------ checkpoint */
 
-/* Size of a compact snapshot (fields, live particles, time, laser) now. */
+/* Size of a compact snapshot (fields, live particles, time, laser) now.  The
+   snapshot calls have no counterpart in the paper: checkpoint and restart of
+   a run.  Each returns PIC_ERR_ARG for NULL arguments or too small a buffer
+   and PIC_ERR_STATE before pic_bind_buffers. */
 pic_status pic_state_bytes(pic_ctx *ctx, size_t *bytes);
 
 /* Writes the snapshot to host or device memory. */
@@ -533,7 +555,8 @@ pic_status pic_set_cell_sort(pic_ctx *ctx, int every);
 /* -------------------------------------------------------------- profiling */
 
 /* While enabled, every phase of later steps is bracketed by CUDA events on the
-   context's stream and the kernels the library launches are counted. */
+   context's stream and the kernels the library launches are counted.  No
+   counterpart in the paper (measurement).  PIC_ERR_ARG for a NULL context. */
 pic_status pic_profile(pic_ctx *ctx, int enable);
 
 /* Accumulated device time since the last read: ms[i] milliseconds and calls[i]
