@@ -238,7 +238,9 @@ pic_status pic_load_plasma(pic_ctx *ctx, const pic_plasma_params *p);
    working precision resolves the plasma's response; pic_get_particles adds
    the drift back.)  ids (may be NULL) are kept
    when track_ids is set.  Positions outside the box are rejected
-   (PIC_ERR_ARG); PIC_ERR_CAPACITY if a tile overflowed. */
+   (PIC_ERR_ARG); PIC_ERR_CAPACITY if a tile overflowed.  No counterpart in
+   the paper: explicit particles for tests and restarts (the paper's plasma
+   is pic_load_plasma's). */
 pic_status pic_load_particles(pic_ctx *ctx, int species, int64_t n, const double *state,
                               const int64_t *ids);
 
@@ -246,7 +248,9 @@ pic_status pic_load_particles(pic_ctx *ctx, int species, int64_t n, const double
    Paper: the laser is launched in the boosted frame, its lab-frame pulse
    Doppler-transformed (amplitude and frequency gamma (1 - beta), duration
    gamma (1 + beta); section "Effect of the hyperbolic rotation in Minkowski
-   space"). */
+   space").  PIC_ERR_ARG for a0 < 0, a waist or duration <= 0, a non-finite
+   z_antenna or an unknown polarisation.  A forward run of the adjoint taken
+   before this call no longer belongs to the context's run. */
 pic_status pic_launch_laser(pic_ctx *ctx, const pic_laser_params *p);
 
 /* ------------------------------------------------------------------ step */
@@ -311,7 +315,8 @@ pic_status pic_get_axis(pic_ctx *ctx, int component, void *dst, size_t dst_bytes
    layout (order unspecified); *n_out receives the count.  (Paper: the
    macroparticles of the PIC method; simulation-frame positions and momenta.)  With dst == NULL
    only *n_out is set.  ids (may be NULL) receives the lattice ids when
-   track_ids is set. */
+   track_ids is set.  PIC_ERR_ARG for an unknown species or too small a
+   destination, PIC_ERR_STATE before pic_bind_buffers. */
 pic_status pic_get_particles(pic_ctx *ctx, int species, double *dst, size_t dst_bytes,
                              int64_t *n_out, int64_t *ids);
 
@@ -329,7 +334,8 @@ pic_status pic_get_rho(pic_ctx *ctx, void *dst, size_t dst_bytes, int dst_is_dev
    electron kinetic energy sum w (gamma - 1), charge sum q w (drifting ions
    +1; lab-frame immobile ions are a background), both energies in units of
    n_c m c^2 lambda0^3.  (Paper: no counterpart; the energy budget of the
-   stage.) */
+   stage.)  PIC_ERR_ARG for a NULL out, PIC_ERR_STATE before
+   pic_bind_buffers. */
 pic_status pic_get_diagnostics(pic_ctx *ctx, pic_diag *out);
 
 /* ------------------------------------------------------------------ batch */
@@ -394,7 +400,8 @@ pic_status pic_batch_set_fused(pic_batch *batch, int fused);
 /* The graph the batch keeps (zeros before the first capture): its launch
    chains if it is the fused form (0: per context), the launches one replay
    issues (kernels and counter resets) and the steps it covers.  Any output
-   pointer may be NULL; PIC_ERR_ARG for a null batch. */
+   pointer may be NULL; PIC_ERR_ARG for a null batch.  No counterpart in the
+   paper. */
 pic_status pic_batch_graph_info(pic_batch *batch, int *fused, int64_t *launches_per_replay, int *steps);
 
 /* ---------------------------------------------------------- moving window */
@@ -444,7 +451,8 @@ typedef struct pic_btd_params {
 /* Bytes of the caller-owned device buffer of the snapshots: n_snapshots
    blocks of [6 components: Ex Ey Ez Bx By Bz][nz][nxs] elements (elem_bytes
    each, nxs = 1 for plane 0, nx for plane 1), then n_snapshots x nz int32
-   fill flags starting at a 256-byte boundary. */
+   fill flags starting at a 256-byte boundary.  PIC_ERR_ARG for NULL
+   arguments, invalid parameters or an unboosted grid. */
 pic_status pic_btd_bytes(const pic_ctx *ctx, const pic_btd_params *p, size_t *bytes);
 
 /* Zeroes buf (device memory of at least pic_btd_bytes, owned by the caller,
@@ -489,13 +497,17 @@ typedef struct {
 /* Bytes of the device buffer an adjoint run needs (ceil(N / K) checkpoints,
    one segment of K + 1 states or, with sub-checkpoints, K2 + 1 states and
    ceil(K / K2) sub-checkpoints, the cotangents).  PIC_ERR_ARG for an unsupported run,
-   PIC_ERR_STATE if a step has been taken since pic_load_plasma. */
+   PIC_ERR_STATE if a step has been taken since pic_load_plasma.  (The
+   library's adjoint: no counterpart in the paper.) */
 pic_status pic_adjoint_bytes(pic_ctx *ctx, const pic_adjoint_params *p, size_t *bytes);
 
 /* The forward run into buf (device memory of at least pic_adjoint_bytes bytes,
    owned by the caller and kept alive until pic_adjoint_backward).  fields_out
    (device, may be NULL) receives E^N, B^N: six components of (nz+1) ny nx
-   elements (ny = 1 in 2D), Ex Ey Ez Bx By Bz. */
+   elements (ny = 1 in 2D), Ex Ey Ez Bx By Bz.  The adjoint calls have no
+   counterpart in the paper (see above).  PIC_ERR_ARG for an unsupported run
+   (a moving window, invalid parameters) or too small a buffer, PIC_ERR_STATE
+   before pic_bind_buffers or once a step has been taken. */
 pic_status pic_adjoint_forward(pic_ctx *ctx, const pic_adjoint_params *p, void *buf, size_t bytes,
                                void *fields_out);
 
@@ -503,7 +515,7 @@ pic_status pic_adjoint_forward(pic_ctx *ctx, const pic_adjoint_params *p, void *
    fields_out).  grad (host, M + 2 doubles): dL/dc_1 .. dL/dc_M, dL/da0,
    dL/dw0.  PIC_ERR_STATE without a preceding pic_adjoint_forward, or when
    pic_load_plasma or pic_launch_laser has been called since it (the gradient
-   would belong to another run). */
+   would belong to another run).  No counterpart in the paper. */
 pic_status pic_adjoint_backward(pic_ctx *ctx, const void *cot, double *grad);
 
 /* The gradients of every run of a batch (the scan's reverse mode): for run
@@ -515,7 +527,7 @@ pic_status pic_adjoint_backward(pic_ctx *ctx, const void *cot, double *grad);
    them, so the runs' adjoint kernels execute concurrently; the call returns
    after one wait per stream, with the first failure (each context's
    pic_last_error has its detail).  PIC_ERR_ARG for null arrays or too small
-   a stride. */
+   a stride.  No counterpart in the paper. */
 pic_status pic_batch_adjoint(pic_batch *batch, const pic_adjoint_params *p, void *const *bufs,
                              const size_t *bytes, const void *const *cots, double *grads, int grad_stride);
 
@@ -527,7 +539,8 @@ pic_status pic_batch_adjoint(pic_batch *batch, const pic_adjoint_params *p, void
    and PIC_ERR_STATE before pic_bind_buffers. */
 pic_status pic_state_bytes(pic_ctx *ctx, size_t *bytes);
 
-/* Writes the snapshot to host or device memory. */
+/* Writes the snapshot to host or device memory (PIC_ERR_ARG if dst_bytes is
+   smaller than pic_state_bytes). */
 pic_status pic_get_state(pic_ctx *ctx, void *dst, size_t dst_bytes, int dst_is_device);
 
 /* Restores a snapshot taken from a context with the same grid parameters.
@@ -543,13 +556,14 @@ pic_status pic_set_state(pic_ctx *ctx, const void *src, size_t src_bytes, int sr
    it read them, so the order decays only by the particles that cross tiles.
    The results of a step do not depend on the order (the deposit sums in
    exact fixed point).  Synchronises the stream.  PIC_ERR_STATE before
-   pic_bind_buffers; the device error word is checked as after a step. */
+   pic_bind_buffers; the device error word is checked as after a step.  No
+   counterpart in the paper: a memory order of the particle store. */
 pic_status pic_sort_cells(pic_ctx *ctx);
 
 /* Sort by cell before every `every`-th step (the step count a multiple of
    every; 0, the default: never).  A context that sorts is stepped launch by
    launch (a batch does not capture it in a graph).  PIC_ERR_ARG for
-   every < 0. */
+   every < 0.  No counterpart in the paper. */
 pic_status pic_set_cell_sort(pic_ctx *ctx, int every);
 
 /* -------------------------------------------------------------- profiling */
@@ -563,7 +577,8 @@ pic_status pic_profile(pic_ctx *ctx, int enable);
    runs of phase bit i (i = 0..6, PIC_PH_ZERO_J .. PIC_PH_INJECT; slot 7, the
    TIME phase's, which launches nothing, holds the cell sorts of
    pic_set_cell_sort), *kernels the number of kernel launches.  Synchronises
-   the stream and resets the sums.  Any output pointer may be NULL. */
+   the stream and resets the sums.  Any output pointer may be NULL.  No
+   counterpart in the paper.  PIC_ERR_ARG for a NULL context. */
 pic_status pic_profile_read(pic_ctx *ctx, double ms[8], int64_t calls[8], int64_t *kernels);
 
 /* --------------------------------------------- allocation-free current filter */
